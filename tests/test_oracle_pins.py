@@ -1,0 +1,545 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, brute force on tiny inputs, closed forms, invariants,
+or a library routine in a special case where it computes the same thing.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import philox as px
+from oracle import squint_sac as o
+from paper_2602_21203_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- RNG
+
+def test_philox_known_answers():
+    """Philox4x32-10 reproduces the published known-answer vectors (Salmon et al., SC'11)."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = px.philox4x32_10(*v[:6])
+        assert [int(x) for x in out] == v[6:]
+
+
+def test_range_draw_is_floor_of_product():
+    """idx = floor(w n / 2^32) checked with Python big integers, and lies in [0, n)."""
+    rng = np.random.default_rng(1)
+    w = rng.integers(0, 2 ** 32, size=1000, dtype=np.uint64)
+    for n in (1, 17, 256, 100_000, 2 ** 31 + 7):
+        got = px.mulhi_range(w, n)
+        ref = np.array([(int(x) * n) >> 32 for x in w])
+        assert np.array_equal(got, ref)
+        assert got.min() >= 0 and got.max() < n
+
+
+def test_uniform_and_normal_moments():
+    """Uniforms lie strictly inside (0,1); Box-Muller normals have mean 0, variance 1, kurtosis 3."""
+    w = px.block(7, np.arange(200_000), 3, 11)
+    u = px.uniform01(w[0])
+    assert u.min() > 0 and u.max() < 1
+    assert abs(u.mean() - 0.5) < 3e-3
+    e = px.normal_pairs(7, px.STREAM_EPS_ACTOR, 5, 100_000, 6).ravel()
+    assert abs(e.mean()) < 1e-2 and abs(e.var() - 1) < 1e-2
+    assert abs(np.mean(e ** 4) - 3) < 5e-2
+
+
+def test_streams_are_distinct():
+    a = px.block(0, np.arange(64), px.STREAM_INDEX, 0)[0]
+    b = px.block(0, np.arange(64), px.STREAM_SHIFT_T, 0)[0]
+    c = px.block(0, np.arange(64), px.STREAM_INDEX, 1)[0]
+    assert not np.array_equal(a, b) and not np.array_equal(a, c)
+
+
+# ---------------------------------------------------------------- squint
+
+def _brute_sums(img, dx, dy, p, f):
+    bsz, c, h, w = img.shape
+    out = np.zeros((bsz, c, h // f, w // f), dtype=np.int64)
+    for b in range(bsz):
+        for ch in range(c):
+            for i in range(h // f):
+                for j in range(w // f):
+                    s = 0
+                    for uu in range(f):
+                        for vv in range(f):
+                            y = min(max(i * f + uu + dy[b] - p, 0), h - 1)
+                            x = min(max(j * f + vv + dx[b] - p, 0), w - 1)
+                            s += int(img[b, ch, y, x])
+                    out[b, ch, i, j] = s
+    return out
+
+
+def test_shift_squint_brute_force():
+    rng = np.random.default_rng(2)
+    img = rng.integers(0, 256, size=(3, 2, 12, 8), dtype=np.uint8)
+    dx = np.array([0, 3, 6])
+    dy = np.array([6, 0, 2])
+    got = o.shift_squint_sums(img, dx, dy, 3, 4)
+    assert np.array_equal(got, _brute_sums(img, dx, dy, 3, 4))
+
+
+def test_squint_constant_image_is_constant():
+    img = np.full((2, 3, 16, 16), 77, dtype=np.uint8)
+    s = o.shift_squint_sums(img, np.array([0, 8]), np.array([5, 1]), 4, 4)
+    assert np.all(s == 77 * 16)
+    assert np.allclose(o.squint_values(s, 4), 77 / 255 - 0.5, rtol=0, atol=1e-15)
+
+
+def test_centre_shift_and_unit_factor_is_identity():
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 256, size=(2, 3, 10, 10), dtype=np.uint8)
+    s = o.shift_squint_sums(img, np.array([4, 4]), np.array([4, 4]), 4, 1)
+    assert np.array_equal(s, img.astype(np.int64))
+
+
+def test_squint_equals_area_pooling():
+    """Unshifted squint equals average pooling / area interpolation (library special case)."""
+    rng = np.random.default_rng(4)
+    img = rng.integers(0, 256, size=(2, 3, 32, 32), dtype=np.uint8)
+    s = o.shift_squint_sums(img, np.array([2, 2]), np.array([2, 2]), 2, 4)
+    t = torch.from_numpy(img.astype(np.float64))
+    pool = torch.nn.functional.avg_pool2d(t, 4).numpy()
+    area = torch.nn.functional.interpolate(t, size=(8, 8), mode="area").numpy()
+    assert np.allclose(s / 16.0, pool, atol=1e-12)
+    assert np.allclose(s / 16.0, area, atol=1e-12)
+
+
+def test_shift_is_a_translation():
+    """Interior pixels move by (dx-p, dy-p): a shift of +1 reads the neighbouring column."""
+    rng = np.random.default_rng(5)
+    img = rng.integers(0, 256, size=(1, 1, 16, 16), dtype=np.uint8)
+    a = o.shift_squint_sums(img, np.array([3]), np.array([2]), 2, 1)
+    assert np.array_equal(a[0, 0, 2:12, 2:12], img[0, 0, 2:12, 3:13].astype(np.int64))
+
+
+# ---------------------------------------------------------------- layers
+
+def test_conv_matches_library_conv():
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=(2, 3, 11, 9))
+    w = rng.normal(size=(4, 3, 3, 3))
+    b = rng.normal(size=4)
+    for s in (1, 2):
+        ref = torch.nn.functional.conv2d(torch.from_numpy(x), torch.from_numpy(w), torch.from_numpy(b), stride=s)
+        assert np.allclose(o.conv3x3_fwd(x, w, b, s), ref.numpy(), atol=1e-12)
+
+
+def test_conv_brute_force():
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(1, 2, 7, 6))
+    w = rng.normal(size=(3, 2, 3, 3))
+    b = rng.normal(size=3)
+    y = o.conv3x3_fwd(x, w, b, 2)
+    for oc in range(3):
+        for i in range(y.shape[2]):
+            for j in range(y.shape[3]):
+                ref = b[oc] + sum(w[oc, c, ky, kx] * x[0, c, 2 * i + ky, 2 * j + kx]
+                                  for c in range(2) for ky in range(3) for kx in range(3))
+                assert abs(y[0, oc, i, j] - ref) < 1e-12
+
+
+def _fd(f, x, h=1e-6):
+    g = np.zeros_like(x)
+    it = np.nditer(x, flags=["multi_index"])
+    for _ in it:
+        i = it.multi_index
+        old = x[i]
+        x[i] = old + h
+        fp = f()
+        x[i] = old - h
+        fm = f()
+        x[i] = old
+        g[i] = (fp - fm) / (2 * h)
+    return g
+
+
+def test_conv_backward_finite_differences():
+    rng = np.random.default_rng(8)
+    x = rng.normal(size=(2, 2, 7, 7))
+    w = rng.normal(size=(3, 2, 3, 3))
+    b = rng.normal(size=3)
+    for s in (1, 2):
+        proj = rng.normal(size=o.conv3x3_fwd(x, w, b, s).shape)
+        f = lambda: float((o.conv3x3_fwd(x, w, b, s) * proj).sum())
+        dx, dw, db = o.conv3x3_bwd(x, w, proj, s)
+        assert np.allclose(dx, _fd(f, x), atol=1e-7)
+        assert np.allclose(dw, _fd(f, w), atol=1e-7)
+        assert np.allclose(db, _fd(f, b), atol=1e-7)
+
+
+def test_layernorm_statistics_and_backward():
+    rng = np.random.default_rng(9)
+    x = rng.normal(size=(5, 16)) * 3 + 1
+    y, cache = o.layernorm_fwd(x, np.ones(16), np.zeros(16), 1e-5)
+    var = x.var(-1)
+    assert np.allclose(y.mean(-1), 0, atol=1e-12)
+    assert np.allclose(y.var(-1), var / (var + 1e-5), atol=1e-12)
+    g = rng.normal(size=16)
+    bb = rng.normal(size=16)
+    proj = rng.normal(size=(5, 16))
+    f = lambda: float((o.layernorm_fwd(x, g, bb, 1e-5)[0] * proj).sum())
+    _, c2 = o.layernorm_fwd(x, g, bb, 1e-5)
+    dx, dg, db = o.layernorm_bwd(proj, g, c2)
+    assert np.allclose(dx, _fd(f, x), atol=1e-7)
+    assert np.allclose(dg, _fd(f, g), atol=1e-7)
+    assert np.allclose(db, _fd(f, bb), atol=1e-7)
+
+
+def test_cross_entropy_gradient_closed_form():
+    """d/dlogits of -sum m log softmax = softmax - m when sum m = 1; and CE >= H(m)."""
+    rng = np.random.default_rng(10)
+    logits = rng.normal(size=(4, 7))
+    m = rng.random((4, 7))
+    m /= m.sum(1, keepdims=True)
+    f = lambda: float(-(m * o.log_softmax(logits)).sum())
+    assert np.allclose(o.softmax(logits) - m, _fd(f, logits), atol=1e-8)
+    ce = -(m * o.log_softmax(logits)).sum(1)
+    ent = -(m * np.log(m)).sum(1)
+    assert np.all(ce >= ent - 1e-12)
+
+
+# ---------------------------------------------------------------- tanh-Gaussian
+
+def _cfg_tiny(**kw):
+    return synth.make_config("tiny_b8", **kw)
+
+
+def test_tanh_gaussian_log_prob_change_of_variables():
+    """log pi(a) = log N(u; mu, sigma) - sum log(1 - tanh(u)^2), evaluated directly."""
+    from scipy.stats import norm
+    cfg = _cfg_tiny()
+    rng = np.random.default_rng(11)
+    out = rng.normal(size=(16, 12))
+    eps = rng.normal(size=(16, 6))
+    a, logp, _ = o.tanh_gaussian(out, eps, cfg)
+    mu = out[:, :6]
+    log_std = -5 + 3.5 * (np.tanh(out[:, 6:]) + 1)
+    u = mu + np.exp(log_std) * eps
+    ref = (norm.logpdf(u, loc=mu, scale=np.exp(log_std)) - np.log(1 - np.tanh(u) ** 2)).sum(1)
+    assert np.allclose(logp, ref, atol=1e-10)
+    assert np.allclose(a, np.tanh(u))
+
+
+def test_tanh_gaussian_density_integrates_to_one():
+    """For one action dimension the squashed density integrates to 1 over (-1, 1)."""
+    from scipy.integrate import quad
+    cfg = _cfg_tiny(action_dim=1)
+    for mu, raw in ((0.3, -0.2), (-1.1, 0.4), (0.0, -1.5)):
+        log_std = -5 + 3.5 * (math.tanh(raw) + 1)
+        sd = math.exp(log_std)
+
+        def dens(a):
+            u = math.atanh(a)
+            eps = (u - mu) / sd
+            _, lp, _ = o.tanh_gaussian(np.array([[mu, raw]]), np.array([[eps]]), cfg)
+            return math.exp(lp[0])
+
+        tot, _ = quad(dens, -1 + 1e-12, 1 - 1e-12, limit=400, points=[math.tanh(mu)])
+        assert abs(tot - 1) < 1e-6
+
+
+def test_tanh_gaussian_backward_finite_differences():
+    cfg = _cfg_tiny()
+    rng = np.random.default_rng(12)
+    out = rng.normal(size=(5, 12))
+    eps = rng.normal(size=(5, 6))
+    wa = rng.normal(size=(5, 6))
+    wl = rng.normal(size=5)
+    f = lambda: float((o.tanh_gaussian(out, eps, cfg)[0] * wa).sum() + (o.tanh_gaussian(out, eps, cfg)[1] * wl).sum())
+    _, _, cache = o.tanh_gaussian(out, eps, cfg)
+    assert np.allclose(o.tanh_gaussian_bwd(wa, wl, cache, cfg), _fd(f, out), atol=1e-7)
+
+
+# ---------------------------------------------------------------- C51 projection
+
+def _hat_projection(pbar, r, d, logp, alpha, cfg):
+    """Brute force: m_j = sum_i P_i max(0, 1 - |b_i - j|) (linear interpolation onto atoms)."""
+    K = cfg["atoms"]
+    dz = (cfg["v_max"] - cfg["v_min"]) / (K - 1)
+    m = np.zeros_like(pbar)
+    for row in range(pbar.shape[0]):
+        for i in range(K):
+            zi = cfg["v_min"] + i * dz
+            tz = min(max(r[row] + cfg["gamma"] * (1 - d[row]) * (zi - alpha * logp[row]), cfg["v_min"]), cfg["v_max"])
+            b = (tz - cfg["v_min"]) / dz
+            for j in range(K):
+                m[row, j] += pbar[row, i] * max(0.0, 1.0 - abs(b - j))
+    return m
+
+
+def _rand_dist(rng, rows, K):
+    p = rng.random((rows, K))
+    return p / p.sum(1, keepdims=True)
+
+
+@pytest.mark.parametrize("name", ["tiny_b8", "small_b32"])
+def test_projection_matches_hat_kernel_and_keeps_mass(name):
+    cfg = synth.make_config(name)
+    rng = np.random.default_rng(13)
+    rows = 12
+    pbar = _rand_dist(rng, rows, cfg["atoms"])
+    r = rng.normal(size=rows) * 3
+    d = (rng.random(rows) < 0.3).astype(float)
+    logp = rng.normal(size=rows) * 4
+    m = o.project_c51(pbar, r, d, logp, 0.2, cfg)
+    assert np.allclose(m, _hat_projection(pbar, r, d, logp, 0.2, cfg), atol=1e-12)
+    assert np.allclose(m.sum(1), 1.0, atol=1e-12)
+    assert np.all(m >= 0)
+
+
+def test_projection_on_atom_is_one_hot():
+    """Terminal transitions whose reward sits on an atom project to a one-hot on that atom."""
+    cfg = _cfg_tiny()                      # 11 atoms on [-10, 10]: spacing exactly 2
+    rng = np.random.default_rng(14)
+    atoms = o.support(cfg)
+    for j in (0, 3, 5, 10):
+        pbar = _rand_dist(rng, 1, 11)
+        m = o.project_c51(pbar, np.array([atoms[j]]), np.array([1.0]), np.array([0.7]), 0.3, cfg)
+        ref = np.zeros(11)
+        ref[j] = 1
+        assert np.allclose(m[0], ref, atol=1e-15)
+    big = synth.make_config("train_b512")
+    for rv in (big["v_min"], 0.0, big["v_max"]):
+        m = o.project_c51(_rand_dist(rng, 1, 101), np.array([rv]), np.array([1.0]), np.array([0.0]), 0.1, big)
+        assert m[0].max() == pytest.approx(1.0, abs=1e-12)
+
+
+def test_projection_preserves_clipped_mean():
+    """sum_j m_j z_j = sum_i P_i clip(Tz_i) (linear splitting preserves the mean)."""
+    cfg = synth.make_config("small_b32")
+    rng = np.random.default_rng(15)
+    pbar = _rand_dist(rng, 20, 51)
+    r = rng.normal(size=20) * 4
+    d = (rng.random(20) < 0.2).astype(float)
+    logp = rng.normal(size=20)
+    m = o.project_c51(pbar, r, d, logp, 0.5, cfg)
+    z = o.support(cfg)
+    tz = np.clip(r[:, None] + 0.99 * (1 - d[:, None]) * (z[None] - 0.5 * logp[:, None]), -10, 10)
+    assert np.allclose((m * z).sum(1), (pbar * tz).sum(1), atol=1e-12)
+
+
+def test_projection_is_linear_in_the_distribution():
+    """Averaging two target critics then projecting = projecting each then averaging."""
+    cfg = synth.make_config("small_b32")
+    rng = np.random.default_rng(16)
+    p1, p2 = _rand_dist(rng, 6, 51), _rand_dist(rng, 6, 51)
+    r, d, lp = rng.normal(size=6), np.zeros(6), rng.normal(size=6)
+    avg = o.project_c51(0.5 * (p1 + p2), r, d, lp, 0.1, cfg)
+    sep = 0.5 * (o.project_c51(p1, r, d, lp, 0.1, cfg) + o.project_c51(p2, r, d, lp, 0.1, cfg))
+    assert np.allclose(avg, sep, atol=1e-14)
+
+
+def test_projection_gamma_zero_is_reward_alone():
+    cfg = _cfg_tiny(gamma=0.0)
+    rng = np.random.default_rng(17)
+    pbar = _rand_dist(rng, 3, 11)
+    m = o.project_c51(pbar, np.array([1.0, -3.0, 20.0]), np.zeros(3), np.ones(3), 0.5, cfg)
+    assert np.allclose(m[0, 5], 0.5) and np.allclose(m[0, 6], 0.5)      # 1.0 halfway between 0 and 2
+    assert np.allclose(m[1, 3], 0.5) and np.allclose(m[1, 4], 0.5)      # -3 between -4 and -2
+    assert np.allclose(m[2, 10], 1.0)                                  # clipped to v_max
+
+
+# ---------------------------------------------------------------- optimiser, polyak, init
+
+def test_adam_first_step_closed_form():
+    cfg = _cfg_tiny()
+    g = np.array([1e-3, -2.0, 0.0, 5e-9])
+    st = dict(params={"w": np.zeros(4)}, m={"w": np.zeros(4)}, v={"w": np.zeros(4)}, steps=dict(critic=0))
+    o.adam_step(st, ["w"], {"w": g}, "critic", cfg)
+    assert np.allclose(st["params"]["w"], -cfg["lr"] * g / (np.abs(g) + cfg["adam_eps"]), rtol=1e-12, atol=0)
+
+
+def test_adam_constant_gradient_steps():
+    """With a constant gradient every bias-corrected step is -lr g/(|g|+eps)."""
+    cfg = _cfg_tiny()
+    g = np.array([0.3, -0.7])
+    st = dict(params={"w": np.zeros(2)}, m={"w": np.zeros(2)}, v={"w": np.zeros(2)}, steps=dict(critic=0))
+    for _ in range(5):
+        o.adam_step(st, ["w"], {"w": g}, "critic", cfg)
+    assert np.allclose(st["params"]["w"], -5 * cfg["lr"] * g / (np.abs(g) + cfg["adam_eps"]), rtol=1e-10)
+
+
+def test_polyak_closed_form():
+    cfg = _cfg_tiny(tau=0.1)
+    st = dict(params={"critic.w": np.array([2.0])}, target={"critic.w": np.array([-1.0])})
+    for _ in range(7):
+        o.polyak(st, cfg)
+    rho = 0.9
+    assert st["target"]["critic.w"][0] == pytest.approx(rho ** 7 * -1 + (1 - rho ** 7) * 2.0, abs=1e-14)
+
+
+def test_init_bounds_and_layout():
+    cfg = synth.make_config("small_b32")
+    p = o.init_params(cfg)
+    spec = o.param_spec(cfg)
+    assert list(p) == [s[0] for s in spec]
+    for name, shape, kind, fan in spec:
+        v = p[name]
+        assert v.shape == tuple(shape)
+        assert np.array_equal(v, v.astype(np.float32).astype(np.float64))
+        if kind == "U":
+            bound = 1 / math.sqrt(fan)
+            assert np.abs(v).max() <= bound
+            if v.size > 2000:
+                assert abs(v.var() - bound ** 2 / 3) < 0.1 * bound ** 2 / 3
+    assert np.all(p["critic0.ln0.g"] == 1) and np.all(p["critic0.ln0.b"] == 0)
+    assert p["log_alpha"][0] == pytest.approx(math.log(0.1), abs=1e-7)
+    dm = o.dims(cfg)
+    assert dm["feat"] == 16 * 5 * 5 and dm["critic_in"] == 418 and dm["actor_in"] == 412
+    big = o.dims(synth.make_config("train_b512"))
+    assert big["feat"] == 2592 and big["critic_in"] == 274 and big["actor_in"] == 268
+
+
+# ---------------------------------------------------------------- whole-loss finite differences
+
+def _tiny_setup(seed=0):
+    cfg = _cfg_tiny()
+    ring = synth.ring_numpy(synth.make_ring(cfg, seed))
+    st = o.init_state(cfg)
+    fe = o.frontend(cfg, ring, 0)
+    return cfg, st, fe
+
+
+def _check_tensor_fd(f, x, an, n_coords=6, h=1e-6, rng=None):
+    """Central differences on a random subset of coordinates of x vs analytic `an`."""
+    rng = rng or np.random.default_rng(0)
+    flat = x.reshape(-1)
+    anf = an.reshape(-1)
+    picks = rng.choice(flat.size, size=min(n_coords, flat.size), replace=False)
+    scale = max(np.abs(anf).max(), 1e-8)
+    bad = []
+    for i in picks:
+        old = flat[i]
+        flat[i] = old + h
+        fp = f()
+        flat[i] = old - h
+        fm = f()
+        flat[i] = old
+        fd = (fp - fm) / (2 * h)
+        if abs(fd - anf[i]) > 1e-6 * scale + 1e-9:
+            bad.append((int(i), fd, anf[i]))
+    return bad
+
+
+def test_critic_loss_gradients_finite_differences():
+    """Every gradient of the critic cross-entropy (critics, encoder) matches central differences."""
+    cfg, st, fe = _tiny_setup()
+    P = st["params"]
+    z1, _ = o.encoder_fwd(P, fe["x_t1"], cfg)
+    eps = px.normal_pairs(cfg["seed"], px.STREAM_EPS_TARGET, 0, cfg["batch"], 6)
+    m = o.target_distribution(P, st["target"], z1, fe, 0.1, eps, cfg)["m"]      # stop-grad target
+    res = o.critic_loss(P, fe["x_t"], fe, m, cfg)
+    f = lambda: o.critic_loss(P, fe["x_t"], fe, m, cfg, with_grads=False)["loss"]
+    rng = np.random.default_rng(1)
+    for name, g in res["grads"].items():
+        assert o.group_of(name) == "critic"
+        assert not _check_tensor_fd(f, P[name], g, rng=rng), name
+    assert set(res["grads"]) == {n for n, *_ in o.param_spec(cfg) if o.group_of(n) == "critic"}
+
+
+def test_actor_loss_gradients_finite_differences():
+    """Every gradient of the actor loss (through the frozen critics and log pi) matches central differences."""
+    cfg, st, fe = _tiny_setup(1)
+    P = st["params"]
+    z, _ = o.encoder_fwd(P, fe["x_t"], cfg)
+    eps = px.normal_pairs(cfg["seed"], px.STREAM_EPS_ACTOR, 0, cfg["batch"], 6)
+    res = o.actor_loss(P, z, fe["p_t"], eps, 0.37, cfg)
+    f = lambda: o.actor_loss(P, z, fe["p_t"], eps, 0.37, cfg, with_grads=False)["loss"]
+    rng = np.random.default_rng(2)
+    for name, g in res["grads"].items():
+        assert o.group_of(name) == "actor"
+        assert not _check_tensor_fd(f, P[name], g, rng=rng), name
+    assert set(res["grads"]) == {n for n, *_ in o.param_spec(cfg) if o.group_of(n) == "actor"}
+
+
+def test_projection_heads_finite_differences():
+    """With a projection layer (train-shape heads on a tiny body), projection grads match FD."""
+    cfg = synth.make_config("tiny_b8", proj_dim=16)
+    ring = synth.ring_numpy(synth.make_ring(cfg, 3))
+    st = o.init_state(cfg)
+    fe = o.frontend(cfg, ring, 0)
+    P = st["params"]
+    z1, _ = o.encoder_fwd(P, fe["x_t1"], cfg)
+    eps = px.normal_pairs(0, px.STREAM_EPS_TARGET, 0, 8, 6)
+    m = o.target_distribution(P, st["target"], z1, fe, 0.1, eps, cfg)["m"]
+    res = o.critic_loss(P, fe["x_t"], fe, m, cfg)
+    f = lambda: o.critic_loss(P, fe["x_t"], fe, m, cfg, with_grads=False)["loss"]
+    rng = np.random.default_rng(3)
+    for name in ("critic.proj.w", "critic.proj.b", "critic.proj.ln.g", "critic.proj.ln.b", "enc.conv0.w"):
+        assert not _check_tensor_fd(f, P[name], res["grads"][name], rng=rng), name
+    z, _ = o.encoder_fwd(P, fe["x_t"], cfg)
+    ra = o.actor_loss(P, z, fe["p_t"], eps, 0.2, cfg)
+    fa = lambda: o.actor_loss(P, z, fe["p_t"], eps, 0.2, cfg, with_grads=False)["loss"]
+    for name in ("actor.proj.w", "actor.proj.ln.g", "actor.fc0.w"):
+        assert not _check_tensor_fd(fa, P[name], ra["grads"][name], rng=rng), name
+
+
+def test_alpha_gradient_finite_difference():
+    cfg = _cfg_tiny()
+    logp = np.array([-3.0, 1.0, 0.5])
+    la = math.log(0.2)
+    _, g = o.alpha_loss(la, logp, cfg)
+    h = 1e-6
+    fd = (o.alpha_loss(la + h, logp, cfg)[0] - o.alpha_loss(la - h, logp, cfg)[0]) / (2 * h)
+    assert g == pytest.approx(fd, rel=1e-8)
+    # entropy below target (log pi large) -> alpha must grow: gradient negative
+    _, g_low = o.alpha_loss(la, np.array([10.0, 10.0]), cfg)
+    assert g_low < 0
+
+
+# ---------------------------------------------------------------- whole update structure
+
+def test_update_zero_lr_keeps_parameters_and_moves_targets_only_by_polyak():
+    cfg = _cfg_tiny(lr=0.0)
+    ring = synth.ring_numpy(synth.make_ring(cfg, 0))
+    st = o.init_state(cfg)
+    p0 = {k: v.copy() for k, v in st["params"].items()}
+    o.update(st, ring, cfg)
+    for k in p0:
+        assert np.array_equal(st["params"][k], p0[k])
+    for k in st["target"]:
+        assert np.allclose(st["target"][k], p0[k], atol=1e-15)
+
+
+def test_update_targets_follow_polyak_of_updated_critics():
+    cfg = _cfg_tiny()
+    ring = synth.ring_numpy(synth.make_ring(cfg, 0))
+    st = o.init_state(cfg)
+    t0 = {k: v.copy() for k, v in st["target"].items()}
+    o.update(st, ring, cfg)
+    for k in t0:
+        assert np.allclose(st["target"][k], 0.995 * t0[k] + 0.005 * st["params"][k], atol=1e-15)
+    assert st["steps"] == dict(critic=1, actor=1, alpha=1) and st["update_idx"] == 1
+
+
+def test_policy_freq_delays_actor():
+    cfg = _cfg_tiny(policy_freq=2)
+    ring = synth.ring_numpy(synth.make_ring(cfg, 0))
+    st = o.init_state(cfg)
+    a0 = st["params"]["actor.fc0.w"].copy()
+    s1, _ = o.update(st, ring, cfg)
+    assert np.array_equal(st["params"]["actor.fc0.w"], a0) and math.isnan(s1["actor_loss"])
+    s2, _ = o.update(st, ring, cfg)
+    assert not np.array_equal(st["params"]["actor.fc0.w"], a0) and not math.isnan(s2["actor_loss"])
+    assert st["steps"] == dict(critic=2, actor=1, alpha=2)
+
+
+def test_act_is_row_independent_and_mean_mode_is_tanh_mu():
+    cfg = _cfg_tiny()
+    P = o.init_params(cfg)
+    obs, prop = synth.make_obs_batch(5, cfg, 9)
+    obs, prop = obs.numpy(), prop.numpy()
+    full = o.act(P, obs, prop, 1234, True, cfg)
+    part = o.act(P, obs[:3], prop[:3], 1234, True, cfg)
+    assert np.allclose(full[:3], part, atol=1e-14)
+    mean = o.act(P, obs, prop, 1234, False, cfg)
+    assert np.all(np.abs(mean) < 1) and not np.allclose(mean, full)
