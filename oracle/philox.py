@@ -69,8 +69,12 @@ def mulhi_range(w, n):
 
 
 def uniform01(w):
-    """Open-interval uniform from the top 24 bits of a word: ((w >> 8) + 0.5) / 2**24."""
-    return ((np.asarray(w, dtype=np.uint64) >> np.uint64(8)).astype(np.float64) + 0.5) * 2.0 ** -24
+    """Open-interval uniform from the top 23 bits of a word: ((w >> 9) + 0.5) / 2**23.
+
+    23 bits keep (w >> 9) + 0.5 exact in FP32 as well as FP64, so both precisions
+    see the same uniform value.
+    """
+    return ((np.asarray(w, dtype=np.uint64) >> np.uint64(9)).astype(np.float64) + 0.5) * 2.0 ** -23
 
 
 def normal_pairs(seed, stream, word, rows, dim):
