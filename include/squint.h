@@ -1,0 +1,235 @@
+/*
+ * squint.h - C ABI of the Squint visual-SAC learner on one GB300 (sm_103a).
+ *
+ * The library runs the batched Soft Actor-Critic update of Squint
+ * (Almuzairee & Christensen, "Squint: Fast Visual Reinforcement Learning for
+ * Sim-to-Real Robotics", Algorithm 1) as hand-written CUDA kernels, k updates
+ * per call captured in one CUDA graph, and batched actor inference for parallel
+ * environments beside it.
+ *
+ * Conventions for every entry point:
+ *   - Return value: SQUINT_OK (0) or a negative SQUINT_E* code; squint_strerror
+ *     gives its text, squint_last_error a message for the calling thread.
+ *     No C++ exception or abort crosses this boundary.
+ *   - Pointers documented as "device" are CUDA global-memory addresses on the
+ *     device that was current when the handle was created; "host" pointers are
+ *     ordinary CPU memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   - Ownership: caller-owned buffers stay caller-owned and must stay valid
+ *     until the work that reads them has completed on the given stream.
+ *     Everything the library allocates is released by squint_destroy.
+ *   - A CUDA failure inside a call returns SQUINT_ECUDA and marks the handle
+ *     failed (sticky): later calls on it return SQUINT_ESTATE.
+ */
+#ifndef SQUINT_H
+#define SQUINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SQUINT_OK 0
+#define SQUINT_EINVAL (-1)   /* bad argument or configuration */
+#define SQUINT_ENOMEM (-2)   /* device allocation failed or memory budget exceeded */
+#define SQUINT_ECUDA (-3)    /* a CUDA call failed (handle becomes failed) */
+#define SQUINT_ETIMEOUT (-4) /* a bounded wait ran out */
+#define SQUINT_EAGAIN (-5)   /* not ready yet / no capacity right now */
+#define SQUINT_ESTATE (-6)   /* call not valid in the handle's current state */
+
+#define SQUINT_MAX_CONV 8
+#define SQUINT_MAX_HIDDEN 4
+
+/* Arithmetic of the update's contractions (convs and linear layers).
+ * Softmax, the atom projection, LayerNorm statistics, Adam and polyak are FP32
+ * in every mode. */
+#define SQUINT_PREC_FP32 0   /* plain FP32 CUDA-core kernels */
+#define SQUINT_PREC_BF16 1   /* BF16 operands, FP32 accumulation (tensor cores) */
+
+/*
+ * Learner configuration (plain data, copied at creation).
+ * Sizes follow the paper: squint = area downsampling of the rendered frame by
+ * an integer factor (Sec. IV "Resolution Squinting"); a conv encoder shared by
+ * actor and critic with per-head one-layer projections (Sec. IV "Encoder Design
+ * Choices"); LayerNorm after every hidden linear layer (Sec. IV "Normalization");
+ * a C51 critic on `atoms` atoms in [v_min, v_max] (Sec. IV "Critic Design
+ * Choices"); two critics averaged in the target (Alg. 1); UTD updates per call.
+ */
+typedef struct {
+    int32_t obs_c, obs_h, obs_w;     /* rendered frame, uint8 NCHW in the ring */
+    int32_t squint_f;                /* area-downsampling factor (obs_h % squint_f == 0) */
+    int32_t shift_pad;               /* random-shift pad p: crops at offsets in [0, 2p] */
+    int32_t proprio_dim, action_dim;
+    int32_t conv_layers, conv_ch;    /* valid 3x3 convs, ReLU after each */
+    int32_t conv_stride[SQUINT_MAX_CONV];
+    int32_t proj_dim;                /* 0: flatten straight into the heads */
+    int32_t n_hidden;                /* hidden layers per MLP */
+    int32_t hidden[SQUINT_MAX_HIDDEN];
+    int32_t n_critics;               /* must be 2 */
+    int32_t atoms;
+    int32_t batch;
+    int32_t policy_freq;             /* actor step when (update_idx + 1) % policy_freq == 0 */
+    int32_t precision;               /* SQUINT_PREC_* */
+    int32_t max_k;                   /* largest k accepted by squint_update */
+    double v_min, v_max, gamma, lr, tau, init_alpha;
+    double target_entropy;           /* NaN: -action_dim */
+    double ln_eps, log_std_min, log_std_max, adam_b1, adam_b2, adam_eps;
+    uint64_t seed;                   /* Philox4x32-10 key for init and every draw */
+} squint_config;
+
+/* Replay ring (caller-owned device memory; the library only reads it).
+ * Slot i holds the transition (o_i, s_i, a_i, r_i, d_i); its next observation is
+ * slot (i + 1) mod n (Alg. 1 stores (o_t, s_t, a_t, r_t, o_{t+1}, s_{t+1})). */
+typedef struct {
+    const uint8_t* obs;      /* device [n, obs_c, obs_h, obs_w] uint8 */
+    const float* proprio;    /* device [n, proprio_dim] */
+    const float* action;     /* device [n, action_dim] in [-1, 1] */
+    const float* reward;     /* device [n] */
+    const uint8_t* done;     /* device [n], 0 or 1 */
+    int64_t n;               /* slots, >= 2 */
+} squint_replay;
+
+/* Per-update diagnostics (one entry per update of a call). */
+typedef struct {
+    float critic_loss;   /* sum over critics of the batch-mean cross entropy */
+    float actor_loss;    /* mean(alpha log pi - mean_i Q_i); NaN when the actor did not step */
+    float alpha_loss;    /* -alpha * mean(log pi + target_entropy) */
+    float alpha;         /* temperature after the step */
+    float q_mean;        /* mean over critics and batch of the online Q(s_t, a_t) */
+    float entropy;       /* -mean log pi at s_t */
+    int64_t update_idx;  /* index of this update (0-based, since creation) */
+} squint_update_stats;
+
+typedef struct squint_handle squint_handle;
+
+/* ------------------------------------------------------------------ lifecycle */
+
+/* Fill `cfg` with a named preset: "small_b32", "train_b512", "tiny_b8". */
+int squint_config_preset(const char* name, squint_config* cfg);
+
+/* Number of FP32 values in the canonical flat parameter layout of `cfg`:
+ * encoder convs (w [co,ci,3,3], b), critic projection (w [d,f], b, ln g, ln b),
+ * each critic's MLP (fc w [out,in], b, ln g, ln b per hidden layer; output fc),
+ * actor projection, actor MLP (output 2*action_dim: mean, raw log-std), log_alpha.
+ * Returns -1 for an invalid configuration. */
+int64_t squint_param_count(const squint_config* cfg);
+
+/* Create a learner on the current CUDA device.  Parameters are initialised from
+ * cfg->seed (uniform +-1/sqrt(fan_in), LayerNorm 1/0, log alpha0), targets copy
+ * the critics, Adam moments are zero.  `ring` may be NULL (inference only). */
+int squint_create(const squint_config* cfg, const squint_replay* ring, squint_handle** out);
+
+/* Replace the replay ring (pointers only; contents are read at update time). */
+int squint_set_replay(squint_handle* h, const squint_replay* ring);
+
+/* Release everything the handle owns; waits for its own streams.  NULL is a no-op. */
+int squint_destroy(squint_handle* h);
+
+/* ------------------------------------------------------------------ hot path */
+
+/*
+ * Run k consecutive SAC updates (Alg. 1, inner loop; UTD k) on `stream`.
+ * Each update: draw a minibatch of `batch` slots, random-shift and squint o_t and
+ * o_{t+1}, encode both, build the C51 target from the averaged target critics,
+ * step critics + encoder (Adam), step log alpha, step the actor on stop-gradient
+ * features (every policy_freq updates), polyak-average the target critics.
+ * The first call with a given k captures the k updates as one CUDA graph; later
+ * calls replay it.  1 <= k <= cfg.max_k.
+ * stats: NULL, or host array of k entries; when given the call waits for the
+ * stream and fills it.  Returns SQUINT_ESTATE if no replay ring is set.
+ */
+int squint_update(squint_handle* h, int k, squint_update_stats* stats, void* stream);
+
+/*
+ * Same k updates issued as individual kernel launches (no graph).  Produces the
+ * same result bit for bit; used to check the graph and for profiling.
+ */
+int squint_update_eager(squint_handle* h, int k, squint_update_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------ inference */
+
+/* One actor query: n environments of one group (Alg. 1, "Sample a_t ~ pi"). */
+typedef struct {
+    uint64_t group_id;       /* caller's tag */
+    int32_t n;               /* environments (rows), >= 1 */
+    int32_t mode;            /* 0: sample a = tanh(mu + sigma eps); 1: mean tanh(mu) */
+    uint64_t rng_key;        /* noise of row r = Philox block (r, act stream, rng_key) */
+    const uint8_t* obs;      /* device [n, obs_c, obs_h, obs_w] uint8 render-resolution frames */
+    const float* proprio;    /* device [n, proprio_dim] */
+    float* actions;          /* device [n, action_dim] output in (-1, 1) */
+} squint_act_request;
+
+/*
+ * Actions for n_reqs requests as one ragged batch on `stream` (squint without
+ * shift, encoder, actor projection, actor MLP, tanh-Gaussian head).  Uses the
+ * inference snapshot of the actor (see squint_refresh_policy); a row's result
+ * does not depend on the other rows of the batch.
+ */
+int squint_act(squint_handle* h, const squint_act_request* reqs, int n_reqs, void* stream);
+
+/*
+ * Copy the current encoder + actor weights into the inference snapshot, ordered
+ * after the work already queued on `stream` (typically the update stream).
+ * Inference launched afterwards sees a consistent snapshot; the snapshot version
+ * increments by one per refresh.
+ */
+int squint_refresh_policy(squint_handle* h, void* stream);
+
+/* ------------------------------------------------------------------ serving loop */
+
+/*
+ * Continuous-batching server for actor queries.  A host scheduler thread takes
+ * submitted requests, admits them while the rows in flight stay within
+ * max_rows and their device memory within mem_budget_bytes, packs every admitted
+ * request into the next batch on its own act stream, and reports completion per
+ * request.  Requests that arrive while a batch runs join the next one.
+ */
+int squint_serve_start(squint_handle* h, int max_rows, size_t mem_budget_bytes);
+/* Queue a request (buffers must stay valid until it completes); *ticket receives its id.
+ * SQUINT_EAGAIN if the queue is full, SQUINT_EINVAL if it can never be admitted. */
+int squint_serve_submit(squint_handle* h, const squint_act_request* req, uint64_t* ticket);
+/* Wait up to timeout_us (0 = poll) for a ticket.  SQUINT_OK when done, with the
+ * submit-to-completion latency in *latency_us and the policy snapshot version it
+ * used in *policy_version (either may be NULL); SQUINT_EAGAIN if not yet. */
+int squint_serve_poll(squint_handle* h, uint64_t ticket, int64_t timeout_us, double* latency_us,
+                      int64_t* policy_version);
+/* Stop the scheduler after the queued work completes. */
+int squint_serve_stop(squint_handle* h);
+
+/* ------------------------------------------------------------------ state */
+
+/* Parameters in the canonical flat FP32 layout (host buffers of squint_param_count values). */
+int squint_get_params(squint_handle* h, float* host, int64_t n);
+int squint_set_params(squint_handle* h, const float* host, int64_t n);
+
+/* Full learner state: params, Adam m and v, target critics, step counters,
+ * update index.  Call with host == NULL to query *bytes. */
+int squint_get_state(squint_handle* h, void* host, size_t* bytes);
+int squint_set_state(squint_handle* h, const void* host, size_t bytes);
+
+/* Copy a named internal buffer of the last update to host (tests, debugging):
+ * "idx" int32[B], "nxt" int32[B], "shift_t"/"shift_t1" int32[B,2] (dx, dy),
+ * "sums_t"/"sums_t1" uint16[B,C,Hs,Ws] box sums, "x_t"/"x_t1" f32[B,C,Hs,Ws],
+ * "m" f32[B,K] projected target, "logits" f32[E,B,K], "logits_target" f32[E,B,K],
+ * "logp_next" f32[B], "logp_t" f32[B], "a_next" f32[B,A], "a_pi" f32[B,A],
+ * "grads" f32[param_count] (critic group from the critic step, actor group from
+ * the actor step), "z_t" f32[B,F].  *bytes in: capacity, out: size. */
+int squint_debug_tensor(squint_handle* h, const char* name, void* host, size_t* bytes);
+
+/* ------------------------------------------------------------------ errors */
+
+/* sizeof of an ABI struct by name ("squint_config", "squint_replay",
+ * "squint_update_stats", "squint_act_request"); 0 for an unknown name.
+ * Lets a binding check its struct layouts against the compiled library. */
+size_t squint_struct_size(const char* name);
+
+const char* squint_strerror(int code);
+/* Message of the last failure on the calling thread ("" if none). */
+const char* squint_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SQUINT_H */

@@ -1,0 +1,102 @@
+// Shared device helpers of the Squint CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace sq {
+
+// Philox4x32-10 (Salmon et al., SC'11, Sec. 3.2): ten rounds of two 32x32->64
+// multiplies; the high halves are xored with the other counter words and the
+// round key; the key is bumped by the Weyl constants between rounds.
+__host__ __device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c[1] ^ k0;
+        const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c[3] ^ k1;
+        c[1] = (uint32_t)p1;
+        c[3] = (uint32_t)p0;
+        c[0] = n0;
+        c[2] = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Draw addressing shared by every random quantity of the learner:
+// counter (element, stream | sub << 16, word_lo, word_hi), key (seed_lo, seed_hi).
+__host__ __device__ __forceinline__ void draw_block(uint32_t out[4], uint64_t seed, uint32_t element,
+                                                    uint32_t stream, uint32_t sub, uint64_t word) {
+    out[0] = element;
+    out[1] = (stream & 0xFFFFu) | (sub << 16);
+    out[2] = (uint32_t)word;
+    out[3] = (uint32_t)(word >> 32);
+    philox4x32_10(out, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+enum Stream : uint32_t {
+    kStreamIndex = 1,
+    kStreamShiftT = 2,
+    kStreamShiftT1 = 3,
+    kStreamEpsTarget = 4,
+    kStreamEpsActor = 5,
+    kStreamInit = 16,
+    kStreamAct = 32,
+};
+
+// floor(w * n / 2^32): integer in [0, n).
+__host__ __device__ __forceinline__ uint32_t range_draw(uint32_t w, uint32_t n) {
+    return (uint32_t)(((uint64_t)w * n) >> 32);
+}
+
+// Uniform in (0, 1) from the top 23 bits: exact in FP32.
+__device__ __forceinline__ float uniform01f(uint32_t w) {
+    return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;  // 2^-23
+}
+
+// Standard normal pair by Box-Muller from two words.
+__device__ __forceinline__ void box_muller(uint32_t w0, uint32_t w1, float& z0, float& z1) {
+    const float u1 = uniform01f(w0);
+    const float u2 = uniform01f(w1);
+    const float rad = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    z0 = rad * c;
+    z1 = rad * s;
+}
+
+// Normal noise eps[k] (k < dim) of row `element` of a stream addressed by `word`.
+__device__ __forceinline__ float normal_draw(uint64_t seed, uint32_t element, uint32_t stream, uint64_t word, int k) {
+    uint32_t w[4];
+    draw_block(w, seed, element, stream, (uint32_t)(k >> 1), word);
+    float z0, z1;
+    box_muller(w[0], w[1], z0, z1);
+    return (k & 1) ? z1 : z0;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return *p; }
+
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ double to_f(double x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+}  // namespace sq

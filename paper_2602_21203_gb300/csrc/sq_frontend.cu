@@ -1,0 +1,139 @@
+// Front end of the update (steps a1-a4) and of inference.
+//
+// One CTA per (sample, frame): it draws the slot and the crop offset, stages
+// the uint8 frame in shared memory with 128-bit loads, and forms the squinted
+// image from integer f x f box sums over the replicate-padded, shifted frame
+// (Sec. IV "Resolution Squinting": area downsampling; the shift is the
+// DrQ-style random-shift augmentation).
+#include "sq_kernels.cuh"
+
+namespace sq {
+
+__global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
+    extern __shared__ __align__(16) uint8_t frame[];
+    const int b = blockIdx.x;
+    const int which = blockIdx.y;                 // 0: o_t, 1: o_{t+1}
+    const uint64_t u = (uint64_t)*a.update_idx;
+
+    uint32_t w[4];
+    draw_block(w, a.seed, (uint32_t)b, kStreamIndex, 0, u);
+    const int64_t idx = (int64_t)range_draw(w[0], (uint32_t)a.n_slots);
+    const int64_t nxt = (idx + 1) % a.n_slots;
+    const int64_t slot = which ? nxt : idx;
+    draw_block(w, a.seed, (uint32_t)b, which ? kStreamShiftT1 : kStreamShiftT, 0, u);
+    const int span = 2 * a.pad + 1;
+    const int dx = (int)range_draw(w[0], (uint32_t)span);
+    const int dy = (int)range_draw(w[1], (uint32_t)span);
+
+    const int64_t fbytes = (int64_t)a.C * a.H * a.W;
+    const uint8_t* src = a.obs + slot * fbytes;
+    if ((fbytes & 15) == 0 && (((uintptr_t)src) & 15) == 0) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(frame);
+        for (int64_t i = threadIdx.x; i < fbytes / 16; i += blockDim.x) d4[i] = __ldg(s4 + i);
+    } else {
+        for (int64_t i = threadIdx.x; i < fbytes; i += blockDim.x) frame[i] = src[i];
+    }
+    __syncthreads();
+
+    const int hs = a.H / a.f, ws = a.W / a.f;
+    const int plane = hs * ws;
+    const int n_out = a.C * plane;
+    const float denom = 255.0f * (float)(a.f * a.f);
+    const int64_t row = (int64_t)which * a.B + b;
+    float* xo = a.x + row * n_out;
+    for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
+        const int c = o / plane;
+        const int i = (o - c * plane) / ws;
+        const int j = o - c * plane - i * ws;
+        uint32_t sum = 0;
+        for (int uu = 0; uu < a.f; ++uu) {
+            const int y = min(max(i * a.f + uu + dy - a.pad, 0), a.H - 1);
+            const uint8_t* rp = frame + ((int64_t)c * a.H + y) * a.W;
+            for (int vv = 0; vv < a.f; ++vv) {
+                const int xx = min(max(j * a.f + vv + dx - a.pad, 0), a.W - 1);
+                sum += rp[xx];
+            }
+        }
+        const float val = (float)sum / denom - 0.5f;
+        xo[o] = val;
+        if (a.x_bf) a.x_bf[row * n_out + o] = __float2bfloat16_rn(val);
+        if (a.sums) a.sums[row * n_out + o] = (uint16_t)sum;
+    }
+
+    if (threadIdx.x == 0) {
+        a.idx_out[row] = (int32_t)slot;
+        a.shift_out[2 * row] = dx;
+        a.shift_out[2 * row + 1] = dy;
+        if (which == 0) {
+            a.r_out[b] = a.reward[idx];
+            a.d_out[b] = (float)a.done[idx];
+        }
+        if (b == 0 && which == 0) {
+            const int act = ((u + 1) % (uint64_t)a.policy_freq) == 0;
+            a.steps[0] += 1;
+            a.steps[2] += 1;
+            a.steps[1] += act;
+            *a.do_actor = act;
+        }
+    }
+    for (int t = 0; t < a.n_dst; ++t) {
+        const CopyDst& d = a.dst[t];
+        const bool mine = (d.which == 1) == (which == 1);
+        if (!mine) continue;
+        const int width = d.which == 2 ? a.A : a.P;
+        const float* s = d.which == 2 ? a.action + idx * a.A : a.proprio + slot * a.P;
+        for (int k = threadIdx.x; k < width; k += blockDim.x) d.ptr[(int64_t)b * d.ld + d.col + k] = s[k];
+    }
+}
+
+void launch_frontend(const FrontendArgs& a, cudaStream_t s) {
+    const size_t smem = (size_t)a.C * a.H * a.W;
+    frontend_kernel<<<dim3(a.B, 2), 256, smem, s>>>(a);
+}
+
+// Inference: one CTA per row; no shift (crop at the centre offset p = pad means
+// the identity, so it is left out entirely).
+__global__ void __launch_bounds__(256) act_frontend_kernel(ActFrontArgs a) {
+    extern __shared__ __align__(16) uint8_t frame[];
+    const int r = blockIdx.x;
+    const int q = a.row_req[r];
+    const int64_t fbytes = (int64_t)a.C * a.H * a.W;
+    const uint8_t* src = a.obs[q] + (int64_t)a.row_in_req[r] * fbytes;
+    if ((fbytes & 15) == 0 && (((uintptr_t)src) & 15) == 0) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(frame);
+        for (int64_t i = threadIdx.x; i < fbytes / 16; i += blockDim.x) d4[i] = __ldg(s4 + i);
+    } else {
+        for (int64_t i = threadIdx.x; i < fbytes; i += blockDim.x) frame[i] = src[i];
+    }
+    __syncthreads();
+    const int hs = a.H / a.f, ws = a.W / a.f, plane = hs * ws, n_out = a.C * plane;
+    const float denom = 255.0f * (float)(a.f * a.f);
+    for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
+        const int c = o / plane, i = (o - c * plane) / ws, j = o - c * plane - i * ws;
+        uint32_t sum = 0;
+        for (int uu = 0; uu < a.f; ++uu) {
+            const uint8_t* rp = frame + ((int64_t)c * a.H + i * a.f + uu) * a.W + j * a.f;
+            for (int vv = 0; vv < a.f; ++vv) sum += rp[vv];
+        }
+        a.x[(int64_t)r * n_out + o] = (float)sum / denom - 0.5f;
+    }
+    const float* p = a.prop[q] + (int64_t)a.row_in_req[r] * a.P;
+    for (int k = threadIdx.x; k < a.P; k += blockDim.x) a.xin[(int64_t)r * a.ld_xin + a.col + k] = p[k];
+}
+
+void launch_act_frontend(const ActFrontArgs& a, cudaStream_t s) {
+    if (a.rows <= 0) return;
+    const size_t smem = (size_t)a.C * a.H * a.W;
+    act_frontend_kernel<<<a.rows, 256, smem, s>>>(a);
+}
+
+void frontend_prepare(size_t frame_bytes) {
+    if (frame_bytes > 48 * 1024) {
+        cudaFuncSetAttribute(frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
+        cudaFuncSetAttribute(act_frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
+    }
+}
+
+}  // namespace sq

@@ -1,0 +1,433 @@
+// Dense contractions on CUDA cores: grouped GEMM and valid 3x3 convolutions as
+// implicit GEMMs.  These are the plain FP32 path of the update (and, in FP64,
+// the reference-precision kernels the layer-level gradient checks use).
+//
+// Tile: 64 x 64 outputs x 16 reduction steps per stage, 256 threads, 4 x 4
+// outputs per thread, operands staged in shared memory k-major.
+#include "sq_kernels.cuh"
+
+#include <algorithm>
+#include <vector>
+
+namespace sq {
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int kMaxProbs = 8;
+
+struct GemmBatch {
+    GemmProblem p[kMaxProbs];
+    int tile_start[kMaxProbs + 1];
+    int tiles_n[kMaxProbs];
+    int n;
+};
+
+template <typename T, int LAYOUT>
+__global__ void __launch_bounds__(NT) gemm_kernel(GemmBatch gb) {
+    __shared__ T As[BK][BM + 4];
+    __shared__ T Bs[BK][BN + 4];
+    int pi = 0;
+    while (pi + 1 < gb.n && (int)blockIdx.x >= gb.tile_start[pi + 1]) ++pi;
+    const GemmProblem& P = gb.p[pi];
+    const int t = blockIdx.x - gb.tile_start[pi];
+    const int m0 = (t / gb.tiles_n[pi]) * BM;
+    const int n0 = (t % gb.tiles_n[pi]) * BN;
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+
+    constexpr bool A_K = (LAYOUT == kKK || LAYOUT == kKN);
+    constexpr bool B_K = (LAYOUT == kKK);
+    for (int s = 0; s < P.n_sum; ++s) {
+        const T* A = static_cast<const T*>(P.A) + (int64_t)s * P.a_sum;
+        const T* Bm = static_cast<const T*>(P.B) + (int64_t)s * P.b_sum;
+        for (int k0 = 0; k0 < P.K; k0 += BK) {
+            // stage A: 64 x 16, 4 elements per thread
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                int ml, kl;
+                if (A_K) { ml = tid / 4; kl = (tid % 4) * 4 + e; }
+                else     { kl = tid / 16; ml = (tid % 16) * 4 + e; }
+                const int m = m0 + ml, k = k0 + kl;
+                As[kl][ml] = (m < P.M && k < P.K) ? A[(int64_t)m * P.sa_m + (int64_t)k * P.sa_k] : T(0);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                int nl, kl;
+                if (B_K) { nl = tid / 4; kl = (tid % 4) * 4 + e; }
+                else     { kl = tid / 16; nl = (tid % 16) * 4 + e; }
+                const int n = n0 + nl, k = k0 + kl;
+                Bs[kl][nl] = (n < P.N && k < P.K) ? Bm[(int64_t)n * P.sb_n + (int64_t)k * P.sb_k] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                T a[4], bb[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+            }
+            __syncthreads();
+        }
+    }
+    T* C = static_cast<T*>(P.C);
+    const T* bias = static_cast<const T*>(P.bias);
+    const T* mask = static_cast<const T*>(P.mask);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty * 4 + i;
+        if (m >= P.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            if (n >= P.N) continue;
+            T v = acc[i][j];
+            if (bias) v += bias[n];
+            if (mask && !(mask[(int64_t)m * P.sm_m + (int64_t)n * P.sm_n] > T(0))) v = T(0);
+            T* dst = C + (int64_t)m * P.sc_m + (int64_t)n * P.sc_n;
+            *dst = P.accumulate ? *dst + v : v;
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+void launch_gemm(const GemmProblem* probs, int n_probs, GemmLayout layout, cudaStream_t s) {
+    for (int base = 0; base < n_probs; base += kMaxProbs) {
+        GemmBatch gb{};
+        gb.n = std::min(kMaxProbs, n_probs - base);
+        int tiles = 0;
+        for (int i = 0; i < gb.n; ++i) {
+            gb.p[i] = probs[base + i];
+            if (gb.p[i].n_sum < 1) gb.p[i].n_sum = 1;
+            gb.tile_start[i] = tiles;
+            gb.tiles_n[i] = (gb.p[i].N + BN - 1) / BN;
+            tiles += ((gb.p[i].M + BM - 1) / BM) * gb.tiles_n[i];
+        }
+        gb.tile_start[gb.n] = tiles;
+        if (tiles == 0) continue;
+        switch (layout) {
+            case kKK: gemm_kernel<T, kKK><<<tiles, NT, 0, s>>>(gb); break;
+            case kKN: gemm_kernel<T, kKN><<<tiles, NT, 0, s>>>(gb); break;
+            case kMN: gemm_kernel<T, kMN><<<tiles, NT, 0, s>>>(gb); break;
+        }
+    }
+}
+template void launch_gemm<float>(const GemmProblem*, int, GemmLayout, cudaStream_t);
+template void launch_gemm<double>(const GemmProblem*, int, GemmLayout, cudaStream_t);
+
+// ---------------------------------------------------------------- convolutions
+// Implicit GEMM, tile 128 pixels x 32 channels x 16 reduction steps.
+namespace {
+constexpr int CBM = 128, CBN = 32, CBK = 16;
+
+// Forward: M = nimg*OH*OW pixels, N = Cout, K = Cin*9.
+template <typename T>
+__global__ void __launch_bounds__(NT) conv_fwd_kernel(ConvShape sh, const T* __restrict__ x, const T* __restrict__ w,
+                                                      const T* __restrict__ bias, T* __restrict__ y, int relu) {
+    __shared__ T As[CBK][CBM + 4];
+    __shared__ T Bs[CBK][CBN + 4];
+    const int tid = threadIdx.x;
+    const int M = sh.nimg * sh.OH * sh.OW, N = sh.Cout, K = sh.Cin * 9;
+    const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * CBN;
+    // each thread stages pixel ml = tid % 128 at reduction rows tid/128 + 2e
+    const int ml = tid % CBM;
+    const int m = m0 + ml;
+    int64_t xbase = -1;
+    if (m < M) {
+        const int img = m / (sh.OH * sh.OW);
+        const int rem = m - img * sh.OH * sh.OW;
+        const int oy = rem / sh.OW, ox = rem - (rem / sh.OW) * sh.OW;
+        xbase = (int64_t)img * sh.x_img_stride + (int64_t)(oy * sh.stride) * sh.W + ox * sh.stride;
+    }
+    const int ty = tid % 32, tx = tid / 32;   // lanes walk pixels (coalesced stores), warps walk channels
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const int64_t plane = (int64_t)sh.H * sh.W;
+    for (int k0 = 0; k0 < K; k0 += CBK) {
+#pragma unroll
+        for (int e = 0; e < CBK / 2; ++e) {
+            const int kl = tid / CBM + 2 * e;
+            const int k = k0 + kl;
+            T v = T(0);
+            if (xbase >= 0 && k < K) {
+                const int ci = k / 9, r = k - ci * 9, ky = r / 3, kx = r - ky * 3;
+                v = x[xbase + ci * plane + ky * sh.W + kx];
+            }
+            As[kl][ml] = v;
+        }
+        for (int e = tid; e < CBK * CBN; e += NT) {
+            const int nl = e / CBK, kl = e % CBK;
+            const int n = n0 + nl, k = k0 + kl;
+            Bs[kl][nl] = (n < N && k < K) ? w[(int64_t)n * K + k] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < CBK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 32 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 8 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int mm = m0 + ty + 32 * i;
+        if (mm >= M) continue;
+        const int img = mm / (sh.OH * sh.OW);
+        const int rem = mm - img * sh.OH * sh.OW;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 8 * j;
+            if (n >= N) continue;
+            T v = acc[i][j] + bias[n];
+            if (relu && !(v > T(0))) v = T(0);
+            y[(int64_t)img * sh.y_img_stride + (int64_t)n * sh.OH * sh.OW + rem] = v;
+        }
+    }
+}
+
+// Data gradient: M = nimg*H*W input pixels, N = Cin, K = Cout*9.
+template <typename T>
+__global__ void __launch_bounds__(NT) conv_dgrad_kernel(ConvShape sh, const T* __restrict__ dy, const T* __restrict__ w,
+                                                        T* __restrict__ dx, const T* __restrict__ mask) {
+    __shared__ T As[CBK][CBM + 4];
+    __shared__ T Bs[CBK][CBN + 4];
+    const int tid = threadIdx.x;
+    const int M = sh.nimg * sh.H * sh.W, N = sh.Cin, K = sh.Cout * 9;
+    const int m0 = blockIdx.x * CBM, n0 = blockIdx.y * CBN;
+    const int ml = tid % CBM;
+    const int m = m0 + ml;
+    int img = 0, iy = 0, ix = 0;
+    if (m < M) {
+        img = m / (sh.H * sh.W);
+        const int rem = m - img * sh.H * sh.W;
+        iy = rem / sh.W;
+        ix = rem - iy * sh.W;
+    }
+    const int ty = tid % 32, tx = tid / 32;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const int64_t oplane = (int64_t)sh.OH * sh.OW;
+    const T* dyi = dy + (int64_t)img * sh.y_img_stride;
+    for (int k0 = 0; k0 < K; k0 += CBK) {
+#pragma unroll
+        for (int e = 0; e < CBK / 2; ++e) {
+            const int kl = tid / CBM + 2 * e;
+            const int k = k0 + kl;
+            T v = T(0);
+            if (m < M && k < K) {
+                const int co = k / 9, r = k - co * 9, ky = r / 3, kx = r - ky * 3;
+                const int ty_ = iy - ky, tx_ = ix - kx;
+                if (ty_ >= 0 && tx_ >= 0 && ty_ % sh.stride == 0 && tx_ % sh.stride == 0) {
+                    const int oy = ty_ / sh.stride, ox = tx_ / sh.stride;
+                    if (oy < sh.OH && ox < sh.OW) v = dyi[co * oplane + oy * sh.OW + ox];
+                }
+            }
+            As[kl][ml] = v;
+        }
+        for (int e = tid; e < CBK * CBN; e += NT) {
+            const int nl = e % CBN, kl = e / CBN;
+            const int n = n0 + nl, k = k0 + kl;
+            T v = T(0);
+            if (n < N && k < K) {
+                const int co = k / 9, r = k - co * 9;
+                v = w[((int64_t)co * sh.Cin + n) * 9 + r];
+            }
+            Bs[kl][nl] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < CBK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 32 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 8 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int mm = m0 + ty + 32 * i;
+        if (mm >= M) continue;
+        const int im = mm / (sh.H * sh.W);
+        const int rem = mm - im * sh.H * sh.W;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 8 * j;
+            if (n >= N) continue;
+            const int64_t off = (int64_t)im * sh.x_img_stride + (int64_t)n * sh.H * sh.W + rem;
+            T v = acc[i][j];
+            if (mask && !(mask[off] > T(0))) v = T(0);
+            dx[off] = v;
+        }
+    }
+}
+
+// Weight gradient, split over the pixel reduction: rows = Cout, cols = Cin*9 + 1
+// (the last column is the bias gradient), partial sums per split in `work`.
+constexpr int WBM = 32, WBN = 64, WBK = 32;
+template <typename T>
+__global__ void __launch_bounds__(NT) conv_wgrad_kernel(ConvShape sh, const T* __restrict__ dy, const T* __restrict__ x,
+                                                        T* __restrict__ work, int chunk) {
+    __shared__ T As[WBK][WBM + 4];
+    __shared__ T Bs[WBK][WBN + 4];
+    const int tid = threadIdx.x;
+    const int M = sh.Cout, N = sh.Cin * 9 + 1;
+    const int P = sh.nimg * sh.OH * sh.OW;
+    const int n0 = blockIdx.x * WBN, m0 = blockIdx.y * WBM;
+    const int p_begin = blockIdx.z * chunk, p_end = min(P, p_begin + chunk);
+    const int tx = tid % 16, ty = tid / 16;   // 16 x 4 cols, 16 x 2 rows
+    T acc[2][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    const int64_t oplane = (int64_t)sh.OH * sh.OW, iplane = (int64_t)sh.H * sh.W;
+    for (int k0 = p_begin; k0 < p_end; k0 += WBK) {
+        // A: dy[co, pixel]; pixel fastest across threads
+        for (int e = tid; e < WBK * WBM; e += NT) {
+            const int kl = e % WBK, ml = e / WBK;
+            const int p = k0 + kl, co = m0 + ml;
+            T v = T(0);
+            if (p < p_end && co < M) {
+                const int img = p / (int)oplane;
+                const int rem = p - img * (int)oplane;
+                v = dy[(int64_t)img * sh.y_img_stride + co * oplane + rem];
+            }
+            As[kl][ml] = v;
+        }
+        // B: x[ci, oy*s+ky, ox*s+kx] for col j = (ci, ky, kx); pixel fastest
+        for (int e = tid; e < WBK * WBN; e += NT) {
+            const int kl = e % WBK, nl = e / WBK;
+            const int p = k0 + kl, j = n0 + nl;
+            T v = T(0);
+            if (p < p_end && j < N) {
+                if (j == N - 1) {
+                    v = T(1);
+                } else {
+                    const int img = p / (int)oplane;
+                    const int rem = p - img * (int)oplane;
+                    const int oy = rem / sh.OW, ox = rem - oy * sh.OW;
+                    const int ci = j / 9, r = j - ci * 9, ky = r / 3, kx = r - ky * 3;
+                    v = x[(int64_t)img * sh.x_img_stride + ci * iplane + (int64_t)(oy * sh.stride + ky) * sh.W +
+                          ox * sh.stride + kx];
+                }
+            }
+            Bs[kl][nl] = v;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < WBK; ++kk) {
+            T a[2], b[4];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+    }
+    T* out = work + (int64_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int co = m0 + ty + 16 * i;
+        if (co >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int col = n0 + tx + 16 * j;
+            if (col < N) out[(int64_t)co * N + col] = acc[i][j];
+        }
+    }
+}
+
+template <typename T>
+__global__ void wgrad_reduce_kernel(const T* __restrict__ work, int splits, int M, int N, T* __restrict__ dw,
+                                    T* __restrict__ db) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= M * N) return;
+    T s = T(0);
+    for (int z = 0; z < splits; ++z) s += work[(int64_t)z * M * N + e];
+    const int co = e / N, col = e - co * N;
+    if (col == N - 1) db[co] = s;
+    else dw[(int64_t)co * (N - 1) + col] = s;
+}
+
+int wgrad_splits(const ConvShape& sh) {
+    const int P = sh.nimg * sh.OH * sh.OW;
+    const int tiles = ((sh.Cin * 9 + 1 + WBN - 1) / WBN) * ((sh.Cout + WBM - 1) / WBM);
+    int splits = std::max(1, (2 * 152 + tiles - 1) / tiles);
+    splits = std::min(splits, std::max(1, P / (4 * WBK)));
+    return splits;
+}
+}  // namespace
+
+template <typename T>
+void launch_conv_fwd(const ConvShape& sh, const T* x, const T* w, const T* b, T* y, bool relu, cudaStream_t s) {
+    const int M = sh.nimg * sh.OH * sh.OW;
+    if (M == 0) return;
+    dim3 grid((M + CBM - 1) / CBM, (sh.Cout + CBN - 1) / CBN);
+    conv_fwd_kernel<T><<<grid, NT, 0, s>>>(sh, x, w, b, y, relu ? 1 : 0);
+}
+template <typename T>
+void launch_conv_dgrad(const ConvShape& sh, const T* dy, const T* w, T* dx, const T* mask, cudaStream_t s) {
+    const int M = sh.nimg * sh.H * sh.W;
+    if (M == 0) return;
+    dim3 grid((M + CBM - 1) / CBM, (sh.Cin + CBN - 1) / CBN);
+    conv_dgrad_kernel<T><<<grid, NT, 0, s>>>(sh, dy, w, dx, mask);
+}
+int64_t conv_wgrad_workspace(const ConvShape& sh) {
+    return (int64_t)wgrad_splits(sh) * sh.Cout * (sh.Cin * 9 + 1);
+}
+template <typename T>
+void launch_conv_wgrad(const ConvShape& sh, const T* dy, const T* x, T* dw, T* db, T* work, cudaStream_t s) {
+    const int P = sh.nimg * sh.OH * sh.OW;
+    const int splits = wgrad_splits(sh);
+    const int chunk = (P + splits - 1) / splits;
+    const int N = sh.Cin * 9 + 1;
+    dim3 grid((N + WBN - 1) / WBN, (sh.Cout + WBM - 1) / WBM, splits);
+    conv_wgrad_kernel<T><<<grid, NT, 0, s>>>(sh, dy, x, work, chunk);
+    const int tot = sh.Cout * N;
+    wgrad_reduce_kernel<T><<<(tot + 255) / 256, 256, 0, s>>>(work, splits, sh.Cout, N, dw, db);
+}
+
+template void launch_conv_fwd<float>(const ConvShape&, const float*, const float*, const float*, float*, bool, cudaStream_t);
+template void launch_conv_fwd<double>(const ConvShape&, const double*, const double*, const double*, double*, bool, cudaStream_t);
+template void launch_conv_dgrad<float>(const ConvShape&, const float*, const float*, float*, const float*, cudaStream_t);
+template void launch_conv_dgrad<double>(const ConvShape&, const double*, const double*, double*, const double*, cudaStream_t);
+template void launch_conv_wgrad<float>(const ConvShape&, const float*, const float*, float*, float*, float*, cudaStream_t);
+template void launch_conv_wgrad<double>(const ConvShape&, const double*, const double*, double*, double*, double*, cudaStream_t);
+
+}  // namespace sq

@@ -1,0 +1,167 @@
+// Internal definition of the learner handle.
+#pragma once
+
+#include "squint.h"
+#include "sq_kernels.cuh"
+
+#include <atomic>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+namespace sq {
+
+extern thread_local std::string g_last_error;
+void set_error(const char* fmt, const char* a, const char* b, int line);
+
+#define SQ_CK(h, call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess) {                                                                \
+            ::sq::set_error("%s: %s (line %d)", #call, cudaGetErrorString(e_), __LINE__);      \
+            (h)->failed = true;                                                                 \
+            return SQUINT_ECUDA;                                                                \
+        }                                                                                       \
+    } while (0)
+
+struct Lin { int64_t w = -1, b = -1, g = -1, beta = -1; int in = 0, out = 0; bool ln = false; };
+struct ConvL { int cin, cout, h, w, oh, ow, s; int64_t wo, bo; };
+
+// Canonical flat parameter layout (offsets in floats).
+struct Layout {
+    int hs = 0, ws = 0;
+    std::vector<ConvL> conv;
+    int feat = 0, D = 0, zdim = 0, dc = 0, da = 0;
+    Lin cproj, aproj;
+    std::vector<Lin> critic[2];
+    std::vector<Lin> actor;
+    int64_t critic_begin = 0, critic_end = 0, actor_begin = 0, actor_end = 0, log_alpha = 0, total = 0, target_n = 0;
+};
+
+bool build_layout(const squint_config& c, Layout& L);
+void init_params_host(const squint_config& c, const Layout& L, std::vector<float>& p);
+
+// Activations of one MLP evaluated on `rows` rows by E parameter sets.
+struct MlpBufs {
+    int E = 0, rows = 0;
+    std::vector<float*> pre, post, mean, rstd;   // per hidden layer: [E, rows, n]
+    float* out = nullptr;                        // [E, rows, n_out]
+};
+
+struct ServeState;
+
+}  // namespace sq
+
+struct squint_handle {
+    squint_config c{};
+    sq::Layout L;
+    squint_replay ring{};
+    bool has_ring = false;
+    bool failed = false;
+    int device = 0;
+
+    // parameters and optimiser state
+    float* params = nullptr;
+    float* grads = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    float* target = nullptr;
+    float* policy_buf[2] = {nullptr, nullptr};   // inference snapshots (same layout as params)
+    int policy_active = 0;
+    int64_t policy_version = 0;
+    cudaEvent_t policy_ready[2] = {nullptr, nullptr};     // copy into buffer i finished
+    cudaEvent_t policy_released[2] = {nullptr, nullptr};  // inference reading buffer i finished
+    int64_t* d_update_idx = nullptr;
+    int32_t* d_steps = nullptr;       // critic, actor, alpha
+    int32_t* d_do_actor = nullptr;
+    float* d_stats = nullptr;         // [max_k, 8]
+    float* h_stats = nullptr;         // pinned
+
+    // update activations
+    float* x2 = nullptr;              // [2B, C, Hs, Ws]
+    uint16_t* sums = nullptr;         // [2B, C, Hs, Ws]
+    int32_t* idx2 = nullptr;          // [2B]
+    int32_t* shift2 = nullptr;        // [2B, 2]
+    std::vector<float*> conv_out;     // [2B, ch, oh, ow]
+    float* proj_pre = nullptr;        // [5, B, D]: ap(z'), cbar(z'), cp(z), ap(z), cp_new(z)
+    float* proj_mean = nullptr;       // [5, B]
+    float* proj_rstd = nullptr;
+    float* xa = nullptr;              // [2B, Da]
+    float* xcbar = nullptr;           // [B, Dc]
+    float* xc = nullptr;              // [B, Dc]
+    float* xq = nullptr;              // [B, Dc]
+    sq::MlpBufs actor_mlp, tcrit_mlp, crit_mlp, qcrit_mlp;
+    float* logp = nullptr;            // [2B]
+    float* eps = nullptr;             // [2B, A]
+    float* m = nullptr;               // [B, K]
+    float* r = nullptr;
+    float* d = nullptr;
+    float* dlogits = nullptr;         // [E, B, K]
+    float* dlogits_q = nullptr;       // [E, B, K]
+    float* row_loss = nullptr;        // [E B]
+    float* row_q = nullptr;           // [E B]
+    float* row_q_actor = nullptr;     // [E B]
+    std::vector<float*> dpost, dpre;  // per hidden layer [E, B, n] (critic bwd; reused by actor bwd)
+    float* dh = nullptr;              // [B, zdim]
+    float* dproj = nullptr;           // [B, D]
+    float* dz = nullptr;              // [B, F] (masked: gradient at the last conv's pre-activation)
+    float* dconv_a = nullptr;         // ping-pong conv gradients
+    float* dconv_b = nullptr;
+    float* wgrad_work = nullptr;
+    float* da = nullptr;              // [B, A]
+    float* dout_a = nullptr;          // [B, 2A]
+
+    // inference
+    int act_cap = 0;
+    float* ax = nullptr;
+    std::vector<float*> aconv;
+    float* apre = nullptr; float* amean = nullptr; float* arstd = nullptr;
+    float* axin = nullptr;
+    sq::MlpBufs act_mlp;
+    int32_t* d_row_req = nullptr; int32_t* d_row_in = nullptr;
+    void* d_req = nullptr;            // packed per-request arrays
+    void* h_req = nullptr;            // pinned staging
+    size_t req_bytes = 0;
+    int req_cap = 0;
+    cudaStream_t capture_stream = nullptr;
+    cudaEvent_t req_event = nullptr;
+    bool req_event_live = false;
+    std::vector<void*> act_allocs;
+    std::map<int, cudaGraphExec_t> graphs;
+
+    std::vector<void*> allocations;
+    sq::ServeState* serve = nullptr;
+    std::mutex act_mu;
+
+    int allocate();
+    void release();
+    int after_param_change();
+    int run_updates(int k, squint_update_stats* stats, cudaStream_t s, bool use_graph);
+    void record_update(int j, cudaStream_t s, bool debug);
+    size_t state_bytes() const;
+    int save_state(uint8_t* out);
+    int load_state(const uint8_t* in);
+    int debug_tensor(const char* name, void* host, size_t* bytes);
+    int refresh_policy(cudaStream_t s);
+    int ensure_act_capacity(int rows, int n_reqs);
+    size_t act_row_bytes() const;
+    int act(const squint_act_request* reqs, int n_reqs, cudaStream_t s, int64_t* version_used = nullptr);
+
+    // Device allocation; a failure is recorded as a null entry that allocate() reports.
+    template <typename T> T* dalloc(int64_t n) {
+        void* p = nullptr;
+        if (n <= 0) n = 1;
+        if (cudaMalloc(&p, (size_t)n * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        allocations.push_back(p);
+        return static_cast<T*>(p);
+    }
+};

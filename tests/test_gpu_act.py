@@ -1,0 +1,148 @@
+"""Actor inference and the continuous-batching server vs the FP64 oracle (needs a GB300)."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import squint_sac as o
+from paper_2602_21203_gb300 import synth
+from util import ring_to_device, split_params
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2602_21203_gb300 import lib
+    return lib
+
+
+def _batch(cfg, n, seed):
+    obs, prop = synth.make_obs_batch(n, cfg, seed, device="cuda")
+    out = torch.full((n, cfg["action_dim"]), float("nan"), device="cuda")
+    return obs, prop, out
+
+
+@pytest.mark.parametrize("name,n", [("small_b32", 37), ("train_b512", 24)])
+@pytest.mark.parametrize("sample", [True, False])
+def test_act_matches_oracle(L, name, n, sample):
+    cfg = synth.make_config(name)
+    learner = L.Learner(cfg, None)
+    P = o.init_params(cfg)
+    obs, prop, out = _batch(cfg, n, 5)
+    learner.act([L.Learner.request(obs, prop, out, key=1234, sample=sample)])
+    torch.cuda.synchronize()
+    ref = o.act(P, obs.cpu().numpy(), prop.cpu().numpy(), 1234, sample, cfg)
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-5
+    learner.close()
+
+
+def test_act_row_results_do_not_depend_on_the_batch(L):
+    cfg = synth.make_config("small_b32")
+    learner = L.Learner(cfg, None)
+    sizes = [1, 5, 17, 3, 64]
+    groups = [_batch(cfg, n, 10 + i) for i, n in enumerate(sizes)]
+    alone = []
+    for i, (obs, prop, out) in enumerate(groups):
+        learner.act([L.Learner.request(obs, prop, out, key=100 + i)])
+        torch.cuda.synchronize()
+        alone.append(out.clone())
+        out.fill_(float("nan"))
+    learner.act([L.Learner.request(obs, prop, out, key=100 + i) for i, (obs, prop, out) in enumerate(groups)])
+    torch.cuda.synchronize()
+    for (obs, prop, out), a in zip(groups, alone):
+        assert torch.equal(out, a)
+    learner.close()
+
+
+def test_act_uses_updated_weights_after_refresh(L):
+    cfg = synth.make_config("tiny_b8")
+    ring = ring_to_device(synth.make_ring(cfg, 0))
+    learner = L.Learner(cfg, ring)
+    obs, prop, out = _batch(cfg, 4, 3)
+    req = L.Learner.request(obs, prop, out, key=9, sample=False)
+    learner.act([req])
+    torch.cuda.synchronize()
+    before = out.clone()
+    learner.update(2)
+    learner.act([req])                       # snapshot not refreshed yet: same weights
+    torch.cuda.synchronize()
+    assert torch.equal(out, before)
+    learner.refresh_policy()
+    learner.act([req])
+    torch.cuda.synchronize()
+    P = split_params(learner.params(), cfg)
+    ref = o.act(P, obs.cpu().numpy(), prop.cpu().numpy(), 9, False, cfg)
+    assert np.abs(out.cpu().numpy() - ref).max() < 1e-5
+    assert not torch.equal(out, before)
+    learner.close()
+
+
+def test_serving_loop_results_equal_alone_and_admission(L):
+    cfg = synth.make_config("small_b32")
+    learner = L.Learner(cfg, None)
+    rng = np.random.default_rng(0)
+    sizes = [int(s) for s in rng.integers(1, 60, size=24)]
+    groups = [_batch(cfg, n, 50 + i) for i, n in enumerate(sizes)]
+    alone = []
+    for i, (obs, prop, out) in enumerate(groups):
+        learner.act([L.Learner.request(obs, prop, out, key=7 + i)])
+        torch.cuda.synchronize()
+        alone.append(out.clone())
+        out.fill_(float("nan"))
+    learner.serve_start(max_rows=128, mem_budget_bytes=1 << 30)
+    tickets = []
+    for i, (obs, prop, out) in enumerate(groups):
+        t = learner.serve_submit(L.Learner.request(obs, prop, out, key=7 + i, group_id=i))
+        assert t is not None
+        tickets.append(t)
+        if i % 5 == 0:
+            time.sleep(0.001)                # arrivals spread over time
+    lats = []
+    for t in tickets:
+        r = None
+        deadline = time.time() + 30
+        while r is None and time.time() < deadline:
+            r = learner.serve_poll(t, timeout_us=100_000)
+        assert r is not None
+        lats.append(r[0])
+    for (obs, prop, out), a in zip(groups, alone):
+        assert torch.equal(out, a)
+    assert all(x > 0 for x in lats)
+    # a group larger than the admission limit is refused, not queued
+    big = _batch(cfg, 200, 1)
+    with pytest.raises(L.SquintError) as e:
+        learner.serve_submit(L.Learner.request(*big, key=1))
+    assert e.value.code == L.EINVAL
+    learner.serve_stop()
+    learner.close()
+
+
+def test_serving_beside_updates_sees_consistent_snapshots(L):
+    """Requests served while the update stream runs UTD steps and refreshes the policy."""
+    cfg = synth.make_config("tiny_b8")
+    ring = ring_to_device(synth.make_ring(cfg, 0))
+    learner = L.Learner(cfg, ring)
+    upd = torch.cuda.Stream()
+    learner.serve_start(max_rows=64, mem_budget_bytes=1 << 28)
+    obs, prop, out = _batch(cfg, 8, 4)
+    versions = []
+    snapshots = {}
+    for step in range(6):
+        with torch.cuda.stream(upd):
+            learner.update(2, stats=False, stream=upd)
+            learner.refresh_policy(stream=upd)
+        t = learner.serve_submit(L.Learner.request(obs, prop, out, key=3, sample=False))
+        r = None
+        deadline = time.time() + 30
+        while r is None and time.time() < deadline:
+            r = learner.serve_poll(t, timeout_us=1_000_000)
+        assert r is not None
+        versions.append(r[1])
+        snapshots.setdefault(r[1], out.clone())
+    upd.synchronize()
+    assert versions == sorted(versions)
+    assert torch.isfinite(out).all() and (out.abs() < 1).all()
+    learner.serve_stop()
+    learner.close()

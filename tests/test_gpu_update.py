@@ -1,0 +1,208 @@
+"""CUDA update path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerances (FP32 path): integer steps (slots, shifts, box sums) bit-exact;
+losses, Q-mean, temperature 1e-4 relative; every gradient tensor 1e-3 relative
+in norm; the parameter change of one update 1e-3 relative in norm per group.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import squint_sac as o
+from paper_2602_21203_gb300 import synth
+from util import flatten, lazy_ring, rel_err, ring_to_device, split_params
+
+pytestmark = pytest.mark.gpu
+
+LOSS_RTOL = 1e-4
+GRAD_RTOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2602_21203_gb300 import lib
+    return lib
+
+
+def _setup(L, name, seed=0, **over):
+    cfg = synth.make_config(name, **over)
+    ring_cpu = synth.make_ring(cfg, seed)
+    ring = ring_to_device(ring_cpu)
+    learner = L.Learner(cfg, ring)
+    return cfg, ring_cpu, ring, learner
+
+
+def _close(a, b, rtol, atol=0.0):
+    return abs(a - b) <= rtol * abs(b) + atol
+
+
+@pytest.mark.parametrize("name", ["small_b32", "train_b512", "tiny_b8"])
+def test_initial_parameters_match_oracle_bitwise(L, name):
+    cfg = synth.make_config(name)
+    learner = L.Learner(cfg, None)
+    got = learner.params()
+    ref = flatten(o.init_params(cfg), cfg).astype(np.float32)
+    assert np.array_equal(got, ref)
+    learner.close()
+
+
+@pytest.mark.parametrize("name", ["small_b32", "tiny_b8"])
+def test_frontend_is_bit_exact(L, name):
+    cfg, ring_cpu, ring, learner = _setup(L, name)
+    for u in range(2):
+        learner.update(1, graph=False)
+        fe = o.frontend(cfg, synth.ring_numpy(ring_cpu), u)
+        assert np.array_equal(learner.debug("idx", np.int32), fe["idx"])
+        assert np.array_equal(learner.debug("nxt", np.int32), fe["nxt"])
+        assert np.array_equal(learner.debug("shift_t", np.int32).reshape(-1, 2), fe["shift_t"])
+        assert np.array_equal(learner.debug("shift_t1", np.int32).reshape(-1, 2), fe["shift_t1"])
+        assert np.array_equal(learner.debug("sums_t", np.uint16).reshape(fe["sums_t"].shape), fe["sums_t"])
+        assert np.array_equal(learner.debug("sums_t1", np.uint16).reshape(fe["sums_t1"].shape), fe["sums_t1"])
+        x = learner.debug("x_t").reshape(fe["x_t"].shape)
+        assert np.abs(x - fe["x_t"]).max() < 1e-6
+    learner.close()
+
+
+def _check_update(cfg, learner, state, ring_np, graph):
+    p_before = learner.params().astype(np.float64)
+    stats = learner.update(1, graph=graph)[0]
+    ref, tr = o.update(state, ring_np, cfg)
+    for key in ("critic_loss", "alpha_loss", "alpha", "entropy", "actor_loss"):
+        assert _close(stats[key], ref[key], LOSS_RTOL, 1e-6), (key, stats[key], ref[key])
+    assert _close(stats["q_mean"], ref["q_mean"], LOSS_RTOL, 1e-5), (stats["q_mean"], ref["q_mean"])
+    return stats, ref, tr, p_before
+
+
+@pytest.mark.parametrize("name", ["small_b32", "tiny_b8"])
+def test_one_update_matches_oracle(L, name):
+    cfg, ring_cpu, ring, learner = _setup(L, name)
+    ring_np = synth.ring_numpy(ring_cpu)
+    state = o.init_state(cfg)
+    stats, ref, tr, p_before = _check_update(cfg, learner, state, ring_np, graph=False)
+    # projected target distribution and critic logits
+    K = cfg["atoms"]
+    m = learner.debug("m").reshape(-1, K)
+    assert np.abs(m - tr["target"]["m"]).max() < 1e-5
+    assert np.allclose(m.sum(1), 1.0, atol=1e-5)
+    logits = learner.debug("logits").reshape(2, -1, K)
+    assert rel_err(logits, tr["critic"]["logits"]) < 1e-5
+    # every gradient tensor
+    g = split_params(learner.debug("grads"), cfg)
+    ref_grads = dict(tr["critic"]["grads"])
+    ref_grads.update(tr["actor"]["grads"])
+    for k, v in ref_grads.items():
+        assert rel_err(g[k], v) < GRAD_RTOL, (k, rel_err(g[k], v))
+    # parameter change of the update, per optimiser group
+    p_after = learner.params().astype(np.float64)
+    ref_after = flatten(state["params"], cfg)
+    for grp in ("critic", "actor", "alpha"):
+        sel = np.concatenate([np.full(int(np.prod(s)), o.group_of(nm) == grp) for nm, s, _, _ in o.param_spec(cfg)])
+        d_gpu = p_after[sel] - p_before[sel]
+        d_ref = ref_after[sel] - p_before[sel]
+        assert rel_err(d_gpu, d_ref) < 1e-3, (grp, rel_err(d_gpu, d_ref))
+    tgt = learner.debug("target")
+    ref_t = np.concatenate([state["target"][nm].ravel() for nm, *_ in o.param_spec(cfg) if o.is_target(nm)])
+    assert np.abs(tgt - ref_t).max() < 1e-5
+    learner.close()
+
+
+def test_graph_replay_equals_eager_bitwise(L):
+    cfg, ring_cpu, ring, a = _setup(L, "small_b32")
+    b = L.Learner(cfg, ring)
+    sa = a.update(3, graph=True)
+    sb = b.update(3, graph=False)
+    assert np.array_equal(a.params(), b.params())
+    assert sa == sb
+    sa = a.update(3, graph=True)      # replay of the captured graph
+    sb = b.update(3, graph=False)
+    assert np.array_equal(a.params(), b.params())
+    assert np.array_equal(a.debug("target"), b.debug("target"))
+    assert [s["update_idx"] for s in sa] == [3, 4, 5]
+    a.close()
+    b.close()
+
+
+def test_k_updates_track_oracle(L):
+    cfg, ring_cpu, ring, learner = _setup(L, "small_b32")
+    ring_np = synth.ring_numpy(ring_cpu)
+    state = o.init_state(cfg)
+    stats = learner.update(4, graph=True)
+    for j in range(4):
+        ref, _ = o.update(state, ring_np, cfg)
+        for key in ("critic_loss", "alpha", "entropy", "actor_loss", "alpha_loss"):
+            assert _close(stats[j][key], ref[key], 1e-3, 1e-5), (j, key, stats[j][key], ref[key])
+    learner.close()
+
+
+def test_policy_freq_two_delays_the_actor(L):
+    cfg, ring_cpu, ring, learner = _setup(L, "tiny_b8", policy_freq=2)
+    n0 = learner.params()
+    spec = o.param_spec(cfg)
+    sel = np.concatenate([np.full(int(np.prod(s)), o.group_of(nm) == "actor") for nm, s, _, _ in spec])
+    s1 = learner.update(1, graph=True)[0]
+    n1 = learner.params()
+    assert np.array_equal(n0[sel], n1[sel]) and math.isnan(s1["actor_loss"])
+    s2 = learner.update(1, graph=True)[0]
+    n2 = learner.params()
+    assert not np.array_equal(n1[sel], n2[sel]) and not math.isnan(s2["actor_loss"])
+    learner.close()
+
+
+def test_state_roundtrip_resumes_bitwise(L):
+    cfg, ring_cpu, ring, a = _setup(L, "tiny_b8")
+    a.update(2, graph=True)
+    blob = a.state()
+    b = L.Learner(cfg, ring)
+    b.set_state(blob)
+    sa = a.update(2, graph=True)
+    sb = b.update(2, graph=True)
+    assert sa == sb
+    assert np.array_equal(a.params(), b.params())
+    a.close()
+    b.close()
+
+
+def test_training_shape_update_matches_oracle(L):
+    """Full size: 100k-slot 3x128x128 ring on the device, batch 512, 4 conv layers, 256-d heads."""
+    cfg = synth.make_config("train_b512")
+    ring = synth.make_ring(cfg, 0, device="cuda")
+    learner = L.Learner(cfg, ring)
+    state = o.init_state(cfg)
+    lazy = lazy_ring(ring)
+    stats = learner.update(1, graph=True)[0]
+    ref, tr = o.update(state, lazy, cfg)
+    for key in ("critic_loss", "alpha_loss", "alpha", "entropy", "actor_loss"):
+        assert _close(stats[key], ref[key], LOSS_RTOL, 1e-6), (key, stats[key], ref[key])
+    assert _close(stats["q_mean"], ref["q_mean"], LOSS_RTOL, 1e-5)
+    g = split_params(learner.debug("grads"), cfg)
+    ref_grads = dict(tr["critic"]["grads"])
+    ref_grads.update(tr["actor"]["grads"])
+    for k, v in ref_grads.items():
+        assert rel_err(g[k], v) < GRAD_RTOL, (k, rel_err(g[k], v))
+    # the UTD-4 graph of the timed configuration runs and stays finite
+    more = learner.update(4, graph=True)
+    assert all(math.isfinite(s["critic_loss"]) and math.isfinite(s["actor_loss"]) for s in more)
+    assert [s["update_idx"] for s in more] == [1, 2, 3, 4]
+    learner.close()
+    del ring
+    torch.cuda.empty_cache()
+
+
+def test_errors_are_codes_not_crashes(L):
+    cfg = synth.make_config("tiny_b8")
+    learner = L.Learner(cfg, None)
+    with pytest.raises(L.SquintError) as e:
+        learner.update(1)
+    assert e.value.code == L.ESTATE
+    ring = ring_to_device(synth.make_ring(cfg, 0))
+    learner.set_replay(ring)
+    for k in (0, 99):
+        with pytest.raises(L.SquintError) as e:
+            learner.update(k)
+        assert e.value.code == L.EINVAL
+    learner.update(1)
+    with pytest.raises(L.SquintError):
+        learner.set_params(np.zeros(3, dtype=np.float32))
+    learner.close()
