@@ -1,0 +1,489 @@
+#!/usr/bin/env python
+"""Benchmark of the Squint learner on GB300: SAC updates/s at batch 512, UTD-4 graph.
+
+A step is one squint_update(k=4) call: four full SAC updates (minibatch draw,
+shift + squint, encoder, target, critic/encoder step, temperature step, actor
+step, polyak) replayed as one CUDA graph, on the training-shape workload: a
+100k-slot ring of 3x128x128 uint8 frames (4.9 GB, uniform random slots, so the
+gathered inputs are larger than L2), batch 512, 4 conv layers of 32 channels,
+256-d projections, critics 512-512 x2 with 101 atoms, actor 512-512.
+
+Prints one JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle
+instead (rank 0 only), on the same workload and metric.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "train_b512"
+UTD_K = 4
+METRIC = "SAC updates/s at B=512 (UTD-4 CUDA graph)"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+# DRAM traffic per launch of the dominant phase from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (phase, precision).
+NCU_TRAFFIC = {}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+# ------------------------------------------------------------------ algorithmic work per phase
+def phase_work(cfg):
+    """(bound, work per update, unit) of each phase of one update, from the shapes alone."""
+    B, C, H, W, f = cfg["batch"], cfg["obs_c"], cfg["obs_h"], cfg["obs_w"], cfg["squint_f"]
+    A, P, K = cfg["action_dim"], cfg["proprio_dim"], cfg["atoms"]
+    hs, ws = H // f, W // f
+    macs = []
+    cin, h, w = C, hs, ws
+    strides = cfg.get("conv_strides") or [2] + [1] * (cfg["conv_layers"] - 1)
+    for s in strides:
+        oh, ow = (h - 3) // s + 1, (w - 3) // s + 1
+        macs.append(oh * ow * cfg["conv_ch"] * cin * 9)
+        cin, h, w = cfg["conv_ch"], oh, ow
+    F = cin * h * w
+    D = cfg["proj_dim"]
+    Z = D if D > 0 else F
+    Dc, Da = Z + P + A, Z + P
+    hid = cfg["hidden"]
+    crit = Dc * hid[0] + sum(hid[i] * hid[i + 1] for i in range(len(hid) - 1)) + hid[-1] * K
+    actor = Da * hid[0] + sum(hid[i] * hid[i + 1] for i in range(len(hid) - 1)) + hid[-1] * 2 * A
+    proj = F * D
+    n_enc = sum(cout * cin_ * 10 for cout, cin_ in [(cfg["conv_ch"], C)] + [(cfg["conv_ch"], cfg["conv_ch"])] *
+                (cfg["conv_layers"] - 1))
+    n_critic_grp = n_enc + (2 * proj + 4 * D if D else 0) + 2 * (crit + sum(3 * x for x in hid) + K)
+    n_actor_grp = (proj + 3 * D if D else 0) + actor + sum(3 * x for x in hid) + 2 * A
+    fl = lambda m: 2.0 * m
+    return {
+        "frontend": ("hbm", 2 * B * C * H * W + 2 * B * C * hs * ws * 4, "B"),
+        "encoder_fwd": ("fma", fl(2 * B * sum(macs)), "FLOP"),
+        "projections": ("fma", fl(4 * B * proj), "FLOP"),
+        "actor_fwd": ("fma", fl(2 * B * actor), "FLOP"),
+        "target_critics": ("fma", fl(2 * B * crit), "FLOP"),
+        "critic_fwd_ce": ("fma", fl(2 * B * crit), "FLOP"),
+        "critic_bwd": ("fma", fl(2 * 2 * B * crit + 2 * B * proj), "FLOP"),
+        "encoder_bwd": ("fma", fl(B * sum(macs) + B * sum(macs[1:])), "FLOP"),
+        "adam_critic": ("hbm", 28 * n_critic_grp, "B"),
+        "alpha_step": ("latency", 0, "B"),
+        "actor_step": ("fma", fl(B * proj + 2 * B * crit + 2 * B * crit + 2 * B * actor + B * proj), "FLOP"),
+        "stats_polyak": ("hbm", 12 * (n_critic_grp - n_enc), "B"),
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ distributed plumbing
+def dist_setup(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_updates_per_s(cfg, ring, budget_s, max_updates=3):
+    """Time the FP64 oracle on a bounded sample: whole updates (or a batch slice) within ~budget_s."""
+    import numpy as np
+    from oracle import squint_sac as o
+    state = o.init_state(cfg)
+    t0 = time.perf_counter()
+    o.update(state, ring, cfg)
+    one = time.perf_counter() - t0
+    n = max(1, min(max_updates, int(budget_s / max(one, 1e-3))))
+    t0 = time.perf_counter()
+    for _ in range(n):
+        o.update(state, ring, cfg)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        info = threadpool_info()
+        n = [d.get("num_threads") for d in info if d.get("user_api") == "blas"]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count()
+
+
+class LazyRows:
+    def __init__(self, t):
+        self.t = t
+        self.shape = tuple(t.shape)
+
+    def __getitem__(self, idx):
+        import numpy as np
+        import torch
+        ii = torch.as_tensor(np.asarray(idx), device=self.t.device, dtype=torch.long)
+        return self.t.index_select(0, ii).cpu().numpy()
+
+
+def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the same workload, rank 0 only."""
+    import torch
+    from paper_2602_21203_gb300 import synth
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    cfg = synth.make_config(WORKLOAD)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    ring = {k: LazyRows(v) for k, v in synth.make_ring(cfg, args.seed, device=dev).items()}
+    from oracle import squint_sac as o
+    # size each step's sample so the whole run stays within ~3 minutes
+    probe = synth.make_config(WORKLOAD, batch=64)
+    st = o.init_state(probe)
+    t0 = time.perf_counter()
+    o.update(st, ring, probe)
+    per_sample = (time.perf_counter() - t0) / 64
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    bsz = 512
+    while bsz > 32 and bsz * per_sample > budget:
+        bsz //= 2
+    scfg = synth.make_config(WORKLOAD, batch=bsz)
+    state = o.init_state(scfg)
+    for _ in range(args.warmup):
+        o.update(state, ring, scfg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.update(state, ring, scfg)
+    dt = time.perf_counter() - t0
+    value = args.steps * (bsz / cfg["batch"]) / dt
+    cores = blas_threads()
+    sample = f"{args.steps} FP64 oracle updates on batch slices of {bsz} of the 512-sample workload, scaled to B=512"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "train_b512: 100k x 3x128x128 uint8 ring, batch 512, UTD 4, 4 conv x 32ch, "
+                               "proj 256, critics 512-512 x2 (101 atoms), actor 512-512"},
+        "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2602_21203_gb300 import lib, synth
+
+    world, rank, local = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the learner has no CPU path)")
+    peaks, peaks_src = load_peaks()
+    cfg = synth.make_config(WORKLOAD)
+    prec = lib.PREC_BF16 if args.precision == "bf16" else lib.PREC_FP32
+    ring = synth.make_ring(cfg, args.seed + rank, device="cuda")
+    learner = lib.Learner(cfg, ring, precision=prec, max_k=8)
+    stream = torch.cuda.Stream()
+    K = args.steps
+    W = max(3, args.warmup)
+
+    with torch.cuda.stream(stream):
+        for _ in range(W):
+            learner.update(UTD_K, stats=False, stream=stream)
+    stream.synchronize()
+
+    # ---- timed region: K graph replays of UTD_K updates, inputs already resident in HBM
+    clocks = ClockSampler(torch.cuda.current_device())
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(K):
+        learner.update(UTD_K, stats=False, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ms, world)
+    updates = world * K * UTD_K
+    value = updates / (ms / 1000.0)
+
+    # ---- end to end through the public API with host buffers: per step, insert the
+    # transitions one environment step adds at UTD 0.25 (4 updates <- 16 transitions)
+    # from pinned host memory into the ring, run the UTD-4 call, read its statistics back.
+    n_new = int(UTD_K / 0.25)
+    host = {k: v[:n_new].cpu().pin_memory() for k, v in ring.items()}
+    h2d = sum(v.numel() * v.element_size() for v in host.values())
+    d2h = UTD_K * 32
+    head = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        with torch.cuda.stream(stream):
+            sl = slice(head, head + n_new)
+            for k2, v in host.items():
+                ring[k2][sl].copy_(v, non_blocking=True)
+            head = (head + n_new) % (cfg["ring_size"] - n_new)
+        learner.update(UTD_K, stats=True, stream=stream)          # waits and reads stats to host
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e = {"value": world * K * UTD_K / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h)}
+
+    # ---- per-phase device times (CUDA events on the launching stream, eager update)
+    prof = {}
+    for _ in range(5):
+        for name, t in learner.profile_update(stream=stream).items():
+            prof.setdefault(name, []).append(t)
+    phase_ms = {k: statistics.median(v) for k, v in prof.items()}
+    work = phase_work(cfg)
+    dom = max((k for k in phase_ms if work[k][0] != "latency"), key=lambda k: phase_ms[k])
+    bound, amount, unit = work[dom]
+    secs = phase_ms[dom] / 1000.0
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if bound == "hbm":
+        achieved = amount / secs / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "unit": "GB/s"}
+        peak_note = f"{peaks_src} copy bandwidth"
+    elif prec == lib.PREC_BF16:
+        achieved = amount / secs / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "unit": "TFLOP/s"}
+        peak_note = f"{peaks_src} bf16 sustained"
+    else:
+        achieved = amount / secs / 1e12
+        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s"}
+        peak_note = f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz (median SM clock)"
+    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "traffic": NCU_TRAFFIC.get((dom, args.precision)), "kernel": dom, "peak_source": peak_note,
+                 "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()}})
+
+    # ---- serving: continuous batching beside the UTD-4 update stream
+    serving = None
+    if not args.no_serving and rank == 0:
+        serving = measure_serving(lib, learner, cfg, stream)
+
+    # ---- CPU baseline: the oracle on this workload, rank 0 at N=1
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        lazy = {k: LazyRows(v) for k, v in ring.items()}
+        ups, n, dt = oracle_updates_per_s(cfg, lazy, budget_s=15.0)
+        cpu = {"value": ups, "unit": "updates/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": f"{n} FP64 oracle update(s) of the full batch-512 workload in {dt:.1f} s"}
+
+    kernels = learner.graph_kernel_count(UTD_K)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec == lib.PREC_BF16 else "f32", "data": "synthetic",
+            "config": {"workload": "train_b512: 100k x 3x128x128 uint8 ring (4.9 GB), batch 512, UTD 4 per step, "
+                                   "shift pad 8, squint 4x to 32x32, 4 conv x 32ch, proj 256 + LN, critics "
+                                   "512-512 x2 (101 atoms), actor 512-512",
+                       "updates_per_step": UTD_K, "precision": args.precision,
+                       "l2": "inputs larger than L2: 4.9 GB ring, 50 MB of uniformly random frames per update; "
+                             "weights and activations stay L2-resident between updates as in training",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": kernels * K, "clocks": clk,
+        }
+        if serving:
+            line["serving"] = serving
+        print(json.dumps(line), flush=True)
+    learner.close()
+
+
+def measure_serving(lib, learner, cfg, upd_stream, seconds=4.0, n_envs=4096, mean_step_us=200.0):
+    """Actor queries for n_envs environments in groups of U{1..512}, beside UTD-4 updates.
+
+    Closed loop: each group submits its query, and after its actions come back
+    waits an exponential environment-step time (mean mean_step_us) before the next
+    one, so arrivals are Poisson-like and about n_envs queries stay in flight.
+    The update thread runs UTD-4 calls and refreshes the policy snapshot after each.
+    """
+    import numpy as np
+    import torch
+    from paper_2602_21203_gb300 import synth
+    rng = np.random.default_rng(1)
+    sizes, left = [], n_envs
+    while left > 0:
+        n = min(int(rng.integers(1, 513)), left)
+        sizes.append(n)
+        left -= n
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    obs, prop = synth.make_obs_batch(n_envs, cfg, 3, device="cuda")
+    out = torch.empty(n_envs, cfg["action_dim"], device="cuda")
+    learner.serve_start(max_rows=n_envs, mem_budget_bytes=16 << 30)
+    stop = threading.Event()
+    counter = {"updates": 0}
+
+    def updater():
+        with torch.cuda.stream(upd_stream):
+            while not stop.is_set():
+                learner.update(UTD_K, stats=False, stream=upd_stream)
+                learner.refresh_policy(stream=upd_stream)
+                upd_stream.synchronize()
+                counter["updates"] += UTD_K
+
+    th = threading.Thread(target=updater)
+    th.start()
+    time.sleep(0.2)
+    t_start = time.perf_counter()
+    tickets = [None] * len(sizes)
+    next_t = [t_start] * len(sizes)
+    lats, rows_done, key = [], 0, 0
+    u0 = counter["updates"]
+    while time.perf_counter() - t_start < seconds:
+        now = time.perf_counter()
+        for g, n in enumerate(sizes):
+            if tickets[g] is None:
+                if now >= next_t[g]:
+                    a, b = int(offs[g]), int(offs[g + 1])
+                    req = lib.Learner.request(obs[a:b], prop[a:b], out[a:b], key=key, group_id=g)
+                    tickets[g] = learner.serve_submit(req)
+                    key += 1
+            else:
+                r = learner.serve_poll(tickets[g], 0)
+                if r is not None:
+                    lats.append(r[0])
+                    rows_done += n
+                    tickets[g] = None
+                    next_t[g] = time.perf_counter() + rng.exponential(mean_step_us * 1e-6)
+    elapsed = time.perf_counter() - t_start
+    u1 = counter["updates"]
+    for g in range(len(sizes)):
+        if tickets[g] is not None:
+            learner.serve_poll(tickets[g], 5_000_000)
+    stop.set()
+    th.join()
+    learner.serve_stop()
+    if not lats:
+        return None
+    return {"envs": n_envs, "groups": len(sizes), "requests_completed": len(lats),
+            "queries_per_s": rows_done / elapsed, "p50_us": float(np.percentile(lats, 50)),
+            "p99_us": float(np.percentile(lats, 99)), "updates_per_s_concurrent": (u1 - u0) / elapsed,
+            "group_sizes": "U{1..512}", "arrivals": f"closed loop, exponential env step mean {mean_step_us:.0f} us",
+            "latency": "submit to completion event, measured by the server thread"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

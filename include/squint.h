@@ -148,6 +148,20 @@ int squint_update(squint_handle* h, int k, squint_update_stats* stats, void* str
  */
 int squint_update_eager(squint_handle* h, int k, squint_update_stats* stats, void* stream);
 
+/* ------------------------------------------------------------------ measurement */
+
+/* Kernel nodes in the graph captured for k updates (0 if none captured yet). */
+int64_t squint_graph_kernel_count(squint_handle* h, int k);
+
+/*
+ * One update issued eagerly on `stream` with a CUDA event at every phase
+ * boundary; ms[i] receives the device time of phase i (see squint_phase_name)
+ * and *n_phases their number (at most cap are written).  Waits for the stream.
+ */
+int squint_profile_update(squint_handle* h, float* ms, int cap, int* n_phases, void* stream);
+/* Name of phase i of squint_profile_update, or NULL. */
+const char* squint_phase_name(int i);
+
 /* ------------------------------------------------------------------ inference */
 
 /* One actor query: n environments of one group (Alg. 1, "Sample a_t ~ pi"). */

@@ -287,6 +287,21 @@ int squint_debug_tensor(squint_handle* h, const char* name, void* host, size_t* 
     return h->debug_tensor(name, host, bytes);
 }
 
+int64_t squint_graph_kernel_count(squint_handle* h, int k) {
+    if (!h) return 0;
+    auto it = h->graph_kernels.find(k);
+    return it == h->graph_kernels.end() ? 0 : it->second;
+}
+
+int squint_profile_update(squint_handle* h, float* ms, int cap, int* n_phases, void* stream) {
+    if (!h || !ms || cap < 0) return SQUINT_EINVAL;
+    if (h->failed) return SQUINT_ESTATE;
+    if (!h->has_ring) return SQUINT_ESTATE;
+    return h->profile_update(ms, cap, n_phases, (cudaStream_t)stream);
+}
+
+const char* squint_phase_name(int i) { return sq::phase_name(i); }
+
 int squint_refresh_policy(squint_handle* h, void* stream) {
     if (!h) return SQUINT_EINVAL;
     if (h->failed) return SQUINT_ESTATE;

@@ -45,6 +45,7 @@ struct Layout {
 };
 
 bool build_layout(const squint_config& c, Layout& L);
+const char* phase_name(int i);
 void init_params_host(const squint_config& c, const Layout& L, std::vector<float>& p);
 
 // Activations of one MLP evaluated on `rows` rows by E parameter sets.
@@ -134,6 +135,17 @@ struct squint_handle {
     bool req_event_live = false;
     std::vector<void*> act_allocs;
     std::map<int, cudaGraphExec_t> graphs;
+    std::map<int, int64_t> graph_kernels;
+    std::vector<cudaEvent_t>* phase_events = nullptr;   // set while profiling an eager update
+    void mark(cudaStream_t s) {
+        if (phase_events) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            cudaEventRecord(e, s);
+            phase_events->push_back(e);
+        }
+    }
+    int profile_update(float* ms, int cap, int* n_phases, cudaStream_t s);
 
     std::vector<void*> allocations;
     sq::ServeState* serve = nullptr;

@@ -317,6 +317,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     float* G = grads;
     float* stats = d_stats + 8 * j;
 
+    mark(s);
     // ---- a1-a4: minibatch, gathers, shift, squint
     FrontendArgs fa{};
     fa.obs = ring.obs; fa.proprio = ring.proprio; fa.action = ring.action; fa.reward = ring.reward; fa.done = ring.done;
@@ -336,6 +337,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     fa.steps = d_steps; fa.do_actor = d_do_actor; fa.policy_freq = c.policy_freq;
     launch_frontend(fa, s);
 
+    mark(s);
     // ---- a5: encoder on o_t (rows < B) and o_{t+1} (rows >= B)
     const float* in = x2;
     for (size_t l = 0; l < L.conv.size(); ++l) {
@@ -348,6 +350,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     const float* z = conv_out.back();          // [2B, F]
     const float* z1 = z + (int64_t)B * F;
 
+    mark(s);
     // ---- a6: per-head projections (or the flattened features straight into the heads)
     const PSet online{W, 0};
     const PSet tgt{target, L.critic_begin};
@@ -383,6 +386,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         cudaMemcpy2DAsync(xq, Dc * sizeof(float), z, fb, fb, B, cudaMemcpyDeviceToDevice, s);
     }
 
+    mark(s);
     // ---- a7: actor (pre-update) on both halves; tanh-Gaussian sample
     const std::vector<Lin>* act_layers[1] = {&L.actor};
     const std::vector<Lin>* crit_layers[2] = {&L.critic[0], &L.critic[1]};
@@ -399,6 +403,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ah.logp = logp; ah.eps = eps;
         launch_actor_head(ah, s);
     }
+    mark(s);
     // ---- a8-a9: target critics and the projected categorical target
     {
         PSet ps[2] = {tgt, tgt};
@@ -411,6 +416,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ct.m = m;
         launch_c51_target(ct, s);
     }
+    mark(s);
     // ---- a10: online critics and the cross entropy
     {
         PSet ps[2] = {online, online};
@@ -421,6 +427,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ce.dlogits = dlogits; ce.row_loss = row_loss; ce.row_q = row_q;
         launch_ce(ce, s);
     }
+    mark(s);
     // ---- a11: backward through critics, critic projection, encoder
     {
         const float* mask = Dd > 0 ? nullptr : z;      // flatten path: mask by the last conv's ReLU
@@ -442,6 +449,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             gx.mask = z; gx.sm_m = F; gx.sm_n = 1;
             launch_gemm<float>(&gx, 1, kKN, s);
         }
+        mark(s);
         const float* cur = dz;
         for (int l = (int)L.conv.size() - 1; l >= 0; --l) {
             const ConvL& cv = L.conv[l];
@@ -456,6 +464,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             }
         }
     }
+    mark(s);
     // ---- a12: Adam over encoder + critic projection + critics
     {
         AdamArgs ad{};
@@ -464,6 +473,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
         launch_adam(ad, s);
     }
+    mark(s);
     // ---- a13: temperature
     {
         AlphaArgs al{};
@@ -475,6 +485,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         al.stats = stats;
         launch_alpha_step(al, s);
     }
+    mark(s);
     // ---- a14: actor step on stop-gradient features with the updated critics
     {
         if (Dd > 0) {
@@ -526,6 +537,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
         launch_adam(ad, s);
     }
+    mark(s);
     // ---- statistics, then a16: polyak (also advances the update index)
     {
         StatsArgs st{};
@@ -536,6 +548,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         PolyakArgs pa{target, W + L.critic_begin, L.target_n, (float)c.tau, d_update_idx};
         launch_polyak(pa, s);
     }
+    mark(s);
 }
 
 int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s, bool use_graph) {
@@ -553,6 +566,17 @@ int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s
             SQ_CK(this, cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
             for (int j = 0; j < k; ++j) record_update(j, capture_stream, false);
             SQ_CK(this, cudaStreamEndCapture(capture_stream, &graph));
+            size_t n_nodes = 0;
+            SQ_CK(this, cudaGraphGetNodes(graph, nullptr, &n_nodes));
+            std::vector<cudaGraphNode_t> nodes(n_nodes);
+            SQ_CK(this, cudaGraphGetNodes(graph, nodes.data(), &n_nodes));
+            int64_t kernels = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                SQ_CK(this, cudaGraphNodeGetType(nd, &t));
+                kernels += t == cudaGraphNodeTypeKernel;
+            }
+            graph_kernels[k] = kernels;
             cudaGraphExec_t exec;
             SQ_CK(this, cudaGraphInstantiate(&exec, graph, 0));
             cudaGraphDestroy(graph);
@@ -817,4 +841,41 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
     SQ_CK(this, cudaEventRecord(policy_released[pi], s));
     SQ_CK(this, cudaGetLastError());
     return SQUINT_OK;
+}
+
+// Phase names, in the order their boundaries are marked in record_update.
+static const char* kPhaseNames[] = {
+    "frontend",          // a1-a4
+    "encoder_fwd",       // a5
+    "projections",       // a6
+    "actor_fwd",         // a7
+    "target_critics",    // a8-a9
+    "critic_fwd_ce",     // a10
+    "critic_bwd",        // a11 (MLP + projection)
+    "encoder_bwd",       // a11 (conv wgrad/dgrad)
+    "adam_critic",       // a12
+    "alpha_step",        // a13
+    "actor_step",        // a14-a15
+    "stats_polyak",      // a16
+};
+
+const char* sq::phase_name(int i) {
+    return (i >= 0 && i < (int)(sizeof(kPhaseNames) / sizeof(kPhaseNames[0]))) ? kPhaseNames[i] : nullptr;
+}
+
+int squint_handle::profile_update(float* ms, int cap, int* n_phases, cudaStream_t s) {
+    std::vector<cudaEvent_t> ev;
+    phase_events = &ev;
+    record_update(0, s, false);
+    phase_events = nullptr;
+    int rc = SQUINT_OK;
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = SQUINT_ECUDA;
+    const int n = (int)ev.size() - 1;
+    if (n_phases) *n_phases = n;
+    for (int i = 0; rc == SQUINT_OK && i < n && i < cap; ++i) {
+        if (cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]) != cudaSuccess) rc = SQUINT_ECUDA;
+    }
+    for (auto e : ev) cudaEventDestroy(e);
+    if (rc != SQUINT_OK) { failed = true; g_last_error = "profiling failed"; }
+    return rc;
 }

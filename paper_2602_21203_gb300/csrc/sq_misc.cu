@@ -70,32 +70,54 @@ __global__ void ln_bwd_row_kernel(Batch<LnBwdProblem> b) {
     }
 }
 
-// Column part: dg = sum dn xh, dbeta = sum dn, dbias = sum dpre (fixed row order).
-__global__ void ln_bwd_col_kernel(Batch<LnBwdProblem> b) {
+// Column part: dg = sum dn xh, dbeta = sum dn, dbias = sum dpre.  Block (32 columns x
+// 16 row slices): thread (x, y) sums rows y, y+16, ... in order, then the 16 slice
+// sums are added in slice order, so the result does not depend on scheduling.
+constexpr int kColX = 32, kColY = 16;
+__global__ void __launch_bounds__(kColX * kColY) ln_bwd_col_kernel(Batch<LnBwdProblem> b) {
+    __shared__ float part[3][kColY][kColX + 1];
     const LnBwdProblem& P = b.p[blockIdx.y];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P.n) return;
+    const int tx = threadIdx.x % kColX, ty = threadIdx.x / kColX;
+    const int j = blockIdx.x * kColX + tx;
     float sg = 0.f, sb = 0.f, sd = 0.f;
-    for (int r = 0; r < P.rows; ++r) {
-        const float o = P.out ? P.out[(int64_t)r * P.ld_out + j] : 1.f;
-        const float dn = (P.out && !(o > 0.f)) ? 0.f : P.dout[(int64_t)r * P.ld_dout + j];
-        const float xh = (P.pre[(int64_t)r * P.ld_pre + j] - P.mean[r]) * P.rstd[r];
-        sg += dn * xh;
-        sb += dn;
-        if (P.dbias) sd += P.dpre[(int64_t)r * P.ld_dpre + j];
+    if (j < P.n) {
+        for (int r = ty; r < P.rows; r += kColY) {
+            const float o = P.out ? P.out[(int64_t)r * P.ld_out + j] : 1.f;
+            const float dn = (P.out && !(o > 0.f)) ? 0.f : P.dout[(int64_t)r * P.ld_dout + j];
+            const float xh = (P.pre[(int64_t)r * P.ld_pre + j] - P.mean[r]) * P.rstd[r];
+            sg += dn * xh;
+            sb += dn;
+            if (P.dbias) sd += P.dpre[(int64_t)r * P.ld_dpre + j];
+        }
     }
-    if (P.dg) P.dg[j] = sg;
-    if (P.dbeta) P.dbeta[j] = sb;
-    if (P.dbias) P.dbias[j] = sd;
+    part[0][ty][tx] = sg;
+    part[1][ty][tx] = sb;
+    part[2][ty][tx] = sd;
+    __syncthreads();
+    if (ty == 0 && j < P.n) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        for (int y = 0; y < kColY; ++y) { a0 += part[0][y][tx]; a1 += part[1][y][tx]; a2 += part[2][y][tx]; }
+        if (P.dg) P.dg[j] = a0;
+        if (P.dbeta) P.dbeta[j] = a1;
+        if (P.dbias) P.dbias[j] = a2;
+    }
 }
 
-__global__ void colsum_kernel(Batch<ColSumProblem> b) {
+__global__ void __launch_bounds__(kColX * kColY) colsum_kernel(Batch<ColSumProblem> b) {
+    __shared__ float part[kColY][kColX + 1];
     const ColSumProblem& P = b.p[blockIdx.y];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P.n) return;
+    const int tx = threadIdx.x % kColX, ty = threadIdx.x / kColX;
+    const int j = blockIdx.x * kColX + tx;
     float s = 0.f;
-    for (int r = 0; r < P.rows; ++r) s += P.in[(int64_t)r * P.ld + j];
-    P.out[j] = s;
+    if (j < P.n)
+        for (int r = ty; r < P.rows; r += kColY) s += P.in[(int64_t)r * P.ld + j];
+    part[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && j < P.n) {
+        float a = 0.f;
+        for (int y = 0; y < kColY; ++y) a += part[y][tx];
+        P.out[j] = a;
+    }
 }
 
 // Block-wide reductions for one row per block (blockDim = 128).
@@ -394,10 +416,15 @@ void launch_ln_bwd(const LnBwdProblem* p, int n, cudaStream_t s) {
         const int cnt = std::min(kMaxLn, n - base);
         auto b = make_batch(p + base, cnt);
         int rows = 0, cols = 0;
-        for (int i = 0; i < cnt; ++i) { rows += b.p[i].rows; cols = std::max(cols, b.p[i].n); }
+        bool any_col = false;
+        for (int i = 0; i < cnt; ++i) {
+            rows += b.p[i].rows;
+            cols = std::max(cols, b.p[i].n);
+            any_col |= b.p[i].dg || b.p[i].dbeta || b.p[i].dbias;
+        }
         if (!rows) continue;
         ln_bwd_row_kernel<<<(rows + 7) / 8, 256, 0, s>>>(b);
-        ln_bwd_col_kernel<<<dim3((cols + 127) / 128, cnt), 128, 0, s>>>(b);
+        if (any_col) ln_bwd_col_kernel<<<dim3((cols + kColX - 1) / kColX, cnt), kColX * kColY, 0, s>>>(b);
     }
 }
 void launch_colsum(const ColSumProblem* p, int n, cudaStream_t s) {
@@ -406,7 +433,7 @@ void launch_colsum(const ColSumProblem* p, int n, cudaStream_t s) {
         auto b = make_batch(p + base, cnt);
         int cols = 0;
         for (int i = 0; i < cnt; ++i) cols = std::max(cols, b.p[i].n);
-        if (cols) colsum_kernel<<<dim3((cols + 127) / 128, cnt), 128, 0, s>>>(b);
+        if (cols) colsum_kernel<<<dim3((cols + kColX - 1) / kColX, cnt), kColX * kColY, 0, s>>>(b);
     }
 }
 void launch_actor_head(const ActorHeadArgs& a, cudaStream_t s) {

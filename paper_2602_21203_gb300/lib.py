@@ -93,6 +93,9 @@ def load():
         "squint_set_state": (I, [P, P, SZ]),
         "squint_debug_tensor": (I, [P, ctypes.c_char_p, P, ctypes.POINTER(SZ)]),
         "squint_struct_size": (SZ, [ctypes.c_char_p]),
+        "squint_graph_kernel_count": (I64, [P, I]),
+        "squint_profile_update": (I, [P, P, I, ctypes.POINTER(I), P]),
+        "squint_phase_name": (ctypes.c_char_p, [I]),
         "squint_strerror": (ctypes.c_char_p, [I]),
         "squint_last_error": (ctypes.c_char_p, []),
     }
@@ -230,6 +233,17 @@ class Learner:
         _check(self.lib.squint_debug_tensor(self.h, name.encode(), out.ctypes.data_as(ctypes.c_void_p),
                                             ctypes.byref(n)), "squint_debug_tensor")
         return out
+
+    def graph_kernel_count(self, k):
+        return int(self.lib.squint_graph_kernel_count(self.h, int(k)))
+
+    def profile_update(self, stream=None):
+        """One eager update timed per phase: {phase name: device ms}."""
+        ms = (ctypes.c_float * 32)()
+        n = ctypes.c_int(0)
+        _check(self.lib.squint_profile_update(self.h, ms, 32, ctypes.byref(n), _stream(stream)),
+               "squint_profile_update")
+        return {self.lib.squint_phase_name(i).decode(): float(ms[i]) for i in range(n.value)}
 
     def refresh_policy(self, stream=None):
         _check(self.lib.squint_refresh_policy(self.h, _stream(stream)), "squint_refresh_policy")
