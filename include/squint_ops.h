@@ -1,0 +1,95 @@
+/*
+ * squint_ops.h - layer operations of the Squint learner on caller-owned device
+ * buffers.  They are the kernels the update is built from, exposed one by one so
+ * that each forward and hand-written backward can be checked on its own (finite
+ * differences in FP64, the FP64 oracle) and wrapped as autograd functions.
+ *
+ * Conventions: every pointer is a device pointer the caller owns; `stream` is a
+ * cudaStream_t as void*; calls are asynchronous on it.  Return value 0, or
+ * SQUINT_EINVAL (-1) for a bad argument / unsupported dtype, SQUINT_ECUDA (-3)
+ * if the launch failed.  Row-major layouts throughout.
+ */
+#ifndef SQUINT_OPS_H
+#define SQUINT_OPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SQUINT_DT_F32 0
+#define SQUINT_DT_F64 1
+#define SQUINT_DT_BF16 2   /* BF16 operands, FP32 accumulation and output (tensor cores) */
+
+/*
+ * C[m, n] (+)= sum_k A(m, k) B(n, k) + bias[n] for m < M, n < N.
+ * A(m, k) = A[m * sa_m + k * sa_k], B(n, k) = B[n * sb_n + k * sb_k];
+ * C[m * ldc + n].  F32/F64: A, B, C, bias of that type, any strides.
+ * BF16: A and B BF16 with one unit stride each (sa_k == 1: K-major, sa_m == 1:
+ * M-major; likewise for B), 16-byte aligned, the other stride a multiple of 8;
+ * C and bias FP32.  This is the dense contraction of every linear layer (Sec. III:
+ * critic and actor networks): forward X W^T, data gradient dY W, weight gradient dY^T X.
+ */
+int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, int64_t sa_k, const void* B,
+                   int64_t sb_n, int64_t sb_k, void* C, int64_t ldc, const void* bias, int accumulate, void* stream);
+
+/*
+ * Valid 3x3 convolution, NCHW (the encoder layers, Sec. III "single shared CNN
+ * encoder"): y[i,o,p,q] = b[o] + sum_{c,u,v} w[o,c,u,v] x[i,c,s p+u,s q+v], ReLU if relu.
+ * x [nimg, cin, h, w], w [cout, cin, 3, 3], y [nimg, cout, oh, ow], oh = (h-3)/s+1.
+ */
+int squint_op_conv3x3_fwd(int dtype, int nimg, int cin, int h, int w, int cout, int stride, const void* x,
+                          const void* wt, const void* b, void* y, int relu, void* stream);
+/* Workspace (bytes) the backward below needs for these shapes. */
+size_t squint_op_conv3x3_workspace(int dtype, int nimg, int cin, int h, int w, int cout, int stride);
+/*
+ * Backward of the convolution given dy at its pre-activation: dw, db (always) and
+ * dx (if non-NULL; zeroed where dx_mask <= 0 when dx_mask is given).
+ */
+int squint_op_conv3x3_bwd(int dtype, int nimg, int cin, int h, int w, int cout, int stride, const void* x,
+                          const void* wt, const void* dy, void* dx, const void* dx_mask, void* dw, void* db,
+                          void* workspace, size_t workspace_bytes, void* stream);
+
+/* LayerNorm over rows of n (Sec. IV "Normalization"), FP32: y = g (x - mean) rstd + b, ReLU if relu. */
+int squint_op_layernorm_fwd(int rows, int n, const float* x, const float* g, const float* b, float eps, int relu,
+                            float* y, float* mean, float* rstd, void* stream);
+/* Backward: dy w.r.t. the output (masked by y > 0 when y is given, i.e. after ReLU). */
+int squint_op_layernorm_bwd(int rows, int n, const float* dy, const float* y, const float* x, const float* mean,
+                            const float* rstd, const float* g, float* dx, float* dg, float* db, void* stream);
+
+/*
+ * Categorical cross entropy against a target distribution m (C51 critic loss,
+ * Sec. IV "Critic Design Choices"): row_loss[r] = -sum_j m[r,j] log softmax(l[r])_j,
+ * dlogits = (softmax(l) - m) * scale, row_q[r] = sum_j softmax(l[r])_j z_j with
+ * z_j = v_min + j (v_max - v_min)/(K-1).
+ */
+int squint_op_categorical_ce(int rows, int K, const float* logits, const float* m, float v_min, float v_max,
+                             float scale, float* dlogits, float* row_loss, float* row_q, void* stream);
+
+/*
+ * C51 target (Alg. 1 "Compute target Q-value", distributional form): the E target
+ * critics' softmax distributions averaged, the support shifted to
+ * clip(r + gamma (1-d)(z_j - alpha logp), v_min, v_max) and projected linearly
+ * onto the atoms.  logits [E, rows, K]; r, d, logp [rows]; m [rows, K].
+ */
+int squint_op_c51_project(int rows, int K, int E, const float* logits, const float* r, const float* d,
+                          const float* logp, float alpha, float gamma, float v_min, float v_max, float* m,
+                          void* stream);
+
+/*
+ * Tanh-Gaussian policy head (SAC, Sec. III) with given noise eps [rows, A]:
+ * out [rows, 2A] = (mu, raw); log_std = lo + (hi-lo)(tanh(raw)+1)/2;
+ * a = tanh(mu + exp(log_std) eps); logp = log density of a.
+ */
+int squint_op_tanh_gaussian_fwd(int rows, int A, const float* out, const float* eps, float lo, float hi, float* a,
+                                float* logp, void* stream);
+/* Backward with eps held fixed: dout from da [rows, A] and dlogp [rows]. */
+int squint_op_tanh_gaussian_bwd(int rows, int A, const float* out, const float* eps, const float* da,
+                                const float* dlogp, float lo, float hi, float* dout, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SQUINT_OPS_H */

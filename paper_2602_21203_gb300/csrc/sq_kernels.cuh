@@ -128,6 +128,7 @@ struct ActorHeadArgs {
     float* a_dst1; int64_t ld1;     // actions of rows >= B
     float* logp;                    // [rows]
     float* eps;                     // [rows, A] saved noise
+    const float* eps_in;            // optional: noise given instead of drawn
 };
 void launch_actor_head(const ActorHeadArgs& a, cudaStream_t s);
 
@@ -139,7 +140,8 @@ struct ActorHeadBwdArgs {
     const float* log_alpha;               // dL/dlogp = exp(log_alpha)/B
     float lo, hi;
     float* dout;                          // [B, 2A]
-    const int32_t* do_actor;
+    const int32_t* do_actor;              // null: always run
+    const float* dlogp_rows;              // optional per-row dL/dlogp instead of exp(log_alpha)/B
 };
 void launch_actor_head_bwd(const ActorHeadBwdArgs& a, cudaStream_t s);
 
@@ -147,7 +149,8 @@ struct C51TargetArgs {
     int B, K, E;
     const float* logits_bar;   // [E, B, K]
     const float* r; const float* d; const float* logp_next;
-    const float* log_alpha;    // alpha = exp(*log_alpha)
+    const float* log_alpha;    // alpha = exp(*log_alpha); null: alpha_value
+    float alpha_value;
     float gamma, v_min, v_max;
     float* m;                  // [B, K]
 };
@@ -158,7 +161,8 @@ struct CeArgs {
     const float* logits;       // [E, B, K]
     const float* m;            // [B, K]
     float v_min, v_max;
-    float* dlogits;            // [E, B, K] = (softmax - m)/B
+    float scale;               // dlogits = (softmax - m) * scale
+    float* dlogits;            // [E, B, K]
     float* row_loss;           // [E*B]
     float* row_q;              // [E*B]
 };

@@ -424,6 +424,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         CeArgs ce{};
         ce.B = B; ce.K = K; ce.E = E; ce.logits = crit_mlp.out; ce.m = m;
         ce.v_min = (float)c.v_min; ce.v_max = (float)c.v_max;
+        ce.scale = 1.0f / (float)B;
         ce.dlogits = dlogits; ce.row_loss = row_loss; ce.row_q = row_q;
         launch_ce(ce, s);
     }

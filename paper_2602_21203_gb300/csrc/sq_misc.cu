@@ -154,7 +154,7 @@ __global__ void c51_target_kernel(C51TargetArgs a) {
     __shared__ float bpos[kMaxAtoms];
     __shared__ float red[32];
     const int row = blockIdx.x;
-    const float alpha = expf(*a.log_alpha);
+    const float alpha = a.log_alpha ? expf(*a.log_alpha) : a.alpha_value;
     const float dz = (a.v_max - a.v_min) / (float)(a.K - 1);
     for (int j = threadIdx.x; j < a.K; j += blockDim.x) pbar[j] = 0.f;
     for (int e = 0; e < a.E; ++e) {
@@ -205,7 +205,7 @@ __global__ void ce_kernel(CeArgs a) {
         const float p = expf(ls);
         loss -= m[j] * ls;
         q += p * (a.v_min + (float)j * dz);
-        a.dlogits[(int64_t)er * a.K + j] = (p - m[j]) / (float)a.B;
+        a.dlogits[(int64_t)er * a.K + j] = (p - m[j]) * a.scale;
     }
     loss = block_sum(loss, red);
     q = block_sum(q, red);
@@ -249,18 +249,19 @@ __global__ void actor_head_kernel(ActorHeadArgs a) {
     if (row >= a.rows) return;
     const bool tgt = row < a.B;
     const int el = tgt ? row : row - a.B;
-    const uint64_t u = (uint64_t)*a.update_idx;
+    const uint64_t u = a.update_idx ? (uint64_t)*a.update_idx : 0;
     const float* o = a.out + (int64_t)row * a.ld_out;
     float lp = 0.f;
     for (int k = 0; k < a.A; ++k) {
-        const float eps = normal_draw(a.seed, (uint32_t)el, tgt ? kStreamEpsTarget : kStreamEpsActor, u, k);
+        const float eps = a.eps_in ? a.eps_in[(int64_t)row * a.A + k]
+                                   : normal_draw(a.seed, (uint32_t)el, tgt ? kStreamEpsTarget : kStreamEpsActor, u, k);
         const float mu = o[k], raw = o[a.A + k];
         const float ls = a.lo + 0.5f * (a.hi - a.lo) * (tanhf(raw) + 1.0f);
         const float sd = expf(ls);
         const float uu = mu + sd * eps;
         const float act = tanhf(uu);
         lp += -0.5f * eps * eps - ls - 0.91893853320467274f - 2.0f * (0.69314718055994531f - uu - softplusf(-2.0f * uu));
-        a.eps[(int64_t)row * a.A + k] = eps;
+        if (a.eps) a.eps[(int64_t)row * a.A + k] = eps;
         if (tgt) a.a_dst0[(int64_t)row * a.ld0 + k] = act;
         else a.a_dst1[(int64_t)el * a.ld1 + k] = act;
     }
@@ -270,10 +271,10 @@ __global__ void actor_head_kernel(ActorHeadArgs a) {
 // Reparameterised backward: du = da (1 - a^2) + dlogp 2a; dlog_std = du std eps - dlogp;
 // draw = dlog_std (hi-lo)/2 (1 - tanh(raw)^2).
 __global__ void actor_head_bwd_kernel(ActorHeadBwdArgs a) {
-    if (!*a.do_actor) return;
+    if (a.do_actor && !*a.do_actor) return;
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= a.B) return;
-    const float dlogp = expf(*a.log_alpha) / (float)a.B;
+    const float dlogp = a.dlogp_rows ? a.dlogp_rows[row] : expf(*a.log_alpha) / (float)a.B;
     const float* o = a.out + (int64_t)row * a.ld_out;
     for (int k = 0; k < a.A; ++k) {
         const float eps = a.eps[(int64_t)row * a.A + k];

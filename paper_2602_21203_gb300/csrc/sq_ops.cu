@@ -1,0 +1,195 @@
+// Layer operations (include/squint_ops.h): the update's kernels on caller buffers.
+#include "squint.h"
+#include "squint_ops.h"
+#include "sq_kernels.cuh"
+#include "sq_tc.cuh"
+
+#include <mutex>
+
+using namespace sq;
+
+namespace {
+
+int launch_status() { return cudaGetLastError() == cudaSuccess ? SQUINT_OK : SQUINT_ECUDA; }
+
+int* tc_error_flag() {
+    static int* flag = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        if (cudaMalloc(&flag, sizeof(int)) == cudaSuccess) cudaMemset(flag, 0, sizeof(int));
+        tc_prepare();
+    });
+    return flag;
+}
+
+ConvShape conv_shape(int nimg, int cin, int h, int w, int cout, int stride) {
+    ConvShape sh{};
+    sh.nimg = nimg; sh.Cin = cin; sh.H = h; sh.W = w; sh.Cout = cout; sh.stride = stride;
+    sh.OH = (h - 3) / stride + 1;
+    sh.OW = (w - 3) / stride + 1;
+    sh.x_img_stride = (int64_t)cin * h * w;
+    sh.y_img_stride = (int64_t)cout * sh.OH * sh.OW;
+    return sh;
+}
+
+bool conv_ok(int nimg, int cin, int h, int w, int cout, int stride) {
+    return nimg >= 0 && cin > 0 && cout > 0 && h >= 3 && w >= 3 && stride >= 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, int64_t sa_k, const void* B,
+                   int64_t sb_n, int64_t sb_k, void* C, int64_t ldc, const void* bias, int accumulate,
+                   void* stream) {
+    if (M < 0 || N < 0 || K < 1 || !A || !B || !C) return SQUINT_EINVAL;
+    if (M == 0 || N == 0) return SQUINT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == SQUINT_DT_F32 || dtype == SQUINT_DT_F64) {
+        GemmProblem p{};
+        p.M = M; p.N = N; p.K = K;
+        p.A = A; p.sa_m = sa_m; p.sa_k = sa_k;
+        p.B = B; p.sb_n = sb_n; p.sb_k = sb_k;
+        p.C = C; p.sc_m = ldc; p.sc_n = 1;
+        p.bias = bias; p.accumulate = accumulate; p.n_sum = 1;
+        GemmLayout lay = kKK;
+        if (sa_k == 1 && sb_k != 1) lay = kKN;
+        else if (sa_k != 1 && sb_k != 1) lay = kMN;
+        if (dtype == SQUINT_DT_F32) launch_gemm<float>(&p, 1, lay, s);
+        else launch_gemm<double>(&p, 1, lay, s);
+        return launch_status();
+    }
+    if (dtype != SQUINT_DT_BF16) return SQUINT_EINVAL;
+    TcGemm g{};
+    g.M = M; g.N = N; g.K = K; g.n_pairs = 1;
+    if (sa_k == 1) g.a[0] = TcOperand{(const __nv_bfloat16*)A, sa_m, false};
+    else if (sa_m == 1) g.a[0] = TcOperand{(const __nv_bfloat16*)A, sa_k, true};
+    else return SQUINT_EINVAL;
+    if (sb_k == 1) g.b[0] = TcOperand{(const __nv_bfloat16*)B, sb_n, false};
+    else if (sb_n == 1) g.b[0] = TcOperand{(const __nv_bfloat16*)B, sb_k, true};
+    else return SQUINT_EINVAL;
+    g.bias = (const float*)bias;
+    g.c = (float*)C; g.ldc = ldc;
+    g.accumulate = accumulate;
+    int* err = tc_error_flag();
+    if (!err) return SQUINT_ECUDA;
+    if (launch_tc_gemm(&g, 1, err, s) != 0) return SQUINT_EINVAL;
+    return launch_status();
+}
+
+int squint_op_conv3x3_fwd(int dtype, int nimg, int cin, int h, int w, int cout, int stride, const void* x,
+                          const void* wt, const void* b, void* y, int relu, void* stream) {
+    if (!conv_ok(nimg, cin, h, w, cout, stride) || !x || !wt || !b || !y) return SQUINT_EINVAL;
+    ConvShape sh = conv_shape(nimg, cin, h, w, cout, stride);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == SQUINT_DT_F32)
+        launch_conv_fwd<float>(sh, (const float*)x, (const float*)wt, (const float*)b, (float*)y, relu != 0, s);
+    else if (dtype == SQUINT_DT_F64)
+        launch_conv_fwd<double>(sh, (const double*)x, (const double*)wt, (const double*)b, (double*)y, relu != 0, s);
+    else
+        return SQUINT_EINVAL;
+    return launch_status();
+}
+
+size_t squint_op_conv3x3_workspace(int dtype, int nimg, int cin, int h, int w, int cout, int stride) {
+    if (!conv_ok(nimg, cin, h, w, cout, stride)) return 0;
+    const size_t el = dtype == SQUINT_DT_F64 ? 8 : 4;
+    return el * (size_t)conv_wgrad_workspace(conv_shape(nimg, cin, h, w, cout, stride));
+}
+
+int squint_op_conv3x3_bwd(int dtype, int nimg, int cin, int h, int w, int cout, int stride, const void* x,
+                          const void* wt, const void* dy, void* dx, const void* dx_mask, void* dw, void* db,
+                          void* workspace, size_t workspace_bytes, void* stream) {
+    if (!conv_ok(nimg, cin, h, w, cout, stride) || !x || !wt || !dy || !dw || !db) return SQUINT_EINVAL;
+    if (workspace_bytes < squint_op_conv3x3_workspace(dtype, nimg, cin, h, w, cout, stride) || !workspace)
+        return SQUINT_EINVAL;
+    ConvShape sh = conv_shape(nimg, cin, h, w, cout, stride);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == SQUINT_DT_F32) {
+        launch_conv_wgrad<float>(sh, (const float*)dy, (const float*)x, (float*)dw, (float*)db, (float*)workspace, s);
+        if (dx) launch_conv_dgrad<float>(sh, (const float*)dy, (const float*)wt, (float*)dx, (const float*)dx_mask, s);
+    } else if (dtype == SQUINT_DT_F64) {
+        launch_conv_wgrad<double>(sh, (const double*)dy, (const double*)x, (double*)dw, (double*)db,
+                                  (double*)workspace, s);
+        if (dx)
+            launch_conv_dgrad<double>(sh, (const double*)dy, (const double*)wt, (double*)dx, (const double*)dx_mask, s);
+    } else {
+        return SQUINT_EINVAL;
+    }
+    return launch_status();
+}
+
+int squint_op_layernorm_fwd(int rows, int n, const float* x, const float* g, const float* b, float eps, int relu,
+                            float* y, float* mean, float* rstd, void* stream) {
+    if (rows < 0 || n < 1 || !x || !g || !b || !y || !mean || !rstd) return SQUINT_EINVAL;
+    LnProblem p{};
+    p.rows = rows; p.n = n; p.pre = x; p.ld_pre = n; p.g = g; p.beta = b;
+    p.out = y; p.ld_out = n; p.mean = mean; p.rstd = rstd;
+    launch_ln_fwd(&p, 1, relu != 0, eps, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int squint_op_layernorm_bwd(int rows, int n, const float* dy, const float* y, const float* x, const float* mean,
+                            const float* rstd, const float* g, float* dx, float* dg, float* db, void* stream) {
+    if (rows < 0 || n < 1 || !dy || !x || !mean || !rstd || !g || !dx) return SQUINT_EINVAL;
+    LnBwdProblem p{};
+    p.rows = rows; p.n = n;
+    p.dout = dy; p.ld_dout = n; p.out = y; p.ld_out = n; p.pre = x; p.ld_pre = n;
+    p.mean = mean; p.rstd = rstd; p.g = g; p.dpre = dx; p.ld_dpre = n;
+    p.dg = dg; p.dbeta = db;
+    launch_ln_bwd(&p, 1, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int squint_op_categorical_ce(int rows, int K, const float* logits, const float* m, float v_min, float v_max,
+                             float scale, float* dlogits, float* row_loss, float* row_q, void* stream) {
+    if (rows < 0 || K < 2 || K > 256 || !logits || !m || !dlogits || !row_loss || !row_q) return SQUINT_EINVAL;
+    if (rows == 0) return SQUINT_OK;
+    CeArgs a{};
+    a.B = rows; a.K = K; a.E = 1; a.logits = logits; a.m = m; a.v_min = v_min; a.v_max = v_max;
+    a.scale = scale; a.dlogits = dlogits; a.row_loss = row_loss; a.row_q = row_q;
+    launch_ce(a, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int squint_op_c51_project(int rows, int K, int E, const float* logits, const float* r, const float* d,
+                          const float* logp, float alpha, float gamma, float v_min, float v_max, float* m,
+                          void* stream) {
+    if (rows < 0 || K < 2 || K > 256 || E < 1 || !logits || !r || !d || !logp || !m || !(v_max > v_min))
+        return SQUINT_EINVAL;
+    if (rows == 0) return SQUINT_OK;
+    C51TargetArgs a{};
+    a.B = rows; a.K = K; a.E = E; a.logits_bar = logits; a.r = r; a.d = d; a.logp_next = logp;
+    a.log_alpha = nullptr; a.alpha_value = alpha; a.gamma = gamma; a.v_min = v_min; a.v_max = v_max; a.m = m;
+    launch_c51_target(a, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int squint_op_tanh_gaussian_fwd(int rows, int A, const float* out, const float* eps, float lo, float hi, float* a,
+                                float* logp, void* stream) {
+    if (rows < 0 || A < 1 || !out || !eps || !a || !logp) return SQUINT_EINVAL;
+    if (rows == 0) return SQUINT_OK;
+    // rows are treated as the "actor" half (rows >= B), so actions land in a_dst1 with ld A
+    ActorHeadArgs h{};
+    h.rows = rows; h.B = 0; h.A = A; h.out = out; h.ld_out = 2 * A; h.lo = lo; h.hi = hi;
+    h.a_dst1 = a; h.ld1 = A; h.a_dst0 = a; h.ld0 = A;
+    h.logp = logp;
+    h.eps = nullptr;
+    h.eps_in = eps;
+    launch_actor_head(h, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int squint_op_tanh_gaussian_bwd(int rows, int A, const float* out, const float* eps, const float* da,
+                                const float* dlogp, float lo, float hi, float* dout, void* stream) {
+    if (rows < 0 || A < 1 || !out || !eps || !da || !dlogp || !dout) return SQUINT_EINVAL;
+    if (rows == 0) return SQUINT_OK;
+    ActorHeadBwdArgs h{};
+    h.B = rows; h.A = A; h.out = out; h.ld_out = 2 * A; h.eps = eps; h.da = da;
+    h.lo = lo; h.hi = hi; h.dout = dout; h.dlogp_rows = dlogp;
+    launch_actor_head_bwd(h, (cudaStream_t)stream);
+    return launch_status();
+}
+
+}  // extern "C"

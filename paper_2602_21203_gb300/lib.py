@@ -96,6 +96,17 @@ def load():
         "squint_graph_kernel_count": (I64, [P, I]),
         "squint_profile_update": (I, [P, P, I, ctypes.POINTER(I), P]),
         "squint_phase_name": (ctypes.c_char_p, [I]),
+        "squint_op_gemm": (I, [I, I, I, I, P, I64, I64, P, I64, I64, P, I64, P, I, P]),
+        "squint_op_conv3x3_fwd": (I, [I, I, I, I, I, I, I, P, P, P, P, I, P]),
+        "squint_op_conv3x3_workspace": (SZ, [I, I, I, I, I, I, I]),
+        "squint_op_conv3x3_bwd": (I, [I, I, I, I, I, I, I, P, P, P, P, P, P, P, P, SZ, P]),
+        "squint_op_layernorm_fwd": (I, [I, I, P, P, P, ctypes.c_float, I, P, P, P, P]),
+        "squint_op_layernorm_bwd": (I, [I, I, P, P, P, P, P, P, P, P, P, P]),
+        "squint_op_categorical_ce": (I, [I, I, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float, P, P, P, P]),
+        "squint_op_c51_project": (I, [I, I, I, P, P, P, P, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_float, P, P]),
+        "squint_op_tanh_gaussian_fwd": (I, [I, I, P, P, ctypes.c_float, ctypes.c_float, P, P, P]),
+        "squint_op_tanh_gaussian_bwd": (I, [I, I, P, P, P, P, ctypes.c_float, ctypes.c_float, P, P]),
         "squint_strerror": (ctypes.c_char_p, [I]),
         "squint_last_error": (ctypes.c_char_p, []),
     }

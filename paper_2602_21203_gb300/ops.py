@@ -1,0 +1,131 @@
+"""Layer operations of include/squint_ops.h on torch CUDA tensors (marshalling only).
+
+Each call launches the library's kernel on the current torch stream.  There is
+no fallback: tensors must be CUDA tensors of the stated dtype and layout.
+"""
+import ctypes
+
+import torch
+
+from . import lib as _lib
+
+DT_F32, DT_F64, DT_BF16 = 0, 1, 2
+_DT = {torch.float32: DT_F32, torch.float64: DT_F64, torch.bfloat16: DT_BF16}
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _s():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _chk(rc, what):
+    if rc != 0:
+        raise _lib.SquintError(rc, what)
+
+
+def _need(t, dtype, name):
+    if not t.is_cuda or t.dtype != dtype:
+        raise TypeError(f"{name}: expected a CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+
+
+def gemm(A, B, bias=None, out=None, accumulate=False, M=None, N=None, K=None):
+    """out[m, n] (+)= sum_k A(m, k) B(n, k) + bias; A, B 2-D views given as (rows = m|n, cols = k) with any strides.
+
+    For BF16 operands each of A, B must have one unit stride; out and bias are FP32.
+    """
+    M = A.shape[0] if M is None else M
+    K = A.shape[1] if K is None else K
+    N = B.shape[0] if N is None else N
+    dt = _DT[A.dtype]
+    odt = torch.float32 if dt == DT_BF16 else A.dtype
+    if out is None:
+        out = torch.zeros(M, N, device=A.device, dtype=odt)
+    _need(out, odt, "out")
+    if bias is not None:
+        _need(bias, odt, "bias")
+    _chk(_lib.load().squint_op_gemm(dt, M, N, K, _p(A), A.stride(0), A.stride(1), _p(B), B.stride(0), B.stride(1),
+                                    _p(out), out.stride(0), _p(bias), int(accumulate), _s()), "squint_op_gemm")
+    return out
+
+
+def conv3x3_fwd(x, w, b, stride, relu):
+    n, cin, h, wd = x.shape
+    cout = w.shape[0]
+    oh, ow = (h - 3) // stride + 1, (wd - 3) // stride + 1
+    y = torch.empty(n, cout, oh, ow, device=x.device, dtype=x.dtype)
+    _chk(_lib.load().squint_op_conv3x3_fwd(_DT[x.dtype], n, cin, h, wd, cout, stride, _p(x), _p(w), _p(b), _p(y),
+                                           int(relu), _s()), "squint_op_conv3x3_fwd")
+    return y
+
+
+def conv3x3_bwd(x, w, dy, stride, need_dx=True, dx_mask=None):
+    n, cin, h, wd = x.shape
+    cout = w.shape[0]
+    L = _lib.load()
+    dt = _DT[x.dtype]
+    ws = L.squint_op_conv3x3_workspace(dt, n, cin, h, wd, cout, stride)
+    work = torch.empty(max(ws, 16), dtype=torch.uint8, device=x.device)
+    dw = torch.empty_like(w)
+    db = torch.empty(cout, device=x.device, dtype=x.dtype)
+    dx = torch.empty_like(x) if need_dx else None
+    _chk(L.squint_op_conv3x3_bwd(dt, n, cin, h, wd, cout, stride, _p(x), _p(w), _p(dy), _p(dx), _p(dx_mask), _p(dw),
+                                 _p(db), _p(work), work.numel(), _s()), "squint_op_conv3x3_bwd")
+    return dx, dw, db
+
+
+def layernorm_fwd(x, g, b, eps=1e-5, relu=False):
+    rows, n = x.shape
+    y = torch.empty_like(x)
+    mean = torch.empty(rows, device=x.device, dtype=torch.float32)
+    rstd = torch.empty_like(mean)
+    _chk(_lib.load().squint_op_layernorm_fwd(rows, n, _p(x), _p(g), _p(b), float(eps), int(relu), _p(y), _p(mean),
+                                             _p(rstd), _s()), "squint_op_layernorm_fwd")
+    return y, mean, rstd
+
+
+def layernorm_bwd(dy, y, x, mean, rstd, g, relu=False):
+    rows, n = x.shape
+    dx = torch.empty_like(x)
+    dg = torch.empty_like(g)
+    db = torch.empty_like(g)
+    _chk(_lib.load().squint_op_layernorm_bwd(rows, n, _p(dy), _p(y) if relu else None, _p(x), _p(mean), _p(rstd),
+                                             _p(g), _p(dx), _p(dg), _p(db), _s()), "squint_op_layernorm_bwd")
+    return dx, dg, db
+
+
+def categorical_ce(logits, m, v_min, v_max, scale):
+    rows, K = logits.shape
+    d = torch.empty_like(logits)
+    loss = torch.empty(rows, device=logits.device, dtype=torch.float32)
+    q = torch.empty_like(loss)
+    _chk(_lib.load().squint_op_categorical_ce(rows, K, _p(logits), _p(m), float(v_min), float(v_max), float(scale),
+                                              _p(d), _p(loss), _p(q), _s()), "squint_op_categorical_ce")
+    return loss, d, q
+
+
+def c51_project(logits, r, d, logp, alpha, gamma, v_min, v_max):
+    E, rows, K = logits.shape
+    m = torch.empty(rows, K, device=logits.device, dtype=torch.float32)
+    _chk(_lib.load().squint_op_c51_project(rows, K, E, _p(logits), _p(r), _p(d), _p(logp), float(alpha), float(gamma),
+                                           float(v_min), float(v_max), _p(m), _s()), "squint_op_c51_project")
+    return m
+
+
+def tanh_gaussian_fwd(out, eps, lo=-5.0, hi=2.0):
+    rows, A = eps.shape
+    a = torch.empty_like(eps)
+    logp = torch.empty(rows, device=out.device, dtype=torch.float32)
+    _chk(_lib.load().squint_op_tanh_gaussian_fwd(rows, A, _p(out), _p(eps), float(lo), float(hi), _p(a), _p(logp),
+                                                 _s()), "squint_op_tanh_gaussian_fwd")
+    return a, logp
+
+
+def tanh_gaussian_bwd(out, eps, da, dlogp, lo=-5.0, hi=2.0):
+    rows, A = eps.shape
+    dout = torch.empty_like(out)
+    _chk(_lib.load().squint_op_tanh_gaussian_bwd(rows, A, _p(out), _p(eps), _p(da), _p(dlogp), float(lo), float(hi),
+                                                 _p(dout), _s()), "squint_op_tanh_gaussian_bwd")
+    return dout

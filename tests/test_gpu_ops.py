@@ -1,0 +1,175 @@
+"""Layer operations (include/squint_ops.h) vs the FP64 oracle's layers (needs a GB300).
+
+The BF16 tensor-core GEMM is checked against the FP64 product of the same
+BF16-rounded operands (only the FP32 accumulation order differs): relative
+error in norm <= 1e-5.  FP64 layer kernels match the oracle to 1e-12, FP32 ones
+to 1e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import squint_sac as o
+from paper_2602_21203_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ops():
+    from paper_2602_21203_gb300 import ops
+    return ops
+
+
+def _rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _operand(rows, cols, mn_major, g):
+    """A (rows x cols) BF16 operand; mn_major stores it transposed (rows contiguous) with a padded stride."""
+    x = torch.randn(rows, cols, generator=g).to(torch.bfloat16)
+    if not mn_major:
+        ld = (cols + 7) // 8 * 8
+        buf = torch.zeros(rows, ld, dtype=torch.bfloat16)
+        buf[:, :cols] = x
+        return x, buf.cuda()[:, :cols]
+    ld = (rows + 7) // 8 * 8
+    buf = torch.zeros(cols, ld, dtype=torch.bfloat16)
+    buf[:, :rows] = x.t()
+    return x, buf.cuda()[:, :rows].t()
+
+
+SHAPES = [(512, 512, 512), (300, 101, 274), (128, 12, 512), (1024, 256, 2592), (7, 16, 64), (256, 200, 512),
+          (1, 1, 8)]
+
+
+@pytest.mark.parametrize("a_mn", [False, True])
+@pytest.mark.parametrize("b_mn", [False, True])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_bf16_tensor_core_gemm(ops, a_mn, b_mn, shape):
+    M, N, K = shape
+    g = torch.Generator().manual_seed(M * 7 + N * 3 + K)
+    a, A = _operand(M, K, a_mn, g)
+    b, B = _operand(N, K, b_mn, g)
+    bias = torch.randn(N, generator=g)
+    out = ops.gemm(A, B, bias=bias.cuda(), M=M, N=N, K=K)
+    torch.cuda.synchronize()
+    ref = a.double().numpy() @ b.double().numpy().T + bias.double().numpy()
+    assert _rel(out.cpu().numpy(), ref) < 1e-5, (shape, a_mn, b_mn)
+
+
+def test_bf16_gemm_accumulates(ops):
+    g = torch.Generator().manual_seed(3)
+    a, A = _operand(256, 128, False, g)
+    b, B = _operand(128, 128, True, g)
+    base = torch.randn(256, 128, generator=g)
+    out = base.clone().cuda()
+    ops.gemm(A, B, out=out, accumulate=True)
+    torch.cuda.synchronize()
+    ref = base.double().numpy() + a.double().numpy() @ b.double().numpy().T
+    assert _rel(out.cpu().numpy(), ref) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_cuda_core_gemm_layouts(ops, dtype):
+    g = torch.Generator().manual_seed(4)
+    for M, N, K in [(70, 33, 129), (512, 512, 512)]:
+        a = torch.randn(M, K, generator=g, dtype=torch.float64)
+        b = torch.randn(N, K, generator=g, dtype=torch.float64)
+        ref = a.numpy() @ b.numpy().T
+        for at in (False, True):
+            for bt in (False, True):
+                A = (a.t().contiguous().t() if at else a).to(dtype).cuda()
+                B = (b.t().contiguous().t() if bt else b).to(dtype).cuda()
+                out = ops.gemm(A, B)
+                torch.cuda.synchronize()
+                tol = 1e-12 if dtype == torch.float64 else 1e-5
+                assert _rel(out.cpu().numpy(), ref) < tol
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-6)])
+@pytest.mark.parametrize("stride", [1, 2])
+def test_conv3x3_matches_oracle(ops, dtype, tol, stride):
+    g = torch.Generator().manual_seed(5 + stride)
+    x = torch.randn(5, 3, 17, 15, generator=g, dtype=torch.float64)
+    w = torch.randn(8, 3, 3, 3, generator=g, dtype=torch.float64) * 0.3
+    b = torch.randn(8, generator=g, dtype=torch.float64)
+    y = ops.conv3x3_fwd(x.to(dtype).cuda(), w.to(dtype).cuda(), b.to(dtype).cuda(), stride, relu=False)
+    ref = o.conv3x3_fwd(x.numpy(), w.numpy(), b.numpy(), stride)
+    assert _rel(y.cpu().numpy(), ref) < tol
+    dy = torch.randn(*ref.shape, generator=g, dtype=torch.float64)
+    dx, dw, db = ops.conv3x3_bwd(x.to(dtype).cuda(), w.to(dtype).cuda(), dy.to(dtype).cuda(), stride)
+    rdx, rdw, rdb = o.conv3x3_bwd(x.numpy(), w.numpy(), dy.numpy(), stride)
+    assert _rel(dx.cpu().numpy(), rdx) < tol
+    assert _rel(dw.cpu().numpy(), rdw) < tol
+    assert _rel(db.cpu().numpy(), rdb) < tol
+
+
+@pytest.mark.parametrize("relu", [False, True])
+def test_layernorm_matches_oracle(ops, relu):
+    g = torch.Generator().manual_seed(6)
+    x = torch.randn(37, 300, generator=g, dtype=torch.float64) * 2 + 0.5
+    gam = torch.rand(300, generator=g, dtype=torch.float64) + 0.5
+    bet = torch.randn(300, generator=g, dtype=torch.float64)
+    y, mean, rstd = ops.layernorm_fwd(x.float().cuda(), gam.float().cuda(), bet.float().cuda(), 1e-5, relu)
+    ry, cache = o.layernorm_fwd(x.numpy(), gam.numpy(), bet.numpy(), 1e-5)
+    if relu:
+        ry = np.maximum(ry, 0)
+    assert _rel(y.cpu().numpy(), ry) < 1e-5
+    dy = torch.randn(37, 300, generator=g, dtype=torch.float64)
+    dx, dg, db = ops.layernorm_bwd(dy.float().cuda(), y, x.float().cuda(), mean, rstd, gam.float().cuda(), relu)
+    dyn = dy.numpy() * (ry > 0) if relu else dy.numpy()
+    rdx, rdg, rdb = o.layernorm_bwd(dyn, gam.numpy(), cache)
+    assert _rel(dx.cpu().numpy(), rdx) < 1e-4
+    assert _rel(dg.cpu().numpy(), rdg) < 1e-5
+    assert _rel(db.cpu().numpy(), rdb) < 1e-5
+
+
+def test_categorical_ce_matches_oracle(ops):
+    cfg = synth.make_config("train_b512")
+    g = torch.Generator().manual_seed(7)
+    logits = torch.randn(64, 101, generator=g, dtype=torch.float64) * 3
+    m = torch.rand(64, 101, generator=g, dtype=torch.float64)
+    m /= m.sum(1, keepdim=True)
+    loss, d, q = ops.categorical_ce(logits.float().cuda(), m.float().cuda(), -20, 20, 1 / 64)
+    lsm = o.log_softmax(logits.numpy())
+    assert _rel(loss.cpu().numpy(), -(m.numpy() * lsm).sum(1)) < 1e-5
+    assert _rel(d.cpu().numpy(), (np.exp(lsm) - m.numpy()) / 64) < 1e-5
+    assert _rel(q.cpu().numpy(), o.q_values(logits.numpy(), cfg)) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["tiny_b8", "small_b32", "train_b512"])
+def test_c51_projection_matches_oracle(ops, name):
+    cfg = synth.make_config(name)
+    K = cfg["atoms"]
+    g = torch.Generator().manual_seed(8)
+    rows = 40
+    logits = torch.randn(2, rows, K, generator=g, dtype=torch.float64) * 2
+    r = torch.randn(rows, generator=g, dtype=torch.float64) * 5
+    d = (torch.rand(rows, generator=g) < 0.3).double()
+    logp = torch.randn(rows, generator=g, dtype=torch.float64) * 3
+    m = ops.c51_project(logits.float().cuda(), r.float().cuda(), d.float().cuda(), logp.float().cuda(), 0.17,
+                        cfg["gamma"], cfg["v_min"], cfg["v_max"])
+    pbar = o.softmax(logits.numpy()).mean(0)
+    ref = o.project_c51(pbar, r.numpy(), d.numpy(), logp.numpy(), 0.17, cfg)
+    mm = m.cpu().numpy()
+    assert np.abs(mm - ref).max() < 2e-5
+    assert np.allclose(mm.sum(1), 1, atol=1e-5)
+
+
+def test_tanh_gaussian_matches_oracle(ops):
+    cfg = synth.make_config("train_b512")
+    g = torch.Generator().manual_seed(9)
+    out = torch.randn(50, 12, generator=g, dtype=torch.float64)
+    eps = torch.randn(50, 6, generator=g, dtype=torch.float64)
+    a, logp = ops.tanh_gaussian_fwd(out.float().cuda(), eps.float().cuda())
+    ra, rl, cache = o.tanh_gaussian(out.numpy(), eps.numpy(), cfg)
+    assert _rel(a.cpu().numpy(), ra) < 1e-5
+    assert np.abs(logp.cpu().numpy() - rl).max() < 1e-4
+    da = torch.randn(50, 6, generator=g, dtype=torch.float64)
+    dl = torch.randn(50, generator=g, dtype=torch.float64)
+    dout = ops.tanh_gaussian_bwd(out.float().cuda(), eps.float().cuda(), da.float().cuda(), dl.float().cuda())
+    ref = o.tanh_gaussian_bwd(da.numpy(), dl.numpy(), cache, cfg)
+    assert _rel(dout.cpu().numpy(), ref) < 1e-5
