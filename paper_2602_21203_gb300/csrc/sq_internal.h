@@ -3,6 +3,7 @@
 
 #include "squint.h"
 #include "sq_kernels.cuh"
+#include "sq_tc.cuh"
 
 #include <atomic>
 #include <condition_variable>
@@ -52,8 +53,12 @@ void init_params_host(const squint_config& c, const Layout& L, std::vector<float
 struct MlpBufs {
     int E = 0, rows = 0;
     std::vector<float*> pre, post, mean, rstd;   // per hidden layer: [E, rows, n]
+    std::vector<__nv_bfloat16*> posth;           // BF16 shadows of post (tensor-core path)
     float* out = nullptr;                        // [E, rows, n_out]
 };
+
+// BF16 padded copy of one linear layer's weight (online and, for the critic range, target).
+struct LinBf { __nv_bfloat16* on = nullptr; __nv_bfloat16* tg = nullptr; int64_t ld = 0; };
 
 struct ServeState;
 
@@ -65,7 +70,10 @@ struct squint_handle {
     squint_replay ring{};
     bool has_ring = false;
     bool failed = false;
+    bool bf16 = false;                // tensor-core contractions (SQUINT_PREC_BF16)
+    bool launch_failed = false;       // a tensor map could not describe an operand
     int device = 0;
+    int* d_err = nullptr;             // device error word of bounded waits
 
     // parameters and optimiser state
     float* params = nullptr;
@@ -115,8 +123,22 @@ struct squint_handle {
     float* dconv_a = nullptr;         // ping-pong conv gradients
     float* dconv_b = nullptr;
     float* wgrad_work = nullptr;
-    float* da = nullptr;              // [B, A]
+    float* dxq = nullptr;             // [B, Dc] input gradient of the critics in the actor step
     float* dout_a = nullptr;          // [B, 2A]
+
+    // BF16 shadows (tensor-core path)
+    std::map<int64_t, sq::LinBf> lin_bf;       // keyed by the canonical weight offset
+    std::vector<sq::CastItem> cast_critic, cast_actor, cast_target;
+    __nv_bfloat16* z_h = nullptr;              // [2B, F]
+    __nv_bfloat16* xa_h = nullptr;             // [2B, Da8]
+    __nv_bfloat16* xcbar_h = nullptr;          // [B, Dc8]
+    __nv_bfloat16* xc_h = nullptr;
+    __nv_bfloat16* xq_h = nullptr;
+    __nv_bfloat16* dlogits_h = nullptr;        // [E, B, K8]
+    __nv_bfloat16* dlogits_qh = nullptr;
+    std::vector<__nv_bfloat16*> dpre_h;        // per hidden layer [E, B, n]
+    __nv_bfloat16* dproj_h = nullptr;          // [B, D]
+    __nv_bfloat16* dout_ah = nullptr;          // [B, 16]
 
     // inference
     int act_cap = 0;

@@ -109,6 +109,7 @@ struct LnBwdProblem {
     const float* mean; const float* rstd;
     const float* g;
     float* dpre;       int64_t ld_dpre;    // gradient w.r.t. pre (written)
+    __nv_bfloat16* dpre_bf; int64_t ld_dpre_bf;  // optional BF16 copy of dpre
     float* dg; float* dbeta;               // column sums (written) or null
     float* dbias;                          // sum of dpre over rows (linear bias grad) or null
 };
@@ -136,10 +137,11 @@ struct ActorHeadBwdArgs {
     int B, A;
     const float* out; int64_t ld_out;     // forward head inputs of the B actor rows
     const float* eps;                     // [B, A]
-    const float* da;                      // [B, A] dL/da
+    const float* da; int64_t ld_da;       // dL/da rows (row stride ld_da; 0 means A)
     const float* log_alpha;               // dL/dlogp = exp(log_alpha)/B
     float lo, hi;
     float* dout;                          // [B, 2A]
+    __nv_bfloat16* dout_bf; int64_t ld_dout_bf;   // optional BF16 copy
     const int32_t* do_actor;              // null: always run
     const float* dlogp_rows;              // optional per-row dL/dlogp instead of exp(log_alpha)/B
 };
@@ -163,6 +165,7 @@ struct CeArgs {
     float v_min, v_max;
     float scale;               // dlogits = (softmax - m) * scale
     float* dlogits;            // [E, B, K]
+    __nv_bfloat16* dlogits_bf; int64_t ld_bf;   // optional BF16 copy [E, B, ld_bf]
     float* row_loss;           // [E*B]
     float* row_q;              // [E*B]
 };
@@ -173,6 +176,7 @@ struct ActorQArgs {
     const float* logits;       // [E, B, K] critics on (z_sg, s, a~)
     float v_min, v_max;
     float* dlogits;            // [E, B, K] = -(1/(E B)) p (z - Q)
+    __nv_bfloat16* dlogits_bf; int64_t ld_bf;   // optional BF16 copy [E, B, ld_bf]
     float* row_q;              // [E*B]
     const int32_t* do_actor;
 };

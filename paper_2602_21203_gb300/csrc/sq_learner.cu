@@ -13,14 +13,20 @@
 //   polyak (a16)           target critics <- (1-tau) target + tau critics
 // Every launch reads its scalars (update index, step counts, alpha, actor flag)
 // from device memory, so k updates are captured once as a graph and replayed.
-#include "sq_internal.h"
+//
+// Contractions go through GemmBuilder: CUDA-core FP32 kernels in the plain path,
+// tcgen05 BF16 kernels (FP32 accumulation) in the tensor-core path, where every
+// GEMM operand has a BF16 shadow written by the kernel that produces it.
+#include "sq_sched.h"
 
 #include <cmath>
 #include <cstring>
 
 using namespace sq;
 
-namespace {
+namespace sq {
+
+static int64_t pad8(int64_t n) { return (n + 7) / 8 * 8; }
 
 GemmProblem lin_fwd(const float* X, int64_t ldx, int rows, const float* W, const float* b, int in, int out, float* Y,
                     int64_t ldy) {
@@ -33,142 +39,229 @@ GemmProblem lin_fwd(const float* X, int64_t ldx, int rows, const float* W, const
     p.n_sum = 1;
     return p;
 }
-// dX[m, j] = sum_n dY[m, n] W[n, col0 + j], j < ncols
-GemmProblem lin_dx(const float* dY, int64_t ldd, int rows, const float* W, int in, int out, int col0, int ncols,
-                   float* dX, int64_t ldx) {
-    GemmProblem p{};
-    p.M = rows; p.N = ncols; p.K = out;
-    p.A = dY; p.sa_m = ldd; p.sa_k = 1;
-    p.B = W + col0; p.sb_n = 1; p.sb_k = in;
-    p.C = dX; p.sc_m = ldx; p.sc_n = 1;
-    p.n_sum = 1;
-    return p;
-}
-// dW[n, j] = sum_m dY[m, n] X[m, j]
-GemmProblem lin_dw(const float* dY, int64_t ldd, int rows, const float* X, int64_t ldx, int in, int out, float* dW) {
-    GemmProblem p{};
-    p.M = out; p.N = in; p.K = rows;
-    p.A = dY; p.sa_m = 1; p.sa_k = ldd;
-    p.B = X; p.sb_n = 1; p.sb_k = ldx;
-    p.C = dW; p.sc_m = in; p.sc_n = 1;
-    p.n_sum = 1;
-    return p;
+
+// ---------------------------------------------------------------- GemmBuilder
+void GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64_t ldy, __nv_bfloat16* Yh,
+                      int64_t ldyh) {
+    if (!bf_) {
+        fp_.push_back(lin_fwd(X.f, X.ld, rows, W.w, W.b, W.in, W.out, Y, ldy));
+        lay_ = kKK;
+        return;
+    }
+    TcGemm g{};
+    g.M = rows; g.N = W.out; g.K = W.in; g.n_pairs = 1;
+    g.a[0] = TcOperand{X.h, X.ldh, false};
+    g.b[0] = TcOperand{W.wh, W.ldh, false};
+    g.bias = W.b;
+    g.c = Y; g.ldc = ldy;
+    g.cbf = Yh; g.ldcbf = ldyh;
+    tc_.push_back(g);
 }
 
-// Parameter pointer of set e: online params, or the target copy of the critic range.
-struct PSet {
-    const float* base;   // params or target
-    int64_t shift;       // subtracted from canonical offsets
-    const float* at(int64_t off) const { return base + (off - shift); }
-};
+void GemmBuilder::dx(const Mat* dY, const LayerRef* W, int n_pairs, int rows, int col0, int ncols, float* dX,
+                     int64_t ldx, const float* mask, int64_t ldm) {
+    if (!bf_) {
+        GemmProblem p{};
+        p.M = rows; p.N = ncols; p.K = W[0].out;
+        p.A = dY[0].f; p.sa_m = dY[0].ld; p.sa_k = 1;
+        p.B = W[0].w + col0; p.sb_n = 1; p.sb_k = W[0].in;
+        p.C = dX; p.sc_m = ldx; p.sc_n = 1;
+        p.n_sum = n_pairs;
+        p.a_sum = n_pairs > 1 ? dY[1].f - dY[0].f : 0;
+        p.b_sum = n_pairs > 1 ? W[1].w - W[0].w : 0;
+        if (mask) { p.mask = mask; p.sm_m = ldm; p.sm_n = 1; }
+        fp_.push_back(p);
+        lay_ = kKN;
+        return;
+    }
+    TcGemm g{};
+    g.M = rows; g.N = ncols; g.K = W[0].out; g.n_pairs = n_pairs;
+    for (int q = 0; q < n_pairs; ++q) {
+        g.a[q] = TcOperand{dY[q].h, dY[q].ldh, false};
+        g.b[q] = TcOperand{W[q].wh + col0, W[q].ldh, true};
+    }
+    g.c = dX; g.ldc = ldx;
+    g.mask = mask; g.ldmask = ldm;
+    tc_.push_back(g);
+}
 
-void mlp_forward(MlpBufs& mb, const std::vector<Lin>* layers[], const PSet sets[], int E, const float* X, int64_t ldx,
-                 int rows, float ln_eps, cudaStream_t s) {
-    const int nh = (int)layers[0]->size() - 1;
-    GemmProblem g[2];
-    LnProblem lp[2];
+void GemmBuilder::dw(const Mat& dY, int rows, const Mat& X, const LayerRef& W, float* dW) {
+    if (!bf_) {
+        GemmProblem p{};
+        p.M = W.out; p.N = W.in; p.K = rows;
+        p.A = dY.f; p.sa_m = 1; p.sa_k = dY.ld;
+        p.B = X.f; p.sb_n = 1; p.sb_k = X.ld;
+        p.C = dW; p.sc_m = W.in; p.sc_n = 1;
+        p.n_sum = 1;
+        fp_.push_back(p);
+        lay_ = kMN;
+        return;
+    }
+    TcGemm g{};
+    g.M = W.out; g.N = W.in; g.K = rows; g.n_pairs = 1;
+    g.a[0] = TcOperand{dY.h, dY.ldh, true};
+    g.b[0] = TcOperand{X.h, X.ldh, true};
+    g.c = dW; g.ldc = W.in;
+    tc_.push_back(g);
+}
+
+void GemmBuilder::flush() {
+    if (!fp_.empty()) launch_gemm<float>(fp_.data(), (int)fp_.size(), lay_, s_);
+    if (!tc_.empty() && launch_tc_gemm(tc_.data(), (int)tc_.size(), h_->d_err, s_) != 0) h_->launch_failed = true;
+    fp_.clear();
+    tc_.clear();
+}
+
+// ---------------------------------------------------------------- parameter views
+LayerRef layer_ref(squint_handle* h, const Lin& ly, bool target, const float* base) {
+    auto P = [&](int64_t off) -> const float* {
+        if (off < 0) return nullptr;
+        if (target) return h->target + (off - h->L.critic_begin);
+        return (base ? base : h->params) + off;
+    };
+    LayerRef r;
+    r.w = P(ly.w); r.b = P(ly.b);
+    r.in = ly.in; r.out = ly.out;
+    if (ly.ln) { r.g = P(ly.g); r.beta = P(ly.beta); }
+    auto it = h->lin_bf.find(ly.w);
+    if (it != h->lin_bf.end() && !base) {
+        r.wh = target ? it->second.tg : it->second.on;
+        r.ldh = it->second.ld;
+    }
+    return r;
+}
+
+MlpRef mlp_ref(squint_handle* h, const std::vector<Lin>& layers, bool target, const float* base) {
+    MlpRef m;
+    for (const auto& l : layers) m.push_back(layer_ref(h, l, target, base));
+    return m;
+}
+
+void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const Mat& X, int rows, bool bf16,
+                 cudaStream_t s) {
+    const int nh = (int)sets[0].size() - 1;
     for (int l = 0; l <= nh; ++l) {
-        for (int e = 0; e < E; ++e) {
-            const Lin& ly = (*layers[e])[l];
-            const float* in = l == 0 ? X : mb.post[l - 1] + (int64_t)e * rows * ly.in;
-            const int64_t ldi = l == 0 ? ldx : ly.in;
-            float* y = l < nh ? mb.pre[l] + (int64_t)e * rows * ly.out : mb.out + (int64_t)e * rows * ly.out;
-            g[e] = lin_fwd(in, ldi, rows, sets[e].at(ly.w), sets[e].at(ly.b), ly.in, ly.out, y, ly.out);
+        {
+            GemmBuilder gb(h, s, bf16);
+            for (int e = 0; e < E; ++e) {
+                const LayerRef& ly = sets[e][l];
+                Mat in = X;
+                if (l > 0) {
+                    in.f = mb.post[l - 1] + (int64_t)e * rows * ly.in;
+                    in.ld = ly.in;
+                    in.h = mb.posth.empty() ? nullptr : mb.posth[l - 1] + (int64_t)e * rows * ly.in;
+                    in.ldh = ly.in;
+                }
+                float* y = l < nh ? mb.pre[l] + (int64_t)e * rows * ly.out : mb.out + (int64_t)e * rows * ly.out;
+                gb.fwd(in, rows, ly, y, ly.out);
+            }
         }
-        launch_gemm<float>(g, E, kKK, s);
         if (l == nh) break;
+        LnProblem lp[2];
         for (int e = 0; e < E; ++e) {
-            const Lin& ly = (*layers[e])[l];
+            const LayerRef& ly = sets[e][l];
             LnProblem p{};
             p.rows = rows; p.n = ly.out;
             p.pre = mb.pre[l] + (int64_t)e * rows * ly.out; p.ld_pre = ly.out;
-            p.g = sets[e].at(ly.g); p.beta = sets[e].at(ly.beta);
+            p.g = ly.g; p.beta = ly.beta;
             p.out = mb.post[l] + (int64_t)e * rows * ly.out; p.ld_out = ly.out;
+            if (bf16 && !mb.posth.empty()) { p.out_bf = mb.posth[l] + (int64_t)e * rows * ly.out; p.ld_out_bf = ly.out; }
             p.mean = mb.mean[l] + (int64_t)e * rows; p.rstd = mb.rstd[l] + (int64_t)e * rows;
             lp[e] = p;
         }
-        launch_ln_fwd(lp, E, true, ln_eps, s);
+        launch_ln_fwd(lp, E, true, (float)h->c.ln_eps, s);
     }
 }
 
-// Backward through an MLP evaluated by E parameter sets (all in `params`).
-// dout: [E, rows, n_out] (contiguous per set), rows offset `r0` into the stored activations.
-// grads: null for input-gradient only.  dX (optional) = sum over sets of the input
-// gradient restricted to columns [col0, col0 + ncols), masked by mask > 0 if given.
-void mlp_backward(const MlpBufs& mb, int r0, const std::vector<Lin>* layers[], const float* params, float* grads,
-                  int E, const float* X, int64_t ldx, int rows, const float* dout, std::vector<float*>& dpost,
-                  std::vector<float*>& dpre, int col0, int ncols, float* dX, int64_t lddx, const float* mask,
-                  int64_t ldmask, cudaStream_t s) {
-    const int nh = (int)layers[0]->size() - 1;
-    const int R = mb.rows;   // rows of the stored activations per set
-    GemmProblem g[4];
+}  // namespace sq
+
+namespace {
+
+// Backward through an MLP evaluated by E online parameter sets.  dout [E, rows, n_out]
+// (FP32 + BF16 shadow); activations stored with R rows per set, read from row r0.
+// Parameter gradients land at the canonical offsets of `grads` (null: input gradient
+// only).  dX (optional) = sum over sets of the input gradient, columns [0, ncols).
+void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* sets, float* grads, int E, const Mat& X,
+                  int rows, const Mat& dout, int ncols, float* dX, int64_t lddx, const float* mask, int64_t ldmask,
+                  cudaStream_t s) {
+    const bool bf = h->bf16;
+    const int nh = (int)sets[0].size() - 1;
+    const int R = mb.rows;
+    auto G = [&](const float* p) { return grads + (p - h->params); };
+    auto post = [&](int l, int e) {
+        const int n = sets[e][l].out;
+        Mat m;
+        m.f = mb.post[l] + ((int64_t)e * R + r0) * n; m.ld = n;
+        if (bf) { m.h = mb.posth[l] + ((int64_t)e * R + r0) * n; m.ldh = n; }
+        return m;
+    };
+    auto dpre = [&](int l, int e) {
+        const int n = sets[e][l].out;
+        Mat m;
+        m.f = h->dpre[l] + (int64_t)e * rows * n; m.ld = n;
+        if (bf) { m.h = h->dpre_h[l] + (int64_t)e * rows * n; m.ldh = n; }
+        return m;
+    };
+    auto dout_e = [&](int e) {
+        Mat m = dout;
+        m.f += (int64_t)e * rows * dout.ld;
+        if (m.h) m.h += (int64_t)e * rows * dout.ldh;
+        return m;
+    };
     // output layer
+    if (grads) {
+        GemmBuilder gb(h, s, bf);
+        for (int e = 0; e < E; ++e) gb.dw(dout_e(e), rows, post(nh - 1, e), sets[e][nh], G(sets[e][nh].w));
+    }
+    if (grads) {
+        ColSumProblem cs[2];
+        for (int e = 0; e < E; ++e)
+            cs[e] = ColSumProblem{rows, sets[e][nh].out, dout_e(e).f, dout.ld, G(sets[e][nh].b)};
+        launch_colsum(cs, E, s);
+    }
     {
-        int n = 0;
+        GemmBuilder gb(h, s, bf);
         for (int e = 0; e < E; ++e) {
-            const Lin& ly = (*layers[e])[nh];
-            const float* de = dout + (int64_t)e * rows * ly.out;
-            const float* h = mb.post[nh - 1] + ((int64_t)e * R + r0) * ly.in;
-            if (grads) g[n++] = lin_dw(de, ly.out, rows, h, ly.in, ly.in, ly.out, grads + ly.w);
+            const Mat d = dout_e(e);
+            gb.dx(&d, &sets[e][nh], 1, rows, 0, sets[e][nh].in, h->dpost[nh - 1] + (int64_t)e * rows * sets[e][nh].in,
+                  sets[e][nh].in);
         }
-        if (n) launch_gemm<float>(g, n, kMN, s);
-        if (grads) {
-            ColSumProblem cs[2];
-            for (int e = 0; e < E; ++e) {
-                const Lin& ly = (*layers[e])[nh];
-                cs[e] = ColSumProblem{rows, ly.out, dout + (int64_t)e * rows * ly.out, ly.out, grads + ly.b};
-            }
-            launch_colsum(cs, E, s);
-        }
-        for (int e = 0; e < E; ++e) {
-            const Lin& ly = (*layers[e])[nh];
-            g[e] = lin_dx(dout + (int64_t)e * rows * ly.out, ly.out, rows, params + ly.w, ly.in, ly.out, 0, ly.in,
-                          dpost[nh - 1] + (int64_t)e * rows * ly.in, ly.in);
-        }
-        launch_gemm<float>(g, E, kKN, s);
     }
     for (int l = nh - 1; l >= 0; --l) {
         LnBwdProblem lb[2];
         for (int e = 0; e < E; ++e) {
-            const Lin& ly = (*layers[e])[l];
+            const LayerRef& ly = sets[e][l];
             LnBwdProblem p{};
             p.rows = rows; p.n = ly.out;
-            p.dout = dpost[l] + (int64_t)e * rows * ly.out; p.ld_dout = ly.out;
-            p.out = mb.post[l] + ((int64_t)e * R + r0) * ly.out; p.ld_out = ly.out;
+            p.dout = h->dpost[l] + (int64_t)e * rows * ly.out; p.ld_dout = ly.out;
+            p.out = post(l, e).f; p.ld_out = ly.out;
             p.pre = mb.pre[l] + ((int64_t)e * R + r0) * ly.out; p.ld_pre = ly.out;
             p.mean = mb.mean[l] + (int64_t)e * R + r0; p.rstd = mb.rstd[l] + (int64_t)e * R + r0;
-            p.g = params + ly.g;
-            p.dpre = dpre[l] + (int64_t)e * rows * ly.out; p.ld_dpre = ly.out;
-            if (grads) { p.dg = grads + ly.g; p.dbeta = grads + ly.beta; p.dbias = grads + ly.b; }
+            p.g = ly.g;
+            p.dpre = dpre(l, e).f; p.ld_dpre = ly.out;
+            if (bf) { p.dpre_bf = dpre(l, e).h; p.ld_dpre_bf = ly.out; }
+            if (grads) { p.dg = G(ly.g); p.dbeta = G(ly.beta); p.dbias = G(ly.b); }
             lb[e] = p;
         }
         launch_ln_bwd(lb, E, s);
         if (grads) {
-            for (int e = 0; e < E; ++e) {
-                const Lin& ly = (*layers[e])[l];
-                const float* xin = l == 0 ? X : mb.post[l - 1] + ((int64_t)e * R + r0) * ly.in;
-                const int64_t ldi = l == 0 ? ldx : ly.in;
-                g[e] = lin_dw(dpre[l] + (int64_t)e * rows * ly.out, ly.out, rows, xin, ldi, ly.in, ly.out, grads + ly.w);
-            }
-            launch_gemm<float>(g, E, kMN, s);
+            GemmBuilder gb(h, s, bf);
+            for (int e = 0; e < E; ++e) gb.dw(dpre(l, e), rows, l == 0 ? X : post(l - 1, e), sets[e][l], G(sets[e][l].w));
         }
         if (l > 0) {
+            GemmBuilder gb(h, s, bf);
             for (int e = 0; e < E; ++e) {
-                const Lin& ly = (*layers[e])[l];
-                g[e] = lin_dx(dpre[l] + (int64_t)e * rows * ly.out, ly.out, rows, params + ly.w, ly.in, ly.out, 0, ly.in,
-                              dpost[l - 1] + (int64_t)e * rows * ly.in, ly.in);
+                const Mat d = dpre(l, e);
+                gb.dx(&d, &sets[e][l], 1, rows, 0, sets[e][l].in, h->dpost[l - 1] + (int64_t)e * rows * sets[e][l].in,
+                      sets[e][l].in);
             }
-            launch_gemm<float>(g, E, kKN, s);
         }
     }
     if (dX) {
-        const Lin& l0 = (*layers[0])[0];
-        GemmProblem p = lin_dx(dpre[0], l0.out, rows, params + l0.w, l0.in, l0.out, col0, ncols, dX, lddx);
-        p.n_sum = E;
-        p.a_sum = (int64_t)rows * l0.out;
-        p.b_sum = E > 1 ? (*layers[1])[0].w - l0.w : 0;
-        if (mask) { p.mask = mask; p.sm_m = ldmask; p.sm_n = 1; }
-        launch_gemm<float>(&p, 1, kKN, s);
+        GemmBuilder gb(h, s, bf);
+        Mat d[2] = {dpre(0, 0), E > 1 ? dpre(0, 1) : dpre(0, 0)};
+        LayerRef w[2] = {sets[0][0], E > 1 ? sets[1][0] : sets[0][0]};
+        gb.dx(d, w, E, rows, 0, ncols, dX, lddx, mask, ldmask);
     }
 }
 
@@ -182,16 +275,16 @@ void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, in
         mb.post[l] = h->dalloc<float>((int64_t)E * rows * layers[l].out);
         mb.mean[l] = h->dalloc<float>((int64_t)E * rows);
         mb.rstd[l] = h->dalloc<float>((int64_t)E * rows);
+        if (h->bf16) mb.posth.push_back(h->dalloc<__nv_bfloat16>((int64_t)E * rows * layers[l].out));
     }
     mb.out = h->dalloc<float>((int64_t)E * rows * layers[nh].out);
 }
-
-constexpr uint32_t kStateMagic = 0x54535153u;  // "SQST"
 
 }  // namespace
 
 int squint_handle::allocate() {
     const int B = c.batch, A = c.action_dim, K = c.atoms, E = 2;
+    bf16 = c.precision == SQUINT_PREC_BF16;
     SQ_CK(this, cudaGetDevice(&device));
     const int64_t n = L.total;
     params = dalloc<float>(n); grads = dalloc<float>(n);
@@ -202,6 +295,7 @@ int squint_handle::allocate() {
     d_update_idx = dalloc<int64_t>(1);
     d_steps = dalloc<int32_t>(4);
     d_do_actor = dalloc<int32_t>(1);
+    d_err = dalloc<int32_t>(1);
     d_stats = dalloc<float>((int64_t)c.max_k * 8);
     const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
     x2 = dalloc<float>(2 * B * img);
@@ -236,6 +330,7 @@ int squint_handle::allocate() {
         const int w = std::max(c.hidden[l], 1);
         dpost.push_back(dalloc<float>((int64_t)E * B * w));
         dpre.push_back(dalloc<float>((int64_t)E * B * w));
+        if (bf16) dpre_h.push_back(dalloc<__nv_bfloat16>((int64_t)E * B * w));
     }
     dh = dalloc<float>((int64_t)B * L.zdim);
     if (L.D > 0) dproj = dalloc<float>((int64_t)B * L.D);
@@ -251,11 +346,46 @@ int squint_handle::allocate() {
     dconv_a = dalloc<float>(maxc);
     dconv_b = dalloc<float>(maxc);
     wgrad_work = dalloc<float>(maxw);
-    da = dalloc<float>((int64_t)B * A);
+    dxq = dalloc<float>((int64_t)B * L.dc);
     dout_a = dalloc<float>((int64_t)B * 2 * A);
+    if (bf16) {
+        // padded BF16 weight copies: online for every linear layer, target for the critic range
+        auto add = [&](const Lin& ly, bool with_target) {
+            LinBf lb;
+            lb.ld = pad8(ly.in);
+            lb.on = dalloc<__nv_bfloat16>((int64_t)ly.out * lb.ld);
+            if (with_target) lb.tg = dalloc<__nv_bfloat16>((int64_t)ly.out * lb.ld);
+            lin_bf[ly.w] = lb;
+        };
+        if (L.D > 0) { add(L.cproj, true); add(L.aproj, false); }
+        for (int e = 0; e < 2; ++e) for (const auto& ly : L.critic[e]) add(ly, true);
+        for (const auto& ly : L.actor) add(ly, false);
+        z_h = dalloc<__nv_bfloat16>((int64_t)2 * B * L.feat);
+        xa_h = dalloc<__nv_bfloat16>((int64_t)2 * B * pad8(L.da));
+        xcbar_h = dalloc<__nv_bfloat16>((int64_t)B * pad8(L.dc));
+        xc_h = dalloc<__nv_bfloat16>((int64_t)B * pad8(L.dc));
+        xq_h = dalloc<__nv_bfloat16>((int64_t)B * pad8(L.dc));
+        dlogits_h = dalloc<__nv_bfloat16>((int64_t)E * B * pad8(K));
+        dlogits_qh = dalloc<__nv_bfloat16>((int64_t)E * B * pad8(K));
+        if (L.D > 0) dproj_h = dalloc<__nv_bfloat16>((int64_t)B * L.D);
+        dout_ah = dalloc<__nv_bfloat16>((int64_t)B * pad8(2 * A));
+    }
     for (void* p : allocations)
         if (!p) { g_last_error = "device allocation failed"; return SQUINT_ENOMEM; }
-    if (allocations.size() && !allocations.back()) return SQUINT_ENOMEM;
+    if (bf16) {
+        if (L.feat % 8) { g_last_error = "BF16 path needs a feature width divisible by 8"; return SQUINT_EINVAL; }
+        auto item = [&](const Lin& ly, bool tgt) {
+            const LinBf& lb = lin_bf[ly.w];
+            const float* src = tgt ? target + (ly.w - L.critic_begin) : params + ly.w;
+            return CastItem{src, ly.in, ly.out, ly.in, tgt ? lb.tg : lb.on, lb.ld};
+        };
+        if (L.D > 0) { cast_critic.push_back(item(L.cproj, false)); cast_target.push_back(item(L.cproj, true)); }
+        for (int e = 0; e < 2; ++e)
+            for (const auto& ly : L.critic[e]) { cast_critic.push_back(item(ly, false)); cast_target.push_back(item(ly, true)); }
+        if (L.D > 0) cast_actor.push_back(item(L.aproj, false));
+        for (const auto& ly : L.actor) cast_actor.push_back(item(ly, false));
+        tc_prepare();
+    }
     if (cudaMallocHost(&h_stats, sizeof(float) * 8 * c.max_k) != cudaSuccess) return SQUINT_ENOMEM;
     SQ_CK(this, cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
     for (int i = 0; i < 2; ++i) {
@@ -275,6 +405,7 @@ int squint_handle::allocate() {
     SQ_CK(this, cudaMemset(d_update_idx, 0, sizeof(int64_t)));
     SQ_CK(this, cudaMemset(d_steps, 0, 4 * sizeof(int32_t)));
     SQ_CK(this, cudaMemset(d_do_actor, 0, sizeof(int32_t)));
+    SQ_CK(this, cudaMemset(d_err, 0, sizeof(int32_t)));
     return after_param_change();
 }
 
@@ -305,6 +436,12 @@ int squint_handle::after_param_change() {
     SQ_CK(this, cudaDeviceSynchronize());
     for (int i = 0; i < 2; ++i)
         SQ_CK(this, cudaMemcpy(policy_buf[i], params, L.total * sizeof(float), cudaMemcpyDeviceToDevice));
+    if (bf16) {
+        launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), 0);
+        launch_cast_rows(cast_actor.data(), (int)cast_actor.size(), 0);
+        launch_cast_rows(cast_target.data(), (int)cast_target.size(), 0);
+        SQ_CK(this, cudaDeviceSynchronize());
+    }
     ++policy_version;
     return SQUINT_OK;
 }
@@ -312,10 +449,16 @@ int squint_handle::after_param_change() {
 void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     const int B = c.batch, A = c.action_dim, P = c.proprio_dim, K = c.atoms, E = 2;
     const int F = L.feat, Z = L.zdim, Dd = L.D, Dc = L.dc, Da = L.da;
+    const int64_t Dc8 = pad8(Dc), Da8 = pad8(Da), K8 = pad8(K);
     const float ln_eps = (float)c.ln_eps;
     float* W = params;
     float* G = grads;
     float* stats = d_stats + 8 * j;
+    auto cast_rows = [&](const float* src, int64_t ld, int rows, int cols, __nv_bfloat16* dst, int64_t ldh) {
+        if (!bf16) return;
+        CastItem it{src, ld, rows, cols, dst, ldh};
+        launch_cast_rows(&it, 1, s);
+    };
 
     mark(s);
     // ---- a1-a4: minibatch, gathers, shift, squint
@@ -347,31 +490,32 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         launch_conv_fwd<float>(sh, in, W + cv.wo, W + cv.bo, conv_out[l], true, s);
         in = conv_out[l];
     }
-    const float* z = conv_out.back();          // [2B, F]
-    const float* z1 = z + (int64_t)B * F;
+    float* z = conv_out.back();                // [2B, F]
+    cast_rows(z, F, 2 * B, F, z_h, F);
+    const Mat zt{z, F, z_h, F};
+    const Mat zt1 = zt.rows(B);
 
     mark(s);
     // ---- a6: per-head projections (or the flattened features straight into the heads)
-    const PSet online{W, 0};
-    const PSet tgt{target, L.critic_begin};
     if (Dd > 0) {
-        GemmProblem g[4] = {
-            lin_fwd(z1, F, B, W + L.aproj.w, W + L.aproj.b, F, Dd, proj_pre + 0 * (int64_t)B * Dd, Dd),
-            lin_fwd(z1, F, B, tgt.at(L.cproj.w), tgt.at(L.cproj.b), F, Dd, proj_pre + 1 * (int64_t)B * Dd, Dd),
-            lin_fwd(z, F, B, W + L.cproj.w, W + L.cproj.b, F, Dd, proj_pre + 2 * (int64_t)B * Dd, Dd),
-            lin_fwd(z, F, B, W + L.aproj.w, W + L.aproj.b, F, Dd, proj_pre + 3 * (int64_t)B * Dd, Dd),
-        };
-        launch_gemm<float>(g, 4, kKK, s);
+        const LayerRef ap = layer_ref(this, L.aproj, false), cp = layer_ref(this, L.cproj, false);
+        const LayerRef cpt = layer_ref(this, L.cproj, true);
+        {
+            GemmBuilder gb(this, s, bf16);
+            gb.fwd(zt1, B, ap, proj_pre + 0 * (int64_t)B * Dd, Dd);
+            gb.fwd(zt1, B, cpt, proj_pre + 1 * (int64_t)B * Dd, Dd);
+            gb.fwd(zt, B, cp, proj_pre + 2 * (int64_t)B * Dd, Dd);
+            gb.fwd(zt, B, ap, proj_pre + 3 * (int64_t)B * Dd, Dd);
+        }
         LnProblem lp[4];
-        const float* gs[4] = {W + L.aproj.g, tgt.at(L.cproj.g), W + L.cproj.g, W + L.aproj.g};
-        const float* bs[4] = {W + L.aproj.beta, tgt.at(L.cproj.beta), W + L.cproj.beta, W + L.aproj.beta};
+        const LayerRef* refs[4] = {&ap, &cpt, &cp, &ap};
         float* outs[4] = {xa, xcbar, xc, xa + (int64_t)B * Da};
         const int64_t lds[4] = {Da, Dc, Dc, Da};
         for (int i = 0; i < 4; ++i) {
             LnProblem p{};
             p.rows = B; p.n = Dd;
             p.pre = proj_pre + i * (int64_t)B * Dd; p.ld_pre = Dd;
-            p.g = gs[i]; p.beta = bs[i];
+            p.g = refs[i]->g; p.beta = refs[i]->beta;
             p.out = outs[i]; p.ld_out = lds[i];
             p.mean = proj_mean + i * B; p.rstd = proj_rstd + i * B;
             lp[i] = p;
@@ -379,20 +523,23 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         launch_ln_fwd(lp, 4, false, ln_eps, s);
     } else {
         const size_t fb = (size_t)F * sizeof(float);
-        cudaMemcpy2DAsync(xa, Da * sizeof(float), z1, fb, fb, B, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpy2DAsync(xa, Da * sizeof(float), zt1.f, fb, fb, B, cudaMemcpyDeviceToDevice, s);
         cudaMemcpy2DAsync(xa + (int64_t)B * Da, Da * sizeof(float), z, fb, fb, B, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpy2DAsync(xcbar, Dc * sizeof(float), z1, fb, fb, B, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpy2DAsync(xcbar, Dc * sizeof(float), zt1.f, fb, fb, B, cudaMemcpyDeviceToDevice, s);
         cudaMemcpy2DAsync(xc, Dc * sizeof(float), z, fb, fb, B, cudaMemcpyDeviceToDevice, s);
         cudaMemcpy2DAsync(xq, Dc * sizeof(float), z, fb, fb, B, cudaMemcpyDeviceToDevice, s);
     }
+    cast_rows(xa, Da, 2 * B, Da, xa_h, Da8);
+    cast_rows(xc, Dc, B, Dc, xc_h, Dc8);
+
+    const MlpRef actor_on = mlp_ref(this, L.actor, false);
+    const MlpRef crit_on[2] = {mlp_ref(this, L.critic[0], false), mlp_ref(this, L.critic[1], false)};
+    const MlpRef crit_tg[2] = {mlp_ref(this, L.critic[0], true), mlp_ref(this, L.critic[1], true)};
 
     mark(s);
     // ---- a7: actor (pre-update) on both halves; tanh-Gaussian sample
-    const std::vector<Lin>* act_layers[1] = {&L.actor};
-    const std::vector<Lin>* crit_layers[2] = {&L.critic[0], &L.critic[1]};
     {
-        PSet ps[1] = {online};
-        mlp_forward(actor_mlp, act_layers, ps, 1, xa, Da, 2 * B, ln_eps, s);
+        mlp_forward(this, actor_mlp, &actor_on, 1, Mat{xa, Da, xa_h, Da8}, 2 * B, bf16, s);
         ActorHeadArgs ah{};
         ah.rows = 2 * B; ah.B = B; ah.A = A;
         ah.out = actor_mlp.out; ah.ld_out = 2 * A;
@@ -402,12 +549,12 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ah.a_dst1 = xq + Z + P; ah.ld1 = Dc;
         ah.logp = logp; ah.eps = eps;
         launch_actor_head(ah, s);
+        cast_rows(xcbar, Dc, B, Dc, xcbar_h, Dc8);
     }
     mark(s);
     // ---- a8-a9: target critics and the projected categorical target
     {
-        PSet ps[2] = {tgt, tgt};
-        mlp_forward(tcrit_mlp, crit_layers, ps, E, xcbar, Dc, B, ln_eps, s);
+        mlp_forward(this, tcrit_mlp, crit_tg, E, Mat{xcbar, Dc, xcbar_h, Dc8}, B, bf16, s);
         C51TargetArgs ct{};
         ct.B = B; ct.K = K; ct.E = E;
         ct.logits_bar = tcrit_mlp.out; ct.r = r; ct.d = d; ct.logp_next = logp;
@@ -419,36 +566,43 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     mark(s);
     // ---- a10: online critics and the cross entropy
     {
-        PSet ps[2] = {online, online};
-        mlp_forward(crit_mlp, crit_layers, ps, E, xc, Dc, B, ln_eps, s);
+        mlp_forward(this, crit_mlp, crit_on, E, Mat{xc, Dc, xc_h, Dc8}, B, bf16, s);
         CeArgs ce{};
         ce.B = B; ce.K = K; ce.E = E; ce.logits = crit_mlp.out; ce.m = m;
         ce.v_min = (float)c.v_min; ce.v_max = (float)c.v_max;
         ce.scale = 1.0f / (float)B;
         ce.dlogits = dlogits; ce.row_loss = row_loss; ce.row_q = row_q;
+        if (bf16) { ce.dlogits_bf = dlogits_h; ce.ld_bf = K8; }
         launch_ce(ce, s);
     }
     mark(s);
     // ---- a11: backward through critics, critic projection, encoder
     {
+        const Mat dl{dlogits, K, dlogits_h, K8};
         const float* mask = Dd > 0 ? nullptr : z;      // flatten path: mask by the last conv's ReLU
-        mlp_backward(crit_mlp, 0, crit_layers, W, G, E, xc, Dc, B, dlogits, dpost, dpre, 0, Z, Dd > 0 ? dh : dz,
+        mlp_backward(this, crit_mlp, 0, crit_on, G, E, Mat{xc, Dc, xc_h, Dc8}, B, dl, Z, Dd > 0 ? dh : dz,
                      Dd > 0 ? Z : F, mask, F, s);
         if (Dd > 0) {
+            const LayerRef cp = layer_ref(this, L.cproj, false);
             LnBwdProblem p{};
             p.rows = B; p.n = Dd;
             p.dout = dh; p.ld_dout = Dd;
             p.pre = proj_pre + 2 * (int64_t)B * Dd; p.ld_pre = Dd;
             p.mean = proj_mean + 2 * B; p.rstd = proj_rstd + 2 * B;
-            p.g = W + L.cproj.g;
+            p.g = cp.g;
             p.dpre = dproj; p.ld_dpre = Dd;
+            if (bf16) { p.dpre_bf = dproj_h; p.ld_dpre_bf = Dd; }
             p.dg = G + L.cproj.g; p.dbeta = G + L.cproj.beta; p.dbias = G + L.cproj.b;
             launch_ln_bwd(&p, 1, s);
-            GemmProblem gw = lin_dw(dproj, Dd, B, z, F, F, Dd, G + L.cproj.w);
-            launch_gemm<float>(&gw, 1, kMN, s);
-            GemmProblem gx = lin_dx(dproj, Dd, B, W + L.cproj.w, F, Dd, 0, F, dz, F);
-            gx.mask = z; gx.sm_m = F; gx.sm_n = 1;
-            launch_gemm<float>(&gx, 1, kKN, s);
+            const Mat dp{dproj, Dd, dproj_h, Dd};
+            {
+                GemmBuilder gb(this, s, bf16);
+                gb.dw(dp, B, zt, cp, G + L.cproj.w);
+            }
+            {
+                GemmBuilder gb(this, s, bf16);
+                gb.dx(&dp, &cp, 1, B, 0, F, dz, F, z, F);
+            }
         }
         mark(s);
         const float* cur = dz;
@@ -473,6 +627,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ad.step = d_steps + 0;
         ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
         launch_adam(ad, s);
+        if (bf16) launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), s);
     }
     mark(s);
     // ---- a13: temperature
@@ -490,46 +645,53 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     // ---- a14: actor step on stop-gradient features with the updated critics
     {
         if (Dd > 0) {
-            GemmProblem g = lin_fwd(z, F, B, W + L.cproj.w, W + L.cproj.b, F, Dd, proj_pre + 4 * (int64_t)B * Dd, Dd);
-            launch_gemm<float>(&g, 1, kKK, s);
+            const LayerRef cp = layer_ref(this, L.cproj, false);
+            {
+                GemmBuilder gb(this, s, bf16);
+                gb.fwd(zt, B, cp, proj_pre + 4 * (int64_t)B * Dd, Dd);
+            }
             LnProblem p{};
             p.rows = B; p.n = Dd;
             p.pre = proj_pre + 4 * (int64_t)B * Dd; p.ld_pre = Dd;
-            p.g = W + L.cproj.g; p.beta = W + L.cproj.beta;
+            p.g = cp.g; p.beta = cp.beta;
             p.out = xq; p.ld_out = Dc;
             p.mean = proj_mean + 4 * B; p.rstd = proj_rstd + 4 * B;
             launch_ln_fwd(&p, 1, false, ln_eps, s);
         }
-        PSet ps[2] = {online, online};
-        mlp_forward(qcrit_mlp, crit_layers, ps, E, xq, Dc, B, ln_eps, s);
+        cast_rows(xq, Dc, B, Dc, xq_h, Dc8);
+        mlp_forward(this, qcrit_mlp, crit_on, E, Mat{xq, Dc, xq_h, Dc8}, B, bf16, s);
         ActorQArgs aq{};
         aq.B = B; aq.K = K; aq.E = E; aq.logits = qcrit_mlp.out;
         aq.v_min = (float)c.v_min; aq.v_max = (float)c.v_max;
         aq.dlogits = dlogits_q; aq.row_q = row_q_actor; aq.do_actor = d_do_actor;
+        if (bf16) { aq.dlogits_bf = dlogits_qh; aq.ld_bf = K8; }
         launch_actor_q(aq, s);
-        mlp_backward(qcrit_mlp, 0, crit_layers, W, nullptr, E, xq, Dc, B, dlogits_q, dpost, dpre, Z + P, A, da, A,
-                     nullptr, 0, s);
+        mlp_backward(this, qcrit_mlp, 0, crit_on, nullptr, E, Mat{xq, Dc, xq_h, Dc8}, B, Mat{dlogits_q, K, dlogits_qh, K8},
+                     Dc, dxq, Dc, nullptr, 0, s);
         ActorHeadBwdArgs hb{};
         hb.B = B; hb.A = A;
         hb.out = actor_mlp.out + (int64_t)B * 2 * A; hb.ld_out = 2 * A;
-        hb.eps = eps + (int64_t)B * A; hb.da = da; hb.log_alpha = W + L.log_alpha;
+        hb.eps = eps + (int64_t)B * A; hb.da = dxq + Z + P; hb.ld_da = Dc; hb.log_alpha = W + L.log_alpha;
         hb.lo = (float)c.log_std_min; hb.hi = (float)c.log_std_max;
         hb.dout = dout_a; hb.do_actor = d_do_actor;
+        if (bf16) { hb.dout_bf = dout_ah; hb.ld_dout_bf = pad8(2 * A); }
         launch_actor_head_bwd(hb, s);
-        mlp_backward(actor_mlp, B, act_layers, W, G, 1, xa + (int64_t)B * Da, Da, B, dout_a, dpost, dpre, 0, Z,
-                     Dd > 0 ? dh : nullptr, Z, nullptr, 0, s);
+        mlp_backward(this, actor_mlp, B, &actor_on, G, 1, Mat{xa, Da, xa_h, Da8}.rows(B), B,
+                     Mat{dout_a, 2 * A, dout_ah, pad8(2 * A)}, Z, Dd > 0 ? dh : nullptr, Z, nullptr, 0, s);
         if (Dd > 0) {
+            const LayerRef ap = layer_ref(this, L.aproj, false);
             LnBwdProblem p{};
             p.rows = B; p.n = Dd;
             p.dout = dh; p.ld_dout = Dd;
             p.pre = proj_pre + 3 * (int64_t)B * Dd; p.ld_pre = Dd;
             p.mean = proj_mean + 3 * B; p.rstd = proj_rstd + 3 * B;
-            p.g = W + L.aproj.g;
+            p.g = ap.g;
             p.dpre = dproj; p.ld_dpre = Dd;
+            if (bf16) { p.dpre_bf = dproj_h; p.ld_dpre_bf = Dd; }
             p.dg = G + L.aproj.g; p.dbeta = G + L.aproj.beta; p.dbias = G + L.aproj.b;
             launch_ln_bwd(&p, 1, s);
-            GemmProblem gw = lin_dw(dproj, Dd, B, z, F, F, Dd, G + L.aproj.w);
-            launch_gemm<float>(&gw, 1, kMN, s);
+            GemmBuilder gb(this, s, bf16);
+            gb.dw(Mat{dproj, Dd, dproj_h, Dd}, B, zt, ap, G + L.aproj.w);
         }
         AdamArgs ad{};
         ad.p = W + L.actor_begin; ad.g = G + L.actor_begin; ad.m = adam_m + L.actor_begin; ad.v = adam_v + L.actor_begin;
@@ -537,6 +699,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ad.step = d_steps + 1; ad.enable = d_do_actor;
         ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
         launch_adam(ad, s);
+        if (bf16) launch_cast_rows(cast_actor.data(), (int)cast_actor.size(), s);
     }
     mark(s);
     // ---- statistics, then a16: polyak (also advances the update index)
@@ -548,11 +711,13 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         launch_stats(st, s);
         PolyakArgs pa{target, W + L.critic_begin, L.target_n, (float)c.tau, d_update_idx};
         launch_polyak(pa, s);
+        if (bf16) launch_cast_rows(cast_target.data(), (int)cast_target.size(), s);
     }
     mark(s);
 }
 
 int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s, bool use_graph) {
+    launch_failed = false;
     if (use_graph) {
         auto it = graphs.find(k);
         if (it == graphs.end()) {
@@ -567,6 +732,11 @@ int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s
             SQ_CK(this, cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
             for (int j = 0; j < k; ++j) record_update(j, capture_stream, false);
             SQ_CK(this, cudaStreamEndCapture(capture_stream, &graph));
+            if (launch_failed) {
+                cudaGraphDestroy(graph);
+                g_last_error = "a tensor-core operand could not be described by a tensor map";
+                return SQUINT_EINVAL;
+            }
             size_t n_nodes = 0;
             SQ_CK(this, cudaGraphGetNodes(graph, nullptr, &n_nodes));
             std::vector<cudaGraphNode_t> nodes(n_nodes);
@@ -587,10 +757,21 @@ int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s
     } else {
         for (int j = 0; j < k; ++j) record_update(j, s, true);
         SQ_CK(this, cudaGetLastError());
+        if (launch_failed) {
+            g_last_error = "a tensor-core operand could not be described by a tensor map";
+            return SQUINT_EINVAL;
+        }
     }
     if (stats) {
+        int32_t err = 0;
         SQ_CK(this, cudaMemcpyAsync(h_stats, d_stats, sizeof(float) * 8 * k, cudaMemcpyDeviceToHost, s));
+        SQ_CK(this, cudaMemcpyAsync(&err, d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         SQ_CK(this, cudaStreamSynchronize(s));
+        if (err) {
+            failed = true;
+            g_last_error = "a bounded device wait ran out";
+            return SQUINT_ETIMEOUT;
+        }
         for (int j = 0; j < k; ++j) {
             const float* q = h_stats + 8 * j;
             squint_update_stats& o = stats[j];
@@ -602,245 +783,6 @@ int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s
             o.update_idx = (int64_t)(((uint64_t)hi << 32) | lo);
         }
     }
-    return SQUINT_OK;
-}
-
-size_t squint_handle::state_bytes() const {
-    return 48 + sizeof(float) * (size_t)(3 * L.total + L.target_n);
-}
-
-int squint_handle::save_state(uint8_t* out) {
-    SQ_CK(this, cudaDeviceSynchronize());
-    uint32_t hdr32[2] = {kStateMagic, 1};
-    int64_t hdr64[2] = {L.total, L.target_n};
-    int32_t steps[4];
-    int64_t u;
-    SQ_CK(this, cudaMemcpy(steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost));
-    SQ_CK(this, cudaMemcpy(&u, d_update_idx, sizeof(u), cudaMemcpyDeviceToHost));
-    std::memcpy(out, hdr32, 8);
-    std::memcpy(out + 8, hdr64, 16);
-    std::memcpy(out + 24, steps, 16);
-    std::memcpy(out + 40, &u, 8);
-    uint8_t* p = out + 48;
-    const size_t nb = sizeof(float) * L.total;
-    SQ_CK(this, cudaMemcpy(p, params, nb, cudaMemcpyDeviceToHost)); p += nb;
-    SQ_CK(this, cudaMemcpy(p, adam_m, nb, cudaMemcpyDeviceToHost)); p += nb;
-    SQ_CK(this, cudaMemcpy(p, adam_v, nb, cudaMemcpyDeviceToHost)); p += nb;
-    SQ_CK(this, cudaMemcpy(p, target, sizeof(float) * L.target_n, cudaMemcpyDeviceToHost));
-    return SQUINT_OK;
-}
-
-int squint_handle::load_state(const uint8_t* in) {
-    uint32_t hdr32[2];
-    int64_t hdr64[2];
-    std::memcpy(hdr32, in, 8);
-    std::memcpy(hdr64, in + 8, 16);
-    if (hdr32[0] != kStateMagic || hdr32[1] != 1 || hdr64[0] != L.total || hdr64[1] != L.target_n) {
-        g_last_error = "state does not match this configuration";
-        return SQUINT_EINVAL;
-    }
-    SQ_CK(this, cudaDeviceSynchronize());
-    SQ_CK(this, cudaMemcpy(d_steps, in + 24, 16, cudaMemcpyHostToDevice));
-    SQ_CK(this, cudaMemcpy(d_update_idx, in + 40, 8, cudaMemcpyHostToDevice));
-    const uint8_t* p = in + 48;
-    const size_t nb = sizeof(float) * L.total;
-    SQ_CK(this, cudaMemcpy(params, p, nb, cudaMemcpyHostToDevice)); p += nb;
-    SQ_CK(this, cudaMemcpy(adam_m, p, nb, cudaMemcpyHostToDevice)); p += nb;
-    SQ_CK(this, cudaMemcpy(adam_v, p, nb, cudaMemcpyHostToDevice)); p += nb;
-    SQ_CK(this, cudaMemcpy(target, p, sizeof(float) * L.target_n, cudaMemcpyHostToDevice));
-    return after_param_change();
-}
-
-int squint_handle::debug_tensor(const char* name, void* host, size_t* bytes) {
-    const int B = c.batch, A = c.action_dim, K = c.atoms;
-    const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
-    const std::string n(name);
-    const void* src = nullptr;
-    size_t sz = 0;
-    if (n == "idx") { src = idx2; sz = 4 * B; }
-    else if (n == "nxt") { src = idx2 + B; sz = 4 * B; }
-    else if (n == "shift_t") { src = shift2; sz = 8 * B; }
-    else if (n == "shift_t1") { src = shift2 + 2 * B; sz = 8 * B; }
-    else if (n == "sums_t") { src = sums; sz = 2 * B * img; }
-    else if (n == "sums_t1") { src = sums + B * img; sz = 2 * B * img; }
-    else if (n == "x_t") { src = x2; sz = 4 * B * img; }
-    else if (n == "x_t1") { src = x2 + B * img; sz = 4 * B * img; }
-    else if (n == "m") { src = m; sz = 4 * (size_t)B * K; }
-    else if (n == "logits") { src = crit_mlp.out; sz = 4 * (size_t)2 * B * K; }
-    else if (n == "logits_target") { src = tcrit_mlp.out; sz = 4 * (size_t)2 * B * K; }
-    else if (n == "logp_next") { src = logp; sz = 4 * B; }
-    else if (n == "logp_t") { src = logp + B; sz = 4 * B; }
-    else if (n == "a_next") { src = nullptr; sz = 4 * (size_t)B * A; }
-    else if (n == "a_pi") { src = nullptr; sz = 4 * (size_t)B * A; }
-    else if (n == "grads") { src = grads; sz = 4 * (size_t)L.total; }
-    else if (n == "z_t") { src = conv_out.back(); sz = 4 * (size_t)B * L.feat; }
-    else if (n == "target") { src = target; sz = 4 * (size_t)L.target_n; }
-    else { g_last_error = "unknown debug tensor"; return SQUINT_EINVAL; }
-    if (!host) { *bytes = sz; return SQUINT_OK; }
-    if (*bytes < sz) { *bytes = sz; return SQUINT_EINVAL; }
-    *bytes = sz;
-    SQ_CK(this, cudaDeviceSynchronize());
-    if (n == "a_next" || n == "a_pi") {
-        const float* base = n == "a_next" ? xcbar : xq;
-        SQ_CK(this, cudaMemcpy2D(host, A * sizeof(float), base + L.zdim + c.proprio_dim, L.dc * sizeof(float),
-                                 A * sizeof(float), B, cudaMemcpyDeviceToHost));
-        return SQUINT_OK;
-    }
-    SQ_CK(this, cudaMemcpy(host, src, sz, cudaMemcpyDeviceToHost));
-    return SQUINT_OK;
-}
-
-int squint_handle::refresh_policy(cudaStream_t s) {
-    std::lock_guard<std::mutex> lk(act_mu);
-    // write the snapshot inference is not using, after inference that last read it
-    const int i = 1 - policy_active;
-    SQ_CK(this, cudaStreamWaitEvent(s, policy_released[i], 0));
-    SQ_CK(this, cudaMemcpyAsync(policy_buf[i], params, L.total * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    SQ_CK(this, cudaEventRecord(policy_ready[i], s));
-    policy_active = i;
-    ++policy_version;
-    return SQUINT_OK;
-}
-
-// ---------------------------------------------------------------- inference
-size_t squint_handle::act_row_bytes() const {
-    size_t f = (size_t)c.obs_c * L.hs * L.ws;
-    for (const auto& cv : L.conv) f += (size_t)cv.cout * cv.oh * cv.ow;
-    f += (size_t)L.D + 2 + L.da;
-    for (int l = 0; l < c.n_hidden; ++l) f += 2 * (size_t)c.hidden[l] + 2;
-    f += 2 * (size_t)c.action_dim;
-    return f * sizeof(float) + 8;
-}
-
-int squint_handle::ensure_act_capacity(int rows, int n_reqs) {
-    if (rows <= act_cap && n_reqs <= req_cap) return SQUINT_OK;
-    SQ_CK(this, cudaDeviceSynchronize());
-    for (void* p : act_allocs) if (p) cudaFree(p);
-    act_allocs.clear();
-    if (h_req) { cudaFreeHost(h_req); h_req = nullptr; }
-    const int cap = std::max(((std::max(rows, act_cap) + 255) / 256) * 256, 256);
-    const int rcap = std::max(std::max(n_reqs, req_cap), 64);
-    auto al = [&](size_t bytes) -> void* {
-        void* p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
-        act_allocs.push_back(p);
-        return p;
-    };
-    const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
-    ax = (float*)al(sizeof(float) * cap * img);
-    aconv.clear();
-    for (const auto& cv : L.conv) aconv.push_back((float*)al(sizeof(float) * (size_t)cap * cv.cout * cv.oh * cv.ow));
-    if (L.D > 0) {
-        apre = (float*)al(sizeof(float) * (size_t)cap * L.D);
-        amean = (float*)al(sizeof(float) * cap);
-        arstd = (float*)al(sizeof(float) * cap);
-    }
-    axin = (float*)al(sizeof(float) * (size_t)cap * L.da);
-    const int nh = c.n_hidden;
-    act_mlp = MlpBufs{};
-    act_mlp.E = 1; act_mlp.rows = cap;
-    act_mlp.pre.resize(nh); act_mlp.post.resize(nh); act_mlp.mean.resize(nh); act_mlp.rstd.resize(nh);
-    for (int l = 0; l < nh; ++l) {
-        act_mlp.pre[l] = (float*)al(sizeof(float) * (size_t)cap * c.hidden[l]);
-        act_mlp.post[l] = (float*)al(sizeof(float) * (size_t)cap * c.hidden[l]);
-        act_mlp.mean[l] = (float*)al(sizeof(float) * cap);
-        act_mlp.rstd[l] = (float*)al(sizeof(float) * cap);
-    }
-    act_mlp.out = (float*)al(sizeof(float) * (size_t)cap * 2 * c.action_dim);
-    req_bytes = (size_t)cap * 8 + (size_t)rcap * (8 * 4 + 4) + 64;
-    d_req = al(req_bytes);
-    for (void* p : act_allocs) if (!p) { g_last_error = "inference allocation failed"; act_cap = 0; return SQUINT_ENOMEM; }
-    if (cudaMallocHost(&h_req, req_bytes) != cudaSuccess) { act_cap = 0; return SQUINT_ENOMEM; }
-    act_cap = cap;
-    req_cap = rcap;
-    req_event_live = false;
-    return SQUINT_OK;
-}
-
-int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t s, int64_t* version_used) {
-    std::lock_guard<std::mutex> lk(act_mu);
-    int rows = 0;
-    for (int q = 0; q < n_reqs; ++q) {
-        const squint_act_request& rq = reqs[q];
-        if (rq.n < 1 || !rq.obs || !rq.proprio || !rq.actions || (rq.mode != 0 && rq.mode != 1)) {
-            g_last_error = "invalid inference request";
-            return SQUINT_EINVAL;
-        }
-        rows += rq.n;
-    }
-    if (rows == 0) return SQUINT_OK;
-    int rc = ensure_act_capacity(rows, n_reqs);
-    if (rc != SQUINT_OK) return rc;
-    if (req_event_live) SQ_CK(this, cudaEventSynchronize(req_event));
-    // pack: row_req[cap] row_in[cap] | obs[rcap] prop[rcap] act[rcap] key[rcap] (8 B each) | mode[rcap]
-    uint8_t* hb = static_cast<uint8_t*>(h_req);
-    int32_t* row_req = reinterpret_cast<int32_t*>(hb);
-    int32_t* row_in = row_req + act_cap;
-    uint64_t* p64 = reinterpret_cast<uint64_t*>(hb + (size_t)act_cap * 8);
-    int32_t* modes = reinterpret_cast<int32_t*>(p64 + 4 * (size_t)req_cap);
-    int r = 0;
-    for (int q = 0; q < n_reqs; ++q) {
-        for (int i = 0; i < reqs[q].n; ++i, ++r) { row_req[r] = q; row_in[r] = i; }
-        p64[q] = (uint64_t)(uintptr_t)reqs[q].obs;
-        p64[req_cap + q] = (uint64_t)(uintptr_t)reqs[q].proprio;
-        p64[2 * req_cap + q] = (uint64_t)(uintptr_t)reqs[q].actions;
-        p64[3 * req_cap + q] = reqs[q].rng_key;
-        modes[q] = reqs[q].mode;
-    }
-    SQ_CK(this, cudaMemcpyAsync(d_req, h_req, req_bytes, cudaMemcpyHostToDevice, s));
-    SQ_CK(this, cudaEventRecord(req_event, s));
-    req_event_live = true;
-    uint8_t* db = static_cast<uint8_t*>(d_req);
-    const int32_t* d_row_req = reinterpret_cast<const int32_t*>(db);
-    const int32_t* d_row_in = d_row_req + act_cap;
-    const uint64_t* d64 = reinterpret_cast<const uint64_t*>(db + (size_t)act_cap * 8);
-    const int32_t* d_modes = reinterpret_cast<const int32_t*>(d64 + 4 * (size_t)req_cap);
-
-    const int pi = policy_active;
-    const float* Wp = policy_buf[pi];
-    SQ_CK(this, cudaStreamWaitEvent(s, policy_ready[pi], 0));
-    if (version_used) *version_used = policy_version;
-
-    const int F = L.feat, Da = L.da, Dd = L.D, A = c.action_dim;
-    ActFrontArgs af{};
-    af.obs = reinterpret_cast<const uint8_t* const*>(d64);
-    af.prop = reinterpret_cast<const float* const*>(d64 + req_cap);
-    af.row_req = d_row_req; af.row_in_req = d_row_in;
-    af.rows = rows; af.C = c.obs_c; af.H = c.obs_h; af.W = c.obs_w; af.f = c.squint_f; af.P = c.proprio_dim;
-    af.x = ax; af.xin = axin; af.ld_xin = Da; af.col = L.zdim;
-    launch_act_frontend(af, s);
-    const float* in = ax;
-    for (size_t l = 0; l < L.conv.size(); ++l) {
-        const ConvL& cv = L.conv[l];
-        ConvShape sh{rows, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
-                     (int64_t)cv.cout * cv.oh * cv.ow};
-        launch_conv_fwd<float>(sh, in, Wp + cv.wo, Wp + cv.bo, aconv[l], true, s);
-        in = aconv[l];
-    }
-    if (Dd > 0) {
-        GemmProblem g = lin_fwd(in, F, rows, Wp + L.aproj.w, Wp + L.aproj.b, F, Dd, apre, Dd);
-        launch_gemm<float>(&g, 1, kKK, s);
-        LnProblem p{};
-        p.rows = rows; p.n = Dd; p.pre = apre; p.ld_pre = Dd;
-        p.g = Wp + L.aproj.g; p.beta = Wp + L.aproj.beta;
-        p.out = axin; p.ld_out = Da; p.mean = amean; p.rstd = arstd;
-        launch_ln_fwd(&p, 1, false, (float)c.ln_eps, s);
-    } else {
-        SQ_CK(this, cudaMemcpy2DAsync(axin, Da * sizeof(float), in, F * sizeof(float), F * sizeof(float), rows,
-                                      cudaMemcpyDeviceToDevice, s));
-    }
-    const std::vector<Lin>* layers[1] = {&L.actor};
-    PSet ps[1] = {PSet{Wp, 0}};
-    mlp_forward(act_mlp, layers, ps, 1, axin, Da, rows, (float)c.ln_eps, s);
-    ActHeadArgs ha{};
-    ha.rows = rows; ha.A = A; ha.out = act_mlp.out; ha.ld_out = 2 * A;
-    ha.row_req = d_row_req; ha.row_in_req = d_row_in;
-    ha.req_key = d64 + 3 * req_cap; ha.req_mode = d_modes;
-    ha.req_actions = reinterpret_cast<float* const*>(d64 + 2 * req_cap);
-    ha.lo = (float)c.log_std_min; ha.hi = (float)c.log_std_max; ha.seed = c.seed;
-    launch_act_head(ha, s);
-    SQ_CK(this, cudaEventRecord(policy_released[pi], s));
-    SQ_CK(this, cudaGetLastError());
     return SQUINT_OK;
 }
 

@@ -66,7 +66,9 @@ __global__ void ln_bwd_row_kernel(Batch<LnBwdProblem> b) {
     for (int j = lane; j < P.n; j += 32) {
         const float dn = (out && !(out[j] > 0.f)) ? 0.f : dout[j];
         const float xh = (pre[j] - mean) * rstd;
-        dpre[j] = rstd * (dn * P.g[j] - m1 - xh * m2);
+        const float v = rstd * (dn * P.g[j] - m1 - xh * m2);
+        dpre[j] = v;
+        if (P.dpre_bf) P.dpre_bf[(int64_t)gw * P.ld_dpre_bf + j] = __float2bfloat16_rn(v);
     }
 }
 
@@ -205,7 +207,9 @@ __global__ void ce_kernel(CeArgs a) {
         const float p = expf(ls);
         loss -= m[j] * ls;
         q += p * (a.v_min + (float)j * dz);
-        a.dlogits[(int64_t)er * a.K + j] = (p - m[j]) * a.scale;
+        const float g = (p - m[j]) * a.scale;
+        a.dlogits[(int64_t)er * a.K + j] = g;
+        if (a.dlogits_bf) a.dlogits_bf[(int64_t)er * a.ld_bf + j] = __float2bfloat16_rn(g);
     }
     loss = block_sum(loss, red);
     q = block_sum(q, red);
@@ -235,7 +239,9 @@ __global__ void actor_q_kernel(ActorQArgs a) {
     const float scale = -1.0f / (float)(a.E * a.B);
     for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
         const float p = expf(lg[j] - mx) / s;
-        a.dlogits[(int64_t)er * a.K + j] = scale * p * (a.v_min + (float)j * dz - qs);
+        const float g = scale * p * (a.v_min + (float)j * dz - qs);
+        a.dlogits[(int64_t)er * a.K + j] = g;
+        if (a.dlogits_bf) a.dlogits_bf[(int64_t)er * a.ld_bf + j] = __float2bfloat16_rn(g);
     }
 }
 
@@ -282,10 +288,16 @@ __global__ void actor_head_bwd_kernel(ActorHeadBwdArgs a) {
         const float th = tanhf(raw);
         const float sd = expf(a.lo + 0.5f * (a.hi - a.lo) * (th + 1.0f));
         const float act = tanhf(mu + sd * eps);
-        const float du = a.da[(int64_t)row * a.A + k] * (1.0f - act * act) + dlogp * 2.0f * act;
+        const int64_t ldd = a.ld_da ? a.ld_da : a.A;
+        const float du = a.da[(int64_t)row * ldd + k] * (1.0f - act * act) + dlogp * 2.0f * act;
         const float dls = du * sd * eps - dlogp;
+        const float draw = dls * 0.5f * (a.hi - a.lo) * (1.0f - th * th);
         a.dout[(int64_t)row * 2 * a.A + k] = du;
-        a.dout[(int64_t)row * 2 * a.A + a.A + k] = dls * 0.5f * (a.hi - a.lo) * (1.0f - th * th);
+        a.dout[(int64_t)row * 2 * a.A + a.A + k] = draw;
+        if (a.dout_bf) {
+            a.dout_bf[(int64_t)row * a.ld_dout_bf + k] = __float2bfloat16_rn(du);
+            a.dout_bf[(int64_t)row * a.ld_dout_bf + a.A + k] = __float2bfloat16_rn(draw);
+        }
     }
 }
 

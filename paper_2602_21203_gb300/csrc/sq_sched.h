@@ -1,0 +1,72 @@
+// Building blocks of the launch schedule shared by the update and inference.
+#pragma once
+
+#include "sq_internal.h"
+#include "sq_tc.cuh"
+
+namespace sq {
+
+// An activation or gradient matrix: FP32 rows plus an optional BF16 shadow
+// (the operand the tensor-core GEMMs read).
+struct Mat {
+    float* f = nullptr;
+    int64_t ld = 0;
+    __nv_bfloat16* h = nullptr;
+    int64_t ldh = 0;
+    Mat rows(int64_t r0) const {
+        Mat m = *this;
+        if (m.f) m.f += r0 * ld;
+        if (m.h) m.h += r0 * ldh;
+        return m;
+    }
+};
+
+// A linear layer of one parameter set: FP32 weight [out, in] and bias, BF16 padded
+// copy of the weight, and the LayerNorm that follows it (g == null: output layer).
+struct LayerRef {
+    const float* w = nullptr;
+    const float* b = nullptr;
+    const __nv_bfloat16* wh = nullptr;
+    int64_t ldh = 0;
+    int in = 0, out = 0;
+    const float* g = nullptr;
+    const float* beta = nullptr;
+};
+using MlpRef = std::vector<LayerRef>;
+
+// Collects dense contractions of one kind and launches them as one grouped
+// kernel: CUDA-core FP32 (plain path) or tcgen05 BF16 (tensor-core path).
+class GemmBuilder {
+public:
+    GemmBuilder(squint_handle* h, cudaStream_t s, bool bf16) : h_(h), s_(s), bf_(bf16) {}
+    ~GemmBuilder() { flush(); }
+    // Y = X W^T + b   (Yh: optional BF16 copy of Y)
+    void fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64_t ldy, __nv_bfloat16* Yh = nullptr,
+             int64_t ldyh = 0);
+    // dX[:, 0:ncols] = sum_q dY_q W_q[:, col0:col0+ncols]  (* (mask > 0))
+    void dx(const Mat* dY, const LayerRef* W, int n_pairs, int rows, int col0, int ncols, float* dX, int64_t ldx,
+            const float* mask = nullptr, int64_t ldm = 0);
+    // dW = dY^T X
+    void dw(const Mat& dY, int rows, const Mat& X, const LayerRef& W, float* dW);
+    void flush();
+
+private:
+    squint_handle* h_;
+    cudaStream_t s_;
+    bool bf_;
+    std::vector<GemmProblem> fp_;
+    GemmLayout lay_ = kKK;
+    std::vector<TcGemm> tc_;
+};
+
+// Forward of E parameter sets of one MLP shape on `rows` rows of X.
+void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const Mat& X, int rows, bool bf16,
+                 cudaStream_t s);
+// Layer view of canonical layer `ly` in the online parameters (base == params), the
+// target copy (target == true) or an inference snapshot (base == a policy buffer, FP32 only).
+LayerRef layer_ref(squint_handle* h, const Lin& ly, bool target, const float* base = nullptr);
+MlpRef mlp_ref(squint_handle* h, const std::vector<Lin>& layers, bool target, const float* base = nullptr);
+GemmProblem lin_fwd(const float* X, int64_t ldx, int rows, const float* W, const float* b, int in, int out, float* Y,
+                    int64_t ldy);
+
+}  // namespace sq

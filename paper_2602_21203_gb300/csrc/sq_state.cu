@@ -1,0 +1,250 @@
+// Learner state transfer, debug views, policy snapshots and batched inference.
+#include "sq_sched.h"
+
+#include <cstring>
+
+using namespace sq;
+
+namespace {
+constexpr uint32_t kStateMagic = 0x54535153u;  // "SQST"
+}  // namespace
+
+size_t squint_handle::state_bytes() const {
+    return 48 + sizeof(float) * (size_t)(3 * L.total + L.target_n);
+}
+
+int squint_handle::save_state(uint8_t* out) {
+    SQ_CK(this, cudaDeviceSynchronize());
+    uint32_t hdr32[2] = {kStateMagic, 1};
+    int64_t hdr64[2] = {L.total, L.target_n};
+    int32_t steps[4];
+    int64_t u;
+    SQ_CK(this, cudaMemcpy(steps, d_steps, sizeof(steps), cudaMemcpyDeviceToHost));
+    SQ_CK(this, cudaMemcpy(&u, d_update_idx, sizeof(u), cudaMemcpyDeviceToHost));
+    std::memcpy(out, hdr32, 8);
+    std::memcpy(out + 8, hdr64, 16);
+    std::memcpy(out + 24, steps, 16);
+    std::memcpy(out + 40, &u, 8);
+    uint8_t* p = out + 48;
+    const size_t nb = sizeof(float) * L.total;
+    SQ_CK(this, cudaMemcpy(p, params, nb, cudaMemcpyDeviceToHost)); p += nb;
+    SQ_CK(this, cudaMemcpy(p, adam_m, nb, cudaMemcpyDeviceToHost)); p += nb;
+    SQ_CK(this, cudaMemcpy(p, adam_v, nb, cudaMemcpyDeviceToHost)); p += nb;
+    SQ_CK(this, cudaMemcpy(p, target, sizeof(float) * L.target_n, cudaMemcpyDeviceToHost));
+    return SQUINT_OK;
+}
+
+int squint_handle::load_state(const uint8_t* in) {
+    uint32_t hdr32[2];
+    int64_t hdr64[2];
+    std::memcpy(hdr32, in, 8);
+    std::memcpy(hdr64, in + 8, 16);
+    if (hdr32[0] != kStateMagic || hdr32[1] != 1 || hdr64[0] != L.total || hdr64[1] != L.target_n) {
+        g_last_error = "state does not match this configuration";
+        return SQUINT_EINVAL;
+    }
+    SQ_CK(this, cudaDeviceSynchronize());
+    SQ_CK(this, cudaMemcpy(d_steps, in + 24, 16, cudaMemcpyHostToDevice));
+    SQ_CK(this, cudaMemcpy(d_update_idx, in + 40, 8, cudaMemcpyHostToDevice));
+    const uint8_t* p = in + 48;
+    const size_t nb = sizeof(float) * L.total;
+    SQ_CK(this, cudaMemcpy(params, p, nb, cudaMemcpyHostToDevice)); p += nb;
+    SQ_CK(this, cudaMemcpy(adam_m, p, nb, cudaMemcpyHostToDevice)); p += nb;
+    SQ_CK(this, cudaMemcpy(adam_v, p, nb, cudaMemcpyHostToDevice)); p += nb;
+    SQ_CK(this, cudaMemcpy(target, p, sizeof(float) * L.target_n, cudaMemcpyHostToDevice));
+    return after_param_change();
+}
+
+int squint_handle::debug_tensor(const char* name, void* host, size_t* bytes) {
+    const int B = c.batch, A = c.action_dim, K = c.atoms;
+    const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
+    const std::string n(name);
+    const void* src = nullptr;
+    size_t sz = 0;
+    if (n == "idx") { src = idx2; sz = 4 * B; }
+    else if (n == "nxt") { src = idx2 + B; sz = 4 * B; }
+    else if (n == "shift_t") { src = shift2; sz = 8 * B; }
+    else if (n == "shift_t1") { src = shift2 + 2 * B; sz = 8 * B; }
+    else if (n == "sums_t") { src = sums; sz = 2 * B * img; }
+    else if (n == "sums_t1") { src = sums + B * img; sz = 2 * B * img; }
+    else if (n == "x_t") { src = x2; sz = 4 * B * img; }
+    else if (n == "x_t1") { src = x2 + B * img; sz = 4 * B * img; }
+    else if (n == "m") { src = m; sz = 4 * (size_t)B * K; }
+    else if (n == "logits") { src = crit_mlp.out; sz = 4 * (size_t)2 * B * K; }
+    else if (n == "logits_target") { src = tcrit_mlp.out; sz = 4 * (size_t)2 * B * K; }
+    else if (n == "logp_next") { src = logp; sz = 4 * B; }
+    else if (n == "logp_t") { src = logp + B; sz = 4 * B; }
+    else if (n == "a_next") { src = nullptr; sz = 4 * (size_t)B * A; }
+    else if (n == "dxq") { src = dxq; sz = 4 * (size_t)B * L.dc; }
+    else if (n == "a_pi") { src = nullptr; sz = 4 * (size_t)B * A; }
+    else if (n == "grads") { src = grads; sz = 4 * (size_t)L.total; }
+    else if (n == "z_t") { src = conv_out.back(); sz = 4 * (size_t)B * L.feat; }
+    else if (n == "target") { src = target; sz = 4 * (size_t)L.target_n; }
+    else { g_last_error = "unknown debug tensor"; return SQUINT_EINVAL; }
+    if (!host) { *bytes = sz; return SQUINT_OK; }
+    if (*bytes < sz) { *bytes = sz; return SQUINT_EINVAL; }
+    *bytes = sz;
+    SQ_CK(this, cudaDeviceSynchronize());
+    if (n == "a_next" || n == "a_pi") {
+        const float* base = n == "a_next" ? xcbar : xq;
+        SQ_CK(this, cudaMemcpy2D(host, A * sizeof(float), base + L.zdim + c.proprio_dim, L.dc * sizeof(float),
+                                 A * sizeof(float), B, cudaMemcpyDeviceToHost));
+        return SQUINT_OK;
+    }
+    SQ_CK(this, cudaMemcpy(host, src, sz, cudaMemcpyDeviceToHost));
+    return SQUINT_OK;
+}
+
+int squint_handle::refresh_policy(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(act_mu);
+    // write the snapshot inference is not using, after inference that last read it
+    const int i = 1 - policy_active;
+    SQ_CK(this, cudaStreamWaitEvent(s, policy_released[i], 0));
+    SQ_CK(this, cudaMemcpyAsync(policy_buf[i], params, L.total * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    SQ_CK(this, cudaEventRecord(policy_ready[i], s));
+    policy_active = i;
+    ++policy_version;
+    return SQUINT_OK;
+}
+
+// ---------------------------------------------------------------- inference
+size_t squint_handle::act_row_bytes() const {
+    size_t f = (size_t)c.obs_c * L.hs * L.ws;
+    for (const auto& cv : L.conv) f += (size_t)cv.cout * cv.oh * cv.ow;
+    f += (size_t)L.D + 2 + L.da;
+    for (int l = 0; l < c.n_hidden; ++l) f += 2 * (size_t)c.hidden[l] + 2;
+    f += 2 * (size_t)c.action_dim;
+    return f * sizeof(float) + 8;
+}
+
+int squint_handle::ensure_act_capacity(int rows, int n_reqs) {
+    if (rows <= act_cap && n_reqs <= req_cap) return SQUINT_OK;
+    SQ_CK(this, cudaDeviceSynchronize());
+    for (void* p : act_allocs) if (p) cudaFree(p);
+    act_allocs.clear();
+    if (h_req) { cudaFreeHost(h_req); h_req = nullptr; }
+    const int cap = std::max(((std::max(rows, act_cap) + 255) / 256) * 256, 256);
+    const int rcap = std::max(std::max(n_reqs, req_cap), 64);
+    auto al = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        act_allocs.push_back(p);
+        return p;
+    };
+    const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
+    ax = (float*)al(sizeof(float) * cap * img);
+    aconv.clear();
+    for (const auto& cv : L.conv) aconv.push_back((float*)al(sizeof(float) * (size_t)cap * cv.cout * cv.oh * cv.ow));
+    if (L.D > 0) {
+        apre = (float*)al(sizeof(float) * (size_t)cap * L.D);
+        amean = (float*)al(sizeof(float) * cap);
+        arstd = (float*)al(sizeof(float) * cap);
+    }
+    axin = (float*)al(sizeof(float) * (size_t)cap * L.da);
+    const int nh = c.n_hidden;
+    act_mlp = MlpBufs{};
+    act_mlp.E = 1; act_mlp.rows = cap;
+    act_mlp.pre.resize(nh); act_mlp.post.resize(nh); act_mlp.mean.resize(nh); act_mlp.rstd.resize(nh);
+    for (int l = 0; l < nh; ++l) {
+        act_mlp.pre[l] = (float*)al(sizeof(float) * (size_t)cap * c.hidden[l]);
+        act_mlp.post[l] = (float*)al(sizeof(float) * (size_t)cap * c.hidden[l]);
+        act_mlp.mean[l] = (float*)al(sizeof(float) * cap);
+        act_mlp.rstd[l] = (float*)al(sizeof(float) * cap);
+    }
+    act_mlp.out = (float*)al(sizeof(float) * (size_t)cap * 2 * c.action_dim);
+    req_bytes = (size_t)cap * 8 + (size_t)rcap * (8 * 4 + 4) + 64;
+    d_req = al(req_bytes);
+    for (void* p : act_allocs) if (!p) { g_last_error = "inference allocation failed"; act_cap = 0; return SQUINT_ENOMEM; }
+    if (cudaMallocHost(&h_req, req_bytes) != cudaSuccess) { act_cap = 0; return SQUINT_ENOMEM; }
+    act_cap = cap;
+    req_cap = rcap;
+    req_event_live = false;
+    return SQUINT_OK;
+}
+
+int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t s, int64_t* version_used) {
+    std::lock_guard<std::mutex> lk(act_mu);
+    int rows = 0;
+    for (int q = 0; q < n_reqs; ++q) {
+        const squint_act_request& rq = reqs[q];
+        if (rq.n < 1 || !rq.obs || !rq.proprio || !rq.actions || (rq.mode != 0 && rq.mode != 1)) {
+            g_last_error = "invalid inference request";
+            return SQUINT_EINVAL;
+        }
+        rows += rq.n;
+    }
+    if (rows == 0) return SQUINT_OK;
+    int rc = ensure_act_capacity(rows, n_reqs);
+    if (rc != SQUINT_OK) return rc;
+    if (req_event_live) SQ_CK(this, cudaEventSynchronize(req_event));
+    // pack: row_req[cap] row_in[cap] | obs[rcap] prop[rcap] act[rcap] key[rcap] (8 B each) | mode[rcap]
+    uint8_t* hb = static_cast<uint8_t*>(h_req);
+    int32_t* row_req = reinterpret_cast<int32_t*>(hb);
+    int32_t* row_in = row_req + act_cap;
+    uint64_t* p64 = reinterpret_cast<uint64_t*>(hb + (size_t)act_cap * 8);
+    int32_t* modes = reinterpret_cast<int32_t*>(p64 + 4 * (size_t)req_cap);
+    int r = 0;
+    for (int q = 0; q < n_reqs; ++q) {
+        for (int i = 0; i < reqs[q].n; ++i, ++r) { row_req[r] = q; row_in[r] = i; }
+        p64[q] = (uint64_t)(uintptr_t)reqs[q].obs;
+        p64[req_cap + q] = (uint64_t)(uintptr_t)reqs[q].proprio;
+        p64[2 * req_cap + q] = (uint64_t)(uintptr_t)reqs[q].actions;
+        p64[3 * req_cap + q] = reqs[q].rng_key;
+        modes[q] = reqs[q].mode;
+    }
+    SQ_CK(this, cudaMemcpyAsync(d_req, h_req, req_bytes, cudaMemcpyHostToDevice, s));
+    SQ_CK(this, cudaEventRecord(req_event, s));
+    req_event_live = true;
+    uint8_t* db = static_cast<uint8_t*>(d_req);
+    const int32_t* d_row_req = reinterpret_cast<const int32_t*>(db);
+    const int32_t* d_row_in = d_row_req + act_cap;
+    const uint64_t* d64 = reinterpret_cast<const uint64_t*>(db + (size_t)act_cap * 8);
+    const int32_t* d_modes = reinterpret_cast<const int32_t*>(d64 + 4 * (size_t)req_cap);
+
+    const int pi = policy_active;
+    const float* Wp = policy_buf[pi];
+    SQ_CK(this, cudaStreamWaitEvent(s, policy_ready[pi], 0));
+    if (version_used) *version_used = policy_version;
+
+    const int F = L.feat, Da = L.da, Dd = L.D, A = c.action_dim;
+    ActFrontArgs af{};
+    af.obs = reinterpret_cast<const uint8_t* const*>(d64);
+    af.prop = reinterpret_cast<const float* const*>(d64 + req_cap);
+    af.row_req = d_row_req; af.row_in_req = d_row_in;
+    af.rows = rows; af.C = c.obs_c; af.H = c.obs_h; af.W = c.obs_w; af.f = c.squint_f; af.P = c.proprio_dim;
+    af.x = ax; af.xin = axin; af.ld_xin = Da; af.col = L.zdim;
+    launch_act_frontend(af, s);
+    const float* in = ax;
+    for (size_t l = 0; l < L.conv.size(); ++l) {
+        const ConvL& cv = L.conv[l];
+        ConvShape sh{rows, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
+                     (int64_t)cv.cout * cv.oh * cv.ow};
+        launch_conv_fwd<float>(sh, in, Wp + cv.wo, Wp + cv.bo, aconv[l], true, s);
+        in = aconv[l];
+    }
+    if (Dd > 0) {
+        GemmProblem g = lin_fwd(in, F, rows, Wp + L.aproj.w, Wp + L.aproj.b, F, Dd, apre, Dd);
+        launch_gemm<float>(&g, 1, kKK, s);
+        LnProblem p{};
+        p.rows = rows; p.n = Dd; p.pre = apre; p.ld_pre = Dd;
+        p.g = Wp + L.aproj.g; p.beta = Wp + L.aproj.beta;
+        p.out = axin; p.ld_out = Da; p.mean = amean; p.rstd = arstd;
+        launch_ln_fwd(&p, 1, false, (float)c.ln_eps, s);
+    } else {
+        SQ_CK(this, cudaMemcpy2DAsync(axin, Da * sizeof(float), in, F * sizeof(float), F * sizeof(float), rows,
+                                      cudaMemcpyDeviceToDevice, s));
+    }
+    const MlpRef actor_ref = mlp_ref(this, L.actor, false, Wp);
+    mlp_forward(this, act_mlp, &actor_ref, 1, Mat{axin, Da, nullptr, 0}, rows, false, s);
+    ActHeadArgs ha{};
+    ha.rows = rows; ha.A = A; ha.out = act_mlp.out; ha.ld_out = 2 * A;
+    ha.row_req = d_row_req; ha.row_in_req = d_row_in;
+    ha.req_key = d64 + 3 * req_cap; ha.req_mode = d_modes;
+    ha.req_actions = reinterpret_cast<float* const*>(d64 + 2 * req_cap);
+    ha.lo = (float)c.log_std_min; ha.hi = (float)c.log_std_max; ha.seed = c.seed;
+    launch_act_head(ha, s);
+    SQ_CK(this, cudaEventRecord(policy_released[pi], s));
+    SQ_CK(this, cudaGetLastError());
+    return SQUINT_OK;
+}
+

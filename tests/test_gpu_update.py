@@ -206,3 +206,59 @@ def test_errors_are_codes_not_crashes(L):
     with pytest.raises(L.SquintError):
         learner.set_params(np.zeros(3, dtype=np.float32))
     learner.close()
+
+
+# ---------------------------------------------------------------- BF16 tensor-core path
+# Per-quantity bounds for BF16 operands with FP32 accumulation (relative, or absolute
+# below 1 for the actor loss): Q-mean 2e-2, critic CE 1e-2, actor loss 3e-2,
+# gradient norm 5e-2; gradients must also point the same way (cosine > 0.98).
+BF16_BOUNDS = dict(q_mean=2e-2, critic_loss=1e-2, actor_loss=3e-2, grad_norm=5e-2)
+
+
+def _bf16_close(key, got, ref):
+    tol = BF16_BOUNDS[key]
+    if key == "actor_loss" and abs(ref) < 1:
+        return abs(got - ref) <= tol
+    return abs(got - ref) <= tol * abs(ref) + 1e-6
+
+
+@pytest.mark.parametrize("name", ["small_b32", "tiny_b8", "train_b512"])
+def test_bf16_update_within_stated_bounds(L, name):
+    cfg = synth.make_config(name)
+    if name == "train_b512":
+        ring = synth.make_ring(cfg, 0, device="cuda")
+        ring_np = lazy_ring(ring)
+    else:
+        ring_cpu = synth.make_ring(cfg, 0)
+        ring = ring_to_device(ring_cpu)
+        ring_np = synth.ring_numpy(ring_cpu)
+    learner = L.Learner(cfg, ring, precision=L.PREC_BF16)
+    state = o.init_state(cfg)
+    stats = learner.update(1, graph=True)[0]
+    ref, tr = o.update(state, ring_np, cfg)
+    for key in ("q_mean", "critic_loss", "actor_loss"):
+        assert _bf16_close(key, stats[key], ref[key]), (key, stats[key], ref[key])
+    g = split_params(learner.debug("grads"), cfg)
+    ref_grads = dict(tr["critic"]["grads"])
+    ref_grads.update(tr["actor"]["grads"])
+    for k, v in ref_grads.items():
+        n_got, n_ref = np.linalg.norm(g[k]), np.linalg.norm(v)
+        assert abs(n_got - n_ref) <= BF16_BOUNDS["grad_norm"] * n_ref + 1e-7, (k, n_got, n_ref)
+        cos = float((g[k].ravel() @ v.ravel()) / max(n_got * n_ref, 1e-30))
+        assert cos > 0.98 or n_ref < 1e-6, (k, cos)
+    more = learner.update(4, graph=True)
+    assert all(np.isfinite([s["critic_loss"], s["actor_loss"], s["q_mean"]]).all() for s in more)
+    learner.close()
+
+
+def test_bf16_graph_equals_eager_bitwise(L):
+    cfg = synth.make_config("small_b32")
+    ring = ring_to_device(synth.make_ring(cfg, 0))
+    a = L.Learner(cfg, ring, precision=L.PREC_BF16)
+    b = L.Learner(cfg, ring, precision=L.PREC_BF16)
+    sa = a.update(3, graph=True)
+    sb = b.update(3, graph=False)
+    assert sa == sb
+    assert np.array_equal(a.params(), b.params())
+    a.close()
+    b.close()
