@@ -52,6 +52,30 @@ int squint_op_conv3x3_bwd(int dtype, int nimg, int cin, int h, int w, int cout, 
                           const void* wt, const void* dy, void* dx, const void* dx_mask, void* dw, void* db,
                           void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Tensor-core convolutions of the encoder's 32 -> 32 channel, stride-1 layers on the
+ * padded-HWC BF16 format: per image (H+4) x (W+4) rows of 32 channels, the pixel
+ * (y, x) at row (y+2)(W+4) + x+2, zeros on the 2-pixel border (buffers the caller
+ * zero-fills once).
+ * to/from: NCHW FP32 [nimg, 32, H, W] <-> padded-HWC BF16 (interior only).
+ */
+int squint_op_to_phwc(int nimg, int H, int W, const float* src, void* dst, void* stream);
+int squint_op_from_phwc(int nimg, int H, int W, const void* src, float* dst, void* stream);
+/* FP32 filter [32, 32, 3, 3] -> BF16 forward and data-gradient layouts (18432 bytes each). */
+int squint_op_conv32_layouts(const float* w, void* fwd_layout, void* dgrad_layout, void* stream);
+/*
+ * mode 0 (forward): x padded [nimg, H, W] -> y (H-2 x W-2): bias, ReLU if relu;
+ * writes padded y (out_phwc, may be NULL) and/or NCHW FP32 y (out_nchw, may be NULL).
+ * mode 1 (data gradient): `in` = padded dy [nimg, H, W] -> dx (H+2 x W+2), zeroed where
+ * mask (padded activation of size H+2 x W+2) <= 0 when mask is given.
+ */
+int squint_op_conv32(int mode, int nimg, int H, int W, const void* in, const void* w_layout, const float* bias,
+                     int relu, const void* mask, void* out_phwc, float* out_nchw, void* stream);
+/* Weight gradient: x padded [nimg, H, W], dy padded [nimg, H-2, W-2] -> dw [32,32,3,3], db [32]. */
+size_t squint_op_wgrad32_workspace(int nimg);
+int squint_op_wgrad32(int nimg, int H, int W, const void* x, const void* dy, float* dw, float* db, void* work,
+                      size_t work_bytes, void* stream);
+
 /* LayerNorm over rows of n (Sec. IV "Normalization"), FP32: y = g (x - mean) rstd + b, ReLU if relu. */
 int squint_op_layernorm_fwd(int rows, int n, const float* x, const float* g, const float* b, float eps, int relu,
                             float* y, float* mean, float* rstd, void* stream);

@@ -1,0 +1,531 @@
+// Tensor-core (tcgen05) 3x3 convolutions for 32 -> 32 channels, stride 1: the
+// forward, the data gradient and the weight gradient of the encoder's inner layers.
+//
+// Activation format between these layers: "padded HWC" BF16 - per image (H+4) x (W+4)
+// rows of 32 channels (64 B), the valid pixels at rows (y+2)(W+4) + x+2, zeros
+// elsewhere.  On a virtual output grid that keeps the input's row width Wp, output
+// pixel q = oy Wp + ox reads input row q + origin(ky, kx), so each of the nine
+// taps is the same shared-memory image seen from a shifted start row: the A
+// operand of tap (ky, kx) is a descriptor whose start address moves by
+// origin(ky, kx) rows, with no im2col copy.  Columns ox >= out_w of the virtual
+// grid are computed and discarded.
+//
+// Shared-memory operand layout: the canonical no-swizzle K-major layout with
+// channels split into 4 planes of 8 (16 B per pixel row per plane): element
+// (row r, channel c) at (c / 8) * PLANE + r * 16 + (c % 8) * 2.  Any start row is a
+// valid descriptor start.  TMA loads each plane of an image box by box.
+#include "sq_tc.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+namespace sq {
+
+namespace {
+
+constexpr long long kWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
+constexpr int kCh = 32;                            // channels in and out
+constexpr int kWBytes = 9 * kCh * kCh * 2;         // 18432 B: one layer's filter in BF16
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > kWaitCycles) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+            "r"(dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"((uint64_t)src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+// No-swizzle shared-memory descriptor (core matrices of 8 rows x 16 B).  K-major operand:
+// lbo = stride between core matrices along K, sbo = along M/N.  MN-major operand:
+// lbo = stride along K, sbo = along M/N (checked against the oracle's convolution).
+__device__ __forceinline__ uint64_t plain_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t cols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(cols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols));
+}
+
+// ---------------------------------------------------------------- forward / data gradient
+struct ConvArgs {
+    CUtensorMap tin;                 // input planes: dims {8, 4, nimg * in_rows}
+    const __nv_bfloat16* w;          // filter, layout [tap][plane][out ch][8]
+    int nimg, in_rows, Wp, out_h, out_w, off0, n_tiles, load_rows, tmem_cols;
+    const float* bias;               // forward: bias[out ch]
+    int relu;
+    const __nv_bfloat16* mask;       // data gradient: padded-HWC activation of the layer below (mask > 0)
+    __nv_bfloat16* out_phwc;         // padded-HWC output (grid width out_w + 4), interior written
+    float* out_chw;                  // optional CHW FP32 output [nimg, 32, out_h, out_w]
+    __nv_bfloat16* out_chw_bf;       // optional CHW BF16 copy
+    int* err;
+};
+
+__global__ void __launch_bounds__(128) conv32_tc_kernel(const __grid_constant__ ConvArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t plane = (uint32_t)a.load_rows * 16;
+    uint8_t* img_s = smem;
+    uint8_t* w_s = smem + 4 * plane;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(w_s + kWBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    const uint32_t load_bar = smem_u32(bars), mma_bar = smem_u32(bars + 1);
+    const int img = blockIdx.x;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
+    if (threadIdx.x == 32) {
+        mbar_init(load_bar, 1);
+        mbar_init(mma_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t img_u = smem_u32(img_s), w_u = smem_u32(w_s);
+
+    if (threadIdx.x == 0) {
+        const int boxes = a.load_rows / 128;
+        mbar_expect_tx(load_bar, 4 * plane + kWBytes);
+        for (int c = 0; c < 4; ++c)
+            for (int b = 0; b < boxes; ++b)
+                tma_load_3d(img_u + c * plane + b * 2048, &a.tin, 0, c, img * a.in_rows + b * 128, load_bar);
+        bulk_load(w_u, a.w, kWBytes, load_bar);
+    } else if (threadIdx.x == 32) {
+        constexpr uint32_t idesc = idesc_bf16(128, kCh, false, false);
+        if (mbar_wait(load_bar, 0, a.err, 11)) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (int t = 0; t < a.n_tiles; ++t) {
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int row0 = t * 128 + a.off0 + (tap / 3) * a.Wp + (tap % 3);
+                    for (int kc = 0; kc < 2; ++kc) {
+                        const uint64_t ad = plain_desc(img_u + 2 * kc * plane + row0 * 16, plane, 128);
+                        const uint64_t bd = plain_desc(w_u + tap * 2048 + 2 * kc * 512, 512, 128);
+                        mma_bf16(tmem + t * kCh, ad, bd, idesc, (tap | kc) ? 1u : 0u);
+                    }
+                }
+            }
+        }
+        mma_commit(mma_bar);
+    }
+    __syncwarp();
+    const bool have = mbar_wait(mma_bar, 0, a.err, 12);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int wpo = a.out_w + 4;
+    const int64_t out_img = (int64_t)(a.out_h + 4) * wpo * kCh;
+    for (int t = 0; t < a.n_tiles; ++t) {
+        uint32_t r0[16], r1[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + t * kCh;
+        tmem_ld16(taddr, r0);
+        tmem_ld16(taddr + 16, r1);
+        const int q = t * 128 + warp * 32 + lane;
+        const int oy = q / a.Wp, ox = q - (q / a.Wp) * a.Wp;
+        if (!have || oy >= a.out_h || ox >= a.out_w) continue;
+        float v[kCh];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) { v[j] = __uint_as_float(r0[j]); v[16 + j] = __uint_as_float(r1[j]); }
+        const int64_t prow = ((int64_t)(oy + 2) * wpo + ox + 2) * kCh;
+        if (a.bias) {
+#pragma unroll
+            for (int j = 0; j < kCh; ++j) v[j] += a.bias[j];
+        }
+        if (a.relu) {
+#pragma unroll
+            for (int j = 0; j < kCh; ++j) v[j] = fmaxf(v[j], 0.f);
+        }
+        if (a.mask) {
+            const uint4* mk = reinterpret_cast<const uint4*>(a.mask + (int64_t)img * out_img + prow);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const uint4 m4 = mk[c];
+                const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m4);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (!(__bfloat162float(mb[j]) > 0.f)) v[c * 8 + j] = 0.f;
+            }
+        }
+        if (a.out_phwc) {
+            uint4* dst = reinterpret_cast<uint4*>(a.out_phwc + (int64_t)img * out_img + prow);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                __align__(16) __nv_bfloat16 hb[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) hb[j] = __float2bfloat16_rn(v[c * 8 + j]);
+                dst[c] = *reinterpret_cast<const uint4*>(hb);
+            }
+        }
+        if (a.out_chw || a.out_chw_bf) {
+            const int64_t plane_px = (int64_t)a.out_h * a.out_w;
+            const int64_t base = (int64_t)img * kCh * plane_px + (int64_t)oy * a.out_w + ox;
+#pragma unroll
+            for (int j = 0; j < kCh; ++j) {
+                if (a.out_chw) a.out_chw[base + j * plane_px] = v[j];
+                if (a.out_chw_bf) a.out_chw_bf[base + j * plane_px] = __float2bfloat16_rn(v[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem_dealloc(tmem, a.tmem_cols);
+    }
+}
+
+// ---------------------------------------------------------------- weight gradient
+// D_tap[co, ci] += sum_q dy[q, co] x[q + origin(tap), ci] over the virtual grid of
+// the input's padded row width (dy = 0 outside the valid outputs).  A = dy^T staged
+// by the threads K-major (q-chunks of 8, 512 B apart: rows 32..127 of the 128-row MMA
+// alias later chunks and land in accumulator rows that are never read); B = the x
+// window, MN-major: channel planes (8 channels) PLANE apart, K groups of 8 pixel rows
+// 128 B apart.  Nine 32-column accumulators.
+struct WgradArgs {
+    CUtensorMap tin;                 // layer input planes, dims {8, 4, nimg * in_rows}
+    const __nv_bfloat16* dy;         // padded-HWC gradient at the layer's pre-activation (grid out_w + 4)
+    int nimg, in_rows, Wp, out_h, out_w, kq, load_rows, per_cta;
+    float* work;                     // [ctas, 32, 289]: partial dW (co, ci*9 + tap) and db (col 288)
+    int* err;
+};
+
+constexpr int kDyBytesMax = 32768;
+
+__global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__ WgradArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t plane = (uint32_t)a.load_rows * 16;
+    const uint32_t xbytes = 4 * plane;
+    const uint32_t dybytes = (uint32_t)(a.kq / 8) * 512 + 2048;   // + slack read by the aliased rows
+    uint8_t* xs[2] = {smem, smem + xbytes};
+    uint8_t* ds[2] = {smem + 2 * xbytes, smem + 2 * xbytes + dybytes};
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * xbytes + 2 * dybytes);
+    float* red = reinterpret_cast<float*>(bars + 8);             // [128][8] bias partials
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(red + 128 * 8);
+    const uint32_t tma_bar[2] = {smem_u32(bars), smem_u32(bars + 1)};
+    const uint32_t mma_bar[2] = {smem_u32(bars + 2), smem_u32(bars + 3)};
+    const uint32_t done_bar = smem_u32(bars + 4);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int i0 = blockIdx.x * a.per_cta, i1 = min(a.nimg, i0 + a.per_cta);
+
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), 512);
+    if (threadIdx.x == 32) {
+        for (int b = 0; b < 2; ++b) { mbar_init(tma_bar[b], 1); mbar_init(mma_bar[b], 1); }
+        mbar_init(done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // slack after each dy^T buffer is read by aliased rows only; keep it finite
+    for (int i = threadIdx.x; i < 2048 / 4; i += blockDim.x) {
+        reinterpret_cast<float*>(ds[0] + dybytes - 2048)[i] = 0.f;
+        reinterpret_cast<float*>(ds[1] + dybytes - 2048)[i] = 0.f;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int wpo = a.out_w + 4;
+    const int64_t dy_img = (int64_t)(a.out_h + 4) * wpo * kCh;
+    float bsum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int cc = threadIdx.x % 4;         // the 8-channel chunk this thread stages
+    bool ok = true;
+    constexpr uint32_t idesc = idesc_bf16(128, kCh, false, true);
+
+    // Every thread runs every iteration (the barriers inside must match); a wait that
+    // gives up only records the error and stops further MMA issue.
+    for (int i = i0; i < i1; ++i) {
+        const int li = i - i0, b = li & 1;
+        if (li >= 2 && !mbar_wait(mma_bar[b], ((li - 2) >> 1) & 1, a.err, 21)) ok = false;
+        if (threadIdx.x == 0 && ok) {
+            const int boxes = a.load_rows / 128;
+            mbar_expect_tx(tma_bar[b], xbytes);
+            for (int c = 0; c < 4; ++c)
+                for (int bb = 0; bb < boxes; ++bb)
+                    tma_load_3d(smem_u32(xs[b]) + c * plane + bb * 2048, &a.tin, 0, c, i * a.in_rows + bb * 128,
+                                tma_bar[b]);
+        }
+        // stage dy^T: element (co, q) at (q / 8) * 512 + co * 16 + (q % 8) * 2
+        uint8_t* d = ds[b];
+        for (int j = threadIdx.x; j < a.kq * 4; j += blockDim.x) {
+            const int q = j >> 2;
+            const int oy = q / a.Wp, ox = q - (q / a.Wp) * a.Wp;
+            uint4 v4 = make_uint4(0, 0, 0, 0);
+            if (oy < a.out_h && ox < a.out_w)
+                v4 = *reinterpret_cast<const uint4*>(a.dy + (int64_t)i * dy_img +
+                                                     ((int64_t)(oy + 2) * wpo + ox + 2) * kCh + cc * 8);
+            const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v4);
+            uint8_t* col = d + (q >> 3) * 512 + (q & 7) * 2;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                *reinterpret_cast<__nv_bfloat16*>(col + (cc * 8 + k) * 16) = hv[k];
+                bsum[k] += __bfloat162float(hv[k]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 32) {
+            if (!ok || !mbar_wait(tma_bar[b], (li >> 1) & 1, a.err, 22)) {
+                ok = false;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t xu = smem_u32(xs[b]), du = smem_u32(ds[b]);
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int org = (2 + tap / 3) * a.Wp + 2 + tap % 3;
+                    for (int k = 0; k < a.kq / 16; ++k) {
+                        const uint64_t ad = plain_desc(du + k * 1024, 512, 128);
+                        const uint64_t bd = plain_desc(xu + (k * 16 + org) * 16, 128, plane);
+                        mma_bf16(tmem + tap * kCh, ad, bd, idesc, (i > i0 || k > 0) ? 1u : 0u);
+                    }
+                }
+            }
+            mma_commit(mma_bar[b]);
+        }
+        __syncwarp();
+    }
+    if (threadIdx.x == 32) mma_commit(done_bar);
+    __syncwarp();
+    const bool have = mbar_wait(done_bar, 0, a.err, 23) && ok && i1 > i0;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // bias partials: reduce the 32 threads of each chunk in a fixed order
+#pragma unroll
+    for (int k = 0; k < 8; ++k) red[threadIdx.x * 8 + k] = bsum[k];
+    __syncthreads();
+    float* out = a.work + (int64_t)blockIdx.x * kCh * (kCh * 9 + 1);
+    if (threadIdx.x < kCh) {
+        const int co = threadIdx.x;
+        float s = 0.f;
+        for (int t = co / 8; t < 128; t += 4) s += red[t * 8 + (co % 8)];
+        out[co * (kCh * 9 + 1) + kCh * 9] = s;
+    }
+    if (warp == 0) {
+        const int co = lane;
+        for (int tap = 0; tap < 9; ++tap) {
+            uint32_t r0[16], r1[16];
+            tmem_ld16(tmem + tap * kCh, r0);
+            tmem_ld16(tmem + tap * kCh + 16, r1);
+            for (int j = 0; j < 16; ++j) {
+                out[co * (kCh * 9 + 1) + j * 9 + tap] = have ? __uint_as_float(r0[j]) : 0.f;
+                out[co * (kCh * 9 + 1) + (16 + j) * 9 + tap] = have ? __uint_as_float(r1[j]) : 0.f;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+__global__ void wgrad32_reduce_kernel(const float* __restrict__ work, int splits, float* __restrict__ dw,
+                                      float* __restrict__ db) {
+    constexpr int N = kCh * 9 + 1;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kCh * N) return;
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += work[(int64_t)z * kCh * N + e];
+    const int co = e / N, col = e - co * N;
+    if (col == N - 1) db[co] = s;
+    else dw[co * (N - 1) + col] = s;
+}
+
+// ---------------------------------------------------------------- layout conversions
+// CHW FP32 (per image stride img_stride) -> padded HWC BF16 interior.
+__global__ void to_phwc_kernel(const float* __restrict__ src, int64_t img_stride, int nimg, int H, int W,
+                               __nv_bfloat16* __restrict__ dst) {
+    const int64_t n = (int64_t)nimg * H * W;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int img = (int)(p / (H * W));
+    const int rem = (int)(p - (int64_t)img * H * W);
+    const int y = rem / W, x = rem - (rem / W) * W;
+    const float* s = src + img * img_stride + rem;
+    __nv_bfloat16* d = dst + ((int64_t)img * (H + 4) * (W + 4) + (int64_t)(y + 2) * (W + 4) + x + 2) * kCh;
+    __align__(16) __nv_bfloat16 hb[kCh];
+#pragma unroll
+    for (int c = 0; c < kCh; ++c) hb[c] = __float2bfloat16_rn(s[(int64_t)c * H * W]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) reinterpret_cast<uint4*>(d)[c] = reinterpret_cast<const uint4*>(hb)[c];
+}
+
+// Padded HWC BF16 interior -> NCHW FP32.
+__global__ void from_phwc_kernel(const __nv_bfloat16* __restrict__ src, int nimg, int H, int W, float* __restrict__ dst) {
+    const int64_t n = (int64_t)nimg * kCh * H * W;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int img = (int)(e / ((int64_t)kCh * H * W));
+    const int rem = (int)(e - (int64_t)img * kCh * H * W);
+    const int c = rem / (H * W), p = rem - (rem / (H * W)) * (H * W);
+    const int y = p / W, x = p - (p / W) * W;
+    dst[e] = __bfloat162float(src[((int64_t)img * (H + 4) * (W + 4) + (int64_t)(y + 2) * (W + 4) + x + 2) * kCh + c]);
+}
+
+// FP32 filter w[co][ci][ky][kx] -> forward layout [tap][ci/8][co][ci%8] and data-gradient
+// layout (tap' = 8 - tap, channels swapped) [tap'][co/8][ci][co%8].
+__global__ void conv_weight_cast_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ fwd,
+                                        __nv_bfloat16* __restrict__ bwd) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kCh * kCh * 9) return;
+    const int co = e / (kCh * 9), rem = e - co * kCh * 9, ci = rem / 9, tap = rem - (rem / 9) * 9;
+    const __nv_bfloat16 v = __float2bfloat16_rn(w[e]);
+    fwd[tap * kCh * kCh + (ci / 8) * kCh * 8 + co * 8 + (ci % 8)] = v;
+    bwd[(8 - tap) * kCh * kCh + (co / 8) * kCh * 8 + ci * 8 + (co % 8)] = v;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Planes of a padded-HWC tensor: dims {8 channels, 4 planes, rows}, box {8, 1, 128}.
+bool plane_map(CUtensorMap* m, const __nv_bfloat16* base, int64_t rows) {
+    auto fn = encode_fn();
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    cuuint64_t dims[3] = {8, 4, (cuuint64_t)rows};
+    cuuint64_t strides[2] = {16, 64};
+    cuuint32_t box[3] = {8, 1, 128};
+    cuuint32_t estr[3] = {1, 1, 1};
+    std::memset(m, 0, sizeof(*m));
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+size_t conv_smem(int load_rows) { return 1024 + 4 * (size_t)load_rows * 16 + kWBytes + 64; }
+size_t wgrad_smem(int load_rows, int kq) {
+    return 1024 + 2 * (4 * (size_t)load_rows * 16) + 2 * ((size_t)(kq / 8) * 512 + 2048) + 64 + 128 * 8 * 4 + 16;
+}
+
+}  // namespace
+
+// Geometry of one call: the conv reads input rows up to (n_tiles * 128 - 1) + off0 + 2 Wp + 2.
+int launch_conv32_tc(const ConvTc& c, int* err, cudaStream_t s) {
+    if (c.nimg <= 0) return 0;
+    ConvArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const int mv = c.out_h * c.Wp;
+    a.n_tiles = (mv + 127) / 128;
+    if (a.n_tiles > 4) return -1;
+    a.tmem_cols = a.n_tiles <= 1 ? 32 : (a.n_tiles <= 2 ? 64 : 128);
+    const int max_row = a.n_tiles * 128 - 1 + c.off0 + 2 * c.Wp + 2;
+    a.load_rows = round_up(max_row + 1, 128);
+    if (conv_smem(a.load_rows) > 200 * 1024) return -1;
+    if (!plane_map(&a.tin, c.in, (int64_t)c.nimg * c.in_rows)) return -2;
+    a.w = c.w; a.nimg = c.nimg; a.in_rows = c.in_rows; a.Wp = c.Wp; a.out_h = c.out_h; a.out_w = c.out_w;
+    a.off0 = c.off0; a.bias = c.bias; a.relu = c.relu; a.mask = c.mask; a.out_phwc = c.out_phwc;
+    a.out_chw = c.out_chw; a.out_chw_bf = c.out_chw_bf; a.err = err;
+    const size_t smem = conv_smem(a.load_rows);
+    conv32_tc_kernel<<<c.nimg, 128, smem, s>>>(a);
+    return 0;
+}
+
+int64_t wgrad32_tc_workspace(int nimg) { return (int64_t)std::min(nimg, 148) * kCh * (kCh * 9 + 1); }
+
+int launch_wgrad32_tc(const WgradTc& c, float* work, float* dw, float* db, int* err, cudaStream_t s) {
+    if (c.nimg <= 0) return 0;
+    WgradArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.kq = round_up(c.out_h * c.Wp, 16);
+    const int max_row = a.kq - 1 + (4 * c.Wp + 4);
+    a.load_rows = round_up(std::max(max_row + 1, c.in_rows), 128);
+    if (wgrad_smem(a.load_rows, a.kq) > 220 * 1024 || (a.kq / 8) * 512 + 2048 > kDyBytesMax + 2048) return -1;
+    if (!plane_map(&a.tin, c.x, (int64_t)c.nimg * c.in_rows)) return -2;
+    const int ctas = std::min(c.nimg, 148);
+    a.per_cta = (c.nimg + ctas - 1) / ctas;
+    const int grid = (c.nimg + a.per_cta - 1) / a.per_cta;
+    a.dy = c.dy; a.nimg = c.nimg; a.in_rows = c.in_rows; a.Wp = c.Wp; a.out_h = c.out_h; a.out_w = c.out_w;
+    a.work = work; a.err = err;
+    wgrad32_tc_kernel<<<grid, 128, wgrad_smem(a.load_rows, a.kq), s>>>(a);
+    wgrad32_reduce_kernel<<<(kCh * (kCh * 9 + 1) + 255) / 256, 256, 0, s>>>(work, grid, dw, db);
+    return 0;
+}
+
+void conv_tc_prepare() {
+    cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(wgrad32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    encode_fn();
+}
+
+void launch_to_phwc(const float* src, int64_t img_stride, int nimg, int H, int W, __nv_bfloat16* dst, cudaStream_t s) {
+    const int64_t n = (int64_t)nimg * H * W;
+    if (n) to_phwc_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(src, img_stride, nimg, H, W, dst);
+}
+void launch_from_phwc(const __nv_bfloat16* src, int nimg, int H, int W, float* dst, cudaStream_t s) {
+    const int64_t n = (int64_t)nimg * kCh * H * W;
+    if (n) from_phwc_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, nimg, H, W, dst);
+}
+void launch_conv_weight_cast(const float* w, __nv_bfloat16* fwd, __nv_bfloat16* bwd, cudaStream_t s) {
+    conv_weight_cast_kernel<<<(kCh * kCh * 9 + 255) / 256, 256, 0, s>>>(w, fwd, bwd);
+}
+
+}  // namespace sq

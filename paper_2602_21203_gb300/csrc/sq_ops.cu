@@ -18,6 +18,7 @@ int* tc_error_flag() {
     std::call_once(once, [] {
         if (cudaMalloc(&flag, sizeof(int)) == cudaSuccess) cudaMemset(flag, 0, sizeof(int));
         tc_prepare();
+        conv_tc_prepare();
     });
     return flag;
 }
@@ -117,6 +118,69 @@ int squint_op_conv3x3_bwd(int dtype, int nimg, int cin, int h, int w, int cout, 
     } else {
         return SQUINT_EINVAL;
     }
+    return launch_status();
+}
+
+int squint_op_to_phwc(int nimg, int H, int W, const float* src, void* dst, void* stream) {
+    if (nimg < 0 || H < 1 || W < 1 || !src || !dst) return SQUINT_EINVAL;
+    launch_to_phwc(src, (int64_t)32 * H * W, nimg, H, W, (__nv_bfloat16*)dst, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int squint_op_from_phwc(int nimg, int H, int W, const void* src, float* dst, void* stream) {
+    if (nimg < 0 || H < 1 || W < 1 || !src || !dst) return SQUINT_EINVAL;
+    launch_from_phwc((const __nv_bfloat16*)src, nimg, H, W, dst, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int squint_op_conv32_layouts(const float* w, void* fwd_layout, void* dgrad_layout, void* stream) {
+    if (!w || !fwd_layout || !dgrad_layout) return SQUINT_EINVAL;
+    launch_conv_weight_cast(w, (__nv_bfloat16*)fwd_layout, (__nv_bfloat16*)dgrad_layout, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int squint_op_conv32(int mode, int nimg, int H, int W, const void* in, const void* w_layout, const float* bias,
+                     int relu, const void* mask, void* out_phwc, float* out_nchw, void* stream) {
+    if ((mode != 0 && mode != 1) || nimg < 0 || !in || !w_layout || (!out_phwc && !out_nchw)) return SQUINT_EINVAL;
+    if (mode == 0 && (H < 3 || W < 3 || !bias)) return SQUINT_EINVAL;
+    if (mode == 1 && (H < 1 || W < 1)) return SQUINT_EINVAL;
+    int* err = tc_error_flag();
+    if (!err) return SQUINT_ECUDA;
+    ConvTc c{};
+    c.in = (const __nv_bfloat16*)in;
+    c.nimg = nimg;
+    c.Wp = W + 4;
+    c.in_rows = (H + 4) * (W + 4);
+    c.out_h = mode == 0 ? H - 2 : H + 2;
+    c.out_w = mode == 0 ? W - 2 : W + 2;
+    c.off0 = mode == 0 ? 2 * c.Wp + 2 : 0;
+    c.w = (const __nv_bfloat16*)w_layout;
+    c.bias = mode == 0 ? bias : nullptr;
+    c.relu = mode == 0 ? relu : 0;
+    c.mask = (const __nv_bfloat16*)mask;
+    c.out_phwc = (__nv_bfloat16*)out_phwc;
+    c.out_chw = out_nchw;
+    if (launch_conv32_tc(c, err, (cudaStream_t)stream) != 0) return SQUINT_EINVAL;
+    return launch_status();
+}
+
+size_t squint_op_wgrad32_workspace(int nimg) { return nimg > 0 ? 4 * (size_t)wgrad32_tc_workspace(nimg) : 0; }
+
+int squint_op_wgrad32(int nimg, int H, int W, const void* x, const void* dy, float* dw, float* db, void* work,
+                      size_t work_bytes, void* stream) {
+    if (nimg < 1 || H < 3 || W < 3 || !x || !dy || !dw || !db || !work) return SQUINT_EINVAL;
+    if (work_bytes < squint_op_wgrad32_workspace(nimg)) return SQUINT_EINVAL;
+    int* err = tc_error_flag();
+    if (!err) return SQUINT_ECUDA;
+    WgradTc c{};
+    c.x = (const __nv_bfloat16*)x;
+    c.dy = (const __nv_bfloat16*)dy;
+    c.nimg = nimg;
+    c.Wp = W + 4;
+    c.in_rows = (H + 4) * (W + 4);
+    c.out_h = H - 2;
+    c.out_w = W - 2;
+    if (launch_wgrad32_tc(c, (float*)work, dw, db, err, (cudaStream_t)stream) != 0) return SQUINT_EINVAL;
     return launch_status();
 }
 

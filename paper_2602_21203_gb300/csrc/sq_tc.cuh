@@ -33,6 +33,39 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s);
 // Opt the kernels in to their shared memory and resolve the tensor-map encoder (call outside capture).
 void tc_prepare();
 
+// 3x3 convolution, 32 -> 32 channels, stride 1, on padded-HWC BF16 activations
+// (per image (H+4) x (W+4) rows of 32 channels, valid pixels at (y+2, x+2)).
+// Forward: in = padded input (grid width Wp = W+4, in_rows = (H+4) Wp), off0 = 2 Wp + 2,
+// w = forward filter layout.  Data gradient: in = padded gradient of the output
+// (Wp = OW+4), off0 = 0, w = data-gradient filter layout, mask = padded activation
+// below (outputs zeroed where it is <= 0).  Output pixel (oy, ox) < (out_h, out_w).
+struct ConvTc {
+    const __nv_bfloat16* in;
+    int nimg, in_rows, Wp, out_h, out_w, off0;
+    const __nv_bfloat16* w;
+    const float* bias;
+    int relu;
+    const __nv_bfloat16* mask;
+    __nv_bfloat16* out_phwc;
+    float* out_chw;
+    __nv_bfloat16* out_chw_bf;
+};
+int launch_conv32_tc(const ConvTc& c, int* err, cudaStream_t s);
+// Weight gradient: x = padded layer input (Wp = W+4), dy = padded gradient at the
+// layer's pre-activation (out_h x out_w); dw [32, 32, 3, 3] and db [32] written.
+struct WgradTc {
+    const __nv_bfloat16* x;
+    const __nv_bfloat16* dy;
+    int nimg, in_rows, Wp, out_h, out_w;
+};
+int64_t wgrad32_tc_workspace(int nimg);
+int launch_wgrad32_tc(const WgradTc& c, float* work, float* dw, float* db, int* err, cudaStream_t s);
+void conv_tc_prepare();
+void launch_to_phwc(const float* src, int64_t img_stride, int nimg, int H, int W, __nv_bfloat16* dst, cudaStream_t s);
+void launch_from_phwc(const __nv_bfloat16* src, int nimg, int H, int W, float* dst, cudaStream_t s);
+// FP32 filter [32, 32, 3, 3] -> BF16 forward and data-gradient layouts (18432 B each).
+void launch_conv_weight_cast(const float* w, __nv_bfloat16* fwd, __nv_bfloat16* bwd, cudaStream_t s);
+
 // FP32 rows -> BF16 rows of a padded matrix (columns cols..dst_ld-1 set to zero).
 struct CastItem { const float* src; int64_t src_ld; int rows, cols; __nv_bfloat16* dst; int64_t dst_ld; };
 void launch_cast_rows(const CastItem* items, int n, cudaStream_t s);

@@ -107,6 +107,12 @@ def load():
                                       ctypes.c_float, P, P]),
         "squint_op_tanh_gaussian_fwd": (I, [I, I, P, P, ctypes.c_float, ctypes.c_float, P, P, P]),
         "squint_op_tanh_gaussian_bwd": (I, [I, I, P, P, P, P, ctypes.c_float, ctypes.c_float, P, P]),
+        "squint_op_to_phwc": (I, [I, I, I, P, P, P]),
+        "squint_op_from_phwc": (I, [I, I, I, P, P, P]),
+        "squint_op_conv32_layouts": (I, [P, P, P, P]),
+        "squint_op_conv32": (I, [I, I, I, I, P, P, P, I, P, P, P, P]),
+        "squint_op_wgrad32_workspace": (SZ, [I]),
+        "squint_op_wgrad32": (I, [I, I, I, P, P, P, P, P, SZ, P]),
         "squint_strerror": (ctypes.c_char_p, [I]),
         "squint_last_error": (ctypes.c_char_p, []),
     }

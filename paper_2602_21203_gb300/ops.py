@@ -129,3 +129,60 @@ def tanh_gaussian_bwd(out, eps, da, dlogp, lo=-5.0, hi=2.0):
     _chk(_lib.load().squint_op_tanh_gaussian_bwd(rows, A, _p(out), _p(eps), _p(da), _p(dlogp), float(lo), float(hi),
                                                  _p(dout), _s()), "squint_op_tanh_gaussian_bwd")
     return dout
+
+
+# ---------------------------------------------------------------- tensor-core convolutions (32 -> 32, stride 1)
+def phwc_empty(nimg, H, W, device="cuda"):
+    """A zero-filled padded-HWC BF16 buffer for nimg images of H x W x 32."""
+    return torch.zeros(nimg, (H + 4) * (W + 4), 32, dtype=torch.bfloat16, device=device)
+
+
+def to_phwc(x):
+    n, c, H, W = x.shape
+    assert c == 32 and x.dtype == torch.float32
+    out = phwc_empty(n, H, W, x.device)
+    _chk(_lib.load().squint_op_to_phwc(n, H, W, _p(x.contiguous()), _p(out), _s()), "squint_op_to_phwc")
+    return out
+
+
+def from_phwc(t, H, W):
+    n = t.shape[0]
+    out = torch.empty(n, 32, H, W, device=t.device, dtype=torch.float32)
+    _chk(_lib.load().squint_op_from_phwc(n, H, W, _p(t), _p(out), _s()), "squint_op_from_phwc")
+    return out
+
+
+def conv32_layouts(w):
+    fwd = torch.empty(9 * 32 * 32, dtype=torch.bfloat16, device=w.device)
+    bwd = torch.empty_like(fwd)
+    _chk(_lib.load().squint_op_conv32_layouts(_p(w.contiguous()), _p(fwd), _p(bwd), _s()), "squint_op_conv32_layouts")
+    return fwd, bwd
+
+
+def conv32_fwd(x_phwc, H, W, w_fwd, bias, relu=True):
+    n = x_phwc.shape[0]
+    y = phwc_empty(n, H - 2, W - 2, x_phwc.device)
+    y_nchw = torch.empty(n, 32, H - 2, W - 2, device=x_phwc.device)
+    _chk(_lib.load().squint_op_conv32(0, n, H, W, _p(x_phwc), _p(w_fwd), _p(bias), int(relu), None, _p(y), _p(y_nchw),
+                                      _s()), "squint_op_conv32")
+    return y, y_nchw
+
+
+def conv32_dgrad(dy_phwc, H, W, w_bwd, mask_phwc=None):
+    n = dy_phwc.shape[0]
+    dx = phwc_empty(n, H + 2, W + 2, dy_phwc.device)
+    dx_nchw = torch.empty(n, 32, H + 2, W + 2, device=dy_phwc.device)
+    _chk(_lib.load().squint_op_conv32(1, n, H, W, _p(dy_phwc), _p(w_bwd), None, 0, _p(mask_phwc), _p(dx),
+                                      _p(dx_nchw), _s()), "squint_op_conv32")
+    return dx, dx_nchw
+
+
+def wgrad32(x_phwc, dy_phwc, H, W):
+    n = x_phwc.shape[0]
+    L = _lib.load()
+    work = torch.empty(max(L.squint_op_wgrad32_workspace(n), 16), dtype=torch.uint8, device=x_phwc.device)
+    dw = torch.empty(32, 32, 3, 3, device=x_phwc.device)
+    db = torch.empty(32, device=x_phwc.device)
+    _chk(L.squint_op_wgrad32(n, H, W, _p(x_phwc), _p(dy_phwc), _p(dw), _p(db), _p(work), work.numel(), _s()),
+         "squint_op_wgrad32")
+    return dw, db

@@ -173,3 +173,34 @@ def test_tanh_gaussian_matches_oracle(ops):
     dout = ops.tanh_gaussian_bwd(out.float().cuda(), eps.float().cuda(), da.float().cuda(), dl.float().cuda())
     ref = o.tanh_gaussian_bwd(da.numpy(), dl.numpy(), cache, cfg)
     assert _rel(dout.cpu().numpy(), ref) < 1e-5
+
+
+# ---------------------------------------------------------------- tensor-core convolutions
+@pytest.mark.parametrize("n,H", [(6, 15), (300, 13), (37, 11)])
+def test_conv32_tensor_core_matches_oracle(ops, n, H):
+    """32->32 stride-1 conv on tcgen05: forward (bias, ReLU), data gradient (ReLU mask of the
+    layer below), weight and bias gradient, each vs the FP64 oracle on BF16-exact inputs."""
+    g = torch.Generator().manual_seed(20 + H)
+    W = H
+    x = torch.randn(n, 32, H, W, generator=g).bfloat16().float()
+    w = (torch.randn(32, 32, 3, 3, generator=g) * 0.1).bfloat16().float()
+    b = torch.randn(32, generator=g)
+    dy = torch.randn(n, 32, H - 2, W - 2, generator=g).bfloat16().float()
+    xp = ops.to_phwc(x.cuda())
+    assert torch.equal(ops.from_phwc(xp, H, W).cpu(), x)
+    wf, wb = ops.conv32_layouts(w.cuda())
+    y_p, y = ops.conv32_fwd(xp, H, W, wf, b.cuda(), relu=True)
+    torch.cuda.synchronize()
+    xn, wn = x.double().numpy(), w.double().numpy()
+    ref = np.maximum(o.conv3x3_fwd(xn, wn, b.double().numpy(), 1), 0)
+    assert _rel(y.cpu().numpy(), ref) < 1e-5
+    assert torch.equal(ops.from_phwc(y_p, H - 2, W - 2).cpu(), y.cpu().bfloat16().float())
+    dyp = ops.to_phwc(dy.cuda())
+    dx_p, dx = ops.conv32_dgrad(dyp, H - 2, W - 2, wb, mask_phwc=xp)
+    torch.cuda.synchronize()
+    rdx, rdw, rdb = o.conv3x3_bwd(xn, wn, dy.double().numpy(), 1)
+    assert _rel(dx.cpu().numpy(), rdx * (xn > 0)) < 1e-5
+    dw, db = ops.wgrad32(xp, dyp, H, W)
+    torch.cuda.synchronize()
+    assert _rel(dw.cpu().numpy(), rdw) < 1e-5
+    assert _rel(db.cpu().numpy(), rdb) < 1e-5
