@@ -139,6 +139,13 @@ struct squint_handle {
     std::vector<__nv_bfloat16*> dpre_h;        // per hidden layer [E, B, n]
     __nv_bfloat16* dproj_h = nullptr;          // [B, D]
     __nv_bfloat16* dout_ah = nullptr;          // [B, 16]
+    // tensor-core convolutions (BF16 mode, inner layers 32 -> 32, stride 1)
+    bool tc_conv = false;
+    std::vector<__nv_bfloat16*> act_p;         // [l]: padded-HWC output of conv l (2B images), l < L-1
+    std::vector<__nv_bfloat16*> dact_p;        // [l]: padded-HWC gradient at conv l's pre-activation (B images)
+    __nv_bfloat16* dz_p = nullptr;             // padded-HWC gradient at the last conv's pre-activation
+    std::vector<__nv_bfloat16*> wconv_fwd, wconv_bwd;   // [l]: BF16 filter layouts (l >= 1)
+    float* wgrad_tc_work = nullptr;
 
     // inference
     int act_cap = 0;
@@ -178,6 +185,7 @@ struct squint_handle {
     int after_param_change();
     int run_updates(int k, squint_update_stats* stats, cudaStream_t s, bool use_graph);
     void record_update(int j, cudaStream_t s, bool debug);
+    void cast_conv_weights(cudaStream_t s);
     size_t state_bytes() const;
     int save_state(uint8_t* out);
     int load_state(const uint8_t* in);

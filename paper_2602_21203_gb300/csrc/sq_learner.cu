@@ -370,8 +370,46 @@ int squint_handle::allocate() {
         if (L.D > 0) dproj_h = dalloc<__nv_bfloat16>((int64_t)B * L.D);
         dout_ah = dalloc<__nv_bfloat16>((int64_t)B * pad8(2 * A));
     }
+    if (bf16) {
+        tc_conv = L.conv.size() >= 2;
+        for (size_t l = 1; l < L.conv.size(); ++l) {
+            const ConvL& cv = L.conv[l];
+            if (cv.cin != 32 || cv.cout != 32 || cv.s != 1) tc_conv = false;
+        }
+        if (L.conv[0].cout != 32) tc_conv = false;
+    }
+    if (tc_conv) {
+        const int nl = (int)L.conv.size();
+        for (int l = 0; l < nl - 1; ++l) {
+            const ConvL& cv = L.conv[l];
+            const int64_t img = (int64_t)(cv.oh + 4) * (cv.ow + 4) * 32;
+            act_p.push_back(dalloc<__nv_bfloat16>(2 * B * img));
+            dact_p.push_back(dalloc<__nv_bfloat16>(B * img));
+        }
+        const ConvL& last = L.conv.back();
+        dz_p = dalloc<__nv_bfloat16>((int64_t)B * (last.oh + 4) * (last.ow + 4) * 32);
+        wconv_fwd.assign(nl, nullptr);
+        wconv_bwd.assign(nl, nullptr);
+        for (int l = 1; l < nl; ++l) {
+            wconv_fwd[l] = dalloc<__nv_bfloat16>(9 * 32 * 32);
+            wconv_bwd[l] = dalloc<__nv_bfloat16>(9 * 32 * 32);
+        }
+        wgrad_tc_work = dalloc<float>(wgrad32_tc_workspace(B));
+    }
     for (void* p : allocations)
         if (!p) { g_last_error = "device allocation failed"; return SQUINT_ENOMEM; }
+    if (tc_conv) {
+        // padded buffers keep zero borders: only interiors are ever written
+        for (size_t l = 0; l < act_p.size(); ++l) {
+            const ConvL& cv = L.conv[l];
+            const int64_t img = (int64_t)(cv.oh + 4) * (cv.ow + 4) * 32;
+            SQ_CK(this, cudaMemset(act_p[l], 0, 2 * B * img * 2));
+            SQ_CK(this, cudaMemset(dact_p[l], 0, B * img * 2));
+        }
+        const ConvL& last = L.conv.back();
+        SQ_CK(this, cudaMemset(dz_p, 0, (size_t)B * (last.oh + 4) * (last.ow + 4) * 32 * 2));
+        conv_tc_prepare();
+    }
     if (bf16) {
         if (L.feat % 8) { g_last_error = "BF16 path needs a feature width divisible by 8"; return SQUINT_EINVAL; }
         auto item = [&](const Lin& ly, bool tgt) {
@@ -440,6 +478,7 @@ int squint_handle::after_param_change() {
         launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), 0);
         launch_cast_rows(cast_actor.data(), (int)cast_actor.size(), 0);
         launch_cast_rows(cast_target.data(), (int)cast_target.size(), 0);
+        cast_conv_weights(0);
         SQ_CK(this, cudaDeviceSynchronize());
     }
     ++policy_version;
@@ -483,15 +522,34 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     mark(s);
     // ---- a5: encoder on o_t (rows < B) and o_{t+1} (rows >= B)
     const float* in = x2;
-    for (size_t l = 0; l < L.conv.size(); ++l) {
+    const int nconv = (int)L.conv.size();
+    for (int l = 0; l < nconv; ++l) {
         const ConvL& cv = L.conv[l];
+        if (tc_conv && l > 0) {
+            ConvTc ct{};
+            ct.in = act_p[l - 1];
+            ct.nimg = 2 * B;
+            ct.Wp = cv.w + 4;
+            ct.in_rows = (cv.h + 4) * ct.Wp;
+            ct.out_h = cv.oh; ct.out_w = cv.ow;
+            ct.off0 = 2 * ct.Wp + 2;
+            ct.w = wconv_fwd[l];
+            ct.bias = W + cv.bo;
+            ct.relu = 1;
+            if (l < nconv - 1) ct.out_phwc = act_p[l];
+            else { ct.out_chw = conv_out[l]; ct.out_chw_bf = z_h; }
+            if (launch_conv32_tc(ct, d_err, s) != 0) launch_failed = true;
+            continue;
+        }
         ConvShape sh{2 * B, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
                      (int64_t)cv.cout * cv.oh * cv.ow};
         launch_conv_fwd<float>(sh, in, W + cv.wo, W + cv.bo, conv_out[l], true, s);
         in = conv_out[l];
+        if (tc_conv && l == 0)
+            launch_to_phwc(conv_out[0], (int64_t)cv.cout * cv.oh * cv.ow, 2 * B, cv.oh, cv.ow, act_p[0], s);
     }
     float* z = conv_out.back();                // [2B, F]
-    cast_rows(z, F, 2 * B, F, z_h, F);
+    if (!tc_conv) cast_rows(z, F, 2 * B, F, z_h, F);
     const Mat zt{z, F, z_h, F};
     const Mat zt1 = zt.rows(B);
 
@@ -606,7 +664,40 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         }
         mark(s);
         const float* cur = dz;
-        for (int l = (int)L.conv.size() - 1; l >= 0; --l) {
+        if (tc_conv) {
+            const ConvL& last = L.conv.back();
+            launch_to_phwc(dz, F, B, last.oh, last.ow, dz_p, s);
+            const __nv_bfloat16* cur_p = dz_p;
+            for (int l = nconv - 1; l >= 1; --l) {
+                const ConvL& cv = L.conv[l];
+                WgradTc wt{};
+                wt.x = act_p[l - 1];
+                wt.dy = cur_p;
+                wt.nimg = B;
+                wt.Wp = cv.w + 4;
+                wt.in_rows = (cv.h + 4) * wt.Wp;
+                wt.out_h = cv.oh; wt.out_w = cv.ow;
+                if (launch_wgrad32_tc(wt, wgrad_tc_work, G + cv.wo, G + cv.bo, d_err, s) != 0) launch_failed = true;
+                ConvTc ct{};
+                ct.in = cur_p;
+                ct.nimg = B;
+                ct.Wp = cv.ow + 4;
+                ct.in_rows = (cv.oh + 4) * ct.Wp;
+                ct.out_h = cv.h; ct.out_w = cv.w;
+                ct.off0 = 0;
+                ct.w = wconv_bwd[l];
+                ct.mask = act_p[l - 1];
+                ct.out_phwc = dact_p[l - 1];
+                if (launch_conv32_tc(ct, d_err, s) != 0) launch_failed = true;
+                cur_p = dact_p[l - 1];
+            }
+            const ConvL& c0 = L.conv[0];
+            launch_from_phwc(dact_p[0], B, c0.oh, c0.ow, dconv_a, s);
+            ConvShape sh{B, c0.cin, c0.h, c0.w, c0.cout, c0.s, c0.oh, c0.ow, (int64_t)c0.cin * c0.h * c0.w,
+                         (int64_t)c0.cout * c0.oh * c0.ow};
+            launch_conv_wgrad<float>(sh, dconv_a, x2, G + c0.wo, G + c0.bo, wgrad_work, s);
+        }
+        for (int l = tc_conv ? -1 : (int)L.conv.size() - 1; l >= 0; --l) {
             const ConvL& cv = L.conv[l];
             ConvShape sh{B, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
                          (int64_t)cv.cout * cv.oh * cv.ow};
@@ -628,6 +719,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
         launch_adam(ad, s);
         if (bf16) launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), s);
+        cast_conv_weights(s);
     }
     mark(s);
     // ---- a13: temperature
@@ -714,6 +806,12 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         if (bf16) launch_cast_rows(cast_target.data(), (int)cast_target.size(), s);
     }
     mark(s);
+}
+
+void squint_handle::cast_conv_weights(cudaStream_t s) {
+    if (!tc_conv) return;
+    for (size_t l = 1; l < L.conv.size(); ++l)
+        launch_conv_weight_cast(params + L.conv[l].wo, wconv_fwd[l], wconv_bwd[l], s);
 }
 
 int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s, bool use_graph) {
