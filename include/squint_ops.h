@@ -76,6 +76,27 @@ size_t squint_op_wgrad32_workspace(int nimg);
 int squint_op_wgrad32(int nimg, int H, int W, const void* x, const void* dy, float* dw, float* db, void* work,
                       size_t work_bytes, void* stream);
 
+/*
+ * Weight and bias gradient of the FP32 3x3 convolution (dw, db of
+ * squint_op_conv3x3_bwd) without any device allocation and without a caller
+ * workspace.  This entry point has no counterpart in the paper: it exists for
+ * callers that cannot allocate device memory when they need the gradient (a
+ * frozen or fully reserved memory pool, a real-time loop that forbids allocator
+ * calls and their synchronisation, a host with its own allocator).  Its split
+ * partial sums live in one fixed device array of squint_op_conv3x3_wgrad_noalloc_max()
+ * floats (4 MiB) that every device loading the library keeps until exit; shapes
+ * needing more return SQUINT_EINVAL with a message in squint_last_error().  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call before
+ * any stream capture.  All calls share the array: two calls whose kernels overlap
+ * on the GPU (different streams, or concurrent host threads) race and give wrong
+ * results; serialise them.  Each call writes every partial it reads, so nothing
+ * carries over between calls.
+ */
+int64_t squint_op_conv3x3_wgrad_noalloc_max(void);
+int squint_op_conv3x3_wgrad_noalloc(int nimg, int cin, int h, int w, int cout, int stride, const float* x,
+                                    const float* dy, float* dw, float* db, void* stream);
+
 /* LayerNorm over rows of n (Sec. IV "Normalization"), FP32: y = g (x - mean) rstd + b, ReLU if relu. */
 int squint_op_layernorm_fwd(int rows, int n, const float* x, const float* g, const float* b, float eps, int relu,
                             float* y, float* mean, float* rstd, void* stream);

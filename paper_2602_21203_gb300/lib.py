@@ -113,6 +113,8 @@ def load():
         "squint_op_conv32": (I, [I, I, I, I, P, P, P, I, P, P, P, P]),
         "squint_op_wgrad32_workspace": (SZ, [I]),
         "squint_op_wgrad32": (I, [I, I, I, P, P, P, P, P, SZ, P]),
+        "squint_op_conv3x3_wgrad_noalloc_max": (I64, []),
+        "squint_op_conv3x3_wgrad_noalloc": (I, [I, I, I, I, I, I, P, P, P, P, P]),
         "squint_strerror": (ctypes.c_char_p, [I]),
         "squint_last_error": (ctypes.c_char_p, []),
     }
