@@ -59,48 +59,6 @@ def load_peaks():
     return dict(PEAKS_FALLBACK), "fallback"
 
 
-# ------------------------------------------------------------------ algorithmic work per phase
-def phase_work(cfg):
-    """(bound, work per update, unit) of each phase of one update, from the shapes alone."""
-    B, C, H, W, f = cfg["batch"], cfg["obs_c"], cfg["obs_h"], cfg["obs_w"], cfg["squint_f"]
-    A, P, K = cfg["action_dim"], cfg["proprio_dim"], cfg["atoms"]
-    hs, ws = H // f, W // f
-    macs = []
-    cin, h, w = C, hs, ws
-    strides = cfg.get("conv_strides") or [2] + [1] * (cfg["conv_layers"] - 1)
-    for s in strides:
-        oh, ow = (h - 3) // s + 1, (w - 3) // s + 1
-        macs.append(oh * ow * cfg["conv_ch"] * cin * 9)
-        cin, h, w = cfg["conv_ch"], oh, ow
-    F = cin * h * w
-    D = cfg["proj_dim"]
-    Z = D if D > 0 else F
-    Dc, Da = Z + P + A, Z + P
-    hid = cfg["hidden"]
-    crit = Dc * hid[0] + sum(hid[i] * hid[i + 1] for i in range(len(hid) - 1)) + hid[-1] * K
-    actor = Da * hid[0] + sum(hid[i] * hid[i + 1] for i in range(len(hid) - 1)) + hid[-1] * 2 * A
-    proj = F * D
-    n_enc = sum(cout * cin_ * 10 for cout, cin_ in [(cfg["conv_ch"], C)] + [(cfg["conv_ch"], cfg["conv_ch"])] *
-                (cfg["conv_layers"] - 1))
-    n_critic_grp = n_enc + (2 * proj + 4 * D if D else 0) + 2 * (crit + sum(3 * x for x in hid) + K)
-    n_actor_grp = (proj + 3 * D if D else 0) + actor + sum(3 * x for x in hid) + 2 * A
-    fl = lambda m: 2.0 * m
-    return {
-        "frontend": ("hbm", 2 * B * C * H * W + 2 * B * C * hs * ws * 4, "B"),
-        "encoder_fwd": ("fma", fl(2 * B * sum(macs)), "FLOP"),
-        "projections": ("fma", fl(4 * B * proj), "FLOP"),
-        "actor_fwd": ("fma", fl(2 * B * actor), "FLOP"),
-        "target_critics": ("fma", fl(2 * B * crit), "FLOP"),
-        "critic_fwd_ce": ("fma", fl(2 * B * crit), "FLOP"),
-        "critic_bwd": ("fma", fl(2 * 2 * B * crit + 2 * B * proj), "FLOP"),
-        "encoder_bwd": ("fma", fl(B * sum(macs) + B * sum(macs[1:])), "FLOP"),
-        "adam_critic": ("hbm", 28 * n_critic_grp, "B"),
-        "alpha_step": ("latency", 0, "B"),
-        "actor_step": ("fma", fl(B * proj + 2 * B * crit + 2 * B * crit + 2 * B * actor + B * proj), "FLOP"),
-        "stats_polyak": ("hbm", 12 * (n_critic_grp - n_enc), "B"),
-    }
-
-
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -339,35 +297,56 @@ def run_ours(args):
     e2e = {"value": world * K * UTD_K / e2e_s, "unit": "updates/s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h)}
 
-    # ---- per-phase device times (CUDA events on the launching stream, eager update)
-    prof = {}
+    # ---- per-kernel device times: one in-order eager update on the timed stream, every
+    # launch bracketed by CUDA events; the roofline is the class with the most device time
+    kprof = {}
     for _ in range(5):
+        for name, (nl, kms, work, unit) in learner.profile_kernels(stream=stream).items():
+            e = kprof.setdefault(name, [nl, [], work, unit])
+            e[1].append(kms)
+    kernels = {}
+    for name, (nl, times, work, unit) in kprof.items():
+        t = statistics.median(times)
+        kernels[name] = {"launches": nl, "ms": round(t, 5), "work": work, "unit": unit}
+    phase_ms = {}
+    for _ in range(3):
         for name, t in learner.profile_update(stream=stream).items():
-            prof.setdefault(name, []).append(t)
-    phase_ms = {k: statistics.median(v) for k, v in prof.items()}
-    work = phase_work(cfg)
-    dom = max((k for k in phase_ms if work[k][0] != "latency"), key=lambda k: phase_ms[k])
-    bound, amount, unit = work[dom]
-    secs = phase_ms[dom] / 1000.0
+            phase_ms.setdefault(name, []).append(t)
+    phase_ms = {k: round(statistics.median(v), 4) for k, v in phase_ms.items()}
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    if bound == "hbm":
-        achieved = amount / secs / 1e9
-        peak = peaks["hbm_gbs"]
-        roof = {"bound": "hbm", "unit": "GB/s"}
-        peak_note = f"{peaks_src} copy bandwidth"
-    elif prec == lib.PREC_BF16:
-        achieved = amount / secs / 1e12
-        peak = peaks["bf16_tflops_sustained"]
-        roof = {"bound": "tensor", "unit": "TFLOP/s"}
-        peak_note = f"{peaks_src} bf16 sustained"
-    else:
-        achieved = amount / secs / 1e12
-        peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-        roof = {"bound": "alu", "unit": "TFLOP/s"}
-        peak_note = f"FP32 FMA: {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz (median SM clock)"
-    roof.update({"achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "traffic": NCU_TRAFFIC.get((dom, args.precision)), "kernel": dom, "peak_source": peak_note,
-                 "phase_ms": {k: round(v, 4) for k, v in phase_ms.items()}})
+    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+    def class_roof(name, k):
+        secs = k["ms"] / 1000.0
+        if k["work"] <= 0 or secs <= 0:
+            return None
+        if k["unit"] == "B":
+            ach = k["work"] / secs / 1e9
+            return {"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peaks["hbm_gbs"],
+                    "peak_source": f"{peaks_src} copy bandwidth"}
+        ach = k["work"] / secs / 1e12
+        if name.startswith("tc_") or name.startswith("conv_tc"):
+            return {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": peaks["bf16_tflops"],
+                    "peak_source": f"{peaks_src} bf16 burst (kernel timed alone)"}
+        return {"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": fp32_peak,
+                "peak_source": f"FP32 FMA {N_SM} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz"}
+
+    ranked = sorted((n for n in kernels if class_roof(n, kernels[n])), key=lambda n: -kernels[n]["ms"])
+    dom = ranked[0]
+    roof = class_roof(dom, kernels[dom])
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = NCU_TRAFFIC.get((dom, args.precision))
+    roof["kernel"] = dom
+    roof["launches_per_update"] = kernels[dom]["launches"]
+    roof["work_per_launch"] = kernels[dom]["work"] / kernels[dom]["launches"]
+    roof["avg_launch_us"] = 1000.0 * kernels[dom]["ms"] / kernels[dom]["launches"]
+    for n in kernels:
+        cr = class_roof(n, kernels[n])
+        if cr:
+            kernels[n]["achieved"] = round(cr["achieved"], 3)
+            kernels[n]["frac"] = round(cr["achieved"] / cr["peak"], 5)
+    roof["kernels_per_update"] = kernels
+    roof["phase_ms"] = phase_ms
 
     # ---- serving: continuous batching beside the UTD-4 update stream
     serving = None

@@ -162,6 +162,17 @@ int squint_profile_update(squint_handle* h, float* ms, int cap, int* n_phases, v
 /* Name of phase i of squint_profile_update, or NULL. */
 const char* squint_phase_name(int i);
 
+/*
+ * One update issued eagerly on `stream` with every kernel launched in order (no
+ * concurrent branches) and timed by its own CUDA events; launches are grouped by
+ * kernel class.  For class i < *n (at most cap written): names + 32 i receives its
+ * NUL-terminated name, launches[i] its launch count, ms[i] its total device time,
+ * work[i] the algorithmic work of those launches and unit[i] its unit (0: FLOP,
+ * 1: bytes of DRAM-level traffic the class needs at minimum).  Waits for the stream.
+ */
+int squint_profile_kernels(squint_handle* h, int cap, char* names, int* launches, float* ms, double* work, int* unit,
+                           int* n, void* stream);
+
 /* ------------------------------------------------------------------ inference */
 
 /* One actor query: n environments of one group (Alg. 1, "Sample a_t ~ pi"). */

@@ -302,6 +302,14 @@ int squint_profile_update(squint_handle* h, float* ms, int cap, int* n_phases, v
 
 const char* squint_phase_name(int i) { return sq::phase_name(i); }
 
+int squint_profile_kernels(squint_handle* h, int cap, char* names, int* launches, float* ms, double* work, int* unit,
+                           int* n, void* stream) {
+    if (!h || cap < 0 || !names || !launches || !ms || !work || !unit || !n) return SQUINT_EINVAL;
+    if (h->failed) return SQUINT_ESTATE;
+    if (!h->has_ring) return SQUINT_ESTATE;
+    return h->profile_kernels(cap, names, launches, ms, work, unit, n, (cudaStream_t)stream);
+}
+
 int squint_refresh_policy(squint_handle* h, void* stream) {
     if (!h) return SQUINT_EINVAL;
     if (h->failed) return SQUINT_ESTATE;

@@ -165,6 +165,24 @@ struct squint_handle {
     std::vector<void*> act_allocs;
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, int64_t> graph_kernels;
+    // concurrent branches of one update: library-owned streams joined back before it ends
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork_ev[32] = {};
+    int fork_next = 0;
+    bool serial = false;                  // profiling: every launch in order on the main stream
+    struct ProfEntry { const char* name; cudaEvent_t a, b; double work; int unit; };
+    std::vector<ProfEntry>* prof = nullptr;   // per-launch records while profiling kernels
+    // stream of branch i (the main stream itself when serial)
+    cudaStream_t branch(cudaStream_t main, int i) const { return serial ? main : side[i]; }
+    // make `to` wait for the work issued so far on `from`
+    void fork(cudaStream_t from, cudaStream_t to) {
+        if (from == to) return;
+        cudaEvent_t e = fork_ev[fork_next++ % 32];
+        cudaEventRecord(e, from);
+        cudaStreamWaitEvent(to, e, 0);
+    }
+    int profile_kernels(int cap, char* names, int* launches, float* ms, double* work, int* unit, int* n,
+                        cudaStream_t s);
     std::vector<cudaEvent_t>* phase_events = nullptr;   // set while profiling an eager update
     void mark(cudaStream_t s) {
         if (phase_events) {

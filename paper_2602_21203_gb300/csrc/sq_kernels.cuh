@@ -200,7 +200,7 @@ struct StatsArgs {
     const float* row_q_actor; const float* logp_t;   // actor step
     const float* log_alpha;
     const int32_t* do_actor;
-    const int64_t* update_idx;
+    int64_t* update_idx;          // read into the statistics, then advanced by one
     float* stats;                 // [8]
 };
 void launch_stats(const StatsArgs& a, cudaStream_t s);

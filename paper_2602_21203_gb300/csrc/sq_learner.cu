@@ -20,7 +20,9 @@
 #include "sq_sched.h"
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <tuple>
 
 using namespace sq;
 
@@ -43,6 +45,8 @@ GemmProblem lin_fwd(const float* X, int64_t ldx, int rows, const float* W, const
 // ---------------------------------------------------------------- GemmBuilder
 void GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64_t ldy, __nv_bfloat16* Yh,
                       int64_t ldyh) {
+    flops_ += 2.0 * rows * W.out * W.in;
+    kind_ = bf_ ? "tc_gemm_fwd" : "gemm_f32_fwd";
     if (!bf_) {
         fp_.push_back(lin_fwd(X.f, X.ld, rows, W.w, W.b, W.in, W.out, Y, ldy));
         lay_ = kKK;
@@ -60,6 +64,8 @@ void GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64
 
 void GemmBuilder::dx(const Mat* dY, const LayerRef* W, int n_pairs, int rows, int col0, int ncols, float* dX,
                      int64_t ldx, const float* mask, int64_t ldm) {
+    flops_ += 2.0 * rows * ncols * W[0].out * n_pairs;
+    kind_ = bf_ ? "tc_gemm_dx" : "gemm_f32_dx";
     if (!bf_) {
         GemmProblem p{};
         p.M = rows; p.N = ncols; p.K = W[0].out;
@@ -86,6 +92,8 @@ void GemmBuilder::dx(const Mat* dY, const LayerRef* W, int n_pairs, int rows, in
 }
 
 void GemmBuilder::dw(const Mat& dY, int rows, const Mat& X, const LayerRef& W, float* dW) {
+    flops_ += 2.0 * rows * W.out * W.in;
+    kind_ = bf_ ? "tc_gemm_dw" : "gemm_f32_dw";
     if (!bf_) {
         GemmProblem p{};
         p.M = W.out; p.N = W.in; p.K = rows;
@@ -106,10 +114,15 @@ void GemmBuilder::dw(const Mat& dY, int rows, const Mat& X, const LayerRef& W, f
 }
 
 void GemmBuilder::flush() {
-    if (!fp_.empty()) launch_gemm<float>(fp_.data(), (int)fp_.size(), lay_, s_);
-    if (!tc_.empty() && launch_tc_gemm(tc_.data(), (int)tc_.size(), h_->d_err, s_) != 0) h_->launch_failed = true;
+    if (fp_.empty() && tc_.empty()) return;
+    {
+        ProfScope ps(h_, s_, kind_, flops_, 0);
+        if (!fp_.empty()) launch_gemm<float>(fp_.data(), (int)fp_.size(), lay_, s_);
+        if (!tc_.empty() && launch_tc_gemm(tc_.data(), (int)tc_.size(), h_->d_err, s_) != 0) h_->launch_failed = true;
+    }
     fp_.clear();
     tc_.clear();
+    flops_ = 0;
 }
 
 // ---------------------------------------------------------------- parameter views
@@ -169,6 +182,7 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
             p.mean = mb.mean[l] + (int64_t)e * rows; p.rstd = mb.rstd[l] + (int64_t)e * rows;
             lp[e] = p;
         }
+        ProfScope ps(h, s, "layernorm_fwd", 4.0 * E * rows * sets[0][l].out * (bf16 ? 3.5 : 3.0), 1);
         launch_ln_fwd(lp, E, true, (float)h->c.ln_eps, s);
     }
 }
@@ -183,7 +197,9 @@ namespace {
 // only).  dX (optional) = sum over sets of the input gradient, columns [0, ncols).
 void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* sets, float* grads, int E, const Mat& X,
                   int rows, const Mat& dout, int ncols, float* dX, int64_t lddx, const float* mask, int64_t ldmask,
-                  cudaStream_t s) {
+                  cudaStream_t s, cudaStream_t side) {
+    // weight and bias gradients go to `side` as soon as their inputs exist; the main
+    // stream carries only the chain of input gradients; `side` is joined at the end
     const bool bf = h->bf16;
     const int nh = (int)sets[0].size() - 1;
     const int R = mb.rows;
@@ -210,14 +226,16 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
     };
     // output layer
     if (grads) {
-        GemmBuilder gb(h, s, bf);
-        for (int e = 0; e < E; ++e) gb.dw(dout_e(e), rows, post(nh - 1, e), sets[e][nh], G(sets[e][nh].w));
-    }
-    if (grads) {
+        h->fork(s, side);
+        {
+            GemmBuilder gb(h, side, bf);
+            for (int e = 0; e < E; ++e) gb.dw(dout_e(e), rows, post(nh - 1, e), sets[e][nh], G(sets[e][nh].w));
+        }
         ColSumProblem cs[2];
         for (int e = 0; e < E; ++e)
             cs[e] = ColSumProblem{rows, sets[e][nh].out, dout_e(e).f, dout.ld, G(sets[e][nh].b)};
-        launch_colsum(cs, E, s);
+        ProfScope ps(h, side, "colsum", 4.0 * E * rows * sets[0][nh].out, 1);
+        launch_colsum(cs, E, side);
     }
     {
         GemmBuilder gb(h, s, bf);
@@ -243,9 +261,13 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
             if (grads) { p.dg = G(ly.g); p.dbeta = G(ly.beta); p.dbias = G(ly.b); }
             lb[e] = p;
         }
-        launch_ln_bwd(lb, E, s);
+        {
+            ProfScope ps(h, s, "layernorm_bwd", 4.0 * E * rows * sets[0][l].out * (grads ? 9.0 : 5.0), 1);
+            launch_ln_bwd(lb, E, s);
+        }
         if (grads) {
-            GemmBuilder gb(h, s, bf);
+            h->fork(s, side);
+            GemmBuilder gb(h, side, bf);
             for (int e = 0; e < E; ++e) gb.dw(dpre(l, e), rows, l == 0 ? X : post(l - 1, e), sets[e][l], G(sets[e][l].w));
         }
         if (l > 0) {
@@ -263,6 +285,7 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
         LayerRef w[2] = {sets[0][0], E > 1 ? sets[1][0] : sets[0][0]};
         gb.dx(d, w, E, rows, 0, ncols, dX, lddx, mask, ldmask);
     }
+    if (grads) h->fork(side, s);
 }
 
 void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, int E, int rows) {
@@ -426,6 +449,8 @@ int squint_handle::allocate() {
     }
     if (cudaMallocHost(&h_stats, sizeof(float) * 8 * c.max_k) != cudaSuccess) return SQUINT_ENOMEM;
     SQ_CK(this, cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
+    for (auto& st : side) SQ_CK(this, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto& e : fork_ev) SQ_CK(this, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i) {
         SQ_CK(this, cudaEventCreateWithFlags(&policy_ready[i], cudaEventDisableTiming));
         SQ_CK(this, cudaEventCreateWithFlags(&policy_released[i], cudaEventDisableTiming));
@@ -459,6 +484,8 @@ void squint_handle::release() {
     h_req = nullptr;
     if (capture_stream) cudaStreamDestroy(capture_stream);
     capture_stream = nullptr;
+    for (auto& st : side) { if (st) cudaStreamDestroy(st); st = nullptr; }
+    for (auto& e : fork_ev) { if (e) cudaEventDestroy(e); e = nullptr; }
     for (int i = 0; i < 2; ++i) {
         if (policy_ready[i]) cudaEventDestroy(policy_ready[i]);
         if (policy_released[i]) cudaEventDestroy(policy_released[i]);
@@ -493,11 +520,37 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     float* W = params;
     float* G = grads;
     float* stats = d_stats + 8 * j;
-    auto cast_rows = [&](const float* src, int64_t ld, int rows, int cols, __nv_bfloat16* dst, int64_t ldh) {
+    // branches: s1 encoder backward, s2 weight gradients of the MLPs, s3 critic forward / polyak
+    cudaStream_t s1 = branch(s, 0), s2 = branch(s, 1), s3 = branch(s, 2);
+    auto cast_rows = [&](const float* src, int64_t ld, int rows, int cols, __nv_bfloat16* dst, int64_t ldh,
+                         cudaStream_t st) {
         if (!bf16) return;
         CastItem it{src, ld, rows, cols, dst, ldh};
-        launch_cast_rows(&it, 1, s);
+        ProfScope ps(this, st, "cast_bf16", 6.0 * rows * cols, 1);
+        launch_cast_rows(&it, 1, st);
     };
+    auto ln_fwd = [&](const LnProblem* p, int n, bool relu, cudaStream_t st) {
+        double bytes = 0;
+        for (int i = 0; i < n; ++i) bytes += 12.0 * p[i].rows * p[i].n;
+        ProfScope ps(this, st, "layernorm_fwd", bytes, 1);
+        launch_ln_fwd(p, n, relu, ln_eps, st);
+    };
+    auto ln_bwd = [&](const LnBwdProblem* p, int n, cudaStream_t st) {
+        double bytes = 0;
+        for (int i = 0; i < n; ++i) bytes += 36.0 * p[i].rows * p[i].n;
+        ProfScope ps(this, st, "layernorm_bwd", bytes, 1);
+        launch_ln_bwd(p, n, st);
+    };
+    auto adam = [&](int64_t begin, int64_t end, const int32_t* step, const int32_t* enable, cudaStream_t st) {
+        AdamArgs ad{};
+        ad.p = W + begin; ad.g = G + begin; ad.m = adam_m + begin; ad.v = adam_v + begin;
+        ad.n = end - begin;
+        ad.step = step; ad.enable = enable;
+        ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
+        ProfScope ps(this, st, "adam", 28.0 * (double)ad.n, 1);
+        launch_adam(ad, st);
+    };
+    auto conv_flops = [&](const ConvL& cv, int nimg) { return 2.0 * nimg * cv.oh * cv.ow * cv.cout * cv.cin * 9; };
 
     mark(s);
     // ---- a1-a4: minibatch, gathers, shift, squint
@@ -517,7 +570,11 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     fa.dst[5] = CopyDst{xcbar, Dc, Z, 1};
     fa.n_dst = 6;
     fa.steps = d_steps; fa.do_actor = d_do_actor; fa.policy_freq = c.policy_freq;
-    launch_frontend(fa, s);
+    {
+        const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
+        ProfScope ps(this, s, "frontend", 2.0 * B * c.obs_c * c.obs_h * c.obs_w + 2.0 * B * img * 4, 1);
+        launch_frontend(fa, s);
+    }
 
     mark(s);
     // ---- a5: encoder on o_t (rows < B) and o_{t+1} (rows >= B)
@@ -538,18 +595,24 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             ct.relu = 1;
             if (l < nconv - 1) ct.out_phwc = act_p[l];
             else { ct.out_chw = conv_out[l]; ct.out_chw_bf = z_h; }
+            ProfScope ps(this, s, "conv_tc_fwd", conv_flops(cv, 2 * B), 0);
             if (launch_conv32_tc(ct, d_err, s) != 0) launch_failed = true;
             continue;
         }
         ConvShape sh{2 * B, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
                      (int64_t)cv.cout * cv.oh * cv.ow};
-        launch_conv_fwd<float>(sh, in, W + cv.wo, W + cv.bo, conv_out[l], true, s);
+        {
+            ProfScope ps(this, s, "conv_f32_fwd", conv_flops(cv, 2 * B), 0);
+            launch_conv_fwd<float>(sh, in, W + cv.wo, W + cv.bo, conv_out[l], true, s);
+        }
         in = conv_out[l];
-        if (tc_conv && l == 0)
+        if (tc_conv && l == 0) {
+            ProfScope ps(this, s, "layout_phwc", (4.0 + 2.0) * 2 * B * cv.cout * cv.oh * cv.ow, 1);
             launch_to_phwc(conv_out[0], (int64_t)cv.cout * cv.oh * cv.ow, 2 * B, cv.oh, cv.ow, act_p[0], s);
+        }
     }
     float* z = conv_out.back();                // [2B, F]
-    if (!tc_conv) cast_rows(z, F, 2 * B, F, z_h, F);
+    if (!tc_conv) cast_rows(z, F, 2 * B, F, z_h, F, s);
     const Mat zt{z, F, z_h, F};
     const Mat zt1 = zt.rows(B);
 
@@ -578,7 +641,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             p.mean = proj_mean + i * B; p.rstd = proj_rstd + i * B;
             lp[i] = p;
         }
-        launch_ln_fwd(lp, 4, false, ln_eps, s);
+        ln_fwd(lp, 4, false, s);
     } else {
         const size_t fb = (size_t)F * sizeof(float);
         cudaMemcpy2DAsync(xa, Da * sizeof(float), zt1.f, fb, fb, B, cudaMemcpyDeviceToDevice, s);
@@ -587,12 +650,16 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         cudaMemcpy2DAsync(xc, Dc * sizeof(float), z, fb, fb, B, cudaMemcpyDeviceToDevice, s);
         cudaMemcpy2DAsync(xq, Dc * sizeof(float), z, fb, fb, B, cudaMemcpyDeviceToDevice, s);
     }
-    cast_rows(xa, Da, 2 * B, Da, xa_h, Da8);
-    cast_rows(xc, Dc, B, Dc, xc_h, Dc8);
+    cast_rows(xa, Da, 2 * B, Da, xa_h, Da8, s);
+    cast_rows(xc, Dc, B, Dc, xc_h, Dc8, s);
 
     const MlpRef actor_on = mlp_ref(this, L.actor, false);
     const MlpRef crit_on[2] = {mlp_ref(this, L.critic[0], false), mlp_ref(this, L.critic[1], false)};
     const MlpRef crit_tg[2] = {mlp_ref(this, L.critic[0], true), mlp_ref(this, L.critic[1], true)};
+
+    // ---- a10 (forward part) on branch s3: online critics on (z, s, a), independent of the target
+    fork(s, s3);
+    mlp_forward(this, crit_mlp, crit_on, E, Mat{xc, Dc, xc_h, Dc8}, B, bf16, s3);
 
     mark(s);
     // ---- a7: actor (pre-update) on both halves; tanh-Gaussian sample
@@ -606,8 +673,11 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ah.a_dst0 = xcbar + Z + P; ah.ld0 = Dc;
         ah.a_dst1 = xq + Z + P; ah.ld1 = Dc;
         ah.logp = logp; ah.eps = eps;
-        launch_actor_head(ah, s);
-        cast_rows(xcbar, Dc, B, Dc, xcbar_h, Dc8);
+        {
+            ProfScope ps(this, s, "heads_losses", 0, 1);
+            launch_actor_head(ah, s);
+        }
+        cast_rows(xcbar, Dc, B, Dc, xcbar_h, Dc8, s);
     }
     mark(s);
     // ---- a8-a9: target critics and the projected categorical target
@@ -619,27 +689,29 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ct.log_alpha = W + L.log_alpha;
         ct.gamma = (float)c.gamma; ct.v_min = (float)c.v_min; ct.v_max = (float)c.v_max;
         ct.m = m;
+        ProfScope ps(this, s, "heads_losses", 0, 1);
         launch_c51_target(ct, s);
     }
     mark(s);
-    // ---- a10: online critics and the cross entropy
+    // ---- a10: cross entropy against the projected target (joins the critic forward)
+    fork(s3, s);
     {
-        mlp_forward(this, crit_mlp, crit_on, E, Mat{xc, Dc, xc_h, Dc8}, B, bf16, s);
         CeArgs ce{};
         ce.B = B; ce.K = K; ce.E = E; ce.logits = crit_mlp.out; ce.m = m;
         ce.v_min = (float)c.v_min; ce.v_max = (float)c.v_max;
         ce.scale = 1.0f / (float)B;
         ce.dlogits = dlogits; ce.row_loss = row_loss; ce.row_q = row_q;
         if (bf16) { ce.dlogits_bf = dlogits_h; ce.ld_bf = K8; }
+        ProfScope ps(this, s, "heads_losses", 0, 1);
         launch_ce(ce, s);
     }
     mark(s);
-    // ---- a11: backward through critics, critic projection, encoder
+    // ---- a11: backward through critics and the critic projection (weight gradients on s2)
     {
         const Mat dl{dlogits, K, dlogits_h, K8};
         const float* mask = Dd > 0 ? nullptr : z;      // flatten path: mask by the last conv's ReLU
         mlp_backward(this, crit_mlp, 0, crit_on, G, E, Mat{xc, Dc, xc_h, Dc8}, B, dl, Z, Dd > 0 ? dh : dz,
-                     Dd > 0 ? Z : F, mask, F, s);
+                     Dd > 0 ? Z : F, mask, F, s, s2);
         if (Dd > 0) {
             const LayerRef cp = layer_ref(this, L.cproj, false);
             LnBwdProblem p{};
@@ -651,22 +723,38 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             p.dpre = dproj; p.ld_dpre = Dd;
             if (bf16) { p.dpre_bf = dproj_h; p.ld_dpre_bf = Dd; }
             p.dg = G + L.cproj.g; p.dbeta = G + L.cproj.beta; p.dbias = G + L.cproj.b;
-            launch_ln_bwd(&p, 1, s);
+            ln_bwd(&p, 1, s);
             const Mat dp{dproj, Dd, dproj_h, Dd};
+            fork(s, s2);
             {
-                GemmBuilder gb(this, s, bf16);
+                GemmBuilder gb(this, s2, bf16);
                 gb.dw(dp, B, zt, cp, G + L.cproj.w);
             }
             {
                 GemmBuilder gb(this, s, bf16);
                 gb.dx(&dp, &cp, 1, B, 0, F, dz, F, z, F);
             }
+            fork(s2, s);
         }
-        mark(s);
+    }
+    mark(s);
+    // ---- a12 (critic range): Adam over critic projection + critics, BF16 copies
+    adam(L.critic_begin, L.critic_end, d_steps + 0, nullptr, s);
+    if (bf16) {
+        ProfScope ps(this, s, "cast_bf16", 6.0 * (double)(L.critic_end - L.critic_begin), 1);
+        launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), s);
+    }
+
+    // ---- a11 (encoder part) + a12 (encoder range) on branch s1, beside the actor step
+    fork(s, s1);
+    {
         const float* cur = dz;
         if (tc_conv) {
             const ConvL& last = L.conv.back();
-            launch_to_phwc(dz, F, B, last.oh, last.ow, dz_p, s);
+            {
+                ProfScope ps(this, s1, "layout_phwc", 6.0 * B * F, 1);
+                launch_to_phwc(dz, F, B, last.oh, last.ow, dz_p, s1);
+            }
             const __nv_bfloat16* cur_p = dz_p;
             for (int l = nconv - 1; l >= 1; --l) {
                 const ConvL& cv = L.conv[l];
@@ -677,7 +765,10 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
                 wt.Wp = cv.w + 4;
                 wt.in_rows = (cv.h + 4) * wt.Wp;
                 wt.out_h = cv.oh; wt.out_w = cv.ow;
-                if (launch_wgrad32_tc(wt, wgrad_tc_work, G + cv.wo, G + cv.bo, d_err, s) != 0) launch_failed = true;
+                {
+                    ProfScope ps(this, s1, "conv_tc_wgrad", conv_flops(cv, B), 0);
+                    if (launch_wgrad32_tc(wt, wgrad_tc_work, G + cv.wo, G + cv.bo, d_err, s1) != 0) launch_failed = true;
+                }
                 ConvTc ct{};
                 ct.in = cur_p;
                 ct.nimg = B;
@@ -688,38 +779,56 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
                 ct.w = wconv_bwd[l];
                 ct.mask = act_p[l - 1];
                 ct.out_phwc = dact_p[l - 1];
-                if (launch_conv32_tc(ct, d_err, s) != 0) launch_failed = true;
+                {
+                    ProfScope ps(this, s1, "conv_tc_dgrad", conv_flops(cv, B), 0);
+                    if (launch_conv32_tc(ct, d_err, s1) != 0) launch_failed = true;
+                }
                 cur_p = dact_p[l - 1];
             }
             const ConvL& c0 = L.conv[0];
-            launch_from_phwc(dact_p[0], B, c0.oh, c0.ow, dconv_a, s);
+            {
+                ProfScope ps(this, s1, "layout_phwc", 6.0 * B * c0.cout * c0.oh * c0.ow, 1);
+                launch_from_phwc(dact_p[0], B, c0.oh, c0.ow, dconv_a, s1);
+            }
             ConvShape sh{B, c0.cin, c0.h, c0.w, c0.cout, c0.s, c0.oh, c0.ow, (int64_t)c0.cin * c0.h * c0.w,
                          (int64_t)c0.cout * c0.oh * c0.ow};
-            launch_conv_wgrad<float>(sh, dconv_a, x2, G + c0.wo, G + c0.bo, wgrad_work, s);
+            ProfScope ps(this, s1, "conv_f32_wgrad", conv_flops(c0, B), 0);
+            launch_conv_wgrad<float>(sh, dconv_a, x2, G + c0.wo, G + c0.bo, wgrad_work, s1);
         }
-        for (int l = tc_conv ? -1 : (int)L.conv.size() - 1; l >= 0; --l) {
+        for (int l = tc_conv ? -1 : nconv - 1; l >= 0; --l) {
             const ConvL& cv = L.conv[l];
             ConvShape sh{B, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
                          (int64_t)cv.cout * cv.oh * cv.ow};
             const float* xin = l == 0 ? x2 : conv_out[l - 1];
-            launch_conv_wgrad<float>(sh, cur, xin, G + cv.wo, G + cv.bo, wgrad_work, s);
+            {
+                ProfScope ps(this, s1, "conv_f32_wgrad", conv_flops(cv, B), 0);
+                launch_conv_wgrad<float>(sh, cur, xin, G + cv.wo, G + cv.bo, wgrad_work, s1);
+            }
             if (l > 0) {
                 float* nxt = (cur == dconv_a) ? dconv_b : dconv_a;
-                launch_conv_dgrad<float>(sh, cur, W + cv.wo, nxt, conv_out[l - 1], s);
+                ProfScope ps(this, s1, "conv_f32_dgrad", conv_flops(cv, B), 0);
+                launch_conv_dgrad<float>(sh, cur, W + cv.wo, nxt, conv_out[l - 1], s1);
                 cur = nxt;
             }
         }
+        adam(0, L.critic_begin, d_steps + 0, nullptr, s1);
+        if (tc_conv) {
+            ProfScope ps(this, s1, "cast_bf16", 6.0 * 9 * 32 * 32 * (nconv - 1), 1);
+            cast_conv_weights(s1);
+        }
     }
-    mark(s);
-    // ---- a12: Adam over encoder + critic projection + critics
+    // ---- a16 on branch s3: polyak of the updated critics, BF16 target copies
+    fork(s, s3);
     {
-        AdamArgs ad{};
-        ad.p = W; ad.g = G; ad.m = adam_m; ad.v = adam_v; ad.n = L.critic_end;
-        ad.step = d_steps + 0;
-        ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
-        launch_adam(ad, s);
-        if (bf16) launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), s);
-        cast_conv_weights(s);
+        PolyakArgs pa{target, W + L.critic_begin, L.target_n, (float)c.tau, nullptr};
+        {
+            ProfScope ps(this, s3, "polyak", 12.0 * (double)L.target_n, 1);
+            launch_polyak(pa, s3);
+        }
+        if (bf16) {
+            ProfScope ps(this, s3, "cast_bf16", 6.0 * (double)L.target_n, 1);
+            launch_cast_rows(cast_target.data(), (int)cast_target.size(), s3);
+        }
     }
     mark(s);
     // ---- a13: temperature
@@ -731,6 +840,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         al.lr = c.lr; al.b1 = c.adam_b1; al.b2 = c.adam_b2; al.eps = c.adam_eps;
         al.target_entropy = std::isnan(c.target_entropy) ? -(float)A : (float)c.target_entropy;
         al.stats = stats;
+        ProfScope ps(this, s, "heads_losses", 0, 1);
         launch_alpha_step(al, s);
     }
     mark(s);
@@ -748,18 +858,21 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             p.g = cp.g; p.beta = cp.beta;
             p.out = xq; p.ld_out = Dc;
             p.mean = proj_mean + 4 * B; p.rstd = proj_rstd + 4 * B;
-            launch_ln_fwd(&p, 1, false, ln_eps, s);
+            ln_fwd(&p, 1, false, s);
         }
-        cast_rows(xq, Dc, B, Dc, xq_h, Dc8);
+        cast_rows(xq, Dc, B, Dc, xq_h, Dc8, s);
         mlp_forward(this, qcrit_mlp, crit_on, E, Mat{xq, Dc, xq_h, Dc8}, B, bf16, s);
         ActorQArgs aq{};
         aq.B = B; aq.K = K; aq.E = E; aq.logits = qcrit_mlp.out;
         aq.v_min = (float)c.v_min; aq.v_max = (float)c.v_max;
         aq.dlogits = dlogits_q; aq.row_q = row_q_actor; aq.do_actor = d_do_actor;
         if (bf16) { aq.dlogits_bf = dlogits_qh; aq.ld_bf = K8; }
-        launch_actor_q(aq, s);
+        {
+            ProfScope ps(this, s, "heads_losses", 0, 1);
+            launch_actor_q(aq, s);
+        }
         mlp_backward(this, qcrit_mlp, 0, crit_on, nullptr, E, Mat{xq, Dc, xq_h, Dc8}, B, Mat{dlogits_q, K, dlogits_qh, K8},
-                     Dc, dxq, Dc, nullptr, 0, s);
+                     Dc, dxq, Dc, nullptr, 0, s, s2);
         ActorHeadBwdArgs hb{};
         hb.B = B; hb.A = A;
         hb.out = actor_mlp.out + (int64_t)B * 2 * A; hb.ld_out = 2 * A;
@@ -767,9 +880,12 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         hb.lo = (float)c.log_std_min; hb.hi = (float)c.log_std_max;
         hb.dout = dout_a; hb.do_actor = d_do_actor;
         if (bf16) { hb.dout_bf = dout_ah; hb.ld_dout_bf = pad8(2 * A); }
-        launch_actor_head_bwd(hb, s);
+        {
+            ProfScope ps(this, s, "heads_losses", 0, 1);
+            launch_actor_head_bwd(hb, s);
+        }
         mlp_backward(this, actor_mlp, B, &actor_on, G, 1, Mat{xa, Da, xa_h, Da8}.rows(B), B,
-                     Mat{dout_a, 2 * A, dout_ah, pad8(2 * A)}, Z, Dd > 0 ? dh : nullptr, Z, nullptr, 0, s);
+                     Mat{dout_a, 2 * A, dout_ah, pad8(2 * A)}, Z, Dd > 0 ? dh : nullptr, Z, nullptr, 0, s, s2);
         if (Dd > 0) {
             const LayerRef ap = layer_ref(this, L.aproj, false);
             LnBwdProblem p{};
@@ -781,29 +897,28 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             p.dpre = dproj; p.ld_dpre = Dd;
             if (bf16) { p.dpre_bf = dproj_h; p.ld_dpre_bf = Dd; }
             p.dg = G + L.aproj.g; p.dbeta = G + L.aproj.beta; p.dbias = G + L.aproj.b;
-            launch_ln_bwd(&p, 1, s);
+            ln_bwd(&p, 1, s);
             GemmBuilder gb(this, s, bf16);
             gb.dw(Mat{dproj, Dd, dproj_h, Dd}, B, zt, ap, G + L.aproj.w);
         }
-        AdamArgs ad{};
-        ad.p = W + L.actor_begin; ad.g = G + L.actor_begin; ad.m = adam_m + L.actor_begin; ad.v = adam_v + L.actor_begin;
-        ad.n = L.actor_end - L.actor_begin;
-        ad.step = d_steps + 1; ad.enable = d_do_actor;
-        ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
-        launch_adam(ad, s);
-        if (bf16) launch_cast_rows(cast_actor.data(), (int)cast_actor.size(), s);
+        adam(L.actor_begin, L.actor_end, d_steps + 1, d_do_actor, s);
+        if (bf16) {
+            ProfScope ps(this, s, "cast_bf16", 6.0 * (double)(L.actor_end - L.actor_begin), 1);
+            launch_cast_rows(cast_actor.data(), (int)cast_actor.size(), s);
+        }
     }
+    // join the encoder and polyak branches
+    fork(s1, s);
+    fork(s3, s);
     mark(s);
-    // ---- statistics, then a16: polyak (also advances the update index)
+    // ---- statistics; advances the update index
     {
         StatsArgs st{};
         st.B = B; st.E = E; st.row_loss = row_loss; st.row_q = row_q; st.row_q_actor = row_q_actor;
         st.logp_t = logp + B; st.log_alpha = W + L.log_alpha; st.do_actor = d_do_actor;
         st.update_idx = d_update_idx; st.stats = stats;
+        ProfScope ps(this, s, "heads_losses", 0, 1);
         launch_stats(st, s);
-        PolyakArgs pa{target, W + L.critic_begin, L.target_n, (float)c.tau, d_update_idx};
-        launch_polyak(pa, s);
-        if (bf16) launch_cast_rows(cast_target.data(), (int)cast_target.size(), s);
     }
     mark(s);
 }
@@ -888,16 +1003,15 @@ int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s
 static const char* kPhaseNames[] = {
     "frontend",          // a1-a4
     "encoder_fwd",       // a5
-    "projections",       // a6
+    "projections",       // a6 (then the online critic forward starts on a side branch)
     "actor_fwd",         // a7
     "target_critics",    // a8-a9
-    "critic_fwd_ce",     // a10
-    "critic_bwd",        // a11 (MLP + projection)
-    "encoder_bwd",       // a11 (conv wgrad/dgrad)
-    "adam_critic",       // a12
+    "critic_ce",         // a10 (waits for the critic forward)
+    "critic_bwd",        // a11 critics and projection (weight gradients on a side branch)
+    "adam_polyak_fork",  // a12 critic range; encoder backward and polyak start on side branches
     "alpha_step",        // a13
-    "actor_step",        // a14-a15
-    "stats_polyak",      // a16
+    "actor_step",        // a14-a15, then waits for the encoder backward and polyak
+    "stats",             // statistics, update index
 };
 
 const char* sq::phase_name(int i) {
@@ -919,4 +1033,46 @@ int squint_handle::profile_update(float* ms, int cap, int* n_phases, cudaStream_
     for (auto e : ev) cudaEventDestroy(e);
     if (rc != SQUINT_OK) { failed = true; g_last_error = "profiling failed"; }
     return rc;
+}
+
+// One eager update with every launch in order on `s`, each timed by its own events;
+// launches are grouped by kernel class.
+int squint_handle::profile_kernels(int cap, char* names, int* launches, float* ms, double* work, int* unit, int* n,
+                                   cudaStream_t s) {
+    std::vector<ProfEntry> recs;
+    prof = &recs;
+    serial = true;
+    record_update(0, s, false);
+    serial = false;
+    prof = nullptr;
+    int rc = SQUINT_OK;
+    if (cudaStreamSynchronize(s) != cudaSuccess) rc = SQUINT_ECUDA;
+    std::vector<std::string> order;
+    std::map<std::string, std::tuple<int, double, double, int>> agg;
+    for (auto& e : recs) {
+        float t = 0.f;
+        if (rc == SQUINT_OK && cudaEventElapsedTime(&t, e.a, e.b) != cudaSuccess) rc = SQUINT_ECUDA;
+        auto it = agg.find(e.name);
+        if (it == agg.end()) {
+            order.push_back(e.name);
+            agg[e.name] = std::make_tuple(1, (double)t, e.work, e.unit);
+        } else {
+            std::get<0>(it->second) += 1;
+            std::get<1>(it->second) += t;
+            std::get<2>(it->second) += e.work;
+        }
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    if (rc != SQUINT_OK) { failed = true; g_last_error = "kernel profiling failed"; return rc; }
+    *n = (int)order.size();
+    for (int i = 0; i < (int)order.size() && i < cap; ++i) {
+        const auto& v = agg[order[i]];
+        std::snprintf(names + 32 * i, 32, "%s", order[i].c_str());
+        launches[i] = std::get<0>(v);
+        ms[i] = (float)std::get<1>(v);
+        work[i] = std::get<2>(v);
+        unit[i] = std::get<3>(v);
+    }
+    return SQUINT_OK;
 }

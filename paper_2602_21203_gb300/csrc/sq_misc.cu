@@ -373,6 +373,7 @@ __global__ void stats_kernel(StatsArgs a) {
         const int64_t u = *a.update_idx;
         a.stats[6] = __int_as_float((int)(u & 0xffffffff));
         a.stats[7] = __int_as_float((int)(u >> 32));
+        *a.update_idx = u + 1;
     }
 }
 

@@ -57,6 +57,27 @@ private:
     std::vector<GemmProblem> fp_;
     GemmLayout lay_ = kKK;
     std::vector<TcGemm> tc_;
+    double flops_ = 0;
+    const char* kind_ = "gemm";
+};
+
+// Times the launches made while it lives (kernel profiling only; no-op otherwise).
+struct ProfScope {
+    squint_handle* h;
+    cudaStream_t s;
+    int idx = -1;
+    ProfScope(squint_handle* hh, cudaStream_t ss, const char* name, double work, int unit) : h(hh), s(ss) {
+        if (!h->prof) return;
+        squint_handle::ProfEntry e{name, nullptr, nullptr, work, unit};
+        cudaEventCreate(&e.a);
+        cudaEventCreate(&e.b);
+        cudaEventRecord(e.a, s);
+        h->prof->push_back(e);
+        idx = (int)h->prof->size() - 1;
+    }
+    ~ProfScope() {
+        if (idx >= 0) cudaEventRecord((*h->prof)[idx].b, s);
+    }
 };
 
 // Forward of E parameter sets of one MLP shape on `rows` rows of X.

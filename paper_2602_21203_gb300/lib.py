@@ -96,6 +96,7 @@ def load():
         "squint_graph_kernel_count": (I64, [P, I]),
         "squint_profile_update": (I, [P, P, I, ctypes.POINTER(I), P]),
         "squint_phase_name": (ctypes.c_char_p, [I]),
+        "squint_profile_kernels": (I, [P, I, P, P, P, P, P, ctypes.POINTER(I), P]),
         "squint_op_gemm": (I, [I, I, I, I, P, I64, I64, P, I64, I64, P, I64, P, I, P]),
         "squint_op_conv3x3_fwd": (I, [I, I, I, I, I, I, I, P, P, P, P, I, P]),
         "squint_op_conv3x3_workspace": (SZ, [I, I, I, I, I, I, I]),
@@ -263,6 +264,22 @@ class Learner:
         _check(self.lib.squint_profile_update(self.h, ms, 32, ctypes.byref(n), _stream(stream)),
                "squint_profile_update")
         return {self.lib.squint_phase_name(i).decode(): float(ms[i]) for i in range(n.value)}
+
+    def profile_kernels(self, stream=None, cap=64):
+        """One in-order eager update timed per launch: {class: (launches, ms, work, unit)}."""
+        names = ctypes.create_string_buffer(32 * cap)
+        launches = (ctypes.c_int * cap)()
+        ms = (ctypes.c_float * cap)()
+        work = (ctypes.c_double * cap)()
+        unit = (ctypes.c_int * cap)()
+        n = ctypes.c_int(0)
+        _check(self.lib.squint_profile_kernels(self.h, cap, names, launches, ms, work, unit, ctypes.byref(n),
+                                               _stream(stream)), "squint_profile_kernels")
+        out = {}
+        for i in range(min(n.value, cap)):
+            nm = names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
+            out[nm] = (int(launches[i]), float(ms[i]), float(work[i]), "FLOP" if unit[i] == 0 else "B")
+        return out
 
     def refresh_policy(self, stream=None):
         _check(self.lib.squint_refresh_policy(self.h, _stream(stream)), "squint_refresh_policy")
