@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--ring-slots", type=int, default=None,
+                    help="replay-ring slots (default: the workload's 100k; smaller only for profiler captures)")
     return ap.parse_args()
 
 
@@ -242,6 +244,8 @@ def run_ours(args):
         raise SystemExit("bench.py needs a CUDA device (the learner has no CPU path)")
     peaks, peaks_src = load_peaks()
     cfg = synth.make_config(WORKLOAD)
+    if args.ring_slots:
+        cfg["ring_size"] = int(args.ring_slots)
     prec = lib.PREC_BF16 if args.precision == "bf16" else lib.PREC_FP32
     ring = synth.make_ring(cfg, args.seed + rank, device="cuda")
     learner = lib.Learner(cfg, ring, precision=prec, max_k=8)

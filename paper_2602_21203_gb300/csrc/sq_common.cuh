@@ -5,7 +5,34 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <utility>
+
+// Programmatic dependent launch: every kernel first waits until the grids it depends on
+// have finished and their writes are visible, then lets its own dependent grid be
+// scheduled, so a dependent kernel's launch overlaps this one's execution.
+#define SQ_KERNEL_ENTRY()                                              \
+    do {                                                               \
+        asm volatile("griddepcontrol.wait;" ::: "memory");             \
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); \
+    } while (0)
+
 namespace sq {
+
+// Launch with programmatic stream serialization allowed (inside graphs: a programmatic edge).
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Philox4x32-10 (Salmon et al., SC'11, Sec. 3.2): ten rounds of two 32x32->64
 // multiplies; the high halves are xored with the other counter words and the

@@ -124,6 +124,7 @@ struct ConvArgs {
 };
 
 __global__ void __launch_bounds__(128) conv32_tc_kernel(const __grid_constant__ ConvArgs a) {
+    SQ_KERNEL_ENTRY();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t plane = (uint32_t)a.load_rows * 16;
@@ -253,6 +254,7 @@ struct WgradArgs {
 constexpr int kDyBytesMax = 32768;
 
 __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__ WgradArgs a) {
+    SQ_KERNEL_ENTRY();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t plane = (uint32_t)a.load_rows * 16;
@@ -379,6 +381,7 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
 
 __global__ void wgrad32_reduce_kernel(const float* __restrict__ work, int splits, float* __restrict__ dw,
                                       float* __restrict__ db) {
+    SQ_KERNEL_ENTRY();
     constexpr int N = kCh * 9 + 1;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= kCh * N) return;
@@ -393,6 +396,7 @@ __global__ void wgrad32_reduce_kernel(const float* __restrict__ work, int splits
 // CHW FP32 (per image stride img_stride) -> padded HWC BF16 interior.
 __global__ void to_phwc_kernel(const float* __restrict__ src, int64_t img_stride, int nimg, int H, int W,
                                __nv_bfloat16* __restrict__ dst) {
+    SQ_KERNEL_ENTRY();
     const int64_t n = (int64_t)nimg * H * W;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
@@ -410,6 +414,7 @@ __global__ void to_phwc_kernel(const float* __restrict__ src, int64_t img_stride
 
 // Padded HWC BF16 interior -> NCHW FP32.
 __global__ void from_phwc_kernel(const __nv_bfloat16* __restrict__ src, int nimg, int H, int W, float* __restrict__ dst) {
+    SQ_KERNEL_ENTRY();
     const int64_t n = (int64_t)nimg * kCh * H * W;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
@@ -424,6 +429,7 @@ __global__ void from_phwc_kernel(const __nv_bfloat16* __restrict__ src, int nimg
 // layout (tap' = 8 - tap, channels swapped) [tap'][co/8][ci][co%8].
 __global__ void conv_weight_cast_kernel(const float* __restrict__ w, __nv_bfloat16* __restrict__ fwd,
                                         __nv_bfloat16* __restrict__ bwd) {
+    SQ_KERNEL_ENTRY();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= kCh * kCh * 9) return;
     const int co = e / (kCh * 9), rem = e - co * kCh * 9, ci = rem / 9, tap = rem - (rem / 9) * 9;
@@ -485,7 +491,7 @@ int launch_conv32_tc(const ConvTc& c, int* err, cudaStream_t s) {
     a.off0 = c.off0; a.bias = c.bias; a.relu = c.relu; a.mask = c.mask; a.out_phwc = c.out_phwc;
     a.out_chw = c.out_chw; a.out_chw_bf = c.out_chw_bf; a.err = err;
     const size_t smem = conv_smem(a.load_rows);
-    conv32_tc_kernel<<<c.nimg, 128, smem, s>>>(a);
+    launch_k(conv32_tc_kernel, dim3(c.nimg), dim3(128), smem, s, a);
     return 0;
 }
 
@@ -505,8 +511,8 @@ int launch_wgrad32_tc(const WgradTc& c, float* work, float* dw, float* db, int* 
     const int grid = (c.nimg + a.per_cta - 1) / a.per_cta;
     a.dy = c.dy; a.nimg = c.nimg; a.in_rows = c.in_rows; a.Wp = c.Wp; a.out_h = c.out_h; a.out_w = c.out_w;
     a.work = work; a.err = err;
-    wgrad32_tc_kernel<<<grid, 128, wgrad_smem(a.load_rows, a.kq), s>>>(a);
-    wgrad32_reduce_kernel<<<(kCh * (kCh * 9 + 1) + 255) / 256, 256, 0, s>>>(work, grid, dw, db);
+    launch_k(wgrad32_tc_kernel, dim3(grid), dim3(128), wgrad_smem(a.load_rows, a.kq), s, a);
+    launch_k(wgrad32_reduce_kernel, dim3((kCh * (kCh * 9 + 1) + 255) / 256), dim3(256), 0, s, work, grid, dw, db);
     return 0;
 }
 
@@ -518,14 +524,14 @@ void conv_tc_prepare() {
 
 void launch_to_phwc(const float* src, int64_t img_stride, int nimg, int H, int W, __nv_bfloat16* dst, cudaStream_t s) {
     const int64_t n = (int64_t)nimg * H * W;
-    if (n) to_phwc_kernel<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(src, img_stride, nimg, H, W, dst);
+    if (n) launch_k(to_phwc_kernel, dim3((unsigned)((n + 127) / 128)), dim3(128), 0, s, src, img_stride, nimg, H, W, dst);
 }
 void launch_from_phwc(const __nv_bfloat16* src, int nimg, int H, int W, float* dst, cudaStream_t s) {
     const int64_t n = (int64_t)nimg * kCh * H * W;
-    if (n) from_phwc_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, nimg, H, W, dst);
+    if (n) launch_k(from_phwc_kernel, dim3((unsigned)((n + 255) / 256)), dim3(256), 0, s, src, nimg, H, W, dst);
 }
 void launch_conv_weight_cast(const float* w, __nv_bfloat16* fwd, __nv_bfloat16* bwd, cudaStream_t s) {
-    conv_weight_cast_kernel<<<(kCh * kCh * 9 + 255) / 256, 256, 0, s>>>(w, fwd, bwd);
+    launch_k(conv_weight_cast_kernel, dim3((kCh * kCh * 9 + 255) / 256), dim3(256), 0, s, w, fwd, bwd);
 }
 
 }  // namespace sq

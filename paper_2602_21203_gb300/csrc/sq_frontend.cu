@@ -10,6 +10,7 @@
 namespace sq {
 
 __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
+    SQ_KERNEL_ENTRY();
     extern __shared__ __align__(16) uint8_t frame[];
     const int b = blockIdx.x;
     const int which = blockIdx.y;                 // 0: o_t, 1: o_{t+1}
@@ -89,12 +90,13 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
 
 void launch_frontend(const FrontendArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)a.C * a.H * a.W;
-    frontend_kernel<<<dim3(a.B, 2), 256, smem, s>>>(a);
+    launch_k(frontend_kernel, dim3(dim3(a.B, 2)), dim3(256), smem, s, a);
 }
 
 // Inference: one CTA per row; no shift (crop at the centre offset p = pad means
 // the identity, so it is left out entirely).
 __global__ void __launch_bounds__(256) act_frontend_kernel(ActFrontArgs a) {
+    SQ_KERNEL_ENTRY();
     extern __shared__ __align__(16) uint8_t frame[];
     const int r = blockIdx.x;
     const int q = a.row_req[r];
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(256) act_frontend_kernel(ActFrontArgs a) {
 void launch_act_frontend(const ActFrontArgs& a, cudaStream_t s) {
     if (a.rows <= 0) return;
     const size_t smem = (size_t)a.C * a.H * a.W;
-    act_frontend_kernel<<<a.rows, 256, smem, s>>>(a);
+    launch_k(act_frontend_kernel, dim3(a.rows), dim3(256), smem, s, a);
 }
 
 void frontend_prepare(size_t frame_bytes) {

@@ -25,6 +25,7 @@ struct GemmBatch {
 
 template <typename T, int LAYOUT>
 __global__ void __launch_bounds__(NT) gemm_kernel(GemmBatch gb) {
+    SQ_KERNEL_ENTRY();
     __shared__ T As[BK][BM + 4];
     __shared__ T Bs[BK][BN + 4];
     int pi = 0;
@@ -119,9 +120,9 @@ void launch_gemm(const GemmProblem* probs, int n_probs, GemmLayout layout, cudaS
         gb.tile_start[gb.n] = tiles;
         if (tiles == 0) continue;
         switch (layout) {
-            case kKK: gemm_kernel<T, kKK><<<tiles, NT, 0, s>>>(gb); break;
-            case kKN: gemm_kernel<T, kKN><<<tiles, NT, 0, s>>>(gb); break;
-            case kMN: gemm_kernel<T, kMN><<<tiles, NT, 0, s>>>(gb); break;
+            case kKK: launch_k(gemm_kernel<T, kKK>, dim3(tiles), dim3(NT), 0, s, gb); break;
+            case kKN: launch_k(gemm_kernel<T, kKN>, dim3(tiles), dim3(NT), 0, s, gb); break;
+            case kMN: launch_k(gemm_kernel<T, kMN>, dim3(tiles), dim3(NT), 0, s, gb); break;
         }
     }
 }
@@ -137,6 +138,7 @@ constexpr int CBM = 128, CBN = 32, CBK = 16;
 template <typename T>
 __global__ void __launch_bounds__(NT) conv_fwd_kernel(ConvShape sh, const T* __restrict__ x, const T* __restrict__ w,
                                                       const T* __restrict__ bias, T* __restrict__ y, int relu) {
+    SQ_KERNEL_ENTRY();
     __shared__ T As[CBK][CBM + 4];
     __shared__ T Bs[CBK][CBN + 4];
     const int tid = threadIdx.x;
@@ -212,6 +214,7 @@ __global__ void __launch_bounds__(NT) conv_fwd_kernel(ConvShape sh, const T* __r
 template <typename T>
 __global__ void __launch_bounds__(NT) conv_dgrad_kernel(ConvShape sh, const T* __restrict__ dy, const T* __restrict__ w,
                                                         T* __restrict__ dx, const T* __restrict__ mask) {
+    SQ_KERNEL_ENTRY();
     __shared__ T As[CBK][CBM + 4];
     __shared__ T Bs[CBK][CBN + 4];
     const int tid = threadIdx.x;
@@ -299,6 +302,7 @@ constexpr int WBM = 32, WBN = 64, WBK = 32;
 template <typename T>
 __global__ void __launch_bounds__(NT) conv_wgrad_kernel(ConvShape sh, const T* __restrict__ dy, const T* __restrict__ x,
                                                         T* __restrict__ work, int chunk) {
+    SQ_KERNEL_ENTRY();
     __shared__ T As[WBK][WBM + 4];
     __shared__ T Bs[WBK][WBN + 4];
     const int tid = threadIdx.x;
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(NT) conv_wgrad_kernel(ConvShape sh, const T* _
 template <typename T>
 __global__ void wgrad_reduce_kernel(const T* __restrict__ work, int splits, int M, int N, T* __restrict__ dw,
                                     T* __restrict__ db) {
+    SQ_KERNEL_ENTRY();
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= M * N) return;
     T s = T(0);
@@ -399,14 +404,14 @@ void launch_conv_fwd(const ConvShape& sh, const T* x, const T* w, const T* b, T*
     const int M = sh.nimg * sh.OH * sh.OW;
     if (M == 0) return;
     dim3 grid((M + CBM - 1) / CBM, (sh.Cout + CBN - 1) / CBN);
-    conv_fwd_kernel<T><<<grid, NT, 0, s>>>(sh, x, w, b, y, relu ? 1 : 0);
+    launch_k(conv_fwd_kernel<T>, dim3(grid), dim3(NT), 0, s, sh, x, w, b, y, relu ? 1 : 0);
 }
 template <typename T>
 void launch_conv_dgrad(const ConvShape& sh, const T* dy, const T* w, T* dx, const T* mask, cudaStream_t s) {
     const int M = sh.nimg * sh.H * sh.W;
     if (M == 0) return;
     dim3 grid((M + CBM - 1) / CBM, (sh.Cin + CBN - 1) / CBN);
-    conv_dgrad_kernel<T><<<grid, NT, 0, s>>>(sh, dy, w, dx, mask);
+    launch_k(conv_dgrad_kernel<T>, dim3(grid), dim3(NT), 0, s, sh, dy, w, dx, mask);
 }
 int64_t conv_wgrad_workspace(const ConvShape& sh) {
     return (int64_t)wgrad_splits(sh) * sh.Cout * (sh.Cin * 9 + 1);
@@ -418,9 +423,9 @@ void launch_conv_wgrad(const ConvShape& sh, const T* dy, const T* x, T* dw, T* d
     const int chunk = (P + splits - 1) / splits;
     const int N = sh.Cin * 9 + 1;
     dim3 grid((N + WBN - 1) / WBN, (sh.Cout + WBM - 1) / WBM, splits);
-    conv_wgrad_kernel<T><<<grid, NT, 0, s>>>(sh, dy, x, work, chunk);
+    launch_k(conv_wgrad_kernel<T>, dim3(grid), dim3(NT), 0, s, sh, dy, x, work, chunk);
     const int tot = sh.Cout * N;
-    wgrad_reduce_kernel<T><<<(tot + 255) / 256, 256, 0, s>>>(work, splits, sh.Cout, N, dw, db);
+    launch_k(wgrad_reduce_kernel<T>, dim3((tot + 255) / 256), dim3(256), 0, s, work, splits, sh.Cout, N, dw, db);
 }
 
 template void launch_conv_fwd<float>(const ConvShape&, const float*, const float*, const float*, float*, bool, cudaStream_t);

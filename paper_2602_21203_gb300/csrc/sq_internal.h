@@ -124,6 +124,7 @@ struct squint_handle {
     float* dconv_b = nullptr;
     float* wgrad_work = nullptr;
     float* dxq = nullptr;             // [B, Dc] input gradient of the critics in the actor step
+    float* ln_work = nullptr;         // LayerNorm backward column partials
     float* dout_a = nullptr;          // [B, 2A]
 
     // BF16 shadows (tensor-core path)
@@ -184,11 +185,18 @@ struct squint_handle {
     int profile_kernels(int cap, char* names, int* launches, float* ms, double* work, int* unit, int* n,
                         cudaStream_t s);
     std::vector<cudaEvent_t>* phase_events = nullptr;   // set while profiling an eager update
+    // timing event on `s`; under stream capture it becomes an event-record node of the graph
+    static void record_timing(cudaEvent_t e, cudaStream_t s) {
+        cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(s, &st);
+        if (st == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
+    }
     void mark(cudaStream_t s) {
         if (phase_events) {
             cudaEvent_t e;
             cudaEventCreate(&e);
-            cudaEventRecord(e, s);
+            record_timing(e, s);
             phase_events->push_back(e);
         }
     }

@@ -113,7 +113,11 @@ struct LnBwdProblem {
     float* dg; float* dbeta;               // column sums (written) or null
     float* dbias;                          // sum of dpre over rows (linear bias grad) or null
 };
-void launch_ln_bwd(const LnBwdProblem* p, int n_probs, cudaStream_t s);
+// Column sums (dg, dbeta, dbias) need `work` of ln_bwd_workspace() floats (null: rows only).
+int64_t ln_bwd_workspace(const LnBwdProblem* p, int n_probs);
+void launch_ln_bwd(const LnBwdProblem* p, int n_probs, float* work, cudaStream_t s);
+// Opt the LayerNorm backward in to its shared memory (rows up to 2048 wide; call outside capture).
+void ln_prepare();
 
 // Column sums over rows: out[j] = sum_r in[r*ld + j] (deterministic order).
 struct ColSumProblem { int rows, n; const float* in; int64_t ld; float* out; };

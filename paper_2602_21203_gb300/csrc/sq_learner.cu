@@ -263,7 +263,7 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
         }
         {
             ProfScope ps(h, s, "layernorm_bwd", 4.0 * E * rows * sets[0][l].out * (grads ? 9.0 : 5.0), 1);
-            launch_ln_bwd(lb, E, s);
+            launch_ln_bwd(lb, E, h->ln_work, s);
         }
         if (grads) {
             h->fork(s, side);
@@ -370,6 +370,12 @@ int squint_handle::allocate() {
     dconv_b = dalloc<float>(maxc);
     wgrad_work = dalloc<float>(maxw);
     dxq = dalloc<float>((int64_t)B * L.dc);
+    {
+        int wmax = std::max(L.D, 1);
+        for (int l = 0; l < c.n_hidden; ++l) wmax = std::max(wmax, c.hidden[l]);
+        ln_work = dalloc<float>((int64_t)2 * ((B + 7) / 8) * 3 * wmax);
+    }
+    ln_prepare();
     dout_a = dalloc<float>((int64_t)B * 2 * A);
     if (bf16) {
         // padded BF16 weight copies: online for every linear layer, target for the critic range
@@ -539,7 +545,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         double bytes = 0;
         for (int i = 0; i < n; ++i) bytes += 36.0 * p[i].rows * p[i].n;
         ProfScope ps(this, st, "layernorm_bwd", bytes, 1);
-        launch_ln_bwd(p, n, st);
+        launch_ln_bwd(p, n, ln_work, st);
     };
     auto adam = [&](int64_t begin, int64_t end, const int32_t* step, const int32_t* enable, cudaStream_t st) {
         AdamArgs ad{};
@@ -1019,34 +1025,52 @@ const char* sq::phase_name(int i) {
 }
 
 int squint_handle::profile_update(float* ms, int cap, int* n_phases, cudaStream_t s) {
+    // captured (with its phase events) and replayed, like the timed graph
     std::vector<cudaEvent_t> ev;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    SQ_CK(this, cudaStreamSynchronize(s));
+    SQ_CK(this, cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
     phase_events = &ev;
-    record_update(0, s, false);
+    record_update(0, capture_stream, false);
     phase_events = nullptr;
-    int rc = SQUINT_OK;
-    if (cudaStreamSynchronize(s) != cudaSuccess) rc = SQUINT_ECUDA;
+    SQ_CK(this, cudaStreamEndCapture(capture_stream, &graph));
+    int rc = launch_failed ? SQUINT_EINVAL : SQUINT_OK;
+    if (rc == SQUINT_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = SQUINT_ECUDA;
+    if (rc == SQUINT_OK && cudaGraphLaunch(exec, s) != cudaSuccess) rc = SQUINT_ECUDA;
+    if (rc == SQUINT_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = SQUINT_ECUDA;
     const int n = (int)ev.size() - 1;
     if (n_phases) *n_phases = n;
     for (int i = 0; rc == SQUINT_OK && i < n && i < cap; ++i) {
         if (cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]) != cudaSuccess) rc = SQUINT_ECUDA;
     }
     for (auto e : ev) cudaEventDestroy(e);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
     if (rc != SQUINT_OK) { failed = true; g_last_error = "profiling failed"; }
     return rc;
 }
 
-// One eager update with every launch in order on `s`, each timed by its own events;
-// launches are grouped by kernel class.
+// One update with every launch in order on one stream, each bracketed by its own
+// events, captured as a graph and replayed (so the host's launch cost does not show up
+// as device time); launches are grouped by kernel class.  The replay is one real update.
 int squint_handle::profile_kernels(int cap, char* names, int* launches, float* ms, double* work, int* unit, int* n,
                                    cudaStream_t s) {
     std::vector<ProfEntry> recs;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    SQ_CK(this, cudaStreamSynchronize(s));
+    SQ_CK(this, cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
     prof = &recs;
     serial = true;
-    record_update(0, s, false);
+    record_update(0, capture_stream, false);
     serial = false;
     prof = nullptr;
-    int rc = SQUINT_OK;
-    if (cudaStreamSynchronize(s) != cudaSuccess) rc = SQUINT_ECUDA;
+    SQ_CK(this, cudaStreamEndCapture(capture_stream, &graph));
+    int rc = launch_failed ? SQUINT_EINVAL : SQUINT_OK;
+    if (rc == SQUINT_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = SQUINT_ECUDA;
+    if (rc == SQUINT_OK && cudaGraphLaunch(exec, s) != cudaSuccess) rc = SQUINT_ECUDA;
+    if (rc == SQUINT_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = SQUINT_ECUDA;
     std::vector<std::string> order;
     std::map<std::string, std::tuple<int, double, double, int>> agg;
     for (auto& e : recs) {
@@ -1064,6 +1088,8 @@ int squint_handle::profile_kernels(int cap, char* names, int* launches, float* m
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
     }
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
     if (rc != SQUINT_OK) { failed = true; g_last_error = "kernel profiling failed"; return rc; }
     *n = (int)order.size();
     for (int i = 0; i < (int)order.size() && i < cap; ++i) {

@@ -13,7 +13,11 @@ template <typename P> struct Batch { P p[kMaxLn]; int n; };
 
 // ---------------------------------------------------------------- LayerNorm
 // One warp per row: mean, variance (two passes over the row), affine, optional ReLU.
+// Rows up to 32 * kVpt wide are held in registers (all loads issued before any use).
+constexpr int kVpt = 16;
+
 __global__ void ln_fwd_kernel(Batch<LnProblem> b, int relu, float eps) {
+    SQ_KERNEL_ENTRY();
     const int warps = blockDim.x / 32;
     const int lane = threadIdx.x % 32;
     int gw = blockIdx.x * warps + threadIdx.x / 32;
@@ -22,6 +26,39 @@ __global__ void ln_fwd_kernel(Batch<LnProblem> b, int relu, float eps) {
     if (pi >= b.n) return;
     const LnProblem& P = b.p[pi];
     const float* x = P.pre + (int64_t)gw * P.ld_pre;
+    float* y = P.out + (int64_t)gw * P.ld_out;
+    if (P.n <= 32 * kVpt) {
+        float xv[kVpt];
+#pragma unroll
+        for (int k = 0; k < kVpt; ++k) {
+            const int j = lane + 32 * k;
+            xv[k] = j < P.n ? x[j] : 0.f;
+        }
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < kVpt; ++k) s += xv[k];
+        const float mean = warp_sum(s) / (float)P.n;
+        float q = 0.f;
+#pragma unroll
+        for (int k = 0; k < kVpt; ++k) {
+            const int j = lane + 32 * k;
+            const float d = j < P.n ? xv[k] - mean : 0.f;
+            q += d * d;
+        }
+        const float var = warp_sum(q) / (float)P.n;
+        const float rstd = 1.0f / sqrtf(var + eps);
+#pragma unroll
+        for (int k = 0; k < kVpt; ++k) {
+            const int j = lane + 32 * k;
+            if (j >= P.n) break;
+            float v = (xv[k] - mean) * rstd * P.g[j] + P.beta[j];
+            if (relu) v = fmaxf(v, 0.f);
+            y[j] = v;
+            if (P.out_bf) P.out_bf[(int64_t)gw * P.ld_out_bf + j] = __float2bfloat16_rn(v);
+        }
+        if (lane == 0) { P.mean[gw] = mean; P.rstd[gw] = rstd; }
+        return;
+    }
     float s = 0.f;
     for (int j = lane; j < P.n; j += 32) s += x[j];
     const float mean = warp_sum(s) / (float)P.n;
@@ -29,7 +66,6 @@ __global__ void ln_fwd_kernel(Batch<LnProblem> b, int relu, float eps) {
     for (int j = lane; j < P.n; j += 32) { const float d = x[j] - mean; q += d * d; }
     const float var = warp_sum(q) / (float)P.n;
     const float rstd = 1.0f / sqrtf(var + eps);
-    float* y = P.out + (int64_t)gw * P.ld_out;
     for (int j = lane; j < P.n; j += 32) {
         float v = (x[j] - mean) * rstd * P.g[j] + P.beta[j];
         if (relu) v = fmaxf(v, 0.f);
@@ -40,72 +76,131 @@ __global__ void ln_fwd_kernel(Batch<LnProblem> b, int relu, float eps) {
 }
 
 // Row part of the LayerNorm backward: dpre = rstd (dxh - mean(dxh) - xh mean(dxh xh)), dxh = dn g.
-__global__ void ln_bwd_row_kernel(Batch<LnBwdProblem> b) {
-    const int warps = blockDim.x / 32;
-    const int lane = threadIdx.x % 32;
-    int gw = blockIdx.x * warps + threadIdx.x / 32;
+// One warp per row, 8 rows per block, all rows of a block from one problem.  When column
+// sums are wanted, each warp also stores its row's dn xh, dn and dpre in shared memory and
+// the block adds its 8 rows in warp order into a partial row of `part`.
+struct LnBwdBatch {
+    LnBwdProblem p[kMaxLn];
+    int block_start[kMaxLn + 1];
+    int64_t part_off[kMaxLn];
+    int n;
+    float* part;
+};
+constexpr int kLnRows = 8;
+
+__global__ void __launch_bounds__(256) ln_bwd_row_kernel(LnBwdBatch b, int want_cols) {
+    SQ_KERNEL_ENTRY();
+    extern __shared__ float acc[];   // [8 warps][3][n] when want_cols
     int pi = 0;
-    while (pi < b.n && gw >= b.p[pi].rows) { gw -= b.p[pi].rows; ++pi; }
-    if (pi >= b.n) return;
+    while (pi + 1 < b.n && (int)blockIdx.x >= b.block_start[pi + 1]) ++pi;
     const LnBwdProblem& P = b.p[pi];
-    const float* dout = P.dout + (int64_t)gw * P.ld_dout;
-    const float* out = P.out ? P.out + (int64_t)gw * P.ld_out : nullptr;
-    const float* pre = P.pre + (int64_t)gw * P.ld_pre;
-    const float mean = P.mean[gw], rstd = P.rstd[gw];
-    float s1 = 0.f, s2 = 0.f;
-    for (int j = lane; j < P.n; j += 32) {
-        const float dn = (out && !(out[j] > 0.f)) ? 0.f : dout[j];
-        const float dxh = dn * P.g[j];
-        const float xh = (pre[j] - mean) * rstd;
-        s1 += dxh;
-        s2 += dxh * xh;
-    }
-    const float m1 = warp_sum(s1) / (float)P.n;
-    const float m2 = warp_sum(s2) / (float)P.n;
-    float* dpre = P.dpre + (int64_t)gw * P.ld_dpre;
-    for (int j = lane; j < P.n; j += 32) {
-        const float dn = (out && !(out[j] > 0.f)) ? 0.f : dout[j];
-        const float xh = (pre[j] - mean) * rstd;
-        const float v = rstd * (dn * P.g[j] - m1 - xh * m2);
-        dpre[j] = v;
-        if (P.dpre_bf) P.dpre_bf[(int64_t)gw * P.ld_dpre_bf + j] = __float2bfloat16_rn(v);
-    }
-}
-
-// Column part: dg = sum dn xh, dbeta = sum dn, dbias = sum dpre.  Block (32 columns x
-// 16 row slices): thread (x, y) sums rows y, y+16, ... in order, then the 16 slice
-// sums are added in slice order, so the result does not depend on scheduling.
-constexpr int kColX = 32, kColY = 16;
-__global__ void __launch_bounds__(kColX * kColY) ln_bwd_col_kernel(Batch<LnBwdProblem> b) {
-    __shared__ float part[3][kColY][kColX + 1];
-    const LnBwdProblem& P = b.p[blockIdx.y];
-    const int tx = threadIdx.x % kColX, ty = threadIdx.x / kColX;
-    const int j = blockIdx.x * kColX + tx;
-    float sg = 0.f, sb = 0.f, sd = 0.f;
-    if (j < P.n) {
-        for (int r = ty; r < P.rows; r += kColY) {
-            const float o = P.out ? P.out[(int64_t)r * P.ld_out + j] : 1.f;
-            const float dn = (P.out && !(o > 0.f)) ? 0.f : P.dout[(int64_t)r * P.ld_dout + j];
-            const float xh = (P.pre[(int64_t)r * P.ld_pre + j] - P.mean[r]) * P.rstd[r];
-            sg += dn * xh;
-            sb += dn;
-            if (P.dbias) sd += P.dpre[(int64_t)r * P.ld_dpre + j];
+    const int lb = blockIdx.x - b.block_start[pi];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int row = lb * kLnRows + warp;
+    const bool cols = want_cols && (P.dg || P.dbeta || P.dbias);
+    float* my = acc + (size_t)warp * 3 * P.n;
+    if (row < P.rows && P.n <= 32 * kVpt) {
+        const float* dout = P.dout + (int64_t)row * P.ld_dout;
+        const float* out = P.out ? P.out + (int64_t)row * P.ld_out : nullptr;
+        const float* pre = P.pre + (int64_t)row * P.ld_pre;
+        const float mean = P.mean[row], rstd = P.rstd[row];
+        float dn[kVpt], xh[kVpt], gg[kVpt];
+#pragma unroll
+        for (int k = 0; k < kVpt; ++k) {
+            const int j = lane + 32 * k;
+            const bool in = j < P.n;
+            const float d = in ? dout[j] : 0.f;
+            const float o = (in && out) ? out[j] : 1.f;
+            dn[k] = (out && !(o > 0.f)) ? 0.f : d;
+            xh[k] = in ? (pre[j] - mean) * rstd : 0.f;
+            gg[k] = in ? P.g[j] : 0.f;
         }
+        float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < kVpt; ++k) {
+            const float dxh = dn[k] * gg[k];
+            s1 += dxh;
+            s2 += dxh * xh[k];
+        }
+        const float m1 = warp_sum(s1) / (float)P.n;
+        const float m2 = warp_sum(s2) / (float)P.n;
+        float* dpre = P.dpre + (int64_t)row * P.ld_dpre;
+#pragma unroll
+        for (int k = 0; k < kVpt; ++k) {
+            const int j = lane + 32 * k;
+            if (j >= P.n) break;
+            const float v = rstd * (dn[k] * gg[k] - m1 - xh[k] * m2);
+            dpre[j] = v;
+            if (P.dpre_bf) P.dpre_bf[(int64_t)row * P.ld_dpre_bf + j] = __float2bfloat16_rn(v);
+            if (cols) {
+                my[j] = dn[k] * xh[k];
+                my[P.n + j] = dn[k];
+                my[2 * P.n + j] = v;
+            }
+        }
+    } else if (row < P.rows) {
+        const float* dout = P.dout + (int64_t)row * P.ld_dout;
+        const float* out = P.out ? P.out + (int64_t)row * P.ld_out : nullptr;
+        const float* pre = P.pre + (int64_t)row * P.ld_pre;
+        const float mean = P.mean[row], rstd = P.rstd[row];
+        float s1 = 0.f, s2 = 0.f;
+        for (int j = lane; j < P.n; j += 32) {
+            const float dn = (out && !(out[j] > 0.f)) ? 0.f : dout[j];
+            const float dxh = dn * P.g[j];
+            const float xh = (pre[j] - mean) * rstd;
+            s1 += dxh;
+            s2 += dxh * xh;
+        }
+        const float m1 = warp_sum(s1) / (float)P.n;
+        const float m2 = warp_sum(s2) / (float)P.n;
+        float* dpre = P.dpre + (int64_t)row * P.ld_dpre;
+        for (int j = lane; j < P.n; j += 32) {
+            const float dn = (out && !(out[j] > 0.f)) ? 0.f : dout[j];
+            const float xh = (pre[j] - mean) * rstd;
+            const float v = rstd * (dn * P.g[j] - m1 - xh * m2);
+            dpre[j] = v;
+            if (P.dpre_bf) P.dpre_bf[(int64_t)row * P.ld_dpre_bf + j] = __float2bfloat16_rn(v);
+            if (cols) {
+                my[j] = dn * xh;
+                my[P.n + j] = dn;
+                my[2 * P.n + j] = v;
+            }
+        }
+    } else if (cols) {
+        for (int j = lane; j < P.n; j += 32) { my[j] = 0.f; my[P.n + j] = 0.f; my[2 * P.n + j] = 0.f; }
     }
-    part[0][ty][tx] = sg;
-    part[1][ty][tx] = sb;
-    part[2][ty][tx] = sd;
+    if (!cols) return;
     __syncthreads();
-    if (ty == 0 && j < P.n) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-        for (int y = 0; y < kColY; ++y) { a0 += part[0][y][tx]; a1 += part[1][y][tx]; a2 += part[2][y][tx]; }
-        if (P.dg) P.dg[j] = a0;
-        if (P.dbeta) P.dbeta[j] = a1;
-        if (P.dbias) P.dbias[j] = a2;
+    float* part = b.part + b.part_off[pi] + (int64_t)lb * 3 * P.n;
+    for (int j = threadIdx.x; j < 3 * P.n; j += blockDim.x) {
+        float t = 0.f;
+        for (int w = 0; w < kLnRows; ++w) t += acc[(size_t)w * 3 * P.n + j];
+        part[j] = t;
     }
 }
 
+// Column sums from the block partials, added in block order.
+__global__ void ln_bwd_col_kernel(LnBwdBatch b) {
+    SQ_KERNEL_ENTRY();
+    const LnBwdProblem& P = b.p[blockIdx.y];
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.n || !(P.dg || P.dbeta || P.dbias)) return;
+    const int blocks = b.block_start[blockIdx.y + 1] - b.block_start[blockIdx.y];
+    const float* part = b.part + b.part_off[blockIdx.y];
+    float sg = 0.f, sb = 0.f, sd = 0.f;
+    for (int k = 0; k < blocks; ++k) {
+        sg += part[(int64_t)k * 3 * P.n + j];
+        sb += part[(int64_t)k * 3 * P.n + P.n + j];
+        sd += part[(int64_t)k * 3 * P.n + 2 * P.n + j];
+    }
+    if (P.dg) P.dg[j] = sg;
+    if (P.dbeta) P.dbeta[j] = sb;
+    if (P.dbias) P.dbias[j] = sd;
+}
+
+constexpr int kColX = 32, kColY = 16;
 __global__ void __launch_bounds__(kColX * kColY) colsum_kernel(Batch<ColSumProblem> b) {
+    SQ_KERNEL_ENTRY();
     __shared__ float part[kColY][kColX + 1];
     const ColSumProblem& P = b.p[blockIdx.y];
     const int tx = threadIdx.x % kColX, ty = threadIdx.x / kColX;
@@ -152,6 +247,7 @@ constexpr int kMaxAtoms = 256;
 // m_j = sum_i P_i max(0, 1 - |b_i - j|)   (linear interpolation between the two
 // neighbouring atoms of b_i = (clip(r + gamma (1-d)(z_i - alpha log pi')) - v_min)/dz).
 __global__ void c51_target_kernel(C51TargetArgs a) {
+    SQ_KERNEL_ENTRY();
     __shared__ float pbar[kMaxAtoms];
     __shared__ float bpos[kMaxAtoms];
     __shared__ float red[32];
@@ -188,6 +284,7 @@ __global__ void c51_target_kernel(C51TargetArgs a) {
 // ---------------------------------------------------------------- cross entropy
 // One block per (critic, sample): -sum m log softmax(l), d/dl = (softmax - m)/B, Q = sum softmax z.
 __global__ void ce_kernel(CeArgs a) {
+    SQ_KERNEL_ENTRY();
     __shared__ float red[32];
     const int er = blockIdx.x;          // e * B + row
     const int row = er % a.B;
@@ -219,6 +316,7 @@ __global__ void ce_kernel(CeArgs a) {
 // Actor objective through the critics: Q = sum p z, dQ/dl_j = p_j (z_j - Q),
 // d(-mean_i Q_i / B)/dl = -(1/(E B)) p (z - Q).
 __global__ void actor_q_kernel(ActorQArgs a) {
+    SQ_KERNEL_ENTRY();
     if (!*a.do_actor) return;
     __shared__ float red[32];
     __shared__ float qs;
@@ -251,6 +349,7 @@ __device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.f) + log
 // log_std = lo + (hi-lo)/2 (tanh(raw)+1); u = mu + std eps; a = tanh(u);
 // log pi = sum_k [-eps^2/2 - log_std - log(2 pi)/2 - 2 (log 2 - u - softplus(-2u))].
 __global__ void actor_head_kernel(ActorHeadArgs a) {
+    SQ_KERNEL_ENTRY();
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= a.rows) return;
     const bool tgt = row < a.B;
@@ -277,6 +376,7 @@ __global__ void actor_head_kernel(ActorHeadArgs a) {
 // Reparameterised backward: du = da (1 - a^2) + dlogp 2a; dlog_std = du std eps - dlogp;
 // draw = dlog_std (hi-lo)/2 (1 - tanh(raw)^2).
 __global__ void actor_head_bwd_kernel(ActorHeadBwdArgs a) {
+    SQ_KERNEL_ENTRY();
     if (a.do_actor && !*a.do_actor) return;
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= a.B) return;
@@ -303,6 +403,7 @@ __global__ void actor_head_bwd_kernel(ActorHeadBwdArgs a) {
 
 // Inference head: tanh(mu) or tanh(mu + std eps) with eps from the request key.
 __global__ void act_head_kernel(ActHeadArgs a) {
+    SQ_KERNEL_ENTRY();
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= a.rows) return;
     const int q = a.row_req[row];
@@ -325,6 +426,7 @@ __global__ void act_head_kernel(ActHeadArgs a) {
 // ---------------------------------------------------------------- temperature + statistics
 // stats layout: 0 critic loss, 1 actor loss, 2 alpha loss, 3 alpha, 4 q mean, 5 entropy, 6 update idx (as float bits: low), 7 unused
 __global__ void alpha_kernel(AlphaArgs a) {
+    SQ_KERNEL_ENTRY();
     __shared__ float red[32];
     float s = 0.f;
     for (int i = threadIdx.x; i < a.B; i += blockDim.x) s += a.logp_t[i];
@@ -349,6 +451,7 @@ __global__ void alpha_kernel(AlphaArgs a) {
 }
 
 __global__ void stats_kernel(StatsArgs a) {
+    SQ_KERNEL_ENTRY();
     __shared__ float red[32];
     const int n = a.E * a.B;
     float l = 0.f, q = 0.f;
@@ -378,7 +481,16 @@ __global__ void stats_kernel(StatsArgs a) {
 }
 
 // ---------------------------------------------------------------- Adam and polyak
+__device__ __forceinline__ float adam_one(float p, float g, float& m, float& v, float b1, float b2, float c1, float c2,
+                                          float lr, float ep, float bc1, float bc2) {
+    m = b1 * m + c1 * g;
+    v = b2 * v + c2 * g * g;
+    return p - lr * (m / bc1) / (sqrtf(v / bc2) + ep);
+}
+
+// Elementwise Adam over [0, n): scalar head up to 16-byte alignment, float4 body, scalar tail.
 __global__ void adam_kernel(AdamArgs a) {
+    SQ_KERNEL_ENTRY();
     if (a.enable && !*a.enable) return;
     __shared__ float bc[2];
     if (threadIdx.x == 0) {
@@ -389,19 +501,45 @@ __global__ void adam_kernel(AdamArgs a) {
     __syncthreads();
     const float b1 = (float)a.b1, b2 = (float)a.b2, lr = (float)a.lr, ep = (float)a.eps;
     const float c1 = (float)(1.0 - a.b1), c2 = (float)(1.0 - a.b2);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float g = a.g[i];
-        const float m = b1 * a.m[i] + c1 * g;
-        const float v = b2 * a.v[i] + c2 * g * g;
-        a.m[i] = m;
-        a.v[i] = v;
-        const float p = a.p[i] - lr * (m / bc[0]) / (sqrtf(v / bc[1]) + ep);
-        a.p[i] = p;
+    const float bc1 = bc[0], bc2 = bc[1];
+    const int64_t mis = (int64_t)((16 - (reinterpret_cast<uintptr_t>(a.p) & 15)) & 15) / 4;
+    const int64_t head = mis < a.n ? mis : a.n;
+    const int64_t nv = (a.n - head) / 4;
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < head; i += stride) {
+        float m = a.m[i], v = a.v[i];
+        const float p = adam_one(a.p[i], a.g[i], m, v, b1, b2, c1, c2, lr, ep, bc1, bc2);
+        a.m[i] = m; a.v[i] = v; a.p[i] = p;
+        if (a.p_bf) a.p_bf[i] = __float2bfloat16_rn(p);
+    }
+    float4* p4 = reinterpret_cast<float4*>(a.p + head);
+    const float4* g4 = reinterpret_cast<const float4*>(a.g + head);
+    float4* m4 = reinterpret_cast<float4*>(a.m + head);
+    float4* v4 = reinterpret_cast<float4*>(a.v + head);
+    for (int64_t i = tid; i < nv; i += stride) {
+        float4 p = p4[i], m = m4[i], v = v4[i];
+        const float4 g = g4[i];
+        p.x = adam_one(p.x, g.x, m.x, v.x, b1, b2, c1, c2, lr, ep, bc1, bc2);
+        p.y = adam_one(p.y, g.y, m.y, v.y, b1, b2, c1, c2, lr, ep, bc1, bc2);
+        p.z = adam_one(p.z, g.z, m.z, v.z, b1, b2, c1, c2, lr, ep, bc1, bc2);
+        p.w = adam_one(p.w, g.w, m.w, v.w, b1, b2, c1, c2, lr, ep, bc1, bc2);
+        p4[i] = p; m4[i] = m; v4[i] = v;
+        if (a.p_bf) {
+            const int64_t e = head + 4 * i;
+            a.p_bf[e] = __float2bfloat16_rn(p.x); a.p_bf[e + 1] = __float2bfloat16_rn(p.y);
+            a.p_bf[e + 2] = __float2bfloat16_rn(p.z); a.p_bf[e + 3] = __float2bfloat16_rn(p.w);
+        }
+    }
+    for (int64_t i = head + 4 * nv + tid; i < a.n; i += stride) {
+        float m = a.m[i], v = a.v[i];
+        const float p = adam_one(a.p[i], a.g[i], m, v, b1, b2, c1, c2, lr, ep, bc1, bc2);
+        a.m[i] = m; a.v[i] = v; a.p[i] = p;
         if (a.p_bf) a.p_bf[i] = __float2bfloat16_rn(p);
     }
 }
 
 __global__ void polyak_kernel(PolyakArgs a) {
+    SQ_KERNEL_ENTRY();
     const float keep = 1.0f - a.tau;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
         a.target[i] = keep * a.target[i] + a.tau * a.src[i];
@@ -422,23 +560,44 @@ void launch_ln_fwd(const LnProblem* p, int n, bool relu, float eps, cudaStream_t
         auto b = make_batch(p + base, cnt);
         int rows = 0;
         for (int i = 0; i < cnt; ++i) rows += b.p[i].rows;
-        if (rows) ln_fwd_kernel<<<(rows + 7) / 8, 256, 0, s>>>(b, relu ? 1 : 0, eps);
+        if (rows) launch_k(ln_fwd_kernel, dim3((rows + 7) / 8), dim3(256), 0, s, b, relu ? 1 : 0, eps);
     }
 }
-void launch_ln_bwd(const LnBwdProblem* p, int n, cudaStream_t s) {
+void ln_prepare() {
+    cudaFuncSetAttribute(ln_bwd_row_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kLnRows * 3 * 2048 * 4);
+}
+
+int64_t ln_bwd_workspace(const LnBwdProblem* p, int n) {
+    int64_t w = 0;
+    for (int i = 0; i < n; ++i) w += (int64_t)((p[i].rows + kLnRows - 1) / kLnRows) * 3 * p[i].n;
+    return w;
+}
+
+void launch_ln_bwd(const LnBwdProblem* p, int n, float* work, cudaStream_t s) {
     for (int base = 0; base < n; base += kMaxLn) {
         const int cnt = std::min(kMaxLn, n - base);
-        auto b = make_batch(p + base, cnt);
-        int rows = 0, cols = 0;
+        LnBwdBatch b{};
+        b.n = cnt;
+        b.part = work;
+        int blocks = 0, cols = 0;
+        int64_t off = 0;
         bool any_col = false;
         for (int i = 0; i < cnt; ++i) {
-            rows += b.p[i].rows;
+            b.p[i] = p[base + i];
+            b.block_start[i] = blocks;
+            b.part_off[i] = off;
+            const int nb = (b.p[i].rows + kLnRows - 1) / kLnRows;
+            blocks += nb;
+            off += (int64_t)nb * 3 * b.p[i].n;
             cols = std::max(cols, b.p[i].n);
-            any_col |= b.p[i].dg || b.p[i].dbeta || b.p[i].dbias;
+            any_col |= (b.p[i].dg || b.p[i].dbeta || b.p[i].dbias);
         }
-        if (!rows) continue;
-        ln_bwd_row_kernel<<<(rows + 7) / 8, 256, 0, s>>>(b);
-        if (any_col) ln_bwd_col_kernel<<<dim3((cols + kColX - 1) / kColX, cnt), kColX * kColY, 0, s>>>(b);
+        b.block_start[cnt] = blocks;
+        if (!blocks) continue;
+        const bool want = any_col && work && cols <= 2048;
+        const size_t smem = want ? (size_t)kLnRows * 3 * cols * sizeof(float) : 0;
+        launch_k(ln_bwd_row_kernel, dim3(blocks), dim3(32 * kLnRows), smem, s, b, want ? 1 : 0);
+        if (want) launch_k(ln_bwd_col_kernel, dim3(dim3((cols + 127) / 128, cnt)), dim3(128), 0, s, b);
     }
 }
 void launch_colsum(const ColSumProblem* p, int n, cudaStream_t s) {
@@ -447,30 +606,30 @@ void launch_colsum(const ColSumProblem* p, int n, cudaStream_t s) {
         auto b = make_batch(p + base, cnt);
         int cols = 0;
         for (int i = 0; i < cnt; ++i) cols = std::max(cols, b.p[i].n);
-        if (cols) colsum_kernel<<<dim3((cols + kColX - 1) / kColX, cnt), kColX * kColY, 0, s>>>(b);
+        if (cols) launch_k(colsum_kernel, dim3(dim3((cols + kColX - 1) / kColX, cnt)), dim3(kColX * kColY), 0, s, b);
     }
 }
 void launch_actor_head(const ActorHeadArgs& a, cudaStream_t s) {
-    actor_head_kernel<<<(a.rows + 127) / 128, 128, 0, s>>>(a);
+    launch_k(actor_head_kernel, dim3((a.rows + 127) / 128), dim3(128), 0, s, a);
 }
 void launch_actor_head_bwd(const ActorHeadBwdArgs& a, cudaStream_t s) {
-    actor_head_bwd_kernel<<<(a.B + 127) / 128, 128, 0, s>>>(a);
+    launch_k(actor_head_bwd_kernel, dim3((a.B + 127) / 128), dim3(128), 0, s, a);
 }
-void launch_c51_target(const C51TargetArgs& a, cudaStream_t s) { c51_target_kernel<<<a.B, 128, 0, s>>>(a); }
-void launch_ce(const CeArgs& a, cudaStream_t s) { ce_kernel<<<a.E * a.B, 128, 0, s>>>(a); }
-void launch_actor_q(const ActorQArgs& a, cudaStream_t s) { actor_q_kernel<<<a.E * a.B, 128, 0, s>>>(a); }
-void launch_alpha_step(const AlphaArgs& a, cudaStream_t s) { alpha_kernel<<<1, 256, 0, s>>>(a); }
-void launch_stats(const StatsArgs& a, cudaStream_t s) { stats_kernel<<<1, 256, 0, s>>>(a); }
+void launch_c51_target(const C51TargetArgs& a, cudaStream_t s) { launch_k(c51_target_kernel, dim3(a.B), dim3(128), 0, s, a); }
+void launch_ce(const CeArgs& a, cudaStream_t s) { launch_k(ce_kernel, dim3(a.E * a.B), dim3(128), 0, s, a); }
+void launch_actor_q(const ActorQArgs& a, cudaStream_t s) { launch_k(actor_q_kernel, dim3(a.E * a.B), dim3(128), 0, s, a); }
+void launch_alpha_step(const AlphaArgs& a, cudaStream_t s) { launch_k(alpha_kernel, dim3(1), dim3(256), 0, s, a); }
+void launch_stats(const StatsArgs& a, cudaStream_t s) { launch_k(stats_kernel, dim3(1), dim3(256), 0, s, a); }
 void launch_adam(const AdamArgs& a, cudaStream_t s) {
-    const int blocks = (int)std::min<int64_t>((a.n + 255) / 256, 152 * 8);
-    if (a.n > 0) adam_kernel<<<blocks, 256, 0, s>>>(a);
+    const int blocks = (int)std::min<int64_t>((a.n / 4 + 255) / 256 + 1, 152 * 4);
+    if (a.n > 0) launch_k(adam_kernel, dim3(blocks), dim3(256), 0, s, a);
 }
 void launch_polyak(const PolyakArgs& a, cudaStream_t s) {
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, 152 * 8));
-    polyak_kernel<<<blocks, 256, 0, s>>>(a);
+    launch_k(polyak_kernel, dim3(blocks), dim3(256), 0, s, a);
 }
 void launch_act_head(const ActHeadArgs& a, cudaStream_t s) {
-    if (a.rows > 0) act_head_kernel<<<(a.rows + 127) / 128, 128, 0, s>>>(a);
+    if (a.rows > 0) launch_k(act_head_kernel, dim3((a.rows + 127) / 128), dim3(128), 0, s, a);
 }
 
 }  // namespace sq

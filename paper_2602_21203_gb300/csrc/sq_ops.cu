@@ -202,7 +202,13 @@ int squint_op_layernorm_bwd(int rows, int n, const float* dy, const float* y, co
     p.dout = dy; p.ld_dout = n; p.out = y; p.ld_out = n; p.pre = x; p.ld_pre = n;
     p.mean = mean; p.rstd = rstd; p.g = g; p.dpre = dx; p.ld_dpre = n;
     p.dg = dg; p.dbeta = db;
-    launch_ln_bwd(&p, 1, (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    float* work = nullptr;
+    const int64_t wn = ln_bwd_workspace(&p, 1);
+    if ((dg || db) && cudaMallocAsync((void**)&work, (size_t)wn * sizeof(float), s) != cudaSuccess) return SQUINT_ECUDA;
+    ln_prepare();
+    launch_ln_bwd(&p, 1, work, s);
+    if (work) cudaFreeAsync(work, s);
     return launch_status();
 }
 

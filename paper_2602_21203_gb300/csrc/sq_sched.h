@@ -71,12 +71,12 @@ struct ProfScope {
         squint_handle::ProfEntry e{name, nullptr, nullptr, work, unit};
         cudaEventCreate(&e.a);
         cudaEventCreate(&e.b);
-        cudaEventRecord(e.a, s);
+        squint_handle::record_timing(e.a, s);
         h->prof->push_back(e);
         idx = (int)h->prof->size() - 1;
     }
     ~ProfScope() {
-        if (idx >= 0) cudaEventRecord((*h->prof)[idx].b, s);
+        if (idx >= 0) squint_handle::record_timing((*h->prof)[idx].b, s);
     }
 };
 

@@ -28,7 +28,7 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
 constexpr int TILE_BYTES = BM * BK * 2;                // 16 KB per operand per stage
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + BN * 4;
 constexpr long long kWaitCycles = 4000000000ll;        // ~2 s at 2 GHz
 constexpr int kMaxProbs = 4;
 
@@ -109,6 +109,17 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -139,10 +150,12 @@ __device__ __forceinline__ void load_operand(uint32_t dst, const CUtensorMap* ma
 
 template <bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ TcBatch gb) {
+    SQ_KERNEL_ENTRY();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    float* bias_s = reinterpret_cast<float*>(tmem_slot + 4);          // [BN]
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done_bar = smem_u32(bars + 2 * STAGES);
 
     int pi = 0;
@@ -165,6 +178,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int j = threadIdx.x; j < BN; j += blockDim.x) bias_s[j] = (P.bias && n0 + j < P.N) ? P.bias[n0 + j] : 0.f;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -209,34 +223,35 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const int row = m0 + warp * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    const bool full_cols = (n0 + BN <= P.N);
+    const bool row_ok = have && row < P.M;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t r[16];
-        tmem_ld16(trow + c0, r);
-        if (!have || row >= P.M || n0 + c0 >= P.N) continue;
-        float v[16];
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        tmem_ld32(trow + c0, r);
+        if (!row_ok || n0 + c0 >= P.N) continue;
+        float v[32];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            v[j] = __uint_as_float(r[j]);
-            const int n = n0 + c0 + j;
-            if (P.bias && n < P.N) v[j] += P.bias[n];
-            if (P.mask && n < P.N && !(P.mask[(int64_t)row * P.ldmask + n] > 0.f)) v[j] = 0.f;
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) + bias_s[c0 + j];
+        if (P.mask) {
+            const float* mk = P.mask + (int64_t)row * P.ldmask + n0 + c0;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (n0 + c0 + j < P.N && !(mk[j] > 0.f)) v[j] = 0.f;
         }
-        const bool vec = full_cols || (n0 + c0 + 16 <= P.N);
+        const bool full = n0 + c0 + 32 <= P.N;
         if (P.c) {
             float* dst = P.c + (int64_t)row * P.ldc + n0 + c0;
-            if (vec && !P.accumulate && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
+            if (full && !P.accumulate && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
 #pragma unroll
-                for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
             } else {
-                for (int j = 0; j < 16; ++j)
+                for (int j = 0; j < 32; ++j)
                     if (n0 + c0 + j < P.N) dst[j] = P.accumulate ? dst[j] + v[j] : v[j];
             }
         }
         if (P.cbf) {
             __nv_bfloat16* dst = P.cbf + (int64_t)row * P.ldcbf + n0 + c0;
-            for (int j = 0; j < 16; ++j)
+            for (int j = 0; j < 32; ++j)
                 if (n0 + c0 + j < P.N) dst[j] = __float2bfloat16_rn(v[j]);
         }
     }
@@ -322,10 +337,10 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s) {
             tiles += ((g.M + BM - 1) / BM) * p.tiles_n;
         }
         if (!tiles) continue;
-        if (!a_mn && !b_mn) tc_gemm_kernel<false, false><<<tiles, 128, SMEM_BYTES, s>>>(gb);
-        else if (!a_mn && b_mn) tc_gemm_kernel<false, true><<<tiles, 128, SMEM_BYTES, s>>>(gb);
-        else if (a_mn && b_mn) tc_gemm_kernel<true, true><<<tiles, 128, SMEM_BYTES, s>>>(gb);
-        else tc_gemm_kernel<true, false><<<tiles, 128, SMEM_BYTES, s>>>(gb);
+        if (!a_mn && !b_mn) launch_k(tc_gemm_kernel<false, false>, dim3(tiles), dim3(128), SMEM_BYTES, s, gb);
+        else if (!a_mn && b_mn) launch_k(tc_gemm_kernel<false, true>, dim3(tiles), dim3(128), SMEM_BYTES, s, gb);
+        else if (a_mn && b_mn) launch_k(tc_gemm_kernel<true, true>, dim3(tiles), dim3(128), SMEM_BYTES, s, gb);
+        else launch_k(tc_gemm_kernel<true, false>, dim3(tiles), dim3(128), SMEM_BYTES, s, gb);
     }
     return 0;
 }
@@ -337,6 +352,7 @@ struct CastBatch { CastItem it[kMaxCast]; int row_start[kMaxCast + 1]; int n; };
 
 // One CTA per (matrix, row): FP32 row -> BF16 row of a padded matrix (pad columns zero).
 __global__ void cast_rows_kernel(CastBatch cb) {
+    SQ_KERNEL_ENTRY();
     int i = 0;
     while (i + 1 < cb.n && (int)blockIdx.x >= cb.row_start[i + 1]) ++i;
     const CastItem& c = cb.it[i];
@@ -359,7 +375,7 @@ void launch_cast_rows(const CastItem* items, int n, cudaStream_t s) {
             rows += items[base + i].rows;
         }
         cb.row_start[cb.n] = rows;
-        if (rows) cast_rows_kernel<<<rows, 128, 0, s>>>(cb);
+        if (rows) launch_k(cast_rows_kernel, dim3(rows), dim3(128), 0, s, cb);
     }
 }
 
