@@ -31,9 +31,12 @@ extern "C" {
  * M-major; likewise for B), 16-byte aligned, the other stride a multiple of 8;
  * C and bias FP32.  This is the dense contraction of every linear layer (Sec. III:
  * critic and actor networks): forward X W^T, data gradient dY W, weight gradient dY^T X.
+ * BF16 products with few 128 x 128 output tiles and a long K split K over a cluster of
+ * CTAs whose partial tiles are added in a fixed order: repeated calls give identical bits.
  */
 int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, int64_t sa_k, const void* B,
                    int64_t sb_n, int64_t sb_k, void* C, int64_t ldc, const void* bias, int accumulate, void* stream);
+
 
 /*
  * Valid 3x3 convolution, NCHW (the encoder layers, Sec. III "single shared CNN

@@ -84,7 +84,10 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
         if (!mine) continue;
         const int width = d.which == 2 ? a.A : a.P;
         const float* s = d.which == 2 ? a.action + idx * a.A : a.proprio + slot * a.P;
-        for (int k = threadIdx.x; k < width; k += blockDim.x) d.ptr[(int64_t)b * d.ld + d.col + k] = s[k];
+        for (int k = threadIdx.x; k < width; k += blockDim.x) {
+            d.ptr[(int64_t)b * d.ld + d.col + k] = s[k];
+            if (d.ptr_h) d.ptr_h[(int64_t)b * d.ld_h + d.col + k] = __float2bfloat16_rn(s[k]);
+        }
     }
 }
 

@@ -12,6 +12,8 @@ struct CopyDst {
     int64_t ld;      // row stride (elements)
     int col;         // first column
     int which;       // 0: proprio[idx], 1: proprio[nxt], 2: action[idx]
+    __nv_bfloat16* ptr_h;   // optional BF16 copy (same column, row stride ld_h)
+    int64_t ld_h;
 };
 struct FrontendArgs {
     const uint8_t* obs;
@@ -114,6 +116,9 @@ struct LnBwdProblem {
     float* dbias;                          // sum of dpre over rows (linear bias grad) or null
 };
 // Column sums (dg, dbeta, dbias) need `work` of ln_bwd_workspace() floats (null: rows only).
+// Its first kLnTickets words are ticket counters that must be zero before the first launch;
+// every launch leaves them zero again.  Launches that share a workspace must be stream-ordered.
+constexpr int kLnTickets = 64;
 int64_t ln_bwd_workspace(const LnBwdProblem* p, int n_probs);
 void launch_ln_bwd(const LnBwdProblem* p, int n_probs, float* work, cudaStream_t s);
 // Opt the LayerNorm backward in to its shared memory (rows up to 2048 wide; call outside capture).
@@ -131,6 +136,8 @@ struct ActorHeadArgs {
     uint64_t seed; const int64_t* update_idx;
     float* a_dst0; int64_t ld0;     // actions of rows < B
     float* a_dst1; int64_t ld1;     // actions of rows >= B
+    __nv_bfloat16* a_dst0_h; int64_t ld0_h;   // optional BF16 copies
+    __nv_bfloat16* a_dst1_h; int64_t ld1_h;
     float* logp;                    // [rows]
     float* eps;                     // [rows, A] saved noise
     const float* eps_in;            // optional: noise given instead of drawn

@@ -373,7 +373,8 @@ int squint_handle::allocate() {
     {
         int wmax = std::max(L.D, 1);
         for (int l = 0; l < c.n_hidden; ++l) wmax = std::max(wmax, c.hidden[l]);
-        ln_work = dalloc<float>((int64_t)2 * ((B + 7) / 8) * 3 * wmax);
+        ln_work = dalloc<float>(kLnTickets + (int64_t)2 * ((B + 7) / 8) * 3 * wmax);
+        if (ln_work) cudaMemset(ln_work, 0, kLnTickets * sizeof(float));
     }
     ln_prepare();
     dout_a = dalloc<float>((int64_t)B * 2 * A);
@@ -568,12 +569,13 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     fa.seed = c.seed; fa.update_idx = d_update_idx;
     fa.x = x2; fa.x_bf = nullptr; fa.sums = debug ? sums : nullptr;
     fa.idx_out = idx2; fa.shift_out = shift2; fa.r_out = r; fa.d_out = d;
-    fa.dst[0] = CopyDst{xc, Dc, Z, 0};
-    fa.dst[1] = CopyDst{xc, Dc, Z + P, 2};
-    fa.dst[2] = CopyDst{xq, Dc, Z, 0};
-    fa.dst[3] = CopyDst{xa + (int64_t)B * Da, Da, Z, 0};
-    fa.dst[4] = CopyDst{xa, Da, Z, 1};
-    fa.dst[5] = CopyDst{xcbar, Dc, Z, 1};
+    // the transition fields land in the head inputs, with their BF16 shadows in BF16 mode
+    fa.dst[0] = CopyDst{xc, Dc, Z, 0, xc_h, Dc8};
+    fa.dst[1] = CopyDst{xc, Dc, Z + P, 2, xc_h, Dc8};
+    fa.dst[2] = CopyDst{xq, Dc, Z, 0, xq_h, Dc8};
+    fa.dst[3] = CopyDst{xa + (int64_t)B * Da, Da, Z, 0, xa_h ? xa_h + (int64_t)B * Da8 : nullptr, Da8};
+    fa.dst[4] = CopyDst{xa, Da, Z, 1, xa_h, Da8};
+    fa.dst[5] = CopyDst{xcbar, Dc, Z, 1, xcbar_h, Dc8};
     fa.n_dst = 6;
     fa.steps = d_steps; fa.do_actor = d_do_actor; fa.policy_freq = c.policy_freq;
     {
@@ -637,13 +639,16 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         LnProblem lp[4];
         const LayerRef* refs[4] = {&ap, &cpt, &cp, &ap};
         float* outs[4] = {xa, xcbar, xc, xa + (int64_t)B * Da};
+        __nv_bfloat16* outs_h[4] = {xa_h, xcbar_h, xc_h, xa_h ? xa_h + (int64_t)B * Da8 : nullptr};
         const int64_t lds[4] = {Da, Dc, Dc, Da};
+        const int64_t lds_h[4] = {Da8, Dc8, Dc8, Da8};
         for (int i = 0; i < 4; ++i) {
             LnProblem p{};
             p.rows = B; p.n = Dd;
             p.pre = proj_pre + i * (int64_t)B * Dd; p.ld_pre = Dd;
             p.g = refs[i]->g; p.beta = refs[i]->beta;
             p.out = outs[i]; p.ld_out = lds[i];
+            if (bf16) { p.out_bf = outs_h[i]; p.ld_out_bf = lds_h[i]; }
             p.mean = proj_mean + i * B; p.rstd = proj_rstd + i * B;
             lp[i] = p;
         }
@@ -656,8 +661,10 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         cudaMemcpy2DAsync(xc, Dc * sizeof(float), z, fb, fb, B, cudaMemcpyDeviceToDevice, s);
         cudaMemcpy2DAsync(xq, Dc * sizeof(float), z, fb, fb, B, cudaMemcpyDeviceToDevice, s);
     }
-    cast_rows(xa, Da, 2 * B, Da, xa_h, Da8, s);
-    cast_rows(xc, Dc, B, Dc, xc_h, Dc8, s);
+    if (Dd == 0) {     // flatten path: the features were copied in FP32 only
+        cast_rows(xa, Da, 2 * B, Da, xa_h, Da8, s);
+        cast_rows(xc, Dc, B, Dc, xc_h, Dc8, s);
+    }
 
     const MlpRef actor_on = mlp_ref(this, L.actor, false);
     const MlpRef crit_on[2] = {mlp_ref(this, L.critic[0], false), mlp_ref(this, L.critic[1], false)};
@@ -678,12 +685,16 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ah.seed = c.seed; ah.update_idx = d_update_idx;
         ah.a_dst0 = xcbar + Z + P; ah.ld0 = Dc;
         ah.a_dst1 = xq + Z + P; ah.ld1 = Dc;
+        if (bf16) {
+            ah.a_dst0_h = xcbar_h + Z + P; ah.ld0_h = Dc8;
+            ah.a_dst1_h = xq_h + Z + P; ah.ld1_h = Dc8;
+        }
         ah.logp = logp; ah.eps = eps;
         {
             ProfScope ps(this, s, "heads_losses", 0, 1);
             launch_actor_head(ah, s);
         }
-        cast_rows(xcbar, Dc, B, Dc, xcbar_h, Dc8, s);
+        if (Dd == 0) cast_rows(xcbar, Dc, B, Dc, xcbar_h, Dc8, s);
     }
     mark(s);
     // ---- a8-a9: target critics and the projected categorical target
@@ -863,10 +874,12 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             p.pre = proj_pre + 4 * (int64_t)B * Dd; p.ld_pre = Dd;
             p.g = cp.g; p.beta = cp.beta;
             p.out = xq; p.ld_out = Dc;
+            if (bf16) { p.out_bf = xq_h; p.ld_out_bf = Dc8; }
             p.mean = proj_mean + 4 * B; p.rstd = proj_rstd + 4 * B;
             ln_fwd(&p, 1, false, s);
+        } else {
+            cast_rows(xq, Dc, B, Dc, xq_h, Dc8, s);
         }
-        cast_rows(xq, Dc, B, Dc, xq_h, Dc8, s);
         mlp_forward(this, qcrit_mlp, crit_on, E, Mat{xq, Dc, xq_h, Dc8}, B, bf16, s);
         ActorQArgs aq{};
         aq.B = B; aq.K = K; aq.E = E; aq.logits = qcrit_mlp.out;

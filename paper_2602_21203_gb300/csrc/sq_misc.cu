@@ -75,16 +75,19 @@ __global__ void ln_fwd_kernel(Batch<LnProblem> b, int relu, float eps) {
     if (lane == 0) { P.mean[gw] = mean; P.rstd[gw] = rstd; }
 }
 
-// Row part of the LayerNorm backward: dpre = rstd (dxh - mean(dxh) - xh mean(dxh xh)), dxh = dn g.
+// LayerNorm backward: dpre = rstd (dxh - mean(dxh) - xh mean(dxh xh)), dxh = dn g.
 // One warp per row, 8 rows per block, all rows of a block from one problem.  When column
 // sums are wanted, each warp also stores its row's dn xh, dn and dpre in shared memory and
-// the block adds its 8 rows in warp order into a partial row of `part`.
+// the block adds its 8 rows in warp order into a partial row of `part`; the block that
+// finishes last for a problem (ticket counter) then adds the partial rows in block order,
+// so the sums do not depend on which block finished when.
 struct LnBwdBatch {
     LnBwdProblem p[kMaxLn];
     int block_start[kMaxLn + 1];
     int64_t part_off[kMaxLn];
     int n;
     float* part;
+    unsigned* tickets;   // one per problem, zero between launches
 };
 constexpr int kLnRows = 8;
 
@@ -171,31 +174,37 @@ __global__ void __launch_bounds__(256) ln_bwd_row_kernel(LnBwdBatch b, int want_
     }
     if (!cols) return;
     __syncthreads();
-    float* part = b.part + b.part_off[pi] + (int64_t)lb * 3 * P.n;
+    float* part = b.part + b.part_off[pi];
     for (int j = threadIdx.x; j < 3 * P.n; j += blockDim.x) {
         float t = 0.f;
         for (int w = 0; w < kLnRows; ++w) t += acc[(size_t)w * 3 * P.n + j];
-        part[j] = t;
+        part[(int64_t)lb * 3 * P.n + j] = t;
     }
-}
-
-// Column sums from the block partials, added in block order.
-__global__ void ln_bwd_col_kernel(LnBwdBatch b) {
-    SQ_KERNEL_ENTRY();
-    const LnBwdProblem& P = b.p[blockIdx.y];
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P.n || !(P.dg || P.dbeta || P.dbias)) return;
-    const int blocks = b.block_start[blockIdx.y + 1] - b.block_start[blockIdx.y];
-    const float* part = b.part + b.part_off[blockIdx.y];
-    float sg = 0.f, sb = 0.f, sd = 0.f;
-    for (int k = 0; k < blocks; ++k) {
-        sg += part[(int64_t)k * 3 * P.n + j];
-        sb += part[(int64_t)k * 3 * P.n + P.n + j];
-        sd += part[(int64_t)k * 3 * P.n + 2 * P.n + j];
+    // publish this block's partial row, then take a ticket
+    __shared__ int last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const int blocks = b.block_start[pi + 1] - b.block_start[pi];
+        last = atomicAdd(&b.tickets[pi], 1u) == (unsigned)(blocks - 1);
     }
-    if (P.dg) P.dg[j] = sg;
-    if (P.dbeta) P.dbeta[j] = sb;
-    if (P.dbias) P.dbias[j] = sd;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int blocks = b.block_start[pi + 1] - b.block_start[pi];
+    for (int j = threadIdx.x; j < P.n; j += blockDim.x) {
+        float sg = 0.f, sb = 0.f, sd = 0.f;
+        for (int k = 0; k < blocks; ++k) {
+            const float* pk = part + (int64_t)k * 3 * P.n;
+            sg += __ldcg(pk + j);
+            sb += __ldcg(pk + P.n + j);
+            sd += __ldcg(pk + 2 * P.n + j);
+        }
+        if (P.dg) P.dg[j] = sg;
+        if (P.dbeta) P.dbeta[j] = sb;
+        if (P.dbias) P.dbias[j] = sd;
+    }
+    if (threadIdx.x == 0) b.tickets[pi] = 0u;
 }
 
 constexpr int kColX = 32, kColY = 16;
@@ -367,8 +376,13 @@ __global__ void actor_head_kernel(ActorHeadArgs a) {
         const float act = tanhf(uu);
         lp += -0.5f * eps * eps - ls - 0.91893853320467274f - 2.0f * (0.69314718055994531f - uu - softplusf(-2.0f * uu));
         if (a.eps) a.eps[(int64_t)row * a.A + k] = eps;
-        if (tgt) a.a_dst0[(int64_t)row * a.ld0 + k] = act;
-        else a.a_dst1[(int64_t)el * a.ld1 + k] = act;
+        if (tgt) {
+            a.a_dst0[(int64_t)row * a.ld0 + k] = act;
+            if (a.a_dst0_h) a.a_dst0_h[(int64_t)row * a.ld0_h + k] = __float2bfloat16_rn(act);
+        } else {
+            a.a_dst1[(int64_t)el * a.ld1 + k] = act;
+            if (a.a_dst1_h) a.a_dst1_h[(int64_t)el * a.ld1_h + k] = __float2bfloat16_rn(act);
+        }
     }
     a.logp[row] = lp;
 }
@@ -570,7 +584,7 @@ void ln_prepare() {
 int64_t ln_bwd_workspace(const LnBwdProblem* p, int n) {
     int64_t w = 0;
     for (int i = 0; i < n; ++i) w += (int64_t)((p[i].rows + kLnRows - 1) / kLnRows) * 3 * p[i].n;
-    return w;
+    return w + kLnTickets;
 }
 
 void launch_ln_bwd(const LnBwdProblem* p, int n, float* work, cudaStream_t s) {
@@ -578,7 +592,6 @@ void launch_ln_bwd(const LnBwdProblem* p, int n, float* work, cudaStream_t s) {
         const int cnt = std::min(kMaxLn, n - base);
         LnBwdBatch b{};
         b.n = cnt;
-        b.part = work;
         int blocks = 0, cols = 0;
         int64_t off = 0;
         bool any_col = false;
@@ -596,8 +609,10 @@ void launch_ln_bwd(const LnBwdProblem* p, int n, float* work, cudaStream_t s) {
         if (!blocks) continue;
         const bool want = any_col && work && cols <= 2048;
         const size_t smem = want ? (size_t)kLnRows * 3 * cols * sizeof(float) : 0;
+        // the tickets sit in the first kLnTickets words of the workspace, the partials after them
+        b.tickets = reinterpret_cast<unsigned*>(work);
+        b.part = work ? work + kLnTickets : nullptr;
         launch_k(ln_bwd_row_kernel, dim3(blocks), dim3(32 * kLnRows), smem, s, b, want ? 1 : 0);
-        if (want) launch_k(ln_bwd_col_kernel, dim3(dim3((cols + 127) / 128, cnt)), dim3(128), 0, s, b);
     }
 }
 void launch_colsum(const ColSumProblem* p, int n, cudaStream_t s) {

@@ -5,8 +5,13 @@
 #include "sq_tc.cuh"
 
 #include <mutex>
+#include <string>
 
 using namespace sq;
+
+namespace sq {
+extern thread_local std::string g_last_error;
+}
 
 namespace {
 
@@ -37,6 +42,22 @@ bool conv_ok(int nimg, int cin, int h, int w, int cout, int stride) {
     return nimg >= 0 && cin > 0 && cout > 0 && h >= 3 && w >= 3 && stride >= 1;
 }
 
+// BF16 problem of the op entry points: majorness from the unit stride of each operand.
+bool bf16_problem(int M, int N, int K, const void* A, int64_t sa_m, int64_t sa_k, const void* B, int64_t sb_n,
+                  int64_t sb_k, void* C, int64_t ldc, const void* bias, int accumulate, TcGemm* g) {
+    g->M = M; g->N = N; g->K = K; g->n_pairs = 1;
+    if (sa_k == 1) g->a[0] = TcOperand{(const __nv_bfloat16*)A, sa_m, false};
+    else if (sa_m == 1) g->a[0] = TcOperand{(const __nv_bfloat16*)A, sa_k, true};
+    else return false;
+    if (sb_k == 1) g->b[0] = TcOperand{(const __nv_bfloat16*)B, sb_n, false};
+    else if (sb_n == 1) g->b[0] = TcOperand{(const __nv_bfloat16*)B, sb_k, true};
+    else return false;
+    g->bias = (const float*)bias;
+    g->c = (float*)C; g->ldc = ldc;
+    g->accumulate = accumulate;
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -63,16 +84,7 @@ int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, 
     }
     if (dtype != SQUINT_DT_BF16) return SQUINT_EINVAL;
     TcGemm g{};
-    g.M = M; g.N = N; g.K = K; g.n_pairs = 1;
-    if (sa_k == 1) g.a[0] = TcOperand{(const __nv_bfloat16*)A, sa_m, false};
-    else if (sa_m == 1) g.a[0] = TcOperand{(const __nv_bfloat16*)A, sa_k, true};
-    else return SQUINT_EINVAL;
-    if (sb_k == 1) g.b[0] = TcOperand{(const __nv_bfloat16*)B, sb_n, false};
-    else if (sb_n == 1) g.b[0] = TcOperand{(const __nv_bfloat16*)B, sb_k, true};
-    else return SQUINT_EINVAL;
-    g.bias = (const float*)bias;
-    g.c = (float*)C; g.ldc = ldc;
-    g.accumulate = accumulate;
+    if (!bf16_problem(M, N, K, A, sa_m, sa_k, B, sb_n, sb_k, C, ldc, bias, accumulate, &g)) return SQUINT_EINVAL;
     int* err = tc_error_flag();
     if (!err) return SQUINT_ECUDA;
     if (launch_tc_gemm(&g, 1, err, s) != 0) return SQUINT_EINVAL;
@@ -206,6 +218,7 @@ int squint_op_layernorm_bwd(int rows, int n, const float* dy, const float* y, co
     float* work = nullptr;
     const int64_t wn = ln_bwd_workspace(&p, 1);
     if ((dg || db) && cudaMallocAsync((void**)&work, (size_t)wn * sizeof(float), s) != cudaSuccess) return SQUINT_ECUDA;
+    if (work) cudaMemsetAsync(work, 0, kLnTickets * sizeof(float), s);
     ln_prepare();
     launch_ln_bwd(&p, 1, work, s);
     if (work) cudaFreeAsync(work, s);

@@ -1,13 +1,19 @@
 // BF16 tensor-core GEMM for sm_103a: D[M,N] (+)= sum_pairs A[M,K] B[N,K]^T, FP32
 // accumulation in tensor memory.
 //
-// Per CTA one 128 x 128 output tile:
-//   warp 0 / lane 0   TMA producer: 128B-swizzled 64-wide K slabs of A and B into a
-//                     4-stage shared-memory ring (mbarrier complete_tx)
-//   warp 1 / lane 0   MMA issuer: 4 x tcgen05.mma (K = 16 each) per slab, commit frees
+// Per CTA one 128 x 128 output tile, or one K range of it when the launch splits K over
+// a thread-block cluster (few output tiles, long K):
+//   warp 1 / lane 0   TMA producer: initialises the barriers (before the programmatic
+//                     wait), then streams 128B-swizzled 64-wide K slabs of A and B into a
+//                     6-stage shared-memory ring (mbarrier complete_tx)
+//   warp 0 / lane 0   MMA issuer: 4 x tcgen05.mma (K = 16 each) per slab, commit frees
 //                     the slab, a final commit signals the accumulator
-//   warps 0-3         epilogue: tcgen05.ld 32 lanes x 16 columns at a time, bias,
-//                     optional ReLU mask, FP32 and/or BF16 stores
+//   warps 0-3         epilogue: each thread moves its accumulator row from tensor memory
+//                     to shared memory (the idle operand ring); after a cluster barrier
+//                     each CTA of the cluster adds the partial tiles of its band of rows
+//                     in rank order through distributed shared memory, then applies
+//                     bias and the optional ReLU mask and stores FP32 and/or BF16 rows
+//                     with coalesced vector stores
 // Operands are K-major (K contiguous) or MN-major (M or N contiguous), so the
 // forward X W^T, the data gradient dY W and the weight gradient dY^T X all run
 // from the row-major buffers without transposed copies.
@@ -25,10 +31,12 @@ namespace sq {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
 constexpr int TILE_BYTES = BM * BK * 2;                // 16 KB per operand per stage
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + BN * 4;
+constexpr int RED_LD = BN + 4;   // FP32 row stride of the accumulator tile in shared memory
+static_assert(BM * RED_LD * 4 <= STAGES * STAGE_BYTES, "accumulator tile must fit in the operand stages");
 constexpr long long kWaitCycles = 4000000000ll;        // ~2 s at 2 GHz
 constexpr int kMaxProbs = 4;
 
@@ -36,7 +44,7 @@ struct TcProb {
     CUtensorMap ta[2];
     CUtensorMap tb[2];
     int M, N, K, n_pairs;
-    int tiles_n, tile_start;
+    int tiles_n, tile_start;   // tile_start: first CTA of this problem
     const float* bias;
     float* c; int64_t ldc;
     __nv_bfloat16* cbf; int64_t ldcbf;
@@ -46,6 +54,7 @@ struct TcProb {
 struct TcBatch {
     TcProb p[kMaxProbs];
     int n;
+    int splits;       // CTAs per output tile = cluster size (K split)
     int* err;
 };
 
@@ -85,6 +94,23 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
         : "memory");
 }
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Arrive at and wait on the cluster barrier (every thread of every CTA of the cluster);
+// release/acquire order this CTA's shared-memory writes before the other CTAs' reads.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Generic address of the same shared-memory location in CTA `rank` of the cluster
+// (distributed shared memory; ordinary loads through it are scheduled like any other).
+__device__ __forceinline__ const float* map_rank(const float* p, int rank) {
+    uint64_t r;
+    asm("mapa.u64 %0, %1, %2;" : "=l"(r) : "l"(reinterpret_cast<uint64_t>(p)), "r"(rank));
+    return reinterpret_cast<const float*>(r);
+}
 // Shared-memory matrix descriptor, 128-byte swizzle (sm_100 family descriptor version 1).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -120,15 +146,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 // Operand tile in shared memory: K-major is 128 rows x 128 B (8-row groups 1024 B apart);
 // MN-major is two 64-wide column blocks of 64 K rows (K groups of 8 rows 1024 B apart,
 // the second MN block 8 KB further).  Descriptor of the 16-wide K step kk.
@@ -150,7 +167,6 @@ __device__ __forceinline__ void load_operand(uint32_t dst, const CUtensorMap* ma
 
 template <bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ TcBatch gb) {
-    SQ_KERNEL_ENTRY();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -161,44 +177,75 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     int pi = 0;
     while (pi + 1 < gb.n && (int)blockIdx.x >= gb.p[pi + 1].tile_start) ++pi;
     const TcProb& P = gb.p[pi];
-    const int t = blockIdx.x - P.tile_start;
-    const int m0 = (t / P.tiles_n) * BM, n0 = (t % P.tiles_n) * BN;
+    // the problem's scalars, read once: P lives in the parameter block and is reached
+    // through a generic pointer, which the compiler would otherwise re-read after every store
+    const int pM = P.M, pN = P.N, pK = P.K, n_pairs = P.n_pairs, tiles_n = P.tiles_n;
+    const float* const p_bias = P.bias;
+    float* const p_c = P.c;
+    const int64_t p_ldc = P.ldc;
+    __nv_bfloat16* const p_cbf = P.cbf;
+    const int64_t p_ldcbf = P.ldcbf;
+    const float* const p_mask = P.mask;
+    const int64_t p_ldmask = P.ldmask;
+    const bool p_acc = P.accumulate != 0;
+    const int cta = blockIdx.x - P.tile_start;
+    const int t = cta / gb.splits, split = (int)cluster_rank();
+    const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const uint32_t base = smem_u32(smem);
+    const int nkb = (pK + BK - 1) / BK;
+    // this CTA's share of the (pair, K slab) iterations
+    const int it0 = (int)((int64_t)nkb * n_pairs * split / gb.splits);
+    const int total = (int)((int64_t)nkb * n_pairs * (split + 1) / gb.splits) - it0;
+    const bool producer = warp == 1 && lane == 0, issuer = warp == 0 && lane == 0;
+    auto load_stage = [&](int i) {
+        const int s = i % STAGES;
+        const int pr = (it0 + i) / nkb, kb = (it0 + i) % nkb;
+        const uint32_t st = base + s * STAGE_BYTES;
+        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+        load_operand<A_MN>(st, &P.ta[pr], m0, kb * BK, full0 + 8 * s);
+        load_operand<B_MN>(st + TILE_BYTES, &P.tb[pr], n0, kb * BK, full0 + 8 * s);
+    };
 
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(BN));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (threadIdx.x == 32) {
+    // CTA-local setup overlaps the tail of the previous kernel (programmatic launch)
+    if (producer) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, 1);
         }
         mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int q = 0; q < n_pairs; ++q) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.ta[q])) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.tb[q])) : "memory");
+        }
     }
-    for (int j = threadIdx.x; j < BN; j += blockDim.x) bias_s[j] = (P.bias && n0 + j < P.N) ? P.bias[n0 + j] : 0.f;
+    // inputs are read, and tensor memory taken, only once the previous kernel has finished:
+    // a kernel that holds tensor memory never waits on a later one
+    SQ_KERNEL_ENTRY();
+    const int pre = total < STAGES ? total : STAGES;
+    if (producer)
+        for (int i = 0; i < pre; ++i) load_stage(i);   // first stages: no slot to wait for
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t base = smem_u32(smem);
-    const int nkb = (P.K + BK - 1) / BK;
-    const int total = nkb * P.n_pairs;
+    // the bias is first read in the epilogue, after the cluster barrier
+    if (warp >= 2)
+        for (int j = threadIdx.x - 64; j < BN; j += 64) bias_s[j] = (p_bias && n0 + j < pN) ? p_bias[n0 + j] : 0.f;
 
-    if (warp == 0 && lane == 0) {
-        // producer
-        for (int i = 0; i < total; ++i) {
+    if (producer) {
+        for (int i = pre; i < total; ++i) {
             const int s = i % STAGES;
-            if (i >= STAGES && !mbar_wait(empty0 + 8 * s, ((i / STAGES) - 1) & 1, gb.err, 1)) break;
-            const int pr = i / nkb, kb = i % nkb;
-            const uint32_t st = base + s * STAGE_BYTES;
-            mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-            load_operand<A_MN>(st, &P.ta[pr], m0, kb * BK, full0 + 8 * s);
-            load_operand<B_MN>(st + TILE_BYTES, &P.tb[pr], n0, kb * BK, full0 + 8 * s);
+            if (!mbar_wait(empty0 + 8 * s, ((i / STAGES) - 1) & 1, gb.err, 1)) break;
+            load_stage(i);
         }
-    } else if (warp == 1 && lane == 0) {
+    } else if (issuer) {
         // MMA issuer
         constexpr uint32_t idesc = idesc_bf16(BM, BN, A_MN, B_MN);
         bool ok = true;
@@ -218,43 +265,165 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     }
     __syncwarp();
 
-    // epilogue
+    // epilogue, part 1: every thread moves its accumulator row from tensor memory into
+    // shared memory (the operand stages are idle once the final commit has arrived)
     const bool have = mbar_wait(done_bar, 0, gb.err, 3);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int row = m0 + warp * 32 + lane;
+    float* red = reinterpret_cast<float*>(smem);   // [BM][RED_LD]
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    const bool row_ok = have && row < P.M;
+    {
+        float* mine = red + (warp * 32 + lane) * RED_LD;
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-        uint32_t r[32];
-        tmem_ld32(trow + c0, r);
-        if (!row_ok || n0 + c0 >= P.N) continue;
-        float v[32];
+        for (int c0 = 0; c0 < BN; c0 += 32) {
+            uint32_t r[32];
+            tmem_ld32(trow + c0, r);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) + bias_s[c0 + j];
-        if (P.mask) {
-            const float* mk = P.mask + (int64_t)row * P.ldmask + n0 + c0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (n0 + c0 + j < P.N && !(mk[j] > 0.f)) v[j] = 0.f;
-        }
-        const bool full = n0 + c0 + 32 <= P.N;
-        if (P.c) {
-            float* dst = P.c + (int64_t)row * P.ldc + n0 + c0;
-            if (full && !P.accumulate && ((reinterpret_cast<uintptr_t>(dst) & 15) == 0)) {
-#pragma unroll
-                for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            } else {
-                for (int j = 0; j < 32; ++j)
-                    if (n0 + c0 + j < P.N) dst[j] = P.accumulate ? dst[j] + v[j] : v[j];
-            }
-        }
-        if (P.cbf) {
-            __nv_bfloat16* dst = P.cbf + (int64_t)row * P.ldcbf + n0 + c0;
-            for (int j = 0; j < 32; ++j)
-                if (n0 + c0 + j < P.N) dst[j] = __float2bfloat16_rn(v[j]);
+            for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4*>(mine + c0 + j) =
+                    make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]), __uint_as_float(r[j + 2]),
+                                __uint_as_float(r[j + 3]));
         }
     }
+    (void)have;   // a wait that gave up has set *err; the tile's values are then meaningless
+    cluster_sync();
+    // part 2: CTA `split` of the cluster finishes rows [split BM / S, (split + 1) BM / S),
+    // adding the S partial tiles in rank order.  Warp w takes rows rb0 + w, rb0 + w + 4, ...,
+    // 4 columns a lane, 8 rows at a time so that their loads are in flight together; each
+    // output (mask, FP32 store or accumulate, BF16 store) then runs as its own loop.
+    {
+        const int S = gb.splits;
+        const int rb0 = split * BM / S, rb1 = (split + 1) * BM / S;
+        const int cq = lane * 4;
+        const int col = n0 + cq;
+        const int nv = col < pN ? min(4, pN - col) : 0;   // valid columns of this lane
+        const int nrows = rb1 - rb0 > warp ? (rb1 - rb0 - warp + 3) / 4 : 0;
+        const bool cvec = nv == 4 && (p_ldc & 3) == 0 && ((reinterpret_cast<uintptr_t>(p_c) & 15) == 0);
+        const bool hvec = nv == 4 && (p_ldcbf & 3) == 0 && ((reinterpret_cast<uintptr_t>(p_cbf) & 7) == 0);
+        const bool mvec = nv == 4 && (p_ldmask & 3) == 0 && ((reinterpret_cast<uintptr_t>(p_mask) & 15) == 0);
+        float bias4[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bias4[j] = bias_s[cq + j];
+        const float* mine = red + (rb0 + warp) * RED_LD + cq;   // row g of this warp at mine + 4 g RED_LD
+#pragma unroll 1
+        for (int g0 = 0; g0 < nrows; g0 += 8) {
+            const int cnt = min(8, nrows - g0);
+            float4 acc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) acc[i] = make_float4(bias4[0], bias4[1], bias4[2], bias4[3]);
+            // rank order: acc = bias + p_0 + p_1 + ... (two ranks' loads in flight at a time)
+            int q = 0;
+            for (; q + 1 < S; q += 2) {
+                const float* s0 = map_rank(mine, q) + (size_t)g0 * 4 * RED_LD;
+                const float* s1 = map_rank(mine, q + 1) + (size_t)g0 * 4 * RED_LD;
+                float4 x0[8], x1[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    x0[i] = i < cnt ? *reinterpret_cast<const float4*>(s0 + (size_t)i * 4 * RED_LD) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    x1[i] = i < cnt ? *reinterpret_cast<const float4*>(s1 + (size_t)i * 4 * RED_LD) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    acc[i].x += x0[i].x; acc[i].y += x0[i].y; acc[i].z += x0[i].z; acc[i].w += x0[i].w;
+                    acc[i].x += x1[i].x; acc[i].y += x1[i].y; acc[i].z += x1[i].z; acc[i].w += x1[i].w;
+                }
+            }
+            if (q < S) {
+                const float* s0 = map_rank(mine, q) + (size_t)g0 * 4 * RED_LD;
+                float4 x0[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    x0[i] = i < cnt ? *reinterpret_cast<const float4*>(s0 + (size_t)i * 4 * RED_LD) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    acc[i].x += x0[i].x; acc[i].y += x0[i].y; acc[i].z += x0[i].z; acc[i].w += x0[i].w;
+                }
+            }
+            const int row0 = m0 + rb0 + warp + 4 * g0;   // row of entry i: row0 + 4 i
+            const int rows_ok = nv > 0 ? max(0, min(cnt, (pM - row0 + 3) / 4)) : 0;
+            if (p_mask) {
+                if (mvec) {
+                    float4 mk[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < rows_ok) mk[i] = *reinterpret_cast<const float4*>(p_mask + (int64_t)(row0 + 4 * i) * p_ldmask + col);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < rows_ok) {
+                            if (!(mk[i].x > 0.f)) acc[i].x = 0.f;
+                            if (!(mk[i].y > 0.f)) acc[i].y = 0.f;
+                            if (!(mk[i].z > 0.f)) acc[i].z = 0.f;
+                            if (!(mk[i].w > 0.f)) acc[i].w = 0.f;
+                        }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < rows_ok) {
+                            const float* mk = p_mask + (int64_t)(row0 + 4 * i) * p_ldmask + col;
+                            if (!(mk[0] > 0.f)) acc[i].x = 0.f;
+                            if (nv > 1 && !(mk[1] > 0.f)) acc[i].y = 0.f;
+                            if (nv > 2 && !(mk[2] > 0.f)) acc[i].z = 0.f;
+                            if (nv > 3 && !(mk[3] > 0.f)) acc[i].w = 0.f;
+                        }
+                }
+            }
+            if (p_c) {
+                if (cvec) {
+                    if (p_acc) {
+                        float4 old[8];
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (i < rows_ok) old[i] = *reinterpret_cast<const float4*>(p_c + (int64_t)(row0 + 4 * i) * p_ldc + col);
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            if (i < rows_ok) {
+                                acc[i].x += old[i].x; acc[i].y += old[i].y; acc[i].z += old[i].z; acc[i].w += old[i].w;
+                            }
+                    }
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < rows_ok) *reinterpret_cast<float4*>(p_c + (int64_t)(row0 + 4 * i) * p_ldc + col) = acc[i];
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < rows_ok) {
+                            float* dst = p_c + (int64_t)(row0 + 4 * i) * p_ldc + col;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const float v = j == 0 ? acc[i].x : j == 1 ? acc[i].y : j == 2 ? acc[i].z : acc[i].w;
+                                if (j < nv) dst[j] = p_acc ? dst[j] + v : v;
+                            }
+                        }
+                }
+            }
+            if (p_cbf) {
+                if (hvec) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < rows_ok) {
+                            __nv_bfloat162 lo = __floats2bfloat162_rn(acc[i].x, acc[i].y);
+                            __nv_bfloat162 hi = __floats2bfloat162_rn(acc[i].z, acc[i].w);
+                            uint2 u;
+                            u.x = *reinterpret_cast<uint32_t*>(&lo);
+                            u.y = *reinterpret_cast<uint32_t*>(&hi);
+                            *reinterpret_cast<uint2*>(p_cbf + (int64_t)(row0 + 4 * i) * p_ldcbf + col) = u;
+                        }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        if (i < rows_ok) {
+                            __nv_bfloat16* dst = p_cbf + (int64_t)(row0 + 4 * i) * p_ldcbf + col;
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) {
+                                const float v = j == 0 ? acc[i].x : j == 1 ? acc[i].y : j == 2 ? acc[i].z : acc[i].w;
+                                if (j < nv) dst[j] = __float2bfloat16_rn(v);
+                            }
+                        }
+                }
+            }
+        }
+    }
+    // no CTA of the cluster leaves while another may still read its shared memory
+    cluster_sync();
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -305,12 +474,42 @@ void set_smem_attr() {
 
 }  // namespace
 
+// K split of a launch (the cluster size): enough CTAs to cover the SMs when the launch
+// has few output tiles, every problem keeping at least kMinSplitIters K slabs per split.
+constexpr int kSplitTarget = 148, kMinSplitIters = 6, kMaxSplits = 8;
+
+namespace {
+int g_max_splits = 1;   // largest cluster the device can co-schedule for the GEMM kernel
+}
+
 void tc_prepare() {
     set_smem_attr<false, false>();
     set_smem_attr<false, true>();
     set_smem_attr<true, true>();
     set_smem_attr<true, false>();
     encode_fn();
+    static bool done = false;
+    if (done) return;
+    done = true;
+    for (int S = 2; S <= kMaxSplits; S *= 2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(S);
+        cfg.blockDim = dim3(128);
+        cfg.dynamicSmemBytes = SMEM_BYTES;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = S;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_kernel<false, false>, &cfg) != cudaSuccess || n < 1) {
+            cudaGetLastError();
+            break;
+        }
+        g_max_splits = S;
+    }
 }
 
 int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s) {
@@ -319,7 +518,7 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s) {
         std::memset(&gb, 0, sizeof(gb));
         gb.n = std::min(kMaxProbs, n_probs - base);
         gb.err = err;
-        int tiles = 0;
+        int tiles = 0, min_iters = 1 << 30;
         bool a_mn = probs[base].a[0].mn_major, b_mn = probs[base].b[0].mn_major;
         for (int i = 0; i < gb.n; ++i) {
             const TcGemm& g = probs[base + i];
@@ -333,14 +532,20 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s) {
             p.bias = g.bias; p.c = g.c; p.ldc = g.ldc; p.cbf = g.cbf; p.ldcbf = g.ldcbf;
             p.mask = g.mask; p.ldmask = g.ldmask; p.accumulate = g.accumulate;
             p.tiles_n = (g.N + BN - 1) / BN;
-            p.tile_start = tiles;
+            p.tile_start = tiles;   // in tiles for now, scaled by the split below
             tiles += ((g.M + BM - 1) / BM) * p.tiles_n;
+            min_iters = std::min(min_iters, ((g.K + BK - 1) / BK) * g.n_pairs);
         }
         if (!tiles) continue;
-        if (!a_mn && !b_mn) launch_k(tc_gemm_kernel<false, false>, dim3(tiles), dim3(128), SMEM_BYTES, s, gb);
-        else if (!a_mn && b_mn) launch_k(tc_gemm_kernel<false, true>, dim3(tiles), dim3(128), SMEM_BYTES, s, gb);
-        else if (a_mn && b_mn) launch_k(tc_gemm_kernel<true, true>, dim3(tiles), dim3(128), SMEM_BYTES, s, gb);
-        else launch_k(tc_gemm_kernel<true, false>, dim3(tiles), dim3(128), SMEM_BYTES, s, gb);
+        int S = std::min(std::min(g_max_splits, std::max(1, kSplitTarget / tiles)), min_iters / kMinSplitIters);
+        S = std::max(S, 1);
+        gb.splits = S;
+        for (int i = 0; i < gb.n; ++i) gb.p[i].tile_start *= S;
+        const dim3 grid(tiles * S), cluster(S);
+        if (!a_mn && !b_mn) launch_kc(tc_gemm_kernel<false, false>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
+        else if (!a_mn && b_mn) launch_kc(tc_gemm_kernel<false, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
+        else if (a_mn && b_mn) launch_kc(tc_gemm_kernel<true, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
+        else launch_kc(tc_gemm_kernel<true, false>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
     }
     return 0;
 }

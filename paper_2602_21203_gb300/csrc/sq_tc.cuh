@@ -26,7 +26,10 @@ struct TcGemm {
     int accumulate;           // c += D instead of c = D
 };
 
-// Launches one grouped kernel per up to 4 problems (all of one A/B majorness).
+// Launches one grouped kernel per up to 4 problems (all of one A/B majorness).  When
+// the launch has few output tiles and a long K, the K range of each tile is split over
+// a thread-block cluster of up to 8 CTAs; the CTAs add their partial tiles through
+// distributed shared memory in rank order, so the result is the same on every run.
 // Returns 0, or < 0 if a tensor map cannot describe an operand (alignment, extents).
 // *err (device int) receives a nonzero code if a bounded wait gave up.
 int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s);

@@ -72,6 +72,34 @@ def test_bf16_gemm_accumulates(ops):
     assert _rel(out.cpu().numpy(), ref) < 1e-5
 
 
+SPLIT_SHAPES = [(512, 256, 2592), (512, 512, 512), (300, 101, 2740), (128, 12, 4096), (1, 1, 800),
+                (256, 2592, 512), (130, 130, 1536)]
+
+
+@pytest.mark.parametrize("a_mn,b_mn", [(False, False), (False, True), (True, True)])
+@pytest.mark.parametrize("shape", SPLIT_SHAPES)
+def test_bf16_gemm_k_split_over_cluster(ops, a_mn, b_mn, shape):
+    """Few output tiles and a long K split K over a CTA cluster: same product (FP64 of
+    the BF16 operands), identical bits on a repeat call, accumulate adds onto the output."""
+    M, N, K = shape
+    g = torch.Generator().manual_seed(M + 5 * N + 11 * K)
+    a, A = _operand(M, K, a_mn, g)
+    b, B = _operand(N, K, b_mn, g)
+    bias = torch.randn(N, generator=g)
+    out = ops.gemm(A, B, bias=bias.cuda(), M=M, N=N, K=K)
+    again = ops.gemm(A, B, bias=bias.cuda(), M=M, N=N, K=K)
+    torch.cuda.synchronize()
+    ref = a.double().numpy() @ b.double().numpy().T + bias.double().numpy()
+    assert _rel(out.cpu().numpy(), ref) < 1e-5, (shape, a_mn, b_mn)
+    assert torch.equal(out, again)
+    base = torch.randn(M, N, generator=g)
+    acc = base.clone().cuda()
+    ops.gemm(A, B, out=acc, accumulate=True, M=M, N=N, K=K)
+    torch.cuda.synchronize()
+    ref2 = base.double().numpy() + a.double().numpy() @ b.double().numpy().T
+    assert _rel(acc.cpu().numpy(), ref2) < 1e-5
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_cuda_core_gemm_layouts(ops, dtype):
     g = torch.Generator().manual_seed(4)
