@@ -27,14 +27,19 @@ if ROOT not in sys.path:
 
 WORKLOAD = "train_b512"
 UTD_K = 4
-METRIC = "SAC updates/s at B=512 (UTD-4 CUDA graph)"
+METRIC = "SAC updates/s at B=512 (BF16 vs FP32 plain); act p50/p99 latency on 1 GB300"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 N_SM = 152
 FP32_LANES_PER_SM = 128
 
-# DRAM traffic per launch of the dominant phase from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by (phase, precision).
-NCU_TRAFFIC = {}
+# DRAM traffic per launch of the dominant kernel class from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the class's launches
+# in one update; ncu replays each launch with cold caches), keyed by (class,
+# precision).  Set back to nothing when the kernel changes.
+NCU_TRAFFIC = {
+    # 14 forward GEMM launches of one BF16 update, 30.07 MB read, 0 written
+    ("tc_gemm_fwd", "bf16"): 2147566,
+}
 
 
 def parse():
@@ -43,7 +48,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="bf16")
+    ap.add_argument("--no-fp32-compare", action="store_true",
+                    help="skip timing the plain FP32 path beside the BF16 one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
@@ -356,6 +363,32 @@ def run_ours(args):
     serving = None
     if not args.no_serving and rank == 0:
         serving = measure_serving(lib, learner, cfg, stream)
+    gpu_launches = learner.graph_kernel_count(UTD_K) * K
+    learner.close()
+
+    # ---- the plain FP32 path on the same ring and schedule, for the BF16-vs-FP32 comparison
+    fp32_plain = None
+    if prec == lib.PREC_BF16 and not args.no_fp32_compare:
+        plain = lib.Learner(cfg, ring, precision=lib.PREC_FP32, max_k=8)
+        with torch.cuda.stream(stream):
+            for _ in range(W):
+                plain.update(UTD_K, stats=False, stream=stream)
+        stream.synchronize()
+        Kp = min(K, 30)
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(Kp):
+            plain.update(UTD_K, stats=False, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        pms = max_over_ranks(ev0.elapsed_time(ev1), world)
+        fp32_plain = {"value": world * Kp * UTD_K / (pms / 1000.0), "unit": "updates/s", "steps": Kp,
+                      "ms_per_step": pms / Kp, "dtype": "f32",
+                      "path": "same kernels' FP32 variants: CUDA-core GEMMs and convolutions, no BF16 casts"}
+        fp32_plain["bf16_speedup"] = value / fp32_plain["value"]
+        plain.close()
 
     # ---- CPU baseline: the oracle on this workload, rank 0 at N=1
     cpu = None
@@ -365,7 +398,6 @@ def run_ours(args):
         cpu = {"value": ups, "unit": "updates/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"{n} FP64 oracle update(s) of the full batch-512 workload in {dt:.1f} s"}
 
-    kernels = learner.graph_kernel_count(UTD_K)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": K, "warmup": W,
@@ -379,12 +411,13 @@ def run_ours(args):
                              "weights and activations stay L2-resident between updates as in training",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": kernels * K, "clocks": clk,
+            "gpu_launches": gpu_launches, "clocks": clk,
         }
+        if fp32_plain:
+            line["fp32_plain"] = fp32_plain
         if serving:
             line["serving"] = serving
         print(json.dumps(line), flush=True)
-    learner.close()
 
 
 def measure_serving(lib, learner, cfg, upd_stream, seconds=4.0, n_envs=4096, mean_step_us=200.0):

@@ -100,6 +100,13 @@ int64_t squint_op_conv3x3_wgrad_noalloc_max(void);
 int squint_op_conv3x3_wgrad_noalloc(int nimg, int cin, int h, int w, int cout, int stride, const float* x,
                                     const float* dy, float* dw, float* db, void* stream);
 
+/*
+ * ReLU backward given the ReLU's output: dx[i] = dy[i] if y[i] > 0 else 0 (the
+ * nonlinearity after every encoder and hidden layer, Sec. IV).  F32 or F64;
+ * dx may alias dy.
+ */
+int squint_op_relu_bwd(int dtype, int64_t n, const void* dy, const void* y, void* dx, void* stream);
+
 /* LayerNorm over rows of n (Sec. IV "Normalization"), FP32: y = g (x - mean) rstd + b, ReLU if relu. */
 int squint_op_layernorm_fwd(int rows, int n, const float* x, const float* g, const float* b, float eps, int relu,
                             float* y, float* mean, float* rstd, void* stream);

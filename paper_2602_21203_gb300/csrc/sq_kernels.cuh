@@ -228,6 +228,8 @@ void launch_adam(const AdamArgs& a, cudaStream_t s);
 
 struct PolyakArgs { float* target; const float* src; int64_t n; float tau; int64_t* update_idx; };
 void launch_polyak(const PolyakArgs& a, cudaStream_t s);
+// dx = dy * (y > 0), elementwise over n values.
+template <typename T> void launch_relu_bwd(int64_t n, const T* dy, const T* y, T* dx, cudaStream_t s);
 
 // Inference head: mean or sampled action per row of a ragged batch.
 struct ActHeadArgs {

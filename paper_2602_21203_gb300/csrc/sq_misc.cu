@@ -552,6 +552,14 @@ __global__ void adam_kernel(AdamArgs a) {
     }
 }
 
+// dx = dy where y > 0, else 0 (the ReLU's backward given its output y).
+template <typename T>
+__global__ void relu_bwd_kernel(int64_t n, const T* __restrict__ dy, const T* __restrict__ y, T* __restrict__ dx) {
+    SQ_KERNEL_ENTRY();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dx[i] = y[i] > T(0) ? dy[i] : T(0);
+}
+
 __global__ void polyak_kernel(PolyakArgs a) {
     SQ_KERNEL_ENTRY();
     const float keep = 1.0f - a.tau;
@@ -639,6 +647,15 @@ void launch_adam(const AdamArgs& a, cudaStream_t s) {
     const int blocks = (int)std::min<int64_t>((a.n / 4 + 255) / 256 + 1, 152 * 4);
     if (a.n > 0) launch_k(adam_kernel, dim3(blocks), dim3(256), 0, s, a);
 }
+template <typename T>
+void launch_relu_bwd(int64_t n, const T* dy, const T* y, T* dx, cudaStream_t s) {
+    if (n <= 0) return;
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    launch_k(relu_bwd_kernel<T>, dim3(blocks), dim3(256), 0, s, n, dy, y, dx);
+}
+template void launch_relu_bwd<float>(int64_t, const float*, const float*, float*, cudaStream_t);
+template void launch_relu_bwd<double>(int64_t, const double*, const double*, double*, cudaStream_t);
+
 void launch_polyak(const PolyakArgs& a, cudaStream_t s) {
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, 152 * 8));
     launch_k(polyak_kernel, dim3(blocks), dim3(256), 0, s, a);

@@ -196,6 +196,15 @@ int squint_op_wgrad32(int nimg, int H, int W, const void* x, const void* dy, flo
     return launch_status();
 }
 
+int squint_op_relu_bwd(int dtype, int64_t n, const void* dy, const void* y, void* dx, void* stream) {
+    if (n < 0 || (n > 0 && (!dy || !y || !dx))) return SQUINT_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == SQUINT_DT_F32) launch_relu_bwd<float>(n, (const float*)dy, (const float*)y, (float*)dx, s);
+    else if (dtype == SQUINT_DT_F64) launch_relu_bwd<double>(n, (const double*)dy, (const double*)y, (double*)dx, s);
+    else return SQUINT_EINVAL;
+    return launch_status();
+}
+
 int squint_op_layernorm_fwd(int rows, int n, const float* x, const float* g, const float* b, float eps, int relu,
                             float* y, float* mean, float* rstd, void* stream) {
     if (rows < 0 || n < 1 || !x || !g || !b || !y || !mean || !rstd) return SQUINT_EINVAL;

@@ -98,6 +98,7 @@ def load():
         "squint_phase_name": (ctypes.c_char_p, [I]),
         "squint_profile_kernels": (I, [P, I, P, P, P, P, P, ctypes.POINTER(I), P]),
         "squint_op_gemm": (I, [I, I, I, I, P, I64, I64, P, I64, I64, P, I64, P, I, P]),
+        "squint_op_relu_bwd": (I, [I, I64, P, P, P, P]),
         "squint_op_conv3x3_fwd": (I, [I, I, I, I, I, I, I, P, P, P, P, I, P]),
         "squint_op_conv3x3_workspace": (SZ, [I, I, I, I, I, I, I]),
         "squint_op_conv3x3_bwd": (I, [I, I, I, I, I, I, I, P, P, P, P, P, P, P, P, SZ, P]),

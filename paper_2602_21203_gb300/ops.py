@@ -76,6 +76,15 @@ def conv3x3_bwd(x, w, dy, stride, need_dx=True, dx_mask=None):
     return dx, dw, db
 
 
+def relu_bwd(dy, y, out=None):
+    """dy * (y > 0) for F32/F64 tensors of the same shape (out may be dy itself)."""
+    _need(y, dy.dtype, "y")
+    dy, y = dy.contiguous(), y.contiguous()
+    out = torch.empty_like(dy) if out is None else out
+    _chk(_lib.load().squint_op_relu_bwd(_DT[dy.dtype], dy.numel(), _p(dy), _p(y), _p(out), _s()), "squint_op_relu_bwd")
+    return out
+
+
 def layernorm_fwd(x, g, b, eps=1e-5, relu=False):
     rows, n = x.shape
     y = torch.empty_like(x)
