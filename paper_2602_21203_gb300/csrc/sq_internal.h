@@ -82,6 +82,15 @@ struct squint_handle {
     float* adam_v = nullptr;
     float* target = nullptr;
     float* policy_buf[2] = {nullptr, nullptr};   // inference snapshots (same layout as params)
+    // BF16 inference: per snapshot, padded BF16 copies of the actor-path matrices (actor
+    // projection and actor MLP; weight offset -> element offset in policy_bf, row stride)
+    // and the tensor-core filter layouts of conv layers 1.. (9 x 32 x 32 each)
+    __nv_bfloat16* policy_bf[2] = {nullptr, nullptr};
+    __nv_bfloat16* policy_wconv[2] = {nullptr, nullptr};
+    __nv_bfloat16* policy_wconv_scratch = nullptr;    // unused data-gradient layout output
+    std::map<int64_t, std::pair<int64_t, int64_t>> policy_bf_off;
+    std::vector<sq::CastItem> cast_policy[2];
+    void snapshot_bf16(int i, cudaStream_t s);
     int policy_active = 0;
     int64_t policy_version = 0;
     cudaEvent_t policy_ready[2] = {nullptr, nullptr};     // copy into buffer i finished
@@ -155,6 +164,9 @@ struct squint_handle {
     float* apre = nullptr; float* amean = nullptr; float* arstd = nullptr;
     float* axin = nullptr;
     sq::MlpBufs act_mlp;
+    std::vector<__nv_bfloat16*> aphwc;    // BF16 inference: padded-HWC conv outputs (l < L-1)
+    __nv_bfloat16* az_h = nullptr;        // BF16 inference: encoder features [cap, F]
+    __nv_bfloat16* axin_h = nullptr;      // BF16 inference: actor input [cap, pad8(Da)]
     int32_t* d_row_req = nullptr; int32_t* d_row_in = nullptr;
     void* d_req = nullptr;            // packed per-request arrays
     void* h_req = nullptr;            // pinned staging

@@ -118,7 +118,7 @@ void GemmBuilder::flush() {
     {
         ProfScope ps(h_, s_, kind_, flops_, 0);
         if (!fp_.empty()) launch_gemm<float>(fp_.data(), (int)fp_.size(), lay_, s_);
-        if (!tc_.empty() && launch_tc_gemm(tc_.data(), (int)tc_.size(), h_->d_err, s_) != 0) h_->launch_failed = true;
+        if (!tc_.empty() && launch_tc_gemm(tc_.data(), (int)tc_.size(), h_->d_err, s_, split_) != 0) h_->launch_failed = true;
     }
     fp_.clear();
     tc_.clear();
@@ -151,11 +151,11 @@ MlpRef mlp_ref(squint_handle* h, const std::vector<Lin>& layers, bool target, co
 }
 
 void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const Mat& X, int rows, bool bf16,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool split) {
     const int nh = (int)sets[0].size() - 1;
     for (int l = 0; l <= nh; ++l) {
         {
-            GemmBuilder gb(h, s, bf16);
+            GemmBuilder gb(h, s, bf16, split);
             for (int e = 0; e < E; ++e) {
                 const LayerRef& ly = sets[e][l];
                 Mat in = X;
@@ -452,6 +452,25 @@ int squint_handle::allocate() {
             for (const auto& ly : L.critic[e]) { cast_critic.push_back(item(ly, false)); cast_target.push_back(item(ly, true)); }
         if (L.D > 0) cast_actor.push_back(item(L.aproj, false));
         for (const auto& ly : L.actor) cast_actor.push_back(item(ly, false));
+        // inference snapshots: BF16 actor-path matrices and conv filter layouts per snapshot
+        std::vector<const Lin*> pol;
+        if (L.D > 0) pol.push_back(&L.aproj);
+        for (const auto& ly : L.actor) pol.push_back(&ly);
+        int64_t tot = 0;
+        for (const Lin* ly : pol) {
+            policy_bf_off[ly->w] = {tot, pad8(ly->in)};
+            tot += (int64_t)ly->out * pad8(ly->in);
+        }
+        for (int i = 0; i < 2; ++i) {
+            policy_bf[i] = dalloc<__nv_bfloat16>(tot);
+            for (const Lin* ly : pol) {
+                const auto& o = policy_bf_off[ly->w];
+                cast_policy[i].push_back(CastItem{policy_buf[i] + ly->w, ly->in, ly->out, ly->in, policy_bf[i] + o.first,
+                                                  o.second});
+            }
+            if (tc_conv) policy_wconv[i] = dalloc<__nv_bfloat16>((int64_t)(L.conv.size() - 1) * 9 * 32 * 32);
+        }
+        if (tc_conv) policy_wconv_scratch = dalloc<__nv_bfloat16>(9 * 32 * 32);
         tc_prepare();
     }
     if (cudaMallocHost(&h_stats, sizeof(float) * 8 * c.max_k) != cudaSuccess) return SQUINT_ENOMEM;
@@ -504,10 +523,21 @@ void squint_handle::release() {
     act_allocs.clear();
 }
 
+void squint_handle::snapshot_bf16(int i, cudaStream_t s) {
+    if (!bf16) return;
+    launch_cast_rows(cast_policy[i].data(), (int)cast_policy[i].size(), s);
+    if (tc_conv)
+        for (size_t l = 1; l < L.conv.size(); ++l)
+            launch_conv_weight_cast(policy_buf[i] + L.conv[l].wo, policy_wconv[i] + (l - 1) * 9 * 32 * 32,
+                                    policy_wconv_scratch, s);
+}
+
 int squint_handle::after_param_change() {
     SQ_CK(this, cudaDeviceSynchronize());
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         SQ_CK(this, cudaMemcpy(policy_buf[i], params, L.total * sizeof(float), cudaMemcpyDeviceToDevice));
+        snapshot_bf16(i, 0);
+    }
     if (bf16) {
         launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), 0);
         launch_cast_rows(cast_actor.data(), (int)cast_actor.size(), 0);

@@ -38,7 +38,8 @@ using MlpRef = std::vector<LayerRef>;
 // kernel: CUDA-core FP32 (plain path) or tcgen05 BF16 (tensor-core path).
 class GemmBuilder {
 public:
-    GemmBuilder(squint_handle* h, cudaStream_t s, bool bf16) : h_(h), s_(s), bf_(bf16) {}
+    GemmBuilder(squint_handle* h, cudaStream_t s, bool bf16, bool split = true)
+        : h_(h), s_(s), bf_(bf16), split_(split) {}
     ~GemmBuilder() { flush(); }
     // Y = X W^T + b   (Yh: optional BF16 copy of Y)
     void fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64_t ldy, __nv_bfloat16* Yh = nullptr,
@@ -54,6 +55,7 @@ private:
     squint_handle* h_;
     cudaStream_t s_;
     bool bf_;
+    bool split_;
     std::vector<GemmProblem> fp_;
     GemmLayout lay_ = kKK;
     std::vector<TcGemm> tc_;
@@ -80,11 +82,13 @@ struct ProfScope {
     }
 };
 
-// Forward of E parameter sets of one MLP shape on `rows` rows of X.
+// Forward of E parameter sets of one MLP shape on `rows` rows of X (split = false: no
+// K split in the tensor-core GEMMs, so each row's result is independent of the others).
 void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const Mat& X, int rows, bool bf16,
-                 cudaStream_t s);
+                 cudaStream_t s, bool split = true);
 // Layer view of canonical layer `ly` in the online parameters (base == params), the
-// target copy (target == true) or an inference snapshot (base == a policy buffer, FP32 only).
+// target copy (target == true) or an inference snapshot (base == a policy buffer; its
+// BF16 weight copy, if any, is filled in by the caller).
 LayerRef layer_ref(squint_handle* h, const Lin& ly, bool target, const float* base = nullptr);
 MlpRef mlp_ref(squint_handle* h, const std::vector<Lin>& layers, bool target, const float* base = nullptr);
 GemmProblem lin_fwd(const float* X, int64_t ldx, int rows, const float* W, const float* b, int in, int out, float* Y,

@@ -101,6 +101,7 @@ int squint_handle::refresh_policy(cudaStream_t s) {
     const int i = 1 - policy_active;
     SQ_CK(this, cudaStreamWaitEvent(s, policy_released[i], 0));
     SQ_CK(this, cudaMemcpyAsync(policy_buf[i], params, L.total * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    snapshot_bf16(i, s);
     SQ_CK(this, cudaEventRecord(policy_ready[i], s));
     policy_active = i;
     ++policy_version;
@@ -152,6 +153,23 @@ int squint_handle::ensure_act_capacity(int rows, int n_reqs) {
         act_mlp.rstd[l] = (float*)al(sizeof(float) * cap);
     }
     act_mlp.out = (float*)al(sizeof(float) * (size_t)cap * 2 * c.action_dim);
+    aphwc.clear();
+    act_mlp.posth.clear();
+    az_h = axin_h = nullptr;
+    if (bf16) {
+        // BF16 inference buffers; padded borders and pad columns stay zero
+        if (tc_conv)
+            for (size_t l = 0; l + 1 < L.conv.size(); ++l) {
+                const size_t bytes = 2 * (size_t)cap * (L.conv[l].oh + 4) * (L.conv[l].ow + 4) * 32;
+                aphwc.push_back((__nv_bfloat16*)al(bytes));
+                if (aphwc.back()) SQ_CK(this, cudaMemset(aphwc.back(), 0, bytes));
+            }
+        az_h = (__nv_bfloat16*)al(2 * (size_t)cap * L.feat);
+        const size_t xb = 2 * (size_t)cap * ((L.da + 7) / 8 * 8);
+        axin_h = (__nv_bfloat16*)al(xb);
+        if (axin_h) SQ_CK(this, cudaMemset(axin_h, 0, xb));
+        for (int l = 0; l < nh; ++l) act_mlp.posth.push_back((__nv_bfloat16*)al(2 * (size_t)cap * c.hidden[l]));
+    }
     req_bytes = (size_t)cap * 8 + (size_t)rcap * (8 * 4 + 4) + 64;
     d_req = al(req_bytes);
     for (void* p : act_allocs) if (!p) { g_last_error = "inference allocation failed"; act_cap = 0; return SQUINT_ENOMEM; }
@@ -214,17 +232,57 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
     af.rows = rows; af.C = c.obs_c; af.H = c.obs_h; af.W = c.obs_w; af.f = c.squint_f; af.P = c.proprio_dim;
     af.x = ax; af.xin = axin; af.ld_xin = Da; af.col = L.zdim;
     launch_act_frontend(af, s);
+    // BF16 policy: layer-0 conv on CUDA cores, the 32-channel convs and every linear
+    // layer on tcgen05 with the snapshot's BF16 copies, no K split (each row's result
+    // is independent of the other rows of the batch)
+    const bool tc = bf16 && tc_conv;
     const float* in = ax;
     for (size_t l = 0; l < L.conv.size(); ++l) {
         const ConvL& cv = L.conv[l];
+        if (tc && l > 0) {
+            ConvTc ct{};
+            ct.in = aphwc[l - 1];
+            ct.nimg = rows;
+            ct.Wp = cv.w + 4;
+            ct.in_rows = (cv.h + 4) * ct.Wp;
+            ct.out_h = cv.oh; ct.out_w = cv.ow;
+            ct.off0 = 2 * ct.Wp + 2;
+            ct.w = policy_wconv[pi] + (l - 1) * 9 * 32 * 32;
+            ct.bias = Wp + cv.bo;
+            ct.relu = 1;
+            if (l + 1 < L.conv.size()) ct.out_phwc = aphwc[l];
+            else { ct.out_chw = aconv[l]; ct.out_chw_bf = az_h; }
+            if (launch_conv32_tc(ct, d_err, s) != 0) { g_last_error = "tensor-core conv launch"; return SQUINT_ECUDA; }
+            in = aconv[l];
+            continue;
+        }
         ConvShape sh{rows, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
                      (int64_t)cv.cout * cv.oh * cv.ow};
         launch_conv_fwd<float>(sh, in, Wp + cv.wo, Wp + cv.bo, aconv[l], true, s);
         in = aconv[l];
+        if (tc && l == 0) launch_to_phwc(aconv[0], (int64_t)cv.cout * cv.oh * cv.ow, rows, cv.oh, cv.ow, aphwc[0], s);
     }
+    if (bf16 && !tc) {
+        CastItem ci{in, F, rows, F, az_h, F};
+        launch_cast_rows(&ci, 1, s);
+    }
+    auto bf_ref = [&](const Lin& ly) {
+        LayerRef r = layer_ref(this, ly, false, Wp);
+        if (bf16) {
+            const auto& o = policy_bf_off.at(ly.w);
+            r.wh = policy_bf[pi] + o.first;
+            r.ldh = o.second;
+        }
+        return r;
+    };
     if (Dd > 0) {
-        GemmProblem g = lin_fwd(in, F, rows, Wp + L.aproj.w, Wp + L.aproj.b, F, Dd, apre, Dd);
-        launch_gemm<float>(&g, 1, kKK, s);
+        if (bf16) {
+            GemmBuilder gb(this, s, true, false);
+            gb.fwd(Mat{const_cast<float*>(in), F, az_h, F}, rows, bf_ref(L.aproj), apre, Dd);
+        } else {
+            GemmProblem g = lin_fwd(in, F, rows, Wp + L.aproj.w, Wp + L.aproj.b, F, Dd, apre, Dd);
+            launch_gemm<float>(&g, 1, kKK, s);
+        }
         LnProblem p{};
         p.rows = rows; p.n = Dd; p.pre = apre; p.ld_pre = Dd;
         p.g = Wp + L.aproj.g; p.beta = Wp + L.aproj.beta;
@@ -234,8 +292,14 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
         SQ_CK(this, cudaMemcpy2DAsync(axin, Da * sizeof(float), in, F * sizeof(float), F * sizeof(float), rows,
                                       cudaMemcpyDeviceToDevice, s));
     }
-    const MlpRef actor_ref = mlp_ref(this, L.actor, false, Wp);
-    mlp_forward(this, act_mlp, &actor_ref, 1, Mat{axin, Da, nullptr, 0}, rows, false, s);
+    const int64_t Da8 = (Da + 7) / 8 * 8;
+    if (bf16) {
+        CastItem ci{axin, Da, rows, Da, axin_h, Da8};   // projected features and proprio, BF16
+        launch_cast_rows(&ci, 1, s);
+    }
+    MlpRef actor_ref;
+    for (const auto& ly : L.actor) actor_ref.push_back(bf_ref(ly));
+    mlp_forward(this, act_mlp, &actor_ref, 1, Mat{axin, Da, axin_h, Da8}, rows, bf16, s, false);
     ActHeadArgs ha{};
     ha.rows = rows; ha.A = A; ha.out = act_mlp.out; ha.ld_out = 2 * A;
     ha.row_req = d_row_req; ha.row_in_req = d_row_in;

@@ -512,7 +512,7 @@ void tc_prepare() {
     }
 }
 
-int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s) {
+int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, bool allow_split) {
     for (int base = 0; base < n_probs; base += kMaxProbs) {
         TcBatch gb;
         std::memset(&gb, 0, sizeof(gb));
@@ -538,7 +538,7 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s) {
         }
         if (!tiles) continue;
         int S = std::min(std::min(g_max_splits, std::max(1, kSplitTarget / tiles)), min_iters / kMinSplitIters);
-        S = std::max(S, 1);
+        S = allow_split ? std::max(S, 1) : 1;
         gb.splits = S;
         for (int i = 0; i < gb.n; ++i) gb.p[i].tile_start *= S;
         const dim3 grid(tiles * S), cluster(S);

@@ -32,7 +32,10 @@ struct TcGemm {
 // distributed shared memory in rank order, so the result is the same on every run.
 // Returns 0, or < 0 if a tensor map cannot describe an operand (alignment, extents).
 // *err (device int) receives a nonzero code if a bounded wait gave up.
-int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s);
+// allow_split = false keeps every output row's arithmetic independent of the other
+// rows of the launch (no K split), e.g. for inference whose result must not depend
+// on which requests share the batch.
+int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, bool allow_split = true);
 // Opt the kernels in to their shared memory and resolve the tensor-map encoder (call outside capture).
 void tc_prepare();
 

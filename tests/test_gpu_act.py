@@ -146,3 +146,55 @@ def test_serving_beside_updates_sees_consistent_snapshots(L):
     assert torch.isfinite(out).all() and (out.abs() < 1).all()
     learner.serve_stop()
     learner.close()
+
+
+# ---------------------------------------------------------------- BF16 policy
+# BF16 operands (8-bit mantissa, relative rounding 2^-9) with FP32 accumulation through
+# the encoder, the projection and three actor layers leave about 1e-2 relative error
+# in the pre-tanh outputs; with |d tanh| <= 1 the actions stay within 5e-2 of the FP64
+# oracle, 1e-2 on average.
+BF16_ACT_MAX, BF16_ACT_MEAN = 5e-2, 1e-2
+
+
+@pytest.mark.parametrize("name,n", [("small_b32", 37), ("train_b512", 24)])
+@pytest.mark.parametrize("sample", [True, False])
+def test_bf16_act_matches_oracle(L, name, n, sample):
+    cfg = synth.make_config(name)
+    learner = L.Learner(cfg, None, precision=L.PREC_BF16)
+    P = o.init_params(cfg)
+    obs, prop, out = _batch(cfg, n, 6)
+    learner.act([L.Learner.request(obs, prop, out, key=4321, sample=sample)])
+    torch.cuda.synchronize()
+    ref = o.act(P, obs.cpu().numpy(), prop.cpu().numpy(), 4321, sample, cfg)
+    err = np.abs(out.cpu().numpy() - ref)
+    assert err.max() < BF16_ACT_MAX and err.mean() < BF16_ACT_MEAN, (err.max(), err.mean())
+    learner.close()
+
+
+def test_bf16_serving_results_equal_alone(L):
+    """Training shapes (tensor-core convs and GEMMs): each group's actions are bit-identical
+    whether it runs alone or batched with other groups by the serving loop."""
+    cfg = synth.make_config("train_b512")
+    learner = L.Learner(cfg, None, precision=L.PREC_BF16)
+    rng = np.random.default_rng(1)
+    sizes = [int(s) for s in rng.integers(1, 200, size=12)]
+    groups = [_batch(cfg, n, 80 + i) for i, n in enumerate(sizes)]
+    alone = []
+    for i, (obs, prop, out) in enumerate(groups):
+        learner.act([L.Learner.request(obs, prop, out, key=11 + i)])
+        torch.cuda.synchronize()
+        alone.append(out.clone())
+        out.fill_(float("nan"))
+    learner.serve_start(max_rows=1024, mem_budget_bytes=4 << 30)
+    tickets = [learner.serve_submit(L.Learner.request(obs, prop, out, key=11 + i, group_id=i))
+               for i, (obs, prop, out) in enumerate(groups)]
+    for t in tickets:
+        r = None
+        deadline = time.time() + 30
+        while r is None and time.time() < deadline:
+            r = learner.serve_poll(t, timeout_us=100_000)
+        assert r is not None
+    for (obs, prop, out), a in zip(groups, alone):
+        assert torch.equal(out, a)
+    learner.serve_stop()
+    learner.close()

@@ -123,7 +123,7 @@ def test_categorical_ce_fp32_vs_oracle_and_fd(ag):
     gl, = torch.autograd.grad(loss, logits)
     lsm = o.log_softmax(logits.detach().double().cpu().numpy())
     mn = m.double().cpu().numpy()
-    assert abs(float(loss) - float(-(mn * lsm).sum(1).mean())) < 1e-5
+    assert abs(float(loss.detach()) - float(-(mn * lsm).sum(1).mean())) < 1e-5
     assert _rel(gl.cpu(), (np.exp(lsm) - mn) / 12) < 1e-4
     _check_fd(_fd_dir(f, (logits,), 0, g))
 
