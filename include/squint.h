@@ -73,6 +73,11 @@ typedef struct {
     int32_t policy_freq;             /* actor step when (update_idx + 1) % policy_freq == 0 */
     int32_t precision;               /* SQUINT_PREC_* */
     int32_t max_k;                   /* largest k accepted by squint_update */
+    int32_t recompute_chunk;         /* 0: keep encoder activations; n > 0: BF16 tensor-core
+                                        encoder only: run it in chunks of n images (rounded up
+                                        to the weight gradient's images per CTA), keep only the
+                                        features, recompute activations in the backward;
+                                        results are bit-identical to n = 0 */
     double v_min, v_max, gamma, lr, tau, init_alpha;
     double target_entropy;           /* NaN: -action_dim */
     double ln_eps, log_std_min, log_std_max, adam_b1, adam_b2, adam_eps;
@@ -152,6 +157,10 @@ int squint_update_eager(squint_handle* h, int k, squint_update_stats* stats, voi
 
 /* Kernel nodes in the graph captured for k updates (0 if none captured yet). */
 int64_t squint_graph_kernel_count(squint_handle* h, int k);
+
+/* Device bytes the learner allocated at creation (parameters, optimiser state,
+ * activations, workspaces; not the caller's ring, not inference buffers).  0 for NULL. */
+int64_t squint_device_bytes(squint_handle* h);
 
 /*
  * One update issued eagerly on `stream` with a CUDA event at every phase

@@ -287,6 +287,8 @@ int squint_debug_tensor(squint_handle* h, const char* name, void* host, size_t* 
     return h->debug_tensor(name, host, bytes);
 }
 
+int64_t squint_device_bytes(squint_handle* h) { return h ? h->device_bytes : 0; }
+
 int64_t squint_graph_kernel_count(squint_handle* h, int k) {
     if (!h) return 0;
     auto it = h->graph_kernels.find(k);

@@ -497,8 +497,14 @@ int launch_conv32_tc(const ConvTc& c, int* err, cudaStream_t s) {
 
 int64_t wgrad32_tc_workspace(int nimg) { return (int64_t)std::min(nimg, 148) * kCh * (kCh * 9 + 1); }
 
-int launch_wgrad32_tc(const WgradTc& c, float* work, float* dw, float* db, int* err, cudaStream_t s) {
+int wgrad32_per_cta(int nimg) {
+    const int ctas = std::max(1, std::min(nimg, 148));
+    return (nimg + ctas - 1) / ctas;
+}
+
+int launch_wgrad32_tc_partials(const WgradTc& c, int per_cta, float* work, int* err, cudaStream_t s) {
     if (c.nimg <= 0) return 0;
+    if (per_cta < 1) return -1;
     WgradArgs a;
     std::memset(&a, 0, sizeof(a));
     a.kq = round_up(c.out_h * c.Wp, 16);
@@ -506,13 +512,24 @@ int launch_wgrad32_tc(const WgradTc& c, float* work, float* dw, float* db, int* 
     a.load_rows = round_up(std::max(max_row + 1, c.in_rows), 128);
     if (wgrad_smem(a.load_rows, a.kq) > 220 * 1024 || (a.kq / 8) * 512 + 2048 > kDyBytesMax + 2048) return -1;
     if (!plane_map(&a.tin, c.x, (int64_t)c.nimg * c.in_rows)) return -2;
-    const int ctas = std::min(c.nimg, 148);
-    a.per_cta = (c.nimg + ctas - 1) / ctas;
-    const int grid = (c.nimg + a.per_cta - 1) / a.per_cta;
+    a.per_cta = per_cta;
+    const int grid = (c.nimg + per_cta - 1) / per_cta;
     a.dy = c.dy; a.nimg = c.nimg; a.in_rows = c.in_rows; a.Wp = c.Wp; a.out_h = c.out_h; a.out_w = c.out_w;
     a.work = work; a.err = err;
     launch_k(wgrad32_tc_kernel, dim3(grid), dim3(128), wgrad_smem(a.load_rows, a.kq), s, a);
-    launch_k(wgrad32_reduce_kernel, dim3((kCh * (kCh * 9 + 1) + 255) / 256), dim3(256), 0, s, work, grid, dw, db);
+    return 0;
+}
+
+void launch_wgrad32_reduce(const float* work, int ctas, float* dw, float* db, cudaStream_t s) {
+    launch_k(wgrad32_reduce_kernel, dim3((kCh * (kCh * 9 + 1) + 255) / 256), dim3(256), 0, s, work, ctas, dw, db);
+}
+
+int launch_wgrad32_tc(const WgradTc& c, float* work, float* dw, float* db, int* err, cudaStream_t s) {
+    if (c.nimg <= 0) return 0;
+    const int pc = wgrad32_per_cta(c.nimg);
+    const int rc = launch_wgrad32_tc_partials(c, pc, work, err, s);
+    if (rc != 0) return rc;
+    launch_wgrad32_reduce(work, (c.nimg + pc - 1) / pc, dw, db, s);
     return 0;
 }
 

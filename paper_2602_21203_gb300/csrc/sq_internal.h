@@ -215,6 +215,8 @@ struct squint_handle {
     int profile_update(float* ms, int cap, int* n_phases, cudaStream_t s);
 
     std::vector<void*> allocations;
+    int64_t device_bytes = 0;             // sum of the dalloc sizes
+    int rc_chunk = 0;                     // encoder recompute chunk (images), 0 = off
     sq::ServeState* serve = nullptr;
     std::mutex act_mu;
 
@@ -242,6 +244,7 @@ struct squint_handle {
             p = nullptr;
         }
         allocations.push_back(p);
+        if (p) device_bytes += (int64_t)((size_t)n * sizeof(T));
         return static_cast<T*>(p);
     }
 };

@@ -29,6 +29,7 @@ using namespace sq;
 namespace sq {
 
 static int64_t pad8(int64_t n) { return (n + 7) / 8 * 8; }
+constexpr int kCh32 = 32;   // channels of the tensor-core convolutions
 
 GemmProblem lin_fwd(const float* X, int64_t ldx, int rows, const float* W, const float* b, int in, int out, float* Y,
                     int64_t ldy) {
@@ -325,7 +326,32 @@ int squint_handle::allocate() {
     sums = dalloc<uint16_t>(2 * B * img);
     idx2 = dalloc<int32_t>(2 * B);
     shift2 = dalloc<int32_t>(4 * B);
-    for (const auto& cv : L.conv) conv_out.push_back(dalloc<float>((int64_t)2 * B * cv.cout * cv.oh * cv.ow));
+    // tensor-core convolutions for the 32 -> 32 stride-1 layers of a BF16 learner
+    if (bf16) {
+        tc_conv = L.conv.size() >= 2 && L.conv[0].cout == 32;
+        for (size_t l = 1; l < L.conv.size(); ++l) {
+            const ConvL& cv = L.conv[l];
+            if (cv.cin != 32 || cv.cout != 32 || cv.s != 1) tc_conv = false;
+        }
+    }
+    // encoder recompute: chunk size rounded up to the weight gradient's images per CTA, so
+    // the chunked weight gradient has the same partition (and bits) as the whole-batch one
+    if (c.recompute_chunk < 0 || (c.recompute_chunk > 0 && !tc_conv)) {
+        g_last_error = "recompute_chunk needs a BF16 learner with 32-channel stride-1 inner convolutions";
+        return SQUINT_EINVAL;
+    }
+    if (c.recompute_chunk > 0) {
+        const int pc = wgrad32_per_cta(B);
+        rc_chunk = std::min((c.recompute_chunk + pc - 1) / pc * pc, 2 * B);
+    }
+    const int enc_imgs = rc_chunk ? rc_chunk : 2 * B;   // images held by the encoder's buffers
+    for (size_t l = 0; l < L.conv.size(); ++l) {
+        const ConvL& cv = L.conv[l];
+        const int64_t per = (int64_t)cv.cout * cv.oh * cv.ow;
+        if (l + 1 == L.conv.size()) conv_out.push_back(dalloc<float>(2 * B * per));     // features z
+        else if (l == 0) conv_out.push_back(dalloc<float>(tc_conv ? enc_imgs * per : 2 * B * per));
+        else conv_out.push_back(tc_conv ? nullptr : dalloc<float>(2 * B * per));
+    }
     if (L.D > 0) {
         proj_pre = dalloc<float>((int64_t)5 * B * L.D);
         proj_mean = dalloc<float>(5 * B);
@@ -367,7 +393,7 @@ int squint_handle::allocate() {
         maxw = std::max(maxw, conv_wgrad_workspace(sh));
     }
     dconv_a = dalloc<float>(maxc);
-    dconv_b = dalloc<float>(maxc);
+    if (!tc_conv) dconv_b = dalloc<float>(maxc);
     wgrad_work = dalloc<float>(maxw);
     dxq = dalloc<float>((int64_t)B * L.dc);
     {
@@ -400,31 +426,26 @@ int squint_handle::allocate() {
         if (L.D > 0) dproj_h = dalloc<__nv_bfloat16>((int64_t)B * L.D);
         dout_ah = dalloc<__nv_bfloat16>((int64_t)B * pad8(2 * A));
     }
-    if (bf16) {
-        tc_conv = L.conv.size() >= 2;
-        for (size_t l = 1; l < L.conv.size(); ++l) {
-            const ConvL& cv = L.conv[l];
-            if (cv.cin != 32 || cv.cout != 32 || cv.s != 1) tc_conv = false;
-        }
-        if (L.conv[0].cout != 32) tc_conv = false;
-    }
+    // padded-HWC BF16 activations (forward: enc_imgs images; backward: one chunk of o_t)
+    const int bwd_imgs = rc_chunk ? rc_chunk : B;
     if (tc_conv) {
         const int nl = (int)L.conv.size();
         for (int l = 0; l < nl - 1; ++l) {
             const ConvL& cv = L.conv[l];
             const int64_t img = (int64_t)(cv.oh + 4) * (cv.ow + 4) * 32;
-            act_p.push_back(dalloc<__nv_bfloat16>(2 * B * img));
-            dact_p.push_back(dalloc<__nv_bfloat16>(B * img));
+            act_p.push_back(dalloc<__nv_bfloat16>(enc_imgs * img));
+            dact_p.push_back(dalloc<__nv_bfloat16>(bwd_imgs * img));
         }
         const ConvL& last = L.conv.back();
-        dz_p = dalloc<__nv_bfloat16>((int64_t)B * (last.oh + 4) * (last.ow + 4) * 32);
+        dz_p = dalloc<__nv_bfloat16>((int64_t)bwd_imgs * (last.oh + 4) * (last.ow + 4) * 32);
         wconv_fwd.assign(nl, nullptr);
         wconv_bwd.assign(nl, nullptr);
         for (int l = 1; l < nl; ++l) {
             wconv_fwd[l] = dalloc<__nv_bfloat16>(9 * 32 * 32);
             wconv_bwd[l] = dalloc<__nv_bfloat16>(9 * 32 * 32);
         }
-        wgrad_tc_work = dalloc<float>(wgrad32_tc_workspace(B));
+        // with recompute every inner layer keeps its partials until all chunks are done
+        wgrad_tc_work = dalloc<float>((rc_chunk ? nl - 1 : 1) * wgrad32_tc_workspace(B));
     }
     for (void* p : allocations)
         if (!p) { g_last_error = "device allocation failed"; return SQUINT_ENOMEM; }
@@ -433,11 +454,11 @@ int squint_handle::allocate() {
         for (size_t l = 0; l < act_p.size(); ++l) {
             const ConvL& cv = L.conv[l];
             const int64_t img = (int64_t)(cv.oh + 4) * (cv.ow + 4) * 32;
-            SQ_CK(this, cudaMemset(act_p[l], 0, 2 * B * img * 2));
-            SQ_CK(this, cudaMemset(dact_p[l], 0, B * img * 2));
+            SQ_CK(this, cudaMemset(act_p[l], 0, (size_t)enc_imgs * img * 2));
+            SQ_CK(this, cudaMemset(dact_p[l], 0, (size_t)bwd_imgs * img * 2));
         }
         const ConvL& last = L.conv.back();
-        SQ_CK(this, cudaMemset(dz_p, 0, (size_t)B * (last.oh + 4) * (last.ow + 4) * 32 * 2));
+        SQ_CK(this, cudaMemset(dz_p, 0, (size_t)bwd_imgs * (last.oh + 4) * (last.ow + 4) * 32 * 2));
         conv_tc_prepare();
     }
     if (bf16) {
@@ -616,14 +637,26 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
 
     mark(s);
     // ---- a5: encoder on o_t (rows < B) and o_{t+1} (rows >= B)
-    const float* in = x2;
     const int nconv = (int)L.conv.size();
-    for (int l = 0; l < nconv; ++l) {
-        const ConvL& cv = L.conv[l];
-        if (tc_conv && l > 0) {
+    // tensor-core encoder over images [i0, i0 + n) of x2; layers 0 .. upto, where layer
+    // nconv - 1 writes the features of those rows (FP32 and BF16)
+    auto enc_tc = [&](int i0, int n, int upto, cudaStream_t st) {
+        const ConvL& c0 = L.conv[0];
+        const int64_t img0 = (int64_t)c.obs_c * c0.h * c0.w;
+        ConvShape sh{n, c0.cin, c0.h, c0.w, c0.cout, c0.s, c0.oh, c0.ow, img0, (int64_t)c0.cout * c0.oh * c0.ow};
+        {
+            ProfScope ps(this, st, "conv_f32_fwd", conv_flops(c0, n), 0);
+            launch_conv_fwd<float>(sh, x2 + (int64_t)i0 * img0, W + c0.wo, W + c0.bo, conv_out[0], true, st);
+        }
+        {
+            ProfScope ps(this, st, "layout_phwc", (4.0 + 2.0) * n * c0.cout * c0.oh * c0.ow, 1);
+            launch_to_phwc(conv_out[0], (int64_t)c0.cout * c0.oh * c0.ow, n, c0.oh, c0.ow, act_p[0], st);
+        }
+        for (int l = 1; l <= upto; ++l) {
+            const ConvL& cv = L.conv[l];
             ConvTc ct{};
             ct.in = act_p[l - 1];
-            ct.nimg = 2 * B;
+            ct.nimg = n;
             ct.Wp = cv.w + 4;
             ct.in_rows = (cv.h + 4) * ct.Wp;
             ct.out_h = cv.oh; ct.out_w = cv.ow;
@@ -632,21 +665,23 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             ct.bias = W + cv.bo;
             ct.relu = 1;
             if (l < nconv - 1) ct.out_phwc = act_p[l];
-            else { ct.out_chw = conv_out[l]; ct.out_chw_bf = z_h; }
-            ProfScope ps(this, s, "conv_tc_fwd", conv_flops(cv, 2 * B), 0);
-            if (launch_conv32_tc(ct, d_err, s) != 0) launch_failed = true;
-            continue;
+            else { ct.out_chw = conv_out[l] + (int64_t)i0 * F; ct.out_chw_bf = z_h + (int64_t)i0 * F; }
+            ProfScope ps(this, st, "conv_tc_fwd", conv_flops(cv, n), 0);
+            if (launch_conv32_tc(ct, d_err, st) != 0) launch_failed = true;
         }
-        ConvShape sh{2 * B, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
-                     (int64_t)cv.cout * cv.oh * cv.ow};
-        {
+    };
+    if (tc_conv) {
+        const int chunk = rc_chunk ? rc_chunk : 2 * B;
+        for (int i0 = 0; i0 < 2 * B; i0 += chunk) enc_tc(i0, std::min(chunk, 2 * B - i0), nconv - 1, s);
+    } else {
+        const float* in = x2;
+        for (int l = 0; l < nconv; ++l) {
+            const ConvL& cv = L.conv[l];
+            ConvShape sh{2 * B, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
+                         (int64_t)cv.cout * cv.oh * cv.ow};
             ProfScope ps(this, s, "conv_f32_fwd", conv_flops(cv, 2 * B), 0);
             launch_conv_fwd<float>(sh, in, W + cv.wo, W + cv.bo, conv_out[l], true, s);
-        }
-        in = conv_out[l];
-        if (tc_conv && l == 0) {
-            ProfScope ps(this, s, "layout_phwc", (4.0 + 2.0) * 2 * B * cv.cout * cv.oh * cv.ow, 1);
-            launch_to_phwc(conv_out[0], (int64_t)cv.cout * cv.oh * cv.ow, 2 * B, cv.oh, cv.ow, act_p[0], s);
+            in = conv_out[l];
         }
     }
     float* z = conv_out.back();                // [2B, F]
@@ -797,46 +832,70 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     {
         const float* cur = dz;
         if (tc_conv) {
+            // o_t images in chunks (one chunk = the whole batch without recompute); with
+            // recompute, each chunk's activations are recomputed first, and the inner
+            // layers' weight-gradient partials stay at their whole-batch CTA slots until
+            // one reduce per layer after the last chunk
             const ConvL& last = L.conv.back();
-            {
-                ProfScope ps(this, s1, "layout_phwc", 6.0 * B * F, 1);
-                launch_to_phwc(dz, F, B, last.oh, last.ow, dz_p, s1);
-            }
-            const __nv_bfloat16* cur_p = dz_p;
-            for (int l = nconv - 1; l >= 1; --l) {
-                const ConvL& cv = L.conv[l];
-                WgradTc wt{};
-                wt.x = act_p[l - 1];
-                wt.dy = cur_p;
-                wt.nimg = B;
-                wt.Wp = cv.w + 4;
-                wt.in_rows = (cv.h + 4) * wt.Wp;
-                wt.out_h = cv.oh; wt.out_w = cv.ow;
-                {
-                    ProfScope ps(this, s1, "conv_tc_wgrad", conv_flops(cv, B), 0);
-                    if (launch_wgrad32_tc(wt, wgrad_tc_work, G + cv.wo, G + cv.bo, d_err, s1) != 0) launch_failed = true;
-                }
-                ConvTc ct{};
-                ct.in = cur_p;
-                ct.nimg = B;
-                ct.Wp = cv.ow + 4;
-                ct.in_rows = (cv.oh + 4) * ct.Wp;
-                ct.out_h = cv.h; ct.out_w = cv.w;
-                ct.off0 = 0;
-                ct.w = wconv_bwd[l];
-                ct.mask = act_p[l - 1];
-                ct.out_phwc = dact_p[l - 1];
-                {
-                    ProfScope ps(this, s1, "conv_tc_dgrad", conv_flops(cv, B), 0);
-                    if (launch_conv32_tc(ct, d_err, s1) != 0) launch_failed = true;
-                }
-                cur_p = dact_p[l - 1];
-            }
             const ConvL& c0 = L.conv[0];
-            {
-                ProfScope ps(this, s1, "layout_phwc", 6.0 * B * c0.cout * c0.oh * c0.ow, 1);
-                launch_from_phwc(dact_p[0], B, c0.oh, c0.ow, dconv_a, s1);
+            const int pc = wgrad32_per_cta(B);
+            const int64_t wslot = (int64_t)kCh32 * (kCh32 * 9 + 1);
+            const int chunk = rc_chunk ? rc_chunk : B;
+            for (int i0 = 0; i0 < B; i0 += chunk) {
+                const int n = std::min(chunk, B - i0);
+                if (rc_chunk) enc_tc(i0, n, nconv - 2, s1);
+                {
+                    ProfScope ps(this, s1, "layout_phwc", 6.0 * n * F, 1);
+                    launch_to_phwc(dz + (int64_t)i0 * F, F, n, last.oh, last.ow, dz_p, s1);
+                }
+                const __nv_bfloat16* cur_p = dz_p;
+                for (int l = nconv - 1; l >= 1; --l) {
+                    const ConvL& cv = L.conv[l];
+                    WgradTc wt{};
+                    wt.x = act_p[l - 1];
+                    wt.dy = cur_p;
+                    wt.nimg = n;
+                    wt.Wp = cv.w + 4;
+                    wt.in_rows = (cv.h + 4) * wt.Wp;
+                    wt.out_h = cv.oh; wt.out_w = cv.ow;
+                    {
+                        ProfScope ps(this, s1, "conv_tc_wgrad", conv_flops(cv, n), 0);
+                        int rc;
+                        if (rc_chunk) {
+                            float* work = wgrad_tc_work + (int64_t)(l - 1) * wgrad32_tc_workspace(B) +
+                                          (int64_t)(i0 / pc) * wslot;
+                            rc = launch_wgrad32_tc_partials(wt, pc, work, d_err, s1);
+                        } else {
+                            rc = launch_wgrad32_tc(wt, wgrad_tc_work, G + cv.wo, G + cv.bo, d_err, s1);
+                        }
+                        if (rc != 0) launch_failed = true;
+                    }
+                    ConvTc ct{};
+                    ct.in = cur_p;
+                    ct.nimg = n;
+                    ct.Wp = cv.ow + 4;
+                    ct.in_rows = (cv.oh + 4) * ct.Wp;
+                    ct.out_h = cv.h; ct.out_w = cv.w;
+                    ct.off0 = 0;
+                    ct.w = wconv_bwd[l];
+                    ct.mask = act_p[l - 1];
+                    ct.out_phwc = dact_p[l - 1];
+                    {
+                        ProfScope ps(this, s1, "conv_tc_dgrad", conv_flops(cv, n), 0);
+                        if (launch_conv32_tc(ct, d_err, s1) != 0) launch_failed = true;
+                    }
+                    cur_p = dact_p[l - 1];
+                }
+                ProfScope ps(this, s1, "layout_phwc", 6.0 * n * c0.cout * c0.oh * c0.ow, 1);
+                launch_from_phwc(dact_p[0], n, c0.oh, c0.ow, dconv_a + (int64_t)i0 * c0.cout * c0.oh * c0.ow, s1);
             }
+            if (rc_chunk)
+                for (int l = nconv - 1; l >= 1; --l) {
+                    const ConvL& cv = L.conv[l];
+                    ProfScope ps(this, s1, "conv_tc_wgrad", 0.0, 0);
+                    launch_wgrad32_reduce(wgrad_tc_work + (int64_t)(l - 1) * wgrad32_tc_workspace(B),
+                                          (B + pc - 1) / pc, G + cv.wo, G + cv.bo, s1);
+                }
             ConvShape sh{B, c0.cin, c0.h, c0.w, c0.cout, c0.s, c0.oh, c0.ow, (int64_t)c0.cin * c0.h * c0.w,
                          (int64_t)c0.cout * c0.oh * c0.ow};
             ProfScope ps(this, s1, "conv_f32_wgrad", conv_flops(c0, B), 0);

@@ -66,6 +66,14 @@ struct WgradTc {
 };
 int64_t wgrad32_tc_workspace(int nimg);
 int launch_wgrad32_tc(const WgradTc& c, float* work, float* dw, float* db, int* err, cudaStream_t s);
+// The same in two parts: CTA i adds images [i per_cta, (i + 1) per_cta) into partial
+// tile work[i] (kCh x (9 kCh + 1) floats); the reduce adds work[0 .. ctas) in order.
+// wgrad32_per_cta(n) is the split launch_wgrad32_tc uses for n images, so a batch
+// processed in chunks of a multiple of it, each chunk's partials written at its first
+// image / per_cta, reduces to the same bits as one launch over the whole batch.
+int wgrad32_per_cta(int nimg);
+int launch_wgrad32_tc_partials(const WgradTc& c, int per_cta, float* work, int* err, cudaStream_t s);
+void launch_wgrad32_reduce(const float* work, int ctas, float* dw, float* db, cudaStream_t s);
 void conv_tc_prepare();
 void launch_to_phwc(const float* src, int64_t img_stride, int nimg, int H, int W, __nv_bfloat16* dst, cudaStream_t s);
 void launch_from_phwc(const __nv_bfloat16* src, int nimg, int H, int W, float* dst, cudaStream_t s);

@@ -35,6 +35,7 @@ class Config(ctypes.Structure):
         ("hidden", ctypes.c_int32 * MAX_HIDDEN),
         ("n_critics", ctypes.c_int32), ("atoms", ctypes.c_int32), ("batch", ctypes.c_int32),
         ("policy_freq", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_k", ctypes.c_int32),
+        ("recompute_chunk", ctypes.c_int32),
         ("v_min", ctypes.c_double), ("v_max", ctypes.c_double), ("gamma", ctypes.c_double),
         ("lr", ctypes.c_double), ("tau", ctypes.c_double), ("init_alpha", ctypes.c_double),
         ("target_entropy", ctypes.c_double), ("ln_eps", ctypes.c_double),
@@ -94,6 +95,7 @@ def load():
         "squint_debug_tensor": (I, [P, ctypes.c_char_p, P, ctypes.POINTER(SZ)]),
         "squint_struct_size": (SZ, [ctypes.c_char_p]),
         "squint_graph_kernel_count": (I64, [P, I]),
+        "squint_device_bytes": (I64, [P]),
         "squint_profile_update": (I, [P, P, I, ctypes.POINTER(I), P]),
         "squint_phase_name": (ctypes.c_char_p, [I]),
         "squint_profile_kernels": (I, [P, I, P, P, P, P, P, ctypes.POINTER(I), P]),
@@ -178,6 +180,7 @@ def make_config(cfg, precision=PREC_FP32, max_k=None):
         c.hidden[i] = int(h)
     c.precision = int(precision)
     c.max_k = int(max_k if max_k is not None else max(8, cfg.get("utd", 1)))
+    c.recompute_chunk = int(cfg.get("recompute_chunk", 0))
     for k in ("v_min", "v_max", "gamma", "lr", "tau", "init_alpha", "ln_eps", "log_std_min", "log_std_max",
               "adam_b1", "adam_b2", "adam_eps"):
         setattr(c, k, float(cfg[k]))
@@ -257,6 +260,10 @@ class Learner:
 
     def graph_kernel_count(self, k):
         return int(self.lib.squint_graph_kernel_count(self.h, int(k)))
+
+    def device_bytes(self):
+        """Device memory the learner allocated at creation (ring and inference buffers excluded)."""
+        return int(self.lib.squint_device_bytes(self.h))
 
     def profile_update(self, stream=None):
         """One eager update timed per phase: {phase name: device ms}."""
