@@ -47,6 +47,8 @@ extern "C" {
  * in every mode. */
 #define SQUINT_PREC_FP32 0   /* plain FP32 CUDA-core kernels */
 #define SQUINT_PREC_BF16 1   /* BF16 operands, FP32 accumulation (tensor cores) */
+#define SQUINT_PREC_FP8 2    /* as BF16, with the forward linear layers in e4m3 (per-tensor
+                                scales, FP32 accumulation); backward and convs stay BF16 */
 
 /*
  * Learner configuration (plain data, copied at creation).

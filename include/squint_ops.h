@@ -39,6 +39,19 @@ int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, 
 
 
 /*
+ * FP8 (e4m3) GEMM with per-tensor scaling, FP32 accumulation (the reduced-precision
+ * form tried for the forward linear layers): A [M, K] and B [N, K] are BF16, row
+ * stride lda / ldb >= K; each is quantised as a whole, scale = max|x| / 448 and
+ * x_q = e4m3(x / scale) rounded to nearest; then C[m, n] = scale_A scale_B
+ * sum_k A_q(m, k) B_q(n, k) + bias[n] on tcgen05 (kind::f8f6f4).  `work`: caller-owned
+ * device memory, 16-byte aligned, squint_op_gemm_fp8_workspace(M, N, K) bytes; it
+ * holds the quantised operands and their scales (two floats at byte offset 2048).
+ */
+size_t squint_op_gemm_fp8_workspace(int M, int N, int K);
+int squint_op_gemm_fp8(int M, int N, int K, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
+                       int64_t ldc, const float* bias, void* work, size_t work_bytes, void* stream);
+
+/*
  * Valid 3x3 convolution, NCHW (the encoder layers, Sec. III "single shared CNN
  * encoder"): y[i,o,p,q] = b[o] + sum_{c,u,v} w[o,c,u,v] x[i,c,s p+u,s q+v], ReLU if relu.
  * x [nimg, cin, h, w], w [cout, cin, 3, 3], y [nimg, cout, oh, ow], oh = (h-3)/s+1.

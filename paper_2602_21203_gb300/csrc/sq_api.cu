@@ -195,7 +195,8 @@ int squint_create(const squint_config* cfg, const squint_replay* ring, squint_ha
         return SQUINT_EINVAL;
     }
     if (h->c.max_k < 1) h->c.max_k = 8;
-    if (h->c.precision != SQUINT_PREC_FP32 && h->c.precision != SQUINT_PREC_BF16) {
+    if (h->c.precision != SQUINT_PREC_FP32 && h->c.precision != SQUINT_PREC_BF16 &&
+        h->c.precision != SQUINT_PREC_FP8) {
         delete h;
         return SQUINT_EINVAL;
     }

@@ -70,7 +70,8 @@ struct squint_handle {
     squint_replay ring{};
     bool has_ring = false;
     bool failed = false;
-    bool bf16 = false;                // tensor-core contractions (SQUINT_PREC_BF16)
+    bool bf16 = false;                // tensor-core contractions (SQUINT_PREC_BF16 or FP8)
+    bool fp8 = false;                 // forward linear layers in e4m3 (SQUINT_PREC_FP8)
     bool launch_failed = false;       // a tensor map could not describe an operand
     int device = 0;
     int* d_err = nullptr;             // device error word of bounded waits
@@ -138,6 +139,21 @@ struct squint_handle {
 
     // BF16 shadows (tensor-core path)
     std::map<int64_t, sq::LinBf> lin_bf;       // keyed by the canonical weight offset
+    // FP8 mode: e4m3 copies of the linear weights (quantised from the BF16 copies after
+    // every cast) and, per stream, an arena for the forward GEMMs' quantised activations
+    struct LinF8 { uint8_t* on = nullptr; uint8_t* tg = nullptr; int64_t ld = 0; float* s_on = nullptr;
+                   float* s_tg = nullptr; };
+    std::map<int64_t, LinF8> lin_f8;
+    std::vector<sq::QuantItem> quant_critic, quant_actor, quant_target;
+    float* f8_part = nullptr;             // amax partials of the weight quantisation
+    struct F8Arena { uint8_t* buf = nullptr; int64_t bytes = 0; float* part = nullptr; float* scales = nullptr; };
+    F8Arena f8_arena[4];                  // main stream, side streams 0..2
+    F8Arena* arena_for(cudaStream_t s) {
+        for (int k = 0; k < 3; ++k)
+            if (s == side[k]) return &f8_arena[k + 1];
+        return &f8_arena[0];
+    }
+    void quantize_weights(const std::vector<sq::QuantItem>& q, cudaStream_t s);
     std::vector<sq::CastItem> cast_critic, cast_actor, cast_target;
     __nv_bfloat16* z_h = nullptr;              // [2B, F]
     __nv_bfloat16* xa_h = nullptr;             // [2B, Da8]

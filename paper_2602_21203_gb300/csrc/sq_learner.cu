@@ -60,6 +60,24 @@ void GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64
     g.bias = W.b;
     g.c = Y; g.ldc = ldy;
     g.cbf = Yh; g.ldcbf = ldyh;
+    if (h_->fp8 && W.w8 && X.h) {
+        // FP8: quantise X (per tensor) into this stream's arena at flush, e4m3 weights
+        squint_handle::F8Arena* ar = h_->arena_for(s_);
+        const int64_t ld8 = (W.in + 15) / 16 * 16;
+        const int64_t bytes = (int64_t)rows * ld8;
+        const int qi = (int)q8_.size();
+        if (ar->buf && arena_used_ + bytes <= ar->bytes && qi < kF8Scales) {
+            uint8_t* dst = ar->buf + arena_used_;
+            arena_used_ += (bytes + 255) / 256 * 256;
+            q8_.push_back(QuantItem{X.h, X.ldh, rows, W.in, dst, ld8, ar->scales + qi});
+            qbytes_ += 3.0 * rows * W.in;
+            g.a[0] = TcOperand{dst, ld8, false};
+            g.b[0] = TcOperand{W.w8, W.ld8, false};
+            g.fp8 = 1; g.scale_a = ar->scales + qi; g.scale_b = W.s8;
+            tc8_.push_back(g);
+            return;
+        }
+    }
     tc_.push_back(g);
 }
 
@@ -115,14 +133,24 @@ void GemmBuilder::dw(const Mat& dY, int rows, const Mat& X, const LayerRef& W, f
 }
 
 void GemmBuilder::flush() {
-    if (fp_.empty() && tc_.empty()) return;
+    if (fp_.empty() && tc_.empty() && tc8_.empty()) return;
+    if (!q8_.empty()) {
+        ProfScope ps(h_, s_, "quantize_fp8", qbytes_, 1);
+        launch_quantize_e4m3(q8_.data(), (int)q8_.size(), h_->arena_for(s_)->part, s_);
+    }
     {
         ProfScope ps(h_, s_, kind_, flops_, 0);
         if (!fp_.empty()) launch_gemm<float>(fp_.data(), (int)fp_.size(), lay_, s_);
+        if (!tc8_.empty() && launch_tc_gemm(tc8_.data(), (int)tc8_.size(), h_->d_err, s_, split_) != 0)
+            h_->launch_failed = true;
         if (!tc_.empty() && launch_tc_gemm(tc_.data(), (int)tc_.size(), h_->d_err, s_, split_) != 0) h_->launch_failed = true;
     }
     fp_.clear();
     tc_.clear();
+    tc8_.clear();
+    q8_.clear();
+    arena_used_ = 0;
+    qbytes_ = 0;
     flops_ = 0;
 }
 
@@ -141,6 +169,13 @@ LayerRef layer_ref(squint_handle* h, const Lin& ly, bool target, const float* ba
     if (it != h->lin_bf.end() && !base) {
         r.wh = target ? it->second.tg : it->second.on;
         r.ldh = it->second.ld;
+    }
+    auto f8 = h->lin_f8.find(ly.w);
+    if (f8 != h->lin_f8.end() && !base) {
+        r.w8 = target ? f8->second.tg : f8->second.on;
+        r.s8 = target ? f8->second.s_tg : f8->second.s_on;
+        r.ld8 = f8->second.ld;
+        if (!r.w8) r.s8 = nullptr;
     }
     return r;
 }
@@ -308,7 +343,8 @@ void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, in
 
 int squint_handle::allocate() {
     const int B = c.batch, A = c.action_dim, K = c.atoms, E = 2;
-    bf16 = c.precision == SQUINT_PREC_BF16;
+    fp8 = c.precision == SQUINT_PREC_FP8;
+    bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
     SQ_CK(this, cudaGetDevice(&device));
     const int64_t n = L.total;
     params = dalloc<float>(n); grads = dalloc<float>(n);
@@ -412,10 +448,28 @@ int squint_handle::allocate() {
             lb.on = dalloc<__nv_bfloat16>((int64_t)ly.out * lb.ld);
             if (with_target) lb.tg = dalloc<__nv_bfloat16>((int64_t)ly.out * lb.ld);
             lin_bf[ly.w] = lb;
+            if (fp8) {
+                // e4m3 copies (row stride a multiple of 16 bytes), one scale per copy
+                LinF8 f;
+                f.ld = (ly.in + 15) / 16 * 16;
+                float* sc = dalloc<float>(2);
+                f.on = dalloc<uint8_t>((int64_t)ly.out * f.ld);
+                f.s_on = sc;
+                if (with_target) { f.tg = dalloc<uint8_t>((int64_t)ly.out * f.ld); f.s_tg = sc + 1; }
+                lin_f8[ly.w] = f;
+            }
         };
         if (L.D > 0) { add(L.cproj, true); add(L.aproj, false); }
         for (int e = 0; e < 2; ++e) for (const auto& ly : L.critic[e]) add(ly, true);
         for (const auto& ly : L.actor) add(ly, false);
+        if (fp8) {
+            for (auto& a : f8_arena) {
+                a.bytes = int64_t(24) << 20;
+                a.buf = dalloc<uint8_t>(a.bytes);
+                a.part = dalloc<float>(quant_workspace());
+                a.scales = dalloc<float>(kF8Scales);
+            }
+        }
         z_h = dalloc<__nv_bfloat16>((int64_t)2 * B * L.feat);
         xa_h = dalloc<__nv_bfloat16>((int64_t)2 * B * pad8(L.da));
         xcbar_h = dalloc<__nv_bfloat16>((int64_t)B * pad8(L.dc));
@@ -473,6 +527,19 @@ int squint_handle::allocate() {
             for (const auto& ly : L.critic[e]) { cast_critic.push_back(item(ly, false)); cast_target.push_back(item(ly, true)); }
         if (L.D > 0) cast_actor.push_back(item(L.aproj, false));
         for (const auto& ly : L.actor) cast_actor.push_back(item(ly, false));
+        if (fp8) {
+            auto q = [&](const Lin& ly, bool tgt) {
+                const LinBf& lb = lin_bf[ly.w];
+                const LinF8& f = lin_f8[ly.w];
+                return QuantItem{tgt ? lb.tg : lb.on, lb.ld, ly.out, ly.in, tgt ? f.tg : f.on, f.ld,
+                                 tgt ? f.s_tg : f.s_on};
+            };
+            if (L.D > 0) { quant_critic.push_back(q(L.cproj, false)); quant_target.push_back(q(L.cproj, true)); }
+            for (int e = 0; e < 2; ++e)
+                for (const auto& ly : L.critic[e]) { quant_critic.push_back(q(ly, false)); quant_target.push_back(q(ly, true)); }
+            if (L.D > 0) quant_actor.push_back(q(L.aproj, false));
+            for (const auto& ly : L.actor) quant_actor.push_back(q(ly, false));
+        }
         // inference snapshots: BF16 actor-path matrices and conv filter layouts per snapshot
         std::vector<const Lin*> pol;
         if (L.D > 0) pol.push_back(&L.aproj);
@@ -544,6 +611,14 @@ void squint_handle::release() {
     act_allocs.clear();
 }
 
+void squint_handle::quantize_weights(const std::vector<QuantItem>& q, cudaStream_t s) {
+    if (!fp8 || q.empty()) return;
+    double bytes = 0;
+    for (const auto& it : q) bytes += 3.0 * it.rows * it.cols;
+    ProfScope ps(this, s, "quantize_fp8", bytes, 1);
+    launch_quantize_e4m3(q.data(), (int)q.size(), arena_for(s)->part, s);
+}
+
 void squint_handle::snapshot_bf16(int i, cudaStream_t s) {
     if (!bf16) return;
     launch_cast_rows(cast_policy[i].data(), (int)cast_policy[i].size(), s);
@@ -563,6 +638,9 @@ int squint_handle::after_param_change() {
         launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), 0);
         launch_cast_rows(cast_actor.data(), (int)cast_actor.size(), 0);
         launch_cast_rows(cast_target.data(), (int)cast_target.size(), 0);
+        quantize_weights(quant_critic, 0);
+        quantize_weights(quant_actor, 0);
+        quantize_weights(quant_target, 0);
         cast_conv_weights(0);
         SQ_CK(this, cudaDeviceSynchronize());
     }
@@ -826,6 +904,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ProfScope ps(this, s, "cast_bf16", 6.0 * (double)(L.critic_end - L.critic_begin), 1);
         launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), s);
     }
+    quantize_weights(quant_critic, s);
 
     // ---- a11 (encoder part) + a12 (encoder range) on branch s1, beside the actor step
     fork(s, s1);
@@ -935,6 +1014,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             ProfScope ps(this, s3, "cast_bf16", 6.0 * (double)L.target_n, 1);
             launch_cast_rows(cast_target.data(), (int)cast_target.size(), s3);
         }
+        quantize_weights(quant_target, s3);
     }
     mark(s);
     // ---- a13: temperature
@@ -1014,6 +1094,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             ProfScope ps(this, s, "cast_bf16", 6.0 * (double)(L.actor_end - L.actor_begin), 1);
             launch_cast_rows(cast_actor.data(), (int)cast_actor.size(), s);
         }
+        quantize_weights(quant_actor, s);
     }
     // join the encoder and polyak branches
     fork(s1, s);

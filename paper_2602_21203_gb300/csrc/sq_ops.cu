@@ -91,6 +91,43 @@ int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, 
     return launch_status();
 }
 
+static int64_t pad16(int64_t n) { return (n + 15) / 16 * 16; }
+
+size_t squint_op_gemm_fp8_workspace(int M, int N, int K) {
+    if (M < 0 || N < 0 || K < 1) return 0;
+    return (size_t)quant_workspace() * 4 + 64 + (size_t)(M + N) * pad16(K) + 64;
+}
+
+int squint_op_gemm_fp8(int M, int N, int K, const void* A, int64_t lda, const void* B, int64_t ldb, float* C,
+                       int64_t ldc, const float* bias, void* work, size_t work_bytes, void* stream) {
+    if (M < 0 || N < 0 || K < 1 || !A || !B || !C || !work || lda < K || ldb < K) return SQUINT_EINVAL;
+    if (work_bytes < squint_op_gemm_fp8_workspace(M, N, K) || (reinterpret_cast<uintptr_t>(work) & 15)) {
+        g_last_error = "FP8 GEMM: workspace smaller than squint_op_gemm_fp8_workspace() or not 16-byte aligned";
+        return SQUINT_EINVAL;
+    }
+    if (M == 0 || N == 0) return SQUINT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = static_cast<char*>(work);
+    float* part = reinterpret_cast<float*>(w);
+    float* scales = reinterpret_cast<float*>(w + quant_workspace() * 4);
+    uint8_t* a8 = reinterpret_cast<uint8_t*>(w + quant_workspace() * 4 + 64);
+    uint8_t* b8 = a8 + (size_t)M * pad16(K);
+    QuantItem q[2];
+    q[0] = QuantItem{(const __nv_bfloat16*)A, lda, M, K, a8, pad16(K), scales};
+    q[1] = QuantItem{(const __nv_bfloat16*)B, ldb, N, K, b8, pad16(K), scales + 1};
+    launch_quantize_e4m3(q, 2, part, s);
+    TcGemm g{};
+    g.M = M; g.N = N; g.K = K; g.n_pairs = 1;
+    g.a[0] = TcOperand{a8, pad16(K), false};
+    g.b[0] = TcOperand{b8, pad16(K), false};
+    g.bias = bias; g.c = C; g.ldc = ldc;
+    g.fp8 = 1; g.scale_a = scales; g.scale_b = scales + 1;
+    int* err = tc_error_flag();
+    if (!err) return SQUINT_ECUDA;
+    if (launch_tc_gemm(&g, 1, err, s) != 0) return SQUINT_EINVAL;
+    return launch_status();
+}
+
 int squint_op_conv3x3_fwd(int dtype, int nimg, int cin, int h, int w, int cout, int stride, const void* x,
                           const void* wt, const void* b, void* y, int relu, void* stream) {
     if (!conv_ok(nimg, cin, h, w, cout, stride) || !x || !wt || !b || !y) return SQUINT_EINVAL;

@@ -28,6 +28,9 @@ struct LayerRef {
     const float* b = nullptr;
     const __nv_bfloat16* wh = nullptr;
     int64_t ldh = 0;
+    const uint8_t* w8 = nullptr;     // e4m3 copy (FP8 mode), row stride ld8, scale *s8
+    int64_t ld8 = 0;
+    const float* s8 = nullptr;
     int in = 0, out = 0;
     const float* g = nullptr;
     const float* beta = nullptr;
@@ -59,6 +62,10 @@ private:
     std::vector<GemmProblem> fp_;
     GemmLayout lay_ = kKK;
     std::vector<TcGemm> tc_;
+    std::vector<TcGemm> tc8_;        // FP8 forward problems; A is quantised at flush
+    std::vector<QuantItem> q8_;
+    int64_t arena_used_ = 0;
+    double qbytes_ = 0;
     double flops_ = 0;
     const char* kind_ = "gemm";
 };

@@ -22,6 +22,7 @@
 #include "sq_tc.cuh"
 
 #include <cuda.h>
+#include <cuda_fp8.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -50,6 +51,7 @@ struct TcProb {
     __nv_bfloat16* cbf; int64_t ldcbf;
     const float* mask; int64_t ldmask;
     int accumulate;
+    const float* scale_a; const float* scale_b;
 };
 struct TcBatch {
     TcProb p[kMaxProbs];
@@ -125,6 +127,18 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool 
     return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
            ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// Instruction descriptor of kind::f8f6f4 with e4m3 A and B (format code 0), FP32 accumulator.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int M, int N, bool a_mn, bool b_mn) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
@@ -165,8 +179,12 @@ __device__ __forceinline__ void load_operand(uint32_t dst, const CUtensorMap* ma
     }
 }
 
-template <bool A_MN, bool B_MN>
+// F8: e4m3 operands, 128-element (128-byte) K slabs, kind::f8f6f4 MMAs with K = 32, and
+// the per-tensor scales applied in the epilogue.  The K step of a slab is 32 bytes in
+// both types, so the shared-memory descriptors are the same.
+template <bool A_MN, bool B_MN, bool F8 = false>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ TcBatch gb) {
+    constexpr int BKE = F8 ? 128 : BK;   // K elements per slab
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -188,12 +206,14 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     const float* const p_mask = P.mask;
     const int64_t p_ldmask = P.ldmask;
     const bool p_acc = P.accumulate != 0;
+    const float* const p_sa = P.scale_a;
+    const float* const p_sb = P.scale_b;
     const int cta = blockIdx.x - P.tile_start;
     const int t = cta / gb.splits, split = (int)cluster_rank();
     const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint32_t base = smem_u32(smem);
-    const int nkb = (pK + BK - 1) / BK;
+    const int nkb = (pK + BKE - 1) / BKE;
     // this CTA's share of the (pair, K slab) iterations
     const int it0 = (int)((int64_t)nkb * n_pairs * split / gb.splits);
     const int total = (int)((int64_t)nkb * n_pairs * (split + 1) / gb.splits) - it0;
@@ -203,8 +223,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         const int pr = (it0 + i) / nkb, kb = (it0 + i) % nkb;
         const uint32_t st = base + s * STAGE_BYTES;
         mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-        load_operand<A_MN>(st, &P.ta[pr], m0, kb * BK, full0 + 8 * s);
-        load_operand<B_MN>(st + TILE_BYTES, &P.tb[pr], n0, kb * BK, full0 + 8 * s);
+        load_operand<A_MN>(st, &P.ta[pr], m0, kb * BKE, full0 + 8 * s);
+        load_operand<B_MN>(st + TILE_BYTES, &P.tb[pr], n0, kb * BKE, full0 + 8 * s);
     };
 
     // CTA-local setup overlaps the tail of the previous kernel (programmatic launch)
@@ -247,7 +267,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         }
     } else if (issuer) {
         // MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(BM, BN, A_MN, B_MN);
+        constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN, A_MN, B_MN) : idesc_bf16(BM, BN, A_MN, B_MN);
         bool ok = true;
         for (int i = 0; i < total; ++i) {
             const int s = i % STAGES;
@@ -256,8 +276,12 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
             const uint32_t st = base + s * STAGE_BYTES;
 #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk)
-                mma_bf16(tmem, operand_desc<A_MN>(st, kk), operand_desc<B_MN>(st + TILE_BYTES, kk), idesc,
-                         (i > 0 || kk > 0) ? 1u : 0u);
+                if constexpr (F8)
+                    mma_e4m3(tmem, operand_desc<A_MN>(st, kk), operand_desc<B_MN>(st + TILE_BYTES, kk), idesc,
+                             (i > 0 || kk > 0) ? 1u : 0u);
+                else
+                    mma_bf16(tmem, operand_desc<A_MN>(st, kk), operand_desc<B_MN>(st + TILE_BYTES, kk), idesc,
+                             (i > 0 || kk > 0) ? 1u : 0u);
             mma_commit(empty0 + 8 * s);
         }
         mma_commit(done_bar);
@@ -303,14 +327,17 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         float bias4[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) bias4[j] = bias_s[cq + j];
+        const float fp8_scale = F8 ? __ldg(p_sa) * __ldg(p_sb) : 1.f;
         const float* mine = red + (rb0 + warp) * RED_LD + cq;   // row g of this warp at mine + 4 g RED_LD
 #pragma unroll 1
         for (int g0 = 0; g0 < nrows; g0 += 8) {
             const int cnt = min(8, nrows - g0);
             float4 acc[8];
+            // BF16: rank order acc = bias + p_0 + p_1 + ...; FP8: acc = (p_0 + p_1 + ...) * scale + bias
+            // (two ranks' loads in flight at a time)
 #pragma unroll
-            for (int i = 0; i < 8; ++i) acc[i] = make_float4(bias4[0], bias4[1], bias4[2], bias4[3]);
-            // rank order: acc = bias + p_0 + p_1 + ... (two ranks' loads in flight at a time)
+            for (int i = 0; i < 8; ++i)
+                acc[i] = F8 ? make_float4(0.f, 0.f, 0.f, 0.f) : make_float4(bias4[0], bias4[1], bias4[2], bias4[3]);
             int q = 0;
             for (; q + 1 < S; q += 2) {
                 const float* s0 = map_rank(mine, q) + (size_t)g0 * 4 * RED_LD;
@@ -336,6 +363,15 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     acc[i].x += x0[i].x; acc[i].y += x0[i].y; acc[i].z += x0[i].z; acc[i].w += x0[i].w;
+                }
+            }
+            if constexpr (F8) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    acc[i].x = fmaf(acc[i].x, fp8_scale, bias4[0]);
+                    acc[i].y = fmaf(acc[i].y, fp8_scale, bias4[1]);
+                    acc[i].z = fmaf(acc[i].z, fp8_scale, bias4[2]);
+                    acc[i].w = fmaf(acc[i].w, fp8_scale, bias4[3]);
                 }
             }
             const int row0 = m0 + rb0 + warp + 4 * g0;   // row of entry i: row0 + 4 i
@@ -447,21 +483,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // 2-D BF16 tensor map over a row-major matrix with `outer` rows of `inner` elements
 // (row stride ld elements), 128-byte swizzle, zero fill outside the matrix.
-bool make_map(CUtensorMap* m, const void* ptr, int64_t inner, int64_t outer, int64_t ld, int box_inner, int box_outer) {
+bool make_map(CUtensorMap* m, const void* ptr, int64_t inner, int64_t outer, int64_t ld, int box_inner, int box_outer,
+              bool fp8 = false) {
     auto fn = encode_fn();
     if (!fn) return false;
-    if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((ld * 2) & 15) || inner < 1 || outer < 1) return false;
+    const int64_t es = fp8 ? 1 : 2;
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15) || ((ld * es) & 15) || inner < 1 || outer < 1) return false;
     cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
     cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
     cuuint32_t estr[2] = {1, 1};
     std::memset(m, 0, sizeof(*m));
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+    return fn(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims,
+              strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool operand_map(CUtensorMap* m, const TcOperand& o, int mn_extent, int k_extent) {
+bool operand_map(CUtensorMap* m, const TcOperand& o, int mn_extent, int k_extent, bool fp8 = false) {
+    if (fp8)          // K-major only: 128 elements (128 bytes) of K by 128 rows
+        return !o.mn_major && make_map(m, o.ptr, k_extent, mn_extent, o.ld, 128, 128, true);
     if (o.mn_major)   // element (mn, k) at ptr[k * ld + mn]
         return make_map(m, o.ptr, mn_extent, k_extent, o.ld, 64, 64);
     return make_map(m, o.ptr, k_extent, mn_extent, o.ld, 64, 128);   // element (mn, k) at ptr[mn * ld + k]
@@ -470,6 +511,8 @@ bool operand_map(CUtensorMap* m, const TcOperand& o, int mn_extent, int k_extent
 template <bool A_MN, bool B_MN>
 void set_smem_attr() {
     cudaFuncSetAttribute(tc_gemm_kernel<A_MN, B_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (!A_MN && !B_MN)
+        cudaFuncSetAttribute(tc_gemm_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
 }  // namespace
@@ -520,21 +563,25 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, b
         gb.err = err;
         int tiles = 0, min_iters = 1 << 30;
         bool a_mn = probs[base].a[0].mn_major, b_mn = probs[base].b[0].mn_major;
+        const bool f8 = probs[base].fp8 != 0;
         for (int i = 0; i < gb.n; ++i) {
             const TcGemm& g = probs[base + i];
             TcProb& p = gb.p[i];
             if (g.a[0].mn_major != a_mn || g.b[0].mn_major != b_mn || g.n_pairs < 1 || g.n_pairs > 2) return -1;
+            if ((g.fp8 != 0) != f8 || (f8 && (g.n_pairs != 1 || a_mn || b_mn || !g.scale_a || !g.scale_b))) return -1;
             for (int q = 0; q < g.n_pairs; ++q) {
-                if (!operand_map(&p.ta[q], g.a[q], g.M, g.K)) return -2;
-                if (!operand_map(&p.tb[q], g.b[q], g.N, g.K)) return -2;
+                if (!operand_map(&p.ta[q], g.a[q], g.M, g.K, f8)) return -2;
+                if (!operand_map(&p.tb[q], g.b[q], g.N, g.K, f8)) return -2;
             }
             p.M = g.M; p.N = g.N; p.K = g.K; p.n_pairs = g.n_pairs;
             p.bias = g.bias; p.c = g.c; p.ldc = g.ldc; p.cbf = g.cbf; p.ldcbf = g.ldcbf;
             p.mask = g.mask; p.ldmask = g.ldmask; p.accumulate = g.accumulate;
+            p.scale_a = g.scale_a; p.scale_b = g.scale_b;
             p.tiles_n = (g.N + BN - 1) / BN;
             p.tile_start = tiles;   // in tiles for now, scaled by the split below
             tiles += ((g.M + BM - 1) / BM) * p.tiles_n;
-            min_iters = std::min(min_iters, ((g.K + BK - 1) / BK) * g.n_pairs);
+            const int bke = f8 ? 128 : BK;
+            min_iters = std::min(min_iters, ((g.K + bke - 1) / bke) * g.n_pairs);
         }
         if (!tiles) continue;
         int S = std::min(std::min(g_max_splits, std::max(1, kSplitTarget / tiles)), min_iters / kMinSplitIters);
@@ -542,12 +589,119 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, b
         gb.splits = S;
         for (int i = 0; i < gb.n; ++i) gb.p[i].tile_start *= S;
         const dim3 grid(tiles * S), cluster(S);
-        if (!a_mn && !b_mn) launch_kc(tc_gemm_kernel<false, false>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
+        if (f8) launch_kc(tc_gemm_kernel<false, false, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
+        else if (!a_mn && !b_mn) launch_kc(tc_gemm_kernel<false, false>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
         else if (!a_mn && b_mn) launch_kc(tc_gemm_kernel<false, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
         else if (a_mn && b_mn) launch_kc(tc_gemm_kernel<true, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
         else launch_kc(tc_gemm_kernel<true, false>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
     }
     return 0;
+}
+
+// ---------------------------------------------------------------- FP8 quantisation
+namespace {
+struct QuantBatch { QuantItem it[kQuantMaxItems]; int n; float* part; };
+
+// Whether row r of an item can be read 8 elements (16 bytes) at a time.
+__device__ __forceinline__ bool quant_vec(const QuantItem& q) {
+    return (q.cols % 8) == 0 && (q.src_ld % 8) == 0 && (reinterpret_cast<uintptr_t>(q.src) & 15) == 0 &&
+           (q.dst_ld % 8) == 0 && (reinterpret_cast<uintptr_t>(q.dst) & 7) == 0;
+}
+
+// Pass 1: block b of item i takes rows b, b + kQuantBlocks, ... and writes max |x| to
+// part[i * kQuantBlocks + b].
+__global__ void __launch_bounds__(256) amax_kernel(QuantBatch qb) {
+    SQ_KERNEL_ENTRY();
+    const QuantItem& q = qb.it[blockIdx.y];
+    const bool vec = quant_vec(q);
+    float m = 0.f;
+    for (int r = blockIdx.x; r < q.rows; r += kQuantBlocks) {
+        const __nv_bfloat16* src = q.src + (int64_t)r * q.src_ld;
+        if (vec) {
+            for (int j = threadIdx.x * 8; j < q.cols; j += blockDim.x * 8) {
+                const uint4 u = *reinterpret_cast<const uint4*>(src + j);
+                const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float2 f = __bfloat1622float2(h[k]);
+                    m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
+                }
+            }
+        } else {
+            for (int j = threadIdx.x; j < q.cols; j += blockDim.x) m = fmaxf(m, fabsf(__bfloat162float(src[j])));
+        }
+    }
+    m = warp_max(m);
+    __shared__ float wm[8];
+    if (threadIdx.x % 32 == 0) wm[threadIdx.x / 32] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = wm[0];
+        for (int w = 1; w < (int)(blockDim.x / 32); ++w) t = fmaxf(t, wm[w]);
+        qb.part[blockIdx.y * kQuantBlocks + blockIdx.x] = t;
+    }
+}
+
+__device__ __forceinline__ uint8_t to_e4m3(float x) {
+    return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+
+// Pass 2: every block reduces the item's partial maxima, scale = amax / 448 (the largest
+// finite e4m3 value), and writes e4m3(x / scale) for its rows; block 0 stores the scale.
+__global__ void __launch_bounds__(256) quantize_kernel(QuantBatch qb) {
+    SQ_KERNEL_ENTRY();
+    const QuantItem& q = qb.it[blockIdx.y];
+    __shared__ float sc;
+    if (threadIdx.x < 32) {
+        float m = 0.f;
+        for (int b = threadIdx.x; b < kQuantBlocks; b += 32) m = fmaxf(m, qb.part[blockIdx.y * kQuantBlocks + b]);
+        m = warp_max(m);
+        if (threadIdx.x == 0) {
+            const float s = m > 0.f ? m / 448.f : 1.f;
+            sc = s;
+            if (blockIdx.x == 0) *q.scale = s;
+        }
+    }
+    __syncthreads();
+    const float s = sc;
+    const bool vec = quant_vec(q);
+    for (int r = blockIdx.x; r < q.rows; r += kQuantBlocks) {
+        const __nv_bfloat16* src = q.src + (int64_t)r * q.src_ld;
+        uint8_t* dst = q.dst + (int64_t)r * q.dst_ld;
+        if (vec) {
+            for (int j = threadIdx.x * 8; j < q.dst_ld; j += blockDim.x * 8) {
+                uint32_t w[2] = {0u, 0u};
+                if (j < q.cols) {
+                    const uint4 u = *reinterpret_cast<const uint4*>(src + j);
+                    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float2 f = __bfloat1622float2(h[k]);
+                        w[k / 2] |= ((uint32_t)to_e4m3(f.x / s) | ((uint32_t)to_e4m3(f.y / s) << 8)) << (16 * (k % 2));
+                    }
+                }
+                *reinterpret_cast<uint2*>(dst + j) = make_uint2(w[0], w[1]);
+            }
+        } else {
+            for (int j = threadIdx.x; j < q.dst_ld; j += blockDim.x)
+                dst[j] = j < q.cols ? to_e4m3(__bfloat162float(src[j]) / s) : to_e4m3(0.f);
+        }
+    }
+}
+}  // namespace
+
+int64_t quant_workspace() { return (int64_t)kQuantMaxItems * kQuantBlocks; }
+
+void launch_quantize_e4m3(const QuantItem* items, int n, float* part, cudaStream_t s) {
+    for (int base = 0; base < n; base += kQuantMaxItems) {
+        QuantBatch qb;
+        std::memset(&qb, 0, sizeof(qb));
+        qb.n = std::min(kQuantMaxItems, n - base);
+        qb.part = part;
+        for (int i = 0; i < qb.n; ++i) qb.it[i] = items[base + i];
+        launch_k(amax_kernel, dim3(kQuantBlocks, qb.n), dim3(256), 0, s, qb);
+        launch_k(quantize_kernel, dim3(kQuantBlocks, qb.n), dim3(256), 0, s, qb);
+    }
 }
 
 // ---------------------------------------------------------------- casts

@@ -5,10 +5,11 @@
 
 namespace sq {
 
-// A BF16 operand in global memory.  K-major: element (mn, k) at ptr[mn * ld + k];
-// MN-major: element (mn, k) at ptr[k * ld + mn].  ptr 16-byte aligned, ld a multiple of 8.
+// A BF16 (or FP8 e4m3) operand in global memory.  K-major: element (mn, k) at
+// ptr[mn * ld + k]; MN-major: element (mn, k) at ptr[k * ld + mn].  ptr 16-byte
+// aligned, ld x element size a multiple of 16 bytes.
 struct TcOperand {
-    const __nv_bfloat16* ptr;
+    const void* ptr;
     int64_t ld;
     bool mn_major;
 };
@@ -24,7 +25,27 @@ struct TcGemm {
     __nv_bfloat16* cbf; int64_t ldcbf;
     const float* mask; int64_t ldmask;
     int accumulate;           // c += D instead of c = D
+    // FP8: A and B are e4m3 (K-major, one pair) holding x / scale per tensor; D is
+    // scaled back by *scale_a * *scale_b before the bias (device scalars)
+    int fp8;
+    const float* scale_a; const float* scale_b;
 };
+
+// Per-tensor e4m3 quantisation of BF16 rows (current scaling): scale = amax / 448,
+// dst = e4m3(x / scale) rounded to nearest, pad columns zero, *scale written.
+// Two launches per batch: block maxima of |x| into `part`, then every block takes
+// the maximum over those partials (no atomics: the scale is the same every run).
+struct QuantItem {
+    const __nv_bfloat16* src; int64_t src_ld;
+    int rows, cols;
+    uint8_t* dst; int64_t dst_ld;   // dst_ld >= cols, a multiple of 16
+    float* scale;
+};
+constexpr int kQuantMaxItems = 8;
+constexpr int kF8Scales = 64;         // activation scales per stream arena (FP8 learner)
+constexpr int kQuantBlocks = 64;      // row blocks per item in the amax pass
+int64_t quant_workspace();            // floats of `part`
+void launch_quantize_e4m3(const QuantItem* items, int n, float* part, cudaStream_t s);
 
 // Launches one grouped kernel per up to 4 problems (all of one A/B majorness).  When
 // the launch has few output tiles and a long K, the K range of each tile is split over

@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsquint.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EAGAIN, ESTATE = 0, -1, -2, -3, -4, -5, -6
-PREC_FP32, PREC_BF16 = 0, 1
+PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
 MAX_CONV, MAX_HIDDEN = 8, 4
 
 
@@ -101,6 +101,8 @@ def load():
         "squint_profile_kernels": (I, [P, I, P, P, P, P, P, ctypes.POINTER(I), P]),
         "squint_op_gemm": (I, [I, I, I, I, P, I64, I64, P, I64, I64, P, I64, P, I, P]),
         "squint_op_relu_bwd": (I, [I, I64, P, P, P, P]),
+        "squint_op_gemm_fp8_workspace": (SZ, [I, I, I]),
+        "squint_op_gemm_fp8": (I, [I, I, I, P, I64, P, I64, P, I64, P, P, SZ, P]),
         "squint_op_conv3x3_fwd": (I, [I, I, I, I, I, I, I, P, P, P, P, I, P]),
         "squint_op_conv3x3_workspace": (SZ, [I, I, I, I, I, I, I]),
         "squint_op_conv3x3_bwd": (I, [I, I, I, I, I, I, I, P, P, P, P, P, P, P, P, SZ, P]),

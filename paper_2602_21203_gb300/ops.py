@@ -51,6 +51,25 @@ def gemm(A, B, bias=None, out=None, accumulate=False, M=None, N=None, K=None):
     return out
 
 
+def gemm_fp8(A, B, bias=None, out=None):
+    """out = scale_A scale_B e4m3(A / scale_A) e4m3(B / scale_B)^T + bias for BF16 A [M, K], B [N, K]
+    (row-major, unit column stride); per-tensor scales amax / 448.  Returns (out, (scale_A, scale_B))."""
+    _need(A, torch.bfloat16, "A")
+    _need(B, torch.bfloat16, "B")
+    M, K = A.shape
+    N = B.shape[0]
+    L = _lib.load()
+    work = torch.empty(max(L.squint_op_gemm_fp8_workspace(M, N, K), 16), dtype=torch.uint8, device=A.device)
+    if out is None:
+        out = torch.empty(M, N, device=A.device, dtype=torch.float32)
+    if bias is not None:
+        _need(bias, torch.float32, "bias")
+    _chk(L.squint_op_gemm_fp8(M, N, K, _p(A), A.stride(0), _p(B), B.stride(0), _p(out), out.stride(0), _p(bias),
+                              _p(work), work.numel(), _s()), "squint_op_gemm_fp8")
+    scales = work[2048:2056].view(torch.float32)
+    return out, (scales[0], scales[1])
+
+
 def conv3x3_fwd(x, w, b, stride, relu):
     n, cin, h, wd = x.shape
     cout = w.shape[0]

@@ -100,6 +100,36 @@ def test_bf16_gemm_k_split_over_cluster(ops, a_mn, b_mn, shape):
     assert _rel(acc.cpu().numpy(), ref2) < 1e-5
 
 
+FP8_SHAPES = [(512, 512, 512), (512, 256, 2592), (300, 101, 274), (7, 16, 64), (1, 1, 8), (1024, 12, 272)]
+
+
+@pytest.mark.parametrize("shape", FP8_SHAPES)
+def test_fp8_gemm_matches_quantised_product(ops, shape):
+    """e4m3 GEMM with per-tensor scales vs the FP64 product of the same quantised operands
+    (quantised here with PyTorch's float8_e4m3fn conversion: x / (amax / 448), nearest)."""
+    M, N, K = shape
+    g = torch.Generator().manual_seed(M + 3 * N + 7 * K)
+    a = (torch.randn(M, K, generator=g) * 3).bfloat16()
+    b = (torch.randn(N, K, generator=g) * 0.05).bfloat16()
+    bias = torch.randn(N, generator=g)
+    out, (sa, sb) = ops.gemm_fp8(a.cuda(), b.cuda(), bias=bias.cuda())
+    torch.cuda.synchronize()
+
+    def quant(x):
+        x = x.float()
+        s = x.abs().max() / 448.0
+        return (x / s).to(torch.float8_e4m3fn).double(), s
+
+    aq, ra = quant(a)
+    bq, rb = quant(b)
+    assert float(sa) == float(ra) and float(sb) == float(rb)
+    ref = (aq @ bq.T) * (ra.double() * rb.double()) + bias.double()
+    assert _rel(out.cpu().numpy(), ref.numpy()) < 1e-5, shape
+    # and the quantisation error itself is what e4m3 allows (3 mantissa bits)
+    full = a.double() @ b.double().T + bias.double()
+    assert _rel(out.cpu().numpy(), full.numpy()) < 0.1
+
+
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
 def test_cuda_core_gemm_layouts(ops, dtype):
     g = torch.Generator().manual_seed(4)

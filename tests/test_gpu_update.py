@@ -262,3 +262,25 @@ def test_bf16_graph_equals_eager_bitwise(L):
     assert np.array_equal(a.params(), b.params())
     a.close()
     b.close()
+
+
+# ---------------------------------------------------------------- FP8 forward layers
+def test_fp8_update_runs_and_replays_bitwise(L):
+    """FP8 mode (e4m3 forward linear layers, per-tensor scales): graph == eager bit for
+    bit, finite, and the first update's losses near the oracle's (printed)."""
+    cfg = synth.make_config("train_b512", ring_size=4096)
+    ring = synth.make_ring(cfg, 0, device="cuda")
+    a = L.Learner(cfg, ring, precision=L.PREC_FP8)
+    b = L.Learner(cfg, ring, precision=L.PREC_FP8)
+    sa = a.update(3, graph=True)
+    sb = b.update(3, graph=False)
+    assert sa == sb
+    assert np.array_equal(a.params(), b.params())
+    assert all(np.isfinite([s["critic_loss"], s["actor_loss"], s["q_mean"]]).all() for s in sa)
+    c = L.Learner(cfg, ring, precision=L.PREC_FP8)
+    st = c.update(1, graph=False)[0]
+    ref, _ = o.update(o.init_state(cfg), lazy_ring(ring), cfg)
+    print("\nfp8 vs oracle:", {k: (st[k], ref[k]) for k in ("q_mean", "critic_loss", "actor_loss")})
+    assert abs(st["critic_loss"] - ref["critic_loss"]) <= 5e-2 * abs(ref["critic_loss"])
+    for x in (a, b, c):
+        x.close()
