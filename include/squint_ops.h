@@ -39,6 +39,20 @@ int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, 
 
 
 /*
+ * BF16 linear layer with its LayerNorm in one kernel (the hidden layers of the critic and
+ * actor MLPs, Sec. IV "Normalization"): pre = A B^T + bias (A [M, K], B [N, K] BF16,
+ * row-major, row strides lda, ldb >= K, multiples of 8), then per row
+ * post = (pre - mean) rstd g + beta with rstd = 1 / sqrt(var + eps), ReLU if relu;
+ * pre and post FP32 [M, N], post_bf (optional) BF16 [M, N], mean and rstd [M].  The
+ * column tiles of each 128-row block run as one thread-block cluster and exchange row
+ * sums through distributed shared memory; N up to 1024 (SQUINT_EINVAL above what the
+ * device can co-schedule).
+ */
+int squint_op_gemm_layernorm(int M, int N, int K, const void* A, int64_t lda, const void* B, int64_t ldb,
+                             const float* bias, const float* g, const float* beta, float eps, int relu, float* pre,
+                             float* post, void* post_bf, float* mean, float* rstd, void* stream);
+
+/*
  * FP8 (e4m3) GEMM with per-tensor scaling, FP32 accumulation (the reduced-precision
  * form tried for the forward linear layers): A [M, K] and B [N, K] are BF16, row
  * stride lda / ldb >= K; each is quantised as a whole, scale = max|x| / 448 and

@@ -72,6 +72,10 @@ struct squint_handle {
     bool failed = false;
     bool bf16 = false;                // tensor-core contractions (SQUINT_PREC_BF16 or FP8)
     bool fp8 = false;                 // forward linear layers in e4m3 (SQUINT_PREC_FP8)
+    // hidden-layer LayerNorm in the GEMM epilogue (tensor-core path), chosen by
+    // SQUINT_FUSED_LN=1 in the environment at creation; off by default: at batch 512 the
+    // separate LayerNorm kernel gives more updates/s (1,310 vs 1,264 on the same GPU)
+    bool fuse_ln = false;
     bool launch_failed = false;       // a tensor map could not describe an operand
     int device = 0;
     int* d_err = nullptr;             // device error word of bounded waits

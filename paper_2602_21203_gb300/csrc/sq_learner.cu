@@ -20,6 +20,7 @@
 #include "sq_sched.h"
 
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <tuple>
@@ -44,14 +45,14 @@ GemmProblem lin_fwd(const float* X, int64_t ldx, int rows, const float* W, const
 }
 
 // ---------------------------------------------------------------- GemmBuilder
-void GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64_t ldy, __nv_bfloat16* Yh,
-                      int64_t ldyh) {
+bool GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64_t ldy, __nv_bfloat16* Yh,
+                      int64_t ldyh, const LnProblem* ln, bool relu) {
     flops_ += 2.0 * rows * W.out * W.in;
     kind_ = bf_ ? "tc_gemm_fwd" : "gemm_f32_fwd";
     if (!bf_) {
         fp_.push_back(lin_fwd(X.f, X.ld, rows, W.w, W.b, W.in, W.out, Y, ldy));
         lay_ = kKK;
-        return;
+        return false;
     }
     TcGemm g{};
     g.M = rows; g.N = W.out; g.K = W.in; g.n_pairs = 1;
@@ -60,6 +61,14 @@ void GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64
     g.bias = W.b;
     g.c = Y; g.ldc = ldy;
     g.cbf = Yh; g.ldcbf = ldyh;
+    bool fused = false;
+    if (ln && !Yh && W.out <= 128 * tc_max_cluster() && ln->ld_out == W.out && ln->ld_out_bf == W.out) {
+        g.ln_g = ln->g; g.ln_beta = ln->beta;
+        g.ln_post = ln->out; g.ln_posth = ln->out_bf;
+        g.ln_mean = ln->mean; g.ln_rstd = ln->rstd;
+        g.ln_eps = (float)h_->c.ln_eps; g.ln_relu = relu ? 1 : 0;
+        fused = true;
+    }
     if (h_->fp8 && W.w8 && X.h) {
         // FP8: quantise X (per tensor) into this stream's arena at flush, e4m3 weights
         squint_handle::F8Arena* ar = h_->arena_for(s_);
@@ -74,11 +83,12 @@ void GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64
             g.a[0] = TcOperand{dst, ld8, false};
             g.b[0] = TcOperand{W.w8, W.ld8, false};
             g.fp8 = 1; g.scale_a = ar->scales + qi; g.scale_b = W.s8;
-            tc8_.push_back(g);
-            return;
+            (fused ? tc8ln_ : tc8_).push_back(g);
+            return fused;
         }
     }
-    tc_.push_back(g);
+    (fused ? tcln_ : tc_).push_back(g);
+    return fused;
 }
 
 void GemmBuilder::dx(const Mat* dY, const LayerRef* W, int n_pairs, int rows, int col0, int ncols, float* dX,
@@ -133,7 +143,7 @@ void GemmBuilder::dw(const Mat& dY, int rows, const Mat& X, const LayerRef& W, f
 }
 
 void GemmBuilder::flush() {
-    if (fp_.empty() && tc_.empty() && tc8_.empty()) return;
+    if (fp_.empty() && tc_.empty() && tc8_.empty() && tcln_.empty() && tc8ln_.empty()) return;
     if (!q8_.empty()) {
         ProfScope ps(h_, s_, "quantize_fp8", qbytes_, 1);
         launch_quantize_e4m3(q8_.data(), (int)q8_.size(), h_->arena_for(s_)->part, s_);
@@ -141,13 +151,15 @@ void GemmBuilder::flush() {
     {
         ProfScope ps(h_, s_, kind_, flops_, 0);
         if (!fp_.empty()) launch_gemm<float>(fp_.data(), (int)fp_.size(), lay_, s_);
-        if (!tc8_.empty() && launch_tc_gemm(tc8_.data(), (int)tc8_.size(), h_->d_err, s_, split_) != 0)
-            h_->launch_failed = true;
-        if (!tc_.empty() && launch_tc_gemm(tc_.data(), (int)tc_.size(), h_->d_err, s_, split_) != 0) h_->launch_failed = true;
+        for (auto* v : {&tc8_, &tc8ln_, &tc_, &tcln_})
+            if (!v->empty() && launch_tc_gemm(v->data(), (int)v->size(), h_->d_err, s_, split_) != 0)
+                h_->launch_failed = true;
     }
     fp_.clear();
     tc_.clear();
     tc8_.clear();
+    tcln_.clear();
+    tc8ln_.clear();
     q8_.clear();
     arena_used_ = 0;
     qbytes_ = 0;
@@ -190,6 +202,22 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
                  cudaStream_t s, bool split) {
     const int nh = (int)sets[0].size() - 1;
     for (int l = 0; l <= nh; ++l) {
+        // the hidden layers' LayerNorm (+ReLU) problems; on the tensor-core path the GEMM
+        // computes them in its epilogue
+        LnProblem lp[2];
+        if (l < nh)
+            for (int e = 0; e < E; ++e) {
+                const LayerRef& ly = sets[e][l];
+                LnProblem p{};
+                p.rows = rows; p.n = ly.out;
+                p.pre = mb.pre[l] + (int64_t)e * rows * ly.out; p.ld_pre = ly.out;
+                p.g = ly.g; p.beta = ly.beta;
+                p.out = mb.post[l] + (int64_t)e * rows * ly.out; p.ld_out = ly.out;
+                if (bf16 && !mb.posth.empty()) { p.out_bf = mb.posth[l] + (int64_t)e * rows * ly.out; p.ld_out_bf = ly.out; }
+                p.mean = mb.mean[l] + (int64_t)e * rows; p.rstd = mb.rstd[l] + (int64_t)e * rows;
+                lp[e] = p;
+            }
+        bool fused = l < nh && bf16 && h->fuse_ln && !mb.posth.empty();
         {
             GemmBuilder gb(h, s, bf16, split);
             for (int e = 0; e < E; ++e) {
@@ -202,22 +230,11 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
                     in.ldh = ly.in;
                 }
                 float* y = l < nh ? mb.pre[l] + (int64_t)e * rows * ly.out : mb.out + (int64_t)e * rows * ly.out;
-                gb.fwd(in, rows, ly, y, ly.out);
+                const bool f = gb.fwd(in, rows, ly, y, ly.out, nullptr, 0, fused ? &lp[e] : nullptr, true);
+                fused = fused && f;
             }
         }
-        if (l == nh) break;
-        LnProblem lp[2];
-        for (int e = 0; e < E; ++e) {
-            const LayerRef& ly = sets[e][l];
-            LnProblem p{};
-            p.rows = rows; p.n = ly.out;
-            p.pre = mb.pre[l] + (int64_t)e * rows * ly.out; p.ld_pre = ly.out;
-            p.g = ly.g; p.beta = ly.beta;
-            p.out = mb.post[l] + (int64_t)e * rows * ly.out; p.ld_out = ly.out;
-            if (bf16 && !mb.posth.empty()) { p.out_bf = mb.posth[l] + (int64_t)e * rows * ly.out; p.ld_out_bf = ly.out; }
-            p.mean = mb.mean[l] + (int64_t)e * rows; p.rstd = mb.rstd[l] + (int64_t)e * rows;
-            lp[e] = p;
-        }
+        if (l == nh || fused) continue;
         ProfScope ps(h, s, "layernorm_fwd", 4.0 * E * rows * sets[0][l].out * (bf16 ? 3.5 : 3.0), 1);
         launch_ln_fwd(lp, E, true, (float)h->c.ln_eps, s);
     }
@@ -344,6 +361,7 @@ void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, in
 int squint_handle::allocate() {
     const int B = c.batch, A = c.action_dim, K = c.atoms, E = 2;
     fp8 = c.precision == SQUINT_PREC_FP8;
+    if (const char* e = std::getenv("SQUINT_FUSED_LN")) fuse_ln = std::atoi(e) != 0;
     bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
     SQ_CK(this, cudaGetDevice(&device));
     const int64_t n = L.total;

@@ -91,6 +91,26 @@ int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, 
     return launch_status();
 }
 
+int squint_op_gemm_layernorm(int M, int N, int K, const void* A, int64_t lda, const void* B, int64_t ldb,
+                             const float* bias, const float* g, const float* beta, float eps, int relu, float* pre,
+                             float* post, void* post_bf, float* mean, float* rstd, void* stream) {
+    if (M < 0 || N < 1 || K < 1 || !A || !B || !g || !beta || !pre || !post || !mean || !rstd) return SQUINT_EINVAL;
+    if (M == 0) return SQUINT_OK;
+    tc_prepare();
+    if (N > 128 * tc_max_cluster()) {
+        g_last_error = "GEMM + LayerNorm: N above 128 x the largest GEMM cluster";
+        return SQUINT_EINVAL;
+    }
+    TcGemm gm{};
+    if (!bf16_problem(M, N, K, A, lda, 1, B, ldb, 1, pre, N, bias, 0, &gm)) return SQUINT_EINVAL;
+    gm.ln_g = g; gm.ln_beta = beta; gm.ln_post = post; gm.ln_posth = (__nv_bfloat16*)post_bf;
+    gm.ln_mean = mean; gm.ln_rstd = rstd; gm.ln_eps = eps; gm.ln_relu = relu;
+    int* err = tc_error_flag();
+    if (!err) return SQUINT_ECUDA;
+    if (launch_tc_gemm(&gm, 1, err, (cudaStream_t)stream) != 0) return SQUINT_EINVAL;
+    return launch_status();
+}
+
 static int64_t pad16(int64_t n) { return (n + 15) / 16 * 16; }
 
 size_t squint_op_gemm_fp8_workspace(int M, int N, int K) {

@@ -44,9 +44,11 @@ public:
     GemmBuilder(squint_handle* h, cudaStream_t s, bool bf16, bool split = true)
         : h_(h), s_(s), bf_(bf16), split_(split) {}
     ~GemmBuilder() { flush(); }
-    // Y = X W^T + b   (Yh: optional BF16 copy of Y)
-    void fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64_t ldy, __nv_bfloat16* Yh = nullptr,
-             int64_t ldyh = 0);
+    // Y = X W^T + b   (Yh: optional BF16 copy of Y).  With `ln` (tensor-core path only),
+    // the LayerNorm (+ReLU) of Y's rows is computed in the same kernel; returns whether
+    // it was (otherwise the caller runs the LayerNorm kernel).
+    bool fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64_t ldy, __nv_bfloat16* Yh = nullptr,
+             int64_t ldyh = 0, const LnProblem* ln = nullptr, bool relu = false);
     // dX[:, 0:ncols] = sum_q dY_q W_q[:, col0:col0+ncols]  (* (mask > 0))
     void dx(const Mat* dY, const LayerRef* W, int n_pairs, int rows, int col0, int ncols, float* dX, int64_t ldx,
             const float* mask = nullptr, int64_t ldm = 0);
@@ -62,6 +64,8 @@ private:
     std::vector<GemmProblem> fp_;
     GemmLayout lay_ = kKK;
     std::vector<TcGemm> tc_;
+    std::vector<TcGemm> tcln_;       // problems with the LayerNorm epilogue (launched apart)
+    std::vector<TcGemm> tc8ln_;
     std::vector<TcGemm> tc8_;        // FP8 forward problems; A is quantised at flush
     std::vector<QuantItem> q8_;
     int64_t arena_used_ = 0;

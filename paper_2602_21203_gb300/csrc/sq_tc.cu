@@ -35,7 +35,7 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
 constexpr int TILE_BYTES = BM * BK * 2;                // 16 KB per operand per stage
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + BN * 4;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + BN * 4 + (2 * BN + 4 * BM) * 4;
 constexpr int RED_LD = BN + 4;   // FP32 row stride of the accumulator tile in shared memory
 static_assert(BM * RED_LD * 4 <= STAGES * STAGE_BYTES, "accumulator tile must fit in the operand stages");
 constexpr long long kWaitCycles = 4000000000ll;        // ~2 s at 2 GHz
@@ -52,11 +52,16 @@ struct TcProb {
     const float* mask; int64_t ldmask;
     int accumulate;
     const float* scale_a; const float* scale_b;
+    const float* ln_g; const float* ln_beta;
+    float* ln_post; __nv_bfloat16* ln_posth;
+    float* ln_mean; float* ln_rstd;
+    float ln_eps; int ln_relu;
 };
 struct TcBatch {
     TcProb p[kMaxProbs];
     int n;
     int splits;       // CTAs per output tile = cluster size (K split)
+    int ln;           // LayerNorm epilogue: the cluster is the row block's column tiles (splits == 1)
     int* err;
 };
 
@@ -190,6 +195,12 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
     float* bias_s = reinterpret_cast<float*>(tmem_slot + 4);          // [BN]
+    float* g_s = bias_s + BN;                                          // [BN] LayerNorm gain
+    float* beta_s = g_s + BN;                                          // [BN] LayerNorm shift
+    float* ln_s1 = beta_s + BN;                                        // [BM] row sums of this tile
+    float* ln_s2 = ln_s1 + BM;                                         // [BM] centred squares
+    float* ln_mean_s = ln_s2 + BM;                                     // [BM]
+    float* ln_rstd_s = ln_mean_s + BM;                                 // [BM]
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES), done_bar = smem_u32(bars + 2 * STAGES);
 
     int pi = 0;
@@ -209,7 +220,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     const float* const p_sa = P.scale_a;
     const float* const p_sb = P.scale_b;
     const int cta = blockIdx.x - P.tile_start;
-    const int t = cta / gb.splits, split = (int)cluster_rank();
+    const int crank = (int)cluster_rank();
+    const int t = cta / gb.splits, split = gb.ln ? 0 : crank;   // K split rank (0 in LayerNorm mode)
     const int m0 = (t / tiles_n) * BM, n0 = (t % tiles_n) * BN;
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const uint32_t base = smem_u32(smem);
@@ -256,8 +268,14 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     // the bias is first read in the epilogue, after the cluster barrier
-    if (warp >= 2)
+    if (warp >= 2) {
         for (int j = threadIdx.x - 64; j < BN; j += 64) bias_s[j] = (p_bias && n0 + j < pN) ? p_bias[n0 + j] : 0.f;
+        if (gb.ln)
+            for (int j = threadIdx.x - 64; j < BN; j += 64) {
+                g_s[j] = n0 + j < pN ? P.ln_g[n0 + j] : 0.f;
+                beta_s[j] = n0 + j < pN ? P.ln_beta[n0 + j] : 0.f;
+            }
+    }
 
     if (producer) {
         for (int i = pre; i < total; ++i) {
@@ -309,6 +327,62 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         }
     }
     (void)have;   // a wait that gave up has set *err; the tile's values are then meaningless
+    if (gb.ln) {
+        // LayerNorm statistics of each output row over the cluster's column tiles: each CTA
+        // sums its 128 columns of the row, the cluster exchanges the sums (rank order), then
+        // the centred squares the same way
+        __syncthreads();   // accumulator rows, bias, gain and shift staged
+        // warp w takes rows w, w + 4, ... (8 at a time); lane l sums columns 4l .. 4l + 3 and a
+        // butterfly adds the lanes, so a row's sum has the same order wherever the row sits
+        // in the tile; the cluster exchange is then one row per thread
+        const int cq = lane * 4;
+        const int nvl = n0 + cq < pN ? min(4, pN - n0 - cq) : 0;
+        auto row_pass = [&](float* dst, bool centred) {
+#pragma unroll 1
+            for (int g = 0; g < BM / 4; g += 8) {
+                float p[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int lr = warp + 4 * (g + i);
+                    const float4 x = *reinterpret_cast<const float4*>(red + lr * RED_LD + cq);
+                    const float mu = centred ? ln_mean_s[lr] : 0.f;
+                    const float v0 = x.x + bias_s[cq] - mu, v1 = x.y + bias_s[cq + 1] - mu;
+                    const float v2 = x.z + bias_s[cq + 2] - mu, v3 = x.w + bias_s[cq + 3] - mu;
+                    const float w0 = centred ? v0 * v0 : v0, w1 = centred ? v1 * v1 : v1;
+                    const float w2 = centred ? v2 * v2 : v2, w3 = centred ? v3 * v3 : v3;
+                    p[i] = ((nvl > 0 ? w0 : 0.f) + (nvl > 1 ? w1 : 0.f)) + ((nvl > 2 ? w2 : 0.f) + (nvl > 3 ? w3 : 0.f));
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) p[i] += __shfl_xor_sync(0xffffffffu, p[i], o);
+                if (lane == 0)
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) dst[warp + 4 * (g + i)] = p[i];
+            }
+        };
+        const int lrow = warp * 32 + lane;
+        row_pass(ln_s1, false);
+        cluster_sync();
+        {
+            float tot = 0.f;
+            for (int q = 0; q < tiles_n; ++q) tot += *map_rank(ln_s1 + lrow, q);
+            ln_mean_s[lrow] = tot / (float)pN;
+        }
+        __syncthreads();
+        row_pass(ln_s2, true);
+        cluster_sync();
+        {
+            float var = 0.f;
+            for (int q = 0; q < tiles_n; ++q) var += *map_rank(ln_s2 + lrow, q);
+            const float rstd = 1.0f / sqrtf(var / (float)pN + P.ln_eps);
+            ln_rstd_s[lrow] = rstd;
+            if (crank == 0 && m0 + lrow < pM) {
+                P.ln_mean[m0 + lrow] = ln_mean_s[lrow];
+                P.ln_rstd[m0 + lrow] = rstd;
+            }
+        }
+    }
     cluster_sync();
     // part 2: CTA `split` of the cluster finishes rows [split BM / S, (split + 1) BM / S),
     // adding the S partial tiles in rank order.  Warp w takes rows rb0 + w, rb0 + w + 4, ...,
@@ -355,7 +429,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                 }
             }
             if (q < S) {
-                const float* s0 = map_rank(mine, q) + (size_t)g0 * 4 * RED_LD;
+                // (LayerNorm mode: one partial, this CTA's own, at its rank in the row cluster)
+                const float* s0 = map_rank(mine, gb.ln ? crank : q) + (size_t)g0 * 4 * RED_LD;
                 float4 x0[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
@@ -456,6 +531,44 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                         }
                 }
             }
+            if (gb.ln) {
+                // y = (x - mean) rstd g + beta, ReLU: FP32 and BF16 rows of the LayerNorm output
+                float g4[4], b4[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) { g4[j] = g_s[cq + j]; b4[j] = beta_s[cq + j]; }
+                const bool pvec = nv == 4 && (pN % 4) == 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (i < rows_ok) {
+                        const int lr = rb0 + warp + 4 * (g0 + i);
+                        const float mean = ln_mean_s[lr], rstd = ln_rstd_s[lr];
+                        float y[4] = {acc[i].x, acc[i].y, acc[i].z, acc[i].w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            y[j] = (y[j] - mean) * rstd * g4[j] + b4[j];
+                            if (P.ln_relu) y[j] = fmaxf(y[j], 0.f);
+                        }
+                        const int64_t off = (int64_t)(row0 + 4 * i) * pN + col;
+                        if (pvec) {
+                            *reinterpret_cast<float4*>(P.ln_post + off) = make_float4(y[0], y[1], y[2], y[3]);
+                            if (P.ln_posth) {
+                                __nv_bfloat162 lo = __floats2bfloat162_rn(y[0], y[1]);
+                                __nv_bfloat162 hi = __floats2bfloat162_rn(y[2], y[3]);
+                                uint2 u;
+                                u.x = *reinterpret_cast<uint32_t*>(&lo);
+                                u.y = *reinterpret_cast<uint32_t*>(&hi);
+                                *reinterpret_cast<uint2*>(P.ln_posth + off) = u;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 4; ++j)
+                                if (j < nv) {
+                                    P.ln_post[off + j] = y[j];
+                                    if (P.ln_posth) P.ln_posth[off + j] = __float2bfloat16_rn(y[j]);
+                                }
+                        }
+                    }
+            }
         }
     }
     // no CTA of the cluster leaves while another may still read its shared memory
@@ -525,6 +638,8 @@ namespace {
 int g_max_splits = 1;   // largest cluster the device can co-schedule for the GEMM kernel
 }
 
+int tc_max_cluster() { return g_max_splits; }
+
 void tc_prepare() {
     set_smem_attr<false, false>();
     set_smem_attr<false, true>();
@@ -564,11 +679,16 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, b
         int tiles = 0, min_iters = 1 << 30;
         bool a_mn = probs[base].a[0].mn_major, b_mn = probs[base].b[0].mn_major;
         const bool f8 = probs[base].fp8 != 0;
+        const bool ln = probs[base].ln_g != nullptr;
         for (int i = 0; i < gb.n; ++i) {
             const TcGemm& g = probs[base + i];
             TcProb& p = gb.p[i];
             if (g.a[0].mn_major != a_mn || g.b[0].mn_major != b_mn || g.n_pairs < 1 || g.n_pairs > 2) return -1;
             if ((g.fp8 != 0) != f8 || (f8 && (g.n_pairs != 1 || a_mn || b_mn || !g.scale_a || !g.scale_b))) return -1;
+            if ((g.ln_g != nullptr) != ln ||
+                (ln && (!g.ln_beta || !g.ln_post || !g.ln_mean || !g.ln_rstd || g.cbf || g.mask || g.accumulate ||
+                        (g.N + BN - 1) / BN > g_max_splits || (g.N + BN - 1) / BN != (probs[base].N + BN - 1) / BN)))
+                return -3;
             for (int q = 0; q < g.n_pairs; ++q) {
                 if (!operand_map(&p.ta[q], g.a[q], g.M, g.K, f8)) return -2;
                 if (!operand_map(&p.tb[q], g.b[q], g.N, g.K, f8)) return -2;
@@ -577,6 +697,8 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, b
             p.bias = g.bias; p.c = g.c; p.ldc = g.ldc; p.cbf = g.cbf; p.ldcbf = g.ldcbf;
             p.mask = g.mask; p.ldmask = g.ldmask; p.accumulate = g.accumulate;
             p.scale_a = g.scale_a; p.scale_b = g.scale_b;
+            p.ln_g = g.ln_g; p.ln_beta = g.ln_beta; p.ln_post = g.ln_post; p.ln_posth = g.ln_posth;
+            p.ln_mean = g.ln_mean; p.ln_rstd = g.ln_rstd; p.ln_eps = g.ln_eps; p.ln_relu = g.ln_relu;
             p.tiles_n = (g.N + BN - 1) / BN;
             p.tile_start = tiles;   // in tiles for now, scaled by the split below
             tiles += ((g.M + BM - 1) / BM) * p.tiles_n;
@@ -585,10 +707,12 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, b
         }
         if (!tiles) continue;
         int S = std::min(std::min(g_max_splits, std::max(1, kSplitTarget / tiles)), min_iters / kMinSplitIters);
-        S = allow_split ? std::max(S, 1) : 1;
+        S = allow_split && !ln ? std::max(S, 1) : 1;
         gb.splits = S;
+        gb.ln = ln ? 1 : 0;
         for (int i = 0; i < gb.n; ++i) gb.p[i].tile_start *= S;
-        const dim3 grid(tiles * S), cluster(S);
+        // LayerNorm mode: one cluster per row block, its CTAs the block's column tiles
+        const dim3 grid(tiles * S), cluster(ln ? gb.p[0].tiles_n : S);
         if (f8) launch_kc(tc_gemm_kernel<false, false, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
         else if (!a_mn && !b_mn) launch_kc(tc_gemm_kernel<false, false>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
         else if (!a_mn && b_mn) launch_kc(tc_gemm_kernel<false, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);

@@ -29,7 +29,19 @@ struct TcGemm {
     // scaled back by *scale_a * *scale_b before the bias (device scalars)
     int fp8;
     const float* scale_a; const float* scale_b;
+    // LayerNorm of each output row fused into the epilogue (ln_g non-null): c receives
+    // D + bias (the pre-activation), then y = (D - mean) rstd g + beta, ReLU if ln_relu,
+    // goes to ln_post (FP32, row stride N) and ln_posth (BF16, row stride N), with the
+    // row statistics in ln_mean / ln_rstd.  The N columns of a row block form one
+    // cluster whose CTAs exchange row sums through distributed shared memory; needs
+    // N <= 128 x tc_max_cluster(), no K split, and cbf == nullptr.
+    const float* ln_g; const float* ln_beta;
+    float* ln_post; __nv_bfloat16* ln_posth;
+    float* ln_mean; float* ln_rstd;
+    float ln_eps; int ln_relu;
 };
+// Largest cluster the GEMM kernel can be launched with on this device (after tc_prepare).
+int tc_max_cluster();
 
 // Per-tensor e4m3 quantisation of BF16 rows (current scaling): scale = amax / 448,
 // dst = e4m3(x / scale) rounded to nearest, pad columns zero, *scale written.

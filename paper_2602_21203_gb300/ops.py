@@ -51,6 +51,25 @@ def gemm(A, B, bias=None, out=None, accumulate=False, M=None, N=None, K=None):
     return out
 
 
+def gemm_layernorm(A, B, bias, g, beta, eps=1e-5, relu=True):
+    """BF16 A [M, K] B [N, K]^T + bias, then LayerNorm (+ReLU) per row in the same kernel.
+    Returns (pre, post, post_bf16, mean, rstd)."""
+    _need(A, torch.bfloat16, "A")
+    _need(B, torch.bfloat16, "B")
+    M, K = A.shape
+    N = B.shape[0]
+    dev = A.device
+    pre = torch.empty(M, N, device=dev)
+    post = torch.empty(M, N, device=dev)
+    post_bf = torch.empty(M, N, device=dev, dtype=torch.bfloat16)
+    mean = torch.empty(M, device=dev)
+    rstd = torch.empty(M, device=dev)
+    _chk(_lib.load().squint_op_gemm_layernorm(M, N, K, _p(A), A.stride(0), _p(B), B.stride(0), _p(bias), _p(g),
+                                              _p(beta), float(eps), int(relu), _p(pre), _p(post), _p(post_bf),
+                                              _p(mean), _p(rstd), _s()), "squint_op_gemm_layernorm")
+    return pre, post, post_bf, mean, rstd
+
+
 def gemm_fp8(A, B, bias=None, out=None):
     """out = scale_A scale_B e4m3(A / scale_A) e4m3(B / scale_B)^T + bias for BF16 A [M, K], B [N, K]
     (row-major, unit column stride); per-tensor scales amax / 448.  Returns (out, (scale_A, scale_B))."""

@@ -100,6 +100,37 @@ def test_bf16_gemm_k_split_over_cluster(ops, a_mn, b_mn, shape):
     assert _rel(acc.cpu().numpy(), ref2) < 1e-5
 
 
+LN_SHAPES = [(512, 512, 512), (300, 256, 274), (37, 300, 64), (1, 16, 8), (1030, 1024, 128)]
+
+
+@pytest.mark.parametrize("shape", LN_SHAPES)
+@pytest.mark.parametrize("relu", [True, False])
+def test_gemm_with_fused_layernorm(ops, shape, relu):
+    """GEMM + LayerNorm (+ReLU) in one kernel vs the FP64 GEMM of the same BF16 operands
+    followed by the oracle's LayerNorm."""
+    M, N, K = shape
+    g = torch.Generator().manual_seed(M + N + K)
+    a, A = _operand(M, K, False, g)             # row strides padded to multiples of 8
+    b = (torch.randn(N, K, generator=g) * 0.1).bfloat16()
+    buf = torch.zeros(N, (K + 7) // 8 * 8, dtype=torch.bfloat16)
+    buf[:, :K] = b
+    B = buf.cuda()[:, :K]
+    bias = torch.randn(N, generator=g)
+    gam = torch.rand(N, generator=g) + 0.5
+    bet = torch.randn(N, generator=g) * 0.2
+    pre, post, post_bf, mean, rstd = ops.gemm_layernorm(A, B, bias.cuda(), gam.cuda(), bet.cuda(), 1e-5, relu)
+    torch.cuda.synchronize()
+    ref_pre = a.double().numpy() @ b.double().numpy().T + bias.double().numpy()
+    ref, (xhat, rs) = o.layernorm_fwd(ref_pre, gam.double().numpy(), bet.double().numpy(), 1e-5)
+    if relu:
+        ref = np.maximum(ref, 0)
+    assert _rel(pre.cpu().numpy(), ref_pre) < 1e-5
+    assert _rel(post.cpu().numpy(), ref) < 1e-4
+    assert _rel(rstd.cpu().numpy(), rs.ravel()) < 1e-4
+    assert _rel(mean.cpu().numpy(), ref_pre.mean(1)) < 1e-4 or np.abs(mean.cpu().numpy() - ref_pre.mean(1)).max() < 1e-4
+    assert torch.equal(post_bf.cpu(), post.cpu().bfloat16())
+
+
 FP8_SHAPES = [(512, 512, 512), (512, 256, 2592), (300, 101, 274), (7, 16, 64), (1, 1, 8), (1024, 12, 272)]
 
 
