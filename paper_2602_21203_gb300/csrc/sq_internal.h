@@ -76,6 +76,10 @@ struct squint_handle {
     // SQUINT_FUSED_LN=1 in the environment at creation; off by default: at batch 512 the
     // separate LayerNorm kernel gives more updates/s (1,310 vs 1,264 on the same GPU)
     bool fuse_ln = false;
+    // K split over clusters in the update's GEMMs, chosen by SQUINT_GEMM_SPLIT=1; off by
+    // default: inside the concurrent update graph it gave 1,307 updates/s against 1,321
+    // without (clusters wait for co-scheduled SMs while the side streams hold some)
+    bool gemm_split = false;
     bool launch_failed = false;       // a tensor map could not describe an operand
     int device = 0;
     int* d_err = nullptr;             // device error word of bounded waits

@@ -152,7 +152,7 @@ void GemmBuilder::flush() {
         ProfScope ps(h_, s_, kind_, flops_, 0);
         if (!fp_.empty()) launch_gemm<float>(fp_.data(), (int)fp_.size(), lay_, s_);
         for (auto* v : {&tc8_, &tc8ln_, &tc_, &tcln_})
-            if (!v->empty() && launch_tc_gemm(v->data(), (int)v->size(), h_->d_err, s_, split_) != 0)
+            if (!v->empty() && launch_tc_gemm(v->data(), (int)v->size(), h_->d_err, s_, split_ && h_->gemm_split) != 0)
                 h_->launch_failed = true;
     }
     fp_.clear();
@@ -362,6 +362,7 @@ int squint_handle::allocate() {
     const int B = c.batch, A = c.action_dim, K = c.atoms, E = 2;
     fp8 = c.precision == SQUINT_PREC_FP8;
     if (const char* e = std::getenv("SQUINT_FUSED_LN")) fuse_ln = std::atoi(e) != 0;
+    if (const char* e = std::getenv("SQUINT_GEMM_SPLIT")) gemm_split = std::atoi(e) != 0;
     bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
     SQ_CK(this, cudaGetDevice(&device));
     const int64_t n = L.total;
