@@ -188,6 +188,17 @@ def shift_squint_sums(img, dx, dy, pad, f):
     return shifted.reshape(bsz, c, hs, f, ws, f).sum(axis=(3, 5))
 
 
+def squint_store(img, f):
+    """Squint at insert (Alg. 1: the transition is stored with Downsample(o); Sec. IV
+    "Resolution Squinting", area downsampling): the f x f area mean of a uint8 frame,
+    rounded half up to uint8, q = floor((S + floor(f^2 / 2)) / f^2), S the integer box sum.
+    The update then reads q with f = 1: x = q / 255 - 0.5."""
+    n, c, h, w = img.shape
+    hs, ws = h // f, w // f
+    s = img[:, :, :hs * f, :ws * f].astype(np.int64).reshape(n, c, hs, f, ws, f).sum(axis=(3, 5))
+    return ((s + (f * f) // 2) // (f * f)).astype(np.uint8)
+
+
 def squint_values(sums, f):
     """Pixel values from box sums: mean intensity in [0,1], centred: S/(255 f^2) - 0.5."""
     return sums.astype(np.float64) / (255.0 * f * f) - 0.5

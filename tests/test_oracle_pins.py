@@ -543,3 +543,39 @@ def test_act_is_row_independent_and_mean_mode_is_tanh_mu():
     assert np.allclose(full[:3], part, atol=1e-14)
     mean = o.act(P, obs, prop, 1234, False, cfg)
     assert np.all(np.abs(mean) < 1) and not np.allclose(mean, full)
+
+
+# ---------------------------------------------------------------- squint at insert
+def test_squint_store_brute_force_and_rounding():
+    rng = np.random.default_rng(11)
+    img = rng.integers(0, 256, size=(3, 2, 12, 8), dtype=np.uint8)
+    f = 4
+    q = o.squint_store(img, f)
+    assert q.dtype == np.uint8 and q.shape == (3, 2, 3, 2)
+    for n in range(3):
+        for c in range(2):
+            for i in range(3):
+                for j in range(2):
+                    s_ = int(img[n, c, i * f:(i + 1) * f, j * f:(j + 1) * f].astype(np.int64).sum())
+                    mean = s_ / (f * f)
+                    want = int(np.floor(mean + 0.5))          # round half up
+                    assert q[n, c, i, j] == want
+                    assert abs(q[n, c, i, j] / 255.0 - mean / 255.0) <= 0.5 / 255 + 1e-15
+
+
+def test_squint_store_special_cases():
+    # constant frames are unchanged; f = 1 is the identity; a half-way mean rounds up
+    const = np.full((1, 3, 16, 16), 77, dtype=np.uint8)
+    assert (o.squint_store(const, 4) == 77).all()
+    rng = np.random.default_rng(12)
+    img = rng.integers(0, 256, size=(2, 3, 5, 7), dtype=np.uint8)
+    assert np.array_equal(o.squint_store(img, 1), img)
+    half = np.zeros((1, 1, 2, 2), dtype=np.uint8)
+    half[0, 0, 0, :] = 1                        # sum 2 over 4 pixels: mean 0.5 -> 1
+    assert o.squint_store(half, 2)[0, 0, 0, 0] == 1
+    # the stored value is within half a level of the update's unrounded squint value
+    img = rng.integers(0, 256, size=(4, 3, 32, 32), dtype=np.uint8)
+    sums = o.shift_squint_sums(img, np.full(4, 0), np.full(4, 0), 0, 4)
+    x_unrounded = o.squint_values(sums, 4)
+    x_stored = o.squint_store(img, 4).astype(np.float64) / 255.0 - 0.5
+    assert np.abs(x_unrounded - x_stored).max() <= 0.5 / 255 + 1e-12
