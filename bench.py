@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--workload", choices=["train_b512", "stored_b512"], default=WORKLOAD,
+                    help="stored_b512: squint at insert, a 1M-slot ring of 3x32x32 frames filled by the insert kernel")
     ap.add_argument("--ring-slots", type=int, default=None,
                     help="replay-ring slots (default: the workload's 100k; smaller only for profiler captures)")
     return ap.parse_args()
@@ -250,11 +252,18 @@ def run_ours(args):
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (the learner has no CPU path)")
     peaks, peaks_src = load_peaks()
-    cfg = synth.make_config(WORKLOAD)
+    cfg = synth.make_config(args.workload)
     if args.ring_slots:
         cfg["ring_size"] = int(args.ring_slots)
+    stored = "render_f" in cfg
     prec = {"fp32": lib.PREC_FP32, "bf16": lib.PREC_BF16, "fp8": lib.PREC_FP8}[args.precision]
     ring = synth.make_ring(cfg, args.seed + rank, device="cuda")
+    if stored:   # squint at insert: the ring's frames come from 3x128x128 renders through the insert kernel
+        from paper_2602_21203_gb300 import ops
+        for c0 in range(0, cfg["ring_size"], 8192):
+            n = min(8192, cfg["ring_size"] - c0)
+            ops.squint_store(synth.render_frames(n, cfg, 1000 + c0, device="cuda"), ring["obs"], c0, cfg["render_f"])
+        torch.cuda.synchronize()
     learner = lib.Learner(cfg, ring, precision=prec, max_k=8)
     stream = torch.cuda.Stream()
     K = args.steps
@@ -289,6 +298,9 @@ def run_ours(args):
     # from pinned host memory into the ring, run the UTD-4 call, read its statistics back.
     n_new = int(UTD_K / 0.25)
     host = {k: v[:n_new].cpu().pin_memory() for k, v in ring.items()}
+    if stored:   # renders arrive at full resolution and are squinted on insert
+        host["obs"] = synth.render_frames(n_new, cfg, 7, device="cpu").pin_memory()
+        staging = torch.empty_like(host["obs"], device="cuda")
     h2d = sum(v.numel() * v.element_size() for v in host.values())
     d2h = UTD_K * 32
     head = 0
@@ -299,7 +311,11 @@ def run_ours(args):
         with torch.cuda.stream(stream):
             sl = slice(head, head + n_new)
             for k2, v in host.items():
-                ring[k2][sl].copy_(v, non_blocking=True)
+                if stored and k2 == "obs":
+                    staging.copy_(v, non_blocking=True)
+                    ops.squint_store(staging, ring["obs"], head, cfg["render_f"])
+                else:
+                    ring[k2][sl].copy_(v, non_blocking=True)
             head = (head + n_new) % (cfg["ring_size"] - n_new)
         learner.update(UTD_K, stats=True, stream=stream)          # waits and reads stats to host
     torch.cuda.synchronize()
@@ -406,12 +422,19 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3+bf16"}[args.precision], "data": "synthetic",
-            "config": {"workload": "train_b512: 100k x 3x128x128 uint8 ring (4.9 GB), batch 512, UTD 4 per step, "
-                                   "shift pad 8, squint 4x to 32x32, 4 conv x 32ch, proj 256 + LN, critics "
-                                   "512-512 x2 (101 atoms), actor 512-512",
+            "config": {"workload": (
+                           "train_b512: 100k x 3x128x128 uint8 ring (4.9 GB), batch 512, UTD 4 per step, shift pad 8, "
+                           "squint 4x to 32x32, 4 conv x 32ch, proj 256 + LN, critics 512-512 x2 (101 atoms), "
+                           "actor 512-512") if not stored else (
+                           "stored_b512: squint at insert, 1M x 3x32x32 uint8 ring (3.1 GB) filled from 3x128x128 "
+                           "renders by the insert kernel, batch 512, UTD 4 per step, shift pad 2 at 32x32, 4 conv x "
+                           "32ch, proj 256 + LN, critics 512-512 x2 (101 atoms), actor 512-512"),
                        "updates_per_step": UTD_K, "precision": args.precision,
-                       "l2": "inputs larger than L2: 4.9 GB ring, 50 MB of uniformly random frames per update; "
-                             "weights and activations stay L2-resident between updates as in training",
+                       "l2": (("inputs larger than L2: 4.9 GB ring, 50 MB of uniformly random frames per update; "
+                               "weights and activations stay L2-resident between updates as in training")
+                              if not stored else
+                              ("inputs larger than L2: 3.1 GB ring, 3.1 MB of uniformly random frames per update; "
+                               "weights and activations stay L2-resident between updates as in training")),
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,

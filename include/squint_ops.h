@@ -66,6 +66,18 @@ int squint_op_gemm_fp8(int M, int N, int K, const void* A, int64_t lda, const vo
                        int64_t ldc, const float* bias, void* work, size_t work_bytes, void* stream);
 
 /*
+ * Squint at insert (Alg. 1 stores the transition with Downsample(o); Sec. IV
+ * "Resolution Squinting": area downsampling): n uint8 frames src [n, C, H, W]
+ * (H, W multiples of f) become their f x f area means rounded half up,
+ * q = (S + f^2/2) / f^2 in integers, written to slots (slot0 + i) mod n_slots of the
+ * uint8 ring [n_slots, C, H/f, W/f].  A learner whose ring holds such frames is
+ * created with obs_h = H/f, obs_w = W/f, squint_f = 1 and the shift pad at that
+ * resolution; it then reads x = q / 255 - 0.5.  Bit-exact integer arithmetic.
+ */
+int squint_op_squint_store(int n, int C, int H, int W, int f, const void* src, void* ring, int64_t slot0,
+                           int64_t n_slots, void* stream);
+
+/*
  * Valid 3x3 convolution, NCHW (the encoder layers, Sec. III "single shared CNN
  * encoder"): y[i,o,p,q] = b[o] + sum_{c,u,v} w[o,c,u,v] x[i,c,s p+u,s q+v], ReLU if relu.
  * x [nimg, cin, h, w], w [cout, cin, 3, 3], y [nimg, cout, oh, ow], oh = (h-3)/s+1.

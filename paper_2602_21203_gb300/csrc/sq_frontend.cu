@@ -134,6 +134,36 @@ void launch_act_frontend(const ActFrontArgs& a, cudaStream_t s) {
     launch_k(act_frontend_kernel, dim3(a.rows), dim3(256), smem, s, a);
 }
 
+// Squint at insert: one thread per output value, the f x f box sum of a uint8 frame
+// rounded half up to its mean, written into ring slot (slot0 + frame) mod n_slots.
+__global__ void __launch_bounds__(256) squint_store_kernel(const uint8_t* __restrict__ src, int n, int C, int H,
+                                                          int W, int f, uint8_t* __restrict__ ring, int64_t slot0,
+                                                          int64_t n_slots) {
+    SQ_KERNEL_ENTRY();
+    const int hs = H / f, ws = W / f;
+    const int64_t per = (int64_t)C * hs * ws;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * per) return;
+    const int img = (int)(e / per);
+    const int r = (int)(e - (int64_t)img * per);
+    const int c = r / (hs * ws), i = (r / ws) % hs, j = r % ws;
+    const uint8_t* p = src + (((int64_t)img * C + c) * H + (int64_t)i * f) * W + (int64_t)j * f;
+    uint32_t sum = 0;
+    for (int u = 0; u < f; ++u)
+        for (int v = 0; v < f; ++v) sum += p[(int64_t)u * W + v];
+    const uint32_t ff = (uint32_t)(f * f);
+    const int64_t slot = (slot0 + img) % n_slots;
+    ring[slot * per + r] = (uint8_t)((sum + ff / 2) / ff);
+}
+
+void launch_squint_store(const uint8_t* src, int n, int C, int H, int W, int f, uint8_t* ring, int64_t slot0,
+                         int64_t n_slots, cudaStream_t s) {
+    const int64_t total = (int64_t)n * C * (H / f) * (W / f);
+    if (total <= 0) return;
+    launch_k(squint_store_kernel, dim3((unsigned)((total + 255) / 256)), dim3(256), 0, s, src, n, C, H, W, f, ring,
+             slot0, n_slots);
+}
+
 void frontend_prepare(size_t frame_bytes) {
     if (frame_bytes > 48 * 1024) {
         cudaFuncSetAttribute(frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);

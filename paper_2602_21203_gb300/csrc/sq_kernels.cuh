@@ -53,6 +53,10 @@ struct ActFrontArgs {
 void launch_act_frontend(const ActFrontArgs& a, cudaStream_t s);
 // Opt the front-end kernels in to `frame_bytes` of dynamic shared memory (call once, outside capture).
 void frontend_prepare(size_t frame_bytes);
+// Squint at insert: n uint8 frames [n, C, H, W] -> rounded f x f area means [C, H/f, W/f]
+// into ring slots (slot0 + i) mod n_slots of a uint8 ring [n_slots, C, H/f, W/f].
+void launch_squint_store(const uint8_t* src, int n, int C, int H, int W, int f, uint8_t* ring, int64_t slot0,
+                         int64_t n_slots, cudaStream_t s);
 
 // ---------------------------------------------------------------- dense contractions (CUDA cores)
 // C(m,n) [+]= sum_s sum_k A_s(m,k) B_s(n,k) (+ bias[n]) (* (mask(m,n) > 0)).

@@ -148,6 +148,16 @@ int squint_op_gemm_fp8(int M, int N, int K, const void* A, int64_t lda, const vo
     return launch_status();
 }
 
+int squint_op_squint_store(int n, int C, int H, int W, int f, const void* src, void* ring, int64_t slot0,
+                           int64_t n_slots, void* stream) {
+    if (n < 0 || C < 1 || f < 1 || H < f || W < f || (H % f) || (W % f) || n_slots < 1 || slot0 < 0 ||
+        (n > 0 && (!src || !ring)))
+        return SQUINT_EINVAL;
+    launch_squint_store((const uint8_t*)src, n, C, H, W, f, (uint8_t*)ring, slot0 % n_slots, n_slots,
+                        (cudaStream_t)stream);
+    return launch_status();
+}
+
 int squint_op_conv3x3_fwd(int dtype, int nimg, int cin, int h, int w, int cout, int stride, const void* x,
                           const void* wt, const void* b, void* y, int relu, void* stream) {
     if (!conv_ok(nimg, cin, h, w, cout, stride) || !x || !wt || !b || !y) return SQUINT_EINVAL;

@@ -51,6 +51,17 @@ def gemm(A, B, bias=None, out=None, accumulate=False, M=None, N=None, K=None):
     return out
 
 
+def squint_store(frames, ring_obs, slot0, f):
+    """Squint at insert: uint8 frames [n, C, H, W] -> rounded f x f means into ring_obs
+    [n_slots, C, H/f, W/f] at slots slot0, slot0 + 1, ... (mod n_slots)."""
+    _need(frames, torch.uint8, "frames")
+    _need(ring_obs, torch.uint8, "ring_obs")
+    n, c, h, w = frames.shape
+    frames = frames.contiguous()
+    _chk(_lib.load().squint_op_squint_store(n, c, h, w, int(f), _p(frames), _p(ring_obs), int(slot0),
+                                            ring_obs.shape[0], _s()), "squint_op_squint_store")
+
+
 def gemm_layernorm(A, B, bias, g, beta, eps=1e-5, relu=True):
     """BF16 A [M, K] B [N, K]^T + bias, then LayerNorm (+ReLU) per row in the same kernel.
     Returns (pre, post, post_bf16, mean, rstd)."""

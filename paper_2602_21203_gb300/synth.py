@@ -32,6 +32,13 @@ PRESETS = {
     "train_b512": dict(ring_size=100_000, obs_h=128, obs_w=128, squint_f=4, shift_pad=8, batch=512,
                        conv_layers=4, conv_ch=32, proj_dim=256, hidden=[512, 512],
                        atoms=101, v_min=-20.0, v_max=20.0, utd=4),
+    # Squint at insert (the paper's replay layout, Alg. 1): 1M slots of squinted
+    # 3x32x32 uint8 frames (3 GB), filled by squint_op_squint_store from 3x128x128
+    # renders, read with f = 1 and the shift at 32x32 (pad 2 = 8 / 4); same networks as
+    # train_b512.
+    "stored_b512": dict(ring_size=1_000_000, obs_h=32, obs_w=32, squint_f=1, shift_pad=2, batch=512,
+                        conv_layers=4, conv_ch=32, proj_dim=256, hidden=[512, 512],
+                        atoms=101, v_min=-20.0, v_max=20.0, utd=4, render_h=128, render_w=128, render_f=4),
     # Tiny net for finite differences: 3x64x64 ring squinted to 3x16x16, 8 channels,
     # MLPs 32-32, 11 atoms on [-10, 10] (atom spacing exactly 2), batch 8.
     "tiny_b8": dict(ring_size=64, obs_h=64, obs_w=64, squint_f=4, shift_pad=4, batch=8,
@@ -59,6 +66,14 @@ def make_ring(cfg, seed=0, device="cpu"):
     reward = torch.randn(n, generator=g, device=device)
     done = (torch.rand(n, generator=g, device=device) < 0.02).to(torch.uint8)
     return dict(obs=obs, proprio=proprio, action=action, reward=reward, done=done)
+
+
+def render_frames(n, cfg, seed, device="cpu"):
+    """Seeded uint8 renders [n, C, render_h, render_w] for a squint-at-insert workload."""
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return torch.randint(0, 256, (n, cfg["obs_c"], cfg["render_h"], cfg["render_w"]), dtype=torch.uint8,
+                         generator=g, device=device)
 
 
 def ring_numpy(ring):
