@@ -97,11 +97,21 @@ def param_spec(cfg):
 
     spec += proj("critic")
     for i in range(cfg["n_critics"]):
-        spec += mlp(f"critic{i}", dm["critic_in"], cfg["atoms"])
+        spec += mlp(f"critic{i}", dm["critic_in"], critic_out(cfg))
     spec += proj("actor")
     spec += mlp("actor", dm["actor_in"], 2 * cfg["action_dim"])
     spec.append(("log_alpha", (1,), "LOGALPHA", 0))
     return spec
+
+
+def critic_kind(cfg):
+    """'c51' (categorical critic, Sec. IV "Critic Design Choices") or 'mse' (scalar Q, Eq. 2)."""
+    return cfg.get("critic", "c51")
+
+
+def critic_out(cfg):
+    """Width of a critic's output layer: the atoms, or one value for the MSE critic."""
+    return 1 if critic_kind(cfg) == "mse" else cfg["atoms"]
 
 
 def group_of(name):
@@ -442,8 +452,22 @@ def project_c51(pbar, r, d, logp, alpha, cfg):
 
 
 def q_values(logits, cfg):
-    """Q_i = sum_j softmax(logits_i)_j z_j: mean of the categorical return distribution."""
+    """Q_i = sum_j softmax(logits_i)_j z_j: mean of the categorical return distribution
+    (the MSE critic's output is Q itself)."""
+    if critic_kind(cfg) == "mse":
+        return logits[..., 0]
     return (softmax(logits) * support(cfg)).sum(-1)
+
+
+def combine_critics(q, cfg):
+    """How the two critics' values combine (Sec. IV "Critic Design Choices"): their average
+    (Squint's choice), or with clipped double Q (cfg "cdq") the smaller per sample, ties to
+    critic 0.  Returns the combined value [B] and the index of the critic used [B] (or None
+    for the average)."""
+    if cfg.get("cdq", False):
+        pick = np.argmin(q, axis=0)
+        return q[pick, np.arange(q.shape[1])], pick
+    return q.mean(0), None
 
 
 # --------------------------------------------------------------------------
@@ -454,13 +478,27 @@ def target_distribution(P, T, z_t1, fe, alpha, eps, cfg):
     """Alg. 1 "Compute target Q-value" in distributional form (no gradient).
 
     a' ~ pi(.|z_{t+1}, s'), target critics on [h_bar(z_{t+1}), s', a'], the two
-    categorical distributions averaged (average, not clipped double Q: Sec. IV),
-    then projected with the soft term alpha log pi'.
+    categorical distributions averaged (Squint: average, not clipped double Q, Sec. IV),
+    then projected with the soft term alpha log pi'.  Variants: with "cdq" the
+    distribution of the target critic with the smaller mean is used per sample; the MSE
+    critic (Eq. 1-2) returns the scalar TD target y as m[:, 0].
     """
     a1, logp1, _ = actor_fwd(P, z_t1, fe["p_t1"], eps, cfg)
     hbar, _ = proj_fwd(T, "critic", z_t1, cfg)
     logits_bar, _ = critics_fwd(T, hbar, fe["p_t1"], a1, cfg)
-    pbar = softmax(logits_bar).mean(0)
+    if critic_kind(cfg) == "mse":
+        # Eq. 1: y = r + gamma (1 - d) (Q_bar(s', a') - alpha log pi'), Q_bar combined over critics
+        qbar, _ = combine_critics(logits_bar[..., 0], cfg)
+        y = fe["r"] + cfg["gamma"] * (1.0 - fe["d"]) * (qbar - alpha * logp1)
+        return dict(a_next=a1, logp_next=logp1, logits_target=logits_bar, m=y[:, None])
+    probs = softmax(logits_bar)
+    if cfg.get("cdq", False):
+        # clipped double Q on distributions: per sample, the distribution of the target critic
+        # whose mean is smaller
+        _, pick = combine_critics(q_values(logits_bar, cfg), cfg)
+        pbar = probs[pick, np.arange(probs.shape[1])]
+    else:
+        pbar = probs.mean(0)
     m = project_c51(pbar, fe["r"], fe["d"], logp1, alpha, cfg)
     return dict(a_next=a1, logp_next=logp1, logits_target=logits_bar, pbar=pbar, m=m)
 
@@ -471,12 +509,21 @@ def critic_loss(P, x_t, fe, m, cfg, with_grads=True):
     z, enc_cache = encoder_fwd(P, x_t, cfg)
     hc, pcache = proj_fwd(P, "critic", z, cfg)
     logits, caches = critics_fwd(P, hc, fe["p_t"], fe["a_t"], cfg)
-    lsm = log_softmax(logits)
-    loss = float(-(m[None] * lsm).sum(-1).mean(1).sum())
-    out = dict(loss=loss, logits=logits, z=z, q=q_values(logits, cfg))
-    if not with_grads:
-        return out
-    dlogits = (np.exp(lsm) - m[None]) / B            # d CE / d logits = softmax - m (sum_j m_j = 1)
+    if critic_kind(cfg) == "mse":
+        # Eq. 2: sum over critics of mean_b (Q_i - y)^2, y = m[:, 0] held fixed
+        err = logits[..., 0] - m[None, :, 0]
+        loss = float((err ** 2).mean(1).sum())
+        out = dict(loss=loss, logits=logits, z=z, q=q_values(logits, cfg))
+        if not with_grads:
+            return out
+        dlogits = (2.0 * err / B)[..., None]
+    else:
+        lsm = log_softmax(logits)
+        loss = float(-(m[None] * lsm).sum(-1).mean(1).sum())
+        out = dict(loss=loss, logits=logits, z=z, q=q_values(logits, cfg))
+        if not with_grads:
+            return out
+        dlogits = (np.exp(lsm) - m[None]) / B            # d CE / d logits = softmax - m (sum_j m_j = 1)
     grads = {}
     zdim = hc.shape[1]
     dhc = np.zeros_like(hc)
@@ -496,7 +543,8 @@ def critic_loss(P, x_t, fe, m, cfg, with_grads=True):
 
 
 def actor_loss(P, z_sg, prop, eps, alpha, cfg, with_grads=True):
-    """L_pi = mean_b [ alpha log pi(a~|z_sg,s) - (1/2) sum_i Q_i(z_sg, s, a~) ]  (Eq. 3, Alg. 1 "Update actor").
+    """L_pi = mean_b [ alpha log pi(a~|z_sg,s) - (1/2) sum_i Q_i(z_sg, s, a~) ]  (Eq. 3, Alg. 1 "Update actor");
+    with "cdq" the smaller of the two Q_i per sample instead of their average.
 
     z_sg is the stop-gradient encoder output; the critics (incl. their projection)
     are held fixed; gradients reach the actor projection and actor MLP only.
@@ -506,18 +554,23 @@ def actor_loss(P, z_sg, prop, eps, alpha, cfg, with_grads=True):
     a, logp, acache = actor_fwd(P, z_sg, prop, eps, cfg)
     hc, _ = proj_fwd(P, "critic", z_sg, cfg)
     logits, caches = critics_fwd(P, hc, prop, a, cfg)
-    prob = softmax(logits)
-    zj = support(cfg)
-    q = (prob * zj).sum(-1)                               # [E, B]
-    loss = float((alpha * logp - q.mean(0)).mean())
+    q = q_values(logits, cfg)                             # [E, B]
+    qc, pick = combine_critics(q, cfg)
+    loss = float((alpha * logp - qc).mean())
     out = dict(loss=loss, a=a, logp=logp, q=q)
     if not with_grads:
         return out
     A = cfg["action_dim"]
     da = np.zeros_like(a)
     for i in range(E):
-        dq = -1.0 / (E * B)
-        dlogit = dq * prob[i] * (zj[None, :] - q[i][:, None])   # dQ/dlogit_j = p_j (z_j - Q)
+        # d(-mean_b Qc)/dQ_i: -1/(E B) for the average, -1/B where critic i is the minimum
+        dq = np.full(B, -1.0 / (E * B)) if pick is None else np.where(pick == i, -1.0 / B, 0.0)
+        if critic_kind(cfg) == "mse":
+            dlogit = dq[:, None]
+        else:
+            prob = softmax(logits[i])
+            zj = support(cfg)
+            dlogit = dq[:, None] * prob * (zj[None, :] - q[i][:, None])   # dQ/dlogit_j = p_j (z_j - Q)
         dx, _ = mlp_bwd(P, f"critic{i}", caches[i], dlogit, cfg, need_param_grads=False)
         da += dx[:, -A:]
     pc, mc, hcache, _ = acache

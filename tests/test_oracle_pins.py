@@ -579,3 +579,76 @@ def test_squint_store_special_cases():
     x_unrounded = o.squint_values(sums, 4)
     x_stored = o.squint_store(img, 4).astype(np.float64) / 255.0 - 0.5
     assert np.abs(x_unrounded - x_stored).max() <= 0.5 / 255 + 1e-12
+
+
+# ---------------------------------------------------------------- critic variants (Sec. IV, Eq. 1-2)
+VARIANTS = [dict(critic="mse"), dict(cdq=True), dict(critic="mse", cdq=True)]
+
+
+def _variant_setup(seed, **kw):
+    cfg = _cfg_tiny(**kw)
+    ring = synth.ring_numpy(synth.make_ring(cfg, seed))
+    st = o.init_state(cfg)
+    return cfg, st, o.frontend(cfg, ring, 0)
+
+
+@pytest.mark.parametrize("var", VARIANTS)
+def test_variant_critic_and_actor_gradients_finite_differences(var):
+    cfg, st, fe = _variant_setup(4, **var)
+    P = st["params"]
+    z1, _ = o.encoder_fwd(P, fe["x_t1"], cfg)
+    eps = px.normal_pairs(cfg["seed"], px.STREAM_EPS_TARGET, 0, cfg["batch"], 6)
+    m = o.target_distribution(P, st["target"], z1, fe, 0.1, eps, cfg)["m"]
+    res = o.critic_loss(P, fe["x_t"], fe, m, cfg)
+    f = lambda: o.critic_loss(P, fe["x_t"], fe, m, cfg, with_grads=False)["loss"]
+    rng = np.random.default_rng(5)
+    for name, g in res["grads"].items():
+        assert not _check_tensor_fd(f, P[name], g, rng=rng), (var, name)
+    z, _ = o.encoder_fwd(P, fe["x_t"], cfg)
+    epa = px.normal_pairs(cfg["seed"], px.STREAM_EPS_ACTOR, 0, cfg["batch"], 6)
+    ra = o.actor_loss(P, z, fe["p_t"], epa, 0.3, cfg)
+    fa = lambda: o.actor_loss(P, z, fe["p_t"], epa, 0.3, cfg, with_grads=False)["loss"]
+    for name, g in ra["grads"].items():
+        assert not _check_tensor_fd(fa, P[name], g, rng=rng), (var, name)
+
+
+def test_mse_critic_shapes_target_and_loss():
+    cfg, st, fe = _variant_setup(6, critic="mse")
+    P = st["params"]
+    assert P["critic0.fc2.w"].shape == (1, 32)
+    z1, _ = o.encoder_fwd(P, fe["x_t1"], cfg)
+    eps = px.normal_pairs(cfg["seed"], px.STREAM_EPS_TARGET, 0, cfg["batch"], 6)
+    tgt = o.target_distribution(P, st["target"], z1, fe, 0.25, eps, cfg)
+    # Eq. 1 written out: average of the two target critics' Q, soft term on log pi'
+    qbar = tgt["logits_target"][..., 0].mean(0)
+    y = fe["r"] + cfg["gamma"] * (1 - fe["d"]) * (qbar - 0.25 * tgt["logp_next"])
+    assert np.allclose(tgt["m"][:, 0], y, rtol=0, atol=1e-12)
+    # gamma = 0: the target is the reward; a critic output equal to y has zero loss
+    cfg0 = dict(cfg, gamma=0.0)
+    y0 = o.target_distribution(P, st["target"], z1, fe, 0.25, eps, cfg0)["m"]
+    assert np.array_equal(y0[:, 0], fe["r"])
+    res = o.critic_loss(P, fe["x_t"], fe, y0, cfg0, with_grads=False)
+    q = res["logits"][..., 0]
+    assert res["loss"] == pytest.approx(float(((q - fe["r"][None]) ** 2).mean(1).sum()), rel=1e-12)
+
+
+def test_clipped_double_q_selects_the_smaller_critic():
+    cfg, st, fe = _variant_setup(7, cdq=True)
+    P, T = st["params"], st["target"]
+    z1, _ = o.encoder_fwd(P, fe["x_t1"], cfg)
+    eps = px.normal_pairs(cfg["seed"], px.STREAM_EPS_TARGET, 0, cfg["batch"], 6)
+    # identical target critics: clipped double Q equals the average exactly
+    T2 = {k: v.copy() for k, v in T.items()}
+    for k in list(T2):
+        if k.startswith("critic1."):
+            T2[k] = T2["critic0." + k[len("critic1."):]].copy()
+    a = o.target_distribution(P, T2, z1, fe, 0.1, eps, cfg)["m"]
+    b = o.target_distribution(P, T2, z1, fe, 0.1, eps, dict(cfg, cdq=False))["m"]
+    assert np.allclose(a, b, rtol=0, atol=1e-15)
+    # otherwise each sample takes the distribution of the critic with the smaller mean
+    tgt = o.target_distribution(P, T, z1, fe, 0.1, eps, cfg)
+    q = o.q_values(tgt["logits_target"], cfg)
+    lo = np.argmin(q, axis=0)
+    want = o.softmax(tgt["logits_target"])[lo, np.arange(q.shape[1])]
+    assert np.allclose(tgt["pbar"], want, rtol=0, atol=1e-15)
+    assert (q.min(0) <= q.mean(0) + 1e-15).all()
