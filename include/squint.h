@@ -75,6 +75,10 @@ typedef struct {
     int32_t policy_freq;             /* actor step when (update_idx + 1) % policy_freq == 0 */
     int32_t precision;               /* SQUINT_PREC_* */
     int32_t max_k;                   /* largest k accepted by squint_update */
+    int32_t critic_kind;             /* 0: categorical C51 critic (Squint); 1: MSE critic with
+                                        a scalar output (Eq. 2) */
+    int32_t cdq;                     /* 0: average of the two critics (Squint); 1: clipped double
+                                        Q, the smaller per sample, in the target and the actor */
     int32_t recompute_chunk;         /* 0: keep encoder activations; n > 0: BF16 tensor-core
                                         encoder only: run it in chunks of n images (rounded up
                                         to the weight gradient's images per CTA), keep only the
@@ -101,7 +105,7 @@ typedef struct {
 /* Per-update diagnostics (one entry per update of a call). */
 typedef struct {
     float critic_loss;   /* sum over critics of the batch-mean cross entropy */
-    float actor_loss;    /* mean(alpha log pi - mean_i Q_i); NaN when the actor did not step */
+    float actor_loss;    /* mean(alpha log pi - mean_i Q_i) (min_i with cdq); NaN when the actor did not step */
     float alpha_loss;    /* -alpha * mean(log pi + target_entropy) */
     float alpha;         /* temperature after the step */
     float q_mean;        /* mean over critics and batch of the online Q(s_t, a_t) */

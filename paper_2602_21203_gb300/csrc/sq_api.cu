@@ -38,6 +38,7 @@ bool build_layout(const squint_config& c, Layout& L) {
     if (c.conv_layers < 1 || c.conv_layers > SQUINT_MAX_CONV || c.conv_ch < 1) return false;
     if (c.n_hidden < 1 || c.n_hidden > SQUINT_MAX_HIDDEN || c.n_critics != 2) return false;
     if (c.atoms < 2 || c.atoms > 256 || c.action_dim < 1 || c.proprio_dim < 0 || c.proj_dim < 0) return false;
+    if (c.critic_kind < 0 || c.critic_kind > 1 || c.cdq < 0 || c.cdq > 1) return false;
     if (c.batch < 1 || c.policy_freq < 1 || c.shift_pad < 0) return false;
     if (!(c.v_max > c.v_min)) return false;
     L = Layout{};
@@ -68,7 +69,7 @@ bool build_layout(const squint_config& c, Layout& L) {
         int in = L.dc;
         L.critic[e].resize(c.n_hidden + 1);
         for (int l = 0; l < c.n_hidden; ++l) { off = add_lin(L, off, L.critic[e][l], in, c.hidden[l], true); in = c.hidden[l]; }
-        off = add_lin(L, off, L.critic[e][c.n_hidden], in, c.atoms, false);
+        off = add_lin(L, off, L.critic[e][c.n_hidden], in, c.critic_kind == 1 ? 1 : c.atoms, false);
     }
     L.critic_end = off;
     L.actor_begin = off;

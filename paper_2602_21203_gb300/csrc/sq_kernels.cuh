@@ -169,7 +169,9 @@ struct C51TargetArgs {
     const float* log_alpha;    // alpha = exp(*log_alpha); null: alpha_value
     float alpha_value;
     float gamma, v_min, v_max;
-    float* m;                  // [B, K]
+    float* m;                  // [B, K]; MSE critic (K = 1): the TD target y
+    int cdq;                   // clipped double Q: per sample the target critic with the smaller mean
+    int mse;                   // scalar critics (Eq. 1): y = r + gamma (1-d)(Q_bar - alpha log pi')
 };
 void launch_c51_target(const C51TargetArgs& a, cudaStream_t s);
 
@@ -183,6 +185,7 @@ struct CeArgs {
     __nv_bfloat16* dlogits_bf; int64_t ld_bf;   // optional BF16 copy [E, B, ld_bf]
     float* row_loss;           // [E*B]
     float* row_q;              // [E*B]
+    int mse;                   // scalar critics (Eq. 2): loss (Q - y)^2, dQ = 2 (Q - y) scale
 };
 void launch_ce(const CeArgs& a, cudaStream_t s);
 
@@ -194,6 +197,8 @@ struct ActorQArgs {
     __nv_bfloat16* dlogits_bf; int64_t ld_bf;   // optional BF16 copy [E, B, ld_bf]
     float* row_q;              // [E*B]
     const int32_t* do_actor;
+    int cdq;                   // clipped double Q: the smaller critic per sample carries the gradient
+    int mse;                   // scalar critics: Q is the output itself
 };
 void launch_actor_q(const ActorQArgs& a, cudaStream_t s);
 
@@ -217,6 +222,7 @@ struct StatsArgs {
     const int32_t* do_actor;
     int64_t* update_idx;          // read into the statistics, then advanced by one
     float* stats;                 // [8]
+    int cdq;                      // actor loss with the smaller critic per sample
 };
 void launch_stats(const StatsArgs& a, cudaStream_t s);
 

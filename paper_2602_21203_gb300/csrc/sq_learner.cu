@@ -359,7 +359,7 @@ void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, in
 }  // namespace
 
 int squint_handle::allocate() {
-    const int B = c.batch, A = c.action_dim, K = c.atoms, E = 2;
+    const int B = c.batch, A = c.action_dim, K = c.critic_kind == 1 ? 1 : c.atoms, E = 2;
     fp8 = c.precision == SQUINT_PREC_FP8;
     if (const char* e = std::getenv("SQUINT_FUSED_LN")) fuse_ln = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_GEMM_SPLIT")) gemm_split = std::atoi(e) != 0;
@@ -668,7 +668,7 @@ int squint_handle::after_param_change() {
 }
 
 void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
-    const int B = c.batch, A = c.action_dim, P = c.proprio_dim, K = c.atoms, E = 2;
+    const int B = c.batch, A = c.action_dim, P = c.proprio_dim, K = c.critic_kind == 1 ? 1 : c.atoms, E = 2;
     const int F = L.feat, Z = L.zdim, Dd = L.D, Dc = L.dc, Da = L.da;
     const int64_t Dc8 = pad8(Dc), Da8 = pad8(Da), K8 = pad8(K);
     const float ln_eps = (float)c.ln_eps;
@@ -868,6 +868,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ct.log_alpha = W + L.log_alpha;
         ct.gamma = (float)c.gamma; ct.v_min = (float)c.v_min; ct.v_max = (float)c.v_max;
         ct.m = m;
+        ct.cdq = c.cdq; ct.mse = c.critic_kind == 1;
         ProfScope ps(this, s, "heads_losses", 0, 1);
         launch_c51_target(ct, s);
     }
@@ -880,6 +881,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ce.v_min = (float)c.v_min; ce.v_max = (float)c.v_max;
         ce.scale = 1.0f / (float)B;
         ce.dlogits = dlogits; ce.row_loss = row_loss; ce.row_q = row_q;
+        ce.mse = c.critic_kind == 1;
         if (bf16) { ce.dlogits_bf = dlogits_h; ce.ld_bf = K8; }
         ProfScope ps(this, s, "heads_losses", 0, 1);
         launch_ce(ce, s);
@@ -1073,6 +1075,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         aq.B = B; aq.K = K; aq.E = E; aq.logits = qcrit_mlp.out;
         aq.v_min = (float)c.v_min; aq.v_max = (float)c.v_max;
         aq.dlogits = dlogits_q; aq.row_q = row_q_actor; aq.do_actor = d_do_actor;
+        aq.cdq = c.cdq; aq.mse = c.critic_kind == 1;
         if (bf16) { aq.dlogits_bf = dlogits_qh; aq.ld_bf = K8; }
         {
             ProfScope ps(this, s, "heads_losses", 0, 1);
@@ -1124,7 +1127,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         StatsArgs st{};
         st.B = B; st.E = E; st.row_loss = row_loss; st.row_q = row_q; st.row_q_actor = row_q_actor;
         st.logp_t = logp + B; st.log_alpha = W + L.log_alpha; st.do_actor = d_do_actor;
-        st.update_idx = d_update_idx; st.stats = stats;
+        st.update_idx = d_update_idx; st.stats = stats; st.cdq = c.cdq;
         ProfScope ps(this, s, "heads_losses", 0, 1);
         launch_stats(st, s);
     }

@@ -255,6 +255,9 @@ constexpr int kMaxAtoms = 256;
 // distributions, projected onto the fixed support as
 // m_j = sum_i P_i max(0, 1 - |b_i - j|)   (linear interpolation between the two
 // neighbouring atoms of b_i = (clip(r + gamma (1-d)(z_i - alpha log pi')) - v_min)/dz).
+// Clipped double Q: per sample the distribution of the target critic with the smaller
+// mean (ties to critic 0).  MSE critics (K = 1): y = r + gamma (1-d)(Q_bar - alpha log pi')
+// with Q_bar the average (or, with clipped double Q, the minimum) of the target outputs.
 __global__ void c51_target_kernel(C51TargetArgs a) {
     SQ_KERNEL_ENTRY();
     __shared__ float pbar[kMaxAtoms];
@@ -262,9 +265,42 @@ __global__ void c51_target_kernel(C51TargetArgs a) {
     __shared__ float red[32];
     const int row = blockIdx.x;
     const float alpha = a.log_alpha ? expf(*a.log_alpha) : a.alpha_value;
+    const float r = a.r[row], nd = 1.0f - a.d[row], lp = a.logp_next[row];
+    if (a.mse) {
+        if (threadIdx.x == 0) {
+            float qb = a.cdq ? INFINITY : 0.f;
+            for (int e = 0; e < a.E; ++e) {
+                const float q = a.logits_bar[(int64_t)e * a.B + row];
+                qb = a.cdq ? fminf(qb, q) : qb + q;
+            }
+            if (!a.cdq) qb /= (float)a.E;
+            a.m[row] = r + a.gamma * nd * (qb - alpha * lp);
+        }
+        return;
+    }
     const float dz = (a.v_max - a.v_min) / (float)(a.K - 1);
+    int pick = -1;   // clipped double Q: the critic whose distribution is used
+    if (a.cdq) {
+        float best = INFINITY;
+        for (int e = 0; e < a.E; ++e) {
+            const float* lg = a.logits_bar + ((int64_t)e * a.B + row) * a.K;
+            float mx = -INFINITY;
+            for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
+            mx = block_max(mx, red);
+            float s = 0.f, q = 0.f;
+            for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
+                const float p = expf(lg[j] - mx);
+                s += p;
+                q += p * (a.v_min + (float)j * dz);
+            }
+            s = block_sum(s, red);
+            q = block_sum(q, red) / s;
+            if (q < best) { best = q; pick = e; }
+        }
+    }
     for (int j = threadIdx.x; j < a.K; j += blockDim.x) pbar[j] = 0.f;
     for (int e = 0; e < a.E; ++e) {
+        if (pick >= 0 && e != pick) continue;
         const float* lg = a.logits_bar + ((int64_t)e * a.B + row) * a.K;
         float mx = -INFINITY;
         for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
@@ -274,9 +310,9 @@ __global__ void c51_target_kernel(C51TargetArgs a) {
         s = block_sum(s, red);
         for (int j = threadIdx.x; j < a.K; j += blockDim.x) pbar[j] += expf(lg[j] - mx) / s;
     }
-    const float r = a.r[row], nd = 1.0f - a.d[row], lp = a.logp_next[row];
+    const float n_used = pick >= 0 ? 1.f : (float)a.E;
     for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
-        pbar[j] /= (float)a.E;
+        pbar[j] /= n_used;
         const float zj = a.v_min + (float)j * dz;
         float tz = r + a.gamma * nd * (zj - alpha * lp);
         tz = fminf(fmaxf(tz, a.v_min), a.v_max);
@@ -292,6 +328,7 @@ __global__ void c51_target_kernel(C51TargetArgs a) {
 
 // ---------------------------------------------------------------- cross entropy
 // One block per (critic, sample): -sum m log softmax(l), d/dl = (softmax - m)/B, Q = sum softmax z.
+// MSE critics (K = 1): loss (Q - y)^2 with y = m[row], dQ = 2 (Q - y) / B, Q = the output.
 __global__ void ce_kernel(CeArgs a) {
     SQ_KERNEL_ENTRY();
     __shared__ float red[32];
@@ -299,6 +336,17 @@ __global__ void ce_kernel(CeArgs a) {
     const int row = er % a.B;
     const float* lg = a.logits + (int64_t)er * a.K;
     const float* m = a.m + (int64_t)row * a.K;
+    if (a.mse) {
+        if (threadIdx.x == 0) {
+            const float q = lg[0], err = q - m[0];
+            const float g = 2.0f * err * a.scale;
+            a.dlogits[er] = g;
+            if (a.dlogits_bf) a.dlogits_bf[(int64_t)er * a.ld_bf] = __float2bfloat16_rn(g);
+            a.row_loss[er] = err * err;
+            a.row_q[er] = q;
+        }
+        return;
+    }
     const float dz = (a.v_max - a.v_min) / (float)(a.K - 1);
     float mx = -INFINITY;
     for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
@@ -322,33 +370,65 @@ __global__ void ce_kernel(CeArgs a) {
     if (threadIdx.x == 0) { a.row_loss[er] = loss; a.row_q[er] = q; }
 }
 
-// Actor objective through the critics: Q = sum p z, dQ/dl_j = p_j (z_j - Q),
-// d(-mean_i Q_i / B)/dl = -(1/(E B)) p (z - Q).
+// Actor objective through the critics, one block per sample over all critics:
+// Q_i = sum p z (or the scalar output), combined as the average (d/dQ_i = -1/(E B)) or,
+// with clipped double Q, the minimum (d/dQ_i = -1/B for the smaller critic, ties to 0);
+// categorical critics pass it on as dQ/dl_j = p_j (z_j - Q).
 __global__ void actor_q_kernel(ActorQArgs a) {
     SQ_KERNEL_ENTRY();
     if (!*a.do_actor) return;
     __shared__ float red[32];
-    __shared__ float qs;
-    const int er = blockIdx.x;
-    const float* lg = a.logits + (int64_t)er * a.K;
-    const float dz = (a.v_max - a.v_min) / (float)(a.K - 1);
-    float mx = -INFINITY;
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
-    mx = block_max(mx, red);
-    float s = 0.f;
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) s += expf(lg[j] - mx);
-    s = block_sum(s, red);
-    float q = 0.f;
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) q += expf(lg[j] - mx) / s * (a.v_min + (float)j * dz);
-    q = block_sum(q, red);
-    if (threadIdx.x == 0) { qs = q; a.row_q[er] = q; }
+    __shared__ float qv[8];
+    const int row = blockIdx.x;
+    const float dz = a.mse ? 0.f : (a.v_max - a.v_min) / (float)(a.K - 1);
+    for (int e = 0; e < a.E; ++e) {
+        const float* lg = a.logits + ((int64_t)e * a.B + row) * a.K;
+        float q;
+        if (a.mse) {
+            q = lg[0];
+        } else {
+            float mx = -INFINITY;
+            for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
+            mx = block_max(mx, red);
+            float s = 0.f;
+            for (int j = threadIdx.x; j < a.K; j += blockDim.x) s += expf(lg[j] - mx);
+            s = block_sum(s, red);
+            q = 0.f;
+            for (int j = threadIdx.x; j < a.K; j += blockDim.x) q += expf(lg[j] - mx) / s * (a.v_min + (float)j * dz);
+            q = block_sum(q, red);
+        }
+        if (threadIdx.x == 0) { qv[e] = q; a.row_q[(int64_t)e * a.B + row] = q; }
+    }
     __syncthreads();
-    const float scale = -1.0f / (float)(a.E * a.B);
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
-        const float p = expf(lg[j] - mx) / s;
-        const float g = scale * p * (a.v_min + (float)j * dz - qs);
-        a.dlogits[(int64_t)er * a.K + j] = g;
-        if (a.dlogits_bf) a.dlogits_bf[(int64_t)er * a.ld_bf + j] = __float2bfloat16_rn(g);
+    int pick = -1;
+    if (a.cdq) {
+        pick = 0;
+        for (int e = 1; e < a.E; ++e)
+            if (qv[e] < qv[pick]) pick = e;
+    }
+    for (int e = 0; e < a.E; ++e) {
+        const float dq = pick < 0 ? -1.0f / (float)(a.E * a.B) : (e == pick ? -1.0f / (float)a.B : 0.f);
+        const float* lg = a.logits + ((int64_t)e * a.B + row) * a.K;
+        const int64_t er = (int64_t)e * a.B + row;
+        if (a.mse) {
+            if (threadIdx.x == 0) {
+                a.dlogits[er] = dq;
+                if (a.dlogits_bf) a.dlogits_bf[er * a.ld_bf] = __float2bfloat16_rn(dq);
+            }
+            continue;
+        }
+        float mx = -INFINITY;
+        for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
+        mx = block_max(mx, red);
+        float s = 0.f;
+        for (int j = threadIdx.x; j < a.K; j += blockDim.x) s += expf(lg[j] - mx);
+        s = block_sum(s, red);
+        for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
+            const float p = expf(lg[j] - mx) / s;
+            const float g = dq * p * (a.v_min + (float)j * dz - qv[e]);
+            a.dlogits[er * a.K + j] = g;
+            if (a.dlogits_bf) a.dlogits_bf[er * a.ld_bf + j] = __float2bfloat16_rn(g);
+        }
     }
 }
 
@@ -477,9 +557,12 @@ __global__ void stats_kernel(StatsArgs a) {
     if (act) {
         const float alpha = expf(*a.log_alpha);
         for (int i = threadIdx.x; i < a.B; i += blockDim.x) {
-            float qm = 0.f;
-            for (int e = 0; e < a.E; ++e) qm += a.row_q_actor[e * a.B + i];
-            al += alpha * a.logp_t[i] - qm / (float)a.E;
+            float qm = a.cdq ? INFINITY : 0.f;
+            for (int e = 0; e < a.E; ++e) {
+                const float q = a.row_q_actor[e * a.B + i];
+                qm = a.cdq ? fminf(qm, q) : qm + q;
+            }
+            al += alpha * a.logp_t[i] - (a.cdq ? qm : qm / (float)a.E);
         }
     }
     al = block_sum(al, red);
@@ -640,7 +723,7 @@ void launch_actor_head_bwd(const ActorHeadBwdArgs& a, cudaStream_t s) {
 }
 void launch_c51_target(const C51TargetArgs& a, cudaStream_t s) { launch_k(c51_target_kernel, dim3(a.B), dim3(128), 0, s, a); }
 void launch_ce(const CeArgs& a, cudaStream_t s) { launch_k(ce_kernel, dim3(a.E * a.B), dim3(128), 0, s, a); }
-void launch_actor_q(const ActorQArgs& a, cudaStream_t s) { launch_k(actor_q_kernel, dim3(a.E * a.B), dim3(128), 0, s, a); }
+void launch_actor_q(const ActorQArgs& a, cudaStream_t s) { launch_k(actor_q_kernel, dim3(a.B), dim3(128), 0, s, a); }
 void launch_alpha_step(const AlphaArgs& a, cudaStream_t s) { launch_k(alpha_kernel, dim3(1), dim3(256), 0, s, a); }
 void launch_stats(const StatsArgs& a, cudaStream_t s) { launch_k(stats_kernel, dim3(1), dim3(256), 0, s, a); }
 void launch_adam(const AdamArgs& a, cudaStream_t s) {

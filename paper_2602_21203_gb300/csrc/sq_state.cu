@@ -56,7 +56,7 @@ int squint_handle::load_state(const uint8_t* in) {
 }
 
 int squint_handle::debug_tensor(const char* name, void* host, size_t* bytes) {
-    const int B = c.batch, A = c.action_dim, K = c.atoms;
+    const int B = c.batch, A = c.action_dim, K = c.critic_kind == 1 ? 1 : c.atoms;
     const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
     const std::string n(name);
     const void* src = nullptr;

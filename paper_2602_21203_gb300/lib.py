@@ -35,7 +35,7 @@ class Config(ctypes.Structure):
         ("hidden", ctypes.c_int32 * MAX_HIDDEN),
         ("n_critics", ctypes.c_int32), ("atoms", ctypes.c_int32), ("batch", ctypes.c_int32),
         ("policy_freq", ctypes.c_int32), ("precision", ctypes.c_int32), ("max_k", ctypes.c_int32),
-        ("recompute_chunk", ctypes.c_int32),
+        ("critic_kind", ctypes.c_int32), ("cdq", ctypes.c_int32), ("recompute_chunk", ctypes.c_int32),
         ("v_min", ctypes.c_double), ("v_max", ctypes.c_double), ("gamma", ctypes.c_double),
         ("lr", ctypes.c_double), ("tau", ctypes.c_double), ("init_alpha", ctypes.c_double),
         ("target_entropy", ctypes.c_double), ("ln_eps", ctypes.c_double),
@@ -185,6 +185,8 @@ def make_config(cfg, precision=PREC_FP32, max_k=None):
     c.precision = int(precision)
     c.max_k = int(max_k if max_k is not None else max(8, cfg.get("utd", 1)))
     c.recompute_chunk = int(cfg.get("recompute_chunk", 0))
+    c.critic_kind = 1 if cfg.get("critic", "c51") == "mse" else 0
+    c.cdq = 1 if cfg.get("cdq", False) else 0
     for k in ("v_min", "v_max", "gamma", "lr", "tau", "init_alpha", "ln_eps", "log_std_min", "log_std_max",
               "adam_b1", "adam_b2", "adam_eps"):
         setattr(c, k, float(cfg[k]))
