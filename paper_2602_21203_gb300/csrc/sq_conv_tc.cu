@@ -14,6 +14,7 @@
 // channels split into 4 planes of 8 (16 B per pixel row per plane): element
 // (row r, channel c) at (c / 8) * PLANE + r * 16 + (c % 8) * 2.  Any start row is a
 // valid descriptor start.  TMA loads each plane of an image box by box.
+#include "sq_kernels.cuh"
 #include "sq_tc.cuh"
 
 #include <cuda.h>
@@ -392,6 +393,56 @@ __global__ void wgrad32_reduce_kernel(const float* __restrict__ work, int splits
     else dw[co * (N - 1) + col] = s;
 }
 
+// ---------------------------------------------------------------- first layer straight to padded HWC
+// The encoder's first convolution (few input channels, any stride, 32 outputs) for the
+// tensor-core path: one thread per output pixel holds its 32 channels, the filter and bias
+// are broadcast from shared memory, and the ReLU output goes straight to the padded-HWC
+// BF16 image the next (tensor-core) layer reads.  Each output is accumulated over
+// k = (ci, ky, kx) in order with fused multiply-adds, then the bias is added: the same
+// arithmetic as the CUDA-core implicit GEMM followed by the layout conversion.
+__global__ void __launch_bounds__(256) conv0_phwc_kernel(ConvShape sh, const float* __restrict__ x,
+                                                         const float* __restrict__ w, const float* __restrict__ bias,
+                                                         __nv_bfloat16* __restrict__ out) {
+    SQ_KERNEL_ENTRY();
+    extern __shared__ float w_s[];   // [K][32] then bias [32]
+    const int K = sh.Cin * 9;
+    for (int e = threadIdx.x; e < K * kCh; e += blockDim.x) {
+        const int k = e / kCh, co = e % kCh;
+        w_s[e] = w[(int64_t)co * K + k];
+    }
+    if (threadIdx.x < kCh) w_s[K * kCh + threadIdx.x] = bias[threadIdx.x];
+    __syncthreads();
+    const int64_t npix = (int64_t)sh.nimg * sh.OH * sh.OW;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    const int img = (int)(p / (sh.OH * sh.OW));
+    const int rem = (int)(p - (int64_t)img * sh.OH * sh.OW);
+    const int oy = rem / sh.OW, ox = rem - (rem / sh.OW) * sh.OW;
+    const float* xb = x + (int64_t)img * sh.x_img_stride + (int64_t)(oy * sh.stride) * sh.W + ox * sh.stride;
+    float acc[kCh];
+#pragma unroll
+    for (int co = 0; co < kCh; ++co) acc[co] = 0.f;
+    for (int ci = 0; ci < sh.Cin; ++ci)
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const float xv = __ldg(xb + (int64_t)ci * sh.H * sh.W + (t / 3) * sh.W + (t % 3));
+            const float* wk = w_s + (ci * 9 + t) * kCh;
+#pragma unroll
+            for (int co = 0; co < kCh; ++co) acc[co] = fmaf(xv, wk[co], acc[co]);
+        }
+    __align__(16) __nv_bfloat16 hb[kCh];
+#pragma unroll
+    for (int co = 0; co < kCh; ++co) {
+        float v = acc[co] + w_s[K * kCh + co];
+        if (!(v > 0.f)) v = 0.f;
+        hb[co] = __float2bfloat16_rn(v);
+    }
+    __nv_bfloat16* d = out + ((int64_t)img * (sh.OH + 4) * (sh.OW + 4) + (int64_t)(oy + 2) * (sh.OW + 4) + ox + 2) * kCh;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) reinterpret_cast<uint4*>(d)[c] = reinterpret_cast<const uint4*>(hb)[c];
+}
+
+
 // ---------------------------------------------------------------- layout conversions
 // CHW FP32 (per image stride img_stride) -> padded HWC BF16 interior.
 __global__ void to_phwc_kernel(const float* __restrict__ src, int64_t img_stride, int nimg, int H, int W,
@@ -537,6 +588,14 @@ void conv_tc_prepare() {
     cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(wgrad32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     encode_fn();
+}
+
+void launch_conv0_phwc(const ConvShape& sh, const float* x, const float* w, const float* b, __nv_bfloat16* out,
+                       cudaStream_t s) {
+    const int64_t npix = (int64_t)sh.nimg * sh.OH * sh.OW;
+    if (npix <= 0) return;
+    const size_t smem = ((size_t)sh.Cin * 9 * kCh + kCh) * sizeof(float);
+    launch_k(conv0_phwc_kernel, dim3((unsigned)((npix + 255) / 256)), dim3(256), smem, s, sh, x, w, b, out);
 }
 
 void launch_to_phwc(const float* src, int64_t img_stride, int nimg, int H, int W, __nv_bfloat16* dst, cudaStream_t s) {

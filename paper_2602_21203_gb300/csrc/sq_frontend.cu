@@ -28,14 +28,20 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
 
     const int64_t fbytes = (int64_t)a.C * a.H * a.W;
     const uint8_t* src = a.obs + slot * fbytes;
-    if ((fbytes & 15) == 0 && (((uintptr_t)src) & 15) == 0) {
-        const uint4* s4 = reinterpret_cast<const uint4*>(src);
-        uint4* d4 = reinterpret_cast<uint4*>(frame);
-        for (int64_t i = threadIdx.x; i < fbytes / 16; i += blockDim.x) d4[i] = __ldg(s4 + i);
+    __shared__ uint64_t bar;
+    // the whole frame in one TMA bulk copy when aligned (most bytes in flight per SM)
+    const bool bulk = (fbytes & 15) == 0 && fbytes < (1 << 20) && (((uintptr_t)src) & 15) == 0;
+    if (bulk) {
+        if (threadIdx.x == 0) {
+            bulk_load_init(&bar);
+            bulk_load(frame, src, (uint32_t)fbytes, &bar);
+        }
+        __syncthreads();
+        if (!bulk_load_wait(&bar, 0) && threadIdx.x == 0 && a.err) atomicCAS(a.err, 0, 31);
     } else {
         for (int64_t i = threadIdx.x; i < fbytes; i += blockDim.x) frame[i] = src[i];
+        __syncthreads();
     }
-    __syncthreads();
 
     const int hs = a.H / a.f, ws = a.W / a.f;
     const int plane = hs * ws;
@@ -164,11 +170,11 @@ void launch_squint_store(const uint8_t* src, int n, int C, int H, int W, int f, 
              slot0, n_slots);
 }
 
+// Opt the kernels in to a whole frame of dynamic shared memory (with the kernel's own
+// static shared memory a 48 KiB frame is already above the default limit).
 void frontend_prepare(size_t frame_bytes) {
-    if (frame_bytes > 48 * 1024) {
-        cudaFuncSetAttribute(frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
-        cudaFuncSetAttribute(act_frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
-    }
+    cudaFuncSetAttribute(frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
+    cudaFuncSetAttribute(act_frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
 }
 
 }  // namespace sq

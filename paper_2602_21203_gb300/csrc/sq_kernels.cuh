@@ -37,6 +37,7 @@ struct FrontendArgs {
     int32_t* steps;              // device [3]: critic, actor, alpha step counts (incremented here)
     int32_t* do_actor;           // device flag: actor steps this update
     int policy_freq;
+    int* err;                    // device error word: a frame copy that never completed
 };
 void launch_frontend(const FrontendArgs& a, cudaStream_t s);
 
@@ -87,6 +88,10 @@ struct ConvShape {
     int64_t x_img_stride;      // elements between images of the input (default Cin*H*W)
     int64_t y_img_stride;      // elements between images of the output (default Cout*OH*OW)
 };
+// First encoder layer (Cin <= 16, any stride, Cout = 32) with ReLU, written as padded-HWC
+// BF16 (grid width OW + 4) for the tensor-core layers; x is NCHW FP32.
+void launch_conv0_phwc(const ConvShape& sh, const float* x, const float* w, const float* b, __nv_bfloat16* out,
+                       cudaStream_t s);
 template <typename T>
 void launch_conv_fwd(const ConvShape& sh, const T* x, const T* w, const T* b, T* y, bool relu, cudaStream_t s);
 // dx = conv-transpose(dy, w) (* (mask > 0) if mask given; mask has the layout of dx).

@@ -404,7 +404,7 @@ int squint_handle::allocate() {
         const ConvL& cv = L.conv[l];
         const int64_t per = (int64_t)cv.cout * cv.oh * cv.ow;
         if (l + 1 == L.conv.size()) conv_out.push_back(dalloc<float>(2 * B * per));     // features z
-        else if (l == 0) conv_out.push_back(dalloc<float>(tc_conv ? enc_imgs * per : 2 * B * per));
+        else if (l == 0) conv_out.push_back(tc_conv ? nullptr : dalloc<float>(2 * B * per));
         else conv_out.push_back(tc_conv ? nullptr : dalloc<float>(2 * B * per));
     }
     if (L.D > 0) {
@@ -725,7 +725,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     fa.dst[4] = CopyDst{xa, Da, Z, 1, xa_h, Da8};
     fa.dst[5] = CopyDst{xcbar, Dc, Z, 1, xcbar_h, Dc8};
     fa.n_dst = 6;
-    fa.steps = d_steps; fa.do_actor = d_do_actor; fa.policy_freq = c.policy_freq;
+    fa.steps = d_steps; fa.do_actor = d_do_actor; fa.policy_freq = c.policy_freq; fa.err = d_err;
     {
         const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
         ProfScope ps(this, s, "frontend", 2.0 * B * c.obs_c * c.obs_h * c.obs_w + 2.0 * B * img * 4, 1);
@@ -742,12 +742,9 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         const int64_t img0 = (int64_t)c.obs_c * c0.h * c0.w;
         ConvShape sh{n, c0.cin, c0.h, c0.w, c0.cout, c0.s, c0.oh, c0.ow, img0, (int64_t)c0.cout * c0.oh * c0.ow};
         {
+            // first layer on CUDA cores, written straight into the padded-HWC input of layer 1
             ProfScope ps(this, st, "conv_f32_fwd", conv_flops(c0, n), 0);
-            launch_conv_fwd<float>(sh, x2 + (int64_t)i0 * img0, W + c0.wo, W + c0.bo, conv_out[0], true, st);
-        }
-        {
-            ProfScope ps(this, st, "layout_phwc", (4.0 + 2.0) * n * c0.cout * c0.oh * c0.ow, 1);
-            launch_to_phwc(conv_out[0], (int64_t)c0.cout * c0.oh * c0.ow, n, c0.oh, c0.ow, act_p[0], st);
+            launch_conv0_phwc(sh, x2 + (int64_t)i0 * img0, W + c0.wo, W + c0.bo, act_p[0], st);
         }
         for (int l = 1; l <= upto; ++l) {
             const ConvL& cv = L.conv[l];

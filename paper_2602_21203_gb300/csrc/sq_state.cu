@@ -258,9 +258,12 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
         }
         ConvShape sh{rows, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
                      (int64_t)cv.cout * cv.oh * cv.ow};
+        if (tc && l == 0) {   // first layer straight into the padded-HWC input of the tensor-core layers
+            launch_conv0_phwc(sh, in, Wp + cv.wo, Wp + cv.bo, aphwc[0], s);
+            continue;
+        }
         launch_conv_fwd<float>(sh, in, Wp + cv.wo, Wp + cv.bo, aconv[l], true, s);
         in = aconv[l];
-        if (tc && l == 0) launch_to_phwc(aconv[0], (int64_t)cv.cout * cv.oh * cv.ow, rows, cv.oh, cv.ow, aphwc[0], s);
     }
     if (bf16 && !tc) {
         CastItem ci{in, F, rows, F, az_h, F};
