@@ -169,6 +169,7 @@ __device__ __forceinline__ bool bulk_load_wait(uint64_t* bar, uint32_t parity) {
             : "memory");
         if (ok) return true;
         if (clock64() - t0 > 2000000000ll) return false;
+        __nanosleep(64);   // leave the issue slots to resident warps with work
     }
 }
 

@@ -28,6 +28,7 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
 
     const int64_t fbytes = (int64_t)a.C * a.H * a.W;
     const uint8_t* src = a.obs + slot * fbytes;
+    {
     __shared__ uint64_t bar;
     // the whole frame in one TMA bulk copy when aligned (most bytes in flight per SM)
     const bool bulk = (fbytes & 15) == 0 && fbytes < (1 << 20) && (((uintptr_t)src) & 15) == 0;
@@ -36,8 +37,9 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
             bulk_load_init(&bar);
             bulk_load(frame, src, (uint32_t)fbytes, &bar);
         }
+        // one thread waits (the others at the block barrier issue nothing meanwhile)
+        if (threadIdx.x == 0 && !bulk_load_wait(&bar, 0) && a.err) atomicCAS(a.err, 0, 31);
         __syncthreads();
-        if (!bulk_load_wait(&bar, 0) && threadIdx.x == 0 && a.err) atomicCAS(a.err, 0, 31);
     } else {
         for (int64_t i = threadIdx.x; i < fbytes; i += blockDim.x) frame[i] = src[i];
         __syncthreads();
@@ -49,6 +51,39 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
     const float denom = 255.0f * (float)(a.f * a.f);
     const int64_t row = (int64_t)which * a.B + b;
     float* xo = a.x + row * n_out;
+    // f = 4 with 4-byte-aligned frame rows: a thread per output column j, one output row
+    // per warp group; each of the 4 source rows contributes its 4 bytes through two aligned
+    // 32-bit words, a funnel shift and one dp4a (exact integer sums), except at the
+    // replicate-padded edges, which take the per-byte path
+    if (a.f == 4 && (a.W & 3) == 0 && ws <= (int)blockDim.x && (blockDim.x % ws) == 0) {
+        const int j = threadIdx.x % ws;
+        const int x0 = j * 4 + dx - a.pad;
+        const bool interior = x0 >= 0 && x0 + 3 <= a.W - 1;
+        const int wq = x0 >> 2, sh = (x0 & 3) * 8;
+        for (int ri = threadIdx.x / ws; ri < a.C * hs; ri += blockDim.x / ws) {
+            const int c = ri / hs, i = ri - c * hs;
+            uint32_t sum = 0;
+#pragma unroll
+            for (int uu = 0; uu < 4; ++uu) {
+                const int y = min(max(i * 4 + uu + dy - a.pad, 0), a.H - 1);
+                const uint8_t* rp = frame + ((int64_t)c * a.H + y) * a.W;
+                if (interior) {
+                    const uint32_t* w32 = reinterpret_cast<const uint32_t*>(rp);
+                    const uint32_t lo = w32[wq];
+                    const uint32_t hi = sh ? w32[wq + 1] : 0u;
+                    sum = __dp4a(__funnelshift_r(lo, hi, sh), 0x01010101u, sum);
+                } else {
+#pragma unroll
+                    for (int vv = 0; vv < 4; ++vv) sum += rp[min(max(x0 + vv, 0), a.W - 1)];
+                }
+            }
+            const int o = ri * ws + j;
+            const float val = (float)sum / denom - 0.5f;
+            xo[o] = val;
+            if (a.x_bf) a.x_bf[row * n_out + o] = __float2bfloat16_rn(val);
+            if (a.sums) a.sums[row * n_out + o] = (uint16_t)sum;
+        }
+    } else
     for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
         const int c = o / plane;
         const int i = (o - c * plane) / ws;
@@ -68,6 +103,9 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
         if (a.sums) a.sums[row * n_out + o] = (uint16_t)sum;
     }
 
+    }
+
+    const int64_t row = (int64_t)which * a.B + b;
     if (threadIdx.x == 0) {
         a.idx_out[row] = (int32_t)slot;
         a.shift_out[2 * row] = dx;
@@ -121,6 +159,18 @@ __global__ void __launch_bounds__(256) act_frontend_kernel(ActFrontArgs a) {
     __syncthreads();
     const int hs = a.H / a.f, ws = a.W / a.f, plane = hs * ws, n_out = a.C * plane;
     const float denom = 255.0f * (float)(a.f * a.f);
+    if (a.f == 4 && (a.W & 3) == 0) {   // aligned 4-byte row segments summed by dp4a
+        for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
+            const int c = o / plane, i = (o - c * plane) / ws, j = o - c * plane - i * ws;
+            uint32_t sum = 0;
+#pragma unroll
+            for (int uu = 0; uu < 4; ++uu) {
+                const uint32_t w = *reinterpret_cast<const uint32_t*>(frame + ((int64_t)c * a.H + i * 4 + uu) * a.W + j * 4);
+                sum = __dp4a(w, 0x01010101u, sum);
+            }
+            a.x[(int64_t)r * n_out + o] = (float)sum / denom - 0.5f;
+        }
+    } else
     for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
         const int c = o / plane, i = (o - c * plane) / ws, j = o - c * plane - i * ws;
         uint32_t sum = 0;
@@ -175,6 +225,9 @@ void launch_squint_store(const uint8_t* src, int n, int C, int H, int W, int f, 
 void frontend_prepare(size_t frame_bytes) {
     cudaFuncSetAttribute(frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
     cudaFuncSetAttribute(act_frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
+    // all of the unified L1 / shared memory as shared: as many whole frames in flight per SM as fit
+    cudaFuncSetAttribute(frontend_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(act_frontend_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
 }
 
 }  // namespace sq
