@@ -44,14 +44,16 @@ def dims(cfg):
     """Derived sizes: training resolution, conv output sizes, feature widths."""
     f = cfg["squint_f"]
     hs, ws = cfg["obs_h"] // f, cfg["obs_w"] // f
-    strides = cfg.get("conv_strides") or [2] + [1] * (cfg["conv_layers"] - 1)
+    n_conv = cfg["conv_layers"]
+    strides = (cfg.get("conv_strides") or [2] + [1] * (n_conv - 1)) if n_conv > 0 else []
     conv = []
     cin, h, w = cfg["obs_c"], hs, ws
     for s in strides:
         oh, ow = (h - 3) // s + 1, (w - 3) // s + 1
         conv.append(dict(cin=cin, cout=cfg["conv_ch"], h=h, w=w, oh=oh, ow=ow, s=s))
         cin, h, w = cfg["conv_ch"], oh, ow
-    feat = cin * h * w
+    # state-based SAC (Fig. 6 left: the encoder removed): no image features at all
+    feat = cin * h * w if n_conv > 0 else 0
     d = cfg["proj_dim"]
     zdim = d if d > 0 else feat
     return dict(hs=hs, ws=ws, conv=conv, feat=feat, zdim=zdim,
@@ -215,9 +217,19 @@ def squint_values(sums, f):
 
 
 def frontend(cfg, ring, u):
-    """Steps a1-a4: indices, gathers, shifts, squint for o_t and o_{t+1}."""
-    n_slots = ring["obs"].shape[0]
+    """Steps a1-a4: indices, gathers, shifts, squint for o_t and o_{t+1} (state-based
+    SAC, conv_layers = 0: no images, only the proprioceptive state and the transition)."""
+    n_slots = ring["proprio"].shape[0]
     idx, nxt = sample_indices(cfg, u, n_slots)
+    if cfg["conv_layers"] == 0:
+        B = len(idx)
+        empty = np.zeros((B, 0))
+        return dict(
+            idx=idx, nxt=nxt, x_t=empty, x_t1=empty,
+            p_t=ring["proprio"][idx].astype(np.float64), a_t=ring["action"][idx].astype(np.float64),
+            r=ring["reward"][idx].astype(np.float64), d=ring["done"][idx].astype(np.float64),
+            p_t1=ring["proprio"][nxt].astype(np.float64),
+        )
     dx0, dy0 = sample_shifts(cfg, u, px.STREAM_SHIFT_T)
     dx1, dy1 = sample_shifts(cfg, u, px.STREAM_SHIFT_T1)
     p, f = cfg["shift_pad"], cfg["squint_f"]
@@ -279,7 +291,10 @@ def layernorm_bwd(dy, g, cache):
 
 
 def encoder_fwd(P, x, cfg):
-    """Conv stack with ReLU after every layer, flattened in (C, H, W) order."""
+    """Conv stack with ReLU after every layer, flattened in (C, H, W) order (no layers:
+    state-based SAC, an empty feature vector)."""
+    if cfg["conv_layers"] == 0:
+        return np.zeros((x.shape[0], 0)), []
     cache = []
     h = x
     for l, c in enumerate(dims(cfg)["conv"]):
@@ -292,6 +307,8 @@ def encoder_fwd(P, x, cfg):
 def encoder_bwd(P, cache, dz, cfg):
     grads = {}
     conv = dims(cfg)["conv"]
+    if not conv:
+        return grads
     dh = dz.reshape(cache[-1][1].shape)
     for l in reversed(range(len(conv))):
         xin, y = cache[l]
@@ -686,11 +703,14 @@ def act(P, obs, prop, key, sample, cfg):
     (b, STREAM_ACT | q << 16, k), so a row's action does not depend on which
     other requests share its batch.  `sample` False returns tanh(mu).
     """
-    n = obs.shape[0]
-    p, f = cfg["shift_pad"], cfg["squint_f"]
-    centre = np.full(n, p)
-    x = squint_values(shift_squint_sums(obs, centre, centre, p, f), f)
-    z, _ = encoder_fwd(P, x, cfg)
+    n = np.asarray(prop).shape[0]
+    if cfg["conv_layers"] == 0:                       # state-based: no observation image
+        z = np.zeros((n, 0))
+    else:
+        p, f = cfg["shift_pad"], cfg["squint_f"]
+        centre = np.full(n, p)
+        x = squint_values(shift_squint_sums(obs, centre, centre, p, f), f)
+        z, _ = encoder_fwd(P, x, cfg)
     A = cfg["action_dim"]
     h, _ = proj_fwd(P, "actor", z, cfg)
     out, _ = mlp_fwd(P, "actor", np.concatenate([h, np.asarray(prop, dtype=np.float64)], 1), cfg)

@@ -39,6 +39,16 @@ PRESETS = {
     "stored_b512": dict(ring_size=1_000_000, obs_h=32, obs_w=32, squint_f=1, shift_pad=2, batch=512,
                         conv_layers=4, conv_ch=32, proj_dim=256, hidden=[512, 512],
                         atoms=101, v_min=-20.0, v_max=20.0, utd=4, render_h=128, render_w=128, render_f=4),
+    # State-based SAC (Sec. VII, Fig. 6 left: the encoder removed): 1M slots of a 48-d
+    # state vector, batch 512, the same critics / actor (512-512, 101 atoms on [-20, 20])
+    # and UTD 4 as train_b512; no image in the ring.
+    "state_b512": dict(ring_size=1_000_000, obs_c=0, obs_h=0, obs_w=0, squint_f=1, shift_pad=0, batch=512,
+                       proprio_dim=48, conv_layers=0, conv_ch=0, proj_dim=0, hidden=[512, 512],
+                       atoms=101, v_min=-20.0, v_max=20.0, utd=4),
+    # Small state-based case for parity: 512 slots of a 20-d state, batch 64, MLPs 256-256.
+    "state_small_b64": dict(ring_size=512, obs_c=0, obs_h=0, obs_w=0, squint_f=1, shift_pad=0, batch=64,
+                            proprio_dim=20, conv_layers=0, conv_ch=0, proj_dim=0, hidden=[256, 256],
+                            atoms=51, v_min=-10.0, v_max=10.0, utd=4),
     # Tiny net for finite differences: 3x64x64 ring squinted to 3x16x16, 8 channels,
     # MLPs 32-32, 11 atoms on [-10, 10] (atom spacing exactly 2), batch 8.
     "tiny_b8": dict(ring_size=64, obs_h=64, obs_w=64, squint_f=4, shift_pad=4, batch=8,
@@ -60,12 +70,16 @@ def make_ring(cfg, seed=0, device="cpu"):
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     n, c, h, w = cfg["ring_size"], cfg["obs_c"], cfg["obs_h"], cfg["obs_w"]
-    obs = torch.randint(0, 256, (n, c, h, w), dtype=torch.uint8, generator=g, device=device)
+    state_based = cfg["conv_layers"] == 0          # no image in the ring
+    obs = None if state_based else torch.randint(0, 256, (n, c, h, w), dtype=torch.uint8, generator=g, device=device)
     proprio = torch.randn(n, cfg["proprio_dim"], generator=g, device=device)
     action = torch.rand(n, cfg["action_dim"], generator=g, device=device) * 2.0 - 1.0
     reward = torch.randn(n, generator=g, device=device)
     done = (torch.rand(n, generator=g, device=device) < 0.02).to(torch.uint8)
-    return dict(obs=obs, proprio=proprio, action=action, reward=reward, done=done)
+    ring = dict(proprio=proprio, action=action, reward=reward, done=done)
+    if not state_based:
+        ring["obs"] = obs
+    return ring
 
 
 def render_frames(n, cfg, seed, device="cpu"):
@@ -85,7 +99,9 @@ def make_obs_batch(n, cfg, seed, device="cpu"):
     """Inference inputs for n environments: uint8 frames at render resolution and proprio."""
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
-    obs = torch.randint(0, 256, (n, cfg["obs_c"], cfg["obs_h"], cfg["obs_w"]), dtype=torch.uint8,
-                        generator=g, device=device)
+    obs = None
+    if cfg["conv_layers"] > 0:
+        obs = torch.randint(0, 256, (n, cfg["obs_c"], cfg["obs_h"], cfg["obs_w"]), dtype=torch.uint8,
+                            generator=g, device=device)
     prop = torch.randn(n, cfg["proprio_dim"], generator=g, device=device)
     return obs, prop

@@ -652,3 +652,118 @@ def test_clipped_double_q_selects_the_smaller_critic():
     want = o.softmax(tgt["logits_target"])[lo, np.arange(q.shape[1])]
     assert np.allclose(tgt["pbar"], want, rtol=0, atol=1e-15)
     assert (q.min(0) <= q.mean(0) + 1e-15).all()
+
+
+# ---------------------------------------------------------------- state-based SAC (Fig. 6 left)
+
+def _state_pair(seed=0):
+    """A tiny visual config and its state-based twin (same heads, no encoder), on one ring."""
+    vis = _cfg_tiny()
+    st = _cfg_tiny(conv_layers=0, conv_ch=0, obs_c=0, obs_h=0, obs_w=0, squint_f=1, shift_pad=0)
+    ring_v = synth.ring_numpy(synth.make_ring(vis, seed))
+    ring_s = {k: v for k, v in ring_v.items() if k != "obs"}
+    return vis, st, ring_v, ring_s
+
+
+def _silent_encoder_params(P_state, vis, rng):
+    """Visual parameters whose encoder outputs exactly zero features (zero conv weights and
+    biases, so every ReLU sees 0), with the state parameters in the heads' state/action
+    columns and arbitrary values in the feature columns of each head's first layer."""
+    feat = o.dims(vis)["feat"]
+    P = {}
+    for name, shape, *_ in o.param_spec(vis):
+        if name.startswith("enc."):
+            P[name] = np.zeros(shape)
+        elif name.endswith("fc0.w"):
+            w = rng.standard_normal(shape)
+            w[:, feat:] = P_state[name]
+            P[name] = w
+        else:
+            P[name] = P_state[name].copy()
+    return P
+
+
+def test_state_based_layout_and_gather():
+    vis, st, _, ring_s = _state_pair()
+    dm = o.dims(st)
+    assert dm["feat"] == 0 and dm["zdim"] == 0 and dm["conv"] == []
+    assert dm["critic_in"] == st["proprio_dim"] + st["action_dim"] and dm["actor_in"] == st["proprio_dim"]
+    names = [n for n, *_ in o.param_spec(st)]
+    assert not any(n.startswith("enc.") for n in names)
+    assert {n for n, *_ in o.param_spec(vis) if not n.startswith("enc.")} == set(names)
+    fe = o.frontend(st, ring_s, 3)
+    assert fe["x_t"].shape == (st["batch"], 0) and fe["x_t1"].shape == (st["batch"], 0)
+    n = ring_s["proprio"].shape[0]
+    for b in range(st["batch"]):                      # row b is slot idx[b]; its next state is slot idx[b] + 1
+        i = int(fe["idx"][b])
+        assert fe["nxt"][b] == (i + 1) % n
+        assert np.array_equal(fe["p_t"][b], ring_s["proprio"][i])
+        assert np.array_equal(fe["p_t1"][b], ring_s["proprio"][(i + 1) % n])
+        assert np.array_equal(fe["a_t"][b], ring_s["action"][i])
+        assert fe["r"][b] == ring_s["reward"][i] and fe["d"][b] == ring_s["done"][i]
+
+
+def test_state_based_update_equals_visual_update_with_a_silent_encoder():
+    """Removing the encoder is the same as an encoder whose features are identically zero:
+    two updates of the state-based config and of the visual config with a silent encoder give
+    the same losses and the same head parameters; the feature columns and the encoder get no
+    gradient and do not move."""
+    vis, st, ring_v, ring_s = _state_pair(2)
+    Ps = o.init_params(st)
+    Pv = _silent_encoder_params(Ps, vis, np.random.default_rng(3))
+    feat = o.dims(vis)["feat"]
+    Sv = o.init_state(vis, params={k: v.copy() for k, v in Pv.items()})
+    Ss = o.init_state(st, params={k: v.copy() for k, v in Ps.items()})
+    for _ in range(2):
+        a, tv = o.update(Sv, ring_v, vis)
+        b, ts = o.update(Ss, ring_s, st)
+        for k in a:
+            assert a[k] == pytest.approx(b[k], rel=1e-12, abs=1e-12), k
+        for name, g in tv["critic"]["grads"].items():
+            if name.startswith("enc."):
+                assert not np.any(g), name
+            elif name.endswith("fc0.w"):
+                assert not np.any(g[:, :feat]), name
+    for name, v in Ss["params"].items():
+        w = Sv["params"][name]
+        if name.endswith("fc0.w"):
+            assert np.array_equal(w[:, :feat], Pv[name][:, :feat]), name
+            w = w[:, feat:]
+        assert np.allclose(w, v, rtol=0, atol=1e-12), name
+    for name, v in Sv["params"].items():
+        if name.startswith("enc."):
+            assert not np.any(v), name
+
+
+def test_state_based_loss_gradients_finite_differences():
+    _, st, _, ring_s = _state_pair(5)
+    S = o.init_state(st)
+    P = S["params"]
+    fe = o.frontend(st, ring_s, 0)
+    z1, _ = o.encoder_fwd(P, fe["x_t1"], st)
+    eps = px.normal_pairs(st["seed"], px.STREAM_EPS_TARGET, 0, st["batch"], 6)
+    m = o.target_distribution(P, S["target"], z1, fe, 0.1, eps, st)["m"]
+    res = o.critic_loss(P, fe["x_t"], fe, m, st)
+    f = lambda: o.critic_loss(P, fe["x_t"], fe, m, st, with_grads=False)["loss"]
+    rng = np.random.default_rng(6)
+    assert set(res["grads"]) == {n for n, *_ in o.param_spec(st) if o.group_of(n) == "critic"}
+    for name, g in res["grads"].items():
+        assert not _check_tensor_fd(f, P[name], g, rng=rng), name
+    z, _ = o.encoder_fwd(P, fe["x_t"], st)
+    epa = px.normal_pairs(st["seed"], px.STREAM_EPS_ACTOR, 0, st["batch"], 6)
+    ra = o.actor_loss(P, z, fe["p_t"], epa, 0.3, st)
+    fa = lambda: o.actor_loss(P, z, fe["p_t"], epa, 0.3, st, with_grads=False)["loss"]
+    for name, g in ra["grads"].items():
+        assert not _check_tensor_fd(fa, P[name], g, rng=rng), name
+
+
+def test_state_based_act_equals_visual_act_with_a_silent_encoder():
+    vis, st, _, _ = _state_pair()
+    Ps = o.init_params(st)
+    Pv = _silent_encoder_params(Ps, vis, np.random.default_rng(8))
+    obs, prop = synth.make_obs_batch(5, vis, 9)
+    obs, prop = obs.numpy(), prop.numpy()
+    for sample in (True, False):
+        a = o.act(Ps, None, prop, 77, sample, st)
+        b = o.act(Pv, obs, prop, 77, sample, vis)
+        assert np.allclose(a, b, rtol=0, atol=1e-13)
