@@ -37,8 +37,25 @@ FP32_LANES_PER_SM = 128
 # in one update; ncu replays each launch with cold caches), keyed by (class,
 # precision).  Set back to nothing when the kernel changes.
 NCU_TRAFFIC = {
-    # 14 forward GEMM launches of one BF16 update, 30.43 MB read, 0 written
-    ("tc_gemm_fwd", "bf16"): 2173385,
+    # train_b512: 14 forward GEMM launches of one BF16 update, 30.43 MB read, 0 written
+    ("tc_gemm_fwd", "bf16", "train_b512"): 2173385,
+}
+
+
+WORKLOAD_TEXT = {
+    "train_b512": ("train_b512: 100k x 3x128x128 uint8 ring (4.9 GB), batch 512, UTD 4 per step, shift pad 8, "
+                   "squint 4x to 32x32, 4 conv x 32ch, proj 256 + LN, critics 512-512 x2 (101 atoms), actor 512-512",
+                   "inputs larger than L2: 4.9 GB ring, 50 MB of uniformly random frames per update; "
+                   "weights and activations stay L2-resident between updates as in training"),
+    "stored_b512": ("stored_b512: squint at insert, 1M x 3x32x32 uint8 ring (3.1 GB) filled from 3x128x128 "
+                    "renders by the insert kernel, batch 512, UTD 4 per step, shift pad 2 at 32x32, 4 conv x "
+                    "32ch, proj 256 + LN, critics 512-512 x2 (101 atoms), actor 512-512",
+                    "inputs larger than L2: 3.1 GB ring, 3.1 MB of uniformly random frames per update; "
+                    "weights and activations stay L2-resident between updates as in training"),
+    "state_b512": ("state_b512: state-based SAC (no encoder), 1M x 48-d state ring (0.2 GB with actions, "
+                   "rewards, dones), batch 512, UTD 4 per step, critics 512-512 x2 (101 atoms), actor 512-512",
+                   "inputs larger than L2: 0.2 GB ring, 0.2 MB of uniformly random rows per update; "
+                   "weights and activations stay L2-resident between updates as in training"),
 }
 
 
@@ -54,8 +71,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--workload", choices=["train_b512", "stored_b512"], default=WORKLOAD,
-                    help="stored_b512: squint at insert, a 1M-slot ring of 3x32x32 frames filled by the insert kernel")
+    ap.add_argument("--workload", choices=["train_b512", "stored_b512", "state_b512"], default=WORKLOAD,
+                    help="stored_b512: squint at insert, a 1M-slot ring of 3x32x32 frames filled by the insert "
+                         "kernel; state_b512: state-based SAC, no encoder, a 1M-slot ring of 48-d states")
     ap.add_argument("--ring-slots", type=int, default=None,
                     help="replay-ring slots (default: the workload's 100k; smaller only for profiler captures)")
     return ap.parse_args()
@@ -365,7 +383,7 @@ def run_ours(args):
     dom = ranked[0]
     roof = class_roof(dom, kernels[dom])
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = NCU_TRAFFIC.get((dom, args.precision))
+    roof["traffic"] = NCU_TRAFFIC.get((dom, args.precision, args.workload))
     roof["kernel"] = dom
     roof["launches_per_update"] = kernels[dom]["launches"]
     roof["work_per_launch"] = kernels[dom]["work"] / kernels[dom]["launches"]
@@ -422,19 +440,9 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3+bf16"}[args.precision], "data": "synthetic",
-            "config": {"workload": (
-                           "train_b512: 100k x 3x128x128 uint8 ring (4.9 GB), batch 512, UTD 4 per step, shift pad 8, "
-                           "squint 4x to 32x32, 4 conv x 32ch, proj 256 + LN, critics 512-512 x2 (101 atoms), "
-                           "actor 512-512") if not stored else (
-                           "stored_b512: squint at insert, 1M x 3x32x32 uint8 ring (3.1 GB) filled from 3x128x128 "
-                           "renders by the insert kernel, batch 512, UTD 4 per step, shift pad 2 at 32x32, 4 conv x "
-                           "32ch, proj 256 + LN, critics 512-512 x2 (101 atoms), actor 512-512"),
+            "config": {"workload": WORKLOAD_TEXT[args.workload][0],
                        "updates_per_step": UTD_K, "precision": args.precision,
-                       "l2": (("inputs larger than L2: 4.9 GB ring, 50 MB of uniformly random frames per update; "
-                               "weights and activations stay L2-resident between updates as in training")
-                              if not stored else
-                              ("inputs larger than L2: 3.1 GB ring, 3.1 MB of uniformly random frames per update; "
-                               "weights and activations stay L2-resident between updates as in training")),
+                       "l2": WORKLOAD_TEXT[args.workload][1],
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
@@ -492,7 +500,8 @@ def measure_serving(lib, learner, cfg, upd_stream, seconds=4.0, n_envs=4096, mea
             if tickets[g] is None:
                 if now >= next_t[g]:
                     a, b = int(offs[g]), int(offs[g + 1])
-                    req = lib.Learner.request(obs[a:b], prop[a:b], out[a:b], key=key, group_id=g)
+                    req = lib.Learner.request(None if obs is None else obs[a:b], prop[a:b], out[a:b], key=key,
+                                              group_id=g)
                     tickets[g] = learner.serve_submit(req)
                     key += 1
             else:

@@ -64,7 +64,11 @@ typedef struct {
     int32_t squint_f;                /* area-downsampling factor (obs_h % squint_f == 0) */
     int32_t shift_pad;               /* random-shift pad p: crops at offsets in [0, 2p] */
     int32_t proprio_dim, action_dim;
-    int32_t conv_layers, conv_ch;    /* valid 3x3 convs, ReLU after each */
+    int32_t conv_layers, conv_ch;    /* valid 3x3 convs, ReLU after each.  conv_layers = 0:
+                                        state-based SAC (Sec. VII, Fig. 6 left): no image and
+                                        no encoder, the heads read the proprio_dim-wide state
+                                        (>= 1); needs proj_dim = 0; obs_c, obs_h, obs_w,
+                                        squint_f, shift_pad and conv_ch are then ignored */
     int32_t conv_stride[SQUINT_MAX_CONV];
     int32_t proj_dim;                /* 0: flatten straight into the heads */
     int32_t n_hidden;                /* hidden layers per MLP */
@@ -94,7 +98,7 @@ typedef struct {
  * Slot i holds the transition (o_i, s_i, a_i, r_i, d_i); its next observation is
  * slot (i + 1) mod n (Alg. 1 stores (o_t, s_t, a_t, r_t, o_{t+1}, s_{t+1})). */
 typedef struct {
-    const uint8_t* obs;      /* device [n, obs_c, obs_h, obs_w] uint8 */
+    const uint8_t* obs;      /* device [n, obs_c, obs_h, obs_w] uint8 (NULL if conv_layers = 0) */
     const float* proprio;    /* device [n, proprio_dim] */
     const float* action;     /* device [n, action_dim] in [-1, 1] */
     const float* reward;     /* device [n] */
@@ -196,7 +200,8 @@ typedef struct {
     int32_t n;               /* environments (rows), >= 1 */
     int32_t mode;            /* 0: sample a = tanh(mu + sigma eps); 1: mean tanh(mu) */
     uint64_t rng_key;        /* noise of row r = Philox block (r, act stream, rng_key) */
-    const uint8_t* obs;      /* device [n, obs_c, obs_h, obs_w] uint8 render-resolution frames */
+    const uint8_t* obs;      /* device [n, obs_c, obs_h, obs_w] uint8 render-resolution frames
+                                (NULL if conv_layers = 0) */
     const float* proprio;    /* device [n, proprio_dim] */
     float* actions;          /* device [n, action_dim] output in (-1, 1) */
 } squint_act_request;

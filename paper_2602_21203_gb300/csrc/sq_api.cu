@@ -33,18 +33,27 @@ static int64_t add_lin(Layout& L, int64_t off, Lin& l, int in, int out, bool ln)
 }
 
 bool build_layout(const squint_config& c, Layout& L) {
-    if (c.obs_c < 1 || c.obs_h < 1 || c.obs_w < 1 || c.squint_f < 1) return false;
-    if (c.obs_h % c.squint_f || c.obs_w % c.squint_f) return false;
-    if (c.conv_layers < 1 || c.conv_layers > SQUINT_MAX_CONV || c.conv_ch < 1) return false;
+    // conv_layers == 0: state-based SAC (Sec. VII, Fig. 6 left), no image and no encoder;
+    // the heads read the state vector (proprio_dim wide) and the observation fields are unused
+    const bool state_based = c.conv_layers == 0;
+    if (state_based) {
+        if (c.proj_dim != 0 || c.proprio_dim < 1) return false;
+    } else {
+        if (c.obs_c < 1 || c.obs_h < 1 || c.obs_w < 1 || c.squint_f < 1) return false;
+        if (c.obs_h % c.squint_f || c.obs_w % c.squint_f) return false;
+        if (c.conv_layers < 1 || c.conv_layers > SQUINT_MAX_CONV || c.conv_ch < 1) return false;
+    }
     if (c.n_hidden < 1 || c.n_hidden > SQUINT_MAX_HIDDEN || c.n_critics != 2) return false;
     if (c.atoms < 2 || c.atoms > 256 || c.action_dim < 1 || c.proprio_dim < 0 || c.proj_dim < 0) return false;
     if (c.critic_kind < 0 || c.critic_kind > 1 || c.cdq < 0 || c.cdq > 1) return false;
     if (c.batch < 1 || c.policy_freq < 1 || c.shift_pad < 0) return false;
     if (!(c.v_max > c.v_min)) return false;
     L = Layout{};
-    int cin = c.obs_c, h = c.obs_h / c.squint_f, w = c.obs_w / c.squint_f;
+    int cin = state_based ? 0 : c.obs_c, h = state_based ? 0 : c.obs_h / c.squint_f,
+        w = state_based ? 0 : c.obs_w / c.squint_f;
     L.hs = h;
     L.ws = w;
+    L.img_c = cin;
     int64_t off = 0;
     for (int l = 0; l < c.conv_layers; ++l) {
         ConvL cv;
@@ -214,8 +223,8 @@ int squint_create(const squint_config* cfg, const squint_replay* ring, squint_ha
 
 int squint_set_replay(squint_handle* h, const squint_replay* ring) {
     if (!h || !ring) return SQUINT_EINVAL;
-    if (ring->n < 2 || ring->n > 0xFFFFFFFFll || !ring->obs || !ring->proprio || !ring->action || !ring->reward ||
-        !ring->done)
+    if (ring->n < 2 || ring->n > 0xFFFFFFFFll || (!ring->obs && !h->L.conv.empty()) || !ring->proprio ||
+        !ring->action || !ring->reward || !ring->done)
         return SQUINT_EINVAL;
     h->ring = *ring;
     h->has_ring = true;

@@ -5,6 +5,9 @@
 // image from integer f x f box sums over the replicate-padded, shifted frame
 // (Sec. IV "Resolution Squinting": area downsampling; the shift is the
 // DrQ-style random-shift augmentation).
+#include <algorithm>
+#include <mutex>
+
 #include "sq_kernels.cuh"
 
 namespace sq {
@@ -31,7 +34,7 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
     {
     __shared__ uint64_t bar;
     // the whole frame in one TMA bulk copy when aligned (most bytes in flight per SM)
-    const bool bulk = (fbytes & 15) == 0 && fbytes < (1 << 20) && (((uintptr_t)src) & 15) == 0;
+    const bool bulk = fbytes > 0 && (fbytes & 15) == 0 && fbytes < (1 << 20) && (((uintptr_t)src) & 15) == 0;
     if (bulk) {
         if (threadIdx.x == 0) {
             bulk_load_init(&bar);
@@ -221,10 +224,15 @@ void launch_squint_store(const uint8_t* src, int n, int C, int H, int W, int f, 
 }
 
 // Opt the kernels in to a whole frame of dynamic shared memory (with the kernel's own
-// static shared memory a 48 KiB frame is already above the default limit).
+// static shared memory a 48 KiB frame is already above the default limit).  The limit is a
+// per-function attribute shared by every handle of the process, so it only ever grows.
 void frontend_prepare(size_t frame_bytes) {
-    cudaFuncSetAttribute(frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
-    cudaFuncSetAttribute(act_frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)frame_bytes);
+    static std::mutex mu;
+    static size_t granted = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    granted = std::max(granted, frame_bytes);
+    cudaFuncSetAttribute(frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)granted);
+    cudaFuncSetAttribute(act_frontend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)granted);
     // all of the unified L1 / shared memory as shared: as many whole frames in flight per SM as fit
     cudaFuncSetAttribute(frontend_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     cudaFuncSetAttribute(act_frontend_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -37,6 +37,7 @@ struct ConvL { int cin, cout, h, w, oh, ow, s; int64_t wo, bo; };
 // Canonical flat parameter layout (offsets in floats).
 struct Layout {
     int hs = 0, ws = 0;
+    int img_c = 0;                        // channels of the training image (0: state-based, no image)
     std::vector<ConvL> conv;
     int feat = 0, D = 0, zdim = 0, dc = 0, da = 0;
     Lin cproj, aproj;

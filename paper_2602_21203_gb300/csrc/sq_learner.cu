@@ -93,6 +93,7 @@ bool GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64
 
 void GemmBuilder::dx(const Mat* dY, const LayerRef* W, int n_pairs, int rows, int col0, int ncols, float* dX,
                      int64_t ldx, const float* mask, int64_t ldm) {
+    if (ncols <= 0 || rows <= 0) return;           // no input columns wanted (state-based: no features)
     flops_ += 2.0 * rows * ncols * W[0].out * n_pairs;
     kind_ = bf_ ? "tc_gemm_dx" : "gemm_f32_dx";
     if (!bf_) {
@@ -376,7 +377,7 @@ int squint_handle::allocate() {
     d_do_actor = dalloc<int32_t>(1);
     d_err = dalloc<int32_t>(1);
     d_stats = dalloc<float>((int64_t)c.max_k * 8);
-    const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
+    const int64_t img = (int64_t)L.img_c * L.hs * L.ws;
     x2 = dalloc<float>(2 * B * img);
     sums = dalloc<uint16_t>(2 * B * img);
     idx2 = dalloc<int32_t>(2 * B);
@@ -589,7 +590,7 @@ int squint_handle::allocate() {
         SQ_CK(this, cudaEventCreateWithFlags(&policy_released[i], cudaEventDisableTiming));
     }
     SQ_CK(this, cudaEventCreateWithFlags(&req_event, cudaEventDisableTiming));
-    frontend_prepare((size_t)c.obs_c * c.obs_h * c.obs_w);
+    frontend_prepare(L.conv.empty() ? 0 : (size_t)c.obs_c * c.obs_h * c.obs_w);
 
     std::vector<float> p;
     init_params_host(c, L, p);
@@ -697,6 +698,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         launch_ln_bwd(p, n, ln_work, st);
     };
     auto adam = [&](int64_t begin, int64_t end, const int32_t* step, const int32_t* enable, cudaStream_t st) {
+        if (end <= begin) return;                  // empty range (state-based: no encoder)
         AdamArgs ad{};
         ad.p = W + begin; ad.g = G + begin; ad.m = adam_m + begin; ad.v = adam_v + begin;
         ad.n = end - begin;
@@ -713,6 +715,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     fa.obs = ring.obs; fa.proprio = ring.proprio; fa.action = ring.action; fa.reward = ring.reward; fa.done = ring.done;
     fa.n_slots = ring.n;
     fa.C = c.obs_c; fa.H = c.obs_h; fa.W = c.obs_w; fa.f = c.squint_f; fa.pad = c.shift_pad;
+    if (L.conv.empty()) { fa.C = 0; fa.H = fa.W = fa.f = 1; fa.pad = 0; }   // state-based: no image
     fa.P = P; fa.A = A; fa.B = B;
     fa.seed = c.seed; fa.update_idx = d_update_idx;
     fa.x = x2; fa.x_bf = nullptr; fa.sums = debug ? sums : nullptr;
@@ -727,8 +730,11 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     fa.n_dst = 6;
     fa.steps = d_steps; fa.do_actor = d_do_actor; fa.policy_freq = c.policy_freq; fa.err = d_err;
     {
-        const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
-        ProfScope ps(this, s, "frontend", 2.0 * B * c.obs_c * c.obs_h * c.obs_w + 2.0 * B * img * 4, 1);
+        // frames read and squinted images written, plus the transition rows gathered
+        // (s_t, s_{t+1}, a_t, r, d) and written into the head inputs (with BF16 shadows)
+        const int64_t img = (int64_t)L.img_c * L.hs * L.ws;
+        const double trans = B * (4.0 * (2 * P + A + 1) + 1 + (5.0 * P + A) * (bf16 ? 6.0 : 4.0) + 8.0);
+        ProfScope ps(this, s, "frontend", 2.0 * B * fa.C * fa.H * fa.W + 2.0 * B * img * 4 + trans, 1);
         launch_frontend(fa, s);
     }
 
@@ -778,8 +784,8 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             in = conv_out[l];
         }
     }
-    float* z = conv_out.back();                // [2B, F]
-    if (!tc_conv) cast_rows(z, F, 2 * B, F, z_h, F, s);
+    float* z = nconv ? conv_out.back() : nullptr;   // [2B, F] (state-based: F = 0, no features)
+    if (!tc_conv && F > 0) cast_rows(z, F, 2 * B, F, z_h, F, s);
     const Mat zt{z, F, z_h, F};
     const Mat zt1 = zt.rows(B);
 
@@ -812,7 +818,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             lp[i] = p;
         }
         ln_fwd(lp, 4, false, s);
-    } else {
+    } else if (F > 0) {
         const size_t fb = (size_t)F * sizeof(float);
         cudaMemcpy2DAsync(xa, Da * sizeof(float), zt1.f, fb, fb, B, cudaMemcpyDeviceToDevice, s);
         cudaMemcpy2DAsync(xa + (int64_t)B * Da, Da * sizeof(float), z, fb, fb, B, cudaMemcpyDeviceToDevice, s);

@@ -121,7 +121,8 @@ int squint_serve_submit(squint_handle* h, const squint_act_request* req, uint64_
         g_last_error = "request larger than the admission limits";
         return SQUINT_EINVAL;
     }
-    if (!req->obs || !req->proprio || !req->actions || (req->mode != 0 && req->mode != 1)) return SQUINT_EINVAL;
+    if ((!req->obs && !h->L.conv.empty()) || !req->proprio || !req->actions || (req->mode != 0 && req->mode != 1))
+        return SQUINT_EINVAL;
     {
         std::lock_guard<std::mutex> lk(st->mu);
         if (st->stop) return SQUINT_ESTATE;

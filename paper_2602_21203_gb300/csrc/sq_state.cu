@@ -57,7 +57,7 @@ int squint_handle::load_state(const uint8_t* in) {
 
 int squint_handle::debug_tensor(const char* name, void* host, size_t* bytes) {
     const int B = c.batch, A = c.action_dim, K = c.critic_kind == 1 ? 1 : c.atoms;
-    const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
+    const int64_t img = (int64_t)L.img_c * L.hs * L.ws;
     const std::string n(name);
     const void* src = nullptr;
     size_t sz = 0;
@@ -78,7 +78,7 @@ int squint_handle::debug_tensor(const char* name, void* host, size_t* bytes) {
     else if (n == "dxq") { src = dxq; sz = 4 * (size_t)B * L.dc; }
     else if (n == "a_pi") { src = nullptr; sz = 4 * (size_t)B * A; }
     else if (n == "grads") { src = grads; sz = 4 * (size_t)L.total; }
-    else if (n == "z_t") { src = conv_out.back(); sz = 4 * (size_t)B * L.feat; }
+    else if (n == "z_t") { src = conv_out.empty() ? nullptr : conv_out.back(); sz = 4 * (size_t)B * L.feat; }
     else if (n == "target") { src = target; sz = 4 * (size_t)L.target_n; }
     else { g_last_error = "unknown debug tensor"; return SQUINT_EINVAL; }
     if (!host) { *bytes = sz; return SQUINT_OK; }
@@ -91,7 +91,7 @@ int squint_handle::debug_tensor(const char* name, void* host, size_t* bytes) {
                                  A * sizeof(float), B, cudaMemcpyDeviceToHost));
         return SQUINT_OK;
     }
-    SQ_CK(this, cudaMemcpy(host, src, sz, cudaMemcpyDeviceToHost));
+    if (sz) SQ_CK(this, cudaMemcpy(host, src, sz, cudaMemcpyDeviceToHost));
     return SQUINT_OK;
 }
 
@@ -110,7 +110,7 @@ int squint_handle::refresh_policy(cudaStream_t s) {
 
 // ---------------------------------------------------------------- inference
 size_t squint_handle::act_row_bytes() const {
-    size_t f = (size_t)c.obs_c * L.hs * L.ws;
+    size_t f = (size_t)L.img_c * L.hs * L.ws;
     for (const auto& cv : L.conv) f += (size_t)cv.cout * cv.oh * cv.ow;
     f += (size_t)L.D + 2 + L.da;
     for (int l = 0; l < c.n_hidden; ++l) f += 2 * (size_t)c.hidden[l] + 2;
@@ -132,7 +132,7 @@ int squint_handle::ensure_act_capacity(int rows, int n_reqs) {
         act_allocs.push_back(p);
         return p;
     };
-    const int64_t img = (int64_t)c.obs_c * L.hs * L.ws;
+    const int64_t img = (int64_t)L.img_c * L.hs * L.ws;
     ax = (float*)al(sizeof(float) * cap * img);
     aconv.clear();
     for (const auto& cv : L.conv) aconv.push_back((float*)al(sizeof(float) * (size_t)cap * cv.cout * cv.oh * cv.ow));
@@ -185,7 +185,7 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
     int rows = 0;
     for (int q = 0; q < n_reqs; ++q) {
         const squint_act_request& rq = reqs[q];
-        if (rq.n < 1 || !rq.obs || !rq.proprio || !rq.actions || (rq.mode != 0 && rq.mode != 1)) {
+        if (rq.n < 1 || (!rq.obs && !L.conv.empty()) || !rq.proprio || !rq.actions || (rq.mode != 0 && rq.mode != 1)) {
             g_last_error = "invalid inference request";
             return SQUINT_EINVAL;
         }
@@ -230,6 +230,7 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
     af.prop = reinterpret_cast<const float* const*>(d64 + req_cap);
     af.row_req = d_row_req; af.row_in_req = d_row_in;
     af.rows = rows; af.C = c.obs_c; af.H = c.obs_h; af.W = c.obs_w; af.f = c.squint_f; af.P = c.proprio_dim;
+    if (L.conv.empty()) { af.C = 0; af.H = af.W = af.f = 1; }   // state-based: no image
     af.x = ax; af.xin = axin; af.ld_xin = Da; af.col = L.zdim;
     launch_act_frontend(af, s);
     // BF16 policy: layer-0 conv on CUDA cores, the 32-channel convs and every linear
@@ -265,7 +266,7 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
         launch_conv_fwd<float>(sh, in, Wp + cv.wo, Wp + cv.bo, aconv[l], true, s);
         in = aconv[l];
     }
-    if (bf16 && !tc) {
+    if (bf16 && !tc && F > 0) {
         CastItem ci{in, F, rows, F, az_h, F};
         launch_cast_rows(&ci, 1, s);
     }
@@ -291,7 +292,7 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
         p.g = Wp + L.aproj.g; p.beta = Wp + L.aproj.beta;
         p.out = axin; p.ld_out = Da; p.mean = amean; p.rstd = arstd;
         launch_ln_fwd(&p, 1, false, (float)c.ln_eps, s);
-    } else {
+    } else if (F > 0) {
         SQ_CK(this, cudaMemcpy2DAsync(axin, Da * sizeof(float), in, F * sizeof(float), F * sizeof(float), rows,
                                       cudaMemcpyDeviceToDevice, s));
     }

@@ -158,7 +158,7 @@ def _check(code, what):
 
 
 def _ptr(t):
-    return ctypes.c_void_p(t.data_ptr())
+    return ctypes.c_void_p(None if t is None else t.data_ptr())
 
 
 def _stream(stream):
@@ -176,7 +176,7 @@ def make_config(cfg, precision=PREC_FP32, max_k=None):
     for k in ("obs_c", "obs_h", "obs_w", "squint_f", "shift_pad", "proprio_dim", "action_dim", "conv_layers",
               "conv_ch", "proj_dim", "n_critics", "atoms", "batch", "policy_freq"):
         setattr(c, k, int(cfg[k]))
-    strides = cfg.get("conv_strides") or [2] + [1] * (cfg["conv_layers"] - 1)
+    strides = (cfg.get("conv_strides") or [2] + [1] * (cfg["conv_layers"] - 1)) if cfg["conv_layers"] > 0 else []
     for i, s in enumerate(strides):
         c.conv_stride[i] = int(s)
     c.n_hidden = len(cfg["hidden"])
@@ -220,8 +220,9 @@ class Learner:
 
     def _replay(self, ring):
         self._ring = ring     # keep the tensors alive
-        return Replay(_ptr(ring["obs"]), _ptr(ring["proprio"]), _ptr(ring["action"]), _ptr(ring["reward"]),
-                      _ptr(ring["done"]), int(ring["obs"].shape[0]))
+        obs = ring.get("obs")     # absent for state-based SAC (conv_layers = 0)
+        return Replay(_ptr(obs), _ptr(ring["proprio"]), _ptr(ring["action"]), _ptr(ring["reward"]),
+                      _ptr(ring["done"]), int(ring["proprio"].shape[0]))
 
     def set_replay(self, ring):
         _check(self.lib.squint_set_replay(self.h, ctypes.byref(self._replay(ring))), "squint_set_replay")
@@ -301,7 +302,7 @@ class Learner:
     @staticmethod
     def request(obs, proprio, actions, key, sample=True, group_id=0):
         """An ActRequest over caller-owned device tensors (obs uint8 [n,C,H,W], proprio f32 [n,P], actions f32 [n,A])."""
-        return ActRequest(int(group_id), int(obs.shape[0]), 0 if sample else 1, int(key), _ptr(obs),
+        return ActRequest(int(group_id), int(proprio.shape[0]), 0 if sample else 1, int(key), _ptr(obs),
                           _ptr(proprio), _ptr(actions))
 
     def act(self, requests, stream=None):
