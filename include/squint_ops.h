@@ -66,6 +66,33 @@ int squint_op_gemm_fp8(int M, int N, int K, const void* A, int64_t lda, const vo
                        int64_t ldc, const float* bias, void* work, size_t work_bytes, void* stream);
 
 /*
+ * MX-FP8 (block-scaled e4m3; OCP Microscaling format: one power-of-two scale per 32
+ * consecutive elements of a row), the finer-grained form of the reduced-precision
+ * forward layers.
+ *
+ * squint_op_quantize_mxfp8: BF16 src [rows, cols] (row stride ld >= cols) -> e4m3 codes
+ * dst [rows, dst_ld] (dst_ld >= cols, a multiple of 16; columns cols .. dst_ld-1 zero)
+ * and UE8M0 scale bytes `sf` (squint_op_mx_scale_bytes(rows, cols) bytes).  Block j of
+ * row r (columns 32 j .. 32 j + 31) gets e = the smallest integer with
+ * max|x| <= 448 2^e (448 = largest finite e4m3; e >= -127, e = -127 for an all-zero
+ * block), byte e + 127 at sf[((r / 128) ceil(cols / 128) + j / 4) 512 + (r % 32) 16 +
+ * ((r % 128) / 32) 4 + j % 4], and codes e4m3(x 2^-e) rounded to nearest even; scale
+ * bytes of rows rows .. 128 ceil(rows / 128) - 1 are zero.  Bit-exact.
+ *
+ * squint_op_gemm_mxfp8: C[m, n] = sum_k 2^(ea(m, k/32) + eb(n, k/32)) A(m, k) B(n, k)
+ * + bias[n] for e4m3 A [M, K] (row stride lda), B [N, K] (ldb) with scale bytes sfa,
+ * sfb laid out as above (rows of A: M, rows of B: N, cols: K), FP32 accumulation on
+ * tcgen05 (kind::mxf8f6f4, block-scaled MMAs).  A, B 16-byte aligned, lda, ldb
+ * multiples of 16; bias may be NULL.  All pointers are caller-owned device memory;
+ * both calls are asynchronous on `stream`.  SQUINT_EINVAL on bad sizes or alignment.
+ */
+int64_t squint_op_mx_scale_bytes(int rows, int cols);
+int squint_op_quantize_mxfp8(int rows, int cols, const void* src, int64_t ld, void* dst, int64_t dst_ld, void* sf,
+                             void* stream);
+int squint_op_gemm_mxfp8(int M, int N, int K, const void* A, int64_t lda, const void* sfa, const void* B, int64_t ldb,
+                         const void* sfb, float* C, int64_t ldc, const float* bias, void* stream);
+
+/*
  * Squint at insert (Alg. 1 stores the transition with Downsample(o); Sec. IV
  * "Resolution Squinting": area downsampling): n uint8 frames src [n, C, H, W]
  * (H, W multiples of f) become their f x f area means rounded half up,

@@ -148,6 +148,39 @@ int squint_op_gemm_fp8(int M, int N, int K, const void* A, int64_t lda, const vo
     return launch_status();
 }
 
+int64_t squint_op_mx_scale_bytes(int rows, int cols) {
+    if (rows < 0 || cols < 0) return -1;
+    return mx_scale_bytes(rows, cols);
+}
+
+int squint_op_quantize_mxfp8(int rows, int cols, const void* src, int64_t ld, void* dst, int64_t dst_ld, void* sf,
+                             void* stream) {
+    if (rows < 0 || cols < 1 || ld < cols || dst_ld < cols || (dst_ld % 16) || (rows > 0 && (!src || !dst || !sf)))
+        return SQUINT_EINVAL;
+    if (rows == 0) return SQUINT_OK;
+    QuantItem q{(const __nv_bfloat16*)src, ld, rows, cols, (uint8_t*)dst, dst_ld, nullptr, (uint8_t*)sf};
+    launch_quantize_mx(&q, 1, (cudaStream_t)stream);
+    return launch_status();
+}
+
+int squint_op_gemm_mxfp8(int M, int N, int K, const void* A, int64_t lda, const void* sfa, const void* B, int64_t ldb,
+                         const void* sfb, float* C, int64_t ldc, const float* bias, void* stream) {
+    if (M < 0 || N < 0 || K < 1 || !A || !B || !C || !sfa || !sfb || lda < K || ldb < K || ldc < N || (lda % 16) ||
+        (ldb % 16) || (reinterpret_cast<uintptr_t>(A) & 15) || (reinterpret_cast<uintptr_t>(B) & 15))
+        return SQUINT_EINVAL;
+    if (M == 0 || N == 0) return SQUINT_OK;
+    TcGemm g{};
+    g.M = M; g.N = N; g.K = K; g.n_pairs = 1;
+    g.a[0] = TcOperand{A, lda, false};
+    g.b[0] = TcOperand{B, ldb, false};
+    g.bias = bias; g.c = C; g.ldc = ldc;
+    g.fp8 = 2; g.sf_a = (const uint8_t*)sfa; g.sf_b = (const uint8_t*)sfb;
+    int* err = tc_error_flag();
+    if (!err) return SQUINT_ECUDA;
+    if (launch_tc_gemm(&g, 1, err, (cudaStream_t)stream) != 0) return SQUINT_EINVAL;
+    return launch_status();
+}
+
 int squint_op_squint_store(int n, int C, int H, int W, int f, const void* src, void* ring, int64_t slot0,
                            int64_t n_slots, void* stream) {
     if (n < 0 || C < 1 || f < 1 || H < f || W < f || (H % f) || (W % f) || n_slots < 1 || slot0 < 0 ||

@@ -36,6 +36,13 @@ constexpr int BM = 128, BN = 128, BK = 64, STAGES = 6;
 constexpr int TILE_BYTES = BM * BK * 2;                // 16 KB per operand per stage
 constexpr int STAGE_BYTES = 2 * TILE_BYTES;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256 + BN * 4 + (2 * BN + 4 * BM) * 4;
+// MX-FP8: each stage also holds the A and B block-scale atoms (512 B each), after the
+// barriers and epilogue vectors (which take < 4 KB past the operand stages)
+constexpr int SF_ATOM = 512;
+constexpr int SF_OFF = STAGES * STAGE_BYTES + 4096;
+constexpr int SMEM_BYTES_MX = SF_OFF + STAGES * 2 * SF_ATOM + 1024;
+static_assert((2 * STAGES + 1) * 8 + 16 + (3 * BN + 4 * BM) * 4 <= 4096, "epilogue vectors overlap the scale atoms");
+static_assert(SMEM_BYTES_MX <= 232448, "shared memory above the per-CTA limit");
 constexpr int RED_LD = BN + 4;   // FP32 row stride of the accumulator tile in shared memory
 static_assert(BM * RED_LD * 4 <= STAGES * STAGE_BYTES, "accumulator tile must fit in the operand stages");
 constexpr long long kWaitCycles = 4000000000ll;        // ~2 s at 2 GHz
@@ -52,6 +59,8 @@ struct TcProb {
     const float* mask; int64_t ldmask;
     int accumulate;
     const float* scale_a; const float* scale_b;
+    const uint8_t* sf_a; const uint8_t* sf_b;   // MX block-scale atoms
+    int64_t sfa_tile, sfb_tile;                 // bytes per 128-row (column) tile of sf_a (sf_b)
     const float* ln_g; const float* ln_beta;
     float* ln_post; __nv_bfloat16* ln_posth;
     float* ln_mean; float* ln_rstd;
@@ -144,6 +153,42 @@ __device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
 }
+// Instruction descriptor of kind::mxf8f6f4 (block-scaled): e4m3 A and B, FP32 accumulator,
+// UE8M0 scales (bit 23), and the byte of each 32-bit scale column this MMA uses
+// (b_sf_id at bits 4-5, a_sf_id at bits 29-30): the 32-element K block within the slab.
+__host__ __device__ constexpr uint32_t idesc_mx(int M, int N, uint32_t sf_id) {
+    return (sf_id << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | (1u << 23) |
+           ((uint32_t)(M >> 4) << 24) | (sf_id << 29);
+}
+// D (+)= (A . 2^sfA) (B . 2^sfB)^T over K = 32, scales per row / column from tensor memory.
+__device__ __forceinline__ void mma_mx(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t sfa_tmem, uint32_t sfb_tmem, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::mxf8f6f4.block_scale.scale_vec::1X [%0], %1, %2, %3, [%4], [%5], p;\n}" ::"r"(
+            d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa_tmem), "r"(sfb_tmem), "r"(acc)
+        : "memory");
+}
+// Shared-memory descriptor of a 32-row x 16-byte block-scale atom without swizzle
+// (8-row core matrices of 128 contiguous bytes, 128 B apart).
+__device__ __forceinline__ uint64_t sf_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(128 >> 4) << 16;
+    d |= (uint64_t)(128 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// Copy a 32 x 128-bit scale atom from shared memory into tensor memory, repeated in each
+// of the four 32-lane quarters (lane r0 + 32 w, 4 columns: the scales of rows r0 + 32 c).
+__device__ __forceinline__ void sf_copy(uint32_t taddr, uint64_t sdesc) {
+    asm volatile("tcgen05.cp.cta_group::1.32x128b.warpx4 [%0], %1;" ::"r"(taddr), "l"(sdesc) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
@@ -184,12 +229,17 @@ __device__ __forceinline__ void load_operand(uint32_t dst, const CUtensorMap* ma
     }
 }
 
-// F8: e4m3 operands, 128-element (128-byte) K slabs, kind::f8f6f4 MMAs with K = 32, and
-// the per-tensor scales applied in the epilogue.  The K step of a slab is 32 bytes in
-// both types, so the shared-memory descriptors are the same.
-template <bool A_MN, bool B_MN, bool F8 = false>
+// F8 = 1: e4m3 operands, 128-element (128-byte) K slabs, kind::f8f6f4 MMAs with K = 32,
+// and the per-tensor scales applied in the epilogue.  The K step of a slab is 32 bytes in
+// both types, so the shared-memory descriptors are the same.  F8 = 2 (MX-FP8): the same
+// slabs with one UE8M0 scale per 32 elements of K per row of A and per column of B; each
+// stage brings the slab's scale atoms along, copies them into tensor memory (columns of
+// their own per stage) and the block-scaled MMAs apply them.
+template <bool A_MN, bool B_MN, int F8 = 0>
 __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__ TcBatch gb) {
+    constexpr bool MX = F8 == 2;
     constexpr int BKE = F8 ? 128 : BK;   // K elements per slab
+    constexpr uint32_t TMEM_COLS = MX ? 256 : BN;   // MX: accumulator + 6 stages x (4 + 4) scale columns
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -234,9 +284,14 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         const int s = i % STAGES;
         const int pr = (it0 + i) / nkb, kb = (it0 + i) % nkb;
         const uint32_t st = base + s * STAGE_BYTES;
-        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+        mbar_expect_tx(full0 + 8 * s, STAGE_BYTES + (MX ? 2 * SF_ATOM : 0));
         load_operand<A_MN>(st, &P.ta[pr], m0, kb * BKE, full0 + 8 * s);
         load_operand<B_MN>(st + TILE_BYTES, &P.tb[pr], n0, kb * BKE, full0 + 8 * s);
+        if constexpr (MX) {
+            const uint32_t sf = base + SF_OFF + s * 2 * SF_ATOM;
+            bulk_copy_s(sf, P.sf_a + (m0 / BM) * P.sfa_tile + (int64_t)kb * SF_ATOM, SF_ATOM, full0 + 8 * s);
+            bulk_copy_s(sf + SF_ATOM, P.sf_b + (n0 / BN) * P.sfb_tile + (int64_t)kb * SF_ATOM, SF_ATOM, full0 + 8 * s);
+        }
     };
 
     // CTA-local setup overlaps the tail of the previous kernel (programmatic launch)
@@ -260,7 +315,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         for (int i = 0; i < pre; ++i) load_stage(i);   // first stages: no slot to wait for
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(BN));
+                     "r"(TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -286,24 +341,44 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     } else if (issuer) {
         // MMA issuer
         constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN, A_MN, B_MN) : idesc_bf16(BM, BN, A_MN, B_MN);
-        bool ok = true;
-        for (int i = 0; i < total; ++i) {
-            const int s = i % STAGES;
-            if (!mbar_wait(full0 + 8 * s, (i / STAGES) & 1, gb.err, 2)) { ok = false; break; }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t st = base + s * STAGE_BYTES;
+        if constexpr (MX) {
+            for (int i = 0; i < total; ++i) {
+                const int s = i % STAGES;
+                if (!mbar_wait(full0 + 8 * s, (i / STAGES) & 1, gb.err, 2)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = base + s * STAGE_BYTES;
+                const uint32_t sf = base + SF_OFF + s * 2 * SF_ATOM;
+                const uint32_t sfa_t = tmem + BN + 8 * s, sfb_t = sfa_t + 4;
+                // scale copies and MMAs issued by one thread run in order
+                sf_copy(sfa_t, sf_desc(sf));
+                sf_copy(sfb_t, sf_desc(sf + SF_ATOM));
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk)
-                if constexpr (F8)
-                    mma_e4m3(tmem, operand_desc<A_MN>(st, kk), operand_desc<B_MN>(st + TILE_BYTES, kk), idesc,
-                             (i > 0 || kk > 0) ? 1u : 0u);
-                else
-                    mma_bf16(tmem, operand_desc<A_MN>(st, kk), operand_desc<B_MN>(st + TILE_BYTES, kk), idesc,
-                             (i > 0 || kk > 0) ? 1u : 0u);
-            mma_commit(empty0 + 8 * s);
+                for (int kk = 0; kk < 4; ++kk)
+                    mma_mx(tmem, operand_desc<false>(st, kk), operand_desc<false>(st + TILE_BYTES, kk),
+                           idesc_mx(BM, BN, (uint32_t)kk), sfa_t, sfb_t, (i > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(done_bar);
+        } else {
+            bool ok = true;
+            for (int i = 0; i < total; ++i) {
+                const int s = i % STAGES;
+                if (!mbar_wait(full0 + 8 * s, (i / STAGES) & 1, gb.err, 2)) { ok = false; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t st = base + s * STAGE_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk)
+                    if constexpr (F8)
+                        mma_e4m3(tmem, operand_desc<A_MN>(st, kk), operand_desc<B_MN>(st + TILE_BYTES, kk), idesc,
+                                 (i > 0 || kk > 0) ? 1u : 0u);
+                    else
+                        mma_bf16(tmem, operand_desc<A_MN>(st, kk), operand_desc<B_MN>(st + TILE_BYTES, kk), idesc,
+                                 (i > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(empty0 + 8 * s);
+            }
+            mma_commit(done_bar);
+            (void)ok;
         }
-        mma_commit(done_bar);
-        (void)ok;
     }
     __syncwarp();
 
@@ -337,6 +412,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         // in the tile; the cluster exchange is then one row per thread
         const int cq = lane * 4;
         const int nvl = n0 + cq < pN ? min(4, pN - n0 - cq) : 0;
+        // per-tensor FP8: the accumulator is scaled back before the bias, as in part 2
+        const float sc = F8 == 1 ? __ldg(p_sa) * __ldg(p_sb) : 1.f;
         auto row_pass = [&](float* dst, bool centred) {
 #pragma unroll 1
             for (int g = 0; g < BM / 4; g += 8) {
@@ -346,8 +423,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                     const int lr = warp + 4 * (g + i);
                     const float4 x = *reinterpret_cast<const float4*>(red + lr * RED_LD + cq);
                     const float mu = centred ? ln_mean_s[lr] : 0.f;
-                    const float v0 = x.x + bias_s[cq] - mu, v1 = x.y + bias_s[cq + 1] - mu;
-                    const float v2 = x.z + bias_s[cq + 2] - mu, v3 = x.w + bias_s[cq + 3] - mu;
+                    const float v0 = fmaf(x.x, sc, bias_s[cq]) - mu, v1 = fmaf(x.y, sc, bias_s[cq + 1]) - mu;
+                    const float v2 = fmaf(x.z, sc, bias_s[cq + 2]) - mu, v3 = fmaf(x.w, sc, bias_s[cq + 3]) - mu;
                     const float w0 = centred ? v0 * v0 : v0, w1 = centred ? v1 * v1 : v1;
                     const float w2 = centred ? v2 * v2 : v2, w3 = centred ? v3 * v3 : v3;
                     p[i] = ((nvl > 0 ? w0 : 0.f) + (nvl > 1 ? w1 : 0.f)) + ((nvl > 2 ? w2 : 0.f) + (nvl > 3 ? w3 : 0.f));
@@ -401,7 +478,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
         float bias4[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) bias4[j] = bias_s[cq + j];
-        const float fp8_scale = F8 ? __ldg(p_sa) * __ldg(p_sb) : 1.f;
+        const float fp8_scale = F8 == 1 ? __ldg(p_sa) * __ldg(p_sb) : 1.f;
         const float* mine = red + (rb0 + warp) * RED_LD + cq;   // row g of this warp at mine + 4 g RED_LD
 #pragma unroll 1
         for (int g0 = 0; g0 < nrows; g0 += 8) {
@@ -577,7 +654,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
 }
 
@@ -624,8 +701,11 @@ bool operand_map(CUtensorMap* m, const TcOperand& o, int mn_extent, int k_extent
 template <bool A_MN, bool B_MN>
 void set_smem_attr() {
     cudaFuncSetAttribute(tc_gemm_kernel<A_MN, B_MN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (!A_MN && !B_MN)
-        cudaFuncSetAttribute(tc_gemm_kernel<false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (!A_MN && !B_MN) {
+        cudaFuncSetAttribute(tc_gemm_kernel<false, false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        cudaFuncSetAttribute(tc_gemm_kernel<false, false, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM_BYTES_MX);
+    }
 }
 
 }  // namespace
@@ -678,13 +758,16 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, b
         gb.err = err;
         int tiles = 0, min_iters = 1 << 30;
         bool a_mn = probs[base].a[0].mn_major, b_mn = probs[base].b[0].mn_major;
-        const bool f8 = probs[base].fp8 != 0;
+        const int f8k = probs[base].fp8;
+        const bool f8 = f8k != 0;
         const bool ln = probs[base].ln_g != nullptr;
         for (int i = 0; i < gb.n; ++i) {
             const TcGemm& g = probs[base + i];
             TcProb& p = gb.p[i];
             if (g.a[0].mn_major != a_mn || g.b[0].mn_major != b_mn || g.n_pairs < 1 || g.n_pairs > 2) return -1;
-            if ((g.fp8 != 0) != f8 || (f8 && (g.n_pairs != 1 || a_mn || b_mn || !g.scale_a || !g.scale_b))) return -1;
+            if (g.fp8 != f8k || f8k < 0 || f8k > 2 || (f8 && (g.n_pairs != 1 || a_mn || b_mn)) ||
+                (f8k == 1 && (!g.scale_a || !g.scale_b)) || (f8k == 2 && (!g.sf_a || !g.sf_b)))
+                return -1;
             if ((g.ln_g != nullptr) != ln ||
                 (ln && (!g.ln_beta || !g.ln_post || !g.ln_mean || !g.ln_rstd || g.cbf || g.mask || g.accumulate ||
                         (g.N + BN - 1) / BN > g_max_splits || (g.N + BN - 1) / BN != (probs[base].N + BN - 1) / BN)))
@@ -697,6 +780,9 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, b
             p.bias = g.bias; p.c = g.c; p.ldc = g.ldc; p.cbf = g.cbf; p.ldcbf = g.ldcbf;
             p.mask = g.mask; p.ldmask = g.ldmask; p.accumulate = g.accumulate;
             p.scale_a = g.scale_a; p.scale_b = g.scale_b;
+            p.sf_a = g.sf_a; p.sf_b = g.sf_b;
+            p.sfa_tile = (int64_t)((g.K + 127) / 128) * SF_ATOM;
+            p.sfb_tile = p.sfa_tile;
             p.ln_g = g.ln_g; p.ln_beta = g.ln_beta; p.ln_post = g.ln_post; p.ln_posth = g.ln_posth;
             p.ln_mean = g.ln_mean; p.ln_rstd = g.ln_rstd; p.ln_eps = g.ln_eps; p.ln_relu = g.ln_relu;
             p.tiles_n = (g.N + BN - 1) / BN;
@@ -713,7 +799,8 @@ int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, b
         for (int i = 0; i < gb.n; ++i) gb.p[i].tile_start *= S;
         // LayerNorm mode: one cluster per row block, its CTAs the block's column tiles
         const dim3 grid(tiles * S), cluster(ln ? gb.p[0].tiles_n : S);
-        if (f8) launch_kc(tc_gemm_kernel<false, false, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
+        if (f8k == 2) launch_kc(tc_gemm_kernel<false, false, 2>, grid, dim3(128), SMEM_BYTES_MX, s, cluster, gb);
+        else if (f8) launch_kc(tc_gemm_kernel<false, false, 1>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
         else if (!a_mn && !b_mn) launch_kc(tc_gemm_kernel<false, false>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
         else if (!a_mn && b_mn) launch_kc(tc_gemm_kernel<false, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
         else if (a_mn && b_mn) launch_kc(tc_gemm_kernel<true, true>, grid, dim3(128), SMEM_BYTES, s, cluster, gb);
@@ -825,6 +912,74 @@ void launch_quantize_e4m3(const QuantItem* items, int n, float* part, cudaStream
         for (int i = 0; i < qb.n; ++i) qb.it[i] = items[base + i];
         launch_k(amax_kernel, dim3(kQuantBlocks, qb.n), dim3(256), 0, s, qb);
         launch_k(quantize_kernel, dim3(kQuantBlocks, qb.n), dim3(256), 0, s, qb);
+    }
+}
+
+// ---------------------------------------------------------------- MX-FP8 quantisation
+namespace {
+// One warp per (row, 128-column slab) of an item: lane l takes columns 4l .. 4l + 3 of the
+// slab, so a 32-element block is 8 lanes.  Block scale 2^e with e the smallest integer for
+// which max|x| <= 448 2^e (448: the largest finite e4m3 value), stored as the UE8M0 byte
+// e + 127 (e >= -127); codes e4m3(x 2^-e) rounded to nearest even.  Rows from the item's
+// end to its last 128-row tile only get zero scale bytes.
+__global__ void __launch_bounds__(256) quantize_mx_kernel(QuantBatch qb) {
+    SQ_KERNEL_ENTRY();
+    const QuantItem& q = qb.it[blockIdx.y];
+    const int slabs = (q.cols + 127) / 128;
+    const int tiles_r = (q.rows + 127) / 128;
+    const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    if (w >= tiles_r * 128 * slabs) return;
+    const int lane = threadIdx.x % 32;
+    const int r = w / slabs, slab = w - r * slabs;
+    const int j0 = slab * 128 + lane * 4;
+    float v[4] = {0.f, 0.f, 0.f, 0.f};
+    if (r < q.rows) {
+        const __nv_bfloat16* src = q.src + (int64_t)r * q.src_ld;
+        if ((q.src_ld & 3) == 0 && (reinterpret_cast<uintptr_t>(q.src) & 7) == 0 && j0 + 3 < q.cols) {
+            const uint2 u = *reinterpret_cast<const uint2*>(src + j0);
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+            v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                if (j0 + t < q.cols) v[t] = __bfloat162float(src[j0 + t]);
+        }
+    }
+    float m = fmaxf(fmaxf(fabsf(v[0]), fabsf(v[1])), fmaxf(fabsf(v[2]), fabsf(v[3])));
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    // m = 1.f 2^(eb - 127): 448 = 1.75 2^8, so e = eb - 135 if the fraction is <= 0.75, else eb - 134
+    const uint32_t bits = __float_as_uint(m);
+    const int eb = (int)(bits >> 23);
+    int e = eb == 0 ? -127 : ((bits & 0x7FFFFFu) <= 0x600000u ? eb - 135 : eb - 134);
+    e = max(e, -127);
+    if ((lane & 7) == 0) {
+        const int rr = r & 127;
+        q.sf[((int64_t)(r >> 7) * slabs + slab) * 512 + (rr & 31) * 16 + (rr >> 5) * 4 + (lane >> 3)] =
+            r < q.rows ? (uint8_t)(e + 127) : (uint8_t)0;
+    }
+    if (r >= q.rows || j0 >= q.dst_ld) return;
+    const float inv = __uint_as_float((uint32_t)(127 - e) << 23);   // 2^-e, exact
+    const uint32_t c = (uint32_t)to_e4m3(v[0] * inv) | ((uint32_t)to_e4m3(v[1] * inv) << 8) |
+                       ((uint32_t)to_e4m3(v[2] * inv) << 16) | ((uint32_t)to_e4m3(v[3] * inv) << 24);
+    *reinterpret_cast<uint32_t*>(q.dst + (int64_t)r * q.dst_ld + j0) = c;
+}
+}  // namespace
+
+int64_t mx_scale_bytes(int rows, int cols) { return (int64_t)((rows + 127) / 128) * ((cols + 127) / 128) * 512; }
+
+void launch_quantize_mx(const QuantItem* items, int n, cudaStream_t s) {
+    for (int base = 0; base < n; base += kQuantMaxItems) {
+        QuantBatch qb;
+        std::memset(&qb, 0, sizeof(qb));
+        qb.n = std::min(kQuantMaxItems, n - base);
+        int64_t warps = 0;
+        for (int i = 0; i < qb.n; ++i) {
+            qb.it[i] = items[base + i];
+            warps = std::max<int64_t>(warps, (int64_t)((qb.it[i].rows + 127) / 128) * 128 * ((qb.it[i].cols + 127) / 128));
+        }
+        if (warps) launch_k(quantize_mx_kernel, dim3((unsigned)((warps + 7) / 8), qb.n), dim3(256), 0, s, qb);
     }
 }
 

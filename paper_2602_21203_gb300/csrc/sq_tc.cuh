@@ -25,10 +25,14 @@ struct TcGemm {
     __nv_bfloat16* cbf; int64_t ldcbf;
     const float* mask; int64_t ldmask;
     int accumulate;           // c += D instead of c = D
-    // FP8: A and B are e4m3 (K-major, one pair) holding x / scale per tensor; D is
-    // scaled back by *scale_a * *scale_b before the bias (device scalars)
+    // fp8 = 1: A and B are e4m3 (K-major, one pair) holding x / scale per tensor; D is
+    // scaled back by *scale_a * *scale_b before the bias (device scalars).  fp8 = 2
+    // (MX-FP8): A and B are e4m3 with block scales sf_a / sf_b in the atoms written by
+    // launch_quantize_mx (per 32 elements of K of each row of A and of B), applied by the
+    // block-scaled MMAs (kind::mxf8f6f4).
     int fp8;
     const float* scale_a; const float* scale_b;
+    const uint8_t* sf_a; const uint8_t* sf_b;
     // LayerNorm of each output row fused into the epilogue (ln_g non-null): c receives
     // D + bias (the pre-activation), then y = (D - mean) rstd g + beta, ReLU if ln_relu,
     // goes to ln_post (FP32, row stride N) and ln_posth (BF16, row stride N), with the
@@ -52,12 +56,22 @@ struct QuantItem {
     int rows, cols;
     uint8_t* dst; int64_t dst_ld;   // dst_ld >= cols, a multiple of 16
     float* scale;
+    uint8_t* sf = nullptr;          // MX-FP8: block-scale atoms (launch_quantize_mx)
 };
 constexpr int kQuantMaxItems = 8;
 constexpr int kF8Scales = 64;         // activation scales per stream arena (FP8 learner)
 constexpr int kQuantBlocks = 64;      // row blocks per item in the amax pass
 int64_t quant_workspace();            // floats of `part`
 void launch_quantize_e4m3(const QuantItem* items, int n, float* part, cudaStream_t s);
+// MX-FP8 (block-scaled e4m3, OCP MX layout of one scale per 32 elements of a row): one
+// launch.  Per 32-element block of a row, scale 2^e with e the smallest integer such that
+// max|x| <= 448 2^e (e >= -127), UE8M0 byte e + 127; dst = e4m3(x 2^-e) rounded to
+// nearest even, pad columns zero.  The scale bytes go to `sf` in the atoms the GEMM
+// reads: for row r and 32-column block j, atom (r / 128) * ceil(cols / 128) + j / 4 of
+// 512 bytes, byte (r % 32) * 16 + ((r % 128) / 32) * 4 + j % 4 (rows up to the end of
+// the last 128-row tile get zero bytes).  mx_scale_bytes(rows, cols) bytes.
+int64_t mx_scale_bytes(int rows, int cols);
+void launch_quantize_mx(const QuantItem* items, int n, cudaStream_t s);
 
 // Launches one grouped kernel per up to 4 problems (all of one A/B majorness).  When
 // the launch has few output tiles and a long K, the K range of each tile is split over

@@ -105,6 +105,9 @@ def load():
         "squint_op_gemm_fp8_workspace": (SZ, [I, I, I]),
         "squint_op_gemm_layernorm": (I, [I, I, I, P, I64, P, I64, P, P, P, ctypes.c_float, I, P, P, P, P, P, P]),
         "squint_op_gemm_fp8": (I, [I, I, I, P, I64, P, I64, P, I64, P, P, SZ, P]),
+        "squint_op_mx_scale_bytes": (I64, [I, I]),
+        "squint_op_quantize_mxfp8": (I, [I, I, P, I64, P, I64, P, P]),
+        "squint_op_gemm_mxfp8": (I, [I, I, I, P, I64, P, P, I64, P, P, I64, P, P]),
         "squint_op_conv3x3_fwd": (I, [I, I, I, I, I, I, I, P, P, P, P, I, P]),
         "squint_op_conv3x3_workspace": (SZ, [I, I, I, I, I, I, I]),
         "squint_op_conv3x3_bwd": (I, [I, I, I, I, I, I, I, P, P, P, P, P, P, P, P, SZ, P]),

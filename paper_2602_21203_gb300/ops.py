@@ -100,6 +100,33 @@ def gemm_fp8(A, B, bias=None, out=None):
     return out, (scales[0], scales[1])
 
 
+def quantize_mxfp8(X):
+    """MX-FP8 codes and scale bytes of BF16 X [rows, cols] (row-major): returns (codes uint8
+    [rows, ceil16(cols)], sf uint8 [squint_op_mx_scale_bytes(rows, cols)])."""
+    _need(X, torch.bfloat16, "X")
+    rows, cols = X.shape
+    L = _lib.load()
+    ld8 = (cols + 15) // 16 * 16
+    codes = torch.empty(rows, ld8, dtype=torch.uint8, device=X.device)
+    sf = torch.empty(max(L.squint_op_mx_scale_bytes(rows, cols), 16), dtype=torch.uint8, device=X.device)
+    _chk(L.squint_op_quantize_mxfp8(rows, cols, _p(X), X.stride(0), _p(codes), codes.stride(0), _p(sf), _s()),
+         "squint_op_quantize_mxfp8")
+    return codes, sf
+
+
+def gemm_mxfp8(A8, sfa, B8, sfb, K, bias=None, out=None):
+    """out = dequant(A) dequant(B)^T + bias for MX-FP8 operands (codes [M, >=K], [N, >=K] with
+    their scale bytes from quantize_mxfp8)."""
+    M, N = A8.shape[0], B8.shape[0]
+    if out is None:
+        out = torch.empty(M, N, device=A8.device, dtype=torch.float32)
+    if bias is not None:
+        _need(bias, torch.float32, "bias")
+    _chk(_lib.load().squint_op_gemm_mxfp8(M, N, K, _p(A8), A8.stride(0), _p(sfa), _p(B8), B8.stride(0), _p(sfb),
+                                          _p(out), out.stride(0), _p(bias), _s()), "squint_op_gemm_mxfp8")
+    return out
+
+
 def conv3x3_fwd(x, w, b, stride, relu):
     n, cin, h, wd = x.shape
     cout = w.shape[0]

@@ -284,3 +284,21 @@ def test_fp8_update_runs_and_replays_bitwise(L):
     assert abs(st["critic_loss"] - ref["critic_loss"]) <= 5e-2 * abs(ref["critic_loss"])
     for x in (a, b, c):
         x.close()
+
+
+def test_fp8_with_fused_layernorm_matches_separate_layernorm(L, monkeypatch):
+    """The LayerNorm fused into the FP8 GEMM epilogue takes its row statistics from the
+    rescaled accumulator, like the separate LayerNorm kernel: same update up to rounding."""
+    cfg = synth.make_config("train_b512", ring_size=4096)
+    ring = synth.make_ring(cfg, 0, device="cuda")
+    a = L.Learner(cfg, ring, precision=L.PREC_FP8)
+    monkeypatch.setenv("SQUINT_FUSED_LN", "1")
+    b = L.Learner(cfg, ring, precision=L.PREC_FP8)
+    sa = a.update(1, graph=False)[0]
+    sb = b.update(1, graph=False)[0]
+    for k in ("critic_loss", "q_mean", "actor_loss", "entropy"):
+        assert abs(sa[k] - sb[k]) <= 1e-3 * max(abs(sa[k]), 1.0), (k, sa[k], sb[k])
+    ga, gb = a.debug("grads").astype(np.float64), b.debug("grads").astype(np.float64)
+    assert float(ga @ gb) / (np.linalg.norm(ga) * np.linalg.norm(gb)) > 0.999
+    a.close()
+    b.close()
