@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8"], default="bf16")
+    ap.add_argument("--precision", choices=["fp32", "bf16", "fp8", "mxfp8"], default="bf16")
     ap.add_argument("--no-fp32-compare", action="store_true",
                     help="skip timing the plain FP32 path beside the BF16 one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -274,7 +274,7 @@ def run_ours(args):
     if args.ring_slots:
         cfg["ring_size"] = int(args.ring_slots)
     stored = "render_f" in cfg
-    prec = {"fp32": lib.PREC_FP32, "bf16": lib.PREC_BF16, "fp8": lib.PREC_FP8}[args.precision]
+    prec = {"fp32": lib.PREC_FP32, "bf16": lib.PREC_BF16, "fp8": lib.PREC_FP8, "mxfp8": lib.PREC_MXFP8}[args.precision]
     ring = synth.make_ring(cfg, args.seed + rank, device="cuda")
     if stored:   # squint at insert: the ring's frames come from 3x128x128 renders through the insert kernel
         from paper_2602_21203_gb300 import ops
@@ -370,7 +370,7 @@ def run_ours(args):
             return {"bound": "hbm", "unit": "GB/s", "achieved": ach, "peak": peaks["hbm_gbs"],
                     "peak_source": f"{peaks_src} copy bandwidth"}
         ach = k["work"] / secs / 1e12
-        if name == "tc_gemm_fwd" and args.precision == "fp8":   # e4m3 operands: FP8 peak
+        if name == "tc_gemm_fwd" and args.precision in ("fp8", "mxfp8"):   # e4m3 operands: FP8 peak
             return {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": 2.0 * peaks["bf16_tflops"],
                     "peak_source": f"{peaks_src} bf16 burst x 2 (nominal fp8/bf16 dense ratio 4.5/2.25)"}
         if name.startswith("tc_") or name.startswith("conv_tc"):
@@ -439,7 +439,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3+bf16"}[args.precision], "data": "synthetic",
+            "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3+bf16", "mxfp8": "e4m3(mx)+bf16"}[args.precision],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload][0],
                        "updates_per_step": UTD_K, "precision": args.precision,
                        "l2": WORKLOAD_TEXT[args.workload][1],

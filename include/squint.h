@@ -49,6 +49,9 @@ extern "C" {
 #define SQUINT_PREC_BF16 1   /* BF16 operands, FP32 accumulation (tensor cores) */
 #define SQUINT_PREC_FP8 2    /* as BF16, with the forward linear layers in e4m3 (per-tensor
                                 scales, FP32 accumulation); backward and convs stay BF16 */
+#define SQUINT_PREC_MXFP8 3  /* as FP8, with MX block scales (one power of two per 32
+                                elements of K of each row of both operands, see
+                                squint_op_quantize_mxfp8) instead of per-tensor scales */
 
 /*
  * Learner configuration (plain data, copied at creation).

@@ -206,7 +206,7 @@ int squint_create(const squint_config* cfg, const squint_replay* ring, squint_ha
     }
     if (h->c.max_k < 1) h->c.max_k = 8;
     if (h->c.precision != SQUINT_PREC_FP32 && h->c.precision != SQUINT_PREC_BF16 &&
-        h->c.precision != SQUINT_PREC_FP8) {
+        h->c.precision != SQUINT_PREC_FP8 && h->c.precision != SQUINT_PREC_MXFP8) {
         delete h;
         return SQUINT_EINVAL;
     }

@@ -72,7 +72,8 @@ struct squint_handle {
     bool has_ring = false;
     bool failed = false;
     bool bf16 = false;                // tensor-core contractions (SQUINT_PREC_BF16 or FP8)
-    bool fp8 = false;                 // forward linear layers in e4m3 (SQUINT_PREC_FP8)
+    bool fp8 = false;                 // forward linear layers in e4m3 (SQUINT_PREC_FP8 or MXFP8)
+    bool mx = false;                  // ... with MX block scales (SQUINT_PREC_MXFP8)
     // hidden-layer LayerNorm in the GEMM epilogue (tensor-core path), chosen by
     // SQUINT_FUSED_LN=1 in the environment at creation; off by default: at batch 512 the
     // separate LayerNorm kernel gives more updates/s (1,310 vs 1,264 on the same GPU)
@@ -151,7 +152,7 @@ struct squint_handle {
     // FP8 mode: e4m3 copies of the linear weights (quantised from the BF16 copies after
     // every cast) and, per stream, an arena for the forward GEMMs' quantised activations
     struct LinF8 { uint8_t* on = nullptr; uint8_t* tg = nullptr; int64_t ld = 0; float* s_on = nullptr;
-                   float* s_tg = nullptr; };
+                   float* s_tg = nullptr; uint8_t* sf_on = nullptr; uint8_t* sf_tg = nullptr; };
     std::map<int64_t, LinF8> lin_f8;
     std::vector<sq::QuantItem> quant_critic, quant_actor, quant_target;
     float* f8_part = nullptr;             // amax partials of the weight quantisation

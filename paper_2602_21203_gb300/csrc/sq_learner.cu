@@ -71,18 +71,25 @@ bool GemmBuilder::fwd(const Mat& X, int rows, const LayerRef& W, float* Y, int64
     }
     if (h_->fp8 && W.w8 && X.h) {
         // FP8: quantise X (per tensor) into this stream's arena at flush, e4m3 weights
+        // (MX-FP8: the codes are followed by their block-scale atoms in the arena)
         squint_handle::F8Arena* ar = h_->arena_for(s_);
         const int64_t ld8 = (W.in + 15) / 16 * 16;
-        const int64_t bytes = (int64_t)rows * ld8;
+        const int64_t codes = ((int64_t)rows * ld8 + 255) / 256 * 256;
+        const int64_t sfb = h_->mx ? (mx_scale_bytes(rows, W.in) + 255) / 256 * 256 : 0;
         const int qi = (int)q8_.size();
-        if (ar->buf && arena_used_ + bytes <= ar->bytes && qi < kF8Scales) {
+        if (ar->buf && arena_used_ + codes + sfb <= ar->bytes && qi < kF8Scales && (!h_->mx || W.sf8)) {
             uint8_t* dst = ar->buf + arena_used_;
-            arena_used_ += (bytes + 255) / 256 * 256;
-            q8_.push_back(QuantItem{X.h, X.ldh, rows, W.in, dst, ld8, ar->scales + qi});
+            uint8_t* sf = h_->mx ? dst + codes : nullptr;
+            arena_used_ += codes + sfb;
+            q8_.push_back(QuantItem{X.h, X.ldh, rows, W.in, dst, ld8, ar->scales + qi, sf});
             qbytes_ += 3.0 * rows * W.in;
             g.a[0] = TcOperand{dst, ld8, false};
             g.b[0] = TcOperand{W.w8, W.ld8, false};
-            g.fp8 = 1; g.scale_a = ar->scales + qi; g.scale_b = W.s8;
+            if (h_->mx) {
+                g.fp8 = 2; g.sf_a = sf; g.sf_b = W.sf8;
+            } else {
+                g.fp8 = 1; g.scale_a = ar->scales + qi; g.scale_b = W.s8;
+            }
             (fused ? tc8ln_ : tc8_).push_back(g);
             return fused;
         }
@@ -146,8 +153,9 @@ void GemmBuilder::dw(const Mat& dY, int rows, const Mat& X, const LayerRef& W, f
 void GemmBuilder::flush() {
     if (fp_.empty() && tc_.empty() && tc8_.empty() && tcln_.empty() && tc8ln_.empty()) return;
     if (!q8_.empty()) {
-        ProfScope ps(h_, s_, "quantize_fp8", qbytes_, 1);
-        launch_quantize_e4m3(q8_.data(), (int)q8_.size(), h_->arena_for(s_)->part, s_);
+        ProfScope ps(h_, s_, h_->mx ? "quantize_mxfp8" : "quantize_fp8", qbytes_, 1);
+        if (h_->mx) launch_quantize_mx(q8_.data(), (int)q8_.size(), s_);
+        else launch_quantize_e4m3(q8_.data(), (int)q8_.size(), h_->arena_for(s_)->part, s_);
     }
     {
         ProfScope ps(h_, s_, kind_, flops_, 0);
@@ -188,6 +196,7 @@ LayerRef layer_ref(squint_handle* h, const Lin& ly, bool target, const float* ba
         r.w8 = target ? f8->second.tg : f8->second.on;
         r.s8 = target ? f8->second.s_tg : f8->second.s_on;
         r.ld8 = f8->second.ld;
+        r.sf8 = target ? f8->second.sf_tg : f8->second.sf_on;
         if (!r.w8) r.s8 = nullptr;
     }
     return r;
@@ -361,7 +370,8 @@ void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, in
 
 int squint_handle::allocate() {
     const int B = c.batch, A = c.action_dim, K = c.critic_kind == 1 ? 1 : c.atoms, E = 2;
-    fp8 = c.precision == SQUINT_PREC_FP8;
+    fp8 = c.precision == SQUINT_PREC_FP8 || c.precision == SQUINT_PREC_MXFP8;
+    mx = c.precision == SQUINT_PREC_MXFP8;
     if (const char* e = std::getenv("SQUINT_FUSED_LN")) fuse_ln = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_GEMM_SPLIT")) gemm_split = std::atoi(e) != 0;
     bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
@@ -476,6 +486,10 @@ int squint_handle::allocate() {
                 f.on = dalloc<uint8_t>((int64_t)ly.out * f.ld);
                 f.s_on = sc;
                 if (with_target) { f.tg = dalloc<uint8_t>((int64_t)ly.out * f.ld); f.s_tg = sc + 1; }
+                if (mx) {
+                    f.sf_on = dalloc<uint8_t>(mx_scale_bytes(ly.out, ly.in));
+                    if (with_target) f.sf_tg = dalloc<uint8_t>(mx_scale_bytes(ly.out, ly.in));
+                }
                 lin_f8[ly.w] = f;
             }
         };
@@ -552,7 +566,7 @@ int squint_handle::allocate() {
                 const LinBf& lb = lin_bf[ly.w];
                 const LinF8& f = lin_f8[ly.w];
                 return QuantItem{tgt ? lb.tg : lb.on, lb.ld, ly.out, ly.in, tgt ? f.tg : f.on, f.ld,
-                                 tgt ? f.s_tg : f.s_on};
+                                 tgt ? f.s_tg : f.s_on, tgt ? f.sf_tg : f.sf_on};
             };
             if (L.D > 0) { quant_critic.push_back(q(L.cproj, false)); quant_target.push_back(q(L.cproj, true)); }
             for (int e = 0; e < 2; ++e)
@@ -635,6 +649,11 @@ void squint_handle::quantize_weights(const std::vector<QuantItem>& q, cudaStream
     if (!fp8 || q.empty()) return;
     double bytes = 0;
     for (const auto& it : q) bytes += 3.0 * it.rows * it.cols;
+    if (mx) {
+        ProfScope ps(this, s, "quantize_mxfp8", bytes, 1);
+        launch_quantize_mx(q.data(), (int)q.size(), s);
+        return;
+    }
     ProfScope ps(this, s, "quantize_fp8", bytes, 1);
     launch_quantize_e4m3(q.data(), (int)q.size(), arena_for(s)->part, s);
 }

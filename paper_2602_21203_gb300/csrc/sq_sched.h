@@ -31,6 +31,7 @@ struct LayerRef {
     const uint8_t* w8 = nullptr;     // e4m3 copy (FP8 mode), row stride ld8, scale *s8
     int64_t ld8 = 0;
     const float* s8 = nullptr;
+    const uint8_t* sf8 = nullptr;    // MX block scales of w8 (MX-FP8 mode)
     int in = 0, out = 0;
     const float* g = nullptr;
     const float* beta = nullptr;

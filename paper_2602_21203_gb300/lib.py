@@ -14,7 +14,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsquint.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EAGAIN, ESTATE = 0, -1, -2, -3, -4, -5, -6
-PREC_FP32, PREC_BF16, PREC_FP8 = 0, 1, 2
+PREC_FP32, PREC_BF16, PREC_FP8, PREC_MXFP8 = 0, 1, 2, 3
 MAX_CONV, MAX_HIDDEN = 8, 4
 
 

@@ -99,11 +99,12 @@ def test_state_graph_replay_equals_eager_bitwise(L):
 @pytest.mark.parametrize("prec,bounds", [
     ("bf16", dict(q_mean=2e-2, critic_loss=1e-2, actor_loss=5e-2, grad_norm=5e-2, cos=0.98)),
     ("fp8", dict(q_mean=1e-1, critic_loss=1e-2, actor_loss=3e-1, grad_norm=3e-1, cos=0.9)),
+    ("mxfp8", dict(q_mean=1e-1, critic_loss=1e-2, actor_loss=3e-1, grad_norm=3e-1, cos=0.9)),
 ])
 def test_state_training_shape_low_precision(L, prec, bounds):
     cfg = synth.make_config(TRAIN)
     ring = synth.make_ring(cfg, 0, device="cuda")
-    learner = L.Learner(cfg, ring, precision={"bf16": L.PREC_BF16, "fp8": L.PREC_FP8}[prec])
+    learner = L.Learner(cfg, ring, precision={"bf16": L.PREC_BF16, "fp8": L.PREC_FP8, "mxfp8": L.PREC_MXFP8}[prec])
     st = learner.update(1, graph=False)[0]
     ref, tr = o.update(o.init_state(cfg), lazy_ring(ring), cfg)
     assert abs(st["q_mean"] - ref["q_mean"]) <= bounds["q_mean"] * max(abs(ref["q_mean"]), 1.0)

@@ -286,6 +286,27 @@ def test_fp8_update_runs_and_replays_bitwise(L):
         x.close()
 
 
+def test_mxfp8_update_runs_and_replays_bitwise(L):
+    """MX-FP8 mode (e4m3 forward linear layers with block scales): graph == eager bit for
+    bit, finite, and the first update's losses near the oracle's (printed)."""
+    cfg = synth.make_config("train_b512", ring_size=4096)
+    ring = synth.make_ring(cfg, 0, device="cuda")
+    a = L.Learner(cfg, ring, precision=L.PREC_MXFP8)
+    b = L.Learner(cfg, ring, precision=L.PREC_MXFP8)
+    sa = a.update(3, graph=True)
+    sb = b.update(3, graph=False)
+    assert sa == sb
+    assert np.array_equal(a.params(), b.params())
+    assert all(np.isfinite([s["critic_loss"], s["actor_loss"], s["q_mean"]]).all() for s in sa)
+    c = L.Learner(cfg, ring, precision=L.PREC_MXFP8)
+    st = c.update(1, graph=False)[0]
+    ref, _ = o.update(o.init_state(cfg), lazy_ring(ring), cfg)
+    print("\nmxfp8 vs oracle:", {k: (st[k], ref[k]) for k in ("q_mean", "critic_loss", "actor_loss")})
+    assert abs(st["critic_loss"] - ref["critic_loss"]) <= 5e-2 * abs(ref["critic_loss"])
+    for x in (a, b, c):
+        x.close()
+
+
 def test_fp8_with_fused_layernorm_matches_separate_layernorm(L, monkeypatch):
     """The LayerNorm fused into the FP8 GEMM epilogue takes its row statistics from the
     rescaled accumulator, like the separate LayerNorm kernel: same update up to rounding."""
