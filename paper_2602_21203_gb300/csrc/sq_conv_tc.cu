@@ -380,17 +380,40 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
     }
 }
 
-__global__ void wgrad32_reduce_kernel(const float* __restrict__ work, int splits, float* __restrict__ dw,
-                                      float* __restrict__ db) {
+// 32 elements per block and 8 groups of CTAs: group g adds CTA partials g, g + 8, ... in
+// increasing order, then the group sums are added in group order (a fixed order, so
+// partials reduced once per whole batch or after chunks give the same bits).
+constexpr int kRed32Groups = 8;
+__global__ void __launch_bounds__(32 * kRed32Groups) wgrad32_reduce_kernel(const float* __restrict__ work, int splits,
+                                                                            float* __restrict__ dw,
+                                                                            float* __restrict__ db) {
     SQ_KERNEL_ENTRY();
     constexpr int N = kCh * 9 + 1;
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= kCh * N) return;
+    constexpr int tot = kCh * N;
+    __shared__ float part[kRed32Groups][33];
+    const int tx = threadIdx.x % 32, g = threadIdx.x / 32;
+    const int e = blockIdx.x * 32 + tx;
     float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += work[(int64_t)z * kCh * N + e];
+    if (e < tot) {
+        int z = g;
+        for (; z + 3 * kRed32Groups < splits; z += 4 * kRed32Groups) {   // four partials' loads in flight
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = work[(int64_t)(z + u * kRed32Groups) * tot + e];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s += v[u];
+        }
+        for (; z < splits; z += kRed32Groups) s += work[(int64_t)z * tot + e];
+    }
+    part[g][tx] = s;
+    __syncthreads();
+    if (g != 0 || e >= tot) return;
+    float a = 0.f;
+#pragma unroll
+    for (int k = 0; k < kRed32Groups; ++k) a += part[k][tx];
     const int co = e / N, col = e - co * N;
-    if (col == N - 1) db[co] = s;
-    else dw[co * (N - 1) + col] = s;
+    if (col == N - 1) db[co] = a;
+    else dw[co * (N - 1) + col] = a;
 }
 
 // ---------------------------------------------------------------- first layer straight to padded HWC
@@ -572,7 +595,8 @@ int launch_wgrad32_tc_partials(const WgradTc& c, int per_cta, float* work, int* 
 }
 
 void launch_wgrad32_reduce(const float* work, int ctas, float* dw, float* db, cudaStream_t s) {
-    launch_k(wgrad32_reduce_kernel, dim3((kCh * (kCh * 9 + 1) + 255) / 256), dim3(256), 0, s, work, ctas, dw, db);
+    launch_k(wgrad32_reduce_kernel, dim3((kCh * (kCh * 9 + 1) + 31) / 32), dim3(32 * kRed32Groups), 0, s, work, ctas,
+             dw, db);
 }
 
 int launch_wgrad32_tc(const WgradTc& c, float* work, float* dw, float* db, int* err, cudaStream_t s) {

@@ -377,17 +377,39 @@ __global__ void __launch_bounds__(NT) conv_wgrad_kernel(ConvShape sh, const T* _
     }
 }
 
+// 32 elements per block and 16 split groups: group g adds splits g, g + 16, ... in
+// increasing order, then the group sums are added in group order (a fixed order).
+constexpr int kRedGroups = 16;
 template <typename T>
-__global__ void wgrad_reduce_kernel(const T* __restrict__ work, int splits, int M, int N, T* __restrict__ dw,
-                                    T* __restrict__ db) {
+__global__ void __launch_bounds__(32 * kRedGroups) wgrad_reduce_kernel(const T* __restrict__ work, int splits,
+                                                                          int M, int N, T* __restrict__ dw,
+                                                                          T* __restrict__ db) {
     SQ_KERNEL_ENTRY();
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= M * N) return;
+    __shared__ T part[kRedGroups][33];
+    const int tx = threadIdx.x % 32, g = threadIdx.x / 32;
+    const int64_t tot = (int64_t)M * N;
+    const int e = blockIdx.x * 32 + tx;
     T s = T(0);
-    for (int z = 0; z < splits; ++z) s += work[(int64_t)z * M * N + e];
+    if (e < tot) {
+        int z = g;
+        for (; z + 3 * kRedGroups < splits; z += 4 * kRedGroups) {   // four splits' loads in flight
+            T v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = work[(int64_t)(z + u * kRedGroups) * tot + e];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s += v[u];
+        }
+        for (; z < splits; z += kRedGroups) s += work[(int64_t)z * tot + e];
+    }
+    part[g][tx] = s;
+    __syncthreads();
+    if (g != 0 || e >= tot) return;
+    T a = T(0);
+#pragma unroll
+    for (int k = 0; k < kRedGroups; ++k) a += part[k][tx];
     const int co = e / N, col = e - co * N;
-    if (col == N - 1) db[co] = s;
-    else dw[(int64_t)co * (N - 1) + col] = s;
+    if (col == N - 1) db[co] = a;
+    else dw[(int64_t)co * (N - 1) + col] = a;
 }
 
 int wgrad_splits(const ConvShape& sh) {
@@ -425,7 +447,8 @@ void launch_conv_wgrad(const ConvShape& sh, const T* dy, const T* x, T* dw, T* d
     dim3 grid((N + WBN - 1) / WBN, (sh.Cout + WBM - 1) / WBM, splits);
     launch_k(conv_wgrad_kernel<T>, dim3(grid), dim3(NT), 0, s, sh, dy, x, work, chunk);
     const int tot = sh.Cout * N;
-    launch_k(wgrad_reduce_kernel<T>, dim3((tot + 255) / 256), dim3(256), 0, s, work, splits, sh.Cout, N, dw, db);
+    launch_k(wgrad_reduce_kernel<T>, dim3((tot + 31) / 32), dim3(32 * kRedGroups), 0, s, work, splits, sh.Cout, N, dw,
+             db);
 }
 
 template void launch_conv_fwd<float>(const ConvShape&, const float*, const float*, const float*, float*, bool, cudaStream_t);

@@ -28,11 +28,14 @@ __global__ void ln_fwd_kernel(Batch<LnProblem> b, int relu, float eps) {
     const float* x = P.pre + (int64_t)gw * P.ld_pre;
     float* y = P.out + (int64_t)gw * P.ld_out;
     if (P.n <= 32 * kVpt) {
-        float xv[kVpt];
+        // the row and its affine parameters are loaded together, before any use
+        float xv[kVpt], gv[kVpt], bv[kVpt];
 #pragma unroll
         for (int k = 0; k < kVpt; ++k) {
             const int j = lane + 32 * k;
             xv[k] = j < P.n ? x[j] : 0.f;
+            gv[k] = j < P.n ? P.g[j] : 0.f;
+            bv[k] = j < P.n ? P.beta[j] : 0.f;
         }
         float s = 0.f;
 #pragma unroll
@@ -51,7 +54,7 @@ __global__ void ln_fwd_kernel(Batch<LnProblem> b, int relu, float eps) {
         for (int k = 0; k < kVpt; ++k) {
             const int j = lane + 32 * k;
             if (j >= P.n) break;
-            float v = (xv[k] - mean) * rstd * P.g[j] + P.beta[j];
+            float v = (xv[k] - mean) * rstd * gv[k] + bv[k];
             if (relu) v = fmaxf(v, 0.f);
             y[j] = v;
             if (P.out_bf) P.out_bf[(int64_t)gw * P.ld_out_bf + j] = __float2bfloat16_rn(v);
@@ -194,7 +197,20 @@ __global__ void __launch_bounds__(256) ln_bwd_row_kernel(LnBwdBatch b, int want_
     const int blocks = b.block_start[pi + 1] - b.block_start[pi];
     for (int j = threadIdx.x; j < P.n; j += blockDim.x) {
         float sg = 0.f, sb = 0.f, sd = 0.f;
-        for (int k = 0; k < blocks; ++k) {
+        int k = 0;
+        for (; k + 8 <= blocks; k += 8) {   // eight partial rows' loads in flight, added in order
+            float g8[8], b8[8], d8[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float* pk = part + (int64_t)(k + u) * 3 * P.n;
+                g8[u] = __ldcg(pk + j);
+                b8[u] = __ldcg(pk + P.n + j);
+                d8[u] = __ldcg(pk + 2 * P.n + j);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) { sg += g8[u]; sb += b8[u]; sd += d8[u]; }
+        }
+        for (; k < blocks; ++k) {
             const float* pk = part + (int64_t)k * 3 * P.n;
             sg += __ldcg(pk + j);
             sb += __ldcg(pk + P.n + j);
@@ -215,8 +231,17 @@ __global__ void __launch_bounds__(kColX * kColY) colsum_kernel(Batch<ColSumProbl
     const int tx = threadIdx.x % kColX, ty = threadIdx.x / kColX;
     const int j = blockIdx.x * kColX + tx;
     float s = 0.f;
-    if (j < P.n)
-        for (int r = ty; r < P.rows; r += kColY) s += P.in[(int64_t)r * P.ld + j];
+    if (j < P.n) {
+        int r = ty;
+        for (; r + 7 * kColY < P.rows; r += 8 * kColY) {   // eight rows' loads in flight, added in order
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = P.in[(int64_t)(r + u * kColY) * P.ld + j];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += v[u];
+        }
+        for (; r < P.rows; r += kColY) s += P.in[(int64_t)r * P.ld + j];
+    }
     part[ty][tx] = s;
     __syncthreads();
     if (ty == 0 && j < P.n) {
@@ -519,6 +544,13 @@ __global__ void act_head_kernel(ActHeadArgs a) {
 
 // ---------------------------------------------------------------- temperature + statistics
 // stats layout: 0 critic loss, 1 actor loss, 2 alpha loss, 3 alpha, 4 q mean, 5 entropy, 6 update idx (as float bits: low), 7 unused
+// Adam's bias correction 1 - beta^t, in FP32 as 1 - 2^(t log2 beta): a handful of
+// instructions where the double-precision pow is a long chain on the FP64 units
+// (relative error of beta^t ~ t |log2 beta| 2^-24, below 1e-4 while beta^t matters).
+__device__ __forceinline__ float bias_correction(double beta, int t) {
+    return 1.0f - exp2f((float)t * log2f((float)beta));
+}
+
 __global__ void alpha_kernel(AlphaArgs a) {
     SQ_KERNEL_ENTRY();
     __shared__ float red[32];
@@ -535,8 +567,8 @@ __global__ void alpha_kernel(AlphaArgs a) {
     const float vv = (float)a.b2 * *a.v + (float)(1.0 - a.b2) * g * g;
     *a.m = mm;
     *a.v = vv;
-    const float bc1 = (float)(1.0 - pow(a.b1, (double)t));
-    const float bc2 = (float)(1.0 - pow(a.b2, (double)t));
+    const float bc1 = bias_correction(a.b1, t);
+    const float bc2 = bias_correction(a.b2, t);
     const float la = *a.log_alpha - (float)a.lr * (mm / bc1) / (sqrtf(vv / bc2) + (float)a.eps);
     *a.log_alpha = la;
     a.stats[2] = loss;
@@ -591,9 +623,8 @@ __global__ void adam_kernel(AdamArgs a) {
     if (a.enable && !*a.enable) return;
     __shared__ float bc[2];
     if (threadIdx.x == 0) {
-        const double t = (double)*a.step;
-        bc[0] = (float)(1.0 - pow(a.b1, t));
-        bc[1] = (float)(1.0 - pow(a.b2, t));
+        bc[0] = bias_correction(a.b1, *a.step);
+        bc[1] = bias_correction(a.b2, *a.step);
     }
     __syncthreads();
     const float b1 = (float)a.b1, b2 = (float)a.b2, lr = (float)a.lr, ep = (float)a.eps;
