@@ -253,6 +253,13 @@ struct WgradArgs {
 };
 
 constexpr int kDyBytesMax = 32768;
+constexpr uint32_t kWgTileBytes = kCh * (kCh * 9 + 1) * 4;   // the partial tile, staged at the end
+// bytes from the (1024-aligned) start of shared memory to the barriers: the operand buffers,
+// at least as many as the partial tile that reuses them
+__host__ __device__ inline uint32_t wgrad_operand_bytes(uint32_t xbytes, uint32_t dybytes) {
+    const uint32_t ops = 2 * xbytes + 2 * dybytes;
+    return ops > kWgTileBytes ? ops : kWgTileBytes;
+}
 
 __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__ WgradArgs a) {
     SQ_KERNEL_ENTRY();
@@ -263,7 +270,7 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
     const uint32_t dybytes = (uint32_t)(a.kq / 8) * 512 + 2048;   // + slack read by the aliased rows
     uint8_t* xs[2] = {smem, smem + xbytes};
     uint8_t* ds[2] = {smem + 2 * xbytes, smem + 2 * xbytes + dybytes};
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + 2 * xbytes + 2 * dybytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + wgrad_operand_bytes(xbytes, dybytes));
     float* red = reinterpret_cast<float*>(bars + 8);             // [128][8] bias partials
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(red + 128 * 8);
     const uint32_t tma_bar[2] = {smem_u32(bars), smem_u32(bars + 1)};
@@ -307,21 +314,33 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
                     tma_load_3d(smem_u32(xs[b]) + c * plane + bb * 2048, &a.tin, 0, c, i * a.in_rows + bb * 128,
                                 tma_bar[b]);
         }
-        // stage dy^T: element (co, q) at (q / 8) * 512 + co * 16 + (q % 8) * 2
+        // stage dy^T: element (co, q) at (q / 8) * 512 + co * 16 + (q % 8) * 2; a thread's
+        // loads for eight pixels are issued before any of them is stored
         uint8_t* d = ds[b];
-        for (int j = threadIdx.x; j < a.kq * 4; j += blockDim.x) {
-            const int q = j >> 2;
-            const int oy = q / a.Wp, ox = q - (q / a.Wp) * a.Wp;
-            uint4 v4 = make_uint4(0, 0, 0, 0);
-            if (oy < a.out_h && ox < a.out_w)
-                v4 = *reinterpret_cast<const uint4*>(a.dy + (int64_t)i * dy_img +
-                                                     ((int64_t)(oy + 2) * wpo + ox + 2) * kCh + cc * 8);
-            const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v4);
-            uint8_t* col = d + (q >> 3) * 512 + (q & 7) * 2;
+        for (int j0 = threadIdx.x; j0 < a.kq * 4; j0 += 8 * blockDim.x) {
+            uint4 v4[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                *reinterpret_cast<__nv_bfloat16*>(col + (cc * 8 + k) * 16) = hv[k];
-                bsum[k] += __bfloat162float(hv[k]);
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * blockDim.x;
+                const int q = j >> 2;
+                const int oy = q / a.Wp, ox = q - (q / a.Wp) * a.Wp;
+                v4[u] = make_uint4(0, 0, 0, 0);
+                if (j < a.kq * 4 && oy < a.out_h && ox < a.out_w)
+                    v4[u] = *reinterpret_cast<const uint4*>(a.dy + (int64_t)i * dy_img +
+                                                            ((int64_t)(oy + 2) * wpo + ox + 2) * kCh + cc * 8);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = j0 + u * blockDim.x;
+                if (j >= a.kq * 4) break;
+                const int q = j >> 2;
+                const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v4[u]);
+                uint8_t* col = d + (q >> 3) * 512 + (q & 7) * 2;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    *reinterpret_cast<__nv_bfloat16*>(col + (cc * 8 + k) * 16) = hv[k];
+                    bsum[k] += __bfloat162float(hv[k]);
+                }
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -349,16 +368,19 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
     __syncwarp();
     const bool have = mbar_wait(done_bar, 0, a.err, 23) && ok && i1 > i0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // bias partials: reduce the 32 threads of each chunk in a fixed order
+    // bias partials: reduce the 32 threads of each chunk in a fixed order.  The partial
+    // tile [co][ci * 9 + tap | bias] is assembled in shared memory (the operand buffers are
+    // idle once the last MMA has completed) and stored by all threads, coalesced.
 #pragma unroll
     for (int k = 0; k < 8; ++k) red[threadIdx.x * 8 + k] = bsum[k];
     __syncthreads();
-    float* out = a.work + (int64_t)blockIdx.x * kCh * (kCh * 9 + 1);
+    constexpr int NW = kCh * 9 + 1;
+    float* tile = reinterpret_cast<float*>(smem);   // [kCh][NW]
     if (threadIdx.x < kCh) {
         const int co = threadIdx.x;
         float s = 0.f;
         for (int t = co / 8; t < 128; t += 4) s += red[t * 8 + (co % 8)];
-        out[co * (kCh * 9 + 1) + kCh * 9] = s;
+        tile[co * NW + kCh * 9] = s;
     }
     if (warp == 0) {
         const int co = lane;
@@ -366,12 +388,16 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
             uint32_t r0[16], r1[16];
             tmem_ld16(tmem + tap * kCh, r0);
             tmem_ld16(tmem + tap * kCh + 16, r1);
+#pragma unroll
             for (int j = 0; j < 16; ++j) {
-                out[co * (kCh * 9 + 1) + j * 9 + tap] = have ? __uint_as_float(r0[j]) : 0.f;
-                out[co * (kCh * 9 + 1) + (16 + j) * 9 + tap] = have ? __uint_as_float(r1[j]) : 0.f;
+                tile[co * NW + j * 9 + tap] = have ? __uint_as_float(r0[j]) : 0.f;
+                tile[co * NW + (16 + j) * 9 + tap] = have ? __uint_as_float(r1[j]) : 0.f;
             }
         }
     }
+    __syncthreads();
+    float* out = a.work + (int64_t)blockIdx.x * kCh * NW;
+    for (int e = threadIdx.x; e < kCh * NW; e += blockDim.x) out[e] = tile[e];
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -543,7 +569,8 @@ int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 size_t conv_smem(int load_rows) { return 1024 + 4 * (size_t)load_rows * 16 + kWBytes + 64; }
 size_t wgrad_smem(int load_rows, int kq) {
-    return 1024 + 2 * (4 * (size_t)load_rows * 16) + 2 * ((size_t)(kq / 8) * 512 + 2048) + 64 + 128 * 8 * 4 + 16;
+    return 1024 + wgrad_operand_bytes(4 * (uint32_t)load_rows * 16, (uint32_t)(kq / 8) * 512 + 2048) + 64 +
+           128 * 8 * 4 + 16;
 }
 
 }  // namespace

@@ -4,6 +4,8 @@
 //
 // Tile: 64 x 64 outputs x 16 reduction steps per stage, 256 threads, 4 x 4
 // outputs per thread, operands staged in shared memory k-major.
+#include <type_traits>
+
 #include "sq_kernels.cuh"
 
 #include <algorithm>
@@ -377,6 +379,89 @@ __global__ void __launch_bounds__(NT) conv_wgrad_kernel(ConvShape sh, const T* _
     }
 }
 
+// Weight gradient of a layer with 32 outputs and at most 31 input taps (Cin * 9 + 1 <= 32
+// columns with the bias), i.e. the encoder's first convolution: 128 threads, thread t
+// owns output rows 2 (t / 8), 2 (t / 8) + 1 and columns 4 (t % 8) .. + 3.  Per tile of 64
+// pixels every thread issues all of its gathers (16 of dy, 16 of x) before storing them,
+// transposed into padded shared memory (pixel fastest), then accumulates over the tile's
+// pixels in order.  Partial sums per split in `work`, as for conv_wgrad_kernel.
+constexpr int kW0Tile = 64;
+__global__ void __launch_bounds__(128) conv_wgrad_c32_kernel(ConvShape sh, const float* __restrict__ dy,
+                                                             const float* __restrict__ x, float* __restrict__ work,
+                                                             int chunk) {
+    SQ_KERNEL_ENTRY();
+    __shared__ float dys[32][kW0Tile + 1];   // [co][pixel]
+    __shared__ float xs[32][kW0Tile + 1];    // [column][pixel]; column N - 1 is the bias (1)
+    const int t = threadIdx.x;
+    const int N = sh.Cin * 9 + 1;
+    const int P = sh.nimg * sh.OH * sh.OW;
+    const int oplane = sh.OH * sh.OW;
+    const int64_t iplane = (int64_t)sh.H * sh.W;
+    const int p_begin = blockIdx.x * chunk, p_end = min(P, p_begin + chunk);
+    const int cg = t / 8, jg = t % 8;
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    for (int k0 = p_begin; k0 < p_end; k0 += kW0Tile) {
+        float vd[16], vx[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = t + u * 128;
+            const int pl = e % kW0Tile, co = e / kW0Tile;
+            const int p = k0 + pl;
+            vd[u] = 0.f;
+            if (p < p_end) {
+                const int img = p / oplane, rem = p - img * oplane;
+                vd[u] = dy[(int64_t)img * sh.y_img_stride + (int64_t)co * oplane + rem];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = t + u * 128;
+            const int pl = e % kW0Tile, j = e / kW0Tile;
+            const int p = k0 + pl;
+            float v = 0.f;
+            if (p < p_end && j < N) {
+                if (j == N - 1) {
+                    v = 1.f;
+                } else {
+                    const int img = p / oplane, rem = p - img * oplane;
+                    const int oy = rem / sh.OW, ox = rem - oy * sh.OW;
+                    const int ci = j / 9, r = j - ci * 9, ky = r / 3, kx = r - ky * 3;
+                    v = x[(int64_t)img * sh.x_img_stride + ci * iplane + (int64_t)(oy * sh.stride + ky) * sh.W +
+                          ox * sh.stride + kx];
+                }
+            }
+            vx[u] = v;
+        }
+        __syncthreads();   // the previous tile has been consumed
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = t + u * 128;
+            dys[e / kW0Tile][e % kW0Tile] = vd[u];
+            xs[e / kW0Tile][e % kW0Tile] = vx[u];
+        }
+        __syncthreads();
+        const int np = min(kW0Tile, p_end - k0);
+#pragma unroll 4
+        for (int pl = 0; pl < np; ++pl) {
+            const float d0 = dys[2 * cg][pl], d1 = dys[2 * cg + 1][pl];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float xv = xs[4 * jg + k][pl];
+                acc[0][k] = fmaf(d0, xv, acc[0][k]);
+                acc[1][k] = fmaf(d1, xv, acc[1][k]);
+            }
+        }
+    }
+    float* out = work + (int64_t)blockIdx.x * 32 * N;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int col = 4 * jg + k;
+            if (col < N) out[(2 * cg + i) * N + col] = acc[i][k];
+        }
+}
+
 // 32 elements per block and 16 split groups: group g adds splits g, g + 16, ... in
 // increasing order, then the group sums are added in group order (a fixed order).
 constexpr int kRedGroups = 16;
@@ -444,8 +529,12 @@ void launch_conv_wgrad(const ConvShape& sh, const T* dy, const T* x, T* dw, T* d
     const int splits = wgrad_splits(sh);
     const int chunk = (P + splits - 1) / splits;
     const int N = sh.Cin * 9 + 1;
-    dim3 grid((N + WBN - 1) / WBN, (sh.Cout + WBM - 1) / WBM, splits);
-    launch_k(conv_wgrad_kernel<T>, dim3(grid), dim3(NT), 0, s, sh, dy, x, work, chunk);
+    if (std::is_same<T, float>::value && sh.Cout == 32 && N <= 32)
+        launch_k(conv_wgrad_c32_kernel, dim3(splits), dim3(128), 0, s, sh, (const float*)dy, (const float*)x,
+                 (float*)work, chunk);
+    else
+        launch_k(conv_wgrad_kernel<T>, dim3((N + WBN - 1) / WBN, (sh.Cout + WBM - 1) / WBM, splits), dim3(NT), 0, s,
+                 sh, dy, x, work, chunk);
     const int tot = sh.Cout * N;
     launch_k(wgrad_reduce_kernel<T>, dim3((tot + 31) / 32), dim3(32 * kRedGroups), 0, s, work, splits, sh.Cout, N, dw,
              db);

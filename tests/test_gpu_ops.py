@@ -180,11 +180,12 @@ def test_cuda_core_gemm_layouts(ops, dtype):
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-6)])
 @pytest.mark.parametrize("stride", [1, 2])
-def test_conv3x3_matches_oracle(ops, dtype, tol, stride):
-    g = torch.Generator().manual_seed(5 + stride)
+@pytest.mark.parametrize("cout", [8, 32])
+def test_conv3x3_matches_oracle(ops, dtype, tol, stride, cout):
+    g = torch.Generator().manual_seed(5 + stride + cout)
     x = torch.randn(5, 3, 17, 15, generator=g, dtype=torch.float64)
-    w = torch.randn(8, 3, 3, 3, generator=g, dtype=torch.float64) * 0.3
-    b = torch.randn(8, generator=g, dtype=torch.float64)
+    w = torch.randn(cout, 3, 3, 3, generator=g, dtype=torch.float64) * 0.3
+    b = torch.randn(cout, generator=g, dtype=torch.float64)
     y = ops.conv3x3_fwd(x.to(dtype).cuda(), w.to(dtype).cuda(), b.to(dtype).cuda(), stride, relu=False)
     ref = o.conv3x3_fwd(x.numpy(), w.numpy(), b.numpy(), stride)
     assert _rel(y.cpu().numpy(), ref) < tol
@@ -194,6 +195,19 @@ def test_conv3x3_matches_oracle(ops, dtype, tol, stride):
     assert _rel(dx.cpu().numpy(), rdx) < tol
     assert _rel(dw.cpu().numpy(), rdw) < tol
     assert _rel(db.cpu().numpy(), rdb) < tol
+
+
+def test_first_layer_weight_gradient_at_training_shape(ops):
+    """The 3 -> 32 stride-2 layer's weight gradient over 512 images of 32x32 (the split
+    over pixels and its fixed-order reduction) vs the FP64 oracle."""
+    g = torch.Generator().manual_seed(77)
+    x = torch.rand(512, 3, 32, 32, generator=g, dtype=torch.float64) - 0.5
+    w = torch.randn(32, 3, 3, 3, generator=g, dtype=torch.float64) * 0.2
+    dy = torch.randn(512, 32, 15, 15, generator=g, dtype=torch.float64) * 1e-3
+    dx, dw, db = ops.conv3x3_bwd(x.float().cuda(), w.float().cuda(), dy.float().cuda(), 2)
+    _, rdw, rdb = o.conv3x3_bwd(x.float().double().numpy(), w.float().double().numpy(), dy.float().double().numpy(), 2)
+    assert _rel(dw.cpu().numpy(), rdw) < 1e-5
+    assert _rel(db.cpu().numpy(), rdb) < 1e-5
 
 
 @pytest.mark.parametrize("relu", [False, True])
