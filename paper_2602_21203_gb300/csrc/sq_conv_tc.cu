@@ -461,34 +461,53 @@ __global__ void __launch_bounds__(256) conv0_phwc_kernel(ConvShape sh, const flo
     }
     if (threadIdx.x < kCh) w_s[K * kCh + threadIdx.x] = bias[threadIdx.x];
     __syncthreads();
+    // two output pixels per thread (blockDim apart, so each half stays coalesced): every
+    // weight read from shared memory feeds both
     const int64_t npix = (int64_t)sh.nimg * sh.OH * sh.OW;
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= npix) return;
-    const int img = (int)(p / (sh.OH * sh.OW));
-    const int rem = (int)(p - (int64_t)img * sh.OH * sh.OW);
-    const int oy = rem / sh.OW, ox = rem - (rem / sh.OW) * sh.OW;
-    const float* xb = x + (int64_t)img * sh.x_img_stride + (int64_t)(oy * sh.stride) * sh.W + ox * sh.stride;
-    float acc[kCh];
+    const int64_t p0 = (int64_t)blockIdx.x * 2 * blockDim.x + threadIdx.x;
+    if (p0 >= npix) return;
+    const int64_t pp[2] = {p0, p0 + blockDim.x};
+    const bool has1 = pp[1] < npix;
+    const float* xb[2];
+    __nv_bfloat16* dst[2];
 #pragma unroll
-    for (int co = 0; co < kCh; ++co) acc[co] = 0.f;
+    for (int h = 0; h < 2; ++h) {
+        const int64_t p = has1 || h == 0 ? pp[h] : pp[0];
+        const int img = (int)(p / (sh.OH * sh.OW));
+        const int rem = (int)(p - (int64_t)img * sh.OH * sh.OW);
+        const int oy = rem / sh.OW, ox = rem - (rem / sh.OW) * sh.OW;
+        xb[h] = x + (int64_t)img * sh.x_img_stride + (int64_t)(oy * sh.stride) * sh.W + ox * sh.stride;
+        dst[h] = out + ((int64_t)img * (sh.OH + 4) * (sh.OW + 4) + (int64_t)(oy + 2) * (sh.OW + 4) + ox + 2) * kCh;
+    }
+    float acc0[kCh], acc1[kCh];
+#pragma unroll
+    for (int co = 0; co < kCh; ++co) { acc0[co] = 0.f; acc1[co] = 0.f; }
     for (int ci = 0; ci < sh.Cin; ++ci)
 #pragma unroll
         for (int t = 0; t < 9; ++t) {
-            const float xv = __ldg(xb + (int64_t)ci * sh.H * sh.W + (t / 3) * sh.W + (t % 3));
+            const int64_t off = (int64_t)ci * sh.H * sh.W + (t / 3) * sh.W + (t % 3);
+            const float xv0 = __ldg(xb[0] + off), xv1 = __ldg(xb[1] + off);
             const float* wk = w_s + (ci * 9 + t) * kCh;
 #pragma unroll
-            for (int co = 0; co < kCh; ++co) acc[co] = fmaf(xv, wk[co], acc[co]);
+            for (int co = 0; co < kCh; ++co) {
+                const float wv = wk[co];
+                acc0[co] = fmaf(xv0, wv, acc0[co]);
+                acc1[co] = fmaf(xv1, wv, acc1[co]);
+            }
         }
-    __align__(16) __nv_bfloat16 hb[kCh];
 #pragma unroll
-    for (int co = 0; co < kCh; ++co) {
-        float v = acc[co] + w_s[K * kCh + co];
-        if (!(v > 0.f)) v = 0.f;
-        hb[co] = __float2bfloat16_rn(v);
+    for (int h = 0; h < 2; ++h) {
+        if (h == 1 && !has1) break;
+        __align__(16) __nv_bfloat16 hb[kCh];
+#pragma unroll
+        for (int co = 0; co < kCh; ++co) {
+            float v = (h == 0 ? acc0[co] : acc1[co]) + w_s[K * kCh + co];
+            if (!(v > 0.f)) v = 0.f;
+            hb[co] = __float2bfloat16_rn(v);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) reinterpret_cast<uint4*>(dst[h])[c] = reinterpret_cast<const uint4*>(hb)[c];
     }
-    __nv_bfloat16* d = out + ((int64_t)img * (sh.OH + 4) * (sh.OW + 4) + (int64_t)(oy + 2) * (sh.OW + 4) + ox + 2) * kCh;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) reinterpret_cast<uint4*>(d)[c] = reinterpret_cast<const uint4*>(hb)[c];
 }
 
 
@@ -646,7 +665,7 @@ void launch_conv0_phwc(const ConvShape& sh, const float* x, const float* w, cons
     const int64_t npix = (int64_t)sh.nimg * sh.OH * sh.OW;
     if (npix <= 0) return;
     const size_t smem = ((size_t)sh.Cin * 9 * kCh + kCh) * sizeof(float);
-    launch_k(conv0_phwc_kernel, dim3((unsigned)((npix + 255) / 256)), dim3(256), smem, s, sh, x, w, b, out);
+    launch_k(conv0_phwc_kernel, dim3((unsigned)((npix + 511) / 512)), dim3(256), smem, s, sh, x, w, b, out);
 }
 
 void launch_to_phwc(const float* src, int64_t img_stride, int nimg, int H, int W, __nv_bfloat16* dst, cudaStream_t s) {

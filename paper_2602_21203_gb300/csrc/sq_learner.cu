@@ -19,6 +19,7 @@
 // GEMM operand has a BF16 shadow written by the kernel that produces it.
 #include "sq_sched.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -30,6 +31,7 @@ using namespace sq;
 namespace sq {
 
 static int64_t pad8(int64_t n) { return (n + 7) / 8 * 8; }
+constexpr int kLongK = 1024;   // reductions at least this long may split K over a cluster
 constexpr int kCh32 = 32;   // channels of the tensor-core convolutions
 
 GemmProblem lin_fwd(const float* X, int64_t ldx, int rows, const float* W, const float* b, int in, int out, float* Y,
@@ -160,9 +162,15 @@ void GemmBuilder::flush() {
     {
         ProfScope ps(h_, s_, kind_, flops_, 0);
         if (!fp_.empty()) launch_gemm<float>(fp_.data(), (int)fp_.size(), lay_, s_);
-        for (auto* v : {&tc8_, &tc8ln_, &tc_, &tcln_})
-            if (!v->empty() && launch_tc_gemm(v->data(), (int)v->size(), h_->d_err, s_, split_ && h_->gemm_split) != 0)
-                h_->launch_failed = true;
+        // the K split over a cluster pays for long reductions over few output tiles (the
+        // projections from the flattened features, K = 2592); elsewhere it is opt-in
+        for (auto* v : {&tc8_, &tc8ln_, &tc_, &tcln_}) {
+            if (v->empty()) continue;
+            int kmax = 0;
+            for (const TcGemm& g : *v) kmax = std::max(kmax, g.K);
+            const bool split = split_ && (h_->gemm_split || kmax >= kLongK);
+            if (launch_tc_gemm(v->data(), (int)v->size(), h_->d_err, s_, split) != 0) h_->launch_failed = true;
+        }
     }
     fp_.clear();
     tc_.clear();
