@@ -56,6 +56,8 @@ struct MlpBufs {
     std::vector<float*> pre, post, mean, rstd;   // per hidden layer: [E, rows, n]
     std::vector<__nv_bfloat16*> posth;           // BF16 shadows of post (tensor-core path)
     float* out = nullptr;                        // [E, rows, n_out]
+    std::vector<float*> lnterms;                 // per hidden layer: [E][2][rows, n] deferred
+                                                 // LayerNorm column-sum terms (backward with weights)
 };
 
 // BF16 padded copy of one linear layer's weight (online and, for the critic range, target).
@@ -165,6 +167,7 @@ struct squint_handle {
     }
     void quantize_weights(const std::vector<sq::QuantItem>& q, cudaStream_t s);
     std::vector<sq::CastItem> cast_critic, cast_actor, cast_target;
+    float* proj_terms = nullptr;               // [2][B, D] deferred LayerNorm column-sum terms
     __nv_bfloat16* z_h = nullptr;              // [2B, F]
     __nv_bfloat16* xa_h = nullptr;             // [2B, Da8]
     __nv_bfloat16* xcbar_h = nullptr;          // [B, Dc8]

@@ -123,6 +123,11 @@ struct LnBwdProblem {
     __nv_bfloat16* dpre_bf; int64_t ld_dpre_bf;  // optional BF16 copy of dpre
     float* dg; float* dbeta;               // column sums (written) or null
     float* dbias;                          // sum of dpre over rows (linear bias grad) or null
+    // Deferred column sums: with `terms` set, the row kernel writes dn xh and dn of every
+    // element to terms[0 .. rows n) and terms[rows n .. 2 rows n) (row stride n) instead
+    // of reducing them, and launch_ln_bwd_cols adds them (and dpre) up later, e.g. on
+    // another stream beside the weight-gradient GEMMs.
+    float* terms;
 };
 // Column sums (dg, dbeta, dbias) need `work` of ln_bwd_workspace() floats (null: rows only).
 // Its first kLnTickets words are ticket counters that must be zero before the first launch;
@@ -136,6 +141,8 @@ void ln_prepare();
 // Column sums over rows: out[j] = sum_r in[r*ld + j] (deterministic order).
 struct ColSumProblem { int rows, n; const float* in; int64_t ld; float* out; };
 void launch_colsum(const ColSumProblem* p, int n_probs, cudaStream_t s);
+// The deferred column sums of LayerNorm backward problems whose `terms` are set.
+void launch_ln_bwd_cols(const LnBwdProblem* p, int n_probs, cudaStream_t s);
 
 // ---------------------------------------------------------------- heads and losses
 struct ActorHeadArgs {

@@ -330,6 +330,7 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
             p.dpre = dpre(l, e).f; p.ld_dpre = ly.out;
             if (bf) { p.dpre_bf = dpre(l, e).h; p.ld_dpre_bf = ly.out; }
             if (grads) { p.dg = G(ly.g); p.dbeta = G(ly.beta); p.dbias = G(ly.b); }
+            if (grads && !mb.lnterms.empty()) p.terms = mb.lnterms[l] + (int64_t)e * 2 * rows * ly.out;
             lb[e] = p;
         }
         {
@@ -337,7 +338,12 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
             launch_ln_bwd(lb, E, h->ln_work, s);
         }
         if (grads) {
+            // the LayerNorm's column sums and the weight gradients beside the input-gradient chain
             h->fork(s, side);
+            {
+                ProfScope ps(h, side, "colsum", 4.0 * E * rows * sets[0][l].out * 3.0, 1);
+                launch_ln_bwd_cols(lb, E, side);
+            }
             GemmBuilder gb(h, side, bf);
             for (int e = 0; e < E; ++e) gb.dw(dpre(l, e), rows, l == 0 ? X : post(l - 1, e), sets[e][l], G(sets[e][l].w));
         }
@@ -359,12 +365,13 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
     if (grads) h->fork(side, s);
 }
 
-void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, int E, int rows) {
+void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, int E, int rows, bool terms = false) {
     const int nh = (int)layers.size() - 1;
     mb.E = E;
     mb.rows = rows;
     mb.pre.resize(nh); mb.post.resize(nh); mb.mean.resize(nh); mb.rstd.resize(nh);
     for (int l = 0; l < nh; ++l) {
+        if (terms) mb.lnterms.push_back(h->dalloc<float>((int64_t)E * 2 * rows * layers[l].out));
         mb.pre[l] = h->dalloc<float>((int64_t)E * rows * layers[l].out);
         mb.post[l] = h->dalloc<float>((int64_t)E * rows * layers[l].out);
         mb.mean[l] = h->dalloc<float>((int64_t)E * rows);
@@ -430,14 +437,15 @@ int squint_handle::allocate() {
         proj_pre = dalloc<float>((int64_t)5 * B * L.D);
         proj_mean = dalloc<float>(5 * B);
         proj_rstd = dalloc<float>(5 * B);
+        proj_terms = dalloc<float>((int64_t)2 * B * L.D);
     }
     xa = dalloc<float>((int64_t)2 * B * L.da);
     xcbar = dalloc<float>((int64_t)B * L.dc);
     xc = dalloc<float>((int64_t)B * L.dc);
     xq = dalloc<float>((int64_t)B * L.dc);
-    alloc_mlp(this, actor_mlp, L.actor, 1, 2 * B);
+    alloc_mlp(this, actor_mlp, L.actor, 1, 2 * B, true);
     alloc_mlp(this, tcrit_mlp, L.critic[0], E, B);
-    alloc_mlp(this, crit_mlp, L.critic[0], E, B);
+    alloc_mlp(this, crit_mlp, L.critic[0], E, B, true);
     alloc_mlp(this, qcrit_mlp, L.critic[0], E, B);
     logp = dalloc<float>(2 * B);
     eps = dalloc<float>(2 * B * A);
@@ -934,9 +942,14 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             p.dpre = dproj; p.ld_dpre = Dd;
             if (bf16) { p.dpre_bf = dproj_h; p.ld_dpre_bf = Dd; }
             p.dg = G + L.cproj.g; p.dbeta = G + L.cproj.beta; p.dbias = G + L.cproj.b;
+            p.terms = proj_terms;
             ln_bwd(&p, 1, s);
             const Mat dp{dproj, Dd, dproj_h, Dd};
             fork(s, s2);
+            {
+                ProfScope ps(this, s2, "colsum", 12.0 * B * Dd, 1);
+                launch_ln_bwd_cols(&p, 1, s2);
+            }
             {
                 GemmBuilder gb(this, s2, bf16);
                 gb.dw(dp, B, zt, cp, G + L.cproj.w);
@@ -1068,7 +1081,8 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         quantize_weights(quant_target, s3);
     }
     mark(s);
-    // ---- a13: temperature
+    // ---- a13 on branch s3: temperature, from log pi of the pre-update actor at s_t; the
+    // actor step first reads the new alpha in its head backward (joined there)
     {
         AlphaArgs al{};
         al.B = B; al.logp_t = logp + B;
@@ -1077,8 +1091,8 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         al.lr = c.lr; al.b1 = c.adam_b1; al.b2 = c.adam_b2; al.eps = c.adam_eps;
         al.target_entropy = std::isnan(c.target_entropy) ? -(float)A : (float)c.target_entropy;
         al.stats = stats;
-        ProfScope ps(this, s, "heads_losses", 0, 1);
-        launch_alpha_step(al, s);
+        ProfScope ps(this, s3, "heads_losses", 0, 1);
+        launch_alpha_step(al, s3);
     }
     mark(s);
     // ---- a14: actor step on stop-gradient features with the updated critics
@@ -1111,8 +1125,20 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             ProfScope ps(this, s, "heads_losses", 0, 1);
             launch_actor_q(aq, s);
         }
+        // ---- statistics on branch s3 once the actor objective is known (nothing later in
+        // the update reads the update index it advances)
+        fork(s, s3);
+        {
+            StatsArgs st{};
+            st.B = B; st.E = E; st.row_loss = row_loss; st.row_q = row_q; st.row_q_actor = row_q_actor;
+            st.logp_t = logp + B; st.log_alpha = W + L.log_alpha; st.do_actor = d_do_actor;
+            st.update_idx = d_update_idx; st.stats = stats; st.cdq = c.cdq;
+            ProfScope ps(this, s3, "heads_losses", 0, 1);
+            launch_stats(st, s3);
+        }
         mlp_backward(this, qcrit_mlp, 0, crit_on, nullptr, E, Mat{xq, Dc, xq_h, Dc8}, B, Mat{dlogits_q, K, dlogits_qh, K8},
                      Dc, dxq, Dc, nullptr, 0, s, s2);
+        fork(s3, s);   // the new alpha (and the statistics) before the head backward
         ActorHeadBwdArgs hb{};
         hb.B = B; hb.A = A;
         hb.out = actor_mlp.out + (int64_t)B * 2 * A; hb.ld_out = 2 * A;
@@ -1137,7 +1163,12 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             p.dpre = dproj; p.ld_dpre = Dd;
             if (bf16) { p.dpre_bf = dproj_h; p.ld_dpre_bf = Dd; }
             p.dg = G + L.aproj.g; p.dbeta = G + L.aproj.beta; p.dbias = G + L.aproj.b;
+            p.terms = proj_terms;
             ln_bwd(&p, 1, s);
+            {
+                ProfScope ps(this, s, "colsum", 12.0 * B * Dd, 1);
+                launch_ln_bwd_cols(&p, 1, s);
+            }
             GemmBuilder gb(this, s, bf16);
             gb.dw(Mat{dproj, Dd, dproj_h, Dd}, B, zt, ap, G + L.aproj.w);
         }
@@ -1148,19 +1179,10 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         }
         quantize_weights(quant_actor, s);
     }
-    // join the encoder and polyak branches
+    // join the encoder branch (the polyak / temperature / statistics branch joined above)
     fork(s1, s);
     fork(s3, s);
     mark(s);
-    // ---- statistics; advances the update index
-    {
-        StatsArgs st{};
-        st.B = B; st.E = E; st.row_loss = row_loss; st.row_q = row_q; st.row_q_actor = row_q_actor;
-        st.logp_t = logp + B; st.log_alpha = W + L.log_alpha; st.do_actor = d_do_actor;
-        st.update_idx = d_update_idx; st.stats = stats; st.cdq = c.cdq;
-        ProfScope ps(this, s, "heads_losses", 0, 1);
-        launch_stats(st, s);
-    }
     mark(s);
 }
 

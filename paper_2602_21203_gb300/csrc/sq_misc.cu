@@ -4,6 +4,7 @@
 #include "sq_kernels.cuh"
 
 #include <algorithm>
+#include <vector>
 
 namespace sq {
 
@@ -103,7 +104,9 @@ __global__ void __launch_bounds__(256) ln_bwd_row_kernel(LnBwdBatch b, int want_
     const int lb = blockIdx.x - b.block_start[pi];
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const int row = lb * kLnRows + warp;
-    const bool cols = want_cols && (P.dg || P.dbeta || P.dbias);
+    const bool cols = want_cols && (P.dg || P.dbeta || P.dbias) && !P.terms;
+    float* tx = P.terms ? P.terms + (int64_t)row * P.n : nullptr;                  // dn xh of this row
+    float* tn = P.terms ? P.terms + ((int64_t)P.rows + row) * P.n : nullptr;       // dn of this row
     float* my = acc + (size_t)warp * 3 * P.n;
     if (row < P.rows && P.n <= 32 * kVpt) {
         const float* dout = P.dout + (int64_t)row * P.ld_dout;
@@ -143,6 +146,7 @@ __global__ void __launch_bounds__(256) ln_bwd_row_kernel(LnBwdBatch b, int want_
                 my[P.n + j] = dn[k];
                 my[2 * P.n + j] = v;
             }
+            if (tx) { tx[j] = dn[k] * xh[k]; tn[j] = dn[k]; }
         }
     } else if (row < P.rows) {
         const float* dout = P.dout + (int64_t)row * P.ld_dout;
@@ -171,6 +175,7 @@ __global__ void __launch_bounds__(256) ln_bwd_row_kernel(LnBwdBatch b, int want_
                 my[P.n + j] = dn;
                 my[2 * P.n + j] = v;
             }
+            if (tx) { tx[j] = dn * xh; tn[j] = dn; }
         }
     } else if (cols) {
         for (int j = lane; j < P.n; j += 32) { my[j] = 0.f; my[P.n + j] = 0.f; my[2 * P.n + j] = 0.f; }
@@ -725,7 +730,7 @@ void launch_ln_bwd(const LnBwdProblem* p, int n, float* work, cudaStream_t s) {
             blocks += nb;
             off += (int64_t)nb * 3 * b.p[i].n;
             cols = std::max(cols, b.p[i].n);
-            any_col |= (b.p[i].dg || b.p[i].dbeta || b.p[i].dbias);
+            any_col |= (b.p[i].dg || b.p[i].dbeta || b.p[i].dbias) && !b.p[i].terms;
         }
         b.block_start[cnt] = blocks;
         if (!blocks) continue;
@@ -737,6 +742,18 @@ void launch_ln_bwd(const LnBwdProblem* p, int n, float* work, cudaStream_t s) {
         launch_k(ln_bwd_row_kernel, dim3(blocks), dim3(32 * kLnRows), smem, s, b, want ? 1 : 0);
     }
 }
+void launch_ln_bwd_cols(const LnBwdProblem* p, int n, cudaStream_t s) {
+    std::vector<ColSumProblem> cs;
+    for (int i = 0; i < n; ++i) {
+        const LnBwdProblem& q = p[i];
+        if (!q.terms || q.rows <= 0) continue;
+        if (q.dg) cs.push_back(ColSumProblem{q.rows, q.n, q.terms, q.n, q.dg});
+        if (q.dbeta) cs.push_back(ColSumProblem{q.rows, q.n, q.terms + (int64_t)q.rows * q.n, q.n, q.dbeta});
+        if (q.dbias) cs.push_back(ColSumProblem{q.rows, q.n, q.dpre, q.ld_dpre, q.dbias});
+    }
+    if (!cs.empty()) launch_colsum(cs.data(), (int)cs.size(), s);
+}
+
 void launch_colsum(const ColSumProblem* p, int n, cudaStream_t s) {
     for (int base = 0; base < n; base += kMaxLn) {
         const int cnt = std::min(kMaxLn, n - base);
