@@ -124,130 +124,188 @@ struct ConvArgs {
     int* err;
 };
 
-__global__ void __launch_bounds__(128) conv32_tc_kernel(const __grid_constant__ ConvArgs a) {
+// Persistent and warp-specialised: CTA c takes images c, c + gridDim.x, ...  Warp 0 (one
+// lane) loads the filter once and each image by TMA into one of two shared-memory
+// buffers; warp 1 (one lane) owns the tensor memory and issues each image's MMAs into
+// one of two accumulators; warps 2..5 (TMEM lane quarters 2, 3, 0, 1) drain an
+// accumulator (bias, ReLU, mask, stores) while the next image is loaded and multiplied.
+// Barriers: full/empty per image buffer, tfull/tempty per accumulator; every wait is
+// bounded and a wait that gives up records its code in *err and stops that role.
+constexpr int kConvThreads = 192;
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__global__ void __launch_bounds__(kConvThreads) conv32_tc_kernel(const __grid_constant__ ConvArgs a) {
     SQ_KERNEL_ENTRY();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t plane = (uint32_t)a.load_rows * 16;
-    uint8_t* img_s = smem;
-    uint8_t* w_s = smem + 4 * plane;
+    const uint32_t ibytes = 4 * plane;
+    uint8_t* w_s = smem + 2 * ibytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(w_s + kWBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
-    const uint32_t load_bar = smem_u32(bars), mma_bar = smem_u32(bars + 1);
-    const int img = blockIdx.x;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 10);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + 2), tfull0 = smem_u32(bars + 4),
+                   tempty0 = smem_u32(bars + 6), done_bar = smem_u32(bars + 8);
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int n_local = (int)blockIdx.x < a.nimg ? (a.nimg - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const uint32_t cols = 2 * (uint32_t)a.tmem_cols;
 
-    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), a.tmem_cols);
-    if (threadIdx.x == 32) {
-        mbar_init(load_bar, 1);
-        mbar_init(mma_bar, 1);
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), cols);
+    if (threadIdx.x == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(full0 + 8 * b, 1);
+            mbar_init(empty0 + 8 * b, 1);
+            mbar_init(tfull0 + 8 * b, 1);
+            mbar_init(tempty0 + 8 * b, 4);   // one arrival per epilogue warp
+        }
+        mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t img_u = smem_u32(img_s), w_u = smem_u32(w_s);
+    const uint32_t w_u = smem_u32(w_s);
 
-    if (threadIdx.x == 0) {
-        const int boxes = a.load_rows / 128;
-        mbar_expect_tx(load_bar, 4 * plane + kWBytes);
-        for (int c = 0; c < 4; ++c)
-            for (int b = 0; b < boxes; ++b)
-                tma_load_3d(img_u + c * plane + b * 2048, &a.tin, 0, c, img * a.in_rows + b * 128, load_bar);
-        bulk_load(w_u, a.w, kWBytes, load_bar);
-    } else if (threadIdx.x == 32) {
-        constexpr uint32_t idesc = idesc_bf16(128, kCh, false, false);
-        if (mbar_wait(load_bar, 0, a.err, 11)) {
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: the filter with the first image, then image i into buffer i % 2 once
+            // the MMAs of image i - 2 have read it
+            int issued = 0;
+            for (int i = 0; i < n_local; ++i) {
+                const int b = i & 1;
+                if (i >= 2 && !mbar_wait(empty0 + 8 * b, ((i - 2) >> 1) & 1, a.err, 13)) break;
+                const int img = (int)blockIdx.x + i * (int)gridDim.x;
+                const uint32_t dst = smem_u32(smem) + b * ibytes;
+                mbar_expect_tx(full0 + 8 * b, ibytes + (i == 0 ? (uint32_t)kWBytes : 0u));
+                for (int c = 0; c < 4; ++c)
+                    for (int bb = 0; bb < a.load_rows / 128; ++bb)
+                        tma_load_3d(dst + c * plane + bb * 2048, &a.tin, 0, c, img * a.in_rows + bb * 128, full0 + 8 * b);
+                if (i == 0) bulk_load(w_u, a.w, kWBytes, full0);
+                issued = i + 1;
+            }
+            // the last loads have landed before the CTA can finish (immediate unless a consumer gave up)
+            for (int i = issued - 2 < 0 ? 0 : issued - 2; i < issued; ++i)
+                mbar_wait(full0 + 8 * (i & 1), (i >> 1) & 1, a.err, 14);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(128, kCh, false, false);
+            for (int i = 0; i < n_local; ++i) {
+                const int b = i & 1;
+                if (!mbar_wait(full0 + 8 * b, (i >> 1) & 1, a.err, 11)) break;
+                if (i >= 2 && !mbar_wait(tempty0 + 8 * b, ((i - 2) >> 1) & 1, a.err, 15)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t img_u = smem_u32(smem) + b * ibytes;
+                const uint32_t acc = tmem + b * (uint32_t)a.tmem_cols;
+                for (int t = 0; t < a.n_tiles; ++t)
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int row0 = t * 128 + a.off0 + (tap / 3) * a.Wp + (tap % 3);
+                        for (int kc = 0; kc < 2; ++kc) {
+                            const uint64_t ad = plain_desc(img_u + 2 * kc * plane + row0 * 16, plane, 128);
+                            const uint64_t bd = plain_desc(w_u + tap * 2048 + 2 * kc * 512, 512, 128);
+                            mma_bf16(acc + t * kCh, ad, bd, idesc, (tap | kc) ? 1u : 0u);
+                        }
+                    }
+                mma_commit(empty0 + 8 * b);
+                mma_commit(tfull0 + 8 * b);
+            }
+            // every MMA this CTA issued has completed before the tensor memory is freed
+            mma_commit(done_bar);
+            mbar_wait(done_bar, 0, a.err, 16);
+        }
+        __syncwarp();
+    } else {
+        const int quarter = warp % 4;
+        const int wpo = a.out_w + 4;
+        const int64_t out_img = (int64_t)(a.out_h + 4) * wpo * kCh;
+        for (int i = 0; i < n_local; ++i) {
+            const int b = i & 1;
+            const bool have = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, a.err, 12);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int t = 0; t < a.n_tiles; ++t) {
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int row0 = t * 128 + a.off0 + (tap / 3) * a.Wp + (tap % 3);
-                    for (int kc = 0; kc < 2; ++kc) {
-                        const uint64_t ad = plain_desc(img_u + 2 * kc * plane + row0 * 16, plane, 128);
-                        const uint64_t bd = plain_desc(w_u + tap * 2048 + 2 * kc * 512, 512, 128);
-                        mma_bf16(tmem + t * kCh, ad, bd, idesc, (tap | kc) ? 1u : 0u);
+            const int img = (int)blockIdx.x + i * (int)gridDim.x;
+            for (int t = 0; t < a.n_tiles && have; ++t) {
+                uint32_t r0[16], r1[16];
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + b * (uint32_t)a.tmem_cols + t * kCh;
+                tmem_ld16(taddr, r0);
+                tmem_ld16(taddr + 16, r1);
+                const int q = t * 128 + quarter * 32 + lane;
+                const int oy = q / a.Wp, ox = q - (q / a.Wp) * a.Wp;
+                if (oy >= a.out_h || ox >= a.out_w) continue;
+                float v[kCh];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) { v[j] = __uint_as_float(r0[j]); v[16 + j] = __uint_as_float(r1[j]); }
+                const int64_t prow = ((int64_t)(oy + 2) * wpo + ox + 2) * kCh;
+                if (a.bias) {
+#pragma unroll
+                    for (int j = 0; j < kCh; ++j) v[j] += a.bias[j];
+                }
+                if (a.relu) {
+#pragma unroll
+                    for (int j = 0; j < kCh; ++j) v[j] = fmaxf(v[j], 0.f);
+                }
+                if (a.mask) {
+                    const uint4* mk = reinterpret_cast<const uint4*>(a.mask + (int64_t)img * out_img + prow);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const uint4 m4 = mk[c];
+                        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m4);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (!(__bfloat162float(mb[j]) > 0.f)) v[c * 8 + j] = 0.f;
+                    }
+                }
+                if (a.out_phwc) {
+                    uint4* dst = reinterpret_cast<uint4*>(a.out_phwc + (int64_t)img * out_img + prow);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        __align__(16) __nv_bfloat16 hb[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) hb[j] = __float2bfloat16_rn(v[c * 8 + j]);
+                        dst[c] = *reinterpret_cast<const uint4*>(hb);
+                    }
+                }
+                if (a.out_chw || a.out_chw_bf) {
+                    const int64_t plane_px = (int64_t)a.out_h * a.out_w;
+                    const int64_t base = (int64_t)img * kCh * plane_px + (int64_t)oy * a.out_w + ox;
+#pragma unroll
+                    for (int j = 0; j < kCh; ++j) {
+                        if (a.out_chw) a.out_chw[base + j * plane_px] = v[j];
+                        if (a.out_chw_bf) a.out_chw_bf[base + j * plane_px] = __float2bfloat16_rn(v[j]);
                     }
                 }
             }
-        }
-        mma_commit(mma_bar);
-    }
-    __syncwarp();
-    const bool have = mbar_wait(mma_bar, 0, a.err, 12);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int wpo = a.out_w + 4;
-    const int64_t out_img = (int64_t)(a.out_h + 4) * wpo * kCh;
-    for (int t = 0; t < a.n_tiles; ++t) {
-        uint32_t r0[16], r1[16];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + t * kCh;
-        tmem_ld16(taddr, r0);
-        tmem_ld16(taddr + 16, r1);
-        const int q = t * 128 + warp * 32 + lane;
-        const int oy = q / a.Wp, ox = q - (q / a.Wp) * a.Wp;
-        if (!have || oy >= a.out_h || ox >= a.out_w) continue;
-        float v[kCh];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) { v[j] = __uint_as_float(r0[j]); v[16 + j] = __uint_as_float(r1[j]); }
-        const int64_t prow = ((int64_t)(oy + 2) * wpo + ox + 2) * kCh;
-        if (a.bias) {
-#pragma unroll
-            for (int j = 0; j < kCh; ++j) v[j] += a.bias[j];
-        }
-        if (a.relu) {
-#pragma unroll
-            for (int j = 0; j < kCh; ++j) v[j] = fmaxf(v[j], 0.f);
-        }
-        if (a.mask) {
-            const uint4* mk = reinterpret_cast<const uint4*>(a.mask + (int64_t)img * out_img + prow);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const uint4 m4 = mk[c];
-                const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&m4);
-#pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (!(__bfloat162float(mb[j]) > 0.f)) v[c * 8 + j] = 0.f;
-            }
-        }
-        if (a.out_phwc) {
-            uint4* dst = reinterpret_cast<uint4*>(a.out_phwc + (int64_t)img * out_img + prow);
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                __align__(16) __nv_bfloat16 hb[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) hb[j] = __float2bfloat16_rn(v[c * 8 + j]);
-                dst[c] = *reinterpret_cast<const uint4*>(hb);
-            }
-        }
-        if (a.out_chw || a.out_chw_bf) {
-            const int64_t plane_px = (int64_t)a.out_h * a.out_w;
-            const int64_t base = (int64_t)img * kCh * plane_px + (int64_t)oy * a.out_w + ox;
-#pragma unroll
-            for (int j = 0; j < kCh; ++j) {
-                if (a.out_chw) a.out_chw[base + j * plane_px] = v[j];
-                if (a.out_chw_bf) a.out_chw_bf[base + j * plane_px] = __float2bfloat16_rn(v[j]);
-            }
+            // this warp's lanes of the accumulator are read: it may take the image after next
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty0 + 8 * b);
+            if (!have) break;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        tmem_dealloc(tmem, a.tmem_cols);
+        tmem_dealloc(tmem, cols);
     }
 }
 
 // ---------------------------------------------------------------- weight gradient
 // D_tap[co, ci] += sum_q dy[q, co] x[q + origin(tap), ci] over the virtual grid of
-// the input's padded row width (dy = 0 outside the valid outputs).  A = dy^T staged
-// by the threads K-major (q-chunks of 8, 512 B apart: rows 32..127 of the 128-row MMA
-// alias later chunks and land in accumulator rows that are never read); B = the x
-// window, MN-major: channel planes (8 channels) PLANE apart, K groups of 8 pixel rows
-// 128 B apart.  Nine 32-column accumulators.
+// the input's padded row width (dy = 0 outside the valid outputs), origin(ky, kx) =
+// (2 + ky) Wp + 2 + kx.  A = dy^T staged by the threads K-major (q-chunks of 8, 512 B
+// apart: rows 32..127 of the 128-row MMA alias later chunks and land in accumulator
+// rows that are never read).  B stacks the three horizontal taps: shared memory holds
+// twelve slots (kx, channel plane), slot (kx, p) = rows origin(0, kx) + [0, slot_rows)
+// of plane p, SLOT apart, so one MN-major operand of N = 96 (kx, ci) starting ky Wp
+// rows into every slot covers taps (ky, 0..2); its accumulator columns ky 96 + kx 32 +
+// ci are tap 32 + ci.  Three MMAs per 16 pixels instead of nine.
 struct WgradArgs {
-    CUtensorMap tin;                 // layer input planes, dims {8, 4, nimg * in_rows}
+    CUtensorMap tin;                 // layer input planes, dims {8, 4, nimg * in_rows}, box {8, 1, box_rows}
     const __nv_bfloat16* dy;         // padded-HWC gradient at the layer's pre-activation (grid out_w + 4)
-    int nimg, in_rows, Wp, out_h, out_w, kq, load_rows, per_cta;
+    int nimg, in_rows, Wp, out_h, out_w, kq, slot_rows, box_rows, per_cta;
     float* work;                     // [ctas, 32, 289]: partial dW (co, ci*9 + tap) and db (col 288)
     int* err;
 };
@@ -265,8 +323,8 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
     SQ_KERNEL_ENTRY();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const uint32_t plane = (uint32_t)a.load_rows * 16;
-    const uint32_t xbytes = 4 * plane;
+    const uint32_t slot = (uint32_t)a.slot_rows * 16;
+    const uint32_t xbytes = 12 * slot;
     const uint32_t dybytes = (uint32_t)(a.kq / 8) * 512 + 2048;   // + slack read by the aliased rows
     uint8_t* xs[2] = {smem, smem + xbytes};
     uint8_t* ds[2] = {smem + 2 * xbytes, smem + 2 * xbytes + dybytes};
@@ -299,7 +357,7 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
     float bsum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int cc = threadIdx.x % 4;         // the 8-channel chunk this thread stages
     bool ok = true;
-    constexpr uint32_t idesc = idesc_bf16(128, kCh, false, true);
+    constexpr uint32_t idesc = idesc_bf16(128, 3 * kCh, false, true);
 
     // Every thread runs every iteration (the barriers inside must match); a wait that
     // gives up only records the error and stops further MMA issue.
@@ -307,12 +365,14 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
         const int li = i - i0, b = li & 1;
         if (li >= 2 && !mbar_wait(mma_bar[b], ((li - 2) >> 1) & 1, a.err, 21)) ok = false;
         if (threadIdx.x == 0 && ok) {
-            const int boxes = a.load_rows / 128;
+            const int boxes = a.slot_rows / a.box_rows;
+            const int row0 = i * a.in_rows + 2 * a.Wp + 2;
             mbar_expect_tx(tma_bar[b], xbytes);
-            for (int c = 0; c < 4; ++c)
-                for (int bb = 0; bb < boxes; ++bb)
-                    tma_load_3d(smem_u32(xs[b]) + c * plane + bb * 2048, &a.tin, 0, c, i * a.in_rows + bb * 128,
-                                tma_bar[b]);
+            for (int kx = 0; kx < 3; ++kx)
+                for (int c = 0; c < 4; ++c)
+                    for (int bb = 0; bb < boxes; ++bb)
+                        tma_load_3d(smem_u32(xs[b]) + (kx * 4 + c) * slot + bb * a.box_rows * 16, &a.tin, 0, c,
+                                    row0 + kx + bb * a.box_rows, tma_bar[b]);
         }
         // stage dy^T: element (co, q) at (q / 8) * 512 + co * 16 + (q % 8) * 2; a thread's
         // loads for eight pixels are issued before any of them is stored
@@ -350,15 +410,15 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
                 ok = false;
             } else {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t xu = smem_u32(xs[b]), du = smem_u32(ds[b]);
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int org = (2 + tap / 3) * a.Wp + 2 + tap % 3;
-                    for (int k = 0; k < a.kq / 16; ++k) {
-                        const uint64_t ad = plain_desc(du + k * 1024, 512, 128);
-                        const uint64_t bd = plain_desc(xu + (k * 16 + org) * 16, 128, plane);
-                        mma_bf16(tmem + tap * kCh, ad, bd, idesc, (i > i0 || k > 0) ? 1u : 0u);
-                    }
-                }
+                // descriptors built once; each MMA adds its start offset in 16-byte units
+                // (shared-memory addresses stay below 2^18: the 14-bit field never carries)
+                const uint64_t a0 = plain_desc(smem_u32(ds[b]), 512, 128);
+                const uint64_t b0 = plain_desc(smem_u32(xs[b]), 128, slot);
+                for (int k = 0; k < a.kq / 16; ++k)
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky)
+                        mma_bf16(tmem + ky * 3 * kCh, a0 + (uint64_t)(k * 64), b0 + (uint64_t)(k * 16 + ky * a.Wp),
+                                 idesc, (i > i0 || k > 0) ? 1u : 0u);
             }
             mma_commit(mma_bar[b]);
         }
@@ -571,12 +631,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Planes of a padded-HWC tensor: dims {8 channels, 4 planes, rows}, box {8, 1, 128}.
-bool plane_map(CUtensorMap* m, const __nv_bfloat16* base, int64_t rows) {
+bool plane_map(CUtensorMap* m, const __nv_bfloat16* base, int64_t rows, int box_rows = 128) {
     auto fn = encode_fn();
-    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15)) return false;
+    if (!fn || (reinterpret_cast<uintptr_t>(base) & 15) || box_rows < 8 || box_rows > 256) return false;
     cuuint64_t dims[3] = {8, 4, (cuuint64_t)rows};
     cuuint64_t strides[2] = {16, 64};
-    cuuint32_t box[3] = {8, 1, 128};
+    cuuint32_t box[3] = {8, 1, (cuuint32_t)box_rows};
     cuuint32_t estr[3] = {1, 1, 1};
     std::memset(m, 0, sizeof(*m));
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(base), dims, strides, box, estr,
@@ -586,9 +646,11 @@ bool plane_map(CUtensorMap* m, const __nv_bfloat16* base, int64_t rows) {
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-size_t conv_smem(int load_rows) { return 1024 + 4 * (size_t)load_rows * 16 + kWBytes + 64; }
-size_t wgrad_smem(int load_rows, int kq) {
-    return 1024 + wgrad_operand_bytes(4 * (uint32_t)load_rows * 16, (uint32_t)(kq / 8) * 512 + 2048) + 64 +
+size_t conv_smem(int load_rows) { return 1024 + 2 * 4 * (size_t)load_rows * 16 + kWBytes + 10 * 8 + 16; }
+constexpr int kConvCtasPerSm = 2;   // resident CTAs per SM of the persistent convolution
+int g_num_sms = 152;                 // set by conv_tc_prepare
+size_t wgrad_smem(int slot_rows, int kq) {
+    return 1024 + wgrad_operand_bytes(12 * (uint32_t)slot_rows * 16, (uint32_t)(kq / 8) * 512 + 2048) + 64 +
            128 * 8 * 4 + 16;
 }
 
@@ -611,7 +673,8 @@ int launch_conv32_tc(const ConvTc& c, int* err, cudaStream_t s) {
     a.off0 = c.off0; a.bias = c.bias; a.relu = c.relu; a.mask = c.mask; a.out_phwc = c.out_phwc;
     a.out_chw = c.out_chw; a.out_chw_bf = c.out_chw_bf; a.err = err;
     const size_t smem = conv_smem(a.load_rows);
-    launch_k(conv32_tc_kernel, dim3(c.nimg), dim3(128), smem, s, a);
+    const int ctas = std::min(c.nimg, g_num_sms * kConvCtasPerSm);
+    launch_k(conv32_tc_kernel, dim3(ctas), dim3(kConvThreads), smem, s, a);
     return 0;
 }
 
@@ -628,15 +691,19 @@ int launch_wgrad32_tc_partials(const WgradTc& c, int per_cta, float* work, int* 
     WgradArgs a;
     std::memset(&a, 0, sizeof(a));
     a.kq = round_up(c.out_h * c.Wp, 16);
-    const int max_row = a.kq - 1 + (4 * c.Wp + 4);
-    a.load_rows = round_up(std::max(max_row + 1, c.in_rows), 128);
-    if (wgrad_smem(a.load_rows, a.kq) > 220 * 1024 || (a.kq / 8) * 512 + 2048 > kDyBytesMax + 2048) return -1;
-    if (!plane_map(&a.tin, c.x, (int64_t)c.nimg * c.in_rows)) return -2;
+    // a slot covers the rows every K step of every vertical tap reads: kq + 2 Wp, loaded in
+    // equal boxes of at most 256 rows, a multiple of 8 rows (128 B) each
+    const int need = a.kq + 2 * c.Wp;
+    const int nb = (need + 255) / 256;
+    a.box_rows = round_up((need + nb - 1) / nb, 8);
+    a.slot_rows = nb * a.box_rows;
+    if (wgrad_smem(a.slot_rows, a.kq) > 220 * 1024 || (a.kq / 8) * 512 + 2048 > kDyBytesMax + 2048) return -1;
+    if (!plane_map(&a.tin, c.x, (int64_t)c.nimg * c.in_rows, a.box_rows)) return -2;
     a.per_cta = per_cta;
     const int grid = (c.nimg + per_cta - 1) / per_cta;
     a.dy = c.dy; a.nimg = c.nimg; a.in_rows = c.in_rows; a.Wp = c.Wp; a.out_h = c.out_h; a.out_w = c.out_w;
     a.work = work; a.err = err;
-    launch_k(wgrad32_tc_kernel, dim3(grid), dim3(128), wgrad_smem(a.load_rows, a.kq), s, a);
+    launch_k(wgrad32_tc_kernel, dim3(grid), dim3(128), wgrad_smem(a.slot_rows, a.kq), s, a);
     return 0;
 }
 
@@ -655,6 +722,10 @@ int launch_wgrad32_tc(const WgradTc& c, float* work, float* dw, float* db, int* 
 }
 
 void conv_tc_prepare() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        sms > 0)
+        g_num_sms = sms;
     cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(wgrad32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     encode_fn();

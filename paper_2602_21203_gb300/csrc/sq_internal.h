@@ -208,7 +208,7 @@ struct squint_handle {
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, int64_t> graph_kernels;
     // concurrent branches of one update: library-owned streams joined back before it ends
-    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+    cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t fork_ev[32] = {};
     int fork_next = 0;
     bool serial = false;                  // profiling: every launch in order on the main stream

@@ -711,8 +711,9 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     float* W = params;
     float* G = grads;
     float* stats = d_stats + 8 * j;
-    // branches: s1 encoder backward, s2 weight gradients of the MLPs, s3 critic forward / polyak
-    cudaStream_t s1 = branch(s, 0), s2 = branch(s, 1), s3 = branch(s, 2);
+    // branches: s1 encoder backward, s2 weight gradients of the MLPs, s3 critic forward / polyak,
+    // s4 the encoder's inner weight gradients beside its data-gradient chain
+    cudaStream_t s1 = branch(s, 0), s2 = branch(s, 1), s3 = branch(s, 2), s4 = branch(s, 3);
     auto cast_rows = [&](const float* src, int64_t ld, int rows, int cols, __nv_bfloat16* dst, int64_t ldh,
                          cudaStream_t st) {
         if (!bf16) return;
@@ -984,6 +985,10 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             const int pc = wgrad32_per_cta(B);
             const int64_t wslot = (int64_t)kCh32 * (kCh32 * 9 + 1);
             const int chunk = rc_chunk ? rc_chunk : B;
+            // without recompute, layer l's weight gradient runs on s4 as soon as its output
+            // gradient exists, beside the data gradients of the layers below (chunks of the
+            // recompute path reuse the activation buffers, so they stay in one order)
+            cudaStream_t sw = rc_chunk ? s1 : s4;
             for (int i0 = 0; i0 < B; i0 += chunk) {
                 const int n = std::min(chunk, B - i0);
                 if (rc_chunk) enc_tc(i0, n, nconv - 2, s1);
@@ -1002,14 +1007,15 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
                     wt.in_rows = (cv.h + 4) * wt.Wp;
                     wt.out_h = cv.oh; wt.out_w = cv.ow;
                     {
-                        ProfScope ps(this, s1, "conv_tc_wgrad", conv_flops(cv, n), 0);
+                        fork(s1, sw);
+                        ProfScope ps(this, sw, "conv_tc_wgrad", conv_flops(cv, n), 0);
                         int rc;
                         if (rc_chunk) {
                             float* work = wgrad_tc_work + (int64_t)(l - 1) * wgrad32_tc_workspace(B) +
                                           (int64_t)(i0 / pc) * wslot;
-                            rc = launch_wgrad32_tc_partials(wt, pc, work, d_err, s1);
+                            rc = launch_wgrad32_tc_partials(wt, pc, work, d_err, sw);
                         } else {
-                            rc = launch_wgrad32_tc(wt, wgrad_tc_work, G + cv.wo, G + cv.bo, d_err, s1);
+                            rc = launch_wgrad32_tc(wt, wgrad_tc_work, G + cv.wo, G + cv.bo, d_err, sw);
                         }
                         if (rc != 0) launch_failed = true;
                     }
@@ -1041,8 +1047,11 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
                 }
             ConvShape sh{B, c0.cin, c0.h, c0.w, c0.cout, c0.s, c0.oh, c0.ow, (int64_t)c0.cin * c0.h * c0.w,
                          (int64_t)c0.cout * c0.oh * c0.ow};
-            ProfScope ps(this, s1, "conv_f32_wgrad", conv_flops(c0, B), 0);
-            launch_conv_wgrad<float>(sh, dconv_a, x2, G + c0.wo, G + c0.bo, wgrad_work, s1);
+            {
+                ProfScope ps(this, s1, "conv_f32_wgrad", conv_flops(c0, B), 0);
+                launch_conv_wgrad<float>(sh, dconv_a, x2, G + c0.wo, G + c0.bo, wgrad_work, s1);
+            }
+            fork(sw, s1);   // the inner layers' weight gradients before the encoder's Adam
         }
         for (int l = tc_conv ? -1 : nconv - 1; l >= 0; --l) {
             const ConvL& cv = L.conv[l];
