@@ -54,37 +54,49 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
     const float denom = 255.0f * (float)(a.f * a.f);
     const int64_t row = (int64_t)which * a.B + b;
     float* xo = a.x + row * n_out;
-    // f = 4 with 4-byte-aligned frame rows: a thread per output column j, one output row
-    // per warp group; each of the 4 source rows contributes its 4 bytes through two aligned
-    // 32-bit words, a funnel shift and one dp4a (exact integer sums), except at the
-    // replicate-padded edges, which take the per-byte path
-    if (a.f == 4 && (a.W & 3) == 0 && ws <= (int)blockDim.x && (blockDim.x % ws) == 0) {
-        const int j = threadIdx.x % ws;
+    // f = 4 with 4-byte-aligned frame rows: a lane per output column j, a warp per output
+    // row.  Each of the 4 source rows gives the lane's 4 bytes as one byte permute of two
+    // aligned 32-bit words and one dp4a (exact integer sums); the permute selector, fixed
+    // per lane, also replicates the edge byte where the shifted window leaves the frame
+    // (replicate padding), so every lane runs the same instructions.
+    if (a.f == 4 && (a.W & 3) == 0 && ws == 32 && (blockDim.x % 32) == 0) {
+        const int j = threadIdx.x % 32;
         const int x0 = j * 4 + dx - a.pad;
-        const bool interior = x0 >= 0 && x0 + 3 <= a.W - 1;
-        const int wq = x0 >> 2, sh = (x0 & 3) * 8;
-        for (int ri = threadIdx.x / ws; ri < a.C * hs; ri += blockDim.x / ws) {
-            const int c = ri / hs, i = ri - c * hs;
-            uint32_t sum = 0;
+        const int wpr = a.W / 4;                        // words per frame row
+        int wlo;
+        uint32_t sel = 0;
+        if (x0 >= 0 && x0 + 3 <= a.W - 1) {             // interior: bytes k .. k+3 of (lo, hi)
+            wlo = x0 >> 2;
+            const int k = x0 & 3;
+            sel = (uint32_t)k | ((uint32_t)(k + 1) << 4) | ((uint32_t)(k + 2) << 8) | ((uint32_t)(k + 3) << 12);
+        } else if (x0 < 0) {                            // left edge: bytes max(x0 + v, 0) of the first word
+            wlo = 0;
 #pragma unroll
-            for (int uu = 0; uu < 4; ++uu) {
-                const int y = min(max(i * 4 + uu + dy - a.pad, 0), a.H - 1);
-                const uint8_t* rp = frame + ((int64_t)c * a.H + y) * a.W;
-                if (interior) {
-                    const uint32_t* w32 = reinterpret_cast<const uint32_t*>(rp);
-                    const uint32_t lo = w32[wq];
-                    const uint32_t hi = sh ? w32[wq + 1] : 0u;
-                    sum = __dp4a(__funnelshift_r(lo, hi, sh), 0x01010101u, sum);
-                } else {
+            for (int v = 0; v < 4; ++v) sel |= (uint32_t)max(x0 + v, 0) << (4 * v);
+        } else {                                        // right edge: bytes of the last word (as hi)
+            wlo = wpr - 2;
 #pragma unroll
-                    for (int vv = 0; vv < 4; ++vv) sum += rp[min(max(x0 + vv, 0), a.W - 1)];
+            for (int v = 0; v < 4; ++v) sel |= (uint32_t)(4 + min(x0 + v, a.W - 1) - (a.W - 4)) << (4 * v);
+        }
+        const int whi = min(wlo + 1, wpr - 1);
+        const uint32_t* f32 = reinterpret_cast<const uint32_t*>(frame);
+        const int warps = blockDim.x / 32;
+        for (int c = 0; c < a.C; ++c) {
+            const uint32_t* plane32 = f32 + (int64_t)c * a.H * wpr;
+            for (int i = threadIdx.x / 32; i < hs; i += warps) {
+                uint32_t sum = 0;
+#pragma unroll
+                for (int uu = 0; uu < 4; ++uu) {
+                    const int y = min(max(i * 4 + uu + dy - a.pad, 0), a.H - 1);
+                    const uint32_t* rp = plane32 + y * wpr;
+                    sum = __dp4a(__byte_perm(rp[wlo], rp[whi], sel), 0x01010101u, sum);
                 }
+                const int o = (c * hs + i) * 32 + j;
+                const float val = (float)sum / denom - 0.5f;
+                xo[o] = val;
+                if (a.x_bf) a.x_bf[row * n_out + o] = __float2bfloat16_rn(val);
+                if (a.sums) a.sums[row * n_out + o] = (uint16_t)sum;
             }
-            const int o = ri * ws + j;
-            const float val = (float)sum / denom - 0.5f;
-            xo[o] = val;
-            if (a.x_bf) a.x_bf[row * n_out + o] = __float2bfloat16_rn(val);
-            if (a.sums) a.sums[row * n_out + o] = (uint16_t)sum;
         }
     } else
     for (int o = threadIdx.x; o < n_out; o += blockDim.x) {
