@@ -167,6 +167,9 @@ struct squint_handle {
     }
     void quantize_weights(const std::vector<sq::QuantItem>& q, cudaStream_t s);
     std::vector<sq::CastItem> cast_critic, cast_actor, cast_target;
+    // the same BF16 copies as segments of the critic / actor / target ranges, written by
+    // Adam and polyak in the update (the casts above serve full refreshes)
+    std::vector<sq::BfSeg> seg_critic, seg_actor, seg_target;
     float* proj_terms = nullptr;               // [2][B, D] deferred LayerNorm column-sum terms
     __nv_bfloat16* z_h = nullptr;              // [2B, F]
     __nv_bfloat16* xa_h = nullptr;             // [2B, Da8]

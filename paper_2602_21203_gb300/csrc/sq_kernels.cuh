@@ -239,16 +239,28 @@ struct StatsArgs {
 void launch_stats(const StatsArgs& a, cudaStream_t s);
 
 // ---------------------------------------------------------------- optimiser
+// A weight matrix inside an updated range whose padded BF16 copy is written by the same
+// kernel: element (r, c) of the rows x cols block at offset `off` from the range start
+// goes to dst[r * ld + c] (pad columns are left as they are).
+struct BfSeg { int64_t off; int rows, cols; int64_t ld; __nv_bfloat16* dst; };
+constexpr int kMaxBfSeg = 8;
+
 struct AdamArgs {
     float* p; const float* g; float* m; float* v; int64_t n;
     const int32_t* step;          // device step count (already incremented)
     double lr, b1, b2, eps;
     const int32_t* enable;        // null or device flag
     __nv_bfloat16* p_bf;          // optional BF16 copy of p
+    BfSeg seg[kMaxBfSeg];         // padded BF16 copies of the range's weight matrices
+    int n_seg;
 };
 void launch_adam(const AdamArgs& a, cudaStream_t s);
 
-struct PolyakArgs { float* target; const float* src; int64_t n; float tau; int64_t* update_idx; };
+struct PolyakArgs {
+    float* target; const float* src; int64_t n; float tau; int64_t* update_idx;
+    BfSeg seg[kMaxBfSeg];         // padded BF16 copies of the target weight matrices
+    int n_seg;
+};
 void launch_polyak(const PolyakArgs& a, cudaStream_t s);
 // dx = dy * (y > 0), elementwise over n values.
 template <typename T> void launch_relu_bwd(int64_t n, const T* dy, const T* y, T* dx, cudaStream_t s);

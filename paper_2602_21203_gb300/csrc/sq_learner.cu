@@ -577,6 +577,25 @@ int squint_handle::allocate() {
             for (const auto& ly : L.critic[e]) { cast_critic.push_back(item(ly, false)); cast_target.push_back(item(ly, true)); }
         if (L.D > 0) cast_actor.push_back(item(L.aproj, false));
         for (const auto& ly : L.actor) cast_actor.push_back(item(ly, false));
+        auto seg = [&](const Lin& ly, int64_t begin, bool tgt) {
+            const LinBf& lb = lin_bf[ly.w];
+            return BfSeg{ly.w - begin, ly.out, ly.in, lb.ld, tgt ? lb.tg : lb.on};
+        };
+        if (L.D > 0) {
+            seg_critic.push_back(seg(L.cproj, L.critic_begin, false));
+            seg_target.push_back(seg(L.cproj, L.critic_begin, true));
+            seg_actor.push_back(seg(L.aproj, L.actor_begin, false));
+        }
+        for (int e = 0; e < 2; ++e)
+            for (const auto& ly : L.critic[e]) {
+                seg_critic.push_back(seg(ly, L.critic_begin, false));
+                seg_target.push_back(seg(ly, L.critic_begin, true));
+            }
+        for (const auto& ly : L.actor) seg_actor.push_back(seg(ly, L.actor_begin, false));
+        if ((int)seg_critic.size() > kMaxBfSeg || (int)seg_actor.size() > kMaxBfSeg) {
+            g_last_error = "too many weight matrices for the fused BF16 copies";
+            return SQUINT_EINVAL;
+        }
         if (fp8) {
             auto q = [&](const Lin& ly, bool tgt) {
                 const LinBf& lb = lin_bf[ly.w];
@@ -733,14 +752,21 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ProfScope ps(this, st, "layernorm_bwd", bytes, 1);
         launch_ln_bwd(p, n, ln_work, st);
     };
-    auto adam = [&](int64_t begin, int64_t end, const int32_t* step, const int32_t* enable, cudaStream_t st) {
+    auto adam = [&](int64_t begin, int64_t end, const int32_t* step, const int32_t* enable, cudaStream_t st,
+                    const std::vector<BfSeg>* segs = nullptr) {
         if (end <= begin) return;                  // empty range (state-based: no encoder)
         AdamArgs ad{};
+        if (segs) {
+            for (size_t k = 0; k < segs->size(); ++k) ad.seg[k] = (*segs)[k];
+            ad.n_seg = (int)segs->size();
+        }
         ad.p = W + begin; ad.g = G + begin; ad.m = adam_m + begin; ad.v = adam_v + begin;
         ad.n = end - begin;
         ad.step = step; ad.enable = enable;
         ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
-        ProfScope ps(this, st, "adam", 28.0 * (double)ad.n, 1);
+        double bf_bytes = 0;   // the BF16 copies written alongside
+        for (int k = 0; k < ad.n_seg; ++k) bf_bytes += 2.0 * ad.seg[k].rows * ad.seg[k].cols;
+        ProfScope ps(this, st, "adam", 28.0 * (double)ad.n + bf_bytes, 1);
         launch_adam(ad, st);
     };
     auto conv_flops = [&](const ConvL& cv, int nimg) { return 2.0 * nimg * cv.oh * cv.ow * cv.cout * cv.cin * 9; };
@@ -964,11 +990,8 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     }
     mark(s);
     // ---- a12 (critic range): Adam over critic projection + critics, BF16 copies
-    adam(L.critic_begin, L.critic_end, d_steps + 0, nullptr, s);
-    if (bf16) {
-        ProfScope ps(this, s, "cast_bf16", 6.0 * (double)(L.critic_end - L.critic_begin), 1);
-        launch_cast_rows(cast_critic.data(), (int)cast_critic.size(), s);
-    }
+    // (Adam writes the BF16 copies of the critic weights as it updates them)
+    adam(L.critic_begin, L.critic_end, d_steps + 0, nullptr, s, bf16 ? &seg_critic : nullptr);
     quantize_weights(quant_critic, s);
 
     // ---- a11 (encoder part) + a12 (encoder range) on branch s1, beside the actor step
@@ -1078,14 +1101,17 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     // ---- a16 on branch s3: polyak of the updated critics, BF16 target copies
     fork(s, s3);
     {
-        PolyakArgs pa{target, W + L.critic_begin, L.target_n, (float)c.tau, nullptr};
-        {
-            ProfScope ps(this, s3, "polyak", 12.0 * (double)L.target_n, 1);
-            launch_polyak(pa, s3);
+        PolyakArgs pa{};
+        pa.target = target; pa.src = W + L.critic_begin; pa.n = L.target_n; pa.tau = (float)c.tau;
+        if (bf16) {   // polyak writes the BF16 copies of the target weights as it updates them
+            for (size_t k = 0; k < seg_target.size(); ++k) pa.seg[k] = seg_target[k];
+            pa.n_seg = (int)seg_target.size();
         }
-        if (bf16) {
-            ProfScope ps(this, s3, "cast_bf16", 6.0 * (double)L.target_n, 1);
-            launch_cast_rows(cast_target.data(), (int)cast_target.size(), s3);
+        {
+            double bf_bytes = 0;
+            for (int k = 0; k < pa.n_seg; ++k) bf_bytes += 2.0 * pa.seg[k].rows * pa.seg[k].cols;
+            ProfScope ps(this, s3, "polyak", 12.0 * (double)L.target_n + bf_bytes, 1);
+            launch_polyak(pa, s3);
         }
         quantize_weights(quant_target, s3);
     }
@@ -1181,11 +1207,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             GemmBuilder gb(this, s, bf16);
             gb.dw(Mat{dproj, Dd, dproj_h, Dd}, B, zt, ap, G + L.aproj.w);
         }
-        adam(L.actor_begin, L.actor_end, d_steps + 1, d_do_actor, s);
-        if (bf16) {
-            ProfScope ps(this, s, "cast_bf16", 6.0 * (double)(L.actor_end - L.actor_begin), 1);
-            launch_cast_rows(cast_actor.data(), (int)cast_actor.size(), s);
-        }
+        adam(L.actor_begin, L.actor_end, d_steps + 1, d_do_actor, s, bf16 ? &seg_actor : nullptr);
         quantize_weights(quant_actor, s);
     }
     // join the encoder branch (the polyak / temperature / statistics branch joined above)

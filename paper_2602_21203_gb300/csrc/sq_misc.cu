@@ -623,7 +623,18 @@ __device__ __forceinline__ float adam_one(float p, float g, float& m, float& v, 
 }
 
 // Elementwise Adam over [0, n): scalar head up to 16-byte alignment, float4 body, scalar tail.
-__global__ void adam_kernel(AdamArgs a) {
+__device__ __forceinline__ void seg_store(const BfSeg* seg, int n_seg, int64_t e, float v) {
+    for (int k = 0; k < n_seg; ++k) {
+        const int64_t rel = e - seg[k].off;
+        if (rel >= 0 && rel < (int64_t)seg[k].rows * seg[k].cols) {
+            const int64_t r = rel / seg[k].cols;
+            seg[k].dst[r * seg[k].ld + (rel - r * seg[k].cols)] = __float2bfloat16_rn(v);
+            return;
+        }
+    }
+}
+
+__global__ void adam_kernel(const __grid_constant__ AdamArgs a) {
     SQ_KERNEL_ENTRY();
     if (a.enable && !*a.enable) return;
     __shared__ float bc[2];
@@ -644,6 +655,7 @@ __global__ void adam_kernel(AdamArgs a) {
         const float p = adam_one(a.p[i], a.g[i], m, v, b1, b2, c1, c2, lr, ep, bc1, bc2);
         a.m[i] = m; a.v[i] = v; a.p[i] = p;
         if (a.p_bf) a.p_bf[i] = __float2bfloat16_rn(p);
+        if (a.n_seg) seg_store(a.seg, a.n_seg, i, p);
     }
     float4* p4 = reinterpret_cast<float4*>(a.p + head);
     const float4* g4 = reinterpret_cast<const float4*>(a.g + head);
@@ -662,12 +674,20 @@ __global__ void adam_kernel(AdamArgs a) {
             a.p_bf[e] = __float2bfloat16_rn(p.x); a.p_bf[e + 1] = __float2bfloat16_rn(p.y);
             a.p_bf[e + 2] = __float2bfloat16_rn(p.z); a.p_bf[e + 3] = __float2bfloat16_rn(p.w);
         }
+        if (a.n_seg) {
+            const int64_t e = head + 4 * i;
+            seg_store(a.seg, a.n_seg, e, p.x);
+            seg_store(a.seg, a.n_seg, e + 1, p.y);
+            seg_store(a.seg, a.n_seg, e + 2, p.z);
+            seg_store(a.seg, a.n_seg, e + 3, p.w);
+        }
     }
     for (int64_t i = head + 4 * nv + tid; i < a.n; i += stride) {
         float m = a.m[i], v = a.v[i];
         const float p = adam_one(a.p[i], a.g[i], m, v, b1, b2, c1, c2, lr, ep, bc1, bc2);
         a.m[i] = m; a.v[i] = v; a.p[i] = p;
         if (a.p_bf) a.p_bf[i] = __float2bfloat16_rn(p);
+        if (a.n_seg) seg_store(a.seg, a.n_seg, i, p);
     }
 }
 
@@ -679,11 +699,14 @@ __global__ void relu_bwd_kernel(int64_t n, const T* __restrict__ dy, const T* __
         dx[i] = y[i] > T(0) ? dy[i] : T(0);
 }
 
-__global__ void polyak_kernel(PolyakArgs a) {
+__global__ void polyak_kernel(const __grid_constant__ PolyakArgs a) {
     SQ_KERNEL_ENTRY();
     const float keep = 1.0f - a.tau;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x)
-        a.target[i] = keep * a.target[i] + a.tau * a.src[i];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float t = keep * a.target[i] + a.tau * a.src[i];
+        a.target[i] = t;
+        if (a.n_seg) seg_store(a.seg, a.n_seg, i, t);
+    }
     if (a.update_idx && blockIdx.x == 0 && threadIdx.x == 0) *a.update_idx += 1;
 }
 
