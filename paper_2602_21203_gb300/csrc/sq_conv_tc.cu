@@ -221,18 +221,30 @@ __global__ void __launch_bounds__(kConvThreads) conv32_tc_kernel(const __grid_co
         const int quarter = warp % 4;
         const int wpo = a.out_w + 4;
         const int64_t out_img = (int64_t)(a.out_h + 4) * wpo * kCh;
+        // a thread's output pixel in each tile, and the bias, are the same for every image
+        int oy_t[4], ox_t[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int q = t * 128 + quarter * 32 + lane;
+            oy_t[t] = q / a.Wp;
+            ox_t[t] = q - oy_t[t] * a.Wp;
+        }
+        float bias_r[kCh];
+#pragma unroll
+        for (int j = 0; j < kCh; ++j) bias_r[j] = a.bias ? a.bias[j] : 0.f;
         for (int i = 0; i < n_local; ++i) {
             const int b = i & 1;
             const bool have = mbar_wait(tfull0 + 8 * b, (i >> 1) & 1, a.err, 12);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int img = (int)blockIdx.x + i * (int)gridDim.x;
-            for (int t = 0; t < a.n_tiles && have; ++t) {
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (t >= a.n_tiles || !have) break;
                 uint32_t r0[16], r1[16];
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + b * (uint32_t)a.tmem_cols + t * kCh;
                 tmem_ld16(taddr, r0);
                 tmem_ld16(taddr + 16, r1);
-                const int q = t * 128 + quarter * 32 + lane;
-                const int oy = q / a.Wp, ox = q - (q / a.Wp) * a.Wp;
+                const int oy = oy_t[t], ox = ox_t[t];
                 if (oy >= a.out_h || ox >= a.out_w) continue;
                 float v[kCh];
 #pragma unroll
@@ -240,7 +252,7 @@ __global__ void __launch_bounds__(kConvThreads) conv32_tc_kernel(const __grid_co
                 const int64_t prow = ((int64_t)(oy + 2) * wpo + ox + 2) * kCh;
                 if (a.bias) {
 #pragma unroll
-                    for (int j = 0; j < kCh; ++j) v[j] += a.bias[j];
+                    for (int j = 0; j < kCh; ++j) v[j] += bias_r[j];
                 }
                 if (a.relu) {
 #pragma unroll
