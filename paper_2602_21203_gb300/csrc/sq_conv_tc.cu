@@ -307,9 +307,11 @@ __global__ void __launch_bounds__(kConvThreads) conv32_tc_kernel(const __grid_co
 // ---------------------------------------------------------------- weight gradient
 // D_tap[co, ci] += sum_q dy[q, co] x[q + origin(tap), ci] over the virtual grid of
 // the input's padded row width (dy = 0 outside the valid outputs), origin(ky, kx) =
-// (2 + ky) Wp + 2 + kx.  A = dy^T staged by the threads K-major (q-chunks of 8, 512 B
-// apart: rows 32..127 of the 128-row MMA alias later chunks and land in accumulator
-// rows that are never read).  B stacks the three horizontal taps: shared memory holds
+// (2 + ky) Wp + 2 + kx.  A = dy^T, MN-major: the threads copy dy's 16-byte pixel chunks
+// unchanged into four channel planes of kq pixel rows (no transpose); rows 32..127 of the
+// 128-row MMA read whatever follows in shared memory (inside the allocation: the dy
+// buffers come first) and land in accumulator rows that are never read.  B stacks the
+// three horizontal taps: shared memory holds
 // twelve slots (kx, channel plane), slot (kx, p) = rows origin(0, kx) + [0, slot_rows)
 // of plane p, SLOT apart, so one MN-major operand of N = 96 (kx, ci) starting ky Wp
 // rows into every slot covers taps (ky, 0..2); its accumulator columns ky 96 + kx 32 +
@@ -337,9 +339,10 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const uint32_t slot = (uint32_t)a.slot_rows * 16;
     const uint32_t xbytes = 12 * slot;
-    const uint32_t dybytes = (uint32_t)(a.kq / 8) * 512 + 2048;   // + slack read by the aliased rows
-    uint8_t* xs[2] = {smem, smem + xbytes};
-    uint8_t* ds[2] = {smem + 2 * xbytes, smem + 2 * xbytes + dybytes};
+    const uint32_t dplane = (uint32_t)a.kq * 16;                 // one 8-channel plane of dy
+    const uint32_t dybytes = 4 * dplane;
+    uint8_t* ds[2] = {smem, smem + dybytes};
+    uint8_t* xs[2] = {smem + 2 * dybytes, smem + 2 * dybytes + xbytes};
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + wgrad_operand_bytes(xbytes, dybytes));
     float* red = reinterpret_cast<float*>(bars + 8);             // [128][8] bias partials
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(red + 128 * 8);
@@ -355,11 +358,6 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
         mbar_init(done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // slack after each dy^T buffer is read by aliased rows only; keep it finite
-    for (int i = threadIdx.x; i < 2048 / 4; i += blockDim.x) {
-        reinterpret_cast<float*>(ds[0] + dybytes - 2048)[i] = 0.f;
-        reinterpret_cast<float*>(ds[1] + dybytes - 2048)[i] = 0.f;
-    }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -369,7 +367,7 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
     float bsum[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     const int cc = threadIdx.x % 4;         // the 8-channel chunk this thread stages
     bool ok = true;
-    constexpr uint32_t idesc = idesc_bf16(128, 3 * kCh, false, true);
+    constexpr uint32_t idesc = idesc_bf16(128, 3 * kCh, true, true);
 
     // Every thread runs every iteration (the barriers inside must match); a wait that
     // gives up only records the error and stops further MMA issue.
@@ -386,8 +384,9 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
                         tma_load_3d(smem_u32(xs[b]) + (kx * 4 + c) * slot + bb * a.box_rows * 16, &a.tin, 0, c,
                                     row0 + kx + bb * a.box_rows, tma_bar[b]);
         }
-        // stage dy^T: element (co, q) at (q / 8) * 512 + co * 16 + (q % 8) * 2; a thread's
-        // loads for eight pixels are issued before any of them is stored
+        // stage dy: the 16-byte chunk of channels 8 cc .. 8 cc + 7 of pixel q at cc PLANE + 16 q
+        // (zero outside the valid outputs); a thread's loads for eight pixels are issued
+        // before any of them is stored
         uint8_t* d = ds[b];
         for (int j0 = threadIdx.x; j0 < a.kq * 4; j0 += 8 * blockDim.x) {
             uint4 v4[8];
@@ -407,12 +406,9 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
                 if (j >= a.kq * 4) break;
                 const int q = j >> 2;
                 const __nv_bfloat16* hv = reinterpret_cast<const __nv_bfloat16*>(&v4[u]);
-                uint8_t* col = d + (q >> 3) * 512 + (q & 7) * 2;
+                *reinterpret_cast<uint4*>(d + cc * dplane + q * 16) = v4[u];
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    *reinterpret_cast<__nv_bfloat16*>(col + (cc * 8 + k) * 16) = hv[k];
-                    bsum[k] += __bfloat162float(hv[k]);
-                }
+                for (int k = 0; k < 8; ++k) bsum[k] += __bfloat162float(hv[k]);
             }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -424,12 +420,12 @@ __global__ void __launch_bounds__(128) wgrad32_tc_kernel(const __grid_constant__
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 // descriptors built once; each MMA adds its start offset in 16-byte units
                 // (shared-memory addresses stay below 2^18: the 14-bit field never carries)
-                const uint64_t a0 = plain_desc(smem_u32(ds[b]), 512, 128);
+                const uint64_t a0 = plain_desc(smem_u32(ds[b]), 128, dplane);
                 const uint64_t b0 = plain_desc(smem_u32(xs[b]), 128, slot);
                 for (int k = 0; k < a.kq / 16; ++k)
 #pragma unroll
                     for (int ky = 0; ky < 3; ++ky)
-                        mma_bf16(tmem + ky * 3 * kCh, a0 + (uint64_t)(k * 64), b0 + (uint64_t)(k * 16 + ky * a.Wp),
+                        mma_bf16(tmem + ky * 3 * kCh, a0 + (uint64_t)(k * 16), b0 + (uint64_t)(k * 16 + ky * a.Wp),
                                  idesc, (i > i0 || k > 0) ? 1u : 0u);
             }
             mma_commit(mma_bar[b]);
@@ -662,8 +658,7 @@ size_t conv_smem(int load_rows) { return 1024 + 2 * 4 * (size_t)load_rows * 16 +
 constexpr int kConvCtasPerSm = 2;   // resident CTAs per SM of the persistent convolution
 int g_num_sms = 152;                 // set by conv_tc_prepare
 size_t wgrad_smem(int slot_rows, int kq) {
-    return 1024 + wgrad_operand_bytes(12 * (uint32_t)slot_rows * 16, (uint32_t)(kq / 8) * 512 + 2048) + 64 +
-           128 * 8 * 4 + 16;
+    return 1024 + wgrad_operand_bytes(12 * (uint32_t)slot_rows * 16, 4 * (uint32_t)kq * 16) + 64 + 128 * 8 * 4 + 16;
 }
 
 }  // namespace
