@@ -384,9 +384,13 @@ __global__ void __launch_bounds__(NT) conv_wgrad_kernel(ConvShape sh, const T* _
 // owns output rows 2 (t / 8), 2 (t / 8) + 1 and columns 4 (t % 8) .. + 3.  Per tile of 64
 // pixels every thread issues all of its gathers (16 of dy, 16 of x) before storing them,
 // transposed into padded shared memory (pixel fastest), then accumulates over the tile's
-// pixels in order.  Partial sums per split in `work`, as for conv_wgrad_kernel.
+// pixels in order.  Partial sums per split in `work`, as for conv_wgrad_kernel.  PHWC: dy
+// is read as the padded-HWC BF16 gradient (grid (OH + 4) x (OW + 4), 32 channels), one
+// 16-byte chunk of 8 channels per load, instead of FP32 planes (the same values: BF16
+// widens exactly).
 constexpr int kW0Tile = 64;
-__global__ void __launch_bounds__(128) conv_wgrad_c32_kernel(ConvShape sh, const float* __restrict__ dy,
+template <bool PHWC>
+__global__ void __launch_bounds__(128) conv_wgrad_c32_kernel(ConvShape sh, const void* __restrict__ dy_v,
                                                              const float* __restrict__ x, float* __restrict__ work,
                                                              int chunk) {
     SQ_KERNEL_ENTRY();
@@ -400,17 +404,38 @@ __global__ void __launch_bounds__(128) conv_wgrad_c32_kernel(ConvShape sh, const
     const int p_begin = blockIdx.x * chunk, p_end = min(P, p_begin + chunk);
     const int cg = t / 8, jg = t % 8;
     float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    const float* dy = static_cast<const float*>(dy_v);
+    const __nv_bfloat16* dyp = static_cast<const __nv_bfloat16*>(dy_v);
+    const int wpo = sh.OW + 4;
+    const int64_t pimg = (int64_t)(sh.OH + 4) * wpo * 32;
     for (int k0 = p_begin; k0 < p_end; k0 += kW0Tile) {
         float vd[16], vx[16];
+        uint4 vq[2];
+        if (PHWC) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
-            const int e = t + u * 128;
-            const int pl = e % kW0Tile, co = e / kW0Tile;
-            const int p = k0 + pl;
-            vd[u] = 0.f;
-            if (p < p_end) {
-                const int img = p / oplane, rem = p - img * oplane;
-                vd[u] = dy[(int64_t)img * sh.y_img_stride + (int64_t)co * oplane + rem];
+            for (int u = 0; u < 2; ++u) {
+                const int e = t + u * 128;
+                const int pl = e % kW0Tile, cc = e / kW0Tile;
+                const int p = k0 + pl;
+                vq[u] = make_uint4(0u, 0u, 0u, 0u);
+                if (p < p_end) {
+                    const int img = p / oplane, rem = p - img * oplane;
+                    const int oy = rem / sh.OW, ox = rem - oy * sh.OW;
+                    vq[u] = *reinterpret_cast<const uint4*>(dyp + (int64_t)img * pimg +
+                                                            ((int64_t)(oy + 2) * wpo + ox + 2) * 32 + cc * 8);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int e = t + u * 128;
+                const int pl = e % kW0Tile, co = e / kW0Tile;
+                const int p = k0 + pl;
+                vd[u] = 0.f;
+                if (p < p_end) {
+                    const int img = p / oplane, rem = p - img * oplane;
+                    vd[u] = dy[(int64_t)img * sh.y_img_stride + (int64_t)co * oplane + rem];
+                }
             }
         }
 #pragma unroll
@@ -433,10 +458,22 @@ __global__ void __launch_bounds__(128) conv_wgrad_c32_kernel(ConvShape sh, const
             vx[u] = v;
         }
         __syncthreads();   // the previous tile has been consumed
+        if (PHWC) {
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int e = t + u * 128;
+                const uint32_t w4[4] = {vq[u].x, vq[u].y, vq[u].z, vq[u].w};
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {   // a BF16 value is the upper half of its FP32 value
+                    const uint32_t wv = w4[k / 2];
+                    dys[(e / kW0Tile) * 8 + k][e % kW0Tile] = __uint_as_float((k & 1) ? (wv & 0xFFFF0000u) : (wv << 16));
+                }
+            }
+        }
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
             const int e = t + u * 128;
-            dys[e / kW0Tile][e % kW0Tile] = vd[u];
+            if (!PHWC) dys[e / kW0Tile][e % kW0Tile] = vd[u];
             xs[e / kW0Tile][e % kW0Tile] = vx[u];
         }
         __syncthreads();
@@ -530,7 +567,7 @@ void launch_conv_wgrad(const ConvShape& sh, const T* dy, const T* x, T* dw, T* d
     const int chunk = (P + splits - 1) / splits;
     const int N = sh.Cin * 9 + 1;
     if (std::is_same<T, float>::value && sh.Cout == 32 && N <= 32)
-        launch_k(conv_wgrad_c32_kernel, dim3(splits), dim3(128), 0, s, sh, (const float*)dy, (const float*)x,
+        launch_k(conv_wgrad_c32_kernel<false>, dim3(splits), dim3(128), 0, s, sh, (const void*)dy, (const float*)x,
                  (float*)work, chunk);
     else
         launch_k(conv_wgrad_kernel<T>, dim3((N + WBN - 1) / WBN, (sh.Cout + WBM - 1) / WBM, splits), dim3(NT), 0, s,
@@ -538,6 +575,19 @@ void launch_conv_wgrad(const ConvShape& sh, const T* dy, const T* x, T* dw, T* d
     const int tot = sh.Cout * N;
     launch_k(wgrad_reduce_kernel<T>, dim3((tot + 31) / 32), dim3(32 * kRedGroups), 0, s, work, splits, sh.Cout, N, dw,
              db);
+}
+
+int launch_conv_wgrad_phwc(const ConvShape& sh, const __nv_bfloat16* dy_phwc, const float* x, float* dw, float* db,
+                           float* work, cudaStream_t s) {
+    const int P = sh.nimg * sh.OH * sh.OW;
+    const int N = sh.Cin * 9 + 1;
+    if (sh.Cout != 32 || N > 32) return -1;
+    const int splits = wgrad_splits(sh);
+    const int chunk = (P + splits - 1) / splits;
+    launch_k(conv_wgrad_c32_kernel<true>, dim3(splits), dim3(128), 0, s, sh, (const void*)dy_phwc, x, work, chunk);
+    launch_k(wgrad_reduce_kernel<float>, dim3((sh.Cout * N + 31) / 32), dim3(32 * kRedGroups), 0, s, work, splits,
+             sh.Cout, N, dw, db);
+    return 0;
 }
 
 template void launch_conv_fwd<float>(const ConvShape&, const float*, const float*, const float*, float*, bool, cudaStream_t);

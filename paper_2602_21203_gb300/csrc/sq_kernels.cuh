@@ -101,6 +101,11 @@ void launch_conv_dgrad(const ConvShape& sh, const T* dy, const T* w, T* dx, cons
 int64_t conv_wgrad_workspace(const ConvShape& sh);
 template <typename T>
 void launch_conv_wgrad(const ConvShape& sh, const T* dy, const T* x, T* dw, T* db, T* work, cudaStream_t s);
+// The same for a 32-output layer with Cin * 9 + 1 <= 32 whose output gradient is the
+// padded-HWC BF16 image (grid (OH + 4) x (OW + 4), 32 channels) of the tensor-core path;
+// returns -1 for other shapes.
+int launch_conv_wgrad_phwc(const ConvShape& sh, const __nv_bfloat16* dy_phwc, const float* x, float* dw, float* db,
+                           float* work, cudaStream_t s);
 
 // ---------------------------------------------------------------- LayerNorm
 struct LnProblem {

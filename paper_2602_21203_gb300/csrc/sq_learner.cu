@@ -1058,8 +1058,13 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
                     }
                     cur_p = dact_p[l - 1];
                 }
-                ProfScope ps(this, s1, "layout_phwc", 6.0 * n * c0.cout * c0.oh * c0.ow, 1);
-                launch_from_phwc(dact_p[0], n, c0.oh, c0.ow, dconv_a + (int64_t)i0 * c0.cout * c0.oh * c0.ow, s1);
+                // with recompute, each chunk's first-layer gradient is kept in FP32 planes (the
+                // padded-HWC buffer holds one chunk); otherwise the first layer's weight
+                // gradient reads the padded-HWC gradient directly
+                if (rc_chunk) {
+                    ProfScope ps(this, s1, "layout_phwc", 6.0 * n * c0.cout * c0.oh * c0.ow, 1);
+                    launch_from_phwc(dact_p[0], n, c0.oh, c0.ow, dconv_a + (int64_t)i0 * c0.cout * c0.oh * c0.ow, s1);
+                }
             }
             if (rc_chunk)
                 for (int l = nconv - 1; l >= 1; --l) {
@@ -1072,7 +1077,10 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
                          (int64_t)c0.cout * c0.oh * c0.ow};
             {
                 ProfScope ps(this, s1, "conv_f32_wgrad", conv_flops(c0, B), 0);
-                launch_conv_wgrad<float>(sh, dconv_a, x2, G + c0.wo, G + c0.bo, wgrad_work, s1);
+                if (rc_chunk)
+                    launch_conv_wgrad<float>(sh, dconv_a, x2, G + c0.wo, G + c0.bo, wgrad_work, s1);
+                else if (launch_conv_wgrad_phwc(sh, dact_p[0], x2, G + c0.wo, G + c0.bo, wgrad_work, s1) != 0)
+                    launch_failed = true;
             }
             fork(sw, s1);   // the inner layers' weight gradients before the encoder's Adam
         }
