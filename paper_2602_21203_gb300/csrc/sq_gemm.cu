@@ -408,55 +408,48 @@ __global__ void __launch_bounds__(128) conv_wgrad_c32_kernel(ConvShape sh, const
     const __nv_bfloat16* dyp = static_cast<const __nv_bfloat16*>(dy_v);
     const int wpo = sh.OW + 4;
     const int64_t pimg = (int64_t)(sh.OH + 4) * wpo * 32;
-    for (int k0 = p_begin; k0 < p_end; k0 += kW0Tile) {
-        float vd[16], vx[16];
-        uint4 vq[2];
+    // every gather of this thread is for pixel pl = t % 64 of the tile; its x gathers are for
+    // columns jb + 2u, whose input offsets do not depend on the tile
+    const int pl_t = t % kW0Tile, jb = t / kW0Tile;
+    int xoff[16];
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+        const int j = jb + 2 * u;
+        const int ci = j / 9, r = j - ci * 9, ky = r / 3, kx = r - ky * 3;
+        xoff[u] = j < N - 1 ? (int)(ci * iplane) + ky * sh.W + kx : 0;
+    }
+    float vd[16], vx[16];
+    uint4 vq[2];
+    // the next tile's loads are issued before the current tile is computed
+    auto gather = [&](int k0) {
+        const int p = k0 + pl_t;
+        const bool in = p < p_end;
+        const int img = in ? p / oplane : 0, rem = in ? p - img * oplane : 0;
+        const int oy = rem / sh.OW, ox = rem - oy * sh.OW;
         if (PHWC) {
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
-                const int e = t + u * 128;
-                const int pl = e % kW0Tile, cc = e / kW0Tile;
-                const int p = k0 + pl;
-                vq[u] = make_uint4(0u, 0u, 0u, 0u);
-                if (p < p_end) {
-                    const int img = p / oplane, rem = p - img * oplane;
-                    const int oy = rem / sh.OW, ox = rem - oy * sh.OW;
-                    vq[u] = *reinterpret_cast<const uint4*>(dyp + (int64_t)img * pimg +
-                                                            ((int64_t)(oy + 2) * wpo + ox + 2) * 32 + cc * 8);
-                }
+                const int cc = jb + 2 * u;   // (t + 128 u) / 64
+                vq[u] = in ? *reinterpret_cast<const uint4*>(dyp + (int64_t)img * pimg +
+                                                              ((int64_t)(oy + 2) * wpo + ox + 2) * 32 + cc * 8)
+                           : make_uint4(0u, 0u, 0u, 0u);
             }
         } else {
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
-                const int e = t + u * 128;
-                const int pl = e % kW0Tile, co = e / kW0Tile;
-                const int p = k0 + pl;
-                vd[u] = 0.f;
-                if (p < p_end) {
-                    const int img = p / oplane, rem = p - img * oplane;
-                    vd[u] = dy[(int64_t)img * sh.y_img_stride + (int64_t)co * oplane + rem];
-                }
+                const int co = jb + 2 * u;
+                vd[u] = in ? dy[(int64_t)img * sh.y_img_stride + (int64_t)co * oplane + rem] : 0.f;
             }
         }
+        const float* xb = x + (int64_t)img * sh.x_img_stride + (int64_t)(oy * sh.stride) * sh.W + ox * sh.stride;
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
-            const int e = t + u * 128;
-            const int pl = e % kW0Tile, j = e / kW0Tile;
-            const int p = k0 + pl;
-            float v = 0.f;
-            if (p < p_end && j < N) {
-                if (j == N - 1) {
-                    v = 1.f;
-                } else {
-                    const int img = p / oplane, rem = p - img * oplane;
-                    const int oy = rem / sh.OW, ox = rem - oy * sh.OW;
-                    const int ci = j / 9, r = j - ci * 9, ky = r / 3, kx = r - ky * 3;
-                    v = x[(int64_t)img * sh.x_img_stride + ci * iplane + (int64_t)(oy * sh.stride + ky) * sh.W +
-                          ox * sh.stride + kx];
-                }
-            }
-            vx[u] = v;
+            const int j = jb + 2 * u;
+            vx[u] = (in && j < N - 1) ? xb[xoff[u]] : ((in && j == N - 1) ? 1.f : 0.f);
         }
+    };
+    if (p_begin < p_end) gather(p_begin);
+    for (int k0 = p_begin; k0 < p_end; k0 += kW0Tile) {
         __syncthreads();   // the previous tile has been consumed
         if (PHWC) {
 #pragma unroll
@@ -477,6 +470,7 @@ __global__ void __launch_bounds__(128) conv_wgrad_c32_kernel(ConvShape sh, const
             xs[e / kW0Tile][e % kW0Tile] = vx[u];
         }
         __syncthreads();
+        if (k0 + kW0Tile < p_end) gather(k0 + kW0Tile);
         const int np = min(kW0Tile, p_end - k0);
 #pragma unroll 4
         for (int pl = 0; pl < np; ++pl) {
