@@ -265,10 +265,11 @@ namespace {
 // Backward through an MLP evaluated by E online parameter sets.  dout [E, rows, n_out]
 // (FP32 + BF16 shadow); activations stored with R rows per set, read from row r0.
 // Parameter gradients land at the canonical offsets of `grads` (null: input gradient
-// only).  dX (optional) = sum over sets of the input gradient, columns [0, ncols).
+// only).  dX (optional) = sum over sets of the input gradient, input columns
+// [col0, col0 + ncols) into dX[:, 0 .. ncols).
 void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* sets, float* grads, int E, const Mat& X,
                   int rows, const Mat& dout, int ncols, float* dX, int64_t lddx, const float* mask, int64_t ldmask,
-                  cudaStream_t s, cudaStream_t side) {
+                  cudaStream_t s, cudaStream_t side, int col0 = 0) {
     // weight and bias gradients go to `side` as soon as their inputs exist; the main
     // stream carries only the chain of input gradients; `side` is joined at the end
     const bool bf = h->bf16;
@@ -360,7 +361,7 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
         GemmBuilder gb(h, s, bf);
         Mat d[2] = {dpre(0, 0), E > 1 ? dpre(0, 1) : dpre(0, 0)};
         LayerRef w[2] = {sets[0][0], E > 1 ? sets[1][0] : sets[0][0]};
-        gb.dx(d, w, E, rows, 0, ncols, dX, lddx, mask, ldmask);
+        gb.dx(d, w, E, rows, col0, ncols, dX, lddx, mask, ldmask);
     }
     if (grads) h->fork(side, s);
 }
@@ -1179,8 +1180,11 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
             ProfScope ps(this, s3, "heads_losses", 0, 1);
             launch_stats(st, s3);
         }
+        // only the action columns of the critics' input gradient are used (the head
+        // backward): from column Z + P rounded down to 8 (16-byte aligned BF16 operand)
+        const int a0 = (Z + P) / 8 * 8;
         mlp_backward(this, qcrit_mlp, 0, crit_on, nullptr, E, Mat{xq, Dc, xq_h, Dc8}, B, Mat{dlogits_q, K, dlogits_qh, K8},
-                     Dc, dxq, Dc, nullptr, 0, s, s2);
+                     Dc - a0, dxq + a0, Dc, nullptr, 0, s, s2, a0);
         fork(s3, s);   // the new alpha (and the statistics) before the head backward
         ActorHeadBwdArgs hb{};
         hb.B = B; hb.A = A;
