@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
     if (bulk) {
         if (threadIdx.x == 0) {
             bulk_load_init(&bar);
-            bulk_load(frame, src, (uint32_t)fbytes, &bar);
+            bulk_load_stream(frame, src, (uint32_t)fbytes, &bar);
         }
         // one thread waits (the others at the block barrier issue nothing meanwhile)
         if (threadIdx.x == 0 && !bulk_load_wait(&bar, 0) && a.err) atomicCAS(a.err, 0, 31);
