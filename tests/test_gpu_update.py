@@ -264,6 +264,46 @@ def test_bf16_graph_equals_eager_bitwise(L):
     b.close()
 
 
+@pytest.mark.parametrize("name,prec", [("small_b32", "BF16"), ("train_b512", "BF16"), ("train_b512", "MXFP8"),
+                                       ("state_small_b64", "BF16")])
+def test_optimiser_written_low_precision_weights_equal_a_fresh_cast(L, name, prec):
+    """Adam and polyak write the BF16 weight copies the next update reads.  A learner that
+    resumes from the same state casts its copies from the FP32 masters instead; the next
+    updates of the two must agree bit for bit."""
+    over = {"ring_size": 4096} if name == "train_b512" else {}
+    cfg = synth.make_config(name, **over)
+    ring = synth.make_ring(cfg, 0, device="cuda") if name == "train_b512" else ring_to_device(synth.make_ring(cfg, 0))
+    p = getattr(L, "PREC_" + prec)
+    a = L.Learner(cfg, ring, precision=p)
+    a.update(3, graph=True)
+    b = L.Learner(cfg, ring, precision=p)
+    b.set_state(a.state())
+    sa = a.update(2, graph=True)
+    sb = b.update(2, graph=True)
+    assert sa == sb
+    assert np.array_equal(a.params(), b.params())
+    assert np.array_equal(a.debug("target"), b.debug("target"))
+    a.close()
+    b.close()
+
+
+def test_bf16_k_updates_track_oracle(L):
+    """Four BF16 updates in one graph against four oracle updates: every update's losses
+    within the per-update BF16 bounds (the later ones read the weights Adam wrote)."""
+    cfg = synth.make_config("small_b32")
+    ring_cpu = synth.make_ring(cfg, 0)
+    ring = ring_to_device(ring_cpu)
+    ring_np = synth.ring_numpy(ring_cpu)
+    learner = L.Learner(cfg, ring, precision=L.PREC_BF16)
+    state = o.init_state(cfg)
+    stats = learner.update(4, graph=True)
+    for j in range(4):
+        ref, _ = o.update(state, ring_np, cfg)
+        for key in ("q_mean", "critic_loss", "actor_loss"):
+            assert _bf16_close(key, stats[j][key], ref[key]), (j, key, stats[j][key], ref[key])
+    learner.close()
+
+
 # ---------------------------------------------------------------- FP8 forward layers
 def test_fp8_update_runs_and_replays_bitwise(L):
     """FP8 mode (e4m3 forward linear layers, per-tensor scales): graph == eager bit for
