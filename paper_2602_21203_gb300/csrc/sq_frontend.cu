@@ -17,7 +17,7 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
     extern __shared__ __align__(16) uint8_t frame[];
     const int b = blockIdx.x;
     const int which = blockIdx.y;                 // 0: o_t, 1: o_{t+1}
-    const uint64_t u = (uint64_t)*a.update_idx;
+    const uint64_t u = (uint64_t)*a.update_idx + (uint64_t)a.idx_offset;
 
     uint32_t w[4];
     draw_block(w, a.seed, (uint32_t)b, kStreamIndex, 0, u);
@@ -128,13 +128,6 @@ __global__ void __launch_bounds__(256) frontend_kernel(FrontendArgs a) {
         if (which == 0) {
             a.r_out[b] = a.reward[idx];
             a.d_out[b] = (float)a.done[idx];
-        }
-        if (b == 0 && which == 0) {
-            const int act = ((u + 1) % (uint64_t)a.policy_freq) == 0;
-            a.steps[0] += 1;
-            a.steps[2] += 1;
-            a.steps[1] += act;
-            *a.do_actor = act;
         }
     }
     for (int t = 0; t < a.n_dst; ++t) {

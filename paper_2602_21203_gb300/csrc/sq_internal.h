@@ -84,6 +84,9 @@ struct squint_handle {
     // default: inside the concurrent update graph it gave 1,307 updates/s against 1,321
     // without (clusters wait for co-scheduled SMs while the side streams hold some)
     bool gemm_split = false;
+    // in a call of k updates, each update's minibatch drawn (front end) while the previous
+    // update runs; SQUINT_DRAW_AHEAD=0 at creation draws every one in line instead
+    bool draw_ahead = true;
     bool launch_failed = false;       // a tensor map could not describe an operand
     int device = 0;
     int* d_err = nullptr;             // device error word of bounded waits
@@ -127,6 +130,22 @@ struct squint_handle {
     float* xcbar = nullptr;           // [B, Dc]
     float* xc = nullptr;              // [B, Dc]
     float* xq = nullptr;              // [B, Dc]
+    // The front end's outputs of one update (squinted images, r, d and the head inputs
+    // it writes the transition fields into).  Update j of a call uses set j % 2, so the
+    // front end of update j + 1 can run while update j still reads its own set; use_set
+    // points the members above and below at a set.
+    struct FeSet {
+        float* x2 = nullptr; float* r = nullptr; float* d = nullptr;
+        float* xa = nullptr; float* xcbar = nullptr; float* xc = nullptr; float* xq = nullptr;
+        __nv_bfloat16* xa_h = nullptr; __nv_bfloat16* xcbar_h = nullptr;
+        __nv_bfloat16* xc_h = nullptr; __nv_bfloat16* xq_h = nullptr;
+    };
+    FeSet fe_set[2];
+    void use_set(int i) {
+        const FeSet& f = fe_set[i];
+        x2 = f.x2; r = f.r; d = f.d; xa = f.xa; xcbar = f.xcbar; xc = f.xc; xq = f.xq;
+        xa_h = f.xa_h; xcbar_h = f.xcbar_h; xc_h = f.xc_h; xq_h = f.xq_h;
+    }
     sq::MlpBufs actor_mlp, tcrit_mlp, crit_mlp, qcrit_mlp;
     float* logp = nullptr;            // [2B]
     float* eps = nullptr;             // [2B, A]
@@ -211,7 +230,8 @@ struct squint_handle {
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, int64_t> graph_kernels;
     // concurrent branches of one update: library-owned streams joined back before it ends
-    cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+    // (side[4]: the next update's front end, drawn while this update runs)
+    cudaStream_t side[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     cudaEvent_t fork_ev[32] = {};
     int fork_next = 0;
     bool serial = false;                  // profiling: every launch in order on the main stream
@@ -256,7 +276,9 @@ struct squint_handle {
     void release();
     int after_param_change();
     int run_updates(int k, squint_update_stats* stats, cudaStream_t s, bool use_graph);
-    void record_update(int j, cudaStream_t s, bool debug);
+    // update j of k recorded on s (its front end drawn by update j - 1 when j > 0; it
+    // draws update j + 1's when j + 1 < k)
+    void record_update(int j, int k, cudaStream_t s, bool debug);
     void cast_conv_weights(cudaStream_t s);
     size_t state_bytes() const;
     int save_state(uint8_t* out);

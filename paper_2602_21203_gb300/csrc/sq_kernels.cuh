@@ -25,6 +25,7 @@ struct FrontendArgs {
     int C, H, W, f, pad, P, A, B;
     uint64_t seed;
     const int64_t* update_idx;   // device scalar
+    int idx_offset;              // draws of update *update_idx + idx_offset (1: the next one)
     float* x;                    // [2B, C, Hs, Ws]: rows < B are o_t, rows >= B are o_{t+1}
     __nv_bfloat16* x_bf;         // optional BF16 copy of x
     uint16_t* sums;              // optional box sums, same layout
@@ -34,9 +35,6 @@ struct FrontendArgs {
     float* d_out;                // [B]
     CopyDst dst[8];
     int n_dst;
-    int32_t* steps;              // device [3]: critic, actor, alpha step counts (incremented here)
-    int32_t* do_actor;           // device flag: actor steps this update
-    int policy_freq;
     int* err;                    // device error word: a frame copy that never completed
 };
 void launch_frontend(const FrontendArgs& a, cudaStream_t s);
@@ -189,6 +187,10 @@ struct C51TargetArgs {
     float* m;                  // [B, K]; MSE critic (K = 1): the TD target y
     int cdq;                   // clipped double Q: per sample the target critic with the smaller mean
     int mse;                   // scalar critics (Eq. 1): y = r + gamma (1-d)(Q_bar - alpha log pi')
+    // the update's step counters (null: left alone), advanced by one thread before any
+    // reader of the update runs: steps [3] critic, actor, alpha; do_actor = whether the
+    // actor steps in update *update_idx (every policy_freq-th)
+    int32_t* steps; int32_t* do_actor; const int64_t* update_idx; int policy_freq;
 };
 void launch_c51_target(const C51TargetArgs& a, cudaStream_t s);
 

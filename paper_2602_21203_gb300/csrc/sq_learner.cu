@@ -390,6 +390,7 @@ int squint_handle::allocate() {
     mx = c.precision == SQUINT_PREC_MXFP8;
     if (const char* e = std::getenv("SQUINT_FUSED_LN")) fuse_ln = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_GEMM_SPLIT")) gemm_split = std::atoi(e) != 0;
+    if (const char* e = std::getenv("SQUINT_DRAW_AHEAD")) draw_ahead = std::atoi(e) != 0;
     bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
     SQ_CK(this, cudaGetDevice(&device));
     const int64_t n = L.total;
@@ -531,6 +532,26 @@ int squint_handle::allocate() {
         if (L.D > 0) dproj_h = dalloc<__nv_bfloat16>((int64_t)B * L.D);
         dout_ah = dalloc<__nv_bfloat16>((int64_t)B * pad8(2 * A));
     }
+    // the front end's outputs twice over: update j of a call reads set j % 2 while the
+    // front end of update j + 1 writes the other
+    fe_set[0] = FeSet{x2, r, d, xa, xcbar, xc, xq, xa_h, xcbar_h, xc_h, xq_h};
+    fe_set[1] = fe_set[0];
+    if (c.max_k > 1) {
+        FeSet& f = fe_set[1];
+        f.x2 = dalloc<float>(2 * B * img);
+        f.r = dalloc<float>(B);
+        f.d = dalloc<float>(B);
+        f.xa = dalloc<float>((int64_t)2 * B * L.da);
+        f.xcbar = dalloc<float>((int64_t)B * L.dc);
+        f.xc = dalloc<float>((int64_t)B * L.dc);
+        f.xq = dalloc<float>((int64_t)B * L.dc);
+        if (bf16) {
+            f.xa_h = dalloc<__nv_bfloat16>((int64_t)2 * B * pad8(L.da));
+            f.xcbar_h = dalloc<__nv_bfloat16>((int64_t)B * pad8(L.dc));
+            f.xc_h = dalloc<__nv_bfloat16>((int64_t)B * pad8(L.dc));
+            f.xq_h = dalloc<__nv_bfloat16>((int64_t)B * pad8(L.dc));
+        }
+    }
     // padded-HWC BF16 activations (forward: enc_imgs images; backward: one chunk of o_t)
     const int bwd_imgs = rc_chunk ? rc_chunk : B;
     if (tc_conv) {
@@ -554,6 +575,13 @@ int squint_handle::allocate() {
     }
     for (void* p : allocations)
         if (!p) { g_last_error = "device allocation failed"; return SQUINT_ENOMEM; }
+    if (bf16)   // the BF16 head inputs' pad columns stay zero
+        for (const FeSet& f : fe_set) {
+            SQ_CK(this, cudaMemset(f.xa_h, 0, (size_t)2 * B * pad8(L.da) * 2));
+            SQ_CK(this, cudaMemset(f.xcbar_h, 0, (size_t)B * pad8(L.dc) * 2));
+            SQ_CK(this, cudaMemset(f.xc_h, 0, (size_t)B * pad8(L.dc) * 2));
+            SQ_CK(this, cudaMemset(f.xq_h, 0, (size_t)B * pad8(L.dc) * 2));
+        }
     if (tc_conv) {
         // padded buffers keep zero borders: only interiors are ever written
         for (size_t l = 0; l < act_p.size(); ++l) {
@@ -723,7 +751,7 @@ int squint_handle::after_param_change() {
     return SQUINT_OK;
 }
 
-void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
+void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
     const int B = c.batch, A = c.action_dim, P = c.proprio_dim, K = c.critic_kind == 1 ? 1 : c.atoms, E = 2;
     const int F = L.feat, Z = L.zdim, Dd = L.D, Dc = L.dc, Da = L.da;
     const int64_t Dc8 = pad8(Dc), Da8 = pad8(Da), K8 = pad8(K);
@@ -734,6 +762,10 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     // branches: s1 encoder backward, s2 weight gradients of the MLPs, s3 critic forward / polyak,
     // s4 the encoder's inner weight gradients beside its data-gradient chain
     cudaStream_t s1 = branch(s, 0), s2 = branch(s, 1), s3 = branch(s, 2), s4 = branch(s, 3);
+    // the next update's front end, drawn beside this update into the other buffer set
+    cudaStream_t sp = branch(s, 4);
+    const bool draw_next = draw_ahead && j + 1 < k;
+    use_set(j & 1);
     auto cast_rows = [&](const float* src, int64_t ld, int rows, int cols, __nv_bfloat16* dst, int64_t ldh,
                          cudaStream_t st) {
         if (!bf16) return;
@@ -773,33 +805,36 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     auto conv_flops = [&](const ConvL& cv, int nimg) { return 2.0 * nimg * cv.oh * cv.ow * cv.cout * cv.cin * 9; };
 
     mark(s);
-    // ---- a1-a4: minibatch, gathers, shift, squint
-    FrontendArgs fa{};
-    fa.obs = ring.obs; fa.proprio = ring.proprio; fa.action = ring.action; fa.reward = ring.reward; fa.done = ring.done;
-    fa.n_slots = ring.n;
-    fa.C = c.obs_c; fa.H = c.obs_h; fa.W = c.obs_w; fa.f = c.squint_f; fa.pad = c.shift_pad;
-    if (L.conv.empty()) { fa.C = 0; fa.H = fa.W = fa.f = 1; fa.pad = 0; }   // state-based: no image
-    fa.P = P; fa.A = A; fa.B = B;
-    fa.seed = c.seed; fa.update_idx = d_update_idx;
-    fa.x = x2; fa.x_bf = nullptr; fa.sums = debug ? sums : nullptr;
-    fa.idx_out = idx2; fa.shift_out = shift2; fa.r_out = r; fa.d_out = d;
-    // the transition fields land in the head inputs, with their BF16 shadows in BF16 mode
-    fa.dst[0] = CopyDst{xc, Dc, Z, 0, xc_h, Dc8};
-    fa.dst[1] = CopyDst{xc, Dc, Z + P, 2, xc_h, Dc8};
-    fa.dst[2] = CopyDst{xq, Dc, Z, 0, xq_h, Dc8};
-    fa.dst[3] = CopyDst{xa + (int64_t)B * Da, Da, Z, 0, xa_h ? xa_h + (int64_t)B * Da8 : nullptr, Da8};
-    fa.dst[4] = CopyDst{xa, Da, Z, 1, xa_h, Da8};
-    fa.dst[5] = CopyDst{xcbar, Dc, Z, 1, xcbar_h, Dc8};
-    fa.n_dst = 6;
-    fa.steps = d_steps; fa.do_actor = d_do_actor; fa.policy_freq = c.policy_freq; fa.err = d_err;
-    {
+    // ---- a1-a4: minibatch, gathers, shift, squint of update j + ahead into set `set`
+    // (the update index the draws use is read before this update advances it)
+    auto frontend = [&](int set, int ahead, cudaStream_t st) {
+        const FeSet& fs = fe_set[set];
+        FrontendArgs fa{};
+        fa.obs = ring.obs; fa.proprio = ring.proprio; fa.action = ring.action; fa.reward = ring.reward; fa.done = ring.done;
+        fa.n_slots = ring.n;
+        fa.C = c.obs_c; fa.H = c.obs_h; fa.W = c.obs_w; fa.f = c.squint_f; fa.pad = c.shift_pad;
+        if (L.conv.empty()) { fa.C = 0; fa.H = fa.W = fa.f = 1; fa.pad = 0; }   // state-based: no image
+        fa.P = P; fa.A = A; fa.B = B;
+        fa.seed = c.seed; fa.update_idx = d_update_idx; fa.idx_offset = ahead;
+        fa.x = fs.x2; fa.x_bf = nullptr; fa.sums = debug ? sums : nullptr;
+        fa.idx_out = idx2; fa.shift_out = shift2; fa.r_out = fs.r; fa.d_out = fs.d;
+        // the transition fields land in the head inputs, with their BF16 shadows in BF16 mode
+        fa.dst[0] = CopyDst{fs.xc, Dc, Z, 0, fs.xc_h, Dc8};
+        fa.dst[1] = CopyDst{fs.xc, Dc, Z + P, 2, fs.xc_h, Dc8};
+        fa.dst[2] = CopyDst{fs.xq, Dc, Z, 0, fs.xq_h, Dc8};
+        fa.dst[3] = CopyDst{fs.xa + (int64_t)B * Da, Da, Z, 0, fs.xa_h ? fs.xa_h + (int64_t)B * Da8 : nullptr, Da8};
+        fa.dst[4] = CopyDst{fs.xa, Da, Z, 1, fs.xa_h, Da8};
+        fa.dst[5] = CopyDst{fs.xcbar, Dc, Z, 1, fs.xcbar_h, Dc8};
+        fa.n_dst = 6;
+        fa.err = d_err;
         // frames read and squinted images written, plus the transition rows gathered
         // (s_t, s_{t+1}, a_t, r, d) and written into the head inputs (with BF16 shadows)
         const int64_t img = (int64_t)L.img_c * L.hs * L.ws;
         const double trans = B * (4.0 * (2 * P + A + 1) + 1 + (5.0 * P + A) * (bf16 ? 6.0 : 4.0) + 8.0);
-        ProfScope ps(this, s, "frontend", 2.0 * B * fa.C * fa.H * fa.W + 2.0 * B * img * 4 + trans, 1);
-        launch_frontend(fa, s);
-    }
+        ProfScope ps(this, st, "frontend", 2.0 * B * fa.C * fa.H * fa.W + 2.0 * B * img * 4 + trans, 1);
+        launch_frontend(fa, st);
+    };
+    if (j == 0 || !draw_ahead) frontend(j & 1, 0, s);   // else drawn by the previous update
 
     mark(s);
     // ---- a5: encoder on o_t (rows < B) and o_{t+1} (rows >= B)
@@ -852,6 +887,13 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
     const Mat zt{z, F, z_h, F};
     const Mat zt1 = zt.rows(B);
 
+    if (draw_next) {
+        // the next update's minibatch while this one runs its latency-bound heads; it
+        // writes the set update j - 1 used (finished: its branches joined before this
+        // update began) and is joined before this update advances the update index
+        fork(s, sp);
+        frontend((j + 1) & 1, 1, sp);
+    }
     mark(s);
     // ---- a6: per-head projections (or the flattened features straight into the heads)
     if (Dd > 0) {
@@ -935,6 +977,8 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         ct.gamma = (float)c.gamma; ct.v_min = (float)c.v_min; ct.v_max = (float)c.v_max;
         ct.m = m;
         ct.cdq = c.cdq; ct.mse = c.critic_kind == 1;
+        // the step counters advance here, before their first reader (the critic Adam)
+        ct.steps = d_steps; ct.do_actor = d_do_actor; ct.update_idx = d_update_idx; ct.policy_freq = c.policy_freq;
         ProfScope ps(this, s, "heads_losses", 0, 1);
         launch_c51_target(ct, s);
     }
@@ -1172,6 +1216,7 @@ void squint_handle::record_update(int j, cudaStream_t s, bool debug) {
         // ---- statistics on branch s3 once the actor objective is known (nothing later in
         // the update reads the update index it advances)
         fork(s, s3);
+        if (draw_next) fork(sp, s3);   // the next front end read the index this advances
         {
             StatsArgs st{};
             st.B = B; st.E = E; st.row_loss = row_loss; st.row_q = row_q; st.row_q_actor = row_q_actor;
@@ -1249,7 +1294,7 @@ int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s
             cudaEventDestroy(ev);
             cudaGraph_t graph;
             SQ_CK(this, cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
-            for (int j = 0; j < k; ++j) record_update(j, capture_stream, false);
+            for (int j = 0; j < k; ++j) record_update(j, k, capture_stream, false);
             SQ_CK(this, cudaStreamEndCapture(capture_stream, &graph));
             if (launch_failed) {
                 cudaGraphDestroy(graph);
@@ -1273,8 +1318,9 @@ int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s
             it = graphs.emplace(k, exec).first;
         }
         SQ_CK(this, cudaGraphLaunch(it->second, s));
+        use_set((k - 1) & 1);   // the debug views show the last update's buffers
     } else {
-        for (int j = 0; j < k; ++j) record_update(j, s, true);
+        for (int j = 0; j < k; ++j) record_update(j, k, s, true);
         SQ_CK(this, cudaGetLastError());
         if (launch_failed) {
             g_last_error = "a tensor-core operand could not be described by a tensor map";
@@ -1332,7 +1378,7 @@ int squint_handle::profile_update(float* ms, int cap, int* n_phases, cudaStream_
     SQ_CK(this, cudaStreamSynchronize(s));
     SQ_CK(this, cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
     phase_events = &ev;
-    record_update(0, capture_stream, false);
+    record_update(0, 1, capture_stream, false);
     phase_events = nullptr;
     SQ_CK(this, cudaStreamEndCapture(capture_stream, &graph));
     int rc = launch_failed ? SQUINT_EINVAL : SQUINT_OK;
@@ -1363,7 +1409,7 @@ int squint_handle::profile_kernels(int cap, char* names, int* launches, float* m
     SQ_CK(this, cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
     prof = &recs;
     serial = true;
-    record_update(0, capture_stream, false);
+    record_update(0, 1, capture_stream, false);
     serial = false;
     prof = nullptr;
     SQ_CK(this, cudaStreamEndCapture(capture_stream, &graph));

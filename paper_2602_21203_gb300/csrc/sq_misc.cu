@@ -294,6 +294,13 @@ __global__ void c51_target_kernel(C51TargetArgs a) {
     __shared__ float bpos[kMaxAtoms];
     __shared__ float red[32];
     const int row = blockIdx.x;
+    if (a.steps && row == 0 && threadIdx.x == 0) {
+        const int act = (((uint64_t)*a.update_idx + 1) % (uint64_t)a.policy_freq) == 0;
+        a.steps[0] += 1;
+        a.steps[2] += 1;
+        a.steps[1] += act;
+        *a.do_actor = act;
+    }
     const float alpha = a.log_alpha ? expf(*a.log_alpha) : a.alpha_value;
     const float r = a.r[row], nd = 1.0f - a.d[row], lp = a.logp_next[row];
     if (a.mse) {

@@ -65,6 +65,30 @@ def test_frontend_is_bit_exact(L, name):
     learner.close()
 
 
+@pytest.mark.parametrize("graph", [False, True])
+def test_frontend_drawn_ahead_is_bit_exact(L, graph):
+    """In a call of k updates, update j + 1's minibatch is drawn while update j runs, into
+    the other of two buffer sets: the last update's draws and images are still those of
+    its own update index, across calls of odd and even k."""
+    cfg, ring_cpu, ring, learner = _setup(L, "small_b32")
+    ring_np = synth.ring_numpy(ring_cpu)
+    u = 0
+    for k in (3, 2, 4):
+        stats = learner.update(k, graph=graph)
+        u += k
+        assert [s["update_idx"] for s in stats] == list(range(u - k, u))
+        fe = o.frontend(cfg, ring_np, u - 1)
+        assert np.array_equal(learner.debug("idx", np.int32), fe["idx"])
+        assert np.array_equal(learner.debug("nxt", np.int32), fe["nxt"])
+        assert np.array_equal(learner.debug("shift_t", np.int32).reshape(-1, 2), fe["shift_t"])
+        assert np.array_equal(learner.debug("shift_t1", np.int32).reshape(-1, 2), fe["shift_t1"])
+        if not graph:   # box sums are kept in eager (debug) updates only
+            assert np.array_equal(learner.debug("sums_t1", np.uint16).reshape(fe["sums_t1"].shape), fe["sums_t1"])
+        x = learner.debug("x_t1").reshape(fe["x_t1"].shape)
+        assert np.abs(x - fe["x_t1"]).max() < 1e-6
+    learner.close()
+
+
 def _check_update(cfg, learner, state, ring_np, graph):
     p_before = learner.params().astype(np.float64)
     stats = learner.update(1, graph=graph)[0]
