@@ -48,9 +48,12 @@ def test_initial_parameters_match_oracle_bitwise(L, name):
     learner.close()
 
 
-@pytest.mark.parametrize("name", ["small_b32", "tiny_b8"])
-def test_frontend_is_bit_exact(L, name):
-    cfg, ring_cpu, ring, learner = _setup(L, name)
+@pytest.mark.parametrize("name,over", [("small_b32", {}), ("tiny_b8", {}),
+                                       ("train_b512", dict(ring_size=300, batch=64))])
+def test_frontend_is_bit_exact(L, name, over):
+    """Slots, shifts, box sums and images of the front end equal the oracle's; the last
+    case has the training frames (3 x 128 x 128, pad 8, squint 4 to 32 x 32)."""
+    cfg, ring_cpu, ring, learner = _setup(L, name, **over)
     for u in range(2):
         learner.update(1, graph=False)
         fe = o.frontend(cfg, synth.ring_numpy(ring_cpu), u)
