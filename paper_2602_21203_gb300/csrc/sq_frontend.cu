@@ -1,10 +1,11 @@
 // Front end of the update (steps a1-a4) and of inference.
 //
-// One CTA per (sample, frame): it draws the slot and the crop offset, stages
-// the uint8 frame in shared memory with 128-bit loads, and forms the squinted
-// image from integer f x f box sums over the replicate-padded, shifted frame
-// (Sec. IV "Resolution Squinting": area downsampling; the shift is the
-// DrQ-style random-shift augmentation).
+// One CTA per (sample, frame): it draws the slot and the crop offset and forms
+// the squinted image from integer f x f box sums over the replicate-padded,
+// shifted frame (Sec. IV "Resolution Squinting": area downsampling; the shift
+// is the DrQ-style random-shift augmentation).  For f = 4 on power-of-two
+// widths up to 128 the rows are read straight from global memory with 16-byte
+// loads; other sizes stage the frame in shared memory first.
 #include <algorithm>
 #include <mutex>
 
