@@ -217,6 +217,12 @@ class LazyRows:
         return self.t.index_select(0, ii).cpu().numpy()
 
 
+def workload_config(workload, precision, world):
+    """The bench line's `config`, the same for both arms (precision: the arm's arithmetic)."""
+    return {"workload": WORKLOAD_TEXT[workload][0], "updates_per_step": UTD_K, "precision": precision,
+            "l2": WORKLOAD_TEXT[workload][1], "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle on the same workload, rank 0 only."""
     import torch
@@ -234,27 +240,28 @@ def run_reference(args):
     t0 = time.perf_counter()
     o.update(st, ring, probe)
     per_sample = (time.perf_counter() - t0) / 64
+    # a step is UTD_K updates, as in our arm
     budget = 150.0 / max(1, args.steps + args.warmup)
     bsz = 512
-    while bsz > 32 and bsz * per_sample > budget:
+    while bsz > 16 and UTD_K * bsz * per_sample > budget:
         bsz //= 2
     scfg = synth.make_config(WORKLOAD, batch=bsz)
     state = o.init_state(scfg)
-    for _ in range(args.warmup):
+    for _ in range(args.warmup * UTD_K):
         o.update(state, ring, scfg)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(args.steps * UTD_K):
         o.update(state, ring, scfg)
     dt = time.perf_counter() - t0
-    value = args.steps * (bsz / cfg["batch"]) / dt
+    value = args.steps * UTD_K * (bsz / cfg["batch"]) / dt
     cores = blas_threads()
-    sample = f"{args.steps} FP64 oracle updates on batch slices of {bsz} of the 512-sample workload, scaled to B=512"
+    sample = (f"{args.steps} steps of {UTD_K} FP64 oracle updates on batch slices of {bsz} of the 512-sample "
+              f"workload, scaled to B=512")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "train_b512: 100k x 3x128x128 uint8 ring, batch 512, UTD 4, 4 conv x 32ch, "
-                               "proj 256, critics 512-512 x2 (101 atoms), actor 512-512"},
+        "config": workload_config(WORKLOAD, "f64 (oracle)", world),
         "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -442,10 +449,7 @@ def run_ours(args):
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3+bf16", "mxfp8": "e4m3(mx)+bf16"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT[args.workload][0],
-                       "updates_per_step": UTD_K, "precision": args.precision,
-                       "l2": WORKLOAD_TEXT[args.workload][1],
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(args.workload, args.precision, world),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
         }
