@@ -139,7 +139,9 @@ int64_t squint_param_count(const squint_config* cfg);
  * the critics, Adam moments are zero.  `ring` may be NULL (inference only). */
 int squint_create(const squint_config* cfg, const squint_replay* ring, squint_handle** out);
 
-/* Replace the replay ring (pointers only; contents are read at update time). */
+/* Replace the replay ring (pointers only; contents are read at update time).  A ring
+ * with other pointers or another size drops the captured update graphs (after waiting
+ * for the device): the next squint_update of each k captures again. */
 int squint_set_replay(squint_handle* h, const squint_replay* ring);
 
 /* Release everything the handle owns; waits for its own streams.  NULL is a no-op. */

@@ -226,6 +226,17 @@ int squint_set_replay(squint_handle* h, const squint_replay* ring) {
     if (ring->n < 2 || ring->n > 0xFFFFFFFFll || (!ring->obs && !h->L.conv.empty()) || !ring->proprio ||
         !ring->action || !ring->reward || !ring->done)
         return SQUINT_EINVAL;
+    const squint_replay& o = h->ring;
+    const bool same = h->has_ring && o.obs == ring->obs && o.proprio == ring->proprio && o.action == ring->action &&
+                      o.reward == ring->reward && o.done == ring->done && o.n == ring->n;
+    if (!same && !h->graphs.empty()) {
+        // captured updates hold the old ring's addresses and size: the next update of
+        // each k captures again
+        SQ_CK(h, cudaDeviceSynchronize());
+        for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+        h->graphs.clear();
+        h->graph_kernels.clear();
+    }
     h->ring = *ring;
     h->has_ring = true;
     return SQUINT_OK;

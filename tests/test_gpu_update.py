@@ -92,6 +92,23 @@ def test_frontend_drawn_ahead_is_bit_exact(L, graph):
     learner.close()
 
 
+def test_new_ring_after_a_capture_is_read(L):
+    """set_replay with another ring after a graph was captured: the next replay of the same
+    k reads the new ring (its images equal the oracle's front end on the new contents)."""
+    cfg, ring_cpu, ring, learner = _setup(L, "small_b32")
+    learner.update(2, graph=True)
+    ring_cpu_b = synth.make_ring(cfg, 1)           # other contents, same size
+    ring_b = ring_to_device(ring_cpu_b)
+    learner.set_replay(ring_b)
+    stats = learner.update(2, graph=True)
+    assert [s["update_idx"] for s in stats] == [2, 3]
+    fe = o.frontend(cfg, synth.ring_numpy(ring_cpu_b), 3)
+    assert np.array_equal(learner.debug("idx", np.int32), fe["idx"])
+    x = learner.debug("x_t1").reshape(fe["x_t1"].shape)
+    assert np.abs(x - fe["x_t1"]).max() < 1e-6
+    learner.close()
+
+
 def _check_update(cfg, learner, state, ring_np, graph):
     p_before = learner.params().astype(np.float64)
     stats = learner.update(1, graph=graph)[0]
