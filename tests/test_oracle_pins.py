@@ -461,6 +461,45 @@ def test_actor_loss_gradients_finite_differences():
     assert set(res["grads"]) == {n for n, *_ in o.param_spec(cfg) if o.group_of(n) == "actor"}
 
 
+def _rows(d, lo, hi, B):
+    """Rows lo:hi of every per-sample array of a front-end dict."""
+    return {k: (v[lo:hi] if isinstance(v, np.ndarray) and v.ndim >= 1 and v.shape[0] == B else v)
+            for k, v in d.items()}
+
+
+@pytest.mark.parametrize("proj", [0, 16])
+def test_losses_and_gradients_are_batch_means(proj):
+    """Eq. 2 and Eq. 3 are expectations over the minibatch, estimated by the mean: on a
+    split of the rows into parts of 3 and 5, the loss and every gradient of the whole
+    batch are the size-weighted averages of the parts' (a sum in place of the mean, a
+    wrong normaliser or rows mixed across samples all break this; finite differences
+    alone would not see a normaliser shared by a loss and its gradient)."""
+    cfg = synth.make_config("tiny_b8", proj_dim=proj)
+    ring = synth.ring_numpy(synth.make_ring(cfg, 4))
+    st = o.init_state(cfg)
+    fe = o.frontend(cfg, ring, 0)
+    P = st["params"]
+    B = cfg["batch"]
+    z1, _ = o.encoder_fwd(P, fe["x_t1"], cfg)
+    eps_t = px.normal_pairs(cfg["seed"], px.STREAM_EPS_TARGET, 0, B, 6)
+    m = o.target_distribution(P, st["target"], z1, fe, 0.1, eps_t, cfg)["m"]
+    z, _ = o.encoder_fwd(P, fe["x_t"], cfg)
+    eps_a = px.normal_pairs(cfg["seed"], px.STREAM_EPS_ACTOR, 0, B, 6)
+    cut = 3
+
+    def parts(loss_fn):
+        whole = loss_fn(0, B)
+        a, b = loss_fn(0, cut), loss_fn(cut, B)
+        assert whole["loss"] == pytest.approx((cut * a["loss"] + (B - cut) * b["loss"]) / B, rel=1e-12, abs=1e-14)
+        assert set(whole["grads"]) == set(a["grads"]) == set(b["grads"])
+        for name, g in whole["grads"].items():
+            avg = (cut * a["grads"][name] + (B - cut) * b["grads"][name]) / B
+            assert np.allclose(g, avg, rtol=1e-10, atol=1e-14 * max(1.0, np.abs(g).max())), name
+
+    parts(lambda lo, hi: o.critic_loss(P, fe["x_t"][lo:hi], _rows(fe, lo, hi, B), m[lo:hi], cfg))
+    parts(lambda lo, hi: o.actor_loss(P, z[lo:hi], fe["p_t"][lo:hi], eps_a[lo:hi], 0.37, cfg))
+
+
 def test_projection_heads_finite_differences():
     """With a projection layer (train-shape heads on a tiny body), projection grads match FD."""
     cfg = synth.make_config("tiny_b8", proj_dim=16)
