@@ -500,6 +500,38 @@ def test_losses_and_gradients_are_batch_means(proj):
     parts(lambda lo, hi: o.actor_loss(P, z[lo:hi], fe["p_t"][lo:hi], eps_a[lo:hi], 0.37, cfg))
 
 
+@pytest.mark.parametrize("proj", [0, 16])
+def test_target_reads_target_critics_and_the_online_actor(proj):
+    """Alg. 1 "compute target": a' comes from the current actor and the distribution from
+    the target critics (and target critic projection).  Perturbing the online critics
+    leaves m unchanged; perturbing the target critics or the online actor changes it."""
+    cfg = synth.make_config("tiny_b8", proj_dim=proj)
+    ring = synth.ring_numpy(synth.make_ring(cfg, 5))
+    st = o.init_state(cfg)
+    fe = o.frontend(cfg, ring, 0)
+    P, T = st["params"], st["target"]
+    B = cfg["batch"]
+    z1, _ = o.encoder_fwd(P, fe["x_t1"], cfg)
+    eps = px.normal_pairs(cfg["seed"], px.STREAM_EPS_TARGET, 0, B, 6)
+    m0 = o.target_distribution(P, T, z1, fe, 0.1, eps, cfg)["m"]
+    rng = np.random.default_rng(6)
+
+    def bumped(d, pred):
+        out = dict(d)
+        for k in d:
+            if pred(k):
+                out[k] = d[k] + 0.3 * rng.standard_normal(d[k].shape)
+        return out
+
+    crit = lambda k: k.startswith("critic")
+    P_on = bumped(P, crit)                                   # online critics (and projection) moved
+    assert np.array_equal(o.target_distribution(P_on, T, z1, fe, 0.1, eps, cfg)["m"], m0)
+    T_moved = bumped(T, lambda k: True)                      # target critics moved
+    assert np.abs(o.target_distribution(P, T_moved, z1, fe, 0.1, eps, cfg)["m"] - m0).max() > 1e-3
+    P_act = bumped(P, lambda k: k.startswith("actor"))       # online actor moved: a', log pi' change
+    assert np.abs(o.target_distribution(P_act, T, z1, fe, 0.1, eps, cfg)["m"] - m0).max() > 1e-3
+
+
 def test_projection_heads_finite_differences():
     """With a projection layer (train-shape heads on a tiny body), projection grads match FD."""
     cfg = synth.make_config("tiny_b8", proj_dim=16)
