@@ -592,6 +592,29 @@ def test_update_targets_follow_polyak_of_updated_critics():
     assert st["steps"] == dict(critic=1, actor=1, alpha=1) and st["update_idx"] == 1
 
 
+def test_actor_step_reads_updated_critics_and_new_alpha():
+    """Alg. 1 order: the critics take their step first, then the temperature, then the
+    actor, whose objective reads the updated critics and the new alpha (and the
+    pre-update encoder features, detached).  Its loss recomputed from the parameters
+    in that state is the update's; with the pre-update critics or alpha it differs."""
+    import copy
+    cfg = _cfg_tiny()
+    ring = synth.ring_numpy(synth.make_ring(cfg, 7))
+    st = o.init_state(cfg)
+    before = copy.deepcopy(st)
+    stats, tr = o.update(st, ring, cfg)
+    mixed = dict(before["params"])
+    for name, *_ in o.param_spec(cfg):
+        if o.group_of(name) == "critic":
+            mixed[name] = st["params"][name]
+    args = (tr["critic"]["z"], tr["frontend"]["p_t"], tr["eps_actor"])
+    got = o.actor_loss(mixed, *args, stats["alpha"], cfg, with_grads=False)["loss"]
+    assert got == stats["actor_loss"]
+    stale_critics = o.actor_loss(before["params"], *args, stats["alpha"], cfg, with_grads=False)["loss"]
+    stale_alpha = o.actor_loss(mixed, *args, tr["alpha_before"], cfg, with_grads=False)["loss"]
+    assert abs(stale_critics - got) > 1e-9 and abs(stale_alpha - got) > 1e-9
+
+
 def test_policy_freq_delays_actor():
     cfg = _cfg_tiny(policy_freq=2)
     ring = synth.ring_numpy(synth.make_ring(cfg, 0))
