@@ -46,6 +46,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts_match(lib):
     L = lib.load()
     assert L.squint_struct_size(b"squint_config") == ctypes.sizeof(lib.Config)
+    assert L.squint_struct_size(b"squint_replay") == ctypes.sizeof(lib.Replay)
+    assert L.squint_struct_size(b"squint_update_stats") == ctypes.sizeof(lib.UpdateStats)
     assert L.squint_struct_size(b"squint_act_request") == ctypes.sizeof(lib.ActRequest)
     assert L.squint_struct_size(b"nope") == 0
 
