@@ -615,6 +615,31 @@ def test_actor_step_reads_updated_critics_and_new_alpha():
     assert abs(stale_critics - got) > 1e-9 and abs(stale_alpha - got) > 1e-9
 
 
+def test_temperature_step_reads_the_pre_update_actor():
+    """Alg. 1 "update entropy temperature": the temperature loss takes log pi of the actor
+    before its step, at s_t with the actor's noise draws; the reported entropy is
+    -mean(log pi); the first Adam step moves log alpha by lr against the sign of the
+    gradient (|m_hat| / sqrt(v_hat) = 1 at t = 1)."""
+    import copy
+    cfg = _cfg_tiny()
+    ring = synth.ring_numpy(synth.make_ring(cfg, 8))
+    st = o.init_state(cfg)
+    before = copy.deepcopy(st)
+    stats, tr = o.update(st, ring, cfg)
+    _, logp, _ = o.actor_fwd(before["params"], tr["critic"]["z"], tr["frontend"]["p_t"], tr["eps_actor"], cfg)
+    la0 = float(before["params"]["log_alpha"][0])
+    loss, grad = o.alpha_loss(la0, logp, cfg)
+    assert stats["alpha_loss"] == loss
+    assert stats["entropy"] == pytest.approx(-float(np.mean(logp)), rel=1e-15)
+    la1 = float(st["params"]["log_alpha"][0])
+    step = cfg["lr"] * abs(grad) / (abs(grad) + cfg["adam_eps"])
+    assert la1 == pytest.approx(la0 - math.copysign(step, grad), rel=0, abs=1e-15)
+    assert stats["alpha"] == pytest.approx(math.exp(la1), rel=1e-15)
+    # the actor after its step gives another log pi (the temperature did not read it)
+    _, logp_after, _ = o.actor_fwd(st["params"], tr["critic"]["z"], tr["frontend"]["p_t"], tr["eps_actor"], cfg)
+    assert np.abs(logp_after - logp).max() > 1e-9
+
+
 def test_policy_freq_delays_actor():
     cfg = _cfg_tiny(policy_freq=2)
     ring = synth.ring_numpy(synth.make_ring(cfg, 0))
