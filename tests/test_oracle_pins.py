@@ -773,6 +773,32 @@ def test_clipped_double_q_selects_the_smaller_critic():
     assert (q.min(0) <= q.mean(0) + 1e-15).all()
 
 
+@pytest.mark.parametrize("name", ["tiny_b8", "train_b512"])
+def test_q_value_is_the_mean_of_the_categorical_distribution(name):
+    """Q = sum_j p_j z_j over the support of K atoms evenly spaced on [v_min, v_max]:
+    equal logits give the midpoint, a dominant logit the value of its atom, a constant
+    added to every logit changes nothing, and random logits match a plain loop."""
+    cfg = synth.make_config(name)
+    K, lo, hi = cfg["atoms"], cfg["v_min"], cfg["v_max"]
+    z = o.support(cfg)
+    assert z[0] == lo and z[-1] == hi and np.allclose(np.diff(z), (hi - lo) / (K - 1), rtol=0, atol=1e-12)
+    assert o.q_values(np.zeros((1, 3, K)), cfg) == pytest.approx(0.5 * (lo + hi), abs=1e-12)
+    for j in (0, K // 3, K - 1):
+        lg = np.zeros((1, 1, K))
+        lg[0, 0, j] = 60.0
+        assert o.q_values(lg, cfg)[0, 0] == pytest.approx(lo + j * (hi - lo) / (K - 1), abs=1e-12)
+    rng = np.random.default_rng(23)
+    lg = rng.normal(size=(2, 5, K)) * 3
+    q = o.q_values(lg, cfg)
+    assert np.allclose(o.q_values(lg + 7.5, cfg), q, rtol=0, atol=1e-12)
+    for e in range(2):
+        for b in range(5):
+            w = [math.exp(v) for v in lg[e, b]]
+            tot = sum(w)
+            ref = sum(wi / tot * (lo + i * (hi - lo) / (K - 1)) for i, wi in enumerate(w))
+            assert q[e, b] == pytest.approx(ref, abs=1e-11)
+
+
 # ---------------------------------------------------------------- state-based SAC (Fig. 6 left)
 
 def _state_pair(seed=0):
