@@ -229,6 +229,21 @@ def test_tanh_gaussian_log_prob_change_of_variables():
     assert np.allclose(a, np.tanh(u))
 
 
+def test_log_std_spans_its_bounds():
+    """Reading R8: log sigma = lo + (hi - lo)(tanh(raw) + 1) / 2 covers [lo, hi], with the
+    midpoint at raw = 0.  Read back from log pi at mu = 0, eps = 0 (u = 0, where the
+    log-determinant term vanishes): log pi = -A (log sigma + log(2 pi) / 2)."""
+    cfg = _cfg_tiny()
+    A = cfg["action_dim"]
+    lo, hi = cfg["log_std_min"], cfg["log_std_max"]
+    for raw, want in ((-40.0, lo), (0.0, 0.5 * (lo + hi)), (40.0, hi)):
+        out = np.concatenate([np.zeros((1, A)), np.full((1, A), raw)], axis=1)
+        a, logp, _ = o.tanh_gaussian(out, np.zeros((1, A)), cfg)
+        assert np.all(a == 0.0)
+        log_std = -logp[0] / A - 0.5 * math.log(2 * math.pi)
+        assert log_std == pytest.approx(want, abs=1e-12)
+
+
 def test_tanh_gaussian_density_integrates_to_one():
     """For one action dimension the squashed density integrates to 1 over (-1, 1)."""
     from scipy.integrate import quad
