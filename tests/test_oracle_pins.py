@@ -78,6 +78,26 @@ def _brute_sums(img, dx, dy, p, f):
     return out
 
 
+def test_minibatch_slots_and_crop_offsets_cover_their_ranges():
+    """Alg. 1 "sample mini-batch": slots in [0, N) with the next slot (idx + 1) mod N;
+    the crop offsets take every value of [0, 2p] and no other (p = 8, 512 samples, eight
+    updates), x and y drawn separately, o_t and o_{t+1} separately."""
+    cfg = synth.make_config("train_b512")
+    p = cfg["shift_pad"]
+    seen_x, seen_y = set(), set()
+    for u in range(8):
+        idx, nxt = o.sample_indices(cfg, u, 300)
+        assert idx.min() >= 0 and idx.max() < 300 and np.array_equal(nxt, (idx + 1) % 300)
+        dx, dy = o.sample_shifts(cfg, u, px.STREAM_SHIFT_T)
+        dx1, dy1 = o.sample_shifts(cfg, u, px.STREAM_SHIFT_T1)
+        seen_x |= set(dx.tolist()) | set(dx1.tolist())
+        seen_y |= set(dy.tolist()) | set(dy1.tolist())
+        assert not np.array_equal(dx, dy) and not np.array_equal(dx, dx1)
+    assert seen_x == set(range(2 * p + 1)) and seen_y == set(range(2 * p + 1))
+    idx, _ = o.sample_indices(cfg, 0, 2)                    # the smallest ring: both slots drawn
+    assert set(idx.tolist()) == {0, 1}
+
+
 def test_shift_squint_brute_force():
     rng = np.random.default_rng(2)
     img = rng.integers(0, 256, size=(3, 2, 12, 8), dtype=np.uint8)
