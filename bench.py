@@ -234,16 +234,22 @@ def run_reference(args):
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     ring = {k: LazyRows(v) for k, v in synth.make_ring(cfg, args.seed, device=dev).items()}
     from oracle import squint_sac as o
-    # size each step's sample so the whole run stays within ~3 minutes
-    probe = synth.make_config(WORKLOAD, batch=64)
-    st = o.init_state(probe)
-    t0 = time.perf_counter()
-    o.update(st, ring, probe)
-    per_sample = (time.perf_counter() - t0) / 64
+    # size each step's sample so the whole run stays within ~3 minutes: an update's time
+    # is a fixed part (optimiser and polyak over every parameter) plus a per-sample part,
+    # fitted from updates at two batch sizes
+    def probe_time(b):
+        pcfg = synth.make_config(WORKLOAD, batch=b)
+        st = o.init_state(pcfg)
+        t0 = time.perf_counter()
+        o.update(st, ring, pcfg)
+        return time.perf_counter() - t0
+    t16, t64 = probe_time(16), probe_time(64)
+    per_sample = max((t64 - t16) / 48, 1e-6)
+    fixed = max(t16 - 16 * per_sample, 0.0)
     # a step is UTD_K updates, as in our arm
     budget = 150.0 / max(1, args.steps + args.warmup)
     bsz = 512
-    while bsz > 16 and UTD_K * bsz * per_sample > budget:
+    while bsz > 16 and UTD_K * (fixed + bsz * per_sample) > budget:
         bsz //= 2
     scfg = synth.make_config(WORKLOAD, batch=bsz)
     state = o.init_state(scfg)
