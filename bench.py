@@ -217,14 +217,20 @@ class LazyRows:
         return self.t.index_select(0, ii).cpu().numpy()
 
 
-def workload_config(workload, precision, world):
-    """The bench line's `config`, the same for both arms (precision: the arm's arithmetic)."""
-    return {"workload": WORKLOAD_TEXT[workload][0], "updates_per_step": UTD_K, "precision": precision,
+def workload_config(workload, world):
+    """The bench line's `config`, the same for both arms (each arm's arithmetic is its `dtype`)."""
+    return {"workload": WORKLOAD_TEXT[workload][0], "updates_per_step": UTD_K,
             "l2": WORKLOAD_TEXT[workload][1], "parallelism": f"replicas x{world}"}
 
 
 def run_reference(args):
-    """The reference arm: the FP64 CPU oracle on the same workload, rank 0 only."""
+    """The reference arm: the FP64 CPU oracle on the same workload, rank 0 only.
+
+    Every timed oracle update is a whole update of the batch-512 workload, as in our
+    arm.  A step holds UTD_K of them when the K + W steps fit in about three minutes,
+    else fewer (at least one): the rate in updates/s does not depend on how many
+    updates a step groups, so the sample is bounded without scaling a smaller batch.
+    """
     import torch
     from paper_2602_21203_gb300 import synth
     world, rank, _ = dist_setup(args)
@@ -234,40 +240,26 @@ def run_reference(args):
     dev = "cuda" if torch.cuda.is_available() else "cpu"
     ring = {k: LazyRows(v) for k, v in synth.make_ring(cfg, args.seed, device=dev).items()}
     from oracle import squint_sac as o
-    # size each step's sample so the whole run stays within ~3 minutes: an update's time
-    # is a fixed part (optimiser and polyak over every parameter) plus a per-sample part,
-    # fitted from updates at two batch sizes
-    def probe_time(b):
-        pcfg = synth.make_config(WORKLOAD, batch=b)
-        st = o.init_state(pcfg)
-        t0 = time.perf_counter()
-        o.update(st, ring, pcfg)
-        return time.perf_counter() - t0
-    t16, t64 = probe_time(16), probe_time(64)
-    per_sample = max((t64 - t16) / 48, 1e-6)
-    fixed = max(t16 - 16 * per_sample, 0.0)
-    # a step is UTD_K updates, as in our arm
-    budget = 150.0 / max(1, args.steps + args.warmup)
-    bsz = 512
-    while bsz > 16 and UTD_K * (fixed + bsz * per_sample) > budget:
-        bsz //= 2
-    scfg = synth.make_config(WORKLOAD, batch=bsz)
-    state = o.init_state(scfg)
-    for _ in range(args.warmup * UTD_K):
-        o.update(state, ring, scfg)
+    state = o.init_state(cfg)
     t0 = time.perf_counter()
-    for _ in range(args.steps * UTD_K):
-        o.update(state, ring, scfg)
+    o.update(state, ring, cfg)                       # also the first warm-up update
+    one = time.perf_counter() - t0
+    per_step = max(1, min(UTD_K, int(180.0 / max(one * (args.steps + args.warmup), 1e-9))))
+    for _ in range(args.warmup * per_step - 1):
+        o.update(state, ring, cfg)
+    t0 = time.perf_counter()
+    for _ in range(args.steps * per_step):
+        o.update(state, ring, cfg)
     dt = time.perf_counter() - t0
-    value = args.steps * UTD_K * (bsz / cfg["batch"]) / dt
+    value = args.steps * per_step / dt
     cores = blas_threads()
-    sample = (f"{args.steps} steps of {UTD_K} FP64 oracle updates on batch slices of {bsz} of the 512-sample "
-              f"workload, scaled to B=512")
+    sample = (f"{args.steps} steps of {per_step} whole FP64 oracle update(s) of the batch-512 workload "
+              f"({args.steps * per_step} updates in {dt:.1f} s)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(WORKLOAD, "f64 (oracle)", world),
+        "config": workload_config(WORKLOAD, world),
         "cpu_baseline": {"value": value, "unit": "updates/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -445,7 +437,7 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         lazy = {k: LazyRows(v) for k, v in ring.items()}
-        ups, n, dt = oracle_updates_per_s(cfg, lazy, budget_s=15.0)
+        ups, n, dt = oracle_updates_per_s(cfg, lazy, budget_s=15.0, max_updates=12)
         cpu = {"value": ups, "unit": "updates/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"{n} FP64 oracle update(s) of the full batch-512 workload in {dt:.1f} s"}
 
@@ -455,7 +447,7 @@ def run_ours(args):
             "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16": "bf16", "fp8": "e4m3+bf16", "mxfp8": "e4m3(mx)+bf16"}[args.precision],
             "data": "synthetic",
-            "config": workload_config(args.workload, args.precision, world),
+            "config": workload_config(args.workload, world),
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": gpu_launches, "clocks": clk,
         }

@@ -265,7 +265,13 @@ int squint_set_state(squint_handle* h, const void* host, size_t bytes);
  * "m" f32[B,K] projected target, "logits" f32[E,B,K], "logits_target" f32[E,B,K],
  * "logp_next" f32[B], "logp_t" f32[B], "a_next" f32[B,A], "a_pi" f32[B,A],
  * "grads" f32[param_count] (critic group from the critic step, actor group from
- * the actor step), "z_t" f32[B,F].  *bytes in: capacity, out: size. */
+ * the actor step), "z_t" f32[B,F], "conv0".."conv7" f32[B,ch,oh,ow] (conv layer l's
+ * output after its ReLU, o_t images; learners that keep FP32 conv planes), "dconv0"
+ * f32[B,ch,oh,ow] (gradient at the first conv's pre-activation, after the ReLU mask;
+ * FP32 planes) or "dconv0_phwc" bf16 (the same in padded HWC: per image (oh+4)(ow+4)
+ * pixels of 32 channels, pixel (y,x) at (y+2)(ow+4)+x+2; tensor-core encoder without
+ * recompute).  *bytes in: capacity, out: size; SQUINT_EINVAL for a name this learner
+ * does not keep. */
 int squint_debug_tensor(squint_handle* h, const char* name, void* host, size_t* bytes);
 
 /* ------------------------------------------------------------------ errors */

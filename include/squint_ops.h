@@ -155,12 +155,14 @@ int squint_op_wgrad32(int nimg, int H, int W, const void* x, const void* dy, flo
  * partial sums live in one fixed device array of squint_op_conv3x3_wgrad_noalloc_max()
  * floats (4 MiB) that every device loading the library keeps until exit; shapes
  * needing more return SQUINT_EINVAL with a message in squint_last_error().  The
- * first call on each device looks up the array's device address
+ * first call in each CUDA context of a device (the device's primary context, and
+ * again after a cudaDeviceReset) looks up the array's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call before
- * any stream capture.  All calls share the array: two calls whose kernels overlap
- * on the GPU (different streams, or concurrent host threads) race and give wrong
- * results; serialise them.  Each call writes every partial it reads, so nothing
- * carries over between calls.
+ * any stream capture.  A CUDA error left pending by an earlier call is reported as
+ * SQUINT_ECUDA before anything is launched.  All calls share the array: two calls
+ * whose kernels overlap on the GPU (different streams, or concurrent host threads)
+ * race and give wrong results; serialise them.  Each call writes every partial it
+ * reads, so nothing carries over between calls.
  */
 int64_t squint_op_conv3x3_wgrad_noalloc_max(void);
 int squint_op_conv3x3_wgrad_noalloc(int nimg, int cin, int h, int w, int cout, int stride, const float* x,

@@ -164,6 +164,9 @@ struct squint_handle {
     float* dconv_a = nullptr;         // ping-pong conv gradients
     float* dconv_b = nullptr;
     float* wgrad_work = nullptr;
+    // FP32 gradient at the first conv's pre-activation [B, ch, oh, ow] as the last update
+    // left it (the buffer the first layer's weight gradient read; FP32-plane paths only)
+    const float* dconv0 = nullptr;
     float* dxq = nullptr;             // [B, Dc] input gradient of the critics in the actor step
     float* ln_work = nullptr;         // LayerNorm backward column partials
     float* dout_a = nullptr;          // [B, 2A]

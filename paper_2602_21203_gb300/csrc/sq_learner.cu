@@ -1122,6 +1122,7 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
                          (int64_t)c0.cout * c0.oh * c0.ow};
             {
                 ProfScope ps(this, s1, "conv_f32_wgrad", conv_flops(c0, B), 0);
+                if (rc_chunk) dconv0 = dconv_a;
                 if (rc_chunk)
                     launch_conv_wgrad<float>(sh, dconv_a, x2, G + c0.wo, G + c0.bo, wgrad_work, s1);
                 else if (launch_conv_wgrad_phwc(sh, dact_p[0], x2, G + c0.wo, G + c0.bo, wgrad_work, s1) != 0)
@@ -1134,6 +1135,7 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
             ConvShape sh{B, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
                          (int64_t)cv.cout * cv.oh * cv.ow};
             const float* xin = l == 0 ? x2 : conv_out[l - 1];
+            if (l == 0) dconv0 = cur;
             {
                 ProfScope ps(this, s1, "conv_f32_wgrad", conv_flops(cv, B), 0);
                 launch_conv_wgrad<float>(sh, cur, xin, G + cv.wo, G + cv.bo, wgrad_work, s1);

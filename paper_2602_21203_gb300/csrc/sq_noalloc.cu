@@ -11,9 +11,12 @@
 #include "squint_ops.h"
 #include "sq_kernels.cuh"
 
+#include <cuda.h>
+
 #include <map>
 #include <mutex>
 #include <string>
+#include <utility>
 
 namespace sq {
 extern thread_local std::string g_last_error;
@@ -27,17 +30,48 @@ namespace {
 constexpr int64_t kScratchFloats = int64_t(1) << 20;
 static __device__ __align__(256) float g_wgrad_scratch[kScratchFloats];
 
-std::mutex g_mu;
-std::map<int, float*> g_scratch_addr;   // device ordinal -> device address of g_wgrad_scratch
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the scratch array on the current device, looked up once per
-// device (the host-side name is only a handle for the runtime, not an address).
+std::mutex g_mu;
+// (device ordinal, context id) -> device address of g_wgrad_scratch in that context.  The
+// context id is unique within the process, so a context torn down and created again
+// (cudaDeviceReset) gets a fresh lookup instead of a stale address.
+std::map<std::pair<int, unsigned long long>, float*> g_scratch_addr;
+
+// Id of the calling thread's current context, from the driver (resolved once).
+bool current_context_id(unsigned long long* id) {
+    static CtxGetCurrentFn get_ctx = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_ctx = reinterpret_cast<CtxGetCurrentFn>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(p);
+    });
+    CUcontext ctx = nullptr;
+    if (!get_ctx || !get_id || get_ctx(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch array in the current device's context, looked up once
+// per context (the host-side name is only a handle for the runtime, not an address).
 float* scratch_on_current_device(int* rc) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) { *rc = SQUINT_ECUDA; return nullptr; }
+    unsigned long long ctx_id = 0;
     std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_scratch_addr.find(dev);
-    if (it != g_scratch_addr.end()) return it->second;
+    if (current_context_id(&ctx_id)) {
+        auto it = g_scratch_addr.find(std::make_pair(dev, ctx_id));
+        if (it != g_scratch_addr.end()) return it->second;
+    }
+    // the lookup also makes the device's context current on this thread if none was
     float* ptr = nullptr;
     const cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_wgrad_scratch);
     if (e != cudaSuccess || !ptr) {
@@ -46,7 +80,12 @@ float* scratch_on_current_device(int* rc) {
         *rc = SQUINT_ECUDA;
         return nullptr;
     }
-    g_scratch_addr[dev] = ptr;
+    if (!current_context_id(&ctx_id)) {
+        sq::g_last_error = "weight-gradient scratch: the current CUDA context could not be identified";
+        *rc = SQUINT_ECUDA;
+        return nullptr;
+    }
+    g_scratch_addr[std::make_pair(dev, ctx_id)] = ptr;
     return ptr;
 }
 
@@ -72,12 +111,23 @@ int squint_op_conv3x3_wgrad_noalloc(int nimg, int cin, int h, int w, int cout, i
                            " scratch floats, more than the fixed " + std::to_string(kScratchFloats);
         return SQUINT_EINVAL;
     }
+    // an error some earlier call left pending is reported as such, not as this launch's
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) {
+        sq::g_last_error = std::string("a CUDA error from an earlier call is pending: ") + cudaGetErrorString(pending);
+        return SQUINT_ECUDA;
+    }
     int rc = SQUINT_OK;
     float* scratch = scratch_on_current_device(&rc);
     if (!scratch) return rc;
     // every partial the reduction reads is written by this call first: nothing to clear
     sq::launch_conv_wgrad<float>(sh, dy, x, dw, db, scratch, (cudaStream_t)stream);
-    return cudaGetLastError() == cudaSuccess ? SQUINT_OK : SQUINT_ECUDA;
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        sq::g_last_error = std::string("conv3x3 weight gradient launch: ") + cudaGetErrorString(e);
+        return SQUINT_ECUDA;
+    }
+    return SQUINT_OK;
 }
 
 }  // extern "C"

@@ -80,6 +80,20 @@ int squint_handle::debug_tensor(const char* name, void* host, size_t* bytes) {
     else if (n == "grads") { src = grads; sz = 4 * (size_t)L.total; }
     else if (n == "z_t") { src = conv_out.empty() ? nullptr : conv_out.back(); sz = 4 * (size_t)B * L.feat; }
     else if (n == "target") { src = target; sz = 4 * (size_t)L.target_n; }
+    else if (n == "dconv0" && !L.conv.empty()) {
+        // gradient at the first conv's pre-activation (after the ReLU mask), FP32 planes
+        src = dconv0; sz = 4 * (size_t)B * L.conv[0].cout * L.conv[0].oh * L.conv[0].ow;
+        if (!src) { g_last_error = "dconv0: this learner keeps that gradient in padded HWC (dconv0_phwc)"; return SQUINT_EINVAL; }
+    } else if (n == "dconv0_phwc" && tc_conv && !rc_chunk) {
+        // the same as BF16 padded HWC: per image (oh + 4) x (ow + 4) pixels of 32 channels,
+        // pixel (y, x) at row (y + 2) (ow + 4) + x + 2
+        src = dact_p[0]; sz = 2 * (size_t)B * (L.conv[0].oh + 4) * (L.conv[0].ow + 4) * 32;
+    } else if (n.size() == 5 && n.compare(0, 4, "conv") == 0 && n[4] >= '0' && n[4] < '0' + (int)L.conv.size() &&
+               conv_out[n[4] - '0']) {
+        // conv layer l's output (after ReLU) for the o_t images, FP32 planes
+        const ConvL& cv = L.conv[n[4] - '0'];
+        src = conv_out[n[4] - '0']; sz = 4 * (size_t)B * cv.cout * cv.oh * cv.ow;
+    }
     else { g_last_error = "unknown debug tensor"; return SQUINT_EINVAL; }
     if (!host) { *bytes = sz; return SQUINT_OK; }
     if (*bytes < sz) { *bytes = sz; return SQUINT_EINVAL; }

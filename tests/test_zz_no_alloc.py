@@ -1,4 +1,5 @@
-"""The allocation-free conv weight gradient against the workspace entry point (needs a GB300).
+"""The allocation-free conv weight gradient against the workspace entry point and the
+FP64 oracle (needs a GB300).
 
 Callers that cannot allocate device memory (a frozen pool, an allocator-free
 real-time loop, a foreign allocator) use squint_op_conv3x3_wgrad_noalloc, whose
@@ -10,6 +11,8 @@ import ctypes
 import numpy as np
 import pytest
 import torch
+
+from oracle import squint_sac as o
 
 pytestmark = pytest.mark.gpu
 
@@ -45,6 +48,12 @@ def test_noalloc_weight_gradient_equals_workspace_entry_on_two_calls():
         assert rc == 0, L.squint_last_error().decode()
         for a, b in ((dw, dw_ref), (db, db_ref)):
             a, b = a.cpu().double().numpy(), b.cpu().double().numpy()
+            assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
+        # and against the FP64 oracle's weight gradient of the same operands
+        _, dw_o, db_o = o.conv3x3_bwd(x.cpu().double().numpy(), w.cpu().double().numpy(),
+                                      dy.cpu().double().numpy(), stride, need_dx=False)
+        for a, b in ((dw, dw_o), (db, db_o)):
+            a = a.cpu().double().numpy()
             assert np.linalg.norm(a - b) <= 1e-5 * np.linalg.norm(b)
 
 

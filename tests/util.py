@@ -17,6 +17,17 @@ def split_params(flat, cfg):
     return out
 
 
+def post_critic_state(P0, p_gpu, cfg):
+    """The oracle's parameters P0 with the GPU's critic group and temperature after an
+    update: the state the GPU's actor step read (Alg. 1: the actor step follows the
+    critic and temperature steps; the actor group is still P0's)."""
+    P = {k: v.copy() for k, v in P0.items()}
+    for name, *_ in o.param_spec(cfg):
+        if o.group_of(name) in ("critic", "alpha"):
+            P[name] = np.array(p_gpu[name], dtype=np.float64)
+    return P
+
+
 def flatten(d, cfg):
     return np.concatenate([np.asarray(d[name], dtype=np.float64).ravel() for name, *_ in o.param_spec(cfg)])
 
