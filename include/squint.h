@@ -274,6 +274,19 @@ int squint_set_state(squint_handle* h, const void* host, size_t bytes);
  * does not keep. */
 int squint_debug_tensor(squint_handle* h, const char* name, void* host, size_t* bytes);
 
+/* Failure-detection settings (tests).  Every wait of the tensor-core kernels on an
+ * mbarrier is bounded: past its limit the waiting thread records a code in the
+ * handle's device error word and gives up, the CTA waits (bounded) for the copies it
+ * still has in flight, frees its tensor memory and returns; squint_update with
+ * statistics then reports SQUINT_ETIMEOUT and the handle is failed.  Settings:
+ * "wait_cycles" = clock cycles a wait of the update's tensor-core GEMMs may take
+ * (0: the default, about 2 s); "stall_gemm_loads" = 1 makes those GEMMs issue no
+ * operand loads, so their first operand wait runs out with nothing in flight (the
+ * way a test makes a wait run out without faulting anything).  Captured update
+ * graphs are dropped when a setting changes.  SQUINT_EINVAL for an unknown name or
+ * value. */
+int squint_set_debug(squint_handle* h, const char* name, int64_t value);
+
 /* ------------------------------------------------------------------ errors */
 
 /* sizeof of an ABI struct by name ("squint_config", "squint_replay",

@@ -233,12 +233,25 @@ int squint_set_replay(squint_handle* h, const squint_replay* ring) {
         // captured updates hold the old ring's addresses and size: the next update of
         // each k captures again
         SQ_CK(h, cudaDeviceSynchronize());
-        for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-        h->graphs.clear();
-        h->graph_kernels.clear();
+        h->drop_graphs();
     }
     h->ring = *ring;
     h->has_ring = true;
+    return SQUINT_OK;
+}
+
+int squint_set_debug(squint_handle* h, const char* name, int64_t value) {
+    if (!h || !name) return SQUINT_EINVAL;
+    const std::string n(name);
+    sq::TcWait w = h->gemm_wait;
+    if (n == "wait_cycles" && value >= 0) w.cycles = value;
+    else if (n == "stall_gemm_loads" && (value == 0 || value == 1)) w.stall = (int)value;
+    else { sq::g_last_error = "unknown debug setting or value"; return SQUINT_EINVAL; }
+    if (w.cycles != h->gemm_wait.cycles || w.stall != h->gemm_wait.stall) {
+        SQ_CK(h, cudaDeviceSynchronize());
+        h->drop_graphs();   // captured updates hold the old settings
+    }
+    h->gemm_wait = w;
     return SQUINT_OK;
 }
 

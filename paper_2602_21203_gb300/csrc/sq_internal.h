@@ -88,6 +88,10 @@ struct squint_handle {
     // update runs; SQUINT_DRAW_AHEAD=0 at creation draws every one in line instead
     bool draw_ahead = true;
     bool launch_failed = false;       // a tensor map could not describe an operand
+    // bounded waits of the update's tensor-core GEMMs (cycles 0: the default limit) and
+    // the failure-test switch that makes them run out (squint_set_debug)
+    sq::TcWait gemm_wait{0, 0};
+    void drop_graphs();
     int device = 0;
     int* d_err = nullptr;             // device error word of bounded waits
 

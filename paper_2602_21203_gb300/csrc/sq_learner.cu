@@ -169,7 +169,8 @@ void GemmBuilder::flush() {
             int kmax = 0;
             for (const TcGemm& g : *v) kmax = std::max(kmax, g.K);
             const bool split = split_ && (h_->gemm_split || kmax >= kLongK);
-            if (launch_tc_gemm(v->data(), (int)v->size(), h_->d_err, s_, split) != 0) h_->launch_failed = true;
+            if (launch_tc_gemm(v->data(), (int)v->size(), h_->d_err, s_, split, &h_->gemm_wait) != 0)
+                h_->launch_failed = true;
         }
     }
     fp_.clear();
@@ -1274,6 +1275,12 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
     fork(s3, s);
     mark(s);
     mark(s);
+}
+
+void squint_handle::drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+    graph_kernels.clear();
 }
 
 void squint_handle::cast_conv_weights(cudaStream_t s) {

@@ -17,8 +17,10 @@
 // Operands are K-major (K contiguous) or MN-major (M or N contiguous), so the
 // forward X W^T, the data gradient dY W and the weight gradient dY^T X all run
 // from the row-major buffers without transposed copies.
-// Every wait is bounded: past kWaitCycles the waiting thread records an error
-// code in *err and gives up; the tile is abandoned and TMEM is still freed.
+// Every wait is bounded: past the launch's wait limit (kWaitCycles unless the host
+// sets another) the waiting thread records an error code in *err and gives up; the
+// tile is abandoned, the CTA waits (bounded again) for the operand copies it still
+// has in flight, and TMEM is still freed.
 #include "sq_tc.cuh"
 
 #include <cuda.h>
@@ -72,6 +74,9 @@ struct TcBatch {
     int splits;       // CTAs per output tile = cluster size (K split)
     int ln;           // LayerNorm epilogue: the cluster is the row block's column tiles (splits == 1)
     int* err;
+    long long wait_limit;   // clock cycles a wait may take before it gives up
+    int stall;        // failure test: the producer issues no operand loads, so the first
+                      // operand wait runs out (nothing else is in flight when it does)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -91,12 +96,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false (and *err = code) if the phase did not complete in time.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code) {
+// Bounded wait: false (and *err = code) if the phase did not complete within `limit` cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err, int code, long long limit) {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > kWaitCycles) {
+        if (clock64() - t0 > limit) {
             atomicCAS(err, 0, code);
             return false;
         }
@@ -244,6 +249,9 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+    // tmem_slot[1]: operand stages the producer issued; tmem_slot[2]: stages the MMA
+    // issuer consumed (the copies of the ones in between are still in flight after a
+    // wait gave up)
     float* bias_s = reinterpret_cast<float*>(tmem_slot + 4);          // [BN]
     float* g_s = bias_s + BN;                                          // [BN] LayerNorm gain
     float* beta_s = g_s + BN;                                          // [BN] LayerNorm shift
@@ -280,6 +288,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     const int it0 = (int)((int64_t)nkb * n_pairs * split / gb.splits);
     const int total = (int)((int64_t)nkb * n_pairs * (split + 1) / gb.splits) - it0;
     const bool producer = warp == 1 && lane == 0, issuer = warp == 0 && lane == 0;
+    const long long wlim = gb.wait_limit;
     auto load_stage = [&](int i) {
         const int s = i % STAGES;
         const int pr = (it0 + i) / nkb, kb = (it0 + i) % nkb;
@@ -301,6 +310,8 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
             mbar_init(empty0 + 8 * s, 1);
         }
         mbar_init(done_bar, 1);
+        tmem_slot[1] = 0;
+        tmem_slot[2] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int q = 0; q < n_pairs; ++q) {
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.ta[q])) : "memory");
@@ -310,7 +321,7 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     // inputs are read, and tensor memory taken, only once the previous kernel has finished:
     // a kernel that holds tensor memory never waits on a later one
     SQ_KERNEL_ENTRY();
-    const int pre = total < STAGES ? total : STAGES;
+    const int pre = gb.stall ? 0 : (total < STAGES ? total : STAGES);
     if (producer)
         for (int i = 0; i < pre; ++i) load_stage(i);   // first stages: no slot to wait for
     if (warp == 0) {
@@ -333,18 +344,22 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     }
 
     if (producer) {
-        for (int i = pre; i < total; ++i) {
+        int issued = pre;
+        for (int i = pre; i < total && !gb.stall; ++i) {
             const int s = i % STAGES;
-            if (!mbar_wait(empty0 + 8 * s, ((i / STAGES) - 1) & 1, gb.err, 1)) break;
+            if (!mbar_wait(empty0 + 8 * s, ((i / STAGES) - 1) & 1, gb.err, 1, wlim)) break;
             load_stage(i);
+            issued = i + 1;
         }
+        tmem_slot[1] = issued;
     } else if (issuer) {
         // MMA issuer
         constexpr uint32_t idesc = F8 ? idesc_e4m3(BM, BN, A_MN, B_MN) : idesc_bf16(BM, BN, A_MN, B_MN);
         if constexpr (MX) {
-            for (int i = 0; i < total; ++i) {
+            int i = 0;
+            for (; i < total; ++i) {
                 const int s = i % STAGES;
-                if (!mbar_wait(full0 + 8 * s, (i / STAGES) & 1, gb.err, 2)) break;
+                if (!mbar_wait(full0 + 8 * s, (i / STAGES) & 1, gb.err, 2, wlim)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = base + s * STAGE_BYTES;
                 const uint32_t sf = base + SF_OFF + s * 2 * SF_ATOM;
@@ -358,12 +373,13 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                            idesc_mx(BM, BN, (uint32_t)kk), sfa_t, sfb_t, (i > 0 || kk > 0) ? 1u : 0u);
                 mma_commit(empty0 + 8 * s);
             }
+            tmem_slot[2] = i;
             mma_commit(done_bar);
         } else {
-            bool ok = true;
-            for (int i = 0; i < total; ++i) {
+            int i = 0;
+            for (; i < total; ++i) {
                 const int s = i % STAGES;
-                if (!mbar_wait(full0 + 8 * s, (i / STAGES) & 1, gb.err, 2)) { ok = false; break; }
+                if (!mbar_wait(full0 + 8 * s, (i / STAGES) & 1, gb.err, 2, wlim)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t st = base + s * STAGE_BYTES;
 #pragma unroll
@@ -376,15 +392,15 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
                                  (i > 0 || kk > 0) ? 1u : 0u);
                 mma_commit(empty0 + 8 * s);
             }
+            tmem_slot[2] = i;
             mma_commit(done_bar);
-            (void)ok;
         }
     }
     __syncwarp();
 
     // epilogue, part 1: every thread moves its accumulator row from tensor memory into
     // shared memory (the operand stages are idle once the final commit has arrived)
-    const bool have = mbar_wait(done_bar, 0, gb.err, 3);
+    const bool have = mbar_wait(done_bar, 0, gb.err, 3, wlim);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float* red = reinterpret_cast<float*>(smem);   // [BM][RED_LD]
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
@@ -650,6 +666,11 @@ __global__ void __launch_bounds__(128, 1) tc_gemm_kernel(const __grid_constant__
     }
     // no CTA of the cluster leaves while another may still read its shared memory
     cluster_sync();
+    // after a wait gave up: operand copies issued but never consumed still land in this
+    // CTA's shared memory; wait for them (bounded) before the CTA can leave
+    if (threadIdx.x == 0)
+        for (int i = (int)tmem_slot[2]; i < (int)tmem_slot[1]; ++i)
+            mbar_wait(full0 + 8 * (i % STAGES), (i / STAGES) & 1, gb.err, 4, wlim);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -750,12 +771,15 @@ void tc_prepare() {
     }
 }
 
-int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, bool allow_split) {
+int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, bool allow_split,
+                   const TcWait* wait) {
     for (int base = 0; base < n_probs; base += kMaxProbs) {
         TcBatch gb;
         std::memset(&gb, 0, sizeof(gb));
         gb.n = std::min(kMaxProbs, n_probs - base);
         gb.err = err;
+        gb.wait_limit = wait && wait->cycles > 0 ? wait->cycles : kWaitCycles;
+        gb.stall = wait ? wait->stall : 0;
         int tiles = 0, min_iters = 1 << 30;
         bool a_mn = probs[base].a[0].mn_major, b_mn = probs[base].b[0].mn_major;
         const int f8k = probs[base].fp8;

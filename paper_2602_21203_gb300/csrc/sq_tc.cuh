@@ -82,7 +82,11 @@ void launch_quantize_mx(const QuantItem* items, int n, cudaStream_t s);
 // allow_split = false keeps every output row's arithmetic independent of the other
 // rows of the launch (no K split), e.g. for inference whose result must not depend
 // on which requests share the batch.
-int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, bool allow_split = true);
+// Bounded waits of a launch: `cycles` per wait (0: the default, about 2 s); `stall` (failure
+// tests only) makes the producer issue no operand loads, so the first operand wait runs out.
+struct TcWait { long long cycles; int stall; };
+int launch_tc_gemm(const TcGemm* probs, int n_probs, int* err, cudaStream_t s, bool allow_split = true,
+                   const TcWait* wait = nullptr);
 // Opt the kernels in to their shared memory and resolve the tensor-map encoder (call outside capture).
 void tc_prepare();
 

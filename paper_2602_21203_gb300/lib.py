@@ -93,6 +93,7 @@ def load():
         "squint_get_state": (I, [P, P, ctypes.POINTER(SZ)]),
         "squint_set_state": (I, [P, P, SZ]),
         "squint_debug_tensor": (I, [P, ctypes.c_char_p, P, ctypes.POINTER(SZ)]),
+        "squint_set_debug": (I, [P, ctypes.c_char_p, I64]),
         "squint_struct_size": (SZ, [ctypes.c_char_p]),
         "squint_graph_kernel_count": (I64, [P, I]),
         "squint_device_bytes": (I64, [P]),
@@ -267,6 +268,9 @@ class Learner:
         _check(self.lib.squint_debug_tensor(self.h, name.encode(), out.ctypes.data_as(ctypes.c_void_p),
                                             ctypes.byref(n)), "squint_debug_tensor")
         return out
+
+    def set_debug(self, name, value):
+        _check(self.lib.squint_set_debug(self.h, name.encode(), int(value)), "squint_set_debug")
 
     def graph_kernel_count(self, k):
         return int(self.lib.squint_graph_kernel_count(self.h, int(k)))

@@ -100,4 +100,5 @@ def test_invalid_configs_are_rejected_without_a_device(lib):
     assert L.squint_config_preset(b"unknown", ctypes.byref(lib.Config())) == lib.EINVAL
     assert L.squint_destroy(None) == 0
     assert L.squint_update(None, 1, None, None) == lib.EINVAL
+    assert L.squint_set_debug(None, b"wait_cycles", 100) == lib.EINVAL
     assert L.squint_strerror(lib.ETIMEOUT).decode() == "timed out"
