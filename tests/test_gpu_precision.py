@@ -16,9 +16,9 @@ and are compared where the conditioning is taken out, at the benchmark spec's bounds:
   moves by 2 lr.  So the oracle's actor step is evaluated on the GPU's own
   post-critic-step parameters and temperature (with the oracle's pre-update actor,
   encoder features and noise); a separate check shows that every critic parameter
-  whose step differs by more than lr / 2 is one whose oracle gradient is within ten
-  times the tensor's RMS gradient error (plus Adam's eps) of zero, with the
-  opposite sign on the GPU unless it is within ten times eps of zero.
+  whose step differs by more than lr / 2 is one whose oracle gradient is below 1e-3
+  of its tensor's norm (an element the FP32 gradient tolerance cannot tell from
+  zero), with the opposite sign on the GPU unless it is within ten times eps of zero.
 * The first convolution's weight gradient sums batch x 15 x 15 pixels at the end
   of the longest ReLU chain: a pre-activation within rounding distance of zero that
   takes the other branch changes one pixel's whole upstream gradient.  It is
@@ -105,7 +105,7 @@ def test_precision_sweep_100_batches():
     lazy = lazy_ring(ring)
     rows = {p: {k: [] for k in KEYS} for p in ("fp32", "bf16", "fp8", "mxfp8")}
     worst_name = {}
-    flips = {"adam": 0, "relu": 0, "batches_relu": 0}
+    flips = {"adam": 0, "adam_ratio": 0.0, "relu": 0, "batches_relu": 0}
     lr = base["lr"]
     for s in range(N_BATCHES):
         cfg = synth.make_config("train_b512", seed=s)
@@ -165,9 +165,11 @@ def test_precision_sweep_100_batches():
                 d_ref = state["params"][k] - P0[k]
                 bad = np.abs(d_gpu - d_ref) > 0.5 * lr
                 if bad.any():
-                    rms_err = float(np.sqrt(np.mean((g[k] - v) ** 2)))
-                    assert np.all(np.abs(v[bad]) <= 10.0 * (rms_err + cfg["adam_eps"])), \
-                        (s, k, float(np.abs(v[bad]).max()), rms_err)
+                    # an element the FP32 gradient tolerance (1e-3 of the tensor's norm)
+                    # cannot tell from zero
+                    scale = float(np.linalg.norm(v))
+                    assert np.all(np.abs(v[bad]) <= 1e-3 * scale), (s, k, float(np.abs(v[bad]).max()), scale)
+                    flips["adam_ratio"] = max(flips["adam_ratio"], float(np.abs(v[bad]).max()) / scale)
                     # the other sign, or a gradient near Adam's eps (a step short of lr)
                     unsat = np.minimum(np.abs(g[k][bad]), np.abs(v[bad])) < 10.0 * cfg["adam_eps"]
                     assert np.all((np.sign(g[k][bad]) != np.sign(v[bad])) | unsat), (s, k)
@@ -202,7 +204,8 @@ def test_precision_sweep_100_batches():
             v = rows[name]["grad_" + grp]
             b = int(np.argmax(v))
             print(f"worst {grp}-group gradient, {name}: batch {b}, {worst_name.get((name, grp, b))}, {v[b]:.3e}")
-    print(f"FP32: {flips['adam']} critic parameters took the other sign of Adam's first step; "
+    print(f"FP32: {flips['adam']} critic parameters took the other sign of Adam's first step (largest "
+          f"|g| there {flips['adam_ratio']:.2e} of its tensor's norm); "
           f"{flips['relu']} encoder ReLU decisions differ, in {flips['batches_relu']} of {N_BATCHES} batches")
     for name, bounds in (("fp32", FP32), ("bf16", BF16), ("fp8", FP8), ("mxfp8", MXFP8)):
         for key, tol in bounds.items():
