@@ -379,7 +379,7 @@ def run_ours(args):
         if name == "tc_gemm_fwd" and args.precision in ("fp8", "mxfp8"):   # e4m3 operands: FP8 peak
             return {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": 2.0 * peaks["bf16_tflops"],
                     "peak_source": f"{peaks_src} bf16 burst x 2 (nominal fp8/bf16 dense ratio 4.5/2.25)"}
-        if name.startswith("tc_") or name.startswith("conv_tc"):
+        if name.startswith(("tc_", "conv_tc", "mlp_tc")):
             return {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach, "peak": peaks["bf16_tflops"],
                     "peak_source": f"{peaks_src} bf16 burst (kernel timed alone)"}
         return {"bound": "alu", "unit": "TFLOP/s", "achieved": ach, "peak": fp32_peak,

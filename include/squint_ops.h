@@ -39,6 +39,31 @@ int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, 
 
 
 /*
+ * A whole LayerNorm MLP head in one BF16 tensor-core launch (the critic and actor MLPs,
+ * Sec. IV "Normalization": nh hidden layers Linear -> LayerNorm -> ReLU, then a plain
+ * Linear output layer; Alg. 1 evaluates them in every step of the update):
+ *   h_0 = x;  pre_l = h_l W_l^T + bias_l;  h_{l+1} = ReLU(LN(pre_l) g_l + beta_l)  (l < nh)
+ *   out = h_nh W_nh^T + bias_nh
+ * x BF16 [M, kin] (row stride ldx >= kin, a multiple of 8, 16-byte aligned); w[l] BF16
+ * [out_l, in_l] row-major with row stride ldw[l] (in_0 = kin, out_l = in_{l+1} = H,
+ * out_nh = nout; strides multiples of 8); bias[l], g[l], beta[l] FP32.  Every hidden
+ * layer's output is rounded to BF16 before the next layer reads it; accumulation and
+ * LayerNorm statistics are FP32 (rstd = 1 / sqrt(var + eps), var the mean square
+ * deviation).  out FP32 [M, nout] (row stride ldo).  Optional per hidden layer (arrays
+ * of nh pointers, or NULL arrays / NULL entries): pre FP32 [M, H], post FP32 [M, H],
+ * post_bf BF16 [M, H], mean and rstd [M].  Shapes: 1 <= nh <= 3, H a multiple of 32 up
+ * to 1024, nout <= 256, kin <= 1024 (SQUINT_EINVAL outside).  cluster = 0 picks the
+ * number of CTAs that share a 128-row block (each computing H / cluster columns); 1, 2
+ * or 4 forces it when the shape allows.  Each row's result does not depend on the other
+ * rows of the call.
+ */
+int squint_op_mlp_bf16(int M, int kin, int nh, int H, int nout, const void* x, int64_t ldx, const void* const* w,
+                       const int64_t* ldw, const float* const* bias, const float* const* g,
+                       const float* const* beta, float eps, float* out, int64_t ldo, float* const* pre,
+                       float* const* post, void* const* post_bf, float* const* mean, float* const* rstd, int cluster,
+                       void* stream);
+
+/*
  * BF16 linear layer with its LayerNorm in one kernel (the hidden layers of the critic and
  * actor MLPs, Sec. IV "Normalization"): pre = A B^T + bias (A [M, K], B [N, K] BF16,
  * row-major, row strides lda, ldb >= K, multiples of 8), then per row

@@ -4,6 +4,7 @@
 #include "squint.h"
 #include "sq_kernels.cuh"
 #include "sq_tc.cuh"
+#include "sq_mlp_tc.cuh"
 
 #include <atomic>
 #include <condition_variable>
@@ -87,6 +88,11 @@ struct squint_handle {
     // in a call of k updates, each update's minibatch drawn (front end) while the previous
     // update runs; SQUINT_DRAW_AHEAD=0 at creation draws every one in line instead
     bool draw_ahead = true;
+    // head MLP chains of the BF16 learner as one fused tensor-core launch each
+    // (SQUINT_MLP_FUSED=0 at creation: a GEMM and a LayerNorm launch per layer instead);
+    // SQUINT_MLP_CL=1/2/4 forces the cluster size of the fused launches
+    bool mlp_fused = true;
+    int mlp_cluster = 0;
     bool launch_failed = false;       // a tensor map could not describe an operand
     // bounded waits of the update's tensor-core GEMMs (cycles 0: the default limit) and
     // the failure-test switch that makes them run out (squint_set_debug)

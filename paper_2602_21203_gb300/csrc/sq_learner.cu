@@ -218,8 +218,42 @@ MlpRef mlp_ref(squint_handle* h, const std::vector<Lin>& layers, bool target, co
 }
 
 void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const Mat& X, int rows, bool bf16,
-                 cudaStream_t s, bool split) {
+                 cudaStream_t s, bool split, bool keep) {
     const int nh = (int)sets[0].size() - 1;
+    if (bf16 && !h->fp8 && h->mlp_fused && X.h && rows > 0 && E <= kMlpMaxProbs) {
+        // the whole chain in one launch: hidden activations stay on chip between layers
+        const int H = sets[0][0].out, nout = sets[0][nh].out, kin = sets[0][0].in;
+        bool ok = mlp_tc_supported(nh, H, nout, kin);
+        for (int l = 0; l < nh; ++l) ok = ok && sets[0][l].out == H;
+        for (int e = 0; e < E && ok; ++e)
+            for (int l = 0; l <= nh; ++l) ok = ok && sets[e][l].wh;
+        if (ok) {
+            MlpTcProblem pr[kMlpMaxProbs];
+            double flops = 0;
+            for (int e = 0; e < E; ++e) {
+                MlpTcProblem& q = pr[e];
+                std::memset(&q, 0, sizeof(q));
+                q.M = rows; q.x = X.h; q.ldx = X.ldh; q.kin = kin;
+                for (int l = 0; l <= nh; ++l) {
+                    const LayerRef& ly = sets[e][l];
+                    q.w[l] = ly.wh; q.ldw[l] = ly.ldh; q.bias[l] = ly.b;
+                    flops += 2.0 * rows * ly.in * ly.out;
+                    if (l == nh) break;
+                    q.g[l] = ly.g; q.beta[l] = ly.beta;
+                    if (keep) {
+                        const int64_t off = (int64_t)e * rows * H;
+                        q.save[l] = MlpTcSave{mb.pre[l] + off, mb.post[l] + off,
+                                              mb.posth.empty() ? nullptr : mb.posth[l] + off,
+                                              mb.mean[l] + (int64_t)e * rows, mb.rstd[l] + (int64_t)e * rows};
+                    }
+                }
+                q.out = mb.out + (int64_t)e * rows * nout; q.ldo = nout;
+            }
+            ProfScope ps(h, s, "mlp_tc_fwd", flops, 0);
+            if (launch_mlp_tc(pr, E, nh, H, nout, (float)h->c.ln_eps, h->d_err, &h->gemm_wait, s, h->mlp_cluster) == 0)
+                return;
+        }
+    }
     for (int l = 0; l <= nh; ++l) {
         // the hidden layers' LayerNorm (+ReLU) problems; on the tensor-core path the GEMM
         // computes them in its epilogue
@@ -392,6 +426,8 @@ int squint_handle::allocate() {
     if (const char* e = std::getenv("SQUINT_FUSED_LN")) fuse_ln = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_GEMM_SPLIT")) gemm_split = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_DRAW_AHEAD")) draw_ahead = std::atoi(e) != 0;
+    if (const char* e = std::getenv("SQUINT_MLP_FUSED")) mlp_fused = std::atoi(e) != 0;
+    if (const char* e = std::getenv("SQUINT_MLP_CL")) mlp_cluster = std::atoi(e);
     bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
     SQ_CK(this, cudaGetDevice(&device));
     const int64_t n = L.total;
@@ -659,6 +695,7 @@ int squint_handle::allocate() {
         }
         if (tc_conv) policy_wconv_scratch = dalloc<__nv_bfloat16>(9 * 32 * 32);
         tc_prepare();
+        mlp_tc_prepare();
     }
     if (cudaMallocHost(&h_stats, sizeof(float) * 8 * c.max_k) != cudaSuccess) return SQUINT_ENOMEM;
     SQ_CK(this, cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
@@ -970,7 +1007,7 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
     mark(s);
     // ---- a8-a9: target critics and the projected categorical target
     {
-        mlp_forward(this, tcrit_mlp, crit_tg, E, Mat{xcbar, Dc, xcbar_h, Dc8}, B, bf16, s);
+        mlp_forward(this, tcrit_mlp, crit_tg, E, Mat{xcbar, Dc, xcbar_h, Dc8}, B, bf16, s, true, false);
         C51TargetArgs ct{};
         ct.B = B; ct.K = K; ct.E = E;
         ct.logits_bar = tcrit_mlp.out; ct.r = r; ct.d = d; ct.logp_next = logp;

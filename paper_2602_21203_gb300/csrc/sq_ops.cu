@@ -3,7 +3,9 @@
 #include "squint_ops.h"
 #include "sq_kernels.cuh"
 #include "sq_tc.cuh"
+#include "sq_mlp_tc.cuh"
 
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -24,6 +26,7 @@ int* tc_error_flag() {
         if (cudaMalloc(&flag, sizeof(int)) == cudaSuccess) cudaMemset(flag, 0, sizeof(int));
         tc_prepare();
         conv_tc_prepare();
+        mlp_tc_prepare();
     });
     return flag;
 }
@@ -108,6 +111,43 @@ int squint_op_gemm_layernorm(int M, int N, int K, const void* A, int64_t lda, co
     int* err = tc_error_flag();
     if (!err) return SQUINT_ECUDA;
     if (launch_tc_gemm(&gm, 1, err, (cudaStream_t)stream) != 0) return SQUINT_EINVAL;
+    return launch_status();
+}
+
+int squint_op_mlp_bf16(int M, int kin, int nh, int H, int nout, const void* x, int64_t ldx, const void* const* w,
+                       const int64_t* ldw, const float* const* bias, const float* const* g,
+                       const float* const* beta, float eps, float* out, int64_t ldo, float* const* pre,
+                       float* const* post, void* const* post_bf, float* const* mean, float* const* rstd, int cluster,
+                       void* stream) {
+    if (M < 0 || kin < 1 || nh < 1 || nh > kMlpMaxHidden || H < 1 || nout < 1 || !x || !w || !ldw || !bias || !g ||
+        !beta || !out || ldo < nout || ldx < kin || (cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4))
+        return SQUINT_EINVAL;
+    if (!mlp_tc_supported(nh, H, nout, kin) || (cluster && !mlp_tc_cluster(H, nout, cluster))) {
+        g_last_error = "fused MLP: shape outside the kernel's range (or cluster size not possible for it)";
+        return SQUINT_EINVAL;
+    }
+    if (M == 0) return SQUINT_OK;
+    MlpTcProblem p;
+    std::memset(&p, 0, sizeof(p));
+    p.M = M; p.x = (const __nv_bfloat16*)x; p.ldx = ldx; p.kin = kin;
+    for (int l = 0; l <= nh; ++l) {
+        if (!w[l] || !bias[l]) return SQUINT_EINVAL;
+        p.w[l] = (const __nv_bfloat16*)w[l]; p.ldw[l] = ldw[l]; p.bias[l] = bias[l];
+        if (l == nh) break;
+        if (!g[l] || !beta[l]) return SQUINT_EINVAL;
+        p.g[l] = g[l]; p.beta[l] = beta[l];
+        p.save[l] = MlpTcSave{pre ? pre[l] : nullptr, post ? post[l] : nullptr,
+                              post_bf ? (__nv_bfloat16*)post_bf[l] : nullptr, mean ? mean[l] : nullptr,
+                              rstd ? rstd[l] : nullptr};
+    }
+    p.out = out; p.ldo = ldo;
+    int* err = tc_error_flag();
+    if (!err) return SQUINT_ECUDA;
+    const int rc = launch_mlp_tc(&p, 1, nh, H, nout, eps, err, nullptr, (cudaStream_t)stream, cluster);
+    if (rc != 0) {
+        g_last_error = "fused MLP: an operand cannot be described by a tensor map (alignment, extents)";
+        return SQUINT_EINVAL;
+    }
     return launch_status();
 }
 

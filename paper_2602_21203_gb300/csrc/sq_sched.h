@@ -96,8 +96,12 @@ struct ProfScope {
 
 // Forward of E parameter sets of one MLP shape on `rows` rows of X (split = false: no
 // K split in the tensor-core GEMMs, so each row's result is independent of the others).
+// On the BF16 path the whole chain is one fused launch when its shape allows (each row's
+// result is independent of the other rows there too).
+// keep = false: only the output is needed (no backward through this evaluation), so the
+// hidden layers' activations need not be saved.
 void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const Mat& X, int rows, bool bf16,
-                 cudaStream_t s, bool split = true);
+                 cudaStream_t s, bool split = true, bool keep = true);
 // Layer view of canonical layer `ly` in the online parameters (base == params), the
 // target copy (target == true) or an inference snapshot (base == a policy buffer; its
 // BF16 weight copy, if any, is filled in by the caller).

@@ -317,7 +317,7 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
     }
     MlpRef actor_ref;
     for (const auto& ly : L.actor) actor_ref.push_back(bf_ref(ly));
-    mlp_forward(this, act_mlp, &actor_ref, 1, Mat{axin, Da, axin_h, Da8}, rows, bf16, s, false);
+    mlp_forward(this, act_mlp, &actor_ref, 1, Mat{axin, Da, axin_h, Da8}, rows, bf16, s, false, false);
     ActHeadArgs ha{};
     ha.rows = rows; ha.A = A; ha.out = act_mlp.out; ha.ld_out = 2 * A;
     ha.row_req = d_row_req; ha.row_in_req = d_row_in;

@@ -104,6 +104,7 @@ def load():
         "squint_op_relu_bwd": (I, [I, I64, P, P, P, P]),
         "squint_op_squint_store": (I, [I, I, I, I, I, P, P, I64, I64, P]),
         "squint_op_gemm_fp8_workspace": (SZ, [I, I, I]),
+        "squint_op_mlp_bf16": (I, [I, I, I, I, I, P, I64, P, P, P, P, P, ctypes.c_float, P, I64, P, P, P, P, P, I, P]),
         "squint_op_gemm_layernorm": (I, [I, I, I, P, I64, P, I64, P, P, P, ctypes.c_float, I, P, P, P, P, P, P]),
         "squint_op_gemm_fp8": (I, [I, I, I, P, I64, P, I64, P, I64, P, P, SZ, P]),
         "squint_op_mx_scale_bytes": (I64, [I, I]),

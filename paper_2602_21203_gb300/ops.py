@@ -81,6 +81,39 @@ def gemm_layernorm(A, B, bias, g, beta, eps=1e-5, relu=True):
     return pre, post, post_bf, mean, rstd
 
 
+def mlp_bf16(x, ws, biases, gs, betas, eps=1e-5, save=True, cluster=0):
+    """A LayerNorm MLP head in one launch: hidden layers Linear -> LayerNorm -> ReLU
+    (weights ws[l] BF16 [out, in], biases FP32), then a plain Linear output layer.
+    x BF16 [M, kin].  Returns (out [M, nout], saved) with saved = per hidden layer
+    (pre, post, post_bf16, mean, rstd) if save, else None."""
+    _need(x, torch.bfloat16, "x")
+    nh = len(ws) - 1
+    M, kin = x.shape
+    H, nout = ws[0].shape[0], ws[-1].shape[0]
+    dev = x.device
+    for w in ws:
+        _need(w, torch.bfloat16, "w")
+    out = torch.empty(M, nout, device=dev)
+
+    def arr(ctype, vals):
+        return (ctype * len(vals))(*vals)
+
+    P = ctypes.c_void_p
+    saved = None
+    pre = post = pbf = mean = rstd = None
+    if save:
+        saved = [(torch.empty(M, H, device=dev), torch.empty(M, H, device=dev),
+                  torch.empty(M, H, device=dev, dtype=torch.bfloat16), torch.empty(M, device=dev),
+                  torch.empty(M, device=dev)) for _ in range(nh)]
+        pre, post, pbf, mean, rstd = (arr(P, [t[i].data_ptr() for t in saved]) for i in range(5))
+    _chk(_lib.load().squint_op_mlp_bf16(M, kin, nh, H, nout, _p(x), x.stride(0), arr(P, [w.data_ptr() for w in ws]),
+                                        arr(ctypes.c_int64, [w.stride(0) for w in ws]),
+                                        arr(P, [b.data_ptr() for b in biases]), arr(P, [g.data_ptr() for g in gs]),
+                                        arr(P, [b.data_ptr() for b in betas]), float(eps), _p(out), out.stride(0),
+                                        pre, post, pbf, mean, rstd, int(cluster), _s()), "squint_op_mlp_bf16")
+    return out, saved
+
+
 def gemm_fp8(A, B, bias=None, out=None):
     """out = scale_A scale_B e4m3(A / scale_A) e4m3(B / scale_B)^T + bias for BF16 A [M, K], B [N, K]
     (row-major, unit column stride); per-tensor scales amax / 448.  Returns (out, (scale_A, scale_B))."""
