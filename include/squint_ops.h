@@ -53,8 +53,8 @@ int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, 
  * of nh pointers, or NULL arrays / NULL entries): pre FP32 [M, H], post FP32 [M, H],
  * post_bf BF16 [M, H], mean and rstd [M].  Shapes: 1 <= nh <= 3, H a multiple of 32 up
  * to 1024, nout <= 256, kin <= 1024 (SQUINT_EINVAL outside).  cluster = 0 picks the
- * number of CTAs that share a 128-row block (each computing H / cluster columns); 1, 2
- * or 4 forces it when the shape allows.  Each row's result does not depend on the other
+ * number of CTAs that share a 128-row block (each computing H / cluster columns); 1, 2,
+ * 4 or 8 forces it when the shape allows.  Each row's result does not depend on the other
  * rows of the call.
  */
 int squint_op_mlp_bf16(int M, int kin, int nh, int H, int nout, const void* x, int64_t ldx, const void* const* w,

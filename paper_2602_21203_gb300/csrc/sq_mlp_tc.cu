@@ -13,18 +13,21 @@
 //   warp 0 / lane 0   MMA issuer: tcgen05.mma M = 128, N = NS (K = 16 per step) from
 //                     the activation region and the ring into tensor memory
 //   warps 0-3         epilogue, one thread per row: bias, LayerNorm statistics over the
-//                     whole row (partial sums of the CL CTAs exchanged through
-//                     distributed shared memory, added in rank order), ReLU; the BF16
-//                     result is written straight into the activation region of every
-//                     CTA of the cluster as the next layer's A operand; saved FP32
+//                     whole row (each CTA's mean and centred sum of squares of its slice,
+//                     sent to every CTA of the cluster with st.async and combined in rank
+//                     order), ReLU; the BF16 result is written into this CTA's activation
+//                     region as the next layer's A operand and copied to the other CTAs of
+//                     the cluster with one shared-to-shared bulk copy each; saved FP32
 //                     activations leave through a per-warp transpose as coalesced rows,
 //                     the BF16 copy by a TMA store of the CTA's own slabs
 //   output layer      K split over the cluster (each CTA multiplies its own column slice
-//                     of the last hidden layer); the partial tiles are pushed to the CTA
-//                     owning each band of rows and added in rank order
+//                     of the last hidden layer); the partial tile is staged in the idle
+//                     weight ring, each band of rows bulk-copied to the CTA that finishes
+//                     it, and the partials added in rank order
 //
-// Cross-CTA ordering uses mbarriers with remote arrivals (release / acquire at cluster
-// scope), so the producer never joins a cluster-wide barrier while it streams ahead.
+// Data that crosses CTAs travels by st.async and bulk copies that complete transaction
+// bytes on the receiver's mbarrier, so no cluster-scope fence or cluster-wide barrier is
+// needed between the layers, and the producer streams ahead undisturbed.
 // Every wait is bounded; past the limit the waiting thread records a code in *err and
 // gives up, the CTA waits (bounded) for its copies in flight, frees its tensor memory and
 // returns.
@@ -47,10 +50,8 @@ constexpr int SLAB_BYTES = BM * 128;      // one activation slab: 128 rows x 128
 constexpr int kThreads = 160;
 constexpr int STG_LD = 36;                // staging row stride (floats)
 constexpr int STG_BYTES = 4 * 32 * STG_LD * 4;
-constexpr int XBUF_BYTES = 2 * 4 * BM * 4;
 constexpr int SMEM_LIMIT = 232448;
 constexpr long long kWaitDefault = 4000000000ll;   // ~2 s at 2 GHz
-constexpr int kMaxCluster = 4;
 
 struct MlpProbDev {
     CUtensorMap tx;                           // X [M, kin], box 64 x 128
@@ -70,7 +71,8 @@ struct MlpProbDev {
 struct MlpArgs {
     MlpProbDev p[kMlpMaxProbs];
     int n_probs, nh, H, CL, NS, nout, nop;
-    int stages, stage_bytes, a_bytes;
+    int stages, stage_bytes, a_bytes, par_floats;
+    int ldr;          // row stride (floats) of the output tile staging: nop, padded when it fits
     uint32_t tmem_cols;
     float eps;
     int* err;
@@ -86,11 +88,6 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 }
 __device__ __forceinline__ void mbar_arrive_local(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-// Arrive on the barrier at a shared::cluster address (this CTA's or a peer's), releasing
-// this thread's earlier writes at cluster scope.
-__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 template <bool CLUSTER>
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
@@ -149,18 +146,22 @@ __device__ __forceinline__ uint32_t mapa(uint32_t addr, uint32_t rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
     return r;
 }
-__device__ __forceinline__ void st_cluster_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
-                 : "memory");
-}
-__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
-    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
-}
-__device__ __forceinline__ void st_cluster_v4f(uint32_t addr, float a, float b, float c, float d) {
-    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
-                 : "memory");
-}
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Two floats into shared memory of a cluster CTA, completing 8 bytes of transaction count
+// on the barrier `bar` (a shared::cluster address in that CTA).
+__device__ __forceinline__ void st_async_v2(uint32_t addr, float x, float y, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(addr),
+                 "f"(x), "f"(y), "r"(bar)
+                 : "memory");
+}
+// Bulk copy of `bytes` (a multiple of 16) from this CTA's shared memory to a cluster CTA's,
+// completing that many bytes of transaction count on its barrier.
+__device__ __forceinline__ void bulk_s2s(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst),
+                 "r"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
     d |= (uint64_t)(16 >> 4) << 16;
@@ -208,6 +209,21 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
+// 32 consecutive floats of shared memory (16-byte aligned, the same for every thread).
+__device__ __forceinline__ void ld_par32(const float* p, float (&v)[32]) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(p + j);
+        v[j] = x.x; v[j + 1] = x.y; v[j + 2] = x.z; v[j + 3] = x.w;
+    }
+}
+// The first n (<= 4, or none if n <= 0) of four consecutive outputs.
+__device__ __forceinline__ void store_out4(float* dst, float4 v, int n) {
+    if (n > 0) dst[0] = v.x;
+    if (n > 1) dst[1] = v.y;
+    if (n > 2) dst[2] = v.z;
+    if (n > 3) dst[3] = v.w;
+}
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
@@ -235,11 +251,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int S = a.stages;
+    const int CL = a.CL, NS = a.NS, H = a.H, nh = a.nh;
     const uint32_t a_base = smem_u32(smem);
     const uint32_t ring = a_base + a.a_bytes;
+    float* ring_f = reinterpret_cast<float*>(smem + a.a_bytes);
     float* stg = reinterpret_cast<float*>(smem + a.a_bytes + S * a.stage_bytes);
-    float* xbuf = stg + 4 * 32 * STG_LD;                                 // [2][kMaxCluster][BM]
-    uint64_t* bars = reinterpret_cast<uint64_t*>(xbuf + 2 * kMaxCluster * BM);
+    float* xbuf = stg + 4 * 32 * STG_LD;                                 // [2][CL][BM][2]: (mean, M2) of each CTA
+    float* par = xbuf + 2 * CL * BM * 2;                                 // bias, g, beta slices; output bias
+    uint64_t* bars = reinterpret_cast<uint64_t*>(par + a.par_floats);
     uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 6);     // tmem address, issued, consumed
     const uint32_t bar0 = smem_u32(bars);
     auto full = [&](int s) { return bar0 + 8 * s; };
@@ -250,7 +269,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
     int pi = 0;
     while (pi + 1 < a.n_probs && (int)blockIdx.x >= a.p[pi + 1].cta0) ++pi;
     const MlpProbDev& P = a.p[pi];
-    const int CL = a.CL, NS = a.NS, H = a.H, nh = a.nh;
     const int rank = CL > 1 ? (int)cluster_rank() : 0;
     const int m0 = ((int)blockIdx.x - P.cta0) / CL * BM;
     const int M = P.M;
@@ -258,6 +276,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
     const long long wlim = a.wait_limit;
     int* err = a.err;
     const int hslabs = (H + SLAB - 1) / SLAB;
+    const int nop = a.nop, ldr = a.ldr;             // row stride of the output staging (floats)
+    const int band = BM / CL;                       // rows of the output each CTA finishes
     auto nk = [&](int l) { return l == 0 ? P.nk0 : (l < nh ? hslabs : (CL > 1 ? NS / SLAB : hslabs)); };
 
     if (threadIdx.x == 0) {
@@ -267,13 +287,20 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
         }
         mbar_init(x_full, 1);
         mbar_init(acc_full, 1);
-        mbar_init(a_ready, CL);
-        mbar_init(xbar0, CL);
-        mbar_init(xbar0 + 8, CL);
-        mbar_init(out_bar, CL);
+        mbar_init(a_ready, 1);
+        mbar_init(xbar0, 1);
+        mbar_init(xbar0 + 8, 1);
+        mbar_init(out_bar, 1);
         slot[1] = 0;
         slot[2] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (CL > 1) {
+            // the bytes the cluster's CTAs send this one: row statistics (each exchange) and
+            // the output partials of its band of rows
+            mbar_expect_tx(xbar0, (uint32_t)(CL * BM * 8));
+            mbar_expect_tx(xbar0 + 8, (uint32_t)(CL * BM * 8));
+            mbar_expect_tx(out_bar, (uint32_t)(CL * band * ldr * 4));
+        }
     }
     if (threadIdx.x == 128) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.tx)) : "memory");
@@ -304,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
             bool ok = true;
             for (int l = 0; l <= nh && ok; ++l) {
                 const bool last = l == nh;
-                const uint32_t bytes = (uint32_t)((last ? a.nop : NS) * 128);
+                const uint32_t bytes = (uint32_t)((last ? nop : NS) * 128);
                 const int row0 = last ? 0 : rank * NS;
                 const int kcol0 = (last && CL > 1) ? rank * NS : 0;
                 for (int kb = 0; kb < nk(l); ++kb, ++it) {
@@ -319,27 +346,24 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
     } else {
         const int r = warp * 32 + lane;                 // row of the block = tensor-memory lane
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        // this CTA's slices of the bias, LayerNorm gain and shift of every hidden layer, and
+        // the output bias, staged by warps 1-3 while the first layer's operands arrive (the
+        // first epilogue's barrier orders them before any use)
+        if (warp > 0) {
+            for (int i = threadIdx.x - 32; i < nh * 3 * NS; i += 96) {
+                const int l = i / (3 * NS), k = (i % (3 * NS)) / NS, j = i % NS;
+                const float* src = k == 0 ? P.bias[l] : (k == 1 ? P.g[l] : P.beta[l]);
+                par[i] = src[rank * NS + j];
+            }
+            for (int j = threadIdx.x - 32; j < nop; j += 96) par[nh * 3 * NS + j] = j < a.nout ? P.bias[nh][j] : 0.f;
+        }
+        // the problem's output pointers, read once: P is reached through a generic pointer
+        // into the parameter block, which the compiler would re-read after every store
+        float* const p_out = P.out;
+        const int64_t p_ldo = P.ldo;
         float* stg_w = stg + warp * 32 * STG_LD;
         int it = 0;                                      // weight slab sequence (issuer)
         bool dead = false;                               // the issuer gave up on a wait
-        int xph = 0;                                     // exchange phase
-        // Sum of v over the CTAs of the cluster, in rank order (every thread: its own row).
-        auto exchange = [&](float v) -> float {
-            if (CL == 1) return v;
-            const int b = xph & 1;
-            float* buf = xbuf + b * kMaxCluster * BM;
-            const uint32_t mine = smem_u32(buf + rank * BM + r);
-            for (int q = 0; q < CL; ++q) st_cluster_f32(mapa(mine, q), v);
-            asm volatile("fence.acq_rel.cluster;" ::: "memory");
-            epi_bar();
-            if (threadIdx.x == 0)
-                for (int q = 0; q < CL; ++q) mbar_arrive_cluster(mapa(xbar0 + 8 * b, q));
-            mbar_wait<true>(xbar0 + 8 * b, (xph >> 1) & 1, err, 35, wlim);
-            ++xph;
-            float t = 0.f;
-            for (int q = 0; q < CL; ++q) t += buf[q * BM + r];
-            return t;
-        };
         for (int l = 0; l <= nh; ++l) {
             const bool last = l == nh;
             // ---------------------------------------------------------------- MMA issue
@@ -349,7 +373,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
                     else dead = !mbar_wait<true>(a_ready, (l - 1) & 1, err, 32, wlim);
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t idesc = idesc_bf16_kk(BM, last ? a.nop : NS);
+                const uint32_t idesc = idesc_bf16_kk(BM, last ? nop : NS);
                 const int nkl = nk(l);
                 for (int kb = 0; kb < nkl && !dead; ++kb) {
                     const int s = it % S;
@@ -368,33 +392,66 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
             __syncwarp();
             mbar_wait(acc_full, l & 1, err, 34, wlim);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (l == 0) epi_bar();   // the staged parameter slices
             if (!last) {
                 // ------------------------------------------------------------ hidden layer epilogue
                 const int c0 = rank * NS;                 // this CTA's first column
-                const float* bias = P.bias[l] + c0;
-                const float* gg = P.g[l] + c0;
-                const float* bb = P.beta[l] + c0;
+                const float* pb = par + l * 3 * NS;       // bias, gain, shift of the slice
+                const float* pg = pb + NS;
+                const float* pbeta = pb + 2 * NS;
+                float* const s_pre = P.pre[l];
+                float* const s_post = P.post[l];
+                float* const s_mean = P.mean[l];
+                float* const s_rstd = P.rstd[l];
+                const bool s_ph = P.has_ph[l] != 0;
+                // statistics of this CTA's NS columns of the row: mean, then centred squares
                 float s1 = 0.f;
                 for (int c = 0; c < NS; c += 32) {
-                    float v[32];
+                    float v[32], b[32];
                     tmem_ld32(trow + c, v);
+                    ld_par32(pb + c, b);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) s1 += v[j] + __ldg(bias + c + j);
+                    for (int j = 0; j < 32; ++j) s1 += v[j] + b[j];
                 }
-                const float mean = exchange(s1) / (float)H;
-                float s2 = 0.f;
+                const float mq = s1 / (float)NS;
+                float m2 = 0.f;
                 for (int c = 0; c < NS; c += 32) {
-                    float v[32];
+                    float v[32], b[32];
                     tmem_ld32(trow + c, v);
+                    ld_par32(pb + c, b);
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const float d = v[j] + __ldg(bias + c + j) - mean;
-                        s2 += d * d;
+                        const float d = v[j] + b[j] - mq;
+                        m2 += d * d;
                     }
                 }
+                // the whole row's statistics: every CTA sends (mean, M2) of its slice to every
+                // CTA of the cluster; they are combined in rank order (Chan et al.'s pairwise
+                // update for equal counts: M2 = sum M2_q + NS sum (mean_q - mean)^2)
+                float mean = mq, var = m2 / (float)H;
+                if (CL > 1) {
+                    const int b = l & 1;
+                    float* buf = xbuf + b * CL * BM * 2;
+                    const uint32_t mine = smem_u32(buf + (rank * BM + r) * 2), xb = xbar0 + 8 * b;
+                    for (int q = 0; q < CL; ++q) st_async_v2(mapa(mine, q), mq, m2, mapa(xb, q));
+                    mbar_wait<true>(xb, (l >> 1) & 1, err, 35, wlim);
+                    // armed again for its next use (every CTA's sends of that use follow this
+                    // CTA's sends of the next exchange, which follow all of its reads here)
+                    if (threadIdx.x == 0) mbar_expect_tx(xb, (uint32_t)(CL * BM * 8));
+                    float ms = 0.f;
+                    for (int q = 0; q < CL; ++q) ms += buf[(q * BM + r) * 2];
+                    mean = ms / (float)CL;
+                    float M2 = 0.f;
+                    for (int q = 0; q < CL; ++q) {
+                        const float d = buf[(q * BM + r) * 2] - mean;
+                        M2 += buf[(q * BM + r) * 2 + 1] + (float)NS * d * d;
+                    }
+                    var = M2 / (float)H;
+                }
+                const float rstd = 1.0f / sqrtf(var + a.eps);
                 // the previous layer's TMA store has read this CTA's slabs before they are rewritten
                 if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                const float rstd = 1.0f / sqrtf(exchange(s2) / (float)H + a.eps);
+                epi_bar();
                 // the last hidden layer feeds only this CTA's K slice of the output layer:
                 // kept locally, at the start of the activation region
                 const bool bcast = CL > 1 && l + 1 < nh;
@@ -402,89 +459,105 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
                 for (int c = 0; c < NS; c += 32) {
                     float v[32], y[32];
                     tmem_ld32(trow + c, v);
+                    ld_par32(pb + c, y);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        v[j] += __ldg(bias + c + j);
-                        y[j] = fmaxf((v[j] - mean) * rstd * __ldg(gg + c + j) + __ldg(bb + c + j), 0.f);
+                    for (int j = 0; j < 32; ++j) v[j] += y[j];
+                    ld_par32(pg + c, y);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) y[j] *= (v[j] - mean) * rstd;
+                    {
+                        float bt[32];
+                        ld_par32(pbeta + c, bt);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) y[j] = fmaxf(y[j] + bt[j], 0.f);
                     }
-                    if (P.pre[l]) store_rows_coalesced(stg_w, v, P.pre[l], H, m0 + warp * 32, M, c0 + c, lane);
-                    if (P.post[l]) store_rows_coalesced(stg_w, y, P.post[l], H, m0 + warp * 32, M, c0 + c, lane);
+                    if (s_pre) store_rows_coalesced(stg_w, v, s_pre, H, m0 + warp * 32, M, c0 + c, lane);
+                    if (s_post) store_rows_coalesced(stg_w, y, s_post, H, m0 + warp * 32, M, c0 + c, lane);
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int k = kpos0 + c + 8 * u;
-                        const uint32_t addr = a_base + (k / SLAB) * SLAB_BYTES + r * 128 + ((((k % SLAB) / 8) ^ (r & 7)) * 16);
-                        const uint32_t w0 = pack_bf16(y[8 * u], y[8 * u + 1]), w1 = pack_bf16(y[8 * u + 2], y[8 * u + 3]);
-                        const uint32_t w2 = pack_bf16(y[8 * u + 4], y[8 * u + 5]), w3 = pack_bf16(y[8 * u + 6], y[8 * u + 7]);
-                        if (bcast)
-                            for (int q = 0; q < CL; ++q) st_cluster_v4(mapa(addr, q), w0, w1, w2, w3);
-                        else
-                            st_cluster_v4(addr, w0, w1, w2, w3);
+                        uint4 w;
+                        w.x = pack_bf16(y[8 * u], y[8 * u + 1]);
+                        w.y = pack_bf16(y[8 * u + 2], y[8 * u + 3]);
+                        w.z = pack_bf16(y[8 * u + 4], y[8 * u + 5]);
+                        w.w = pack_bf16(y[8 * u + 6], y[8 * u + 7]);
+                        *reinterpret_cast<uint4*>(smem + (k / SLAB) * SLAB_BYTES + r * 128 +
+                                                  ((((k % SLAB) / 8) ^ (r & 7)) * 16)) = w;
                     }
                 }
                 if (H % SLAB)   // the K padding of the last slab reads as zero in the next layer
-                    for (int k = H; k < hslabs * SLAB; k += 8) {
-                        const uint32_t addr = a_base + (k / SLAB) * SLAB_BYTES + r * 128 + ((((k % SLAB) / 8) ^ (r & 7)) * 16);
-                        st_cluster_v4(addr, 0u, 0u, 0u, 0u);
-                    }
+                    for (int k = H; k < hslabs * SLAB; k += 8)
+                        *reinterpret_cast<uint4*>(smem + (k / SLAB) * SLAB_BYTES + r * 128 +
+                                                  ((((k % SLAB) / 8) ^ (r & 7)) * 16)) = make_uint4(0u, 0u, 0u, 0u);
                 if (rank == 0 && m0 + r < M) {
-                    if (P.mean[l]) P.mean[l][m0 + r] = mean;
-                    if (P.rstd[l]) P.rstd[l][m0 + r] = rstd;
+                    if (s_mean) s_mean[m0 + r] = mean;
+                    if (s_rstd) s_rstd[m0 + r] = rstd;
                 }
-                // generic-proxy writes of the activation region before the async proxy (MMA,
-                // TMA store) reads it; tensor-memory reads before the next layer's MMAs
-                asm volatile("fence.proxy.async;" ::: "memory");
-                asm volatile("fence.acq_rel.cluster;" ::: "memory");
+                // the activation writes before the async proxy (MMA, TMA store, bulk copies)
+                // reads them; tensor-memory reads before the next layer's MMAs
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 epi_bar();
                 if (threadIdx.x == 0) {
-                    if (P.has_ph[l]) {
+                    if (s_ph) {
                         for (int j = 0; j < (NS + SLAB - 1) / SLAB; ++j)
                             tma_store_2d(&P.tph[l], a_base + (kpos0 / SLAB + j) * SLAB_BYTES, c0 + j * SLAB, m0);
                         asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                     }
-                    if (CL > 1)
-                        for (int q = 0; q < CL; ++q) mbar_arrive_cluster(mapa(a_ready, q));
-                    else
+                    if (bcast) {
+                        // this CTA's slice (whole slabs) into the same place of every other
+                        // CTA's activation region; each copy completes on the receiver's barrier
+                        const uint32_t src = a_base + (c0 / SLAB) * SLAB_BYTES, bytes = (uint32_t)NS * 256;
+                        for (int q = 0; q < CL; ++q)
+                            if (q != rank) bulk_s2s(mapa(src, q), src, bytes, mapa(a_ready, q));
+                        mbar_expect_tx(a_ready, (uint32_t)(CL - 1) * bytes);
+                    } else {
                         mbar_arrive_local(a_ready);
+                    }
                 }
             } else {
                 // ------------------------------------------------------------ output layer epilogue
-                const int nop = a.nop, nout = a.nout;
-                const float* bias = P.bias[nh];
-                if (CL == 1) {
-                    for (int c = 0; c < nop; c += 16) {
-                        float v[16];
-                        tmem_ld16(trow + c, v);
-                        if (m0 + r < M)
+                const int nout = a.nout;
+                const float* pob = par + nh * 3 * NS;
+                // this row's output (or partial output) into the idle weight ring, then coalesced
+                for (int c = 0; c < nop; c += 16) {
+                    float v[16];
+                    tmem_ld16(trow + c, v);
 #pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (c + j < nout) P.out[(int64_t)(m0 + r) * P.ldo + c + j] = v[j] + __ldg(bias + c + j);
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(ring_f + r * ldr + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                epi_bar();
+                // four consecutive columns a thread: element e of the band is (row, 4 c4)
+                const int nq = (nout + 3) / 4;
+                if (CL == 1) {
+                    for (int e = threadIdx.x; e < BM * nq; e += BM) {
+                        const int row = e / nq, col = 4 * (e % nq);
+                        const float4 x = *reinterpret_cast<const float4*>(ring_f + row * ldr + col);
+                        const float4 bo = *reinterpret_cast<const float4*>(pob + col);
+                        store_out4(p_out + (int64_t)(m0 + row) * p_ldo + col, make_float4(x.x + bo.x, x.y + bo.y,
+                                   x.z + bo.z, x.w + bo.w), m0 + row < M ? nout - col : 0);
                     }
                 } else {
-                    // push this row's partial to the CTA that owns its band of rows: slot
-                    // [rank][row in band] of that CTA's receive area (after its own K slice)
-                    const int band = BM / CL;
-                    const uint32_t recv = a_base + (uint32_t)NS * 256;
-                    const uint32_t dst = mapa(recv + (uint32_t)((rank * band + r % band) * nop) * 4, r / band);
-                    for (int c = 0; c < nop; c += 16) {
-                        float v[16];
-                        tmem_ld16(trow + c, v);
-#pragma unroll
-                        for (int j = 0; j < 16; j += 4) st_cluster_v4f(dst + (c + j) * 4, v[j], v[j + 1], v[j + 2], v[j + 3]);
-                    }
-                    asm volatile("fence.acq_rel.cluster;" ::: "memory");
-                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-                    epi_bar();
+                    // band q of the partial tile to CTA q (slot `rank` of its receive area,
+                    // after its own K slice); the K split's partials are added in rank order
+                    const uint32_t recv = a_base + (uint32_t)NS * 256, bb = (uint32_t)(band * ldr * 4);
                     if (threadIdx.x == 0)
-                        for (int q = 0; q < CL; ++q) mbar_arrive_cluster(mapa(out_bar, q));
+                        for (int q = 0; q < CL; ++q)
+                            bulk_s2s(mapa(recv + rank * bb, q), ring + q * bb, bb, mapa(out_bar, q));
                     mbar_wait<true>(out_bar, 0, err, 36, wlim);
                     const float* rv = reinterpret_cast<const float*>(smem + (size_t)NS * 256);
-                    for (int e = threadIdx.x; e < band * nout; e += BM) {
-                        const int row = e / nout, col = e % nout;
-                        float v = __ldg(bias + col);
-                        for (int q = 0; q < CL; ++q) v += rv[(q * band + row) * nop + col];
+                    for (int e = threadIdx.x; e < band * nq; e += BM) {
+                        const int row = e / nq, col = 4 * (e % nq);
+                        float4 v = *reinterpret_cast<const float4*>(pob + col);
+                        for (int q = 0; q < CL; ++q) {
+                            const float4 x = *reinterpret_cast<const float4*>(rv + (q * band + row) * ldr + col);
+                            v.x += x.x; v.y += x.y; v.z += x.z; v.w += x.w;
+                        }
                         const int grow = m0 + rank * band + row;
-                        if (grow < M) P.out[(int64_t)grow * P.ldo + col] = v;
+                        store_out4(p_out + (int64_t)grow * p_ldo + col, v, grow < M ? nout - col : 0);
                     }
                 }
             }
@@ -539,16 +612,30 @@ bool make_map(CUtensorMap* m, const void* ptr, int64_t inner, int64_t outer, int
 
 int round16(int n) { return (n + 15) / 16 * 16; }
 
-// Shared-memory plan of one launch; false if it does not fit.
-bool plan(int H, int CL, int nop, int kin, int* a_bytes, int* stage_bytes, int* stages) {
+// Shared-memory plan of one launch; false if it does not fit: the activation region (the
+// input's or a hidden layer's K slabs, whichever is wider), the weight ring (which also
+// stages the output tile), the FP32 store staging, the statistics exchange buffers, the
+// parameter slices and the barriers.
+bool plan(int H, int CL, int nh, int nop, int kin, int* a_bytes, int* stage_bytes, int* stages, int* par_floats,
+          int* smem) {
     const int NS = H / CL;
     const int k0 = (kin + SLAB - 1) / SLAB, hs = (H + SLAB - 1) / SLAB;
     *a_bytes = std::max(k0, hs) * SLAB_BYTES;
     *stage_bytes = std::max(NS, nop) * 128;
-    const int fixed = 1024 + STG_BYTES + XBUF_BYTES + 256;
+    *par_floats = (nh * 3 * NS + nop + 3) / 4 * 4;
+    const int fixed = 1024 + STG_BYTES + 2 * CL * BM * 2 * 4 + *par_floats * 4 + 256;
     const int n = (SMEM_LIMIT - fixed - *a_bytes) / *stage_bytes;
     *stages = std::min(n, 8);
-    return *stages >= 2;
+    *smem = fixed + *a_bytes + *stages * *stage_bytes;
+    return *stages >= 2 && *stages * *stage_bytes >= BM * nop * 4;
+}
+
+// Row stride of the output staging: padded by 4 floats (fewer bank conflicts) when the
+// receive area after the CTA's own K slice has room for it.
+int out_ldr(int H, int CL, int nop, int ring_bytes) {
+    const int NS = H / CL;
+    const bool recv_room = CL == 1 || (nop + 4) * 2 <= H - NS;
+    return (recv_room && BM * (nop + 4) * 4 <= ring_bytes) ? nop + 4 : nop;
 }
 
 }  // namespace
@@ -563,12 +650,14 @@ int mlp_tc_cluster(int H, int nout, int force) {
     auto ok = [&](int CL) {
         const int NS = H / CL;
         if (H % CL || NS > 256 || NS % 32) return false;
-        if (CL > 1 && (NS % SLAB || nop > (H - NS) / 2)) return false;   // slices in whole slabs; output receive area
-        int ab, sb, st;
-        return plan(H, CL, nop, std::min(H, 1024), &ab, &sb, &st);
+        if (force && force != 1 && force != 2 && force != 4 && force != 8) return false;
+        // slices in whole slabs; the output receive area after the CTA's own K slice
+        if (CL > 1 && (NS % SLAB || nop * 2 > H - NS)) return false;
+        int ab, sb, st, pf, sm;
+        return plan(H, CL, kMlpMaxHidden, nop, std::min(H, 1024), &ab, &sb, &st, &pf, &sm);
     };
     if (force) return ok(force) ? force : 0;
-    for (int CL : {4, 2, 1})
+    for (int CL : {4, 8, 2, 1})
         if (ok(CL)) return CL;
     return 0;
 }
@@ -587,11 +676,14 @@ int launch_mlp_tc(const MlpTcProblem* p, int n, int nh, int H, int nout, float e
     std::memset(&a, 0, sizeof(a));
     a.n_probs = n; a.nh = nh; a.H = H; a.CL = CL; a.NS = H / CL; a.nout = nout; a.nop = round16(nout);
     a.eps = eps; a.err = err;
+
     a.wait_limit = wait && wait->cycles > 0 ? wait->cycles : kWaitDefault;
     int kin_max = 0;
     for (int i = 0; i < n; ++i) kin_max = std::max(kin_max, p[i].kin);
     if (kin_max > 1024) return -1;
-    if (!plan(H, CL, a.nop, kin_max, &a.a_bytes, &a.stage_bytes, &a.stages)) return -1;
+    int smem = 0;
+    if (!plan(H, CL, nh, a.nop, kin_max, &a.a_bytes, &a.stage_bytes, &a.stages, &a.par_floats, &smem)) return -1;
+    a.ldr = out_ldr(H, CL, a.nop, a.stages * a.stage_bytes);
     const int need_cols = std::max(std::max(a.NS, a.nop), 32);
     a.tmem_cols = 32;
     while ((int)a.tmem_cols < need_cols) a.tmem_cols *= 2;
@@ -621,7 +713,7 @@ int launch_mlp_tc(const MlpTcProblem* p, int n, int nh, int H, int nout, float e
         d.cta0 = ctas;
         ctas += (q.M + BM - 1) / BM * CL;
     }
-    launch_kc(mlp_tc_kernel, dim3(ctas), dim3(kThreads), SMEM_LIMIT, s, dim3(CL), a);
+    launch_kc(mlp_tc_kernel, dim3(ctas), dim3(kThreads), (size_t)smem, s, dim3(CL), a);
     return 0;
 }
 

@@ -34,7 +34,7 @@ struct MlpTcProblem {
 // H (a multiple of 32, at most 1024), 1 <= nout <= 256, kin <= 1024.
 bool mlp_tc_supported(int nh, int H, int nout, int kin);
 // Cluster size (CTAs sharing a row block, each computing H / CL columns of every hidden
-// layer) the launcher would pick for H; `force` (1, 2 or 4) if the shape allows it.
+// layer) the launcher would pick for H; `force` (1, 2, 4 or 8) if the shape allows it.
 int mlp_tc_cluster(int H, int nout, int force = 0);
 // Launches the n (<= 2) problems as one grid.  Returns 0, or < 0 if a shape or operand
 // cannot be described (the caller then uses the layer-by-layer path).

@@ -120,7 +120,7 @@ int squint_op_mlp_bf16(int M, int kin, int nh, int H, int nout, const void* x, i
                        float* const* post, void* const* post_bf, float* const* mean, float* const* rstd, int cluster,
                        void* stream) {
     if (M < 0 || kin < 1 || nh < 1 || nh > kMlpMaxHidden || H < 1 || nout < 1 || !x || !w || !ldw || !bias || !g ||
-        !beta || !out || ldo < nout || ldx < kin || (cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4))
+        !beta || !out || ldo < nout || ldx < kin || (cluster != 0 && cluster != 1 && cluster != 2 && cluster != 4 && cluster != 8))
         return SQUINT_EINVAL;
     if (!mlp_tc_supported(nh, H, nout, kin) || (cluster && !mlp_tc_cluster(H, nout, cluster))) {
         g_last_error = "fused MLP: shape outside the kernel's range (or cluster size not possible for it)";
