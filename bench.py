@@ -31,6 +31,14 @@ METRIC = "SAC updates/s at B=512 (BF16 vs FP32 plain); act p50/p99 latency on 1 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
 N_SM = 152
 FP32_LANES_PER_SM = 128
+# act floor per query at the training shape: the 3x128x128 uint8 frame read once, and the
+# encoder + actor projection + actor MLP contractions
+ACT_BYTES = 3 * 128 * 128
+ACT_FLOPS = 9.37e6
+# update floor at the training shape (B = 512): HBM bytes (gather, Adam, polyak) and
+# contraction FLOPs of one update
+UPDATE_BYTES = 50.33e6 + 74.9e6 + 18.9e6
+UPDATE_FLOPS = 27.96e9
 
 # DRAM traffic per launch of the dominant kernel class from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the class's launches
@@ -401,12 +409,23 @@ def run_ours(args):
             kernels[n]["frac"] = round(cr["achieved"] / cr["peak"], 5)
     roof["kernels_per_update"] = kernels
     roof["phase_ms"] = phase_ms
+    # the whole update against its floor at the measured peaks (training shape): HBM bytes
+    # and contraction FLOPs overlapped (the larger time) or serial (the sum)
+    if args.workload == "train_b512":
+        t_h = UPDATE_BYTES / (peaks["hbm_gbs"] * 1e9) * 1e6
+        t_t = UPDATE_FLOPS / (peaks["bf16_tflops_sustained"] * 1e12) * 1e6
+        us = 1e6 / value
+        roof["update"] = {"us_per_update": us, "floor_us_overlapped": max(t_h, t_t), "floor_us_serial": t_h + t_t,
+                          "frac_overlapped": max(t_h, t_t) / us, "frac_serial": (t_h + t_t) / us,
+                          "floor": "HBM: gather 50.3 MB + Adam 74.9 MB + polyak 18.9 MB; tensor: 27.96 GFLOP at "
+                                   "the sustained bf16 peak"}
 
     # ---- serving: continuous batching beside the UTD-4 update stream
     serving = None
     if not args.no_serving and rank == 0:
         serving = measure_serving(lib, learner, cfg, stream)
     gpu_launches = learner.graph_kernel_count(UTD_K) * K
+    pflat = learner.params()
     learner.close()
 
     # ---- the plain FP32 path on the same ring and schedule, for the BF16-vs-FP32 comparison
@@ -440,6 +459,20 @@ def run_ours(args):
         ups, n, dt = oracle_updates_per_s(cfg, lazy, budget_s=15.0, max_updates=12)
         cpu = {"value": ups, "unit": "updates/s", "cores": blas_threads(), "kind": "oracle",
                "sample": f"{n} FP64 oracle update(s) of the full batch-512 workload in {dt:.1f} s"}
+        if serving and cfg.get("conv_layers", 0) > 0:
+            # the oracle's inference on the same policy: 512 queries (one group of the serving mix)
+            from oracle import squint_sac as o
+            P, off = {}, 0
+            for name, shape, _, _ in o.param_spec(cfg):
+                k = int(np.prod(shape))
+                P[name] = np.asarray(pflat[off:off + k], dtype=np.float64).reshape(shape)
+                off += k
+            obs_c, prop_c = synth.make_obs_batch(512, cfg, 5, device="cpu")
+            t0 = time.perf_counter()
+            o.act(P, obs_c.numpy(), prop_c.numpy(), 1, True, cfg)
+            adt = time.perf_counter() - t0
+            serving["cpu_baseline"] = {"value": 512 / adt, "unit": "queries/s", "cores": blas_threads(),
+                                       "kind": "oracle", "sample": f"512 FP64 oracle queries in {adt:.2f} s"}
 
     if rank == 0:
         line = {
@@ -522,14 +555,27 @@ def measure_serving(lib, learner, cfg, upd_stream, seconds=4.0, n_envs=4096, mea
             learner.serve_poll(tickets[g], 5_000_000)
     stop.set()
     th.join()
+    info = learner.serve_info()
     learner.serve_stop()
     if not lats:
         return None
+    qps = rows_done / elapsed
+    # act floor per query: 49,152 B of observation read (HBM) and 9.37 MFLOP (tensor), at the
+    # measured peaks; overlapped (the larger) and serial (the sum)
+    peaks, _ = load_peaks()
+    t_hbm = ACT_BYTES / (peaks["hbm_gbs"] * 1e9)
+    t_ten = ACT_FLOPS / (peaks["bf16_tflops"] * 1e12)
     return {"envs": n_envs, "groups": len(sizes), "requests_completed": len(lats),
-            "queries_per_s": rows_done / elapsed, "p50_us": float(np.percentile(lats, 50)),
+            "queries_per_s": qps, "p50_us": float(np.percentile(lats, 50)),
             "p99_us": float(np.percentile(lats, 99)), "updates_per_s_concurrent": (u1 - u0) / elapsed,
+            "slots": info["slots"], "slot_rows": info["slot_rows"], "arena_bytes": info["arena_bytes"],
+            "floor": {"bytes_per_query": ACT_BYTES, "flops_per_query": ACT_FLOPS,
+                      "queries_per_s_overlapped": 1.0 / max(t_hbm, t_ten), "queries_per_s_serial": 1.0 / (t_hbm + t_ten),
+                      "frac_of_serial_floor": qps * (t_hbm + t_ten), "frac_of_overlapped_floor": qps * max(t_hbm, t_ten),
+                      "peaks": "measured HBM copy and bf16 burst"},
             "group_sizes": "U{1..512}", "arrivals": f"closed loop, exponential env step mean {mean_step_us:.0f} us",
-            "latency": "submit to completion event, measured by the server thread"}
+            "latency": "host queueing until the batch's launch plus the batch's device time (launch marker to "
+                       "completion event)"}
 
 
 def main():

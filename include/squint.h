@@ -230,22 +230,46 @@ int squint_refresh_policy(squint_handle* h, void* stream);
 /* ------------------------------------------------------------------ serving loop */
 
 /*
- * Continuous-batching server for actor queries.  A host scheduler thread takes
- * submitted requests, admits them while the rows in flight stay within
- * max_rows and their device memory within mem_budget_bytes, packs every admitted
- * request into the next batch on its own act stream, and reports completion per
- * request.  Requests that arrive while a batch runs join the next one.
+ * Continuous-batching server for actor queries (Alg. 1, "Sample a_t ~ pi": batched
+ * inference for the parallel environments).  A host scheduler thread keeps up to
+ * `slots` batches in flight (3 by default; SQUINT_SERVE_SLOTS=1..4 in the environment
+ * at start), each slot with its own activation arena and its own stream at the
+ * device's highest priority.  Whenever a slot is free it admits queued requests in
+ * arrival order up to the slot's rows and launches them as one ragged batch, so
+ * requests that arrive while others run are admitted as slots free up and their work
+ * overlaps the batches still on the GPU.  Admission by memory: the arenas are
+ * allocated at start and hold at most mem_budget_bytes (and at most 90% of the
+ * device's free memory); max_rows bounds a batch (fewer rows per slot, or fewer
+ * slots, when the budget asks for it).  A row's result does not depend on the other
+ * requests of its batch.
  */
 int squint_serve_start(squint_handle* h, int max_rows, size_t mem_budget_bytes);
 /* Queue a request (buffers must stay valid until it completes); *ticket receives its id.
- * SQUINT_EAGAIN if the queue is full, SQUINT_EINVAL if it can never be admitted. */
+ * SQUINT_EAGAIN if the queue is full, SQUINT_EINVAL if it can never be admitted (more
+ * rows than a slot holds), SQUINT_ESTATE if the server is not running. */
 int squint_serve_submit(squint_handle* h, const squint_act_request* req, uint64_t* ticket);
-/* Wait up to timeout_us (0 = poll) for a ticket.  SQUINT_OK when done, with the
- * submit-to-completion latency in *latency_us and the policy snapshot version it
- * used in *policy_version (either may be NULL); SQUINT_EAGAIN if not yet. */
+/* What a completed request reports. */
+typedef struct {
+    double latency_us;        /* submit to completion: queueing on the host until its batch was
+                                 launched, plus the batch's device time from its launch marker
+                                 to its completion event */
+    int64_t policy_version;   /* policy snapshot the batch read */
+    double device_begin_us;   /* the batch's launch marker and completion on the device, in */
+    double device_end_us;     /* microseconds from the server's start */
+    int32_t slot;             /* the slot (arena and stream) that ran it */
+    int32_t batch_rows;       /* rows of its batch */
+} squint_serve_result;
+/* Wait up to timeout_us (0 = poll) for a ticket.  SQUINT_OK when done (*out filled if not
+ * NULL); SQUINT_EAGAIN if not yet; SQUINT_ESTATE if the server stopped without it. */
+int squint_serve_poll_ex(squint_handle* h, uint64_t ticket, int64_t timeout_us, squint_serve_result* out);
+/* The same, reporting only the latency and the policy version (either may be NULL). */
 int squint_serve_poll(squint_handle* h, uint64_t ticket, int64_t timeout_us, double* latency_us,
                       int64_t* policy_version);
-/* Stop the scheduler after the queued work completes. */
+/* Slots, rows per slot and the device bytes the slots' arenas hold. */
+int squint_serve_info(squint_handle* h, int* slots, int* slot_rows, int64_t* arena_bytes);
+/* Stop the scheduler after the queued and in-flight work completes; waiting pollers
+ * of tickets it never completes return SQUINT_ESTATE.  Safe while other threads submit
+ * or poll. */
 int squint_serve_stop(squint_handle* h);
 
 /* ------------------------------------------------------------------ state */

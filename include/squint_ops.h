@@ -39,6 +39,14 @@ int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, 
 
 
 /*
+ * FP32 rows to BF16 rows with round-to-nearest-even (the rounding of every BF16 operand
+ * the tensor-core path reads): dst[r, c] = bf16(src[r, c]) for c < cols, and zero in the
+ * pad columns cols <= c < ld_dst.  Row strides in elements.
+ */
+int squint_op_cast_bf16(int rows, int cols, const float* src, int64_t ld_src, void* dst, int64_t ld_dst,
+                        void* stream);
+
+/*
  * A whole LayerNorm MLP head in one BF16 tensor-core launch (the critic and actor MLPs,
  * Sec. IV "Normalization": nh hidden layers Linear -> LayerNorm -> ReLU, then a plain
  * Linear output layer; Alg. 1 evaluates them in every step of the update):

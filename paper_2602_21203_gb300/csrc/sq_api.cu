@@ -154,6 +154,7 @@ size_t squint_struct_size(const char* name) {
     if (n == "squint_replay") return sizeof(squint_replay);
     if (n == "squint_update_stats") return sizeof(squint_update_stats);
     if (n == "squint_act_request") return sizeof(squint_act_request);
+    if (n == "squint_serve_result") return sizeof(squint_serve_result);
     return 0;
 }
 
@@ -356,7 +357,7 @@ int squint_refresh_policy(squint_handle* h, void* stream) {
 int squint_act(squint_handle* h, const squint_act_request* reqs, int n_reqs, void* stream) {
     if (!h || (!reqs && n_reqs > 0) || n_reqs < 0) return SQUINT_EINVAL;
     if (h->failed) return SQUINT_ESTATE;
-    return h->act(reqs, n_reqs, (cudaStream_t)stream);
+    return h->act(h->arena, reqs, n_reqs, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -64,6 +64,28 @@ struct MlpBufs {
 // BF16 padded copy of one linear layer's weight (online and, for the critic range, target).
 struct LinBf { __nv_bfloat16* on = nullptr; __nv_bfloat16* tg = nullptr; int64_t ld = 0; };
 
+// Activation buffers of one inference batch: the one squint_act uses, or a serving
+// slot's (several batches in flight each need their own).
+struct ActArena {
+    int cap = 0, rcap = 0;                 // rows and requests the buffers hold
+    float* ax = nullptr;
+    std::vector<float*> aconv;
+    float* apre = nullptr; float* amean = nullptr; float* arstd = nullptr;
+    float* axin = nullptr;
+    MlpBufs mlp;
+    std::vector<__nv_bfloat16*> aphwc;     // BF16 inference: padded-HWC conv outputs (l < L-1)
+    __nv_bfloat16* az_h = nullptr;         // BF16 inference: encoder features [cap, F]
+    __nv_bfloat16* axin_h = nullptr;       // BF16 inference: actor input [cap, pad8(Da)]
+    void* d_req = nullptr;                 // packed per-request arrays
+    void* h_req = nullptr;                 // pinned staging
+    size_t req_bytes = 0;
+    cudaEvent_t req_event = nullptr;       // the staging's upload finished
+    bool req_event_live = false;
+    cudaEvent_t released[2] = {nullptr, nullptr};   // this arena's last batch finished reading policy buffer i
+    std::vector<void*> allocs;
+    size_t bytes = 0;                      // device bytes held
+};
+
 struct ServeState;
 
 }  // namespace sq
@@ -120,7 +142,6 @@ struct squint_handle {
     int policy_active = 0;
     int64_t policy_version = 0;
     cudaEvent_t policy_ready[2] = {nullptr, nullptr};     // copy into buffer i finished
-    cudaEvent_t policy_released[2] = {nullptr, nullptr};  // inference reading buffer i finished
     int64_t* d_update_idx = nullptr;
     int32_t* d_steps = nullptr;       // critic, actor, alpha
     int32_t* d_do_actor = nullptr;
@@ -221,25 +242,11 @@ struct squint_handle {
     std::vector<__nv_bfloat16*> wconv_fwd, wconv_bwd;   // [l]: BF16 filter layouts (l >= 1)
     float* wgrad_tc_work = nullptr;
 
-    // inference
-    int act_cap = 0;
-    float* ax = nullptr;
-    std::vector<float*> aconv;
-    float* apre = nullptr; float* amean = nullptr; float* arstd = nullptr;
-    float* axin = nullptr;
-    sq::MlpBufs act_mlp;
-    std::vector<__nv_bfloat16*> aphwc;    // BF16 inference: padded-HWC conv outputs (l < L-1)
-    __nv_bfloat16* az_h = nullptr;        // BF16 inference: encoder features [cap, F]
-    __nv_bfloat16* axin_h = nullptr;      // BF16 inference: actor input [cap, pad8(Da)]
-    int32_t* d_row_req = nullptr; int32_t* d_row_in = nullptr;
-    void* d_req = nullptr;            // packed per-request arrays
-    void* h_req = nullptr;            // pinned staging
-    size_t req_bytes = 0;
-    int req_cap = 0;
+    // inference: the arena squint_act uses, and every arena that may read a policy buffer
+    // (this one and the serving slots'), guarded by act_mu
+    sq::ActArena arena;
+    std::vector<sq::ActArena*> arenas;
     cudaStream_t capture_stream = nullptr;
-    cudaEvent_t req_event = nullptr;
-    bool req_event_live = false;
-    std::vector<void*> act_allocs;
     std::map<int, cudaGraphExec_t> graphs;
     std::map<int, int64_t> graph_kernels;
     // concurrent branches of one update: library-owned streams joined back before it ends
@@ -282,7 +289,8 @@ struct squint_handle {
     std::vector<void*> allocations;
     int64_t device_bytes = 0;             // sum of the dalloc sizes
     int rc_chunk = 0;                     // encoder recompute chunk (images), 0 = off
-    sq::ServeState* serve = nullptr;
+    std::shared_ptr<sq::ServeState> serve;   // guarded by serve_mu
+    std::mutex serve_mu;
     std::mutex act_mu;
 
     int allocate();
@@ -298,9 +306,13 @@ struct squint_handle {
     int load_state(const uint8_t* in);
     int debug_tensor(const char* name, void* host, size_t* bytes);
     int refresh_policy(cudaStream_t s);
-    int ensure_act_capacity(int rows, int n_reqs);
+    // (re)allocate an arena for `rows` rows and `n_reqs` requests (caller holds act_mu)
+    int alloc_arena(sq::ActArena& a, int rows, int n_reqs);
+    void free_arena(sq::ActArena& a);
     size_t act_row_bytes() const;
-    int act(const squint_act_request* reqs, int n_reqs, cudaStream_t s, int64_t* version_used = nullptr);
+    // one ragged inference batch with arena a on stream s
+    int act(sq::ActArena& a, const squint_act_request* reqs, int n_reqs, cudaStream_t s,
+            int64_t* version_used = nullptr);
 
     // Device allocation; a failure is recorded as a null entry that allocate() reports.
     template <typename T> T* dalloc(int64_t n) {

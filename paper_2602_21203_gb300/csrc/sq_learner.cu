@@ -701,11 +701,8 @@ int squint_handle::allocate() {
     SQ_CK(this, cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
     for (auto& st : side) SQ_CK(this, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     for (auto& e : fork_ev) SQ_CK(this, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    for (int i = 0; i < 2; ++i) {
-        SQ_CK(this, cudaEventCreateWithFlags(&policy_ready[i], cudaEventDisableTiming));
-        SQ_CK(this, cudaEventCreateWithFlags(&policy_released[i], cudaEventDisableTiming));
-    }
-    SQ_CK(this, cudaEventCreateWithFlags(&req_event, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) SQ_CK(this, cudaEventCreateWithFlags(&policy_ready[i], cudaEventDisableTiming));
+    arenas.push_back(&arena);
     frontend_prepare(L.conv.empty() ? 0 : (size_t)c.obs_c * c.obs_h * c.obs_w);
 
     std::vector<float> p;
@@ -730,21 +727,16 @@ void squint_handle::release() {
     allocations.clear();
     if (h_stats) cudaFreeHost(h_stats);
     h_stats = nullptr;
-    if (h_req) cudaFreeHost(h_req);
-    h_req = nullptr;
+    free_arena(arena);
+    arenas.clear();
     if (capture_stream) cudaStreamDestroy(capture_stream);
     capture_stream = nullptr;
     for (auto& st : side) { if (st) cudaStreamDestroy(st); st = nullptr; }
     for (auto& e : fork_ev) { if (e) cudaEventDestroy(e); e = nullptr; }
     for (int i = 0; i < 2; ++i) {
         if (policy_ready[i]) cudaEventDestroy(policy_ready[i]);
-        if (policy_released[i]) cudaEventDestroy(policy_released[i]);
-        policy_ready[i] = policy_released[i] = nullptr;
+        policy_ready[i] = nullptr;
     }
-    if (req_event) cudaEventDestroy(req_event);
-    req_event = nullptr;
-    for (void* p : act_allocs) if (p) cudaFree(p);
-    act_allocs.clear();
 }
 
 void squint_handle::quantize_weights(const std::vector<QuantItem>& q, cudaStream_t s) {

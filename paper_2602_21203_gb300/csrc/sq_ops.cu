@@ -151,6 +151,15 @@ int squint_op_mlp_bf16(int M, int kin, int nh, int H, int nout, const void* x, i
     return launch_status();
 }
 
+int squint_op_cast_bf16(int rows, int cols, const float* src, int64_t ld_src, void* dst, int64_t ld_dst,
+                        void* stream) {
+    if (rows < 0 || cols < 1 || !src || !dst || ld_src < cols || ld_dst < cols) return SQUINT_EINVAL;
+    if (rows == 0) return SQUINT_OK;
+    CastItem it{src, ld_src, rows, cols, (__nv_bfloat16*)dst, ld_dst};
+    launch_cast_rows(&it, 1, (cudaStream_t)stream);
+    return launch_status();
+}
+
 static int64_t pad16(int64_t n) { return (n + 15) / 16 * 16; }
 
 size_t squint_op_gemm_fp8_workspace(int M, int N, int K) {

@@ -113,7 +113,8 @@ int squint_handle::refresh_policy(cudaStream_t s) {
     std::lock_guard<std::mutex> lk(act_mu);
     // write the snapshot inference is not using, after inference that last read it
     const int i = 1 - policy_active;
-    SQ_CK(this, cudaStreamWaitEvent(s, policy_released[i], 0));
+    for (sq::ActArena* a : arenas)
+        if (a->released[i]) SQ_CK(this, cudaStreamWaitEvent(s, a->released[i], 0));
     SQ_CK(this, cudaMemcpyAsync(policy_buf[i], params, L.total * sizeof(float), cudaMemcpyDeviceToDevice, s));
     snapshot_bf16(i, s);
     SQ_CK(this, cudaEventRecord(policy_ready[i], s));
@@ -132,69 +133,91 @@ size_t squint_handle::act_row_bytes() const {
     return f * sizeof(float) + 8;
 }
 
-int squint_handle::ensure_act_capacity(int rows, int n_reqs) {
-    if (rows <= act_cap && n_reqs <= req_cap) return SQUINT_OK;
-    SQ_CK(this, cudaDeviceSynchronize());
-    for (void* p : act_allocs) if (p) cudaFree(p);
-    act_allocs.clear();
-    if (h_req) { cudaFreeHost(h_req); h_req = nullptr; }
-    const int cap = std::max(((std::max(rows, act_cap) + 255) / 256) * 256, 256);
-    const int rcap = std::max(std::max(n_reqs, req_cap), 64);
+void squint_handle::free_arena(sq::ActArena& a) {
+    if (a.req_event_live) cudaEventSynchronize(a.req_event);
+    for (int i = 0; i < 2; ++i)
+        if (a.released[i]) cudaEventSynchronize(a.released[i]);
+    for (void* p : a.allocs) if (p) cudaFree(p);
+    a.allocs.clear();
+    if (a.h_req) cudaFreeHost(a.h_req);
+    a.h_req = nullptr;
+    if (a.req_event) cudaEventDestroy(a.req_event);
+    a.req_event = nullptr;
+    for (int i = 0; i < 2; ++i) {
+        if (a.released[i]) cudaEventDestroy(a.released[i]);
+        a.released[i] = nullptr;
+    }
+    a.cap = a.rcap = 0;
+    a.bytes = 0;
+    a.req_event_live = false;
+}
+
+int squint_handle::alloc_arena(sq::ActArena& a, int rows, int n_reqs) {
+    if (rows <= a.cap && n_reqs <= a.rcap) return SQUINT_OK;
+    const int cap = std::max(((std::max(rows, a.cap) + 255) / 256) * 256, 256);
+    const int rcap = std::max(std::max(n_reqs, a.rcap), 64);
+    free_arena(a);
     auto al = [&](size_t bytes) -> void* {
         void* p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
-        act_allocs.push_back(p);
+        bytes = std::max<size_t>(bytes, 16);
+        if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        a.allocs.push_back(p);
+        a.bytes += bytes;
         return p;
     };
     const int64_t img = (int64_t)L.img_c * L.hs * L.ws;
-    ax = (float*)al(sizeof(float) * cap * img);
-    aconv.clear();
-    for (const auto& cv : L.conv) aconv.push_back((float*)al(sizeof(float) * (size_t)cap * cv.cout * cv.oh * cv.ow));
+    a.ax = (float*)al(sizeof(float) * cap * img);
+    a.aconv.clear();
+    for (const auto& cv : L.conv) a.aconv.push_back((float*)al(sizeof(float) * (size_t)cap * cv.cout * cv.oh * cv.ow));
     if (L.D > 0) {
-        apre = (float*)al(sizeof(float) * (size_t)cap * L.D);
-        amean = (float*)al(sizeof(float) * cap);
-        arstd = (float*)al(sizeof(float) * cap);
+        a.apre = (float*)al(sizeof(float) * (size_t)cap * L.D);
+        a.amean = (float*)al(sizeof(float) * cap);
+        a.arstd = (float*)al(sizeof(float) * cap);
     }
-    axin = (float*)al(sizeof(float) * (size_t)cap * L.da);
+    a.axin = (float*)al(sizeof(float) * (size_t)cap * L.da);
     const int nh = c.n_hidden;
-    act_mlp = MlpBufs{};
-    act_mlp.E = 1; act_mlp.rows = cap;
-    act_mlp.pre.resize(nh); act_mlp.post.resize(nh); act_mlp.mean.resize(nh); act_mlp.rstd.resize(nh);
+    a.mlp = MlpBufs{};
+    a.mlp.E = 1; a.mlp.rows = cap;
+    a.mlp.pre.resize(nh); a.mlp.post.resize(nh); a.mlp.mean.resize(nh); a.mlp.rstd.resize(nh);
     for (int l = 0; l < nh; ++l) {
-        act_mlp.pre[l] = (float*)al(sizeof(float) * (size_t)cap * c.hidden[l]);
-        act_mlp.post[l] = (float*)al(sizeof(float) * (size_t)cap * c.hidden[l]);
-        act_mlp.mean[l] = (float*)al(sizeof(float) * cap);
-        act_mlp.rstd[l] = (float*)al(sizeof(float) * cap);
+        a.mlp.pre[l] = (float*)al(sizeof(float) * (size_t)cap * c.hidden[l]);
+        a.mlp.post[l] = (float*)al(sizeof(float) * (size_t)cap * c.hidden[l]);
+        a.mlp.mean[l] = (float*)al(sizeof(float) * cap);
+        a.mlp.rstd[l] = (float*)al(sizeof(float) * cap);
     }
-    act_mlp.out = (float*)al(sizeof(float) * (size_t)cap * 2 * c.action_dim);
-    aphwc.clear();
-    act_mlp.posth.clear();
-    az_h = axin_h = nullptr;
+    a.mlp.out = (float*)al(sizeof(float) * (size_t)cap * 2 * c.action_dim);
+    a.aphwc.clear();
+    a.mlp.posth.clear();
+    a.az_h = a.axin_h = nullptr;
     if (bf16) {
         // BF16 inference buffers; padded borders and pad columns stay zero
         if (tc_conv)
             for (size_t l = 0; l + 1 < L.conv.size(); ++l) {
                 const size_t bytes = 2 * (size_t)cap * (L.conv[l].oh + 4) * (L.conv[l].ow + 4) * 32;
-                aphwc.push_back((__nv_bfloat16*)al(bytes));
-                if (aphwc.back()) SQ_CK(this, cudaMemset(aphwc.back(), 0, bytes));
+                a.aphwc.push_back((__nv_bfloat16*)al(bytes));
+                if (a.aphwc.back()) SQ_CK(this, cudaMemset(a.aphwc.back(), 0, bytes));
             }
-        az_h = (__nv_bfloat16*)al(2 * (size_t)cap * L.feat);
+        a.az_h = (__nv_bfloat16*)al(2 * (size_t)cap * L.feat);
         const size_t xb = 2 * (size_t)cap * ((L.da + 7) / 8 * 8);
-        axin_h = (__nv_bfloat16*)al(xb);
-        if (axin_h) SQ_CK(this, cudaMemset(axin_h, 0, xb));
-        for (int l = 0; l < nh; ++l) act_mlp.posth.push_back((__nv_bfloat16*)al(2 * (size_t)cap * c.hidden[l]));
+        a.axin_h = (__nv_bfloat16*)al(xb);
+        if (a.axin_h) SQ_CK(this, cudaMemset(a.axin_h, 0, xb));
+        for (int l = 0; l < nh; ++l) a.mlp.posth.push_back((__nv_bfloat16*)al(2 * (size_t)cap * c.hidden[l]));
     }
-    req_bytes = (size_t)cap * 8 + (size_t)rcap * (8 * 4 + 4) + 64;
-    d_req = al(req_bytes);
-    for (void* p : act_allocs) if (!p) { g_last_error = "inference allocation failed"; act_cap = 0; return SQUINT_ENOMEM; }
-    if (cudaMallocHost(&h_req, req_bytes) != cudaSuccess) { act_cap = 0; return SQUINT_ENOMEM; }
-    act_cap = cap;
-    req_cap = rcap;
-    req_event_live = false;
+    a.req_bytes = (size_t)cap * 8 + (size_t)rcap * (8 * 4 + 4) + 64;
+    a.d_req = al(a.req_bytes);
+    for (void* p : a.allocs)
+        if (!p) { g_last_error = "inference allocation failed"; free_arena(a); return SQUINT_ENOMEM; }
+    if (cudaMallocHost(&a.h_req, a.req_bytes) != cudaSuccess) { free_arena(a); return SQUINT_ENOMEM; }
+    SQ_CK(this, cudaEventCreateWithFlags(&a.req_event, cudaEventDisableTiming));
+    for (int i = 0; i < 2; ++i) SQ_CK(this, cudaEventCreateWithFlags(&a.released[i], cudaEventDisableTiming));
+    SQ_CK(this, cudaDeviceSynchronize());   // the zeroed borders before any batch
+    a.cap = cap;
+    a.rcap = rcap;
     return SQUINT_OK;
 }
 
-int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t s, int64_t* version_used) {
+int squint_handle::act(sq::ActArena& a, const squint_act_request* reqs, int n_reqs, cudaStream_t s,
+                       int64_t* version_used) {
     std::lock_guard<std::mutex> lk(act_mu);
     int rows = 0;
     for (int q = 0; q < n_reqs; ++q) {
@@ -206,11 +229,16 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
         rows += rq.n;
     }
     if (rows == 0) return SQUINT_OK;
-    int rc = ensure_act_capacity(rows, n_reqs);
+    int rc = alloc_arena(a, rows, n_reqs);
     if (rc != SQUINT_OK) return rc;
-    if (req_event_live) SQ_CK(this, cudaEventSynchronize(req_event));
+    if (a.req_event_live) SQ_CK(this, cudaEventSynchronize(a.req_event));
+    const int act_cap = a.cap, req_cap = a.rcap;
+    float* ax = a.ax; float* apre = a.apre; float* amean = a.amean; float* arstd = a.arstd; float* axin = a.axin;
+    const std::vector<float*>& aconv = a.aconv;
+    const std::vector<__nv_bfloat16*>& aphwc = a.aphwc;
+    __nv_bfloat16* az_h = a.az_h; __nv_bfloat16* axin_h = a.axin_h;
     // pack: row_req[cap] row_in[cap] | obs[rcap] prop[rcap] act[rcap] key[rcap] (8 B each) | mode[rcap]
-    uint8_t* hb = static_cast<uint8_t*>(h_req);
+    uint8_t* hb = static_cast<uint8_t*>(a.h_req);
     int32_t* row_req = reinterpret_cast<int32_t*>(hb);
     int32_t* row_in = row_req + act_cap;
     uint64_t* p64 = reinterpret_cast<uint64_t*>(hb + (size_t)act_cap * 8);
@@ -224,10 +252,10 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
         p64[3 * req_cap + q] = reqs[q].rng_key;
         modes[q] = reqs[q].mode;
     }
-    SQ_CK(this, cudaMemcpyAsync(d_req, h_req, req_bytes, cudaMemcpyHostToDevice, s));
-    SQ_CK(this, cudaEventRecord(req_event, s));
-    req_event_live = true;
-    uint8_t* db = static_cast<uint8_t*>(d_req);
+    SQ_CK(this, cudaMemcpyAsync(a.d_req, a.h_req, a.req_bytes, cudaMemcpyHostToDevice, s));
+    SQ_CK(this, cudaEventRecord(a.req_event, s));
+    a.req_event_live = true;
+    uint8_t* db = static_cast<uint8_t*>(a.d_req);
     const int32_t* d_row_req = reinterpret_cast<const int32_t*>(db);
     const int32_t* d_row_in = d_row_req + act_cap;
     const uint64_t* d64 = reinterpret_cast<const uint64_t*>(db + (size_t)act_cap * 8);
@@ -317,15 +345,15 @@ int squint_handle::act(const squint_act_request* reqs, int n_reqs, cudaStream_t 
     }
     MlpRef actor_ref;
     for (const auto& ly : L.actor) actor_ref.push_back(bf_ref(ly));
-    mlp_forward(this, act_mlp, &actor_ref, 1, Mat{axin, Da, axin_h, Da8}, rows, bf16, s, false, false);
+    mlp_forward(this, a.mlp, &actor_ref, 1, Mat{axin, Da, axin_h, Da8}, rows, bf16, s, false, false);
     ActHeadArgs ha{};
-    ha.rows = rows; ha.A = A; ha.out = act_mlp.out; ha.ld_out = 2 * A;
+    ha.rows = rows; ha.A = A; ha.out = a.mlp.out; ha.ld_out = 2 * A;
     ha.row_req = d_row_req; ha.row_in_req = d_row_in;
     ha.req_key = d64 + 3 * req_cap; ha.req_mode = d_modes;
     ha.req_actions = reinterpret_cast<float* const*>(d64 + 2 * req_cap);
     ha.lo = (float)c.log_std_min; ha.hi = (float)c.log_std_max; ha.seed = c.seed;
     launch_act_head(ha, s);
-    SQ_CK(this, cudaEventRecord(policy_released[pi], s));
+    SQ_CK(this, cudaEventRecord(a.released[pi], s));
     SQ_CK(this, cudaGetLastError());
     return SQUINT_OK;
 }

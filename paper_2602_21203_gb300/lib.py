@@ -56,6 +56,12 @@ class UpdateStats(ctypes.Structure):
                 ("update_idx", ctypes.c_int64)]
 
 
+class ServeResult(ctypes.Structure):
+    _fields_ = [("latency_us", ctypes.c_double), ("policy_version", ctypes.c_int64),
+                ("device_begin_us", ctypes.c_double), ("device_end_us", ctypes.c_double),
+                ("slot", ctypes.c_int32), ("batch_rows", ctypes.c_int32)]
+
+
 class ActRequest(ctypes.Structure):
     _fields_ = [("group_id", ctypes.c_uint64), ("n", ctypes.c_int32), ("mode", ctypes.c_int32),
                 ("rng_key", ctypes.c_uint64), ("obs", ctypes.c_void_p), ("proprio", ctypes.c_void_p),
@@ -87,6 +93,8 @@ def load():
         "squint_serve_start": (I, [P, I, SZ]),
         "squint_serve_submit": (I, [P, P, ctypes.POINTER(U64)]),
         "squint_serve_poll": (I, [P, U64, I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]),
+        "squint_serve_poll_ex": (I, [P, U64, I64, P]),
+        "squint_serve_info": (I, [P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I64)]),
         "squint_serve_stop": (I, [P]),
         "squint_get_params": (I, [P, P, I64]),
         "squint_set_params": (I, [P, P, I64]),
@@ -104,6 +112,7 @@ def load():
         "squint_op_relu_bwd": (I, [I, I64, P, P, P, P]),
         "squint_op_squint_store": (I, [I, I, I, I, I, P, P, I64, I64, P]),
         "squint_op_gemm_fp8_workspace": (SZ, [I, I, I]),
+        "squint_op_cast_bf16": (I, [I, I, P, I64, P, I64, P]),
         "squint_op_mlp_bf16": (I, [I, I, I, I, I, P, I64, P, P, P, P, P, ctypes.c_float, P, I64, P, P, P, P, P, I, P]),
         "squint_op_gemm_layernorm": (I, [I, I, I, P, I64, P, I64, P, P, P, ctypes.c_float, I, P, P, P, P, P, P]),
         "squint_op_gemm_fp8": (I, [I, I, I, P, I64, P, I64, P, I64, P, P, SZ, P]),
@@ -337,6 +346,21 @@ class Learner:
             return None
         _check(rc, "squint_serve_poll")
         return lat.value, ver.value
+
+    def serve_poll_ex(self, ticket, timeout_us=0):
+        """None if not done yet, else a dict: latency_us, policy_version, device_begin_us,
+        device_end_us, slot, batch_rows."""
+        r = ServeResult()
+        rc = self.lib.squint_serve_poll_ex(self.h, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(r))
+        if rc == EAGAIN:
+            return None
+        _check(rc, "squint_serve_poll_ex")
+        return {f: getattr(r, f) for f, _ in ServeResult._fields_}
+
+    def serve_info(self):
+        a, b, c = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int64(0)
+        _check(self.lib.squint_serve_info(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "squint_serve_info")
+        return {"slots": a.value, "slot_rows": b.value, "arena_bytes": c.value}
 
     def serve_stop(self):
         _check(self.lib.squint_serve_stop(self.h), "squint_serve_stop")

@@ -81,6 +81,19 @@ def gemm_layernorm(A, B, bias, g, beta, eps=1e-5, relu=True):
     return pre, post, post_bf, mean, rstd
 
 
+def cast_bf16(x):
+    """FP32 [rows, cols] -> BF16 (round to nearest even) in a buffer whose row stride is
+    cols rounded up to 8 (the tensor-core operand alignment); returns the [rows, cols] view."""
+    _need(x, torch.float32, "x")
+    rows, cols = x.shape
+    ld = (cols + 7) // 8 * 8
+    buf = torch.empty(rows, ld, dtype=torch.bfloat16, device=x.device)
+    if x.stride(1) != 1:
+        x = x.contiguous()
+    _chk(_lib.load().squint_op_cast_bf16(rows, cols, _p(x), x.stride(0), _p(buf), ld, _s()), "squint_op_cast_bf16")
+    return buf[:, :cols]
+
+
 def mlp_bf16(x, ws, biases, gs, betas, eps=1e-5, save=True, cluster=0):
     """A LayerNorm MLP head in one launch: hidden layers Linear -> LayerNorm -> ReLU
     (weights ws[l] BF16 [out, in], biases FP32), then a plain Linear output layer.

@@ -49,6 +49,7 @@ def test_struct_layouts_match(lib):
     assert L.squint_struct_size(b"squint_replay") == ctypes.sizeof(lib.Replay)
     assert L.squint_struct_size(b"squint_update_stats") == ctypes.sizeof(lib.UpdateStats)
     assert L.squint_struct_size(b"squint_act_request") == ctypes.sizeof(lib.ActRequest)
+    assert L.squint_struct_size(b"squint_serve_result") == ctypes.sizeof(lib.ServeResult)
     assert L.squint_struct_size(b"nope") == 0
 
 

@@ -198,3 +198,68 @@ def test_bf16_serving_results_equal_alone(L):
         assert torch.equal(out, a)
     learner.serve_stop()
     learner.close()
+
+
+def test_serving_overlaps_batches_and_each_result_matches_alone(L):
+    """Continuous batching: groups submitted together run as batches in several slots at
+    once (their device intervals overlap), and every group's actions are the same bits as
+    the group evaluated alone (the BF16 training-shape policy)."""
+    cfg = synth.make_config("train_b512")
+    learner = L.Learner(cfg, None, precision=L.PREC_BF16)
+    groups = [_batch(cfg, n, 40 + i) for i, n in enumerate([512, 512, 300, 512, 77, 512])]
+    alone = []
+    for i, (obs, prop, out) in enumerate(groups):
+        learner.act([L.Learner.request(obs, prop, out, key=90 + i)])
+        torch.cuda.synchronize()
+        alone.append(out.clone())
+        out.fill_(float("nan"))
+    learner.serve_start(max_rows=512, mem_budget_bytes=8 << 30)
+    info = learner.serve_info()
+    assert info["slots"] >= 2 and info["slot_rows"] == 512
+    overlapped = False
+    for attempt in range(5):
+        tickets = [learner.serve_submit(L.Learner.request(obs, prop, out, key=90 + i, group_id=i))
+                   for i, (obs, prop, out) in enumerate(groups)]
+        res = []
+        for t in tickets:
+            r = None
+            deadline = time.time() + 30
+            while r is None and time.time() < deadline:
+                r = learner.serve_poll_ex(t, timeout_us=100_000)
+            assert r is not None
+            res.append(r)
+        for (obs, prop, out), a in zip(groups, alone):
+            assert torch.equal(out, a)
+            out.fill_(float("nan"))
+        for i in range(len(res)):
+            for j in range(len(res)):
+                a, b = res[i], res[j]
+                if a["slot"] != b["slot"] and max(a["device_begin_us"], b["device_begin_us"]) < \
+                        min(a["device_end_us"], b["device_end_us"]):
+                    overlapped = True
+        assert all(r["latency_us"] > 0 and r["device_end_us"] > r["device_begin_us"] for r in res)
+        if overlapped:
+            break
+    assert overlapped, res
+    learner.serve_stop()
+    learner.close()
+
+
+def test_serving_admission_follows_the_memory_budget(L):
+    """A budget that holds one slot of 256 rows runs one slot; a group larger than a slot is refused."""
+    cfg = synth.make_config("small_b32")
+    learner = L.Learner(cfg, None)
+    rb = None
+    learner.serve_start(max_rows=4096, mem_budget_bytes=1 << 34)
+    big = learner.serve_info()
+    learner.serve_stop()
+    rb = big["arena_bytes"] / big["slots"] / ((big["slot_rows"] + 255) // 256 * 256)
+    learner.serve_start(max_rows=4096, mem_budget_bytes=int(rb * 300))
+    info = learner.serve_info()
+    assert info["slots"] == 1 and info["slot_rows"] <= 300
+    obs, prop, out = _batch(cfg, info["slot_rows"] + 1, 2)
+    with pytest.raises(L.SquintError) as e:
+        learner.serve_submit(L.Learner.request(obs, prop, out, key=1))
+    assert e.value.code == L.EINVAL
+    learner.serve_stop()
+    learner.close()

@@ -205,3 +205,104 @@ def test_small_critic_composition_matches_oracle_chain(ag):
     _, R["w1"], R["b1"] = o.conv3x3_bwd(xn, N["w1"], da1 * (a1 > 0), 2, need_dx=False)
     for k in shapes:
         assert _rel(grads[k].cpu(), R[k]) < 1e-4, k
+
+
+# ---------------------------------------------------------------- BF16 tensor-core wrappers
+def _bf(t):
+    """FP64 numpy copy of t rounded to BF16 (the operand the tensor-core kernels read)."""
+    return t.detach().to(torch.bfloat16).double().cpu().numpy()
+
+
+def _fd_check(F, X, G, g, n=3, h=1e-6):
+    """Central differences of the FP64 function F at X along n random directions against
+    the analytic gradient G (FP64 numpy arrays): the largest discrepancy relative to the
+    typical size of a directional derivative, ||G|| ||V|| / sqrt(size) (a single projection
+    can pass near zero, where a plain relative error says nothing)."""
+    worst = 0.0
+    for _ in range(n):
+        V = torch.randn(X.shape, generator=g, dtype=torch.float64).numpy()
+        fd = (F(X + h * V) - F(X - h * V)) / (2 * h)
+        an = float((G * V).sum())
+        scale = float(np.linalg.norm(G) * np.linalg.norm(V)) / np.sqrt(V.size)
+        worst = max(worst, abs(fd - an) / max(scale, 1e-30))
+    return worst
+
+
+def test_linear_bf16_gradients_vs_fp64_on_bf16_operands(ag):
+    """Forward within 1e-5 of FP64 on the same BF16 operands; dx and dW within 1e-2 of the
+    FP64 gradients and of FP64 central differences (dy is rounded to BF16: 2^-9 per element)."""
+    g = torch.Generator().manual_seed(11)
+    x = torch.randn(37, 70, generator=g).cuda().requires_grad_()
+    w = (torch.randn(50, 70, generator=g) * 0.1).cuda().requires_grad_()
+    b = torch.randn(50, generator=g).cuda().requires_grad_()
+    r = torch.randn(37, 50, generator=g).cuda()
+    y = ag.linear_bf16(x, w, b)
+    (y * r).sum().backward()
+    xh, wh, bn, rn = _bf(x), _bf(w), b.detach().double().cpu().numpy(), r.double().cpu().numpy()
+    assert _rel(y.detach().cpu().numpy(), xh @ wh.T + bn) < 1e-5
+    gx, gw, gb = x.grad.double().cpu().numpy(), w.grad.double().cpu().numpy(), b.grad.double().cpu().numpy()
+    assert _rel(gx, rn @ wh) < 1e-2
+    assert _rel(gw, rn.T @ xh) < 1e-2
+    assert _rel(gb, rn.sum(0)) < 1e-5
+    assert _fd_check(lambda X: float((rn * (X @ wh.T + bn)).sum()), xh, gx, g) < 1e-2
+    assert _fd_check(lambda W: float((rn * (xh @ W.T + bn)).sum()), wh, gw, g) < 1e-2
+
+
+@pytest.mark.parametrize("relu", [False, True])
+def test_conv32_bf16_gradients_vs_oracle(ag, relu):
+    """The tensor-core 32-channel convolution (forward, data gradient, weight gradient) against
+    the oracle's conv3x3 on the same BF16 operands: forward 1e-5, gradients 1e-2 of the
+    oracle's conv3x3_bwd and of FP64 central differences."""
+    g = torch.Generator().manual_seed(12 + relu)
+    x = torch.randn(6, 32, 13, 11, generator=g).cuda().requires_grad_()
+    w = (torch.randn(32, 32, 3, 3, generator=g) * 0.06).cuda().requires_grad_()
+    b = (0.1 * torch.randn(32, generator=g)).cuda().requires_grad_()
+    y = ag.conv32_bf16(x, w, b, relu)
+    r = torch.randn(y.shape, generator=g).cuda()
+    (y * r).sum().backward()
+    xh, wh, bn, rn = _bf(x), _bf(w), b.detach().double().cpu().numpy(), r.double().cpu().numpy()
+    pre = o.conv3x3_fwd(xh, wh, bn, 1)
+    act = (lambda v: np.maximum(v, 0.0)) if relu else (lambda v: v)
+    assert _rel(y.detach().cpu().numpy(), act(pre)) < 1e-5
+    rdx, rdw, rdb = o.conv3x3_bwd(xh, wh, rn * (pre > 0) if relu else rn, 1)
+    gx, gw, gb = x.grad.double().cpu().numpy(), w.grad.double().cpu().numpy(), b.grad.double().cpu().numpy()
+    assert _rel(gx, rdx) < 1e-2 and _rel(gw, rdw) < 1e-2 and _rel(gb, rdb) < 1e-2
+    assert _fd_check(lambda X: float((rn * act(o.conv3x3_fwd(X, wh, bn, 1))).sum()), xh, gx, g) < 1e-2
+    assert _fd_check(lambda W: float((rn * act(o.conv3x3_fwd(xh, W, bn, 1))).sum()), wh, gw, g) < 1e-2
+
+
+def test_mlp_head_bf16_gradients_vs_oracle(ag):
+    """A LayerNorm MLP head through MlpHeadBF16 (fused forward, hand-written backward
+    kernels) against the oracle's mlp_fwd / mlp_bwd on the same BF16 weights and input:
+    output and every gradient within the BF16 bounds (5e-2 relative in norm, cosine > 0.99)."""
+    g = torch.Generator().manual_seed(13)
+    rows, kin, H, nout = 50, 40, 64, 11
+    cfg = dict(hidden=[H, H], ln_eps=1e-5)
+    params, P = [], {}
+    ins = [kin, H, H]
+    for l in range(3):
+        n_out = H if l < 2 else nout
+        w = (torch.rand(n_out, ins[l], generator=g) * 2 - 1) / ins[l] ** 0.5
+        bb = 0.1 * torch.randn(n_out, generator=g)
+        params += [w.cuda().requires_grad_(), bb.cuda().requires_grad_()]
+        P[f"c.fc{l}.w"], P[f"c.fc{l}.b"] = _bf(w), bb.double().numpy()
+        if l < 2:
+            gg, be = 1 + 0.1 * torch.randn(H, generator=g), 0.1 * torch.randn(H, generator=g)
+            params += [gg.cuda().requires_grad_(), be.cuda().requires_grad_()]
+            P[f"c.ln{l}.g"], P[f"c.ln{l}.b"] = gg.double().numpy(), be.double().numpy()
+    x = torch.randn(rows, kin, generator=g).cuda().requires_grad_()
+    out = ag.mlp_head_bf16(x, params)
+    r = torch.randn(rows, nout, generator=g).cuda()
+    (out * r).sum().backward()
+    ref, cache = o.mlp_fwd(P, "c", _bf(x), cfg)
+    assert _rel(out.detach().cpu().numpy(), ref) < 1e-2
+    rdx, rg = o.mlp_bwd(P, "c", cache, r.double().cpu().numpy(), cfg)
+    names = []
+    for l in range(3):
+        names += [f"c.fc{l}.w", f"c.fc{l}.b"] + ([f"c.ln{l}.g", f"c.ln{l}.b"] if l < 2 else [])
+    for name, p in zip(names, params):
+        got, want = p.grad.double().cpu().numpy(), rg[name]
+        cos = float((got.ravel() @ want.ravel()) / max(np.linalg.norm(got) * np.linalg.norm(want), 1e-30))
+        assert _rel(got, want) < 5e-2 and cos > 0.99, (name, _rel(got, want), cos)
+    gx = x.grad.double().cpu().numpy()
+    assert _rel(gx, rdx) < 5e-2
