@@ -45,9 +45,9 @@ UPDATE_FLOPS = 27.96e9
 # in one update; ncu replays each launch with cold caches), keyed by (class,
 # precision).  Set back to nothing when the kernel changes.
 NCU_TRAFFIC = {
-    # train_b512: 14 forward GEMM launches of one BF16 update, 30.42 MB read, 0 written
+    # train_b512: the four fused head launches of one BF16 update, 8.09 MB read, 0 written
     # (ncu dram__bytes_read.sum + dram__bytes_write.sum, second update of the small-ring run)
-    ("tc_gemm_fwd", "bf16", "train_b512"): 2172709,
+    ("mlp_tc_fwd", "bf16", "train_b512"): 2023680,
 }
 
 
