@@ -197,6 +197,17 @@ const char* squint_phase_name(int i);
 int squint_profile_kernels(squint_handle* h, int cap, char* names, int* launches, float* ms, double* work, int* unit,
                            int* n, void* stream);
 
+/*
+ * A timeline of one update as the timed graph runs it (its concurrent branches kept):
+ * every launch bracketed by CUDA events.  For launch i < *n (at most cap written, in
+ * issue order): names + 32 i its kernel class (NUL-terminated), lanes[i] the branch it
+ * ran on (0: the main stream; 1 ..: the learner's side streams), t0[i] and t1[i] its
+ * start and end in ms after the update's start.  The event pairs themselves add a
+ * little time per launch.  Waits for the stream.
+ */
+int squint_trace_update(squint_handle* h, int cap, char* names, int* lanes, float* t0, float* t1, int* n,
+                        void* stream);
+
 /* ------------------------------------------------------------------ inference */
 
 /* One actor query: n environments of one group (Alg. 1, "Sample a_t ~ pi"). */

@@ -39,6 +39,33 @@ int squint_op_gemm(int dtype, int M, int N, int K, const void* A, int64_t sa_m, 
 
 
 /*
+ * The input-gradient chain of the same head in one BF16 tensor-core launch (the
+ * backward of the critic and actor MLPs in Alg. 1's critic and actor steps):
+ *   dpost_{nh-1} = dout W_nh;  for l = nh-1 .. 0: dn = dpost_l (x) [post_l > 0],
+ *   dxh = dn (x) g_l, dpre_l = rstd_l (dxh - mean_row(dxh) - xhat_l mean_row(dxh (x) xhat_l))
+ *   with xhat_l = (pre_l - mean_l) rstd_l;  dpost_{l-1} = dpre_l W_l (l > 0);
+ *   dx = dpre_0 W_0[:, c0 : c0 + ncols].
+ * dout BF16 [M, nout] (row stride ld_dout, a multiple of 8); w, ldw as for
+ * squint_op_mlp_bf16; g[l] FP32; pre[l], post[l] FP32 [M, H] and mean[l], rstd[l] [M]:
+ * the forward's saves.  beta (optional, every hidden layer's LayerNorm shift): the mask
+ * [post_l > 0] is rebuilt as [fma(g_l, xhat_l, beta_l) > 0], the rounding with which
+ * squint_op_mlp_bf16 forms post_l, and post may be NULL; without beta post is read.
+ * Every dpre_l is rounded to BF16 before the next product reads it.
+ * Optional per hidden layer (NULL arrays or entries): dpre_bf[l] BF16 [M, H], and
+ * colpart[l] FP32 [ceil(M / 128)][3][H], per 128-row block the column sums of dn xhat,
+ * dn and dpre (FP32, before rounding), whose sums over the row blocks are the LayerNorm
+ * gain, shift and the linear bias gradients.  dx FP32 [M, ncols] (row stride lddx).
+ * Shapes: those of squint_op_mlp_bf16, c0 a multiple of 8, c0 + ncols <= kin, and ncols
+ * a multiple of 64 per CTA of the cluster the kernel picks, or at most 64 (SQUINT_EINVAL
+ * otherwise).
+ */
+int squint_op_mlp_bwd_bf16(int M, int kin, int nh, int H, int nout, const void* dout, int64_t ld_dout,
+                           const void* const* w, const int64_t* ldw, const float* const* g,
+                           const float* const* beta, const float* const* pre, const float* const* post,
+                           const float* const* mean, const float* const* rstd, void* const* dpre_bf,
+                           float* const* colpart, int c0, int ncols, float* dx, int64_t lddx, void* stream);
+
+/*
  * FP32 rows to BF16 rows with round-to-nearest-even (the rounding of every BF16 operand
  * the tensor-core path reads): dst[r, c] = bf16(src[r, c]) for c < cols, and zero in the
  * pad columns cols <= c < ld_dst.  Row strides in elements.

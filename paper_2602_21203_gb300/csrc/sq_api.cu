@@ -340,6 +340,13 @@ int squint_profile_update(squint_handle* h, float* ms, int cap, int* n_phases, v
 
 const char* squint_phase_name(int i) { return sq::phase_name(i); }
 
+int squint_trace_update(squint_handle* h, int cap, char* names, int* lanes, float* t0, float* t1, int* n, void* stream) {
+    if (!h || cap < 0 || !names || !lanes || !t0 || !t1 || !n) return SQUINT_EINVAL;
+    if (h->failed) return SQUINT_ESTATE;
+    if (!h->has_ring) return SQUINT_ESTATE;
+    return h->trace_update(cap, names, lanes, t0, t1, n, (cudaStream_t)stream);
+}
+
 int squint_profile_kernels(squint_handle* h, int cap, char* names, int* launches, float* ms, double* work, int* unit,
                            int* n, void* stream) {
     if (!h || cap < 0 || !names || !launches || !ms || !work || !unit || !n) return SQUINT_EINVAL;

@@ -18,6 +18,15 @@
 
 namespace sq {
 
+// The scheduling priority of a launch: its stream's (kept by graph kernel nodes, so a
+// graph instantiated to use node priorities schedules each branch's blocks as its
+// stream would).
+inline int stream_priority(cudaStream_t s) {
+    int p = 0;
+    if (cudaStreamGetPriority(s, &p) != cudaSuccess) p = 0;
+    return p;
+}
+
 // Launch with programmatic stream serialization allowed (inside graphs: a programmatic edge).
 template <typename... KArgs, typename... Args>
 inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args&&... args) {
@@ -26,11 +35,13 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
+    at[1].id = cudaLaunchAttributePriority;
+    at[1].val.priority = stream_priority(s);
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
@@ -43,15 +54,17 @@ inline void launch_kc(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sm
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[2];
+    cudaLaunchAttribute at[3];
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
-    at[1].id = cudaLaunchAttributeClusterDimension;
-    at[1].val.clusterDim.x = cluster.x;
-    at[1].val.clusterDim.y = 1;
-    at[1].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributePriority;
+    at[1].val.priority = stream_priority(s);
+    at[2].id = cudaLaunchAttributeClusterDimension;
+    at[2].val.clusterDim.x = cluster.x;
+    at[2].val.clusterDim.y = 1;
+    at[2].val.clusterDim.z = 1;
     cfg.attrs = at;
-    cfg.numAttrs = cluster.x > 1 ? 2 : 1;
+    cfg.numAttrs = cluster.x > 1 ? 3 : 2;
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 

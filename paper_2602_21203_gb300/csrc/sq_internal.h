@@ -59,6 +59,7 @@ struct MlpBufs {
     float* out = nullptr;                        // [E, rows, n_out]
     std::vector<float*> lnterms;                 // per hidden layer: [E][2][rows, n] deferred
                                                  // LayerNorm column-sum terms (backward with weights)
+    bool tc_saved = false;                       // the saves were written by the fused forward kernel
 };
 
 // BF16 padded copy of one linear layer's weight (online and, for the critic range, target).
@@ -112,9 +113,17 @@ struct squint_handle {
     bool draw_ahead = true;
     // head MLP chains of the BF16 learner as one fused tensor-core launch each
     // (SQUINT_MLP_FUSED=0 at creation: a GEMM and a LayerNorm launch per layer instead);
-    // SQUINT_MLP_CL=1/2/4 forces the cluster size of the fused launches
+    // SQUINT_MLP_CL=1/2/4/8 forces the cluster size of the fused launches.  The backward
+    // chains run as GEMMs beside LayerNorm-backward launches unless SQUINT_MLP_BWD=1 (one
+    // fused chain launch each; SQUINT_MLP_BWD_CL: its cluster size): inside the update's
+    // concurrent graph the GEMM path measures faster, the clusters of the fused launch
+    // waiting for free SMs beside the encoder backward
     bool mlp_fused = true;
     int mlp_cluster = 0;
+    bool mlp_bwd_fused = false;
+    int mlp_bwd_cluster = 0;
+    // branch priorities (SQUINT_PRIO=0 at creation: every stream at the default priority)
+    bool prio_branches = true;
     bool launch_failed = false;       // a tensor map could not describe an operand
     // bounded waits of the update's tensor-core GEMMs (cycles 0: the default limit) and
     // the failure-test switch that makes them run out (squint_set_debug)
@@ -200,6 +209,9 @@ struct squint_handle {
     const float* dconv0 = nullptr;
     float* dxq = nullptr;             // [B, Dc] input gradient of the critics in the actor step
     float* ln_work = nullptr;         // LayerNorm backward column partials
+    // fused head backward: per hidden layer [2][row blocks][3][H] column sums of each 128-row
+    // block (LayerNorm gain, shift and bias gradients once the row blocks are added)
+    std::vector<float*> mlp_colpart;
     float* dout_a = nullptr;          // [B, 2A]
 
     // BF16 shadows (tensor-core path)
@@ -255,7 +267,7 @@ struct squint_handle {
     cudaEvent_t fork_ev[32] = {};
     int fork_next = 0;
     bool serial = false;                  // profiling: every launch in order on the main stream
-    struct ProfEntry { const char* name; cudaEvent_t a, b; double work; int unit; };
+    struct ProfEntry { const char* name; cudaEvent_t a, b; double work; int unit; int lane; };
     std::vector<ProfEntry>* prof = nullptr;   // per-launch records while profiling kernels
     // stream of branch i (the main stream itself when serial)
     cudaStream_t branch(cudaStream_t main, int i) const { return serial ? main : side[i]; }
@@ -268,6 +280,15 @@ struct squint_handle {
     }
     int profile_kernels(int cap, char* names, int* launches, float* ms, double* work, int* unit, int* n,
                         cudaStream_t s);
+    int trace_update(int cap, char* names, int* lanes, float* t0, float* t1, int* n, cudaStream_t s);
+    // one update captured with an event pair around every launch and replayed
+    int replay_profiled(std::vector<ProfEntry>& recs, bool in_order, cudaEvent_t base, cudaStream_t s);
+    // the branch a stream is: 0 the main stream, i + 1 side[i]
+    int lane_of(cudaStream_t st) const {
+        for (int i = 0; i < 5; ++i)
+            if (side[i] && st == side[i]) return i + 1;
+        return 0;
+    }
     std::vector<cudaEvent_t>* phase_events = nullptr;   // set while profiling an eager update
     // timing event on `s`; under stream capture it becomes an event-record node of the graph
     static void record_timing(cudaEvent_t e, cudaStream_t s) {

@@ -250,10 +250,13 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
                 q.out = mb.out + (int64_t)e * rows * nout; q.ldo = nout;
             }
             ProfScope ps(h, s, "mlp_tc_fwd", flops, 0);
-            if (launch_mlp_tc(pr, E, nh, H, nout, (float)h->c.ln_eps, h->d_err, &h->gemm_wait, s, h->mlp_cluster) == 0)
+            if (launch_mlp_tc(pr, E, nh, H, nout, (float)h->c.ln_eps, h->d_err, &h->gemm_wait, s, h->mlp_cluster) == 0) {
+                if (keep) mb.tc_saved = true;
                 return;
+            }
         }
     }
+    mb.tc_saved = false;
     for (int l = 0; l <= nh; ++l) {
         // the hidden layers' LayerNorm (+ReLU) problems; on the tensor-core path the GEMM
         // computes them in its epilogue
@@ -297,6 +300,112 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
 
 namespace {
 
+// The BF16 backward through a head MLP with the fused chain kernel: one launch for the
+// input-gradient chain and every hidden LayerNorm backward (the input gradient itself in
+// the same launch for one parameter set, else one GEMM that adds the sets' products);
+// the weight gradients (GEMMs) and the gain, shift and bias gradients (column sums of
+// the kernel's per-row-block sums) on `side`.  False (nothing launched) if the shapes
+// are outside the kernel's range.
+bool fused_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* sets, float* grads, int E, const Mat& X,
+                    int rows, const Mat& dout, int ncols, float* dX, int64_t lddx, const float* mask, int64_t ldmask,
+                    cudaStream_t s, cudaStream_t side, int col0, bool join) {
+    const int nh = (int)sets[0].size() - 1;
+    const int R = mb.rows;
+    const int H = sets[0][0].out, nout = sets[0][nh].out, kin = sets[0][0].in;
+    if (mb.posth.empty() || (grads && (int)h->mlp_colpart.size() < nh)) return false;
+    for (int l = 0; l < nh; ++l)
+        if (sets[0][l].out != H) return false;
+    for (int e = 0; e < E; ++e)
+        for (int l = 0; l <= nh; ++l)
+            if (!sets[e][l].wh) return false;
+    const int fcl = h->mlp_bwd_cluster;
+    if (!mlp_bwd_tc_supported(nh, H, nout, kin, 0, 0, fcl)) return false;
+    const bool fin = dX && ncols > 0 && E == 1 && !mask && mlp_bwd_tc_supported(nh, H, nout, kin, col0, ncols, fcl);
+    const int nrb = (rows + 127) / 128;
+    auto G = [&](const float* p) { return grads + (p - h->params); };
+    auto post = [&](int l, int e) {
+        Mat m;
+        m.f = mb.post[l] + ((int64_t)e * R + r0) * H; m.ld = H;
+        m.h = mb.posth[l] + ((int64_t)e * R + r0) * H; m.ldh = H;
+        return m;
+    };
+    auto dpre = [&](int l, int e) {
+        Mat m;
+        m.f = h->dpre[l] + (int64_t)e * rows * H; m.ld = H;
+        m.h = h->dpre_h[l] + (int64_t)e * rows * H; m.ldh = H;
+        return m;
+    };
+    auto dout_e = [&](int e) {
+        Mat m = dout;
+        m.f += (int64_t)e * rows * dout.ld;
+        m.h += (int64_t)e * rows * dout.ldh;
+        return m;
+    };
+    if (grads) {   // the output layer's weight and bias gradients need only dout
+        h->fork(s, side);
+        {
+            GemmBuilder gb(h, side, true);
+            for (int e = 0; e < E; ++e) gb.dw(dout_e(e), rows, post(nh - 1, e), sets[e][nh], G(sets[e][nh].w));
+        }
+        ColSumProblem cs[2];
+        for (int e = 0; e < E; ++e) cs[e] = ColSumProblem{rows, nout, dout_e(e).f, dout.ld, G(sets[e][nh].b)};
+        ProfScope ps(h, side, "colsum", 4.0 * E * rows * nout, 1);
+        launch_colsum(cs, E, side);
+    }
+    MlpTcBwdProblem pr[kMlpMaxProbs];
+    double flops = 0;
+    for (int e = 0; e < E; ++e) {
+        MlpTcBwdProblem& q = pr[e];
+        std::memset(&q, 0, sizeof(q));
+        q.M = rows; q.dout = dout_e(e).h; q.ld_dout = dout.ldh;
+        for (int l = 0; l <= nh; ++l) {
+            q.w[l] = sets[e][l].wh; q.ldw[l] = sets[e][l].ldh;
+            if (l == nh) break;
+            const int64_t off = ((int64_t)e * R + r0) * H;
+            q.g[l] = sets[e][l].g;
+            // the fused forward's saves: the ReLU mask is rebuilt from pre, g and beta
+            if (mb.tc_saved) q.beta[l] = sets[e][l].beta;
+            q.pre[l] = mb.pre[l] + off; q.post[l] = mb.post[l] + off;
+            q.mean[l] = mb.mean[l] + (int64_t)e * R + r0; q.rstd[l] = mb.rstd[l] + (int64_t)e * R + r0;
+            if (grads || (l == 0 && !fin)) q.dpre_bf[l] = dpre(l, e).h;
+            if (grads) q.colpart[l] = h->mlp_colpart[l] + (int64_t)e * nrb * 3 * H;
+        }
+        if (fin) { q.dx = dX; q.lddx = lddx; }
+        flops += 2.0 * rows * ((double)nout * H + (double)(nh - 1) * H * H + (fin ? (double)H * ncols : 0.0));
+    }
+    {
+        ProfScope ps(h, s, "mlp_tc_bwd", flops, 0);
+        if (launch_mlp_bwd_tc(pr, E, nh, H, nout, kin, fin ? col0 : 0, fin ? ncols : 0, h->d_err, &h->gemm_wait, s, fcl) != 0)
+            h->launch_failed = true;
+    }
+    if (!fin && dX && ncols > 0) {   // the input gradient summed over the parameter sets
+        GemmBuilder gb(h, s, true);
+        Mat d[2] = {dpre(0, 0), E > 1 ? dpre(0, 1) : dpre(0, 0)};
+        LayerRef w[2] = {sets[0][0], E > 1 ? sets[1][0] : sets[0][0]};
+        gb.dx(d, w, E, rows, col0, ncols, dX, lddx, mask, ldmask);
+    }
+    if (grads) {
+        h->fork(s, side);
+        {
+            GemmBuilder gb(h, side, true);
+            for (int l = nh - 1; l >= 0; --l)
+                for (int e = 0; e < E; ++e) gb.dw(dpre(l, e), rows, l == 0 ? X : post(l - 1, e), sets[e][l], G(sets[e][l].w));
+        }
+        std::vector<ColSumProblem> cs;
+        for (int l = 0; l < nh; ++l)
+            for (int e = 0; e < E; ++e) {
+                const float* part = h->mlp_colpart[l] + (int64_t)e * nrb * 3 * H;
+                cs.push_back(ColSumProblem{nrb, H, part, 3 * H, G(sets[e][l].g)});
+                cs.push_back(ColSumProblem{nrb, H, part + H, 3 * H, G(sets[e][l].beta)});
+                cs.push_back(ColSumProblem{nrb, H, part + 2 * H, 3 * H, G(sets[e][l].b)});
+            }
+        ProfScope ps(h, side, "colsum", 4.0 * cs.size() * nrb * H, 1);
+        launch_colsum(cs.data(), (int)cs.size(), side);
+        if (join) h->fork(side, s);
+    }
+    return true;
+}
+
 // Backward through an MLP evaluated by E online parameter sets.  dout [E, rows, n_out]
 // (FP32 + BF16 shadow); activations stored with R rows per set, read from row r0.
 // Parameter gradients land at the canonical offsets of `grads` (null: input gradient
@@ -304,12 +413,16 @@ namespace {
 // [col0, col0 + ncols) into dX[:, 0 .. ncols).
 void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* sets, float* grads, int E, const Mat& X,
                   int rows, const Mat& dout, int ncols, float* dX, int64_t lddx, const float* mask, int64_t ldmask,
-                  cudaStream_t s, cudaStream_t side, int col0 = 0) {
+                  cudaStream_t s, cudaStream_t side, int col0 = 0, bool join = true) {
     // weight and bias gradients go to `side` as soon as their inputs exist; the main
     // stream carries only the chain of input gradients; `side` is joined at the end
+    // (join = false: the caller joins it later)
     const bool bf = h->bf16;
     const int nh = (int)sets[0].size() - 1;
     const int R = mb.rows;
+    if (bf && h->mlp_fused && h->mlp_bwd_fused && dout.h && rows > 0 && E <= kMlpMaxProbs &&
+        fused_backward(h, mb, r0, sets, grads, E, X, rows, dout, ncols, dX, lddx, mask, ldmask, s, side, col0, join))
+        return;
     auto G = [&](const float* p) { return grads + (p - h->params); };
     auto post = [&](int l, int e) {
         const int n = sets[e][l].out;
@@ -398,7 +511,7 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
         LayerRef w[2] = {sets[0][0], E > 1 ? sets[1][0] : sets[0][0]};
         gb.dx(d, w, E, rows, col0, ncols, dX, lddx, mask, ldmask);
     }
-    if (grads) h->fork(side, s);
+    if (grads && join) h->fork(side, s);
 }
 
 void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, int E, int rows, bool terms = false) {
@@ -428,6 +541,9 @@ int squint_handle::allocate() {
     if (const char* e = std::getenv("SQUINT_DRAW_AHEAD")) draw_ahead = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_FUSED")) mlp_fused = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_CL")) mlp_cluster = std::atoi(e);
+    if (const char* e = std::getenv("SQUINT_MLP_BWD")) mlp_bwd_fused = std::atoi(e) != 0;
+    if (const char* e = std::getenv("SQUINT_PRIO")) prio_branches = std::atoi(e) != 0;
+    if (const char* e = std::getenv("SQUINT_MLP_BWD_CL")) mlp_bwd_cluster = std::atoi(e);
     bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
     SQ_CK(this, cudaGetDevice(&device));
     const int64_t n = L.total;
@@ -524,6 +640,9 @@ int squint_handle::allocate() {
         if (ln_work) cudaMemset(ln_work, 0, kLnTickets * sizeof(float));
     }
     ln_prepare();
+    if (bf16)
+        for (int l = 0; l < c.n_hidden; ++l)
+            mlp_colpart.push_back(dalloc<float>((int64_t)2 * ((B + 127) / 128) * 3 * std::max(c.hidden[l], 1)));
     dout_a = dalloc<float>((int64_t)B * 2 * A);
     if (bf16) {
         // padded BF16 weight copies: online for every linear layer, target for the critic range
@@ -696,10 +815,24 @@ int squint_handle::allocate() {
         if (tc_conv) policy_wconv_scratch = dalloc<__nv_bfloat16>(9 * 32 * 32);
         tc_prepare();
         mlp_tc_prepare();
+        mlp_bwd_tc_prepare();
     }
     if (cudaMallocHost(&h_stats, sizeof(float) * 8 * c.max_k) != cudaSuccess) return SQUINT_ENOMEM;
-    SQ_CK(this, cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
-    for (auto& st : side) SQ_CK(this, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    {
+        // the update's critical chain (main stream; weight gradients, critic forward and
+        // polyak branches, which it joins) one level below the serving streams; the
+        // encoder backward (which has slack until the update ends) and the next update's
+        // front end at the lowest priority
+        int least = 0, greatest = 0;
+        SQ_CK(this, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        const int crit = greatest < least ? greatest + 1 : greatest;
+        SQ_CK(this, cudaStreamCreateWithPriority(&capture_stream, cudaStreamNonBlocking, prio_branches ? crit : 0));
+        for (int i = 0; i < 5; ++i) {
+            const bool low = i == 0 || i == 3 || i == 4;
+            SQ_CK(this, cudaStreamCreateWithPriority(&side[i], cudaStreamNonBlocking,
+                                                     prio_branches ? (low ? least : crit) : 0));
+        }
+    }
     for (auto& e : fork_ev) SQ_CK(this, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (int i = 0; i < 2; ++i) SQ_CK(this, cudaEventCreateWithFlags(&policy_ready[i], cudaEventDisableTiming));
     arenas.push_back(&arena);
@@ -1031,8 +1164,9 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
     {
         const Mat dl{dlogits, K, dlogits_h, K8};
         const float* mask = Dd > 0 ? nullptr : z;      // flatten path: mask by the last conv's ReLU
+        // (with a projection its backward below joins s2 before the critic Adam)
         mlp_backward(this, crit_mlp, 0, crit_on, G, E, Mat{xc, Dc, xc_h, Dc8}, B, dl, Z, Dd > 0 ? dh : dz,
-                     Dd > 0 ? Z : F, mask, F, s, s2);
+                     Dd > 0 ? Z : F, mask, F, s, s2, 0, Dd == 0);
         if (Dd > 0) {
             const LayerRef cp = layer_ref(this, L.cproj, false);
             LnBwdProblem p{};
@@ -1274,8 +1408,11 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
             ProfScope ps(this, s, "heads_losses", 0, 1);
             launch_actor_head_bwd(hb, s);
         }
+        // the actor MLP's weight gradients stay on s2 beside the projection's backward and
+        // are joined before the actor Adam
         mlp_backward(this, actor_mlp, B, &actor_on, G, 1, Mat{xa, Da, xa_h, Da8}.rows(B), B,
-                     Mat{dout_a, 2 * A, dout_ah, pad8(2 * A)}, Z, Dd > 0 ? dh : nullptr, Z, nullptr, 0, s, s2);
+                     Mat{dout_a, 2 * A, dout_ah, pad8(2 * A)}, Z, Dd > 0 ? dh : nullptr, Z, nullptr, 0, s, s2, 0,
+                     false);
         if (Dd > 0) {
             const LayerRef ap = layer_ref(this, L.aproj, false);
             LnBwdProblem p{};
@@ -1296,6 +1433,7 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
             GemmBuilder gb(this, s, bf16);
             gb.dw(Mat{dproj, Dd, dproj_h, Dd}, B, zt, ap, G + L.aproj.w);
         }
+        fork(s2, s);
         adam(L.actor_begin, L.actor_end, d_steps + 1, d_do_actor, s, bf16 ? &seg_actor : nullptr);
         quantize_weights(quant_actor, s);
     }
@@ -1351,7 +1489,8 @@ int squint_handle::run_updates(int k, squint_update_stats* stats, cudaStream_t s
             }
             graph_kernels[k] = kernels;
             cudaGraphExec_t exec;
-            SQ_CK(this, cudaGraphInstantiate(&exec, graph, 0));
+            SQ_CK(this, cudaGraphInstantiateWithFlags(&exec, graph,
+                                                      prio_branches ? cudaGraphInstantiateFlagUseNodePriority : 0));
             cudaGraphDestroy(graph);
             it = graphs.emplace(k, exec).first;
         }
@@ -1438,15 +1577,14 @@ int squint_handle::profile_update(float* ms, int cap, int* n_phases, cudaStream_
 // One update with every launch in order on one stream, each bracketed by its own
 // events, captured as a graph and replayed (so the host's launch cost does not show up
 // as device time); launches are grouped by kernel class.  The replay is one real update.
-int squint_handle::profile_kernels(int cap, char* names, int* launches, float* ms, double* work, int* unit, int* n,
-                                   cudaStream_t s) {
-    std::vector<ProfEntry> recs;
+int squint_handle::replay_profiled(std::vector<ProfEntry>& recs, bool in_order, cudaEvent_t base, cudaStream_t s) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     SQ_CK(this, cudaStreamSynchronize(s));
     SQ_CK(this, cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
+    if (base) record_timing(base, capture_stream);
     prof = &recs;
-    serial = true;
+    serial = in_order;
     record_update(0, 1, capture_stream, false);
     serial = false;
     prof = nullptr;
@@ -1455,6 +1593,43 @@ int squint_handle::profile_kernels(int cap, char* names, int* launches, float* m
     if (rc == SQUINT_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) rc = SQUINT_ECUDA;
     if (rc == SQUINT_OK && cudaGraphLaunch(exec, s) != cudaSuccess) rc = SQUINT_ECUDA;
     if (rc == SQUINT_OK && cudaStreamSynchronize(s) != cudaSuccess) rc = SQUINT_ECUDA;
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+}
+
+// One update as the timed graph runs it (concurrent branches), with an event pair around
+// every launch: each launch's start and end relative to the update's start, and its branch.
+int squint_handle::trace_update(int cap, char* names, int* lanes, float* t0, float* t1, int* n, cudaStream_t s) {
+    std::vector<ProfEntry> recs;
+    cudaEvent_t base = nullptr;
+    SQ_CK(this, cudaEventCreate(&base));
+    int rc = replay_profiled(recs, false, base, s);
+    for (size_t i = 0; i < recs.size(); ++i) {
+        const ProfEntry& e = recs[i];
+        float a = 0.f, b = 0.f;
+        if (rc == SQUINT_OK && (cudaEventElapsedTime(&a, base, e.a) != cudaSuccess ||
+                                cudaEventElapsedTime(&b, base, e.b) != cudaSuccess))
+            rc = SQUINT_ECUDA;
+        if (rc == SQUINT_OK && (int)i < cap) {
+            std::snprintf(names + 32 * i, 32, "%s", e.name);
+            lanes[i] = e.lane;
+            t0[i] = a;
+            t1[i] = b;
+        }
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    cudaEventDestroy(base);
+    if (rc != SQUINT_OK) { failed = true; g_last_error = "update trace failed"; return rc; }
+    *n = (int)recs.size();
+    return SQUINT_OK;
+}
+
+int squint_handle::profile_kernels(int cap, char* names, int* launches, float* ms, double* work, int* unit, int* n,
+                                   cudaStream_t s) {
+    std::vector<ProfEntry> recs;
+    int rc = replay_profiled(recs, true, nullptr, s);
     std::vector<std::string> order;
     std::map<std::string, std::tuple<int, double, double, int>> agg;
     for (auto& e : recs) {
@@ -1472,8 +1647,6 @@ int squint_handle::profile_kernels(int cap, char* names, int* launches, float* m
         cudaEventDestroy(e.a);
         cudaEventDestroy(e.b);
     }
-    if (exec) cudaGraphExecDestroy(exec);
-    if (graph) cudaGraphDestroy(graph);
     if (rc != SQUINT_OK) { failed = true; g_last_error = "kernel profiling failed"; return rc; }
     *n = (int)order.size();
     for (int i = 0; i < (int)order.size() && i < cap; ++i) {

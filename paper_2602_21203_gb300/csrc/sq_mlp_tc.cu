@@ -463,13 +463,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] += y[j];
                     ld_par32(pg + c, y);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) y[j] *= (v[j] - mean) * rstd;
-                    {
+                    {   // g xhat + beta rounded once: the backward rebuilds the ReLU mask the same way
                         float bt[32];
                         ld_par32(pbeta + c, bt);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) y[j] = fmaxf(y[j] + bt[j], 0.f);
+                        for (int j = 0; j < 32; ++j) y[j] = fmaxf(__fmaf_rn(y[j], (v[j] - mean) * rstd, bt[j]), 0.f);
                     }
                     if (s_pre) store_rows_coalesced(stg_w, v, s_pre, H, m0 + warp * 32, M, c0 + c, lane);
                     if (s_post) store_rows_coalesced(stg_w, y, s_post, H, m0 + warp * 32, M, c0 + c, lane);
@@ -580,6 +578,473 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const __grid_consta
     }
 }
 
+// ============================================================================ backward
+// The input-gradient chain of a LayerNorm MLP head (Alg. 1's critic and actor steps):
+//   step 0          dpost_{nh-1} = dout W_nh
+//   hidden lh       dpre_lh = LayerNorm(+ReLU) backward of dpost_lh (Ba et al.):
+//                   dn = dpost (x) [post > 0], dxh = dn (x) g,
+//                   dpre = rstd (dxh - mean(dxh) - xhat mean(dxh (x) xhat)),
+//                   then dpost_{lh-1} = dpre_lh W_lh (lh > 0)
+//   final           dX[:, c0 : c0 + ncols] = dpre_0 W_0[:, c0 : c0 + ncols]
+// in one launch, with the same cluster split as the forward: CTA q computes columns
+// [q NS, (q + 1) NS) of every hidden gradient (tcgen05 M = 128, N = NS, the weights as
+// MN-major operands streamed by TMA), xhat and dxh kept in tensor memory between the
+// two LayerNorm passes, the row sums of dxh and dxh xhat exchanged with st.async, the
+// BF16 dpre slice copied to the other CTAs by bulk copies.  Per hidden layer the kernel
+// also leaves what the weight gradients need: dpre in BF16 (TMA store) and, per 128-row
+// block, the column sums of dn xhat, dn and dpre (the LayerNorm gain, shift and bias
+// gradients once the row blocks are added).  The final step is split over the output
+// columns (each CTA ncols / CL of them) or, for a few columns, over K (each CTA its own
+// dpre_0 slice; the partial tiles added in rank order by the CTA owning each band of rows).
+struct MlpBwdProbDev {
+    CUtensorMap tdo;                          // dout [M, nout], box 64 x 128 (K-major A of step 0)
+    CUtensorMap tw[kMlpMaxHidden + 1];        // W_l [out_l, in_l] as MN-major B: dims {in_l, out_l}, box 64 x 64
+    CUtensorMap tdp[kMlpMaxHidden];           // dpre of hidden layer l, BF16 [M, H], box 64 x 128 (store)
+    const float* g[kMlpMaxHidden];
+    const float* beta[kMlpMaxHidden];         // set: the ReLU mask is rebuilt from pre
+    const float* pre[kMlpMaxHidden];
+    const float* post[kMlpMaxHidden];
+    const float* mean[kMlpMaxHidden];
+    const float* rstd[kMlpMaxHidden];
+    float* colpart[kMlpMaxHidden];            // [row blocks][3][H] or null
+    int has_dp[kMlpMaxHidden];
+    float* dx; int64_t lddx;
+    int M, cta0;
+};
+struct MlpBwdArgs {
+    MlpBwdProbDev p[kMlpMaxProbs];
+    int n_probs, nh, H, CL, NS, nko;
+    int c0, ncols, nfin, fin_ksplit;   // ncols = 0: no final step (the chain stops at dpre_0)
+    int stages, stage_bytes, a_bytes, ldr;
+    uint32_t tmem_cols;
+    int* err;
+    long long wait_limit;
+};
+
+// MN-major operand tile: 64-wide blocks of 64 K rows (128-byte swizzled), the blocks 8 KB
+// apart along MN; the descriptor of K step kk of a slab.
+__device__ __forceinline__ uint64_t sw128_desc_mn(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)(8192 >> 4) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+__host__ __device__ constexpr uint32_t idesc_bf16_kn(int M, int N) {   // A K-major, B MN-major
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+        "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]),
+        "f"(v[19]), "f"(v[20]), "f"(v[21]), "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]),
+        "f"(v[28]), "f"(v[29]), "f"(v[30]), "f"(v[31])
+        : "memory");
+}
+// Row `lane` of this warp's rows [row0, row0 + 32), columns [col, col + 32) of src, read as
+// coalesced 128-byte row segments through the warp's staging tile (rows >= M read as 0).
+__device__ __forceinline__ void load_rows_coalesced(float* stg, const float* src, int64_t ld, int row0, int M, int col,
+                                                    int lane, float (&v)[32]) {
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int rr = 4 * i + lane / 8;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row0 + rr < M) x = *reinterpret_cast<const float4*>(src + (int64_t)(row0 + rr) * ld + col + 4 * (lane % 8));
+        *reinterpret_cast<float4*>(stg + rr * STG_LD + 4 * (lane % 8)) = x;
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(stg + lane * STG_LD + j);
+        v[j] = x.x; v[j + 1] = x.y; v[j + 2] = x.z; v[j + 3] = x.w;
+    }
+}
+// The two halves of load_rows_coalesced, for software pipelining: issue the eight 16-byte
+// reads of a 32 x 32 tile (kept in flight in registers), then pass them through the
+// staging tile into row `lane`.
+__device__ __forceinline__ void issue_rows(float4 (&pf)[8], const float* src, int64_t ld, int row0, int M, int col,
+                                           int lane) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int rr = 4 * i + lane / 8;
+        pf[i] = row0 + rr < M ? __ldg(reinterpret_cast<const float4*>(src + (int64_t)(row0 + rr) * ld + col + 4 * (lane % 8)))
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+__device__ __forceinline__ void stage_rows(float* stg, const float4 (&pf)[8], int lane, float (&v)[32]) {
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) *reinterpret_cast<float4*>(stg + (4 * i + lane / 8) * STG_LD + 4 * (lane % 8)) = pf[i];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(stg + lane * STG_LD + j);
+        v[j] = x.x; v[j + 1] = x.y; v[j + 2] = x.z; v[j + 3] = x.w;
+    }
+}
+// Column sums (as warp_col_sum) of the elementwise product a (x) b.
+__device__ __forceinline__ float warp_col_sum_prod(float* stg, const float (&a)[32], const float (&b)[32], int lane) {
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4*>(stg + lane * STG_LD + j) =
+            make_float4(a[j] * b[j], a[j + 1] * b[j + 1], a[j + 2] * b[j + 2], a[j + 3] * b[j + 3]);
+    __syncwarp();
+    float t = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) t += stg[rr * STG_LD + lane];
+    return t;
+}
+// Sum over this warp's 32 rows of each of 32 columns (lane j returns column j's sum, rows
+// added in order) through the warp's staging tile.
+__device__ __forceinline__ float warp_col_sum(float* stg, const float (&v)[32], int lane) {
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4*>(stg + lane * STG_LD + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    __syncwarp();
+    float t = 0.f;
+#pragma unroll
+    for (int rr = 0; rr < 32; ++rr) t += stg[rr * STG_LD + lane];
+    return t;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) mlp_bwd_tc_kernel(const __grid_constant__ MlpBwdArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int S = a.stages;
+    const int CL = a.CL, NS = a.NS, H = a.H, nh = a.nh, nfin = a.nfin;
+    const bool ksplit = a.fin_ksplit != 0;
+    const int nsteps = nh + (a.ncols > 0 ? 1 : 0);
+    const uint32_t a_base = smem_u32(smem);
+    const uint32_t ring = a_base + a.a_bytes;
+    float* ring_f = reinterpret_cast<float*>(smem + a.a_bytes);
+    float* stg = reinterpret_cast<float*>(smem + a.a_bytes + S * a.stage_bytes);
+    float* xbuf = stg + 4 * 32 * STG_LD;                                 // [2][CL][BM][2]: row sums of each CTA
+    float* colacc = xbuf + 2 * CL * BM * 2;                              // [4 warps][3][NS] column sums
+    float* par = colacc + 4 * 3 * NS;                                    // g (then beta) slices of the hidden layers
+    uint64_t* bars = reinterpret_cast<uint64_t*>(par + ((2 * nh * NS + 3) / 4) * 4);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2 * S + 6);     // tmem address, issued, consumed
+    const uint32_t bar0 = smem_u32(bars);
+    auto full = [&](int s) { return bar0 + 8 * s; };
+    auto empty = [&](int s) { return bar0 + 8 * (S + s); };
+    const uint32_t a0_full = bar0 + 8 * (2 * S), acc_full = a0_full + 8, a_ready = a0_full + 16;
+    const uint32_t xbar0 = a0_full + 24, out_bar = a0_full + 40;
+
+    int pi = 0;
+    while (pi + 1 < a.n_probs && (int)blockIdx.x >= a.p[pi + 1].cta0) ++pi;
+    const MlpBwdProbDev& P = a.p[pi];
+    const int rank = CL > 1 ? (int)cluster_rank() : 0;
+    const int m0 = ((int)blockIdx.x - P.cta0) / CL * BM;
+    const int rb = m0 / BM;
+    const int M = P.M;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const long long wlim = a.wait_limit;
+    int* err = a.err;
+    const int hslabs = (H + SLAB - 1) / SLAB;
+    const int ldr = a.ldr, band = BM / CL;
+    // K slabs of step s: dout's, H's, or (final, split over K) this CTA's slice
+    auto nk = [&](int st) { return st == 0 ? a.nko : (st < nh ? hslabs : ((ksplit && CL > 1) ? NS / SLAB : hslabs)); };
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        mbar_init(a0_full, 1);
+        mbar_init(acc_full, 1);
+        mbar_init(a_ready, 1);
+        mbar_init(xbar0, 1);
+        mbar_init(xbar0 + 8, 1);
+        mbar_init(out_bar, 1);
+        slot[1] = 0;
+        slot[2] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        if (CL > 1) {
+            mbar_expect_tx(xbar0, (uint32_t)(CL * BM * 8));
+            mbar_expect_tx(xbar0 + 8, (uint32_t)(CL * BM * 8));
+            if (ksplit) mbar_expect_tx(out_bar, (uint32_t)(CL * band * ldr * 4));
+        }
+    }
+    if (threadIdx.x == 128) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.tdo)) : "memory");
+        for (int l = a.ncols > 0 ? 0 : 1; l <= nh; ++l)
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&P.tw[l])) : "memory");
+    }
+    __syncthreads();
+    if (CL > 1) cluster_sync_all();
+    SQ_KERNEL_ENTRY();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                     "r"(a.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = slot[0];
+
+    if (warp == 4) {
+        // ---------------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            mbar_expect_tx(a0_full, (uint32_t)(a.nko * SLAB_BYTES));
+            for (int kb = 0; kb < a.nko; ++kb) tma_load_2d(a_base + kb * SLAB_BYTES, &P.tdo, kb * SLAB, m0, a0_full);
+            int it = 0;
+            bool ok = true;
+            for (int st = 0; st < nsteps && ok; ++st) {
+                const bool fin = st == nh;
+                const int wl = nh - st;                        // the weight this step multiplies by
+                const int N = fin ? nfin : NS;
+                const int n0 = fin ? (ksplit ? a.c0 : a.c0 + rank * nfin) : rank * NS;
+                const int k0 = (fin && ksplit) ? rank * NS : 0;
+                for (int kb = 0; kb < nk(st); ++kb, ++it) {
+                    const int s = it % S;
+                    if (it >= S && !mbar_wait(empty(s), ((it / S) - 1) & 1, err, 40, wlim)) { ok = false; break; }
+                    mbar_expect_tx(full(s), (uint32_t)(N * 128));
+                    for (int j = 0; j < N / 64; ++j)
+                        tma_load_2d(ring + s * a.stage_bytes + j * 8192, &P.tw[wl], n0 + 64 * j, k0 + kb * SLAB, full(s));
+                }
+            }
+            slot[1] = it;
+        }
+    } else {
+        const int r = warp * 32 + lane;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        float* stg_w = stg + warp * 32 * STG_LD;
+        const bool rebuild = P.beta[0] != nullptr;   // the ReLU mask from pre, g and beta
+        if (warp > 0)
+            for (int i = threadIdx.x - 32; i < (rebuild ? 2 : 1) * nh * NS; i += 96) {
+                const int l = (i / NS) % nh;
+                par[i] = (i < nh * NS ? P.g[l] : P.beta[l])[rank * NS + i % NS];
+            }
+        float* const p_dx = P.dx;
+        const int64_t p_lddx = P.lddx;
+        int it = 0;
+        bool dead = false;
+        for (int st = 0; st < nsteps; ++st) {
+            const bool fin = st == nh;
+            // this step's first tile of pre and the row statistics, read while its MMAs run
+            const int lh = nh - 1 - st;
+            const bool valid = m0 + r < M;
+            float4 pf[8];
+            float mean = 0.f, rstd = 0.f;
+            if (!fin) {
+                if (rebuild) issue_rows(pf, P.pre[lh], H, m0 + warp * 32, M, rank * NS, lane);
+                if (valid) {
+                    mean = __ldg(P.mean[lh] + m0 + r);
+                    rstd = __ldg(P.rstd[lh] + m0 + r);
+                }
+            }
+            // ---------------------------------------------------------------- MMA issue
+            if (threadIdx.x == 0) {
+                if (!dead) {
+                    if (st == 0) dead = !mbar_wait(a0_full, 0, err, 41, wlim);
+                    else dead = !mbar_wait<true>(a_ready, (st - 1) & 1, err, 42, wlim);
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t idesc = idesc_bf16_kn(BM, fin ? nfin : NS);
+                for (int kb = 0; kb < nk(st) && !dead; ++kb) {
+                    const int s = it % S;
+                    if (!mbar_wait(full(s), (it / S) & 1, err, 43, wlim)) { dead = true; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t as = a_base + kb * SLAB_BYTES, bs = ring + s * a.stage_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_bf16(tmem, sw128_desc(as + kk * 32), sw128_desc_mn(bs + kk * 2048), idesc,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(empty(s));
+                    ++it;
+                }
+                slot[2] = it;
+                mma_commit(acc_full);
+            }
+            __syncwarp();
+            mbar_wait(acc_full, st & 1, err, 44, wlim);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (st == 0) epi_bar();   // the staged g slices
+            if (!fin) {
+                // ------------------------------------------------------------ LayerNorm (+ReLU) backward
+                const int c0 = rank * NS;
+                const float* gsl = par + lh * NS;
+                const float* bsl = par + (nh + lh) * NS;
+                const float* const s_pre = P.pre[lh];
+                const float* const s_post = P.post[lh];
+                float* const s_col = P.colpart[lh];
+                const bool s_dp = P.has_dp[lh] != 0;
+                float s1 = 0.f, s2 = 0.f;
+                for (int c = 0; c < NS; c += 32) {
+                    float dp[32], xh[32], t[32];
+                    if (rebuild) {
+                        stage_rows(stg_w, pf, lane, xh);
+                        if (c + 32 < NS) issue_rows(pf, s_pre, H, m0 + warp * 32, M, c0 + c + 32, lane);
+                    } else {
+                        load_rows_coalesced(stg_w, s_pre, H, m0 + warp * 32, M, c0 + c, lane, xh);
+                    }
+                    tmem_ld32(trow + c, dp);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) xh[j] = (xh[j] - mean) * rstd;
+                    ld_par32(gsl + c, t);
+                    if (rebuild) {
+                        float bt[32];
+                        ld_par32(bsl + c, bt);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) dp[j] = (valid && __fmaf_rn(t[j], xh[j], bt[j]) > 0.f) ? dp[j] : 0.f;
+                    } else {
+                        float po[32];
+                        load_rows_coalesced(stg_w, s_post, H, m0 + warp * 32, M, c0 + c, lane, po);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) dp[j] = (valid && po[j] > 0.f) ? dp[j] : 0.f;   // dn
+                    }
+                    if (s_col) {
+                        colacc[(warp * 3 + 0) * NS + c + lane] = warp_col_sum_prod(stg_w, dp, xh, lane);
+                        colacc[(warp * 3 + 1) * NS + c + lane] = warp_col_sum(stg_w, dp, lane);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        t[j] *= dp[j];                          // dxh
+                        s1 += t[j];
+                        s2 += t[j] * xh[j];
+                    }
+                    tmem_st32(trow + NS + c, xh);
+                    tmem_st32(trow + 2 * NS + c, t);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                if (CL > 1) {
+                    const int b = st & 1;
+                    float* buf = xbuf + b * CL * BM * 2;
+                    const uint32_t mine = smem_u32(buf + (rank * BM + r) * 2), xb = xbar0 + 8 * b;
+                    for (int q = 0; q < CL; ++q) st_async_v2(mapa(mine, q), s1, s2, mapa(xb, q));
+                    mbar_wait<true>(xb, (st >> 1) & 1, err, 45, wlim);
+                    if (threadIdx.x == 0) mbar_expect_tx(xb, (uint32_t)(CL * BM * 8));
+                    s1 = 0.f;
+                    s2 = 0.f;
+                    for (int q = 0; q < CL; ++q) {
+                        s1 += buf[(q * BM + r) * 2];
+                        s2 += buf[(q * BM + r) * 2 + 1];
+                    }
+                }
+                const float m1 = s1 / (float)H, m2 = s2 / (float)H;
+                // the previous layer's TMA store has read this CTA's slabs before they are rewritten
+                if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                epi_bar();
+                const bool last_hidden = lh == 0;
+                // dpre_0 feeds the final step: every CTA needs all of it when that step splits
+                // the output columns, only its own slice (kept at the start) when it splits K
+                const bool bcast = CL > 1 && !(last_hidden && (ksplit || nsteps == nh));
+                const int kpos0 = (CL > 1 && last_hidden && ksplit && nsteps > nh) ? 0 : c0;
+                for (int c = 0; c < NS; c += 32) {
+                    float xh[32], v[32];
+                    {
+                        float dxh[32];
+                        tmem_ld32(trow + NS + c, xh);
+                        tmem_ld32(trow + 2 * NS + c, dxh);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = rstd * (dxh[j] - m1 - xh[j] * m2);   // dpre
+                    }
+                    if (s_col) colacc[(warp * 3 + 2) * NS + c + lane] = warp_col_sum(stg_w, v, lane);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int k = kpos0 + c + 8 * u;
+                        uint4 w;
+                        w.x = pack_bf16(v[8 * u], v[8 * u + 1]);
+                        w.y = pack_bf16(v[8 * u + 2], v[8 * u + 3]);
+                        w.z = pack_bf16(v[8 * u + 4], v[8 * u + 5]);
+                        w.w = pack_bf16(v[8 * u + 6], v[8 * u + 7]);
+                        *reinterpret_cast<uint4*>(smem + (k / SLAB) * SLAB_BYTES + r * 128 +
+                                                  ((((k % SLAB) / 8) ^ (r & 7)) * 16)) = w;
+                    }
+                }
+                if (H % SLAB)
+                    for (int k = H; k < hslabs * SLAB; k += 8)
+                        *reinterpret_cast<uint4*>(smem + (k / SLAB) * SLAB_BYTES + r * 128 +
+                                                  ((((k % SLAB) / 8) ^ (r & 7)) * 16)) = make_uint4(0u, 0u, 0u, 0u);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                epi_bar();
+                if (s_col) {   // this row block's column sums of the slice, warps added in order
+                    for (int i = threadIdx.x; i < 3 * NS; i += BM) {
+                        const int k = i / NS, j = i % NS;
+                        const float t = ((colacc[(0 * 3 + k) * NS + j] + colacc[(1 * 3 + k) * NS + j]) +
+                                         colacc[(2 * 3 + k) * NS + j]) + colacc[(3 * 3 + k) * NS + j];
+                        s_col[((int64_t)rb * 3 + k) * H + c0 + j] = t;
+                    }
+                    epi_bar();   // read before the next layer's column sums overwrite them
+                }
+                if (threadIdx.x == 0) {
+                    if (s_dp) {
+                        for (int j = 0; j < (NS + SLAB - 1) / SLAB; ++j)
+                            tma_store_2d(&P.tdp[lh], a_base + (kpos0 / SLAB + j) * SLAB_BYTES, c0 + j * SLAB, m0);
+                        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    }
+                    if (bcast) {
+                        const uint32_t src = a_base + (c0 / SLAB) * SLAB_BYTES, bytes = (uint32_t)NS * 256;
+                        for (int q = 0; q < CL; ++q)
+                            if (q != rank) bulk_s2s(mapa(src, q), src, bytes, mapa(a_ready, q));
+                        mbar_expect_tx(a_ready, (uint32_t)(CL - 1) * bytes);
+                    } else {
+                        mbar_arrive_local(a_ready);
+                    }
+                }
+            } else if (!ksplit) {
+                // ------------------------------------------------------------ final step, split over columns
+                for (int c = 0; c < nfin; c += 32) {
+                    float v[32];
+                    tmem_ld32(trow + c, v);
+                    store_rows_coalesced(stg_w, v, p_dx, p_lddx, m0 + warp * 32, M, rank * nfin + c, lane);
+                }
+            } else {
+                // ------------------------------------------------------------ final step, split over K
+                for (int c = 0; c < nfin; c += 16) {
+                    float v[16];
+                    tmem_ld16(trow + c, v);
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(ring_f + r * ldr + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                epi_bar();
+                const int ncols = a.ncols;
+                if (CL == 1) {
+                    for (int e = threadIdx.x; e < BM * ncols; e += BM) {
+                        const int row = e / ncols, col = e % ncols;
+                        if (m0 + row < M) p_dx[(int64_t)(m0 + row) * p_lddx + col] = ring_f[row * ldr + col];
+                    }
+                } else {
+                    const uint32_t recv = a_base + (uint32_t)NS * 256, bb = (uint32_t)(band * ldr * 4);
+                    if (threadIdx.x == 0)
+                        for (int q = 0; q < CL; ++q) bulk_s2s(mapa(recv + rank * bb, q), ring + q * bb, bb, mapa(out_bar, q));
+                    mbar_wait<true>(out_bar, 0, err, 46, wlim);
+                    const float* rv = reinterpret_cast<const float*>(smem + (size_t)NS * 256);
+                    for (int e = threadIdx.x; e < band * ncols; e += BM) {
+                        const int row = e / ncols, col = e % ncols;
+                        float v = 0.f;
+                        for (int q = 0; q < CL; ++q) v += rv[(q * band + row) * ldr + col];
+                        const int grow = m0 + rank * band + row;
+                        if (grow < M) p_dx[(int64_t)grow * p_lddx + col] = v;
+                    }
+                }
+            }
+        }
+        if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        (void)dead;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = (int)slot[2]; i < (int)slot[1]; ++i) mbar_wait(full(i % S), (i / S) & 1, err, 47, wlim);
+    if (CL > 1) cluster_sync_all();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols));
+    }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -639,6 +1104,120 @@ int out_ldr(int H, int CL, int nop, int ring_bytes) {
 }
 
 }  // namespace
+
+namespace {
+
+// Shared-memory plan of a backward launch (the same regions as the forward's, plus the
+// column-sum staging; no output receive area unless the final step splits K).
+bool plan_bwd(int H, int CL, int nh, int nko, int nfin, bool ksplit, int* a_bytes, int* stage_bytes, int* stages,
+              int* ldr, int* smem) {
+    const int NS = H / CL;
+    const int hs = (H + SLAB - 1) / SLAB;
+    *ldr = nfin + 4;
+    // the activation region also holds the final step's receive area after the own slice
+    *a_bytes = std::max(nko, hs) * SLAB_BYTES;
+    if (ksplit && CL > 1) *a_bytes = std::max(*a_bytes, (NS * 256 + BM * *ldr * 4 + 1023) / 1024 * 1024);
+    *stage_bytes = std::max(NS, nfin) * 128;
+    const int fixed = 1024 + STG_BYTES + 2 * CL * BM * 2 * 4 + 4 * 3 * NS * 4 + ((2 * nh * NS + 3) / 4) * 16 + 256;
+    const int n = (SMEM_LIMIT - fixed - *a_bytes) / *stage_bytes;
+    *stages = std::min(n, 8);
+    *smem = fixed + *a_bytes + *stages * *stage_bytes;
+    if (*stages < 2) return false;
+    if (ksplit && *stages * *stage_bytes < BM * *ldr * 4) return false;   // the partial tile staged in the ring
+    return true;
+}
+
+// Cluster size of a backward launch: slices of whole 64-column blocks (the MN-major
+// weight tiles are 64 columns wide) whose gradient, xhat and dxh fit in tensor memory
+// (3 NS <= 512 columns).
+int mlp_bwd_cluster(int H, int nout, int force) {
+    auto ok = [&](int CL) {
+        const int NS = H / CL;
+        return H % CL == 0 && NS % SLAB == 0 && 3 * NS <= 512;
+    };
+    (void)nout;
+    if ((force == 1 || force == 2 || force == 4 || force == 8) && ok(force)) return force;
+    for (int CL : {4, 2, 1})
+        if (ok(CL)) return CL;
+    return 0;
+}
+
+// Final step: split over the output columns when each CTA gets a multiple of 64 of them,
+// else over K with one 64-column tile.
+void fin_split(int ncols, int CL, int* nfin, bool* ksplit) {
+    if (CL == 1 && ncols % 64 == 0 && ncols <= 256) { *nfin = ncols; *ksplit = false; return; }
+    if (CL > 1 && ncols % (64 * CL) == 0 && ncols / CL <= 256) { *nfin = ncols / CL; *ksplit = false; return; }
+    *nfin = 64;
+    *ksplit = true;
+}
+
+}  // namespace
+
+bool mlp_bwd_tc_supported(int nh, int H, int nout, int kin, int c0, int ncols, int force_cluster) {
+    if (nh < 1 || nh > kMlpMaxHidden || H < 32 || H > 1024 || H % 32 || nout < 1 || nout > 256 || kin < 1 ||
+        c0 < 0 || c0 % 8 || ncols < 0 || c0 + ncols > kin)
+        return false;
+    const int CL = mlp_bwd_cluster(H, nout, force_cluster);
+    if (!CL) return false;
+    int nfin = 0;
+    bool ks = false;
+    if (ncols > 0) fin_split(ncols, CL, &nfin, &ks);
+    if (ks && ncols > 64) return false;
+    int ab, sb, st, ldr, sm;
+    return plan_bwd(H, CL, nh, (nout + SLAB - 1) / SLAB, nfin, ks, &ab, &sb, &st, &ldr, &sm);
+}
+
+void mlp_bwd_tc_prepare() {
+    cudaFuncSetAttribute(mlp_bwd_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_LIMIT);
+}
+
+int launch_mlp_bwd_tc(const MlpTcBwdProblem* p, int n, int nh, int H, int nout, int kin, int c0, int ncols, int* err,
+                      const TcWait* wait, cudaStream_t s, int force_cluster) {
+    if (n < 1 || n > kMlpMaxProbs || !mlp_bwd_tc_supported(nh, H, nout, kin, c0, ncols, force_cluster)) return -1;
+    const int CL = mlp_bwd_cluster(H, nout, force_cluster);
+    MlpBwdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n_probs = n; a.nh = nh; a.H = H; a.CL = CL; a.NS = H / CL; a.nko = (nout + SLAB - 1) / SLAB;
+    a.c0 = c0; a.ncols = ncols;
+    bool ks = false;
+    if (ncols > 0) fin_split(ncols, CL, &a.nfin, &ks);
+    a.fin_ksplit = ks ? 1 : 0;
+    a.err = err;
+    a.wait_limit = wait && wait->cycles > 0 ? wait->cycles : kWaitDefault;
+    int smem = 0;
+    if (!plan_bwd(H, CL, nh, a.nko, a.nfin, ks, &a.a_bytes, &a.stage_bytes, &a.stages, &a.ldr, &smem)) return -1;
+    const int need_cols = std::max(3 * a.NS, a.nfin);
+    a.tmem_cols = 32;
+    while ((int)a.tmem_cols < need_cols) a.tmem_cols *= 2;
+    int ctas = 0;
+    for (int i = 0; i < n; ++i) {
+        const MlpTcBwdProblem& q = p[i];
+        MlpBwdProbDev& d = a.p[i];
+        if (q.M < 1 || !q.dout || (ncols > 0 && !q.dx) || (ncols == 0 && !q.dpre_bf[0])) return -1;
+        if (!make_map(&d.tdo, q.dout, nout, q.M, q.ld_dout, SLAB, BM)) return -2;
+        for (int l = 0; l <= nh; ++l) {
+            const int in = l == 0 ? kin : H, out = l == nh ? nout : H;
+            if (!q.w[l] && (l > 0 || ncols > 0)) return -1;
+            if (q.w[l] && !make_map(&d.tw[l], q.w[l], in, out, q.ldw[l], SLAB, SLAB)) return -2;
+            if (l == nh) break;
+            // the shifts of every hidden layer or of none; post only when they are absent
+            if (!q.g[l] || !q.pre[l] || !q.mean[l] || !q.rstd[l] || (!q.beta[l]) != (!q.beta[0]) ||
+                (!q.beta[l] && !q.post[l]))
+                return -1;
+            d.g[l] = q.g[l]; d.beta[l] = q.beta[l]; d.pre[l] = q.pre[l]; d.post[l] = q.post[l];
+            d.mean[l] = q.mean[l]; d.rstd[l] = q.rstd[l];
+            d.colpart[l] = q.colpart[l];
+            d.has_dp[l] = q.dpre_bf[l] != nullptr;
+            if (d.has_dp[l] && !make_map(&d.tdp[l], q.dpre_bf[l], H, q.M, H, SLAB, BM)) return -2;
+        }
+        d.dx = q.dx; d.lddx = q.lddx;
+        d.M = q.M;
+        d.cta0 = ctas;
+        ctas += (q.M + BM - 1) / BM * CL;
+    }
+    launch_kc(mlp_bwd_tc_kernel, dim3(ctas), dim3(kThreads), (size_t)smem, s, dim3(CL), a);
+    return 0;
+}
 
 bool mlp_tc_supported(int nh, int H, int nout, int kin) {
     return nh >= 1 && nh <= kMlpMaxHidden && H >= 32 && H <= 1024 && H % 32 == 0 && nout >= 1 && nout <= 256 &&

@@ -42,4 +42,37 @@ int launch_mlp_tc(const MlpTcProblem* p, int n, int nh, int H, int nout, float e
                   cudaStream_t s, int force_cluster = 0);
 void mlp_tc_prepare();
 
+// Backward through the same head (the input-gradient chain; its weight gradients are
+// left to GEMMs): dout BF16 [M, nout] (row stride ld_dout, a multiple of 8); the weights
+// as in the forward; the forward's saves of every hidden layer (pre-activation and
+// LayerNorm + ReLU output FP32 with row stride H, row statistics).  Per hidden layer,
+// optionally: dpre_bf, the gradient at its pre-activation in BF16 [M, H], and colpart,
+// [ceil(M / 128)][3][H] per 128-row block column sums of dn xhat, dn and dpre (dn the
+// gradient at the LayerNorm output after the ReLU mask): the gain, shift and bias
+// gradients once the row blocks are added.  dx FP32 [M, ncols] (row stride lddx)
+// receives columns [c0, c0 + ncols) of the input gradient; ncols = 0 stops the chain at
+// dpre_0 (then dpre_bf[0] is required and w[0] unused), for callers that form the input
+// gradient themselves (e.g. summed over a critic pair).  With the LayerNorm shifts beta
+// given (every hidden layer's, saves written by the fused forward, which rounds the
+// LayerNorm output as fma(g, xhat, beta)), the ReLU mask is rebuilt from pre by the same
+// expression and post is not read; without them post is required.
+struct MlpTcBwdProblem {
+    int M;
+    const __nv_bfloat16* dout; int64_t ld_dout;
+    const __nv_bfloat16* w[kMlpMaxHidden + 1]; int64_t ldw[kMlpMaxHidden + 1];
+    const float* g[kMlpMaxHidden]; const float* beta[kMlpMaxHidden];
+    const float* pre[kMlpMaxHidden]; const float* post[kMlpMaxHidden];
+    const float* mean[kMlpMaxHidden]; const float* rstd[kMlpMaxHidden];
+    __nv_bfloat16* dpre_bf[kMlpMaxHidden];
+    float* colpart[kMlpMaxHidden];
+    float* dx; int64_t lddx;
+};
+// Shapes the fused backward takes: those of the forward, c0 a multiple of 8, and ncols
+// either a multiple of 64 per CTA of the cluster, at most 64, or 0.
+// force_cluster (1, 2, 4 or 8): the cluster size to use if the shape allows it.
+bool mlp_bwd_tc_supported(int nh, int H, int nout, int kin, int c0, int ncols, int force_cluster = 0);
+int launch_mlp_bwd_tc(const MlpTcBwdProblem* p, int n, int nh, int H, int nout, int kin, int c0, int ncols, int* err,
+                      const TcWait* wait, cudaStream_t s, int force_cluster = 0);
+void mlp_bwd_tc_prepare();
+
 }  // namespace sq

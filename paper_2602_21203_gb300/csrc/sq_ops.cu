@@ -27,6 +27,7 @@ int* tc_error_flag() {
         tc_prepare();
         conv_tc_prepare();
         mlp_tc_prepare();
+        mlp_bwd_tc_prepare();
     });
     return flag;
 }
@@ -146,6 +147,40 @@ int squint_op_mlp_bf16(int M, int kin, int nh, int H, int nout, const void* x, i
     const int rc = launch_mlp_tc(&p, 1, nh, H, nout, eps, err, nullptr, (cudaStream_t)stream, cluster);
     if (rc != 0) {
         g_last_error = "fused MLP: an operand cannot be described by a tensor map (alignment, extents)";
+        return SQUINT_EINVAL;
+    }
+    return launch_status();
+}
+
+int squint_op_mlp_bwd_bf16(int M, int kin, int nh, int H, int nout, const void* dout, int64_t ld_dout,
+                           const void* const* w, const int64_t* ldw, const float* const* g,
+                           const float* const* beta, const float* const* pre, const float* const* post,
+                           const float* const* mean, const float* const* rstd, void* const* dpre_bf,
+                           float* const* colpart, int c0, int ncols, float* dx, int64_t lddx, void* stream) {
+    if (M < 0 || nh < 1 || nh > kMlpMaxHidden || !dout || !w || !ldw || !g || !pre || (!post && !beta) || !mean || !rstd ||
+        (ncols > 0 && !dx) || lddx < ncols || (ncols == 0 && (!dpre_bf || !dpre_bf[0])))
+        return SQUINT_EINVAL;
+    if (!mlp_bwd_tc_supported(nh, H, nout, kin, c0, ncols)) {
+        g_last_error = "fused MLP backward: shape outside the kernel's range";
+        return SQUINT_EINVAL;
+    }
+    if (M == 0) return SQUINT_OK;
+    MlpTcBwdProblem p;
+    std::memset(&p, 0, sizeof(p));
+    p.M = M; p.dout = (const __nv_bfloat16*)dout; p.ld_dout = ld_dout;
+    for (int l = 0; l <= nh; ++l) {
+        p.w[l] = (const __nv_bfloat16*)w[l]; p.ldw[l] = ldw[l];
+        if (l == nh) break;
+        p.g[l] = g[l]; p.beta[l] = beta ? beta[l] : nullptr; p.pre[l] = pre[l]; p.post[l] = post ? post[l] : nullptr;
+        p.mean[l] = mean[l]; p.rstd[l] = rstd[l];
+        p.dpre_bf[l] = dpre_bf ? (__nv_bfloat16*)dpre_bf[l] : nullptr;
+        p.colpart[l] = colpart ? colpart[l] : nullptr;
+    }
+    p.dx = dx; p.lddx = lddx;
+    int* err = tc_error_flag();
+    if (!err) return SQUINT_ECUDA;
+    if (launch_mlp_bwd_tc(&p, 1, nh, H, nout, kin, c0, ncols, err, nullptr, (cudaStream_t)stream) != 0) {
+        g_last_error = "fused MLP backward: an operand cannot be described by a tensor map (alignment, extents)";
         return SQUINT_EINVAL;
     }
     return launch_status();

@@ -82,7 +82,7 @@ struct ProfScope {
     int idx = -1;
     ProfScope(squint_handle* hh, cudaStream_t ss, const char* name, double work, int unit) : h(hh), s(ss) {
         if (!h->prof) return;
-        squint_handle::ProfEntry e{name, nullptr, nullptr, work, unit};
+        squint_handle::ProfEntry e{name, nullptr, nullptr, work, unit, h->lane_of(s)};
         cudaEventCreate(&e.a);
         cudaEventCreate(&e.b);
         squint_handle::record_timing(e.a, s);

@@ -108,11 +108,13 @@ def load():
         "squint_profile_update": (I, [P, P, I, ctypes.POINTER(I), P]),
         "squint_phase_name": (ctypes.c_char_p, [I]),
         "squint_profile_kernels": (I, [P, I, P, P, P, P, P, ctypes.POINTER(I), P]),
+        "squint_trace_update": (I, [P, I, P, P, P, P, ctypes.POINTER(I), P]),
         "squint_op_gemm": (I, [I, I, I, I, P, I64, I64, P, I64, I64, P, I64, P, I, P]),
         "squint_op_relu_bwd": (I, [I, I64, P, P, P, P]),
         "squint_op_squint_store": (I, [I, I, I, I, I, P, P, I64, I64, P]),
         "squint_op_gemm_fp8_workspace": (SZ, [I, I, I]),
         "squint_op_cast_bf16": (I, [I, I, P, I64, P, I64, P]),
+        "squint_op_mlp_bwd_bf16": (I, [I, I, I, I, I, P, I64, P, P, P, P, P, P, P, P, P, P, I, I, P, I64, P]),
         "squint_op_mlp_bf16": (I, [I, I, I, I, I, P, I64, P, P, P, P, P, ctypes.c_float, P, I64, P, P, P, P, P, I, P]),
         "squint_op_gemm_layernorm": (I, [I, I, I, P, I64, P, I64, P, P, P, ctypes.c_float, I, P, P, P, P, P, P]),
         "squint_op_gemm_fp8": (I, [I, I, I, P, I64, P, I64, P, I64, P, P, SZ, P]),
@@ -312,6 +314,18 @@ class Learner:
             nm = names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
             out[nm] = (int(launches[i]), float(ms[i]), float(work[i]), "FLOP" if unit[i] == 0 else "B")
         return out
+
+    def trace_update(self, stream=None, cap=512):
+        """One update as the graph runs it, every launch timed: [(class, branch, start ms, end ms)]."""
+        names = ctypes.create_string_buffer(32 * cap)
+        lanes = (ctypes.c_int * cap)()
+        t0 = (ctypes.c_float * cap)()
+        t1 = (ctypes.c_float * cap)()
+        n = ctypes.c_int(0)
+        _check(self.lib.squint_trace_update(self.h, cap, names, lanes, t0, t1, ctypes.byref(n), _stream(stream)),
+               "squint_trace_update")
+        return [(names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode(), int(lanes[i]), float(t0[i]), float(t1[i]))
+                for i in range(min(n.value, cap))]
 
     def refresh_policy(self, stream=None):
         _check(self.lib.squint_refresh_policy(self.h, _stream(stream)), "squint_refresh_policy")

@@ -127,6 +127,37 @@ def mlp_bf16(x, ws, biases, gs, betas, eps=1e-5, save=True, cluster=0):
     return out, saved
 
 
+def mlp_bf16_bwd(dout, ws, gs, saved, kin, c0, ncols, want_dpre=True, want_cols=True, betas=None):
+    """The input-gradient chain of a head evaluated by mlp_bf16 (saved = its per-layer
+    (pre, post, post_bf16, mean, rstd)): dout BF16 [M, nout], weights as for mlp_bf16.
+    With betas (the LayerNorm shifts) the ReLU mask is rebuilt from pre and post is not read.
+    Returns (dx [M, ncols] = columns c0 .. c0 + ncols of the input gradient,
+    dpre_bf16 per hidden layer or None, colpart per hidden layer [ceil(M/128), 3, H] or None)."""
+    _need(dout, torch.bfloat16, "dout")
+    nh = len(ws) - 1
+    M, nout = dout.shape
+    H = ws[0].shape[0]
+    dev = dout.device
+    dx = torch.empty(M, ncols, device=dev)
+
+    def arr(ctype, vals):
+        return (ctype * len(vals))(*vals)
+
+    P = ctypes.c_void_p
+    dp = [torch.empty(M, H, device=dev, dtype=torch.bfloat16) for _ in range(nh)] if want_dpre else None
+    cp = [torch.empty((M + 127) // 128, 3, H, device=dev) for _ in range(nh)] if want_cols else None
+    _chk(_lib.load().squint_op_mlp_bwd_bf16(
+        M, kin, nh, H, nout, _p(dout), dout.stride(0), arr(P, [w.data_ptr() for w in ws]),
+        arr(ctypes.c_int64, [w.stride(0) for w in ws]), arr(P, [t.data_ptr() for t in gs]),
+        arr(P, [t.data_ptr() for t in betas]) if betas is not None else None,
+        arr(P, [sv[0].data_ptr() for sv in saved]),
+        arr(P, [sv[1].data_ptr() for sv in saved]) if betas is None else None,
+        arr(P, [sv[3].data_ptr() for sv in saved]), arr(P, [sv[4].data_ptr() for sv in saved]),
+        arr(P, [t.data_ptr() for t in dp]) if dp else None, arr(P, [t.data_ptr() for t in cp]) if cp else None,
+        int(c0), int(ncols), _p(dx), dx.stride(0), _s()), "squint_op_mlp_bwd_bf16")
+    return dx, dp, cp
+
+
 def gemm_fp8(A, B, bias=None, out=None):
     """out = scale_A scale_B e4m3(A / scale_A) e4m3(B / scale_B)^T + bias for BF16 A [M, K], B [N, K]
     (row-major, unit column stride); per-tensor scales amax / 448.  Returns (out, (scale_A, scale_B))."""

@@ -129,3 +129,108 @@ def test_fused_mlp_rejects_shapes_outside_its_range():
     with pytest.raises(lib.SquintError) as e:
         ops.mlp_bf16(x[:, :64], [ws[0][:, :64], ws[1][:, :48], ws[2][:, :48]], bs, gs, betas)
     assert e.value.code == lib.EINVAL
+
+
+# ---------------------------------------------------------------- the backward chain
+# (M, kin, H, nout, hidden layers, c0, ncols): the critics' backward to the projected
+# features (columns 0..255 of 274, split over the output columns), the actor step's
+# backward to the action columns (264..273, split over K), the actor's backward (268
+# inputs, 12 outputs), ragged rows, the small head and a 64-wide one, one and three hidden
+# layers (hidden widths below 64 are outside the kernel's range)
+BWD_CASES = [
+    (512, 274, 512, 101, 2, 0, 256), (512, 274, 512, 101, 2, 264, 10), (512, 268, 512, 12, 2, 0, 256),
+    (37, 274, 512, 101, 2, 0, 256), (300, 274, 512, 101, 2, 264, 10), (300, 418, 256, 51, 2, 400, 18),
+    (8, 218, 64, 11, 2, 200, 18), (200, 64, 256, 16, 1, 0, 64), (130, 96, 128, 1, 3, 0, 64),
+]
+
+
+@pytest.mark.parametrize("rebuild", [False, True], ids=["post", "rebuild"])
+@pytest.mark.parametrize("M,kin,H,nout,nh,c0,ncols", BWD_CASES)
+def test_fused_mlp_backward_matches_oracle_layer_by_layer(M, kin, H, nout, nh, c0, ncols, rebuild):
+    """Each hidden layer's dpre against the oracle's LayerNorm backward (FP64) of dout or
+    the kernel's own BF16 dpre of the layer above times the weight (5e-3 relative in norm:
+    the BF16 rounding of dpre, 2^-9 per element); the input gradient 1e-5 of FP64 of the
+    kernel's own dpre_0; the per-row-block column sums 1e-4 of FP64 column sums.  The ReLU
+    mask read from the saved post, or rebuilt from pre, g and beta."""
+    from paper_2602_21203_gb300 import ops
+    x, ws, bs, gs, betas = _make(M, kin, H, nout, nh, seed=5 * M + kin + H)
+    wv = [w[:, :(kin if l == 0 else H)] for l, w in enumerate(ws)]
+    _, saved = ops.mlp_bf16(x[:, :kin], wv, bs, gs, betas, eps=EPS)
+    g = torch.Generator().manual_seed(M + nout)
+    ld = (nout + 7) // 8 * 8
+    dbuf = torch.zeros(M, ld)
+    dbuf[:, :nout] = torch.randn(M, nout, generator=g) * 0.1
+    dout = dbuf.to(torch.bfloat16).cuda()[:, :nout]
+    dx, dps, cps = ops.mlp_bf16_bwd(dout, wv, gs, saved, kin, c0, ncols, betas=betas if rebuild else None)
+    torch.cuda.synchronize()
+    d = lambda t: t.float().cpu().double().numpy()
+    dy = d(dout)
+    for lh in range(nh - 1, -1, -1):
+        w_above = d(ws[lh + 1])[:, :H]
+        dpost = dy @ w_above
+        pre, post, _, mean, rstd = (d(t) for t in saved[lh])
+        xhat = (pre - mean[:, None]) * rstd[:, None]
+        dn = dpost * (post > 0)
+        dpre, dg, db = o.layernorm_bwd(dn, d(gs[lh]), (xhat, rstd[:, None]))
+        got = d(dps[lh])
+        assert _rel(got, dpre) < 5e-3, (lh, "dpre", _rel(got, dpre))
+        cols = d(cps[lh]).sum(0)                       # the row blocks added
+        assert _rel(cols[0], dg) < 1e-4, (lh, "dg", _rel(cols[0], dg))
+        assert _rel(cols[1], db) < 1e-4, (lh, "dbeta", _rel(cols[1], db))
+        assert _rel(cols[2], dpre.sum(0)) < 1e-4, (lh, "dbias", _rel(cols[2], dpre.sum(0)))
+        dy = got                                       # the next product reads the BF16 dpre
+    ref_dx = dy @ d(ws[0])[:, c0:c0 + ncols]
+    assert _rel(d(dx), ref_dx) < 1e-5, ("dx", _rel(d(dx), ref_dx))
+
+
+def test_fused_mlp_backward_rejects_shapes_outside_its_range():
+    from paper_2602_21203_gb300 import lib, ops
+    x, ws, bs, gs, betas = _make(8, 218, 32, 11, 2, seed=9)     # 32-wide hidden layers
+    wv = [w[:, :(218 if l == 0 else 32)] for l, w in enumerate(ws)]
+    _, saved = ops.mlp_bf16(x[:, :218], wv, bs, gs, betas, eps=EPS)
+    dout = torch.zeros(8, 16, dtype=torch.bfloat16, device="cuda")[:, :11]
+    with pytest.raises(lib.SquintError) as e:
+        ops.mlp_bf16_bwd(dout, wv, gs, saved, 218, 200, 18)
+    assert e.value.code == lib.EINVAL
+
+
+def test_fused_mlp_backward_rows_are_independent_of_their_batch():
+    """The input gradient of a row is the same bits in the whole batch and in a sub-batch."""
+    from paper_2602_21203_gb300 import ops
+    M, kin, H, nout = 300, 274, 512, 101
+    x, ws, bs, gs, betas = _make(M, kin, H, nout, 2, seed=17)
+    wv = [w[:, :(kin if l == 0 else H)] for l, w in enumerate(ws)]
+    _, saved = ops.mlp_bf16(x[:, :kin], wv, bs, gs, betas, eps=EPS)
+    g = torch.Generator().manual_seed(3)
+    dbuf = torch.zeros(M, 104)
+    dbuf[:, :nout] = torch.randn(M, nout, generator=g) * 0.1
+    dout = dbuf.to(torch.bfloat16).cuda()
+    for c0, ncols in ((0, 256), (264, 10)):
+        full, _, _ = ops.mlp_bf16_bwd(dout[:, :nout], wv, gs, saved, kin, c0, ncols, False, False)
+        sub = [tuple(t[128:300] for t in sv) for sv in saved]
+        part, _, _ = ops.mlp_bf16_bwd(dout[128:300, :nout], wv, gs, sub, kin, c0, ncols, False, False)
+        torch.cuda.synchronize()
+        assert torch.equal(full[128:300], part)
+
+
+@pytest.mark.parametrize("M,kin,H,nout,nh,c0,ncols", [BWD_CASES[0], BWD_CASES[1], BWD_CASES[5], BWD_CASES[8]])
+def test_fused_mlp_backward_rebuilt_mask_is_the_forward_mask(M, kin, H, nout, nh, c0, ncols):
+    """The forward rounds post = max(fma(g, xhat, beta), 0) once; the backward's mask
+    rebuilt from pre by the same expression is the saved post's mask, so the two modes
+    give the same bits."""
+    from paper_2602_21203_gb300 import ops
+    x, ws, bs, gs, betas = _make(M, kin, H, nout, nh, seed=7 * M + H)
+    wv = [w[:, :(kin if l == 0 else H)] for l, w in enumerate(ws)]
+    _, saved = ops.mlp_bf16(x[:, :kin], wv, bs, gs, betas, eps=EPS)
+    g = torch.Generator().manual_seed(M)
+    ld = (nout + 7) // 8 * 8
+    dbuf = torch.zeros(M, ld)
+    dbuf[:, :nout] = torch.randn(M, nout, generator=g) * 0.1
+    dout = dbuf.to(torch.bfloat16).cuda()[:, :nout]
+    a = ops.mlp_bf16_bwd(dout, wv, gs, saved, kin, c0, ncols)
+    b = ops.mlp_bf16_bwd(dout, wv, gs, saved, kin, c0, ncols, betas=betas)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0])
+    for l in range(nh):
+        assert torch.equal(a[1][l], b[1][l])
+        assert torch.equal(a[2][l], b[2][l])

@@ -475,3 +475,58 @@ def test_ragged_batch_update_matches_oracle(L, batch, prec):
     learner.close()
     del ring
     torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------- fused backward chains
+@pytest.mark.parametrize("cluster", ["4", "8"])
+def test_fused_backward_update_within_bf16_bounds(L, monkeypatch, cluster):
+    """The BF16 update with the head MLPs' backward chains as fused launches (one per
+    chain, the ReLU mask rebuilt from the fused forward's pre-activations) against the
+    oracle within the BF16 bounds, and graph replay equal to eager bit for bit."""
+    monkeypatch.setenv("SQUINT_MLP_BWD", "1")
+    monkeypatch.setenv("SQUINT_MLP_BWD_CL", cluster)
+    cfg = synth.make_config("train_b512", ring_size=4096)
+    ring = synth.make_ring(cfg, 0, device="cuda")
+    lazy = lazy_ring(ring)
+    learner = L.Learner(cfg, ring, precision=L.PREC_BF16, max_k=2)
+    twin = L.Learner(cfg, ring, precision=L.PREC_BF16, max_k=2)
+    state = o.init_state(cfg)
+    P0 = {k: v.copy() for k, v in state["params"].items()}
+    stats = learner.update(1, graph=False)[0]
+    twin.update(1, graph=True)
+    assert np.array_equal(learner.params(), twin.params())
+    ref, tr = o.update(state, lazy, cfg)
+    g = split_params(learner.debug("grads"), cfg)
+    mix = post_critic_state(P0, split_params(learner.params(), cfg), cfg)
+    act = o.actor_loss(mix, tr["critic"]["z"], tr["frontend"]["p_t"], tr["eps_actor"],
+                       math.exp(float(mix["log_alpha"][0])), cfg)
+    assert abs(stats["q_mean"] - ref["q_mean"]) <= 2e-2 * max(abs(ref["q_mean"]), 1.0)
+    assert abs(stats["critic_loss"] - ref["critic_loss"]) <= 1e-2 * abs(ref["critic_loss"])
+    assert abs(stats["actor_loss"] - act["loss"]) <= 3e-2 * max(abs(act["loss"]), 1.0)
+    ref_grads = dict(tr["critic"]["grads"])
+    ref_grads.update(act["grads"])
+    for k, v in ref_grads.items():
+        n_got, n_ref = np.linalg.norm(g[k]), np.linalg.norm(v)
+        assert abs(n_got - n_ref) <= 5e-2 * n_ref + 1e-7, (k, n_got, n_ref)
+    learner.close()
+    twin.close()
+
+
+# ---------------------------------------------------------------- update timeline
+def test_trace_update_reports_every_launch_on_its_branch(L):
+    """The traced update has every launch with 0 <= start <= end, the main stream's
+    launches in issue order without overlap, launches on the side branches, and the
+    kernel classes of the in-order profile."""
+    cfg = synth.make_config("small_b32")
+    ring = synth.make_ring(cfg, 0, device="cuda")
+    learner = L.Learner(cfg, ring, precision=L.PREC_BF16, max_k=2)
+    learner.update(1)
+    tr = learner.trace_update()
+    assert len(tr) > 10
+    assert all(0.0 <= a <= b for _, _, a, b in tr)
+    main = [(a, b) for _, lane, a, b in tr if lane == 0]
+    assert all(main[i][1] <= main[i + 1][0] + 1e-6 for i in range(len(main) - 1))
+    assert any(lane > 0 for _, lane, _, _ in tr)
+    classes = set(learner.profile_kernels())
+    assert {n for n, _, _, _ in tr} == classes
+    learner.close()
