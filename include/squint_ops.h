@@ -200,6 +200,16 @@ int squint_op_conv32_layouts(const float* w, void* fwd_layout, void* dgrad_layou
  */
 int squint_op_conv32(int mode, int nimg, int H, int W, const void* in, const void* w_layout, const float* bias,
                      int relu, const void* mask, void* out_phwc, float* out_nchw, void* stream);
+/*
+ * The encoder's first layer on tensor cores (Sec. IV encoder: 3x3 convolution, stride s,
+ * no padding, ReLU): x NCHW FP32 [nimg, Cin, H, W] (1 <= Cin <= 16), w FP32
+ * [32, Cin, 3, 3], bias [32] -> y = ReLU(conv(x, w) + bias) as padded-HWC BF16 with
+ * OH = (H-3)/s + 1, OW = (W-3)/s + 1 (the input format of squint_op_conv32; only the
+ * interior is written).  x and w are rounded to BF16, products accumulated in FP32 over
+ * k = (ci, ky, kx).  out_phwc 16-byte aligned.
+ */
+int squint_op_conv0_bf16(int nimg, int Cin, int H, int W, int stride, const float* x, const float* w,
+                         const float* bias, void* out_phwc, void* stream);
 /* Weight gradient: x padded [nimg, H, W], dy padded [nimg, H-2, W-2] -> dw [32,32,3,3], db [32]. */
 size_t squint_op_wgrad32_workspace(int nimg);
 int squint_op_wgrad32(int nimg, int H, int W, const void* x, const void* dy, float* dw, float* db, void* work,

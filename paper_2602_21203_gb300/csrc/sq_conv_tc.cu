@@ -21,6 +21,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 
 namespace sq {
@@ -579,6 +580,174 @@ __global__ void __launch_bounds__(256) conv0_phwc_kernel(ConvShape sh, const flo
 }
 
 
+// ---------------------------------------------------------------- first layer on tensor cores
+// The first encoder layer (few input channels, any stride, 32 outputs) as an implicit GEMM
+// on tcgen05: D[pixel, co] = sum_k A[pixel, k] W[co, k] with k = (ci, ky, kx) in the
+// filter's own order, K = 9 Cin zero-padded to 8 PL.  A 128-pixel tile of A is gathered
+// by the threads (thread r: pixel r, its K inputs rounded to BF16) into the canonical
+// no-swizzle K-major layout, PL planes of 8 k-values (2048 B each); the filter is held as
+// the N = 32 operand in the same layout.  One thread issues the PL / 2 MMAs (K = 16) of a
+// tile into one of two accumulators; while they run the threads drain the previous tile
+// (bias, ReLU, BF16, padded-HWC store) and then gather the next one.  Persistent CTAs.
+struct Conv0Args {
+    ConvShape sh;
+    const float* x;       // NCHW FP32, image stride sh.x_img_stride
+    const float* w;       // [32][K] FP32
+    const float* bias;    // [32]
+    __nv_bfloat16* out;   // padded HWC BF16, grid (OH + 4) x (OW + 4) per image
+    int64_t npix;
+    int K, n_tiles;
+    int* err;
+};
+
+// two floats rounded to BF16 (nearest even), the first in the low half
+__device__ __forceinline__ uint32_t pack2_bf16(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+template <int PL>
+__global__ void __launch_bounds__(128, PL == 4 ? 5 : 2) conv0_tc_kernel(const __grid_constant__ Conv0Args a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    constexpr uint32_t kTile = PL * 2048;            // one A tile: PL planes of 128 rows x 16 B
+    uint8_t* b_s = smem + 2 * kTile;                  // the filter: PL planes of 32 rows x 16 B
+    float* bias_s = reinterpret_cast<float*>(b_s + PL * 512);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(bias_s + kCh);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+    const uint32_t a_u = smem_u32(smem), b_u = smem_u32(b_s), bar0 = smem_u32(bars);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const ConvShape& sh = a.sh;
+    const int opix = sh.OH * sh.OW;
+
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), 64);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar0 + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    SQ_KERNEL_ENTRY();   // the input and the filter come from earlier kernels
+    for (int e = threadIdx.x; e < 32 * PL; e += 128) {   // filter row co, 8 k-values of plane c
+        const int co = e / PL, c = e % PL;
+        __align__(16) __nv_bfloat16 hb[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int k = 8 * c + j;
+            hb[j] = __float2bfloat16_rn(k < a.K ? a.w[(int64_t)co * a.K + k] : 0.f);
+        }
+        *reinterpret_cast<uint4*>(b_s + c * 512 + co * 16) = *reinterpret_cast<const uint4*>(hb);
+    }
+    if (threadIdx.x < kCh) bias_s[threadIdx.x] = a.bias[threadIdx.x];
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+    const int n_local = (int)blockIdx.x < a.n_tiles ? (a.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int hw = sh.H * sh.W;
+    bool ok = true;
+
+    // this thread's pixel of tile t: its K inputs (loads issued, not yet waited for) ...
+    auto load = [&](int t, float (&v)[8 * PL]) {
+        const int64_t p = (int64_t)t * 128 + threadIdx.x;
+        const bool valid = p < a.npix;
+        const float* src = a.x;
+        if (valid) {
+            const int img = (int)(p / opix);
+            const int rem = (int)(p - (int64_t)img * opix);
+            const int oy = rem / sh.OW, ox = rem - oy * sh.OW;
+            src += (int64_t)img * sh.x_img_stride + (int64_t)(oy * sh.stride) * sh.W + ox * sh.stride;
+        }
+#pragma unroll
+        for (int k = 0; k < 8 * PL; ++k) {
+            const int ci = k / 9, tap = k % 9;
+            v[k] = (valid && k < a.K) ? __ldg(src + ci * hw + (tap / 3) * sh.W + tap % 3) : 0.f;
+        }
+    };
+    // ... and written as BF16 into its row of A tile buffer b
+    auto put = [&](int b, const float (&v)[8 * PL]) {
+        uint8_t* dst = smem + b * kTile + threadIdx.x * 16;
+#pragma unroll
+        for (int c = 0; c < PL; ++c) {
+            uint4 w4;
+            w4.x = pack2_bf16(v[8 * c], v[8 * c + 1]);
+            w4.y = pack2_bf16(v[8 * c + 2], v[8 * c + 3]);
+            w4.z = pack2_bf16(v[8 * c + 4], v[8 * c + 5]);
+            w4.w = pack2_bf16(v[8 * c + 6], v[8 * c + 7]);
+            *reinterpret_cast<uint4*>(dst + c * 2048) = w4;
+        }
+    };
+    // epilogue: this thread's accumulator row of tile t (buffer b) to its output pixel
+    auto drain = [&](int t, int b) {
+        uint32_t r0[16], r1[16];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)b * kCh;
+        tmem_ld16(taddr, r0);
+        tmem_ld16(taddr + 16, r1);
+        const int64_t p = (int64_t)t * 128 + threadIdx.x;
+        if (p >= a.npix) return;
+        const int img = (int)(p / opix);
+        const int rem = (int)(p - (int64_t)img * opix);
+        const int oy = rem / sh.OW, ox = rem - oy * sh.OW;
+        uint4* dst = reinterpret_cast<uint4*>(
+            a.out + (((int64_t)img * (sh.OH + 4) + oy + 2) * (sh.OW + 4) + ox + 2) * kCh);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float f[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int co = 8 * c + j;
+                const float v = __uint_as_float(co < 16 ? r0[co] : r1[co - 16]) + bias_s[co];
+                f[j] = v > 0.f ? v : 0.f;
+            }
+            uint4 w4;
+            w4.x = pack2_bf16(f[0], f[1]);
+            w4.y = pack2_bf16(f[2], f[3]);
+            w4.z = pack2_bf16(f[4], f[5]);
+            w4.w = pack2_bf16(f[6], f[7]);
+            dst[c] = w4;
+        }
+    };
+
+    constexpr uint32_t idesc = idesc_bf16(128, kCh, false, false);
+    for (int i = 0; i < n_local; ++i) {
+        const int t = (int)blockIdx.x + i * (int)gridDim.x, b = i & 1;
+        float v[8 * PL];
+        load(t, v);   // in flight while the previous tile drains
+        if (i > 0 && ok) {
+            // the MMAs of tile i - 1 (and so of tile i - 2, which read buffer b) are complete
+            const int pb = b ^ 1;
+            ok = mbar_wait(bar0 + 8 * pb, ((i - 1) >> 1) & 1, a.err, 17);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (ok) drain(t - (int)gridDim.x, pb);
+        }
+        put(b, v);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+            for (int kc = 0; kc < PL / 2; ++kc)
+                mma_bf16(tmem + (uint32_t)b * kCh, plain_desc(a_u + b * kTile + kc * 4096, 2048, 128),
+                         plain_desc(b_u + kc * 1024, 512, 128), idesc, kc > 0 ? 1u : 0u);
+            mma_commit(bar0 + 8 * b);
+        }
+        __syncwarp();
+    }
+    if (n_local > 0) {
+        const int i = n_local - 1, b = i & 1;
+        if (mbar_wait(bar0 + 8 * b, (i >> 1) & 1, a.err, 18) && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            drain((int)blockIdx.x + i * (int)gridDim.x, b);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        tmem_dealloc(tmem, 64);
+    }
+}
+
 // ---------------------------------------------------------------- layout conversions
 // CHW FP32 (per image stride img_stride) -> padded HWC BF16 interior.
 __global__ void to_phwc_kernel(const float* __restrict__ src, int64_t img_stride, int nimg, int H, int W,
@@ -735,6 +904,9 @@ void conv_tc_prepare() {
         g_num_sms = sms;
     cudaFuncSetAttribute(conv32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(wgrad32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(conv0_tc_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(conv0_tc_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 1024);
+    cudaFuncSetAttribute(conv0_tc_kernel<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     encode_fn();
 }
 
@@ -744,6 +916,44 @@ void launch_conv0_phwc(const ConvShape& sh, const float* x, const float* w, cons
     if (npix <= 0) return;
     const size_t smem = ((size_t)sh.Cin * 9 * kCh + kCh) * sizeof(float);
     launch_k(conv0_phwc_kernel, dim3((unsigned)((npix + 511) / 512)), dim3(256), smem, s, sh, x, w, b, out);
+}
+
+namespace {
+template <int PL>
+size_t conv0_tc_smem() { return 128 + 2 * PL * 2048 + PL * 512 + kCh * 4 + 32; }
+// CTAs per SM in the grid (each holds 64 tensor-memory columns, 512 per SM); the
+// SQUINT_CONV0_CTAS environment variable (1..8) overrides it
+int conv0_ctas_per_sm() {
+    static int n = [] {
+        const char* e = std::getenv("SQUINT_CONV0_CTAS");
+        const int v = e ? std::atoi(e) : 4;
+        return v >= 1 && v <= 8 ? v : 4;
+    }();
+    return n;
+}
+template <int PL>
+void conv0_tc_go(const Conv0Args& a, cudaStream_t s) {
+    // at least 28 KB of shared memory per CTA keeps at most 8 of them (8 x 64 columns) on an SM
+    const size_t smem = std::max(conv0_tc_smem<PL>(), (size_t)28 * 1024 + 1);
+    const int ctas = std::min(a.n_tiles, g_num_sms * conv0_ctas_per_sm());
+    launch_k(conv0_tc_kernel<PL>, dim3(ctas), dim3(128), smem, s, a);
+}
+}  // namespace
+
+int launch_conv0_tc(const ConvShape& sh, const float* x, const float* w, const float* b, __nv_bfloat16* out,
+                    int* err, cudaStream_t s) {
+    const int K = sh.Cin * 9;
+    if (sh.Cout != kCh || K > 144 || sh.nimg < 0 || sh.stride < 1) return -1;
+    const int64_t npix = (int64_t)sh.nimg * sh.OH * sh.OW;
+    if (npix <= 0) return 0;
+    Conv0Args a;
+    std::memset(&a, 0, sizeof(a));
+    a.sh = sh; a.x = x; a.w = w; a.bias = b; a.out = out; a.npix = npix; a.K = K; a.err = err;
+    a.n_tiles = (int)((npix + 127) / 128);
+    if (K <= 32) conv0_tc_go<4>(a, s);
+    else if (K <= 64) conv0_tc_go<8>(a, s);
+    else conv0_tc_go<18>(a, s);
+    return 0;
 }
 
 void launch_to_phwc(const float* src, int64_t img_stride, int nimg, int H, int W, __nv_bfloat16* dst, cudaStream_t s) {

@@ -124,6 +124,9 @@ struct squint_handle {
     int mlp_bwd_cluster = 0;
     // branch priorities (SQUINT_PRIO=0 at creation: every stream at the default priority)
     bool prio_branches = true;
+    // the polyak of the target critics inside the critic Adam's pass (SQUINT_FUSE_POLYAK=0
+    // at creation: its own launch beside the actor step)
+    bool fuse_polyak = true;
     bool launch_failed = false;       // a tensor map could not describe an operand
     // bounded waits of the update's tensor-core GEMMs (cycles 0: the default limit) and
     // the failure-test switch that makes them run out (squint_set_debug)

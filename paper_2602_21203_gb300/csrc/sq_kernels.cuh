@@ -90,6 +90,11 @@ struct ConvShape {
 // BF16 (grid width OW + 4) for the tensor-core layers; x is NCHW FP32.
 void launch_conv0_phwc(const ConvShape& sh, const float* x, const float* w, const float* b, __nv_bfloat16* out,
                        cudaStream_t s);
+// The same layer on tensor cores (BF16 operands, FP32 accumulation; Cin <= 16, Cout = 32):
+// 0, or < 0 if the shape is outside its range.  A bounded wait that gives up records its
+// code in *err.
+int launch_conv0_tc(const ConvShape& sh, const float* x, const float* w, const float* b, __nv_bfloat16* out,
+                    int* err, cudaStream_t s);
 template <typename T>
 void launch_conv_fwd(const ConvShape& sh, const T* x, const T* w, const T* b, T* y, bool relu, cudaStream_t s);
 // dx = conv-transpose(dy, w) (* (mask > 0) if mask given; mask has the layout of dx).
@@ -260,15 +265,22 @@ struct AdamArgs {
     __nv_bfloat16* p_bf;          // optional BF16 copy of p
     BfSeg seg[kMaxBfSeg];         // padded BF16 copies of the range's weight matrices
     int n_seg;
+    // optional polyak of a target copy in the same pass: target[i] <- (1 - tau) target[i]
+    // + tau p_new[i] for i < n, with the padded BF16 copies tseg (matrix k at seg[k]'s
+    // offset and shape)
+    float* target; float tau;
+    BfSeg tseg[kMaxBfSeg];
+    int n_tseg;
 };
-void launch_adam(const AdamArgs& a, cudaStream_t s);
+// 0, or -1 if the BF16 copies do not describe the range (overlapping or outside it).
+int launch_adam(const AdamArgs& a, cudaStream_t s);
 
 struct PolyakArgs {
     float* target; const float* src; int64_t n; float tau; int64_t* update_idx;
     BfSeg seg[kMaxBfSeg];         // padded BF16 copies of the target weight matrices
     int n_seg;
 };
-void launch_polyak(const PolyakArgs& a, cudaStream_t s);
+int launch_polyak(const PolyakArgs& a, cudaStream_t s);
 // dx = dy * (y > 0), elementwise over n values.
 template <typename T> void launch_relu_bwd(int64_t n, const T* dy, const T* y, T* dx, cudaStream_t s);
 

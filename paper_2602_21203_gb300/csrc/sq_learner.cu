@@ -543,6 +543,7 @@ int squint_handle::allocate() {
     if (const char* e = std::getenv("SQUINT_MLP_CL")) mlp_cluster = std::atoi(e);
     if (const char* e = std::getenv("SQUINT_MLP_BWD")) mlp_bwd_fused = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_PRIO")) prio_branches = std::atoi(e) != 0;
+    if (const char* e = std::getenv("SQUINT_FUSE_POLYAK")) fuse_polyak = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_BWD_CL")) mlp_bwd_cluster = std::atoi(e);
     bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
     SQ_CK(this, cudaGetDevice(&device));
@@ -949,12 +950,20 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
         launch_ln_bwd(p, n, ln_work, st);
     };
     auto adam = [&](int64_t begin, int64_t end, const int32_t* step, const int32_t* enable, cudaStream_t st,
-                    const std::vector<BfSeg>* segs = nullptr) {
+                    const std::vector<BfSeg>* segs = nullptr, bool with_polyak = false) {
         if (end <= begin) return;                  // empty range (state-based: no encoder)
         AdamArgs ad{};
         if (segs) {
             for (size_t k = 0; k < segs->size(); ++k) ad.seg[k] = (*segs)[k];
             ad.n_seg = (int)segs->size();
+        }
+        if (with_polyak) {   // the target copy of this (critic) range in the same pass
+            ad.target = target;
+            ad.tau = (float)c.tau;
+            if (bf16) {
+                for (size_t k = 0; k < seg_target.size(); ++k) ad.tseg[k] = seg_target[k];
+                ad.n_tseg = (int)seg_target.size();
+            }
         }
         ad.p = W + begin; ad.g = G + begin; ad.m = adam_m + begin; ad.v = adam_v + begin;
         ad.n = end - begin;
@@ -962,8 +971,9 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
         ad.lr = c.lr; ad.b1 = c.adam_b1; ad.b2 = c.adam_b2; ad.eps = c.adam_eps;
         double bf_bytes = 0;   // the BF16 copies written alongside
         for (int k = 0; k < ad.n_seg; ++k) bf_bytes += 2.0 * ad.seg[k].rows * ad.seg[k].cols;
-        ProfScope ps(this, st, "adam", 28.0 * (double)ad.n + bf_bytes, 1);
-        launch_adam(ad, st);
+        for (int k = 0; k < ad.n_tseg; ++k) bf_bytes += 2.0 * ad.tseg[k].rows * ad.tseg[k].cols;
+        ProfScope ps(this, st, "adam", (with_polyak ? 36.0 : 28.0) * (double)ad.n + bf_bytes, 1);
+        if (launch_adam(ad, st) != 0) launch_failed = true;
     };
     auto conv_flops = [&](const ConvL& cv, int nimg) { return 2.0 * nimg * cv.oh * cv.ow * cv.cout * cv.cin * 9; };
 
@@ -1009,9 +1019,11 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
         const int64_t img0 = (int64_t)c.obs_c * c0.h * c0.w;
         ConvShape sh{n, c0.cin, c0.h, c0.w, c0.cout, c0.s, c0.oh, c0.ow, img0, (int64_t)c0.cout * c0.oh * c0.ow};
         {
-            // first layer on CUDA cores, written straight into the padded-HWC input of layer 1
-            ProfScope ps(this, st, "conv_f32_fwd", conv_flops(c0, n), 0);
-            launch_conv0_phwc(sh, x2 + (int64_t)i0 * img0, W + c0.wo, W + c0.bo, act_p[0], st);
+            // first layer on tensor cores (CUDA cores outside that kernel's range), written
+            // straight into the padded-HWC input of layer 1
+            ProfScope ps(this, st, "conv_tc_fwd", conv_flops(c0, n), 0);
+            if (launch_conv0_tc(sh, x2 + (int64_t)i0 * img0, W + c0.wo, W + c0.bo, act_p[0], d_err, st) < 0)
+                launch_conv0_phwc(sh, x2 + (int64_t)i0 * img0, W + c0.wo, W + c0.bo, act_p[0], st);
         }
         for (int l = 1; l <= upto; ++l) {
             const ConvL& cv = L.conv[l];
@@ -1200,7 +1212,7 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
     mark(s);
     // ---- a12 (critic range): Adam over critic projection + critics, BF16 copies
     // (Adam writes the BF16 copies of the critic weights as it updates them)
-    adam(L.critic_begin, L.critic_end, d_steps + 0, nullptr, s, bf16 ? &seg_critic : nullptr);
+    adam(L.critic_begin, L.critic_end, d_steps + 0, nullptr, s, bf16 ? &seg_critic : nullptr, fuse_polyak);
     quantize_weights(quant_critic, s);
 
     // ---- a11 (encoder part) + a12 (encoder range) on branch s1, beside the actor step
@@ -1317,9 +1329,10 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
             cast_conv_weights(s1);
         }
     }
-    // ---- a16 on branch s3: polyak of the updated critics, BF16 target copies
+    // ---- a16 on branch s3: polyak of the updated critics, BF16 target copies (or in the
+    // critic Adam's pass)
     fork(s, s3);
-    {
+    if (!fuse_polyak) {
         PolyakArgs pa{};
         pa.target = target; pa.src = W + L.critic_begin; pa.n = L.target_n; pa.tau = (float)c.tau;
         if (bf16) {   // polyak writes the BF16 copies of the target weights as it updates them
@@ -1330,10 +1343,10 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
             double bf_bytes = 0;
             for (int k = 0; k < pa.n_seg; ++k) bf_bytes += 2.0 * pa.seg[k].rows * pa.seg[k].cols;
             ProfScope ps(this, s3, "polyak", 12.0 * (double)L.target_n + bf_bytes, 1);
-            launch_polyak(pa, s3);
+            if (launch_polyak(pa, s3) != 0) launch_failed = true;
         }
-        quantize_weights(quant_target, s3);
     }
+    quantize_weights(quant_target, s3);
     mark(s);
     // ---- a13 on branch s3: temperature, from log pi of the pre-update actor at s_t; the
     // actor step first reads the new alpha in its head backward (joined there)

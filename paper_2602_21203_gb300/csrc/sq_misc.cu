@@ -4,6 +4,7 @@
 #include "sq_kernels.cuh"
 
 #include <algorithm>
+#include <cstring>
 #include <vector>
 
 namespace sq {
@@ -629,73 +630,143 @@ __device__ __forceinline__ float adam_one(float p, float g, float& m, float& v, 
     return p - lr * (m / bc1) / (sqrtf(v / bc2) + ep);
 }
 
-// Elementwise Adam over [0, n): scalar head up to 16-byte alignment, float4 body, scalar tail.
-__device__ __forceinline__ void seg_store(const BfSeg* seg, int n_seg, int64_t e, float v) {
-    for (int k = 0; k < n_seg; ++k) {
-        const int64_t rel = e - seg[k].off;
-        if (rel >= 0 && rel < (int64_t)seg[k].rows * seg[k].cols) {
-            const int64_t r = rel / seg[k].cols;
-            seg[k].dst[r * seg[k].ld + (rel - r * seg[k].cols)] = __float2bfloat16_rn(v);
-            return;
+// Row tasks of an elementwise pass over [0, n) of a parameter range: each weight matrix
+// with a BF16 copy is walked by its rows (a row's element c lands at dst[r ld + c]), the
+// elements between and after the matrices in rows of kPlainCols.  A block takes one row:
+// no per-element search for the copy an element belongs to.
+constexpr int kPlainCols = 1024, kMaxRowRanges = 2 * kMaxBfSeg + 1;
+struct RowRange {
+    int64_t off, len;             // elements [off, off + len) of the range
+    int cols;                     // row length (the last row may be shorter: len)
+    int row0;                     // first row task of this range
+    int64_t ld, ldt;              // row strides of the copies
+    __nv_bfloat16* dst;           // BF16 copy of the updated value (or null)
+    __nv_bfloat16* tdst;          // BF16 copy of the updated target (or null)
+};
+struct RowPlan { RowRange r[kMaxRowRanges]; int n, rows; };
+
+__device__ __forceinline__ float polyak_one(float t, float s, float keep, float tau) {
+    return __fmaf_rn(keep, t, tau * s);
+}
+
+// Adam over one row task (with the polyak of the target copy when a.target is set).
+__global__ void __launch_bounds__(256) adam_rows_kernel(const __grid_constant__ AdamArgs a,
+                                                        const __grid_constant__ RowPlan plan) {
+    SQ_KERNEL_ENTRY();
+    if (a.enable && !*a.enable) return;
+    const int t = *a.step;
+    const float bc1 = bias_correction(a.b1, t), bc2 = bias_correction(a.b2, t);
+    const float b1 = (float)a.b1, b2 = (float)a.b2, lr = (float)a.lr, ep = (float)a.eps;
+    const float c1 = (float)(1.0 - a.b1), c2 = (float)(1.0 - a.b2);
+    const float tau = a.tau, keep = 1.0f - a.tau;
+    int k = 0;
+    while (k + 1 < plan.n && (int)blockIdx.x >= plan.r[k + 1].row0) ++k;
+    const RowRange& R = plan.r[k];
+    const int r = (int)blockIdx.x - R.row0;
+    const int64_t base = R.off + (int64_t)r * R.cols;
+    const int lim = (int)min((int64_t)R.cols, R.len - (int64_t)r * R.cols);
+    float* __restrict__ p = a.p + base;
+    const float* __restrict__ g = a.g + base;
+    float* __restrict__ m = a.m + base;
+    float* __restrict__ v = a.v + base;
+    float* __restrict__ tg = a.target ? a.target + base : nullptr;
+    __nv_bfloat16* dst = R.dst ? R.dst + (int64_t)r * R.ld : nullptr;
+    __nv_bfloat16* tdst = R.tdst ? R.tdst + (int64_t)r * R.ldt : nullptr;
+    __nv_bfloat16* pbf = a.p_bf ? a.p_bf + base : nullptr;
+    constexpr int U = 4;
+    for (int c0 = threadIdx.x; c0 < lim; c0 += U * blockDim.x) {
+        float pv[U], gv[U], mv[U], vv[U], tv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {   // every load of the group in flight before the math
+            const int c = c0 + u * blockDim.x;
+            if (c < lim) {
+                pv[u] = p[c]; gv[u] = g[c]; mv[u] = m[c]; vv[u] = v[c];
+                tv[u] = tg ? tg[c] : 0.f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = c0 + u * blockDim.x;
+            if (c >= lim) break;
+            const float np = adam_one(pv[u], gv[u], mv[u], vv[u], b1, b2, c1, c2, lr, ep, bc1, bc2);
+            p[c] = np; m[c] = mv[u]; v[c] = vv[u];
+            if (dst) dst[c] = __float2bfloat16_rn(np);
+            if (pbf) pbf[c] = __float2bfloat16_rn(np);
+            if (tg) {
+                const float nt = polyak_one(tv[u], np, keep, tau);
+                tg[c] = nt;
+                if (tdst) tdst[c] = __float2bfloat16_rn(nt);
+            }
         }
     }
 }
 
-__global__ void adam_kernel(const __grid_constant__ AdamArgs a) {
+// Polyak alone (target <- (1 - tau) target + tau src) over the same row tasks.
+__global__ void __launch_bounds__(256) polyak_rows_kernel(const __grid_constant__ PolyakArgs a,
+                                                          const __grid_constant__ RowPlan plan) {
     SQ_KERNEL_ENTRY();
-    if (a.enable && !*a.enable) return;
-    __shared__ float bc[2];
-    if (threadIdx.x == 0) {
-        bc[0] = bias_correction(a.b1, *a.step);
-        bc[1] = bias_correction(a.b2, *a.step);
-    }
-    __syncthreads();
-    const float b1 = (float)a.b1, b2 = (float)a.b2, lr = (float)a.lr, ep = (float)a.eps;
-    const float c1 = (float)(1.0 - a.b1), c2 = (float)(1.0 - a.b2);
-    const float bc1 = bc[0], bc2 = bc[1];
-    const int64_t mis = (int64_t)((16 - (reinterpret_cast<uintptr_t>(a.p) & 15)) & 15) / 4;
-    const int64_t head = mis < a.n ? mis : a.n;
-    const int64_t nv = (a.n - head) / 4;
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = tid; i < head; i += stride) {
-        float m = a.m[i], v = a.v[i];
-        const float p = adam_one(a.p[i], a.g[i], m, v, b1, b2, c1, c2, lr, ep, bc1, bc2);
-        a.m[i] = m; a.v[i] = v; a.p[i] = p;
-        if (a.p_bf) a.p_bf[i] = __float2bfloat16_rn(p);
-        if (a.n_seg) seg_store(a.seg, a.n_seg, i, p);
-    }
-    float4* p4 = reinterpret_cast<float4*>(a.p + head);
-    const float4* g4 = reinterpret_cast<const float4*>(a.g + head);
-    float4* m4 = reinterpret_cast<float4*>(a.m + head);
-    float4* v4 = reinterpret_cast<float4*>(a.v + head);
-    for (int64_t i = tid; i < nv; i += stride) {
-        float4 p = p4[i], m = m4[i], v = v4[i];
-        const float4 g = g4[i];
-        p.x = adam_one(p.x, g.x, m.x, v.x, b1, b2, c1, c2, lr, ep, bc1, bc2);
-        p.y = adam_one(p.y, g.y, m.y, v.y, b1, b2, c1, c2, lr, ep, bc1, bc2);
-        p.z = adam_one(p.z, g.z, m.z, v.z, b1, b2, c1, c2, lr, ep, bc1, bc2);
-        p.w = adam_one(p.w, g.w, m.w, v.w, b1, b2, c1, c2, lr, ep, bc1, bc2);
-        p4[i] = p; m4[i] = m; v4[i] = v;
-        if (a.p_bf) {
-            const int64_t e = head + 4 * i;
-            a.p_bf[e] = __float2bfloat16_rn(p.x); a.p_bf[e + 1] = __float2bfloat16_rn(p.y);
-            a.p_bf[e + 2] = __float2bfloat16_rn(p.z); a.p_bf[e + 3] = __float2bfloat16_rn(p.w);
+    const float tau = a.tau, keep = 1.0f - a.tau;
+    int k = 0;
+    while (k + 1 < plan.n && (int)blockIdx.x >= plan.r[k + 1].row0) ++k;
+    const RowRange& R = plan.r[k];
+    const int r = (int)blockIdx.x - R.row0;
+    const int64_t base = R.off + (int64_t)r * R.cols;
+    const int lim = (int)min((int64_t)R.cols, R.len - (int64_t)r * R.cols);
+    float* __restrict__ tg = a.target + base;
+    const float* __restrict__ sv = a.src + base;
+    __nv_bfloat16* tdst = R.tdst ? R.tdst + (int64_t)r * R.ldt : nullptr;
+    constexpr int U = 4;
+    for (int c0 = threadIdx.x; c0 < lim; c0 += U * blockDim.x) {
+        float tv[U], xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = c0 + u * blockDim.x;
+            if (c < lim) { tv[u] = tg[c]; xv[u] = sv[c]; }
         }
-        if (a.n_seg) {
-            const int64_t e = head + 4 * i;
-            seg_store(a.seg, a.n_seg, e, p.x);
-            seg_store(a.seg, a.n_seg, e + 1, p.y);
-            seg_store(a.seg, a.n_seg, e + 2, p.z);
-            seg_store(a.seg, a.n_seg, e + 3, p.w);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = c0 + u * blockDim.x;
+            if (c >= lim) break;
+            const float nt = polyak_one(tv[u], xv[u], keep, tau);
+            tg[c] = nt;
+            if (tdst) tdst[c] = __float2bfloat16_rn(nt);
         }
     }
-    for (int64_t i = head + 4 * nv + tid; i < a.n; i += stride) {
-        float m = a.m[i], v = a.v[i];
-        const float p = adam_one(a.p[i], a.g[i], m, v, b1, b2, c1, c2, lr, ep, bc1, bc2);
-        a.m[i] = m; a.v[i] = v; a.p[i] = p;
-        if (a.p_bf) a.p_bf[i] = __float2bfloat16_rn(p);
-        if (a.n_seg) seg_store(a.seg, a.n_seg, i, p);
+    if (a.update_idx && blockIdx.x == 0 && threadIdx.x == 0) *a.update_idx += 1;
+}
+
+// The row tasks of [0, n) with the matrices seg (copies dst) and, matching them one for
+// one, tseg (copies tdst; may be empty).  False if the segments overlap or leave [0, n).
+bool row_plan(int64_t n, const BfSeg* seg, int n_seg, const BfSeg* tseg, int n_tseg, RowPlan* plan) {
+    std::memset(plan, 0, sizeof(*plan));
+    int order[kMaxBfSeg];
+    for (int i = 0; i < n_seg; ++i) order[i] = i;
+    std::sort(order, order + n_seg, [&](int x, int y) { return seg[x].off < seg[y].off; });
+    int64_t cur = 0;
+    int rows = 0;
+    auto add = [&](int64_t off, int64_t len, int cols, int64_t ld, __nv_bfloat16* dst, int64_t ldt,
+                   __nv_bfloat16* tdst) {
+        if (len <= 0) return true;
+        if (plan->n >= kMaxRowRanges) return false;
+        RowRange& R = plan->r[plan->n++];
+        R.off = off; R.len = len; R.cols = cols; R.row0 = rows; R.ld = ld; R.ldt = ldt; R.dst = dst; R.tdst = tdst;
+        rows += (int)((len + cols - 1) / cols);
+        return true;
+    };
+    for (int q = 0; q < n_seg; ++q) {
+        const int i = order[q];
+        const BfSeg& S = seg[i];
+        const int64_t len = (int64_t)S.rows * S.cols;
+        if (S.off < cur || S.off + len > n || S.cols < 1) return false;
+        if (!add(cur, S.off - cur, kPlainCols, 0, nullptr, 0, nullptr)) return false;
+        const bool t = i < n_tseg;
+        if (t && (tseg[i].off != S.off || tseg[i].rows != S.rows || tseg[i].cols != S.cols)) return false;
+        if (!add(S.off, len, S.cols, S.ld, S.dst, t ? tseg[i].ld : 0, t ? tseg[i].dst : nullptr)) return false;
+        cur = S.off + len;
     }
+    if (!add(cur, n - cur, kPlainCols, 0, nullptr, 0, nullptr)) return false;
+    plan->rows = rows;
+    return true;
 }
 
 // dx = dy where y > 0, else 0 (the ReLU's backward given its output y).
@@ -704,17 +775,6 @@ __global__ void relu_bwd_kernel(int64_t n, const T* __restrict__ dy, const T* __
     SQ_KERNEL_ENTRY();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         dx[i] = y[i] > T(0) ? dy[i] : T(0);
-}
-
-__global__ void polyak_kernel(const __grid_constant__ PolyakArgs a) {
-    SQ_KERNEL_ENTRY();
-    const float keep = 1.0f - a.tau;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float t = keep * a.target[i] + a.tau * a.src[i];
-        a.target[i] = t;
-        if (a.n_seg) seg_store(a.seg, a.n_seg, i, t);
-    }
-    if (a.update_idx && blockIdx.x == 0 && threadIdx.x == 0) *a.update_idx += 1;
 }
 
 template <typename P> Batch<P> make_batch(const P* p, int n) {
@@ -804,9 +864,12 @@ void launch_ce(const CeArgs& a, cudaStream_t s) { launch_k(ce_kernel, dim3(a.E *
 void launch_actor_q(const ActorQArgs& a, cudaStream_t s) { launch_k(actor_q_kernel, dim3(a.B), dim3(128), 0, s, a); }
 void launch_alpha_step(const AlphaArgs& a, cudaStream_t s) { launch_k(alpha_kernel, dim3(1), dim3(256), 0, s, a); }
 void launch_stats(const StatsArgs& a, cudaStream_t s) { launch_k(stats_kernel, dim3(1), dim3(256), 0, s, a); }
-void launch_adam(const AdamArgs& a, cudaStream_t s) {
-    const int blocks = (int)std::min<int64_t>((a.n / 4 + 255) / 256 + 1, 152 * 4);
-    if (a.n > 0) launch_k(adam_kernel, dim3(blocks), dim3(256), 0, s, a);
+int launch_adam(const AdamArgs& a, cudaStream_t s) {
+    if (a.n <= 0) return 0;
+    RowPlan plan;
+    if (!row_plan(a.n, a.seg, a.n_seg, a.tseg, a.target ? a.n_tseg : 0, &plan) || plan.rows < 1) return -1;
+    launch_k(adam_rows_kernel, dim3(plan.rows), dim3(256), 0, s, a, plan);
+    return 0;
 }
 template <typename T>
 void launch_relu_bwd(int64_t n, const T* dy, const T* y, T* dx, cudaStream_t s) {
@@ -817,9 +880,13 @@ void launch_relu_bwd(int64_t n, const T* dy, const T* y, T* dx, cudaStream_t s) 
 template void launch_relu_bwd<float>(int64_t, const float*, const float*, float*, cudaStream_t);
 template void launch_relu_bwd<double>(int64_t, const double*, const double*, double*, cudaStream_t);
 
-void launch_polyak(const PolyakArgs& a, cudaStream_t s) {
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((a.n + 255) / 256, 152 * 8));
-    launch_k(polyak_kernel, dim3(blocks), dim3(256), 0, s, a);
+int launch_polyak(const PolyakArgs& a, cudaStream_t s) {
+    if (a.n <= 0) return 0;
+    // the copies are described by the target segments alone: pass them as both lists
+    RowPlan plan;
+    if (!row_plan(a.n, a.seg, a.n_seg, a.seg, a.n_seg, &plan) || plan.rows < 1) return -1;
+    launch_k(polyak_rows_kernel, dim3(plan.rows), dim3(256), 0, s, a, plan);
+    return 0;
 }
 void launch_act_head(const ActHeadArgs& a, cudaStream_t s) {
     if (a.rows > 0) launch_k(act_head_kernel, dim3((a.rows + 127) / 128), dim3(128), 0, s, a);

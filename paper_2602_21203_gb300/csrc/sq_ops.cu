@@ -360,6 +360,19 @@ int squint_op_conv32(int mode, int nimg, int H, int W, const void* in, const voi
     return launch_status();
 }
 
+int squint_op_conv0_bf16(int nimg, int Cin, int H, int W, int stride, const float* x, const float* w,
+                         const float* bias, void* out_phwc, void* stream) {
+    if (nimg < 0 || Cin < 1 || Cin > 16 || stride < 1 || H < 3 || W < 3 || !x || !w || !bias || !out_phwc)
+        return SQUINT_EINVAL;
+    if (reinterpret_cast<uintptr_t>(out_phwc) & 15) return SQUINT_EINVAL;
+    int* err = tc_error_flag();
+    if (!err) return SQUINT_ECUDA;
+    const int OH = (H - 3) / stride + 1, OW = (W - 3) / stride + 1;
+    ConvShape sh{nimg, Cin, H, W, 32, stride, OH, OW, (int64_t)Cin * H * W, (int64_t)32 * OH * OW};
+    if (launch_conv0_tc(sh, x, w, bias, (__nv_bfloat16*)out_phwc, err, (cudaStream_t)stream) != 0) return SQUINT_EINVAL;
+    return launch_status();
+}
+
 size_t squint_op_wgrad32_workspace(int nimg) { return nimg > 0 ? 4 * (size_t)wgrad32_tc_workspace(nimg) : 0; }
 
 int squint_op_wgrad32(int nimg, int H, int W, const void* x, const void* dy, float* dw, float* db, void* work,

@@ -302,7 +302,8 @@ int squint_handle::act(sq::ActArena& a, const squint_act_request* reqs, int n_re
         ConvShape sh{rows, cv.cin, cv.h, cv.w, cv.cout, cv.s, cv.oh, cv.ow, (int64_t)cv.cin * cv.h * cv.w,
                      (int64_t)cv.cout * cv.oh * cv.ow};
         if (tc && l == 0) {   // first layer straight into the padded-HWC input of the tensor-core layers
-            launch_conv0_phwc(sh, in, Wp + cv.wo, Wp + cv.bo, aphwc[0], s);
+            if (launch_conv0_tc(sh, in, Wp + cv.wo, Wp + cv.bo, aphwc[0], d_err, s) < 0)
+                launch_conv0_phwc(sh, in, Wp + cv.wo, Wp + cv.bo, aphwc[0], s);
             continue;
         }
         launch_conv_fwd<float>(sh, in, Wp + cv.wo, Wp + cv.bo, aconv[l], true, s);

@@ -135,6 +135,7 @@ def load():
         "squint_op_from_phwc": (I, [I, I, I, P, P, P]),
         "squint_op_conv32_layouts": (I, [P, P, P, P]),
         "squint_op_conv32": (I, [I, I, I, I, P, P, P, I, P, P, P, P]),
+        "squint_op_conv0_bf16": (I, [I, I, I, I, I, P, P, P, P, P]),
         "squint_op_wgrad32_workspace": (SZ, [I]),
         "squint_op_wgrad32": (I, [I, I, I, P, P, P, P, P, SZ, P]),
         "squint_op_conv3x3_wgrad_noalloc_max": (I64, []),

@@ -314,6 +314,19 @@ def from_phwc(t, H, W):
     return out
 
 
+def conv0_bf16(x, w, bias, stride, out=None):
+    """The encoder's first layer on tensor cores: x NCHW FP32 [n, Cin, H, W], w [32, Cin, 3, 3],
+    bias [32] -> ReLU(conv + bias) as padded-HWC BF16 (interior written; `out` defaults to a
+    zero-filled buffer)."""
+    n, cin, H, W = x.shape
+    OH, OW = (H - 3) // stride + 1, (W - 3) // stride + 1
+    if out is None:
+        out = phwc_empty(n, OH, OW, x.device)
+    _chk(_lib.load().squint_op_conv0_bf16(n, cin, H, W, int(stride), _p(x.contiguous()), _p(w.contiguous()),
+                                          _p(bias.contiguous()), _p(out), _s()), "squint_op_conv0_bf16")
+    return out
+
+
 def conv32_layouts(w):
     fwd = torch.empty(9 * 32 * 32, dtype=torch.bfloat16, device=w.device)
     bwd = torch.empty_like(fwd)

@@ -307,3 +307,34 @@ def test_conv32_tensor_core_matches_oracle(ops, n, H):
     torch.cuda.synchronize()
     assert _rel(dw.cpu().numpy(), rdw) < 1e-5
     assert _rel(db.cpu().numpy(), rdb) < 1e-5
+
+
+# (images, input channels, height = width, stride): the training encoder's first layer
+# (3 x 32 x 32, stride 2) over several 128-pixel tiles with a ragged last one, a single
+# image, one channel at stride 1, and the wider filters (K = 63, K = 108) of the other
+# tile widths, stride 3
+@pytest.mark.parametrize("n,cin,H,s", [(300, 3, 32, 2), (1, 3, 32, 2), (5, 1, 11, 1), (7, 7, 20, 2), (3, 12, 17, 3)])
+def test_conv0_tensor_core_matches_oracle(ops, n, cin, H, s):
+    """The first layer on tcgen05 (BF16 operands, FP32 accumulation) against the FP64
+    oracle on the same BF16-rounded inputs: each output is the BF16 rounding of the
+    oracle's value, or (an FP32 sum that lands on the other side of a rounding boundary)
+    within one BF16 step of it; the 2-pixel border of the padded output is not touched."""
+    g = torch.Generator().manual_seed(40 + cin + H)
+    W = H
+    x = torch.rand(n, cin, H, W, generator=g).bfloat16().float()
+    w = (torch.randn(32, cin, 3, 3, generator=g) * 0.3).bfloat16().float()
+    b = torch.randn(32, generator=g) * 0.1
+    OH = (H - 3) // s + 1
+    out = torch.full((n, OH + 4, OH + 4, 32), float("nan"), dtype=torch.bfloat16, device="cuda")
+    ops.conv0_bf16(x.cuda(), w.cuda(), b.cuda(), s, out=out)
+    torch.cuda.synchronize()
+    got = out.float().cpu()
+    border = torch.ones(OH + 4, OH + 4, dtype=torch.bool)
+    border[2:OH + 2, 2:OH + 2] = False
+    assert torch.isnan(got[:, border]).all()
+    y = got[:, 2:OH + 2, 2:OH + 2, :].permute(0, 3, 1, 2).double().numpy()
+    ref = np.maximum(o.conv3x3_fwd(x.double().numpy(), w.double().numpy(), b.double().numpy(), s), 0)
+    ref_bf = torch.from_numpy(ref).to(torch.bfloat16).double().numpy()
+    off = y != ref_bf
+    assert np.all(np.abs(y - ref)[off] <= 2.0 ** -8 * np.abs(ref)[off] + 1e-6)
+    assert off.mean() < 1e-2, off.mean()

@@ -530,3 +530,26 @@ def test_trace_update_reports_every_launch_on_its_branch(L):
     classes = set(learner.profile_kernels())
     assert {n for n, _, _, _ in tr} == classes
     learner.close()
+
+
+# ---------------------------------------------------------------- polyak in the Adam pass
+@pytest.mark.parametrize("prec", ["FP32", "BF16"])
+def test_polyak_fused_into_adam_equals_its_own_launch(L, monkeypatch, prec):
+    """The target critics' polyak done inside the critic Adam's pass gives the same bits
+    (parameters, target, Adam moments, statistics) as its own launch after it."""
+    cfg = synth.make_config("small_b32")
+    ring = synth.make_ring(cfg, 0, device="cuda")
+    monkeypatch.setenv("SQUINT_FUSE_POLYAK", "0")
+    a = L.Learner(cfg, ring, precision=getattr(L, "PREC_" + prec), max_k=2)
+    monkeypatch.setenv("SQUINT_FUSE_POLYAK", "1")
+    b = L.Learner(cfg, ring, precision=getattr(L, "PREC_" + prec), max_k=2)
+    sa = a.update(2)
+    sb = b.update(2)
+    for x, y in zip(sa, sb):
+        for k in ("critic_loss", "actor_loss", "q_mean"):
+            assert x[k] == y[k] or (math.isnan(x[k]) and math.isnan(y[k])), k
+    assert np.array_equal(a.params(), b.params())
+    assert np.array_equal(a.debug("target"), b.debug("target"))
+    assert a.state() == b.state()
+    a.close()
+    b.close()
