@@ -620,13 +620,16 @@ __global__ void __launch_bounds__(128, PL == 4 ? 5 : 2) conv0_tc_kernel(const __
     const ConvShape& sh = a.sh;
     const int opix = sh.OH * sh.OW;
 
+    // inputs are read, and tensor memory taken, only once the previous kernel has finished,
+    // as in every tcgen05 kernel of the library: a kernel lets its dependents launch before
+    // it allocates, so one that allocated before its wait could hold columns its primary needs
+    SQ_KERNEL_ENTRY();
     if (warp == 0) tmem_alloc(smem_u32(tmem_slot), 64);
     if (threadIdx.x == 0) {
         mbar_init(bar0, 1);
         mbar_init(bar0 + 8, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    SQ_KERNEL_ENTRY();   // the input and the filter come from earlier kernels
     for (int e = threadIdx.x; e < 32 * PL; e += 128) {   // filter row co, 8 k-values of plane c
         const int co = e / PL, c = e % PL;
         __align__(16) __nv_bfloat16 hb[8];
