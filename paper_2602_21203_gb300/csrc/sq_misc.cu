@@ -268,44 +268,36 @@ __device__ float block_sum(float v, float* sh) {
     for (int i = 0; i < (int)(blockDim.x / 32); ++i) t += sh[i];
     return t;
 }
-__device__ float block_max(float v, float* sh) {
-    v = warp_max(v);
-    const int w = threadIdx.x / 32, lane = threadIdx.x % 32;
-    __syncthreads();
-    if (lane == 0) sh[w] = v;
-    __syncthreads();
-    float t = -INFINITY;
-    for (int i = 0; i < (int)(blockDim.x / 32); ++i) t = fmaxf(t, sh[i]);
-    return t;
-}
-
-constexpr int kMaxAtoms = 256;
 
 // ---------------------------------------------------------------- C51 target
-// One block per sample: average of the target critics' categorical
-// distributions, projected onto the fixed support as
-// m_j = sum_i P_i max(0, 1 - |b_i - j|)   (linear interpolation between the two
-// neighbouring atoms of b_i = (clip(r + gamma (1-d)(z_i - alpha log pi')) - v_min)/dz).
-// Clipped double Q: per sample the distribution of the target critic with the smaller
-// mean (ties to critic 0).  MSE critics (K = 1): y = r + gamma (1-d)(Q_bar - alpha log pi')
-// with Q_bar the average (or, with clipped double Q, the minimum) of the target outputs.
-__global__ void c51_target_kernel(C51TargetArgs a) {
+// One warp per sample (kHeadRows samples a block, V atoms a lane: atom j = lane + 32 k):
+// average of the target critics' categorical distributions, projected onto the fixed
+// support as m_j = sum_i P_i max(0, 1 - |b_i - j|)   (linear interpolation between the
+// two neighbouring atoms of b_i = (clip(r + gamma (1-d)(z_i - alpha log pi')) - v_min)/dz),
+// the sum over i in order.  Clipped double Q: per sample the distribution of the target
+// critic with the smaller mean (ties to critic 0).  MSE critics (K = 1): y = r + gamma
+// (1-d)(Q_bar - alpha log pi') with Q_bar the average (or, with clipped double Q, the
+// minimum) of the target outputs.  Softmax statistics by warp shuffles, no block barrier.
+constexpr int kHeadRows = 8;
+
+template <int V>
+__global__ void __launch_bounds__(32 * kHeadRows) c51_target_kernel(C51TargetArgs a) {
     SQ_KERNEL_ENTRY();
-    __shared__ float pbar[kMaxAtoms];
-    __shared__ float bpos[kMaxAtoms];
-    __shared__ float red[32];
-    const int row = blockIdx.x;
-    if (a.steps && row == 0 && threadIdx.x == 0) {
+    __shared__ float sp[kHeadRows][32 * V], sb[kHeadRows][32 * V];
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int row = blockIdx.x * kHeadRows + warp;
+    if (a.steps && blockIdx.x == 0 && threadIdx.x == 0) {
         const int act = (((uint64_t)*a.update_idx + 1) % (uint64_t)a.policy_freq) == 0;
         a.steps[0] += 1;
         a.steps[2] += 1;
         a.steps[1] += act;
         *a.do_actor = act;
     }
+    if (row >= a.B) return;
     const float alpha = a.log_alpha ? expf(*a.log_alpha) : a.alpha_value;
     const float r = a.r[row], nd = 1.0f - a.d[row], lp = a.logp_next[row];
     if (a.mse) {
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             float qb = a.cdq ? INFINITY : 0.f;
             for (int e = 0; e < a.E; ++e) {
                 const float q = a.logits_bar[(int64_t)e * a.B + row];
@@ -316,66 +308,96 @@ __global__ void c51_target_kernel(C51TargetArgs a) {
         }
         return;
     }
-    const float dz = (a.v_max - a.v_min) / (float)(a.K - 1);
+    const int K = a.K;
+    const float dz = (a.v_max - a.v_min) / (float)(K - 1);
     int pick = -1;   // clipped double Q: the critic whose distribution is used
     if (a.cdq) {
         float best = INFINITY;
         for (int e = 0; e < a.E; ++e) {
-            const float* lg = a.logits_bar + ((int64_t)e * a.B + row) * a.K;
-            float mx = -INFINITY;
-            for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
-            mx = block_max(mx, red);
-            float s = 0.f, q = 0.f;
-            for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
-                const float p = expf(lg[j] - mx);
-                s += p;
-                q += p * (a.v_min + (float)j * dz);
+            const float* lg = a.logits_bar + ((int64_t)e * a.B + row) * K;
+            float l[V], mx = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int j = lane + 32 * k;
+                l[k] = j < K ? lg[j] : -INFINITY;
+                mx = fmaxf(mx, l[k]);
             }
-            s = block_sum(s, red);
-            q = block_sum(q, red) / s;
+            mx = warp_max(mx);
+            float s = 0.f, q = 0.f;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int j = lane + 32 * k;
+                if (j < K) {
+                    const float p = expf(l[k] - mx);
+                    s += p;
+                    q += p * (a.v_min + (float)j * dz);
+                }
+            }
+            s = warp_sum(s);
+            q = warp_sum(q) / s;
             if (q < best) { best = q; pick = e; }
         }
     }
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) pbar[j] = 0.f;
+    float pb[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) pb[k] = 0.f;
     for (int e = 0; e < a.E; ++e) {
         if (pick >= 0 && e != pick) continue;
-        const float* lg = a.logits_bar + ((int64_t)e * a.B + row) * a.K;
-        float mx = -INFINITY;
-        for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
-        mx = block_max(mx, red);
+        const float* lg = a.logits_bar + ((int64_t)e * a.B + row) * K;
+        float l[V], mx = -INFINITY;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int j = lane + 32 * k;
+            l[k] = j < K ? lg[j] : -INFINITY;
+            mx = fmaxf(mx, l[k]);
+        }
+        mx = warp_max(mx);
         float s = 0.f;
-        for (int j = threadIdx.x; j < a.K; j += blockDim.x) s += expf(lg[j] - mx);
-        s = block_sum(s, red);
-        for (int j = threadIdx.x; j < a.K; j += blockDim.x) pbar[j] += expf(lg[j] - mx) / s;
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if (lane + 32 * k < K) s += expf(l[k] - mx);
+        s = warp_sum(s);
+#pragma unroll
+        for (int k = 0; k < V; ++k)
+            if (lane + 32 * k < K) pb[k] += expf(l[k] - mx) / s;
     }
     const float n_used = pick >= 0 ? 1.f : (float)a.E;
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
-        pbar[j] /= n_used;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const int j = lane + 32 * k;
+        if (j >= K) break;
         const float zj = a.v_min + (float)j * dz;
         float tz = r + a.gamma * nd * (zj - alpha * lp);
         tz = fminf(fmaxf(tz, a.v_min), a.v_max);
-        bpos[j] = fminf(fmaxf((tz - a.v_min) / dz, 0.f), (float)(a.K - 1));
+        sp[warp][j] = pb[k] / n_used;
+        sb[warp][j] = fminf(fmaxf((tz - a.v_min) / dz, 0.f), (float)(K - 1));
     }
-    __syncthreads();
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const int j = lane + 32 * k;
+        if (j >= K) break;
         float acc = 0.f;
-        for (int i = 0; i < a.K; ++i) acc += pbar[i] * fmaxf(0.f, 1.0f - fabsf(bpos[i] - (float)j));
-        a.m[(int64_t)row * a.K + j] = acc;
+        for (int i = 0; i < K; ++i) acc += sp[warp][i] * fmaxf(0.f, 1.0f - fabsf(sb[warp][i] - (float)j));
+        a.m[(int64_t)row * K + j] = acc;
     }
 }
 
 // ---------------------------------------------------------------- cross entropy
-// One block per (critic, sample): -sum m log softmax(l), d/dl = (softmax - m)/B, Q = sum softmax z.
+// One warp per (critic, sample): -sum m log softmax(l), d/dl = (softmax - m)/B, Q = sum softmax z.
 // MSE critics (K = 1): loss (Q - y)^2 with y = m[row], dQ = 2 (Q - y) / B, Q = the output.
-__global__ void ce_kernel(CeArgs a) {
+template <int V>
+__global__ void __launch_bounds__(32 * kHeadRows) ce_kernel(CeArgs a) {
     SQ_KERNEL_ENTRY();
-    __shared__ float red[32];
-    const int er = blockIdx.x;          // e * B + row
+    const int lane = threadIdx.x % 32;
+    const int er = blockIdx.x * kHeadRows + threadIdx.x / 32;   // e * B + row
+    if (er >= a.E * a.B) return;
     const int row = er % a.B;
-    const float* lg = a.logits + (int64_t)er * a.K;
-    const float* m = a.m + (int64_t)row * a.K;
+    const int K = a.K;
+    const float* lg = a.logits + (int64_t)er * K;
+    const float* m = a.m + (int64_t)row * K;
     if (a.mse) {
-        if (threadIdx.x == 0) {
+        if (lane == 0) {
             const float q = lg[0], err = q - m[0];
             const float g = 2.0f * err * a.scale;
             a.dlogits[er] = g;
@@ -385,86 +407,114 @@ __global__ void ce_kernel(CeArgs a) {
         }
         return;
     }
-    const float dz = (a.v_max - a.v_min) / (float)(a.K - 1);
-    float mx = -INFINITY;
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
-    mx = block_max(mx, red);
+    const float dz = (a.v_max - a.v_min) / (float)(K - 1);
+    float l[V], mv[V], mx = -INFINITY;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const int j = lane + 32 * k;
+        l[k] = j < K ? lg[j] : -INFINITY;
+        mv[k] = j < K ? m[j] : 0.f;
+        mx = fmaxf(mx, l[k]);
+    }
+    mx = warp_max(mx);
     float s = 0.f;
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) s += expf(lg[j] - mx);
-    s = block_sum(s, red);
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+        if (lane + 32 * k < K) s += expf(l[k] - mx);
+    s = warp_sum(s);
     const float lse = mx + logf(s);
     float loss = 0.f, q = 0.f;
-    for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
-        const float ls = lg[j] - lse;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        const int j = lane + 32 * k;
+        if (j >= K) break;
+        const float ls = l[k] - lse;
         const float p = expf(ls);
-        loss -= m[j] * ls;
+        loss -= mv[k] * ls;
         q += p * (a.v_min + (float)j * dz);
-        const float g = (p - m[j]) * a.scale;
-        a.dlogits[(int64_t)er * a.K + j] = g;
+        const float g = (p - mv[k]) * a.scale;
+        a.dlogits[(int64_t)er * K + j] = g;
         if (a.dlogits_bf) a.dlogits_bf[(int64_t)er * a.ld_bf + j] = __float2bfloat16_rn(g);
     }
-    loss = block_sum(loss, red);
-    q = block_sum(q, red);
-    if (threadIdx.x == 0) { a.row_loss[er] = loss; a.row_q[er] = q; }
+    loss = warp_sum(loss);
+    q = warp_sum(q);
+    if (lane == 0) { a.row_loss[er] = loss; a.row_q[er] = q; }
 }
 
-// Actor objective through the critics, one block per sample over all critics:
+// Actor objective through the critics, one warp per sample over all critics:
 // Q_i = sum p z (or the scalar output), combined as the average (d/dQ_i = -1/(E B)) or,
 // with clipped double Q, the minimum (d/dQ_i = -1/B for the smaller critic, ties to 0);
 // categorical critics pass it on as dQ/dl_j = p_j (z_j - Q).
-__global__ void actor_q_kernel(ActorQArgs a) {
+constexpr int kMaxE = 8;
+template <int V>
+__global__ void __launch_bounds__(32 * kHeadRows) actor_q_kernel(ActorQArgs a) {
     SQ_KERNEL_ENTRY();
     if (!*a.do_actor) return;
-    __shared__ float red[32];
-    __shared__ float qv[8];
-    const int row = blockIdx.x;
-    const float dz = a.mse ? 0.f : (a.v_max - a.v_min) / (float)(a.K - 1);
-    for (int e = 0; e < a.E; ++e) {
-        const float* lg = a.logits + ((int64_t)e * a.B + row) * a.K;
-        float q;
+    const int lane = threadIdx.x % 32;
+    const int row = blockIdx.x * kHeadRows + threadIdx.x / 32;
+    if (row >= a.B) return;
+    const int K = a.K;
+    const float dz = a.mse ? 0.f : (a.v_max - a.v_min) / (float)(K - 1);
+    float qv[kMaxE], mxv[kMaxE], sv[kMaxE];
+#pragma unroll
+    for (int e = 0; e < kMaxE; ++e) {
+        if (e >= a.E) break;
+        const float* lg = a.logits + ((int64_t)e * a.B + row) * K;
         if (a.mse) {
-            q = lg[0];
+            qv[e] = lg[0];
         } else {
-            float mx = -INFINITY;
-            for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
-            mx = block_max(mx, red);
+            float l[V], mx = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int j = lane + 32 * k;
+                l[k] = j < K ? lg[j] : -INFINITY;
+                mx = fmaxf(mx, l[k]);
+            }
+            mx = warp_max(mx);
             float s = 0.f;
-            for (int j = threadIdx.x; j < a.K; j += blockDim.x) s += expf(lg[j] - mx);
-            s = block_sum(s, red);
-            q = 0.f;
-            for (int j = threadIdx.x; j < a.K; j += blockDim.x) q += expf(lg[j] - mx) / s * (a.v_min + (float)j * dz);
-            q = block_sum(q, red);
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (lane + 32 * k < K) s += expf(l[k] - mx);
+            s = warp_sum(s);
+            float q = 0.f;
+#pragma unroll
+            for (int k = 0; k < V; ++k) {
+                const int j = lane + 32 * k;
+                if (j < K) q += expf(l[k] - mx) / s * (a.v_min + (float)j * dz);
+            }
+            qv[e] = warp_sum(q);
+            mxv[e] = mx;
+            sv[e] = s;
         }
-        if (threadIdx.x == 0) { qv[e] = q; a.row_q[(int64_t)e * a.B + row] = q; }
+        if (lane == 0) a.row_q[(int64_t)e * a.B + row] = qv[e];
     }
-    __syncthreads();
     int pick = -1;
     if (a.cdq) {
         pick = 0;
-        for (int e = 1; e < a.E; ++e)
-            if (qv[e] < qv[pick]) pick = e;
+#pragma unroll
+        for (int e = 1; e < kMaxE; ++e)
+            if (e < a.E && qv[e] < qv[pick]) pick = e;
     }
-    for (int e = 0; e < a.E; ++e) {
+#pragma unroll
+    for (int e = 0; e < kMaxE; ++e) {
+        if (e >= a.E) break;
         const float dq = pick < 0 ? -1.0f / (float)(a.E * a.B) : (e == pick ? -1.0f / (float)a.B : 0.f);
-        const float* lg = a.logits + ((int64_t)e * a.B + row) * a.K;
         const int64_t er = (int64_t)e * a.B + row;
         if (a.mse) {
-            if (threadIdx.x == 0) {
+            if (lane == 0) {
                 a.dlogits[er] = dq;
                 if (a.dlogits_bf) a.dlogits_bf[er * a.ld_bf] = __float2bfloat16_rn(dq);
             }
             continue;
         }
-        float mx = -INFINITY;
-        for (int j = threadIdx.x; j < a.K; j += blockDim.x) mx = fmaxf(mx, lg[j]);
-        mx = block_max(mx, red);
-        float s = 0.f;
-        for (int j = threadIdx.x; j < a.K; j += blockDim.x) s += expf(lg[j] - mx);
-        s = block_sum(s, red);
-        for (int j = threadIdx.x; j < a.K; j += blockDim.x) {
-            const float p = expf(lg[j] - mx) / s;
+        const float* lg = a.logits + er * K;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int j = lane + 32 * k;
+            if (j >= K) break;
+            const float p = expf(lg[j] - mxv[e]) / sv[e];
             const float g = dq * p * (a.v_min + (float)j * dz - qv[e]);
-            a.dlogits[er * a.K + j] = g;
+            a.dlogits[er * K + j] = g;
             if (a.dlogits_bf) a.dlogits_bf[er * a.ld_bf + j] = __float2bfloat16_rn(g);
         }
     }
@@ -859,9 +909,22 @@ void launch_actor_head(const ActorHeadArgs& a, cudaStream_t s) {
 void launch_actor_head_bwd(const ActorHeadBwdArgs& a, cudaStream_t s) {
     launch_k(actor_head_bwd_kernel, dim3((a.B + 127) / 128), dim3(128), 0, s, a);
 }
-void launch_c51_target(const C51TargetArgs& a, cudaStream_t s) { launch_k(c51_target_kernel, dim3(a.B), dim3(128), 0, s, a); }
-void launch_ce(const CeArgs& a, cudaStream_t s) { launch_k(ce_kernel, dim3(a.E * a.B), dim3(128), 0, s, a); }
-void launch_actor_q(const ActorQArgs& a, cudaStream_t s) { launch_k(actor_q_kernel, dim3(a.B), dim3(128), 0, s, a); }
+// atoms per lane: 4 up to 128 atoms, 8 up to 256 (the most a configuration takes)
+void launch_c51_target(const C51TargetArgs& a, cudaStream_t s) {
+    const dim3 g((a.B + kHeadRows - 1) / kHeadRows), t(32 * kHeadRows);
+    if (a.K <= 128) launch_k(c51_target_kernel<4>, g, t, 0, s, a);
+    else launch_k(c51_target_kernel<8>, g, t, 0, s, a);
+}
+void launch_ce(const CeArgs& a, cudaStream_t s) {
+    const dim3 g((a.E * a.B + kHeadRows - 1) / kHeadRows), t(32 * kHeadRows);
+    if (a.K <= 128) launch_k(ce_kernel<4>, g, t, 0, s, a);
+    else launch_k(ce_kernel<8>, g, t, 0, s, a);
+}
+void launch_actor_q(const ActorQArgs& a, cudaStream_t s) {
+    const dim3 g((a.B + kHeadRows - 1) / kHeadRows), t(32 * kHeadRows);
+    if (a.K <= 128) launch_k(actor_q_kernel<4>, g, t, 0, s, a);
+    else launch_k(actor_q_kernel<8>, g, t, 0, s, a);
+}
 void launch_alpha_step(const AlphaArgs& a, cudaStream_t s) { launch_k(alpha_kernel, dim3(1), dim3(256), 0, s, a); }
 void launch_stats(const StatsArgs& a, cudaStream_t s) { launch_k(stats_kernel, dim3(1), dim3(256), 0, s, a); }
 int launch_adam(const AdamArgs& a, cudaStream_t s) {

@@ -15,7 +15,10 @@ from util import lazy_ring, rel_err, ring_to_device, split_params
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = {"mse": dict(critic="mse"), "cdq": dict(cdq=True), "mse_cdq": dict(critic="mse", cdq=True)}
+# the MSE critic, clipped double Q, both; 201 atoms (more than four a lane in the warp-per-
+# sample head kernels) with and without clipped double Q
+VARIANTS = {"mse": dict(critic="mse"), "cdq": dict(cdq=True), "mse_cdq": dict(critic="mse", cdq=True),
+            "atoms201": dict(atoms=201), "atoms201_cdq": dict(atoms=201, cdq=True)}
 
 
 @pytest.fixture(scope="module")
