@@ -673,11 +673,13 @@ __global__ void stats_kernel(StatsArgs a) {
 }
 
 // ---------------------------------------------------------------- Adam and polyak
+// One Adam step; ibc1, ibc2 the reciprocals of the bias corrections 1 - beta^t (one
+// division and one square root an element).
 __device__ __forceinline__ float adam_one(float p, float g, float& m, float& v, float b1, float b2, float c1, float c2,
-                                          float lr, float ep, float bc1, float bc2) {
+                                          float lr, float ep, float ibc1, float ibc2) {
     m = b1 * m + c1 * g;
     v = b2 * v + c2 * g * g;
-    return p - lr * (m / bc1) / (sqrtf(v / bc2) + ep);
+    return p - (lr * (m * ibc1)) / (sqrtf(v * ibc2) + ep);
 }
 
 // Row tasks of an elementwise pass over [0, n) of a parameter range: each weight matrix
@@ -685,6 +687,8 @@ __device__ __forceinline__ float adam_one(float p, float g, float& m, float& v, 
 // elements between and after the matrices in rows of kPlainCols.  A block takes one row:
 // no per-element search for the copy an element belongs to.
 constexpr int kPlainCols = 1024, kMaxRowRanges = 2 * kMaxBfSeg + 1;
+// threads of a row task: rows of the heads are 101 to 2,592 elements long
+constexpr int kRowThreads = 128;
 struct RowRange {
     int64_t off, len;             // elements [off, off + len) of the range
     int cols;                     // row length (the last row may be shorter: len)
@@ -700,12 +704,12 @@ __device__ __forceinline__ float polyak_one(float t, float s, float keep, float 
 }
 
 // Adam over one row task (with the polyak of the target copy when a.target is set).
-__global__ void __launch_bounds__(256) adam_rows_kernel(const __grid_constant__ AdamArgs a,
+__global__ void __launch_bounds__(kRowThreads) adam_rows_kernel(const __grid_constant__ AdamArgs a,
                                                         const __grid_constant__ RowPlan plan) {
     SQ_KERNEL_ENTRY();
     if (a.enable && !*a.enable) return;
     const int t = *a.step;
-    const float bc1 = bias_correction(a.b1, t), bc2 = bias_correction(a.b2, t);
+    const float ibc1 = 1.0f / bias_correction(a.b1, t), ibc2 = 1.0f / bias_correction(a.b2, t);
     const float b1 = (float)a.b1, b2 = (float)a.b2, lr = (float)a.lr, ep = (float)a.eps;
     const float c1 = (float)(1.0 - a.b1), c2 = (float)(1.0 - a.b2);
     const float tau = a.tau, keep = 1.0f - a.tau;
@@ -738,7 +742,7 @@ __global__ void __launch_bounds__(256) adam_rows_kernel(const __grid_constant__ 
         for (int u = 0; u < U; ++u) {
             const int c = c0 + u * blockDim.x;
             if (c >= lim) break;
-            const float np = adam_one(pv[u], gv[u], mv[u], vv[u], b1, b2, c1, c2, lr, ep, bc1, bc2);
+            const float np = adam_one(pv[u], gv[u], mv[u], vv[u], b1, b2, c1, c2, lr, ep, ibc1, ibc2);
             p[c] = np; m[c] = mv[u]; v[c] = vv[u];
             if (dst) dst[c] = __float2bfloat16_rn(np);
             if (pbf) pbf[c] = __float2bfloat16_rn(np);
@@ -752,7 +756,7 @@ __global__ void __launch_bounds__(256) adam_rows_kernel(const __grid_constant__ 
 }
 
 // Polyak alone (target <- (1 - tau) target + tau src) over the same row tasks.
-__global__ void __launch_bounds__(256) polyak_rows_kernel(const __grid_constant__ PolyakArgs a,
+__global__ void __launch_bounds__(kRowThreads) polyak_rows_kernel(const __grid_constant__ PolyakArgs a,
                                                           const __grid_constant__ RowPlan plan) {
     SQ_KERNEL_ENTRY();
     const float tau = a.tau, keep = 1.0f - a.tau;
@@ -931,7 +935,7 @@ int launch_adam(const AdamArgs& a, cudaStream_t s) {
     if (a.n <= 0) return 0;
     RowPlan plan;
     if (!row_plan(a.n, a.seg, a.n_seg, a.tseg, a.target ? a.n_tseg : 0, &plan) || plan.rows < 1) return -1;
-    launch_k(adam_rows_kernel, dim3(plan.rows), dim3(256), 0, s, a, plan);
+    launch_k(adam_rows_kernel, dim3(plan.rows), dim3(kRowThreads), 0, s, a, plan);
     return 0;
 }
 template <typename T>
@@ -948,7 +952,7 @@ int launch_polyak(const PolyakArgs& a, cudaStream_t s) {
     // the copies are described by the target segments alone: pass them as both lists
     RowPlan plan;
     if (!row_plan(a.n, a.seg, a.n_seg, a.seg, a.n_seg, &plan) || plan.rows < 1) return -1;
-    launch_k(polyak_rows_kernel, dim3(plan.rows), dim3(256), 0, s, a, plan);
+    launch_k(polyak_rows_kernel, dim3(plan.rows), dim3(kRowThreads), 0, s, a, plan);
     return 0;
 }
 void launch_act_head(const ActHeadArgs& a, cudaStream_t s) {
