@@ -113,14 +113,16 @@ struct squint_handle {
     bool draw_ahead = true;
     // head MLP chains of the BF16 learner as one fused tensor-core launch each
     // (SQUINT_MLP_FUSED=0 at creation: a GEMM and a LayerNorm launch per layer instead);
-    // SQUINT_MLP_CL=1/2/4/8 forces the cluster size of the fused launches.  The backward
-    // chains run as GEMMs beside LayerNorm-backward launches unless SQUINT_MLP_BWD=1 (one
-    // fused chain launch each; SQUINT_MLP_BWD_CL: its cluster size): inside the update's
-    // concurrent graph the GEMM path measures faster, the clusters of the fused launch
-    // waiting for free SMs beside the encoder backward
+    // SQUINT_MLP_CL=1/2/4/8 forces the cluster size of the fused launches.  Backward chains
+    // without weight gradients (the actor step's, through the critics) run as one fused
+    // launch; those with weight gradients as GEMMs beside LayerNorm-backward launches, which
+    // measure faster inside the update's concurrent graph (the clusters of a fused launch
+    // wait for free SMs beside the encoder backward).  SQUINT_MLP_BWD at creation: 0 no
+    // fused chain, 1 every chain, 2 the default, 3 chains of one parameter set;
+    // SQUINT_MLP_BWD_CL: the fused chain's cluster size
     bool mlp_fused = true;
     int mlp_cluster = 0;
-    bool mlp_bwd_fused = false;
+    int mlp_bwd_fused = 2;
     int mlp_bwd_cluster = 0;
     // branch priorities (SQUINT_PRIO=0 at creation: every stream at the default priority)
     bool prio_branches = true;

@@ -420,7 +420,11 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
     const bool bf = h->bf16;
     const int nh = (int)sets[0].size() - 1;
     const int R = mb.rows;
-    if (bf && h->mlp_fused && h->mlp_bwd_fused && dout.h && rows > 0 && E <= kMlpMaxProbs &&
+    // which chains take the fused kernel: all (1), those without weight gradients (2), those
+    // of one parameter set (3)
+    const bool want_fused = h->mlp_bwd_fused == 1 || (h->mlp_bwd_fused == 2 && !grads) ||
+                            (h->mlp_bwd_fused == 3 && E == 1);
+    if (bf && h->mlp_fused && want_fused && dout.h && rows > 0 && E <= kMlpMaxProbs &&
         fused_backward(h, mb, r0, sets, grads, E, X, rows, dout, ncols, dX, lddx, mask, ldmask, s, side, col0, join))
         return;
     auto G = [&](const float* p) { return grads + (p - h->params); };
@@ -541,7 +545,7 @@ int squint_handle::allocate() {
     if (const char* e = std::getenv("SQUINT_DRAW_AHEAD")) draw_ahead = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_FUSED")) mlp_fused = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_CL")) mlp_cluster = std::atoi(e);
-    if (const char* e = std::getenv("SQUINT_MLP_BWD")) mlp_bwd_fused = std::atoi(e) != 0;
+    if (const char* e = std::getenv("SQUINT_MLP_BWD")) mlp_bwd_fused = std::atoi(e);
     if (const char* e = std::getenv("SQUINT_PRIO")) prio_branches = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_FUSE_POLYAK")) fuse_polyak = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_BWD_CL")) mlp_bwd_cluster = std::atoi(e);
