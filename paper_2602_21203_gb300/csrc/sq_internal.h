@@ -122,6 +122,7 @@ struct squint_handle {
     // SQUINT_MLP_BWD_CL: the fused chain's cluster size
     bool mlp_fused = true;
     int mlp_cluster = 0;
+    int mlp_fused_sites = 15;   // SQUINT_MLP_SITES: which forward chains are fused (bit mask)
     int mlp_bwd_fused = 2;
     int mlp_bwd_cluster = 0;
     // branch priorities (SQUINT_PRIO=0 at creation: every stream at the default priority)

@@ -220,7 +220,12 @@ MlpRef mlp_ref(squint_handle* h, const std::vector<Lin>& layers, bool target, co
 void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const Mat& X, int rows, bool bf16,
                  cudaStream_t s, bool split, bool keep) {
     const int nh = (int)sets[0].size() - 1;
-    if (bf16 && !h->fp8 && h->mlp_fused && X.h && rows > 0 && E <= kMlpMaxProbs) {
+    // the chains that take the fused kernel (bit 0 online critics, 1 actor, 2 target
+    // critics, 3 the actor step's critics; other buffers always)
+    const int site = &mb == &h->crit_mlp ? 1 : &mb == &h->actor_mlp ? 2 : &mb == &h->tcrit_mlp ? 4
+                   : &mb == &h->qcrit_mlp ? 8 : 0;
+    if (bf16 && !h->fp8 && h->mlp_fused && (site == 0 || (h->mlp_fused_sites & site)) && X.h && rows > 0 &&
+        E <= kMlpMaxProbs) {
         // the whole chain in one launch: hidden activations stay on chip between layers
         const int H = sets[0][0].out, nout = sets[0][nh].out, kin = sets[0][0].in;
         bool ok = mlp_tc_supported(nh, H, nout, kin);
@@ -545,6 +550,7 @@ int squint_handle::allocate() {
     if (const char* e = std::getenv("SQUINT_DRAW_AHEAD")) draw_ahead = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_FUSED")) mlp_fused = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_CL")) mlp_cluster = std::atoi(e);
+    if (const char* e = std::getenv("SQUINT_MLP_SITES")) mlp_fused_sites = std::atoi(e);
     if (const char* e = std::getenv("SQUINT_MLP_BWD")) mlp_bwd_fused = std::atoi(e);
     if (const char* e = std::getenv("SQUINT_PRIO")) prio_branches = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_FUSE_POLYAK")) fuse_polyak = std::atoi(e) != 0;
