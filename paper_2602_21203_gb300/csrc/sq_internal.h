@@ -123,6 +123,11 @@ struct squint_handle {
     bool mlp_fused = true;
     int mlp_cluster = 0;
     int mlp_fused_sites = 15;   // SQUINT_MLP_SITES: which forward chains are fused (bit mask)
+    // cluster size per chain (bit order of the mask; 0: the launcher's choice, 4 for 512-wide
+    // heads): the actor's and the target critics' chains on the main stream take 8 (more
+    // SMs for their latency-bound layers; the online critics beside them and the actor
+    // step's critics beside the encoder backward keep 4, which co-schedule more easily)
+    int mlp_cluster_site[4] = {0, 8, 8, 0};
     int mlp_bwd_fused = 2;
     int mlp_bwd_cluster = 0;
     // branch priorities (SQUINT_PRIO=0 at creation: every stream at the default priority)

@@ -255,7 +255,8 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
                 q.out = mb.out + (int64_t)e * rows * nout; q.ldo = nout;
             }
             ProfScope ps(h, s, "mlp_tc_fwd", flops, 0);
-            if (launch_mlp_tc(pr, E, nh, H, nout, (float)h->c.ln_eps, h->d_err, &h->gemm_wait, s, h->mlp_cluster) == 0) {
+            if (launch_mlp_tc(pr, E, nh, H, nout, (float)h->c.ln_eps, h->d_err, &h->gemm_wait, s,
+                              site ? h->mlp_cluster_site[__builtin_ctz(site)] : h->mlp_cluster) == 0) {
                 if (keep) mb.tc_saved = true;
                 return;
             }
@@ -549,7 +550,17 @@ int squint_handle::allocate() {
     if (const char* e = std::getenv("SQUINT_GEMM_SPLIT")) gemm_split = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_DRAW_AHEAD")) draw_ahead = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_FUSED")) mlp_fused = std::atoi(e) != 0;
-    if (const char* e = std::getenv("SQUINT_MLP_CL")) mlp_cluster = std::atoi(e);
+    if (const char* e = std::getenv("SQUINT_MLP_CL")) {
+        // one value for every chain, or one per chain: "online,actor,target,actor-step"
+        mlp_cluster = std::atoi(e);
+        for (int i = 0; i < 4; ++i) mlp_cluster_site[i] = mlp_cluster;   // (also replaces the defaults)
+        const char* p = e;
+        for (int i = 0; i < 4 && p; ++i) {
+            mlp_cluster_site[i] = std::atoi(p);
+            p = std::strchr(p, ',');
+            if (p) ++p;
+        }
+    }
     if (const char* e = std::getenv("SQUINT_MLP_SITES")) mlp_fused_sites = std::atoi(e);
     if (const char* e = std::getenv("SQUINT_MLP_BWD")) mlp_bwd_fused = std::atoi(e);
     if (const char* e = std::getenv("SQUINT_PRIO")) prio_branches = std::atoi(e) != 0;
