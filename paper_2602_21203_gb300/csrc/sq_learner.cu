@@ -254,9 +254,12 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
                 }
                 q.out = mb.out + (int64_t)e * rows * nout; q.ldo = nout;
             }
+            // the chain's cluster size; the per-chain 8 only where each CTA keeps at least 64
+            // of the hidden columns (an explicit SQUINT_MLP_CL applies as given)
+            int cluster = site ? h->mlp_cluster_site[__builtin_ctz(site)] : h->mlp_cluster;
+            if (!h->mlp_cluster && cluster == 8 && H / 8 < 64) cluster = 0;
             ProfScope ps(h, s, "mlp_tc_fwd", flops, 0);
-            if (launch_mlp_tc(pr, E, nh, H, nout, (float)h->c.ln_eps, h->d_err, &h->gemm_wait, s,
-                              site ? h->mlp_cluster_site[__builtin_ctz(site)] : h->mlp_cluster) == 0) {
+            if (launch_mlp_tc(pr, E, nh, H, nout, (float)h->c.ln_eps, h->d_err, &h->gemm_wait, s, cluster) == 0) {
                 if (keep) mb.tc_saved = true;
                 return;
             }
@@ -428,8 +431,9 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
     const int R = mb.rows;
     // which chains take the fused kernel: all (1), those without weight gradients (2), those
     // of one parameter set (3)
-    const bool want_fused = h->mlp_bwd_fused == 1 || (h->mlp_bwd_fused == 2 && !grads) ||
-                            (h->mlp_bwd_fused == 3 && E == 1);
+    // (2 and 3 only after the fused forward, whose saves the chain reads without post)
+    const bool want_fused = h->mlp_bwd_fused == 1 ||
+                            (mb.tc_saved && ((h->mlp_bwd_fused == 2 && !grads) || (h->mlp_bwd_fused == 3 && E == 1)));
     if (bf && h->mlp_fused && want_fused && dout.h && rows > 0 && E <= kMlpMaxProbs &&
         fused_backward(h, mb, r0, sets, grads, E, X, rows, dout, ncols, dX, lddx, mask, ldmask, s, side, col0, join))
         return;
