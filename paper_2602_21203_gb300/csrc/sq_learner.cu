@@ -458,18 +458,19 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
         if (m.h) m.h += (int64_t)e * rows * dout.ldh;
         return m;
     };
-    // output layer
+    // output layer; the column sums of the whole chain (biases, LayerNorm gains and shifts)
+    // are collected and added up in one launch after the last weight gradient
+    std::vector<ColSumProblem> cols;
+    double col_bytes = 0;
     if (grads) {
         h->fork(s, side);
         {
             GemmBuilder gb(h, side, bf);
             for (int e = 0; e < E; ++e) gb.dw(dout_e(e), rows, post(nh - 1, e), sets[e][nh], G(sets[e][nh].w));
         }
-        ColSumProblem cs[2];
         for (int e = 0; e < E; ++e)
-            cs[e] = ColSumProblem{rows, sets[e][nh].out, dout_e(e).f, dout.ld, G(sets[e][nh].b)};
-        ProfScope ps(h, side, "colsum", 4.0 * E * rows * sets[0][nh].out, 1);
-        launch_colsum(cs, E, side);
+            cols.push_back(ColSumProblem{rows, sets[e][nh].out, dout_e(e).f, dout.ld, G(sets[e][nh].b)});
+        col_bytes += 4.0 * E * rows * sets[0][nh].out;
     }
     {
         GemmBuilder gb(h, s, bf);
@@ -503,10 +504,15 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
         if (grads) {
             // the LayerNorm's column sums and the weight gradients beside the input-gradient chain
             h->fork(s, side);
-            {
-                ProfScope ps(h, side, "colsum", 4.0 * E * rows * sets[0][l].out * 3.0, 1);
-                launch_ln_bwd_cols(lb, E, side);
+            for (int e = 0; e < E; ++e) {
+                const LnBwdProblem& q = lb[e];
+                if (q.terms) {
+                    if (q.dg) cols.push_back(ColSumProblem{q.rows, q.n, q.terms, q.n, q.dg});
+                    if (q.dbeta) cols.push_back(ColSumProblem{q.rows, q.n, q.terms + (int64_t)q.rows * q.n, q.n, q.dbeta});
+                    if (q.dbias) cols.push_back(ColSumProblem{q.rows, q.n, q.dpre, q.ld_dpre, q.dbias});
+                }
             }
+            col_bytes += 4.0 * E * rows * sets[0][l].out * 3.0;
             GemmBuilder gb(h, side, bf);
             for (int e = 0; e < E; ++e) gb.dw(dpre(l, e), rows, l == 0 ? X : post(l - 1, e), sets[e][l], G(sets[e][l].w));
         }
@@ -518,6 +524,10 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
                       sets[e][l].in);
             }
         }
+    }
+    if (!cols.empty()) {
+        ProfScope ps(h, side, "colsum", col_bytes, 1);
+        launch_colsum(cols.data(), (int)cols.size(), side);
     }
     if (dX) {
         GemmBuilder gb(h, s, bf);

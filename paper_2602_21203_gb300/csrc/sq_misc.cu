@@ -229,8 +229,9 @@ __global__ void __launch_bounds__(256) ln_bwd_row_kernel(LnBwdBatch b, int want_
     if (threadIdx.x == 0) b.tickets[pi] = 0u;
 }
 
-constexpr int kColX = 32, kColY = 16;
-__global__ void __launch_bounds__(kColX * kColY) colsum_kernel(Batch<ColSumProblem> b) {
+constexpr int kColX = 32, kColY = 16, kMaxCol = 16;
+struct ColBatch { ColSumProblem p[kMaxCol]; int n; };
+__global__ void __launch_bounds__(kColX * kColY) colsum_kernel(ColBatch b) {
     SQ_KERNEL_ENTRY();
     __shared__ float part[kColY][kColX + 1];
     const ColSumProblem& P = b.p[blockIdx.y];
@@ -899,9 +900,11 @@ void launch_ln_bwd_cols(const LnBwdProblem* p, int n, cudaStream_t s) {
 }
 
 void launch_colsum(const ColSumProblem* p, int n, cudaStream_t s) {
-    for (int base = 0; base < n; base += kMaxLn) {
-        const int cnt = std::min(kMaxLn, n - base);
-        auto b = make_batch(p + base, cnt);
+    for (int base = 0; base < n; base += kMaxCol) {
+        const int cnt = std::min(kMaxCol, n - base);
+        ColBatch b{};
+        b.n = cnt;
+        for (int i = 0; i < cnt; ++i) b.p[i] = p[base + i];
         int cols = 0;
         for (int i = 0; i < cnt; ++i) cols = std::max(cols, b.p[i].n);
         if (cols) launch_k(colsum_kernel, dim3(dim3((cols + kColX - 1) / kColX, cnt)), dim3(kColX * kColY), 0, s, b);
