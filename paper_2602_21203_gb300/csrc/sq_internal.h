@@ -130,6 +130,10 @@ struct squint_handle {
     int mlp_cluster_site[4] = {0, 8, 8, 0};
     int mlp_bwd_fused = 2;
     int mlp_bwd_cluster = 0;
+    // the actor step's chain through the two critics ends with each critic's input
+    // gradient in the same fused launch (two buffers, added by the head backward) instead
+    // of a GEMM over both (SQUINT_MLP_FIN_SPLIT=0 at creation: the GEMM)
+    bool mlp_fin_split = true;
     // branch priorities (SQUINT_PRIO=0 at creation: every stream at the default priority)
     bool prio_branches = true;
     // the polyak of the target critics inside the critic Adam's pass (SQUINT_FUSE_POLYAK=0
@@ -219,6 +223,7 @@ struct squint_handle {
     // left it (the buffer the first layer's weight gradient read; FP32-plane paths only)
     const float* dconv0 = nullptr;
     float* dxq = nullptr;             // [B, Dc] input gradient of the critics in the actor step
+    float* dxq2 = nullptr;            // [B, Dc] the second critic's part of it, when kept apart
     float* ln_work = nullptr;         // LayerNorm backward column partials
     // fused head backward: per hidden layer [2][row blocks][3][H] column sums of each 128-row
     // block (LayerNorm gain, shift and bias gradients once the row blocks are added)

@@ -173,6 +173,7 @@ struct ActorHeadBwdArgs {
     const float* out; int64_t ld_out;     // forward head inputs of the B actor rows
     const float* eps;                     // [B, A]
     const float* da; int64_t ld_da;       // dL/da rows (row stride ld_da; 0 means A)
+    const float* da2;                     // optional second part of dL/da (same layout), added to da
     const float* log_alpha;               // dL/dlogp = exp(log_alpha)/B
     float lo, hi;
     float* dout;                          // [B, 2A]

@@ -311,13 +311,15 @@ namespace {
 
 // The BF16 backward through a head MLP with the fused chain kernel: one launch for the
 // input-gradient chain and every hidden LayerNorm backward (the input gradient itself in
-// the same launch for one parameter set, else one GEMM that adds the sets' products);
-// the weight gradients (GEMMs) and the gain, shift and bias gradients (column sums of
-// the kernel's per-row-block sums) on `side`.  False (nothing launched) if the shapes
-// are outside the kernel's range.
+// the same launch for one parameter set, or for two sets given a second destination dX2,
+// which then holds set 1's product and dX set 0's; else one GEMM that adds the sets'
+// products); the weight gradients (GEMMs) and the gain, shift and bias gradients (column
+// sums of the kernel's per-row-block sums) on `side`.  False (nothing launched) if the
+// shapes are outside the kernel's range; *split = whether dX and dX2 hold the sets'
+// products apart.
 bool fused_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* sets, float* grads, int E, const Mat& X,
                     int rows, const Mat& dout, int ncols, float* dX, int64_t lddx, const float* mask, int64_t ldmask,
-                    cudaStream_t s, cudaStream_t side, int col0, bool join) {
+                    cudaStream_t s, cudaStream_t side, int col0, bool join, float* dX2, bool* split) {
     const int nh = (int)sets[0].size() - 1;
     const int R = mb.rows;
     const int H = sets[0][0].out, nout = sets[0][nh].out, kin = sets[0][0].in;
@@ -329,7 +331,9 @@ bool fused_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* s
             if (!sets[e][l].wh) return false;
     const int fcl = h->mlp_bwd_cluster;
     if (!mlp_bwd_tc_supported(nh, H, nout, kin, 0, 0, fcl)) return false;
-    const bool fin = dX && ncols > 0 && E == 1 && !mask && mlp_bwd_tc_supported(nh, H, nout, kin, col0, ncols, fcl);
+    const bool fin = dX && ncols > 0 && (E == 1 || dX2) && !mask &&
+                     mlp_bwd_tc_supported(nh, H, nout, kin, col0, ncols, fcl);
+    *split = fin && E > 1;
     const int nrb = (rows + 127) / 128;
     auto G = [&](const float* p) { return grads + (p - h->params); };
     auto post = [&](int l, int e) {
@@ -379,7 +383,7 @@ bool fused_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* s
             if (grads || (l == 0 && !fin)) q.dpre_bf[l] = dpre(l, e).h;
             if (grads) q.colpart[l] = h->mlp_colpart[l] + (int64_t)e * nrb * 3 * H;
         }
-        if (fin) { q.dx = dX; q.lddx = lddx; }
+        if (fin) { q.dx = e == 0 ? dX : dX2; q.lddx = lddx; }
         flops += 2.0 * rows * ((double)nout * H + (double)(nh - 1) * H * H + (fin ? (double)H * ncols : 0.0));
     }
     {
@@ -419,10 +423,12 @@ bool fused_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* s
 // (FP32 + BF16 shadow); activations stored with R rows per set, read from row r0.
 // Parameter gradients land at the canonical offsets of `grads` (null: input gradient
 // only).  dX (optional) = sum over sets of the input gradient, input columns
-// [col0, col0 + ncols) into dX[:, 0 .. ncols).
-void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* sets, float* grads, int E, const Mat& X,
+// [col0, col0 + ncols) into dX[:, 0 .. ncols).  With dX2 (same layout) the fused chain
+// may leave the two sets' input gradients apart, set 0's in dX and set 1's in dX2, for
+// the reader to add: the return value says whether it did (false: dX holds the sum).
+bool mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* sets, float* grads, int E, const Mat& X,
                   int rows, const Mat& dout, int ncols, float* dX, int64_t lddx, const float* mask, int64_t ldmask,
-                  cudaStream_t s, cudaStream_t side, int col0 = 0, bool join = true) {
+                  cudaStream_t s, cudaStream_t side, int col0 = 0, bool join = true, float* dX2 = nullptr) {
     // weight and bias gradients go to `side` as soon as their inputs exist; the main
     // stream carries only the chain of input gradients; `side` is joined at the end
     // (join = false: the caller joins it later)
@@ -434,9 +440,11 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
     // (2 and 3 only after the fused forward, whose saves the chain reads without post)
     const bool want_fused = h->mlp_bwd_fused == 1 ||
                             (mb.tc_saved && ((h->mlp_bwd_fused == 2 && !grads) || (h->mlp_bwd_fused == 3 && E == 1)));
+    bool split = false;
     if (bf && h->mlp_fused && want_fused && dout.h && rows > 0 && E <= kMlpMaxProbs &&
-        fused_backward(h, mb, r0, sets, grads, E, X, rows, dout, ncols, dX, lddx, mask, ldmask, s, side, col0, join))
-        return;
+        fused_backward(h, mb, r0, sets, grads, E, X, rows, dout, ncols, dX, lddx, mask, ldmask, s, side, col0, join,
+                       h->mlp_fin_split ? dX2 : nullptr, &split))
+        return split;
     auto G = [&](const float* p) { return grads + (p - h->params); };
     auto post = [&](int l, int e) {
         const int n = sets[e][l].out;
@@ -536,6 +544,7 @@ void mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
         gb.dx(d, w, E, rows, col0, ncols, dX, lddx, mask, ldmask);
     }
     if (grads && join) h->fork(side, s);
+    return false;
 }
 
 void alloc_mlp(squint_handle* h, MlpBufs& mb, const std::vector<Lin>& layers, int E, int rows, bool terms = false) {
@@ -580,6 +589,7 @@ int squint_handle::allocate() {
     if (const char* e = std::getenv("SQUINT_PRIO")) prio_branches = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_FUSE_POLYAK")) fuse_polyak = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_BWD_CL")) mlp_bwd_cluster = std::atoi(e);
+    if (const char* e = std::getenv("SQUINT_MLP_FIN_SPLIT")) mlp_fin_split = std::atoi(e) != 0;
     bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
     SQ_CK(this, cudaGetDevice(&device));
     const int64_t n = L.total;
@@ -669,6 +679,7 @@ int squint_handle::allocate() {
     if (!tc_conv) dconv_b = dalloc<float>(maxc);
     wgrad_work = dalloc<float>(maxw);
     dxq = dalloc<float>((int64_t)B * L.dc);
+    dxq2 = dalloc<float>((int64_t)B * L.dc);
     {
         int wmax = std::max(L.D, 1);
         for (int l = 0; l < c.n_hidden; ++l) wmax = std::max(wmax, c.hidden[l]);
@@ -1442,13 +1453,15 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
         // only the action columns of the critics' input gradient are used (the head
         // backward): from column Z + P rounded down to 8 (16-byte aligned BF16 operand)
         const int a0 = (Z + P) / 8 * 8;
-        mlp_backward(this, qcrit_mlp, 0, crit_on, nullptr, E, Mat{xq, Dc, xq_h, Dc8}, B, Mat{dlogits_q, K, dlogits_qh, K8},
-                     Dc - a0, dxq + a0, Dc, nullptr, 0, s, s2, a0);
+        const bool dxq_split = mlp_backward(this, qcrit_mlp, 0, crit_on, nullptr, E, Mat{xq, Dc, xq_h, Dc8}, B,
+                                            Mat{dlogits_q, K, dlogits_qh, K8}, Dc - a0, dxq + a0, Dc, nullptr, 0, s, s2,
+                                            a0, true, dxq2 + a0);
         fork(s3, s);   // the new alpha (and the statistics) before the head backward
         ActorHeadBwdArgs hb{};
         hb.B = B; hb.A = A;
         hb.out = actor_mlp.out + (int64_t)B * 2 * A; hb.ld_out = 2 * A;
         hb.eps = eps + (int64_t)B * A; hb.da = dxq + Z + P; hb.ld_da = Dc; hb.log_alpha = W + L.log_alpha;
+        if (dxq_split) hb.da2 = dxq2 + Z + P;   // the second critic's part, added in the head
         hb.lo = (float)c.log_std_min; hb.hi = (float)c.log_std_max;
         hb.dout = dout_a; hb.do_actor = d_do_actor;
         if (bf16) { hb.dout_bf = dout_ah; hb.ld_dout_bf = pad8(2 * A); }

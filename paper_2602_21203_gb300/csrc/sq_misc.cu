@@ -572,7 +572,9 @@ __global__ void actor_head_bwd_kernel(ActorHeadBwdArgs a) {
         const float sd = expf(a.lo + 0.5f * (a.hi - a.lo) * (th + 1.0f));
         const float act = tanhf(mu + sd * eps);
         const int64_t ldd = a.ld_da ? a.ld_da : a.A;
-        const float du = a.da[(int64_t)row * ldd + k] * (1.0f - act * act) + dlogp * 2.0f * act;
+        float dq = a.da[(int64_t)row * ldd + k];
+        if (a.da2) dq += a.da2[(int64_t)row * ldd + k];
+        const float du = dq * (1.0f - act * act) + dlogp * 2.0f * act;
         const float dls = du * sd * eps - dlogp;
         const float draw = dls * 0.5f * (a.hi - a.lo) * (1.0f - th * th);
         a.dout[(int64_t)row * 2 * a.A + k] = du;
@@ -705,6 +707,11 @@ __device__ __forceinline__ float polyak_one(float t, float s, float keep, float 
 }
 
 // Adam over one row task (with the polyak of the target copy when a.target is set).
+// Rows whose FP32 arrays share one 16-byte alignment go by float4: the first elements up
+// to the boundary and the last ones past the final whole vector one a thread, the rest
+// four a thread (the BF16 copies as pairs where their row offset is even); rows whose
+// arrays are aligned differently go one element a thread.  Every element takes the same
+// arithmetic either way.
 __global__ void __launch_bounds__(kRowThreads) adam_rows_kernel(const __grid_constant__ AdamArgs a,
                                                         const __grid_constant__ RowPlan plan) {
     SQ_KERNEL_ENTRY();
@@ -728,30 +735,86 @@ __global__ void __launch_bounds__(kRowThreads) adam_rows_kernel(const __grid_con
     __nv_bfloat16* dst = R.dst ? R.dst + (int64_t)r * R.ld : nullptr;
     __nv_bfloat16* tdst = R.tdst ? R.tdst + (int64_t)r * R.ldt : nullptr;
     __nv_bfloat16* pbf = a.p_bf ? a.p_bf + base : nullptr;
-    constexpr int U = 4;
-    for (int c0 = threadIdx.x; c0 < lim; c0 += U * blockDim.x) {
-        float pv[U], gv[U], mv[U], vv[U], tv[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {   // every load of the group in flight before the math
-            const int c = c0 + u * blockDim.x;
-            if (c < lim) {
-                pv[u] = p[c]; gv[u] = g[c]; mv[u] = m[c]; vv[u] = v[c];
-                tv[u] = tg ? tg[c] : 0.f;
-            }
+    auto one = [&](int c) {
+        const float np = adam_one(p[c], g[c], m[c], v[c], b1, b2, c1, c2, lr, ep, ibc1, ibc2);
+        p[c] = np;
+        if (dst) dst[c] = __float2bfloat16_rn(np);
+        if (pbf) pbf[c] = __float2bfloat16_rn(np);
+        if (tg) {
+            const float nt = polyak_one(tg[c], np, keep, tau);
+            tg[c] = nt;
+            if (tdst) tdst[c] = __float2bfloat16_rn(nt);
         }
+    };
+    const uintptr_t ap = reinterpret_cast<uintptr_t>(p);
+    const bool same = ((ap ^ reinterpret_cast<uintptr_t>(g)) & 15) == 0 &&
+                      ((ap ^ reinterpret_cast<uintptr_t>(m)) & 15) == 0 &&
+                      ((ap ^ reinterpret_cast<uintptr_t>(v)) & 15) == 0 &&
+                      (!tg || ((ap ^ reinterpret_cast<uintptr_t>(tg)) & 15) == 0) && (ap & 3) == 0;
+    if (!same) {
+        for (int c = threadIdx.x; c < lim; c += blockDim.x) one(c);
+        return;
+    }
+    const int head = min(lim, (int)(((16 - (ap & 15)) & 15) / 4));
+    const int nvec = (lim - head) / 4;
+    const int tail0 = head + 4 * nvec;
+    // the scalar elements: [0, head) and [tail0, lim), at most three of each, taken by the
+    // first threads after their vectors (their loads issued first, so that both are in flight)
+    const int ns = head + (lim - tail0);
+    const int cs = (int)threadIdx.x < head ? (int)threadIdx.x : tail0 + (int)threadIdx.x - head;
+    float sp = 0.f, sg = 0.f, sm = 0.f, sv = 0.f, st = 0.f;
+    if ((int)threadIdx.x < ns) {
+        sp = p[cs]; sg = g[cs]; sm = m[cs]; sv = v[cs];
+        if (tg) st = tg[cs];
+    }
+    // a BF16 copy takes pairs where its first vector element is 4-byte aligned (then every
+    // one is: vectors are 8 bytes of BF16 apart)
+    auto even = [&](const __nv_bfloat16* d) { return d && (reinterpret_cast<uintptr_t>(d + head) & 3) == 0; };
+    const bool pr_dst = even(dst), pr_pbf = even(pbf), pr_tdst = even(tdst);
+    auto put4 = [&](__nv_bfloat16* d, bool pairs, int c, const float (&x)[4]) {
+        if (pairs) {
+            *reinterpret_cast<__nv_bfloat162*>(d + c) = __floats2bfloat162_rn(x[0], x[1]);
+            *reinterpret_cast<__nv_bfloat162*>(d + c + 2) = __floats2bfloat162_rn(x[2], x[3]);
+        } else {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int c = c0 + u * blockDim.x;
-            if (c >= lim) break;
-            const float np = adam_one(pv[u], gv[u], mv[u], vv[u], b1, b2, c1, c2, lr, ep, ibc1, ibc2);
-            p[c] = np; m[c] = mv[u]; v[c] = vv[u];
-            if (dst) dst[c] = __float2bfloat16_rn(np);
-            if (pbf) pbf[c] = __float2bfloat16_rn(np);
-            if (tg) {
-                const float nt = polyak_one(tv[u], np, keep, tau);
-                tg[c] = nt;
-                if (tdst) tdst[c] = __float2bfloat16_rn(nt);
-            }
+            for (int u = 0; u < 4; ++u) d[c + u] = __float2bfloat16_rn(x[u]);
+        }
+    };
+    for (int q = threadIdx.x; q < nvec; q += blockDim.x) {
+        const int c = head + 4 * q;
+        const float4 p4 = *reinterpret_cast<const float4*>(p + c);
+        const float4 g4 = *reinterpret_cast<const float4*>(g + c);
+        float4 m4 = *reinterpret_cast<const float4*>(m + c);
+        float4 v4 = *reinterpret_cast<const float4*>(v + c);
+        const float4 t4 = tg ? *reinterpret_cast<const float4*>(tg + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float np[4], nt[4];
+        np[0] = adam_one(p4.x, g4.x, m4.x, v4.x, b1, b2, c1, c2, lr, ep, ibc1, ibc2);
+        np[1] = adam_one(p4.y, g4.y, m4.y, v4.y, b1, b2, c1, c2, lr, ep, ibc1, ibc2);
+        np[2] = adam_one(p4.z, g4.z, m4.z, v4.z, b1, b2, c1, c2, lr, ep, ibc1, ibc2);
+        np[3] = adam_one(p4.w, g4.w, m4.w, v4.w, b1, b2, c1, c2, lr, ep, ibc1, ibc2);
+        *reinterpret_cast<float4*>(p + c) = make_float4(np[0], np[1], np[2], np[3]);
+        *reinterpret_cast<float4*>(m + c) = m4;
+        *reinterpret_cast<float4*>(v + c) = v4;
+        if (dst) put4(dst, pr_dst, c, np);
+        if (pbf) put4(pbf, pr_pbf, c, np);
+        if (tg) {
+            nt[0] = polyak_one(t4.x, np[0], keep, tau);
+            nt[1] = polyak_one(t4.y, np[1], keep, tau);
+            nt[2] = polyak_one(t4.z, np[2], keep, tau);
+            nt[3] = polyak_one(t4.w, np[3], keep, tau);
+            *reinterpret_cast<float4*>(tg + c) = make_float4(nt[0], nt[1], nt[2], nt[3]);
+            if (tdst) put4(tdst, pr_tdst, c, nt);
+        }
+    }
+    if ((int)threadIdx.x < ns) {
+        const float np = adam_one(sp, sg, sm, sv, b1, b2, c1, c2, lr, ep, ibc1, ibc2);
+        p[cs] = np; m[cs] = sm; v[cs] = sv;
+        if (dst) dst[cs] = __float2bfloat16_rn(np);
+        if (pbf) pbf[cs] = __float2bfloat16_rn(np);
+        if (tg) {
+            const float nt = polyak_one(st, np, keep, tau);
+            tg[cs] = nt;
+            if (tdst) tdst[cs] = __float2bfloat16_rn(nt);
         }
     }
 }

@@ -512,6 +512,34 @@ def test_fused_backward_update_within_bf16_bounds(L, monkeypatch, cluster):
     twin.close()
 
 
+def test_actor_step_input_gradients_kept_apart_match_their_gemm_sum(L, monkeypatch):
+    """The actor step's gradient at the action through the two critics: each critic's part
+    left by its fused chain launch and added in the tanh-Gaussian head backward, against
+    one GEMM over both critics' products.  Only the FP32 summation order differs: the
+    critic range (gradients and updated parameters) is bit-identical, the actor
+    gradients agree to 1e-3 relative in norm per tensor and the actor loss exactly."""
+    cfg = synth.make_config("train_b512", ring_size=4096)
+    ring = synth.make_ring(cfg, 0, device="cuda")
+    monkeypatch.setenv("SQUINT_MLP_FIN_SPLIT", "0")
+    a = L.Learner(cfg, ring, precision=L.PREC_BF16, max_k=2)
+    monkeypatch.setenv("SQUINT_MLP_FIN_SPLIT", "1")
+    b = L.Learner(cfg, ring, precision=L.PREC_BF16, max_k=2)
+    sa = a.update(1, graph=True)[0]
+    sb = b.update(1, graph=True)[0]
+    assert sa["critic_loss"] == sb["critic_loss"] and sa["actor_loss"] == sb["actor_loss"]
+    ga, gb = split_params(a.debug("grads"), cfg), split_params(b.debug("grads"), cfg)
+    pa, pb = split_params(a.params(), cfg), split_params(b.params(), cfg)
+    for k in ga:
+        if o.group_of(k) == "actor":
+            n = np.linalg.norm(ga[k])
+            assert np.linalg.norm(ga[k] - gb[k]) <= 1e-3 * n + 1e-9, k
+        else:
+            assert np.array_equal(ga[k], gb[k]), k
+            assert np.array_equal(pa[k], pb[k]), k
+    a.close()
+    b.close()
+
+
 # ---------------------------------------------------------------- update timeline
 def test_trace_update_reports_every_launch_on_its_branch(L):
     """The traced update has every launch with 0 <= start <= end, the main stream's
