@@ -1487,9 +1487,11 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
             p.dg = G + L.aproj.g; p.dbeta = G + L.aproj.beta; p.dbias = G + L.aproj.b;
             p.terms = proj_terms;
             ln_bwd(&p, 1, s);
+            // the projection's gain, shift and bias gradients beside its weight gradient
+            fork(s, s2);
             {
-                ProfScope ps(this, s, "colsum", 12.0 * B * Dd, 1);
-                launch_ln_bwd_cols(&p, 1, s);
+                ProfScope ps(this, s2, "colsum", 12.0 * B * Dd, 1);
+                launch_ln_bwd_cols(&p, 1, s2);
             }
             GemmBuilder gb(this, s, bf16);
             gb.dw(Mat{dproj, Dd, dproj_h, Dd}, B, zt, ap, G + L.aproj.w);

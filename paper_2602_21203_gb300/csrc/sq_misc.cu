@@ -677,12 +677,14 @@ __global__ void stats_kernel(StatsArgs a) {
 
 // ---------------------------------------------------------------- Adam and polyak
 // One Adam step; ibc1, ibc2 the reciprocals of the bias corrections 1 - beta^t (one
-// division and one square root an element).
+// division and one square root an element).  Every operation's rounding is spelled out,
+// so an element gets the same bits whichever code path (four a thread or one) takes it.
 __device__ __forceinline__ float adam_one(float p, float g, float& m, float& v, float b1, float b2, float c1, float c2,
                                           float lr, float ep, float ibc1, float ibc2) {
-    m = b1 * m + c1 * g;
-    v = b2 * v + c2 * g * g;
-    return p - (lr * (m * ibc1)) / (sqrtf(v * ibc2) + ep);
+    m = __fmaf_rn(b1, m, __fmul_rn(c1, g));
+    v = __fmaf_rn(b2, v, __fmul_rn(__fmul_rn(c2, g), g));
+    const float step = __fdiv_rn(__fmul_rn(lr, __fmul_rn(m, ibc1)), __fadd_rn(__fsqrt_rn(__fmul_rn(v, ibc2)), ep));
+    return __fsub_rn(p, step);
 }
 
 // Row tasks of an elementwise pass over [0, n) of a parameter range: each weight matrix
