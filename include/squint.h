@@ -168,6 +168,26 @@ int squint_update(squint_handle* h, int k, squint_update_stats* stats, void* str
  */
 int squint_update_eager(squint_handle* h, int k, squint_update_stats* stats, void* stream);
 
+/*
+ * squint_update (the same k updates, Alg. 1 inner loop, as one graph) without waiting:
+ * when stats is given, the stream itself copies the k entries there after the updates,
+ * so the call returns at once and a training loop can issue the next call (and the
+ * copies of new transitions) before it reads these statistics.  stats: NULL, or host
+ * memory for k entries that the caller has page-locked (cudaMallocHost or
+ * cudaHostRegister; pageable memory is rejected with SQUINT_EINVAL); its contents are
+ * valid once the stream has passed this call (cudaStreamSynchronize, or an event the
+ * caller records after it), and the caller must not reuse the buffer before then.
+ * A bounded device wait that ran out is reported by the next call that waits
+ * (squint_update with stats, squint_update_check).  Returns as squint_update otherwise.
+ */
+int squint_update_async(squint_handle* h, int k, squint_update_stats* stats, void* stream);
+
+/*
+ * Waits for `stream` and reports whether a bounded device wait of the updates issued
+ * so far ran out (SQUINT_ETIMEOUT, and the handle is marked failed) or not (0).
+ */
+int squint_update_check(squint_handle* h, void* stream);
+
 /* ------------------------------------------------------------------ measurement */
 
 /* Kernel nodes in the graph captured for k updates (0 if none captured yet). */

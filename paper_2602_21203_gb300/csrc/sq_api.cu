@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <string>
 
@@ -278,6 +279,44 @@ int squint_update_eager(squint_handle* h, int k, squint_update_stats* stats, voi
     if (!h->has_ring) return SQUINT_ESTATE;
     if (k < 1 || k > h->c.max_k) return SQUINT_EINVAL;
     return h->run_updates(k, stats, (cudaStream_t)stream, false);
+}
+
+// The device statistics (8 words an update: six floats, the update index as two 32-bit
+// halves, low first) are the bytes of squint_update_stats on a little-endian host.
+static_assert(sizeof(squint_update_stats) == 32 && offsetof(squint_update_stats, update_idx) == 24,
+              "squint_update_stats must match the device statistics layout");
+
+int squint_update_async(squint_handle* h, int k, squint_update_stats* stats, void* stream) {
+    if (!h) return SQUINT_EINVAL;
+    if (h->failed) return SQUINT_ESTATE;
+    if (!h->has_ring) return SQUINT_ESTATE;
+    if (k < 1 || k > h->c.max_k) return SQUINT_EINVAL;
+    if (stats) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, stats) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+            cudaGetLastError();
+            g_last_error = "squint_update_async: stats must be page-locked host memory";
+            return SQUINT_EINVAL;
+        }
+    }
+    const cudaStream_t s = (cudaStream_t)stream;
+    const int rc = h->run_updates(k, nullptr, s, true);
+    if (rc != SQUINT_OK || !stats) return rc;
+    SQ_CK(h, cudaMemcpyAsync(stats, h->d_stats, sizeof(squint_update_stats) * k, cudaMemcpyDeviceToHost, s));
+    return SQUINT_OK;
+}
+
+int squint_update_check(squint_handle* h, void* stream) {
+    if (!h) return SQUINT_EINVAL;
+    int32_t err = 0;
+    SQ_CK(h, cudaMemcpyAsync(&err, h->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    SQ_CK(h, cudaStreamSynchronize((cudaStream_t)stream));
+    if (err) {
+        h->failed = true;
+        g_last_error = "a bounded device wait ran out";
+        return SQUINT_ETIMEOUT;
+    }
+    return h->failed ? SQUINT_ESTATE : SQUINT_OK;
 }
 
 int squint_get_params(squint_handle* h, float* host, int64_t n) {

@@ -56,6 +56,24 @@ class UpdateStats(ctypes.Structure):
                 ("update_idx", ctypes.c_int64)]
 
 
+class PinnedStats:
+    """Page-locked host room for the statistics of k updates: the buffer squint_update_async
+    fills from the stream (read it once the stream has passed that call)."""
+
+    def __init__(self, k):
+        import torch
+        self.k = int(k)
+        self._buf = torch.empty(self.k * ctypes.sizeof(UpdateStats), dtype=torch.uint8, pin_memory=True)
+        self._arr = (UpdateStats * self.k).from_address(self._buf.data_ptr())
+
+    @property
+    def ptr(self):
+        return self._buf.data_ptr()
+
+    def read(self):
+        return [{f: getattr(s, f) for f, _ in UpdateStats._fields_} for s in self._arr]
+
+
 class ServeResult(ctypes.Structure):
     _fields_ = [("latency_us", ctypes.c_double), ("policy_version", ctypes.c_int64),
                 ("device_begin_us", ctypes.c_double), ("device_end_us", ctypes.c_double),
@@ -88,6 +106,8 @@ def load():
         "squint_destroy": (I, [P]),
         "squint_update": (I, [P, I, P, P]),
         "squint_update_eager": (I, [P, I, P, P]),
+        "squint_update_async": (I, [P, I, P, P]),
+        "squint_update_check": (I, [P, P]),
         "squint_act": (I, [P, P, I, P]),
         "squint_refresh_policy": (I, [P, P]),
         "squint_serve_start": (I, [P, I, SZ]),
@@ -251,6 +271,18 @@ class Learner:
         if not stats:
             return None
         return [{f: getattr(s, f) for f, _ in UpdateStats._fields_} for s in st]
+
+    def update_async(self, k, stats=None, stream=None):
+        """k updates as one graph without waiting; `stats` (a PinnedStats of at least k
+        entries, or None) is filled by the stream."""
+        if stats is not None and stats.k < k:
+            raise ValueError("PinnedStats holds fewer than k entries")
+        _check(self.lib.squint_update_async(self.h, int(k), ctypes.c_void_p(stats.ptr) if stats is not None else None,
+                                            _stream(stream)), "squint_update_async")
+
+    def update_check(self, stream=None):
+        """Waits for the stream; raises if a bounded device wait of the updates ran out."""
+        _check(self.lib.squint_update_check(self.h, _stream(stream)), "squint_update_check")
 
     def params(self):
         out = np.empty(self.n_params, dtype=np.float32)
