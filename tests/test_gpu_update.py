@@ -168,6 +168,33 @@ def test_graph_replay_equals_eager_bitwise(L):
     b.close()
 
 
+def test_async_update_statistics_equal_the_waiting_call(L):
+    """squint_update_async leaves the statistics to the stream: once it is synchronised,
+    the caller's page-locked buffer holds what squint_update returns for a twin learner,
+    bit for bit, over calls that reuse the buffer; the parameters agree too.  Pageable
+    host memory is refused, and squint_update_check reports no timed-out wait."""
+    import ctypes
+    cfg, ring_cpu, ring, a = _setup(L, "small_b32")
+    b = L.Learner(cfg, ring)
+    buf = L.PinnedStats(3)
+    s = torch.cuda.Stream()
+    for call in range(3):
+        ref = a.update(3, stream=s)
+        b.update_async(3, buf, stream=s)
+        s.synchronize()
+        assert buf.read() == ref, call
+    b.update_check(stream=s)
+    assert np.array_equal(a.params(), b.params())
+    assert [x["update_idx"] for x in buf.read()] == [6, 7, 8]
+    pageable = (L.UpdateStats * 3)()
+    rc = b.lib.squint_update_async(b.h, 3, ctypes.cast(pageable, ctypes.c_void_p), ctypes.c_void_p(s.cuda_stream))
+    assert rc == L.EINVAL
+    b.update_async(3, None, stream=s)     # no statistics: nothing copied back
+    b.update_check(stream=s)
+    a.close()
+    b.close()
+
+
 def test_k_updates_track_oracle(L):
     cfg, ring_cpu, ring, learner = _setup(L, "small_b32")
     ring_np = synth.ring_numpy(ring_cpu)
