@@ -132,7 +132,8 @@ struct squint_handle {
     int mlp_bwd_cluster = 0;
     // the actor step's chain through the two critics ends with each critic's input
     // gradient in the same fused launch (two buffers, added by the head backward) instead
-    // of a GEMM over both (SQUINT_MLP_FIN_SPLIT=0 at creation: the GEMM)
+    // of a GEMM over both, from a batch of two row blocks on (SQUINT_MLP_FIN_SPLIT=0 at
+    // creation: the GEMM at every batch)
     bool mlp_fin_split = true;
     // branch priorities (SQUINT_PRIO=0 at creation: every stream at the default priority)
     bool prio_branches = true;

@@ -32,6 +32,11 @@ namespace sq {
 
 static int64_t pad8(int64_t n) { return (n + 7) / 8 * 8; }
 constexpr int kLongK = 1024;   // reductions at least this long may split K over a cluster
+// The sets' input gradients are left apart by the fused chain from two row blocks a set
+// on: with one, the GEMM that adds them is a single short CTA and the chain's own final
+// step costs more (batch 32: 3,404 against 3,876 updates/s), while at batch 512 the GEMM's
+// few long CTAs sit on the critical chain beside the encoder backward (2,474 against 2,405)
+constexpr int kFinSplitRows = 256;
 constexpr int kCh32 = 32;   // channels of the tensor-core convolutions
 
 GemmProblem lin_fwd(const float* X, int64_t ldx, int rows, const float* W, const float* b, int in, int out, float* Y,
@@ -443,7 +448,7 @@ bool mlp_backward(squint_handle* h, const MlpBufs& mb, int r0, const MlpRef* set
     bool split = false;
     if (bf && h->mlp_fused && want_fused && dout.h && rows > 0 && E <= kMlpMaxProbs &&
         fused_backward(h, mb, r0, sets, grads, E, X, rows, dout, ncols, dX, lddx, mask, ldmask, s, side, col0, join,
-                       h->mlp_fin_split ? dX2 : nullptr, &split))
+                       h->mlp_fin_split && rows >= kFinSplitRows ? dX2 : nullptr, &split))
         return split;
     auto G = [&](const float* p) { return grads + (p - h->params); };
     auto post = [&](int l, int e) {
