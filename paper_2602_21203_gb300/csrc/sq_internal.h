@@ -135,6 +135,10 @@ struct squint_handle {
     // of a GEMM over both, from a batch of two row blocks on (SQUINT_MLP_FIN_SPLIT=0 at
     // creation: the GEMM at every batch)
     bool mlp_fin_split = true;
+    // the actor's forward as two launches (the target's half on the critical chain without
+    // saves, the o_t half with its saves on a side branch) on the fused BF16 path
+    // (SQUINT_SPLIT_ACTOR_FWD=0 at creation: one launch over both halves)
+    bool split_actor_fwd = true;
     // branch priorities (SQUINT_PRIO=0 at creation: every stream at the default priority)
     bool prio_branches = true;
     // the polyak of the target critics inside the critic Adam's pass (SQUINT_FUSE_POLYAK=0

@@ -165,6 +165,7 @@ struct ActorHeadArgs {
     float* logp;                    // [rows]
     float* eps;                     // [rows, A] saved noise
     const float* eps_in;            // optional: noise given instead of drawn
+    int row0;                       // rows [row0, rows) are computed (0: all)
 };
 void launch_actor_head(const ActorHeadArgs& a, cudaStream_t s);
 

@@ -223,7 +223,7 @@ MlpRef mlp_ref(squint_handle* h, const std::vector<Lin>& layers, bool target, co
 }
 
 void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const Mat& X, int rows, bool bf16,
-                 cudaStream_t s, bool split, bool keep) {
+                 cudaStream_t s, bool split, bool keep, int r0) {
     const int nh = (int)sets[0].size() - 1;
     // the chains that take the fused kernel (bit 0 online critics, 1 actor, 2 target
     // critics, 3 the actor step's critics; other buffers always)
@@ -251,13 +251,13 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
                     if (l == nh) break;
                     q.g[l] = ly.g; q.beta[l] = ly.beta;
                     if (keep) {
-                        const int64_t off = (int64_t)e * rows * H;
+                        const int64_t off = ((int64_t)e * rows + r0) * H;
                         q.save[l] = MlpTcSave{mb.pre[l] + off, mb.post[l] + off,
                                               mb.posth.empty() ? nullptr : mb.posth[l] + off,
-                                              mb.mean[l] + (int64_t)e * rows, mb.rstd[l] + (int64_t)e * rows};
+                                              mb.mean[l] + ((int64_t)e * rows + r0), mb.rstd[l] + ((int64_t)e * rows + r0)};
                     }
                 }
-                q.out = mb.out + (int64_t)e * rows * nout; q.ldo = nout;
+                q.out = mb.out + ((int64_t)e * rows + r0) * nout; q.ldo = nout;
             }
             // the chain's cluster size; the per-chain 8 only where each CTA keeps at least 64
             // of the hidden columns (an explicit SQUINT_MLP_CL applies as given)
@@ -280,11 +280,11 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
                 const LayerRef& ly = sets[e][l];
                 LnProblem p{};
                 p.rows = rows; p.n = ly.out;
-                p.pre = mb.pre[l] + (int64_t)e * rows * ly.out; p.ld_pre = ly.out;
+                p.pre = mb.pre[l] + ((int64_t)e * rows + r0) * ly.out; p.ld_pre = ly.out;
                 p.g = ly.g; p.beta = ly.beta;
-                p.out = mb.post[l] + (int64_t)e * rows * ly.out; p.ld_out = ly.out;
-                if (bf16 && !mb.posth.empty()) { p.out_bf = mb.posth[l] + (int64_t)e * rows * ly.out; p.ld_out_bf = ly.out; }
-                p.mean = mb.mean[l] + (int64_t)e * rows; p.rstd = mb.rstd[l] + (int64_t)e * rows;
+                p.out = mb.post[l] + ((int64_t)e * rows + r0) * ly.out; p.ld_out = ly.out;
+                if (bf16 && !mb.posth.empty()) { p.out_bf = mb.posth[l] + ((int64_t)e * rows + r0) * ly.out; p.ld_out_bf = ly.out; }
+                p.mean = mb.mean[l] + ((int64_t)e * rows + r0); p.rstd = mb.rstd[l] + ((int64_t)e * rows + r0);
                 lp[e] = p;
             }
         bool fused = l < nh && bf16 && h->fuse_ln && !mb.posth.empty();
@@ -294,12 +294,12 @@ void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const
                 const LayerRef& ly = sets[e][l];
                 Mat in = X;
                 if (l > 0) {
-                    in.f = mb.post[l - 1] + (int64_t)e * rows * ly.in;
+                    in.f = mb.post[l - 1] + ((int64_t)e * rows + r0) * ly.in;
                     in.ld = ly.in;
-                    in.h = mb.posth.empty() ? nullptr : mb.posth[l - 1] + (int64_t)e * rows * ly.in;
+                    in.h = mb.posth.empty() ? nullptr : mb.posth[l - 1] + ((int64_t)e * rows + r0) * ly.in;
                     in.ldh = ly.in;
                 }
-                float* y = l < nh ? mb.pre[l] + (int64_t)e * rows * ly.out : mb.out + (int64_t)e * rows * ly.out;
+                float* y = l < nh ? mb.pre[l] + ((int64_t)e * rows + r0) * ly.out : mb.out + ((int64_t)e * rows + r0) * ly.out;
                 const bool f = gb.fwd(in, rows, ly, y, ly.out, nullptr, 0, fused ? &lp[e] : nullptr, true);
                 fused = fused && f;
             }
@@ -595,6 +595,7 @@ int squint_handle::allocate() {
     if (const char* e = std::getenv("SQUINT_FUSE_POLYAK")) fuse_polyak = std::atoi(e) != 0;
     if (const char* e = std::getenv("SQUINT_MLP_BWD_CL")) mlp_bwd_cluster = std::atoi(e);
     if (const char* e = std::getenv("SQUINT_MLP_FIN_SPLIT")) mlp_fin_split = std::atoi(e) != 0;
+    if (const char* e = std::getenv("SQUINT_SPLIT_ACTOR_FWD")) split_actor_fwd = std::atoi(e) != 0;
     bf16 = c.precision == SQUINT_PREC_BF16 || fp8;
     SQ_CK(this, cudaGetDevice(&device));
     const int64_t n = L.total;
@@ -1171,9 +1172,21 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
     mlp_forward(this, crit_mlp, crit_on, E, Mat{xc, Dc, xc_h, Dc8}, B, bf16, s3);
 
     mark(s);
-    // ---- a7: actor (pre-update) on both halves; tanh-Gaussian sample
+    // ---- a7: actor (pre-update) on both halves; tanh-Gaussian sample.  Split: the o_{t+1}
+    // half, which only the target reads, on the critical chain without saved activations,
+    // and the o_t half (read by the temperature and actor steps, differentiated in the
+    // actor step) with its saves and its sample on s2, joined before the critic Adam
+    // (rows are independent in the fused forward and the sample, so the results are those
+    // of one launch over both halves)
+    const bool split_actor = split_actor_fwd && bf16 && !fp8 && mlp_fused && (mlp_fused_sites & 2);
+    if (split_actor) {
+        fork(s, s2);
+        mlp_forward(this, actor_mlp, &actor_on, 1, Mat{xa + (int64_t)B * Da, Da, xa_h + (int64_t)B * Da8, Da8}, B, bf16,
+                    s2, true, true, B);
+    }
     {
-        mlp_forward(this, actor_mlp, &actor_on, 1, Mat{xa, Da, xa_h, Da8}, 2 * B, bf16, s);
+        if (split_actor) mlp_forward(this, actor_mlp, &actor_on, 1, Mat{xa, Da, xa_h, Da8}, B, bf16, s, true, false);
+        else mlp_forward(this, actor_mlp, &actor_on, 1, Mat{xa, Da, xa_h, Da8}, 2 * B, bf16, s);
         ActorHeadArgs ah{};
         ah.rows = 2 * B; ah.B = B; ah.A = A;
         ah.out = actor_mlp.out; ah.ld_out = 2 * A;
@@ -1186,7 +1199,14 @@ void squint_handle::record_update(int j, int k, cudaStream_t s, bool debug) {
             ah.a_dst1_h = xq_h + Z + P; ah.ld1_h = Dc8;
         }
         ah.logp = logp; ah.eps = eps;
+        if (split_actor) {
+            ActorHeadArgs at = ah;   // the o_t half's sample on s2, after its forward
+            at.row0 = B;
+            ProfScope ps(this, s2, "heads_losses", 0, 1);
+            launch_actor_head(at, s2);
+        }
         {
+            if (split_actor) ah.rows = B;   // the target half
             ProfScope ps(this, s, "heads_losses", 0, 1);
             launch_actor_head(ah, s);
         }

@@ -528,7 +528,7 @@ __device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.f) + log
 // log pi = sum_k [-eps^2/2 - log_std - log(2 pi)/2 - 2 (log 2 - u - softplus(-2u))].
 __global__ void actor_head_kernel(ActorHeadArgs a) {
     SQ_KERNEL_ENTRY();
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = a.row0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= a.rows) return;
     const bool tgt = row < a.B;
     const int el = tgt ? row : row - a.B;
@@ -976,7 +976,7 @@ void launch_colsum(const ColSumProblem* p, int n, cudaStream_t s) {
     }
 }
 void launch_actor_head(const ActorHeadArgs& a, cudaStream_t s) {
-    launch_k(actor_head_kernel, dim3((a.rows + 127) / 128), dim3(128), 0, s, a);
+    if (a.rows > a.row0) launch_k(actor_head_kernel, dim3((a.rows - a.row0 + 127) / 128), dim3(128), 0, s, a);
 }
 void launch_actor_head_bwd(const ActorHeadBwdArgs& a, cudaStream_t s) {
     launch_k(actor_head_bwd_kernel, dim3((a.B + 127) / 128), dim3(128), 0, s, a);

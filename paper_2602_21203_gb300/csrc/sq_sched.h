@@ -99,9 +99,10 @@ struct ProfScope {
 // On the BF16 path the whole chain is one fused launch when its shape allows (each row's
 // result is independent of the other rows there too).
 // keep = false: only the output is needed (no backward through this evaluation), so the
-// hidden layers' activations need not be saved.
+// hidden layers' activations need not be saved.  r0 (one parameter set only): the rows
+// are rows r0 .. r0 + rows of the buffers (outputs and saves), X already pointing at them.
 void mlp_forward(squint_handle* h, MlpBufs& mb, const MlpRef* sets, int E, const Mat& X, int rows, bool bf16,
-                 cudaStream_t s, bool split = true, bool keep = true);
+                 cudaStream_t s, bool split = true, bool keep = true, int r0 = 0);
 // Layer view of canonical layer `ly` in the online parameters (base == params), the
 // target copy (target == true) or an inference snapshot (base == a policy buffer; its
 // BF16 weight copy, if any, is filled in by the caller).

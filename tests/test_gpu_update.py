@@ -567,6 +567,27 @@ def test_actor_step_input_gradients_kept_apart_match_their_gemm_sum(L, monkeypat
     b.close()
 
 
+@pytest.mark.parametrize("name", ["train_b512", "small_b32"])
+def test_actor_forward_in_two_launches_equals_one(L, monkeypatch, name):
+    """The actor's fused forward split in two launches (the target's o_{t+1} half on the
+    critical chain without saved activations, the o_t half with its saves and its sample
+    on a side branch) gives the same bits as one launch over both halves: statistics,
+    parameters and target over three updates (rows are independent in the fused kernel)."""
+    cfg = synth.make_config(name, **({"ring_size": 4096} if name == "train_b512" else {}))
+    ring = synth.make_ring(cfg, 0, device="cuda")
+    monkeypatch.setenv("SQUINT_SPLIT_ACTOR_FWD", "0")
+    a = L.Learner(cfg, ring, precision=L.PREC_BF16, max_k=4)
+    monkeypatch.setenv("SQUINT_SPLIT_ACTOR_FWD", "1")
+    b = L.Learner(cfg, ring, precision=L.PREC_BF16, max_k=4)
+    sa = a.update(3)
+    sb = b.update(3)
+    assert sa == sb
+    assert np.array_equal(a.params(), b.params())
+    assert np.array_equal(a.debug("target"), b.debug("target"))
+    a.close()
+    b.close()
+
+
 # ---------------------------------------------------------------- update timeline
 def test_trace_update_reports_every_launch_on_its_branch(L):
     """The traced update has every launch with 0 <= start <= end, the main stream's
