@@ -45,10 +45,10 @@ UPDATE_FLOPS = 27.96e9
 # in one update; ncu replays each launch with cold caches), keyed by (class,
 # precision).  Set back to nothing when the kernel changes.
 NCU_TRAFFIC = {
-    # train_b512: the four fused head launches of one BF16 update, 8.09 MB read, 0 written
-    # (ncu dram__bytes_read.sum + dram__bytes_write.sum, third update of the small-ring run,
-    # with the clusters of 8 for the actor and target-critic chains)
-    ("mlp_tc_fwd", "bf16", "train_b512"): 2023744,
+    # train_b512: the five fused head launches of one BF16 update (the actor's two halves
+    # apart), 8.98 MB read, 0 written (ncu dram__bytes_read.sum + dram__bytes_write.sum,
+    # third update of the small-ring run)
+    ("mlp_tc_fwd", "bf16", "train_b512"): 1796506,
 }
 
 
